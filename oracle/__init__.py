@@ -1,0 +1,367 @@
+"""FP64 CPU oracle (test infrastructure).
+
+A ctypes binding over ``oracle.c``: a plain, slow, FP64 restatement of the AlGDock BPMF hot path
+(arXiv:1507.03703), written to check the CUDA library against.  Only the tests, the package's
+smoke check and the benchmark's CPU-baseline leg may import this module; the product path never
+does.  It shares no code with the CUDA library.  ``build()`` compiles ``oracle.c`` with gcc.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# Own copies of the unit conventions (A, kcal/mol, amu, fs).
+KB = 0.0019872043                      # kcal/(mol K)
+K_RESTRAINT = 10000.0 / 4.184 / 100.0  # 10000 kJ/(mol nm^2) in kcal/(mol A^2), Eq. (binding_site)
+D0 = 6.0                               # A, binding-site radius
+VMAX_R = 10.0 / 4.184                  # soft repulsive cap: 10 kJ/mol per unit scale factor, in kcal/mol
+
+_d = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_i = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_i64 = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_u32 = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+_u8 = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so next to its source (portable C11, no intrinsics)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-pthread", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    L = C.CDLL(_LIB)
+    L.oracle_philox4x32_10.argtypes = [_u32, _u32, _u32]
+    L.oracle_u53.argtypes = [C.c_uint32, C.c_uint32]
+    L.oracle_u53.restype = C.c_double
+    L.oracle_grid_points.argtypes = [C.c_int, _d, _d, _d, _d, C.c_int64, _d, _d, _d, _d, C.c_int]
+    L.oracle_grid_points.restype = C.c_int
+    L.oracle_grid_direct_sum.argtypes = [C.c_int, _d, _d, _d, _d, _d, C.c_double, _i, _d, _d, _d, C.c_int]
+    L.oracle_grid_direct_sum.restype = C.c_int
+    L.oracle_soft_elec_cap.argtypes = [C.c_double, C.c_int, _d, _d, _d]
+    L.oracle_soft_elec_cap.restype = C.c_double
+    L.oracle_prepare_lattices.argtypes = [C.c_int64, _d, _d, C.c_double, C.c_double, _d, _d, _d]
+    L.oracle_interp.argtypes = [_d, _i, _d, C.c_double, _d, C.POINTER(C.c_double), _d]
+    L.oracle_alpha_sg.argtypes = [C.c_double]
+    L.oracle_alpha_sg.restype = C.c_double
+    L.oracle_alpha_g.argtypes = [C.c_double]
+    L.oracle_alpha_g.restype = C.c_double
+    L.oracle_beta.argtypes = [C.c_double]
+    L.oracle_beta.restype = C.c_double
+    L.oracle_system_create.argtypes = [
+        _i, _d, C.c_double, _d, _d, _d, C.c_double, C.c_double, _d, C.c_double, C.c_double,
+        C.c_int, _d, _d, _d, _d, C.c_int, _i, _d, _d, C.c_int, _i, _d, _d, C.c_int, _i, _d, _d,
+        C.c_int, _d, _d, _d]
+    L.oracle_system_create.restype = C.c_void_p
+    L.oracle_system_destroy.argtypes = [C.c_void_p]
+    L.oracle_system_npairs.argtypes = [C.c_void_p]
+    L.oracle_system_npairs.restype = C.c_int
+    L.oracle_system_pairs.argtypes = [C.c_void_p, _i, _d, _d]
+    L.oracle_state_weights.argtypes = [C.c_void_p, _d, _d, _d]
+    L.oracle_grid_terms.argtypes = [C.c_void_p, _d, _d, C.c_void_p, C.c_void_p]
+    L.oracle_restraint.argtypes = [C.c_void_p, _d, C.c_void_p]
+    L.oracle_restraint.restype = C.c_double
+    L.oracle_ligand_ff.argtypes = [C.c_void_p, _d, C.c_void_p, C.c_void_p]
+    L.oracle_ligand_ff.restype = C.c_double
+    L.oracle_energy_force.argtypes = [C.c_void_p, _d, C.c_double, C.c_double, C.c_void_p, _d]
+    L.oracle_vv.argtypes = [C.c_void_p, _d, _d, C.c_double, C.c_double, C.c_double, C.c_int, C.c_void_p]
+    L.oracle_hmc.argtypes = [C.c_void_p, C.c_int64, _i, C.c_int64, _d, _d, _d, _u8, C.c_int, C.c_uint64,
+                             C.c_uint64, C.c_int]
+    L.oracle_hmc.restype = C.c_int
+    L.oracle_exchange.argtypes = [C.c_int, C.c_int, _d, _d, _d, _i, C.c_int, C.c_int, C.c_uint64,
+                                  C.c_uint64, C.c_int64, _i64, _i64]
+    L.oracle_reduced_energies.argtypes = [C.c_void_p, C.c_int64, _d, C.c_void_p, C.c_void_p]
+    L.oracle_ukn_from_comps.argtypes = [C.c_int, _d, _d, C.c_int64, _d, _d]
+    L.oracle_mbar.argtypes = [C.c_int, C.c_int64, _d, _i64, C.c_double, C.c_int, _d]
+    L.oracle_mbar.restype = C.c_int
+    L.oracle_statistical_inefficiency.argtypes = [C.c_int64, _d]
+    L.oracle_statistical_inefficiency.restype = C.c_double
+    _lib = L
+    return L
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# ------------------------------------------------------------------ primitives
+def philox4x32_10(ctr, key):
+    out = np.zeros(4, dtype=np.uint32)
+    _load().oracle_philox4x32_10(np.asarray(ctr, dtype=np.uint32), np.asarray(key, dtype=np.uint32), out)
+    return out
+
+
+def u53(a: int, b: int) -> float:
+    return _load().oracle_u53(a, b)
+
+
+def alpha_sg(a: float) -> float:
+    return _load().oracle_alpha_sg(float(a))
+
+
+def alpha_g(a: float) -> float:
+    return _load().oracle_alpha_g(float(a))
+
+
+def beta(T: float) -> float:
+    return _load().oracle_beta(float(T))
+
+
+def grid_points(receptor, pts, n_threads: int = 0):
+    pts = _f64(pts).reshape(-1, 3)
+    n = pts.shape[0]
+    ljr, lja, elec = np.empty(n), np.empty(n), np.empty(n)
+    _load().oracle_grid_points(receptor.n_atoms, _f64(receptor.xyz), _f64(receptor.rstar), _f64(receptor.eps),
+                               _f64(receptor.charge), n, pts, ljr, lja, elec, n_threads)
+    return ljr, lja, elec
+
+
+def grid_direct_sum(receptor, grid, n_threads: int = 0):
+    """Raw (untransformed) LJr, LJa and elec grids, each [nz, ny, nx] float64."""
+    nx, ny, nz = grid.n
+    out = [np.empty(nx * ny * nz) for _ in range(3)]
+    _load().oracle_grid_direct_sum(receptor.n_atoms, _f64(receptor.xyz), _f64(receptor.rstar),
+                                   _f64(receptor.eps), _f64(receptor.charge), _f64(grid.origin),
+                                   float(grid.spacing), np.array(grid.n, dtype=np.int32), out[0], out[1],
+                                   out[2], n_threads)
+    return tuple(o.reshape(nz, ny, nx) for o in out)
+
+
+def soft_elec_cap(ligand, vmax_r: float = VMAX_R) -> float:
+    return _load().oracle_soft_elec_cap(vmax_r, ligand.n_atoms, _f64(ligand.rstar), _f64(ligand.eps),
+                                        _f64(ligand.charge))
+
+
+def prepare_lattices(ljr, elec, vmax_r, vmax_e):
+    shp = np.shape(ljr)
+    ljr, elec = _f64(ljr).ravel(), _f64(elec).ravel()
+    a, b, c = np.empty_like(ljr), np.empty_like(ljr), np.empty_like(ljr)
+    _load().oracle_prepare_lattices(ljr.size, ljr, elec, vmax_r, vmax_e, a, b, c)
+    return a.reshape(shp), b.reshape(shp), c.reshape(shp)
+
+
+def interp(L, grid, x):
+    v = C.c_double()
+    g = np.zeros(3)
+    _load().oracle_interp(_f64(L).ravel(), np.array(grid.n, dtype=np.int32), _f64(grid.origin),
+                          float(grid.spacing), _f64(x), C.byref(v), g)
+    return v.value, g
+
+
+class OracleSystem:
+    """Lattices + ligand + restraint + one state table (the oracle's own copy of each)."""
+
+    def __init__(self, grid, ljr, lja, elec, ligand, T, alpha, dt_fs, site=None, vmax_r=VMAX_R,
+                 vmax_e=None, k_rest=K_RESTRAINT, d0=D0):
+        L = _load()
+        self._L = L
+        self.ligand = ligand
+        self.na = ligand.n_atoms
+        if vmax_e is None:
+            vmax_e = soft_elec_cap(ligand, vmax_r)
+        self.vmax_e = vmax_e
+        site = grid.center if site is None else site
+        self.T, self.alpha, self.dt = _f64(T), _f64(alpha), _f64(dt_fs)
+        self.K = int(self.T.size)
+        lg = ligand
+        self._keep = [_f64(ljr).ravel(), _f64(lja).ravel(), _f64(elec).ravel()]
+        self.h = L.oracle_system_create(
+            np.array(grid.n, dtype=np.int32), _f64(grid.origin), float(grid.spacing), self._keep[0],
+            self._keep[1], self._keep[2], float(vmax_r), float(vmax_e), _f64(site), float(k_rest), float(d0),
+            self.na, _f64(lg.mass), _f64(lg.charge), _f64(lg.rstar), _f64(lg.eps), lg.bonds.shape[0],
+            _i32(lg.bonds), _f64(lg.bond_k), _f64(lg.bond_r0), lg.angles.shape[0], _i32(lg.angles),
+            _f64(lg.angle_k), _f64(lg.angle_theta0), lg.torsions.shape[0], _i32(lg.torsions),
+            _f64(lg.torsion_V), _f64(lg.torsion_gamma), self.K, self.T, self.alpha, self.dt)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self._L.oracle_system_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def pairs(self):
+        n = self._L.oracle_system_npairs(self.h)
+        p, sl, se = np.zeros((max(n, 1), 2), dtype=np.int32), np.zeros(max(n, 1)), np.zeros(max(n, 1))
+        self._L.oracle_system_pairs(self.h, p, sl, se)
+        return p[:n], sl[:n], se[:n]
+
+    def state_weights(self):
+        a, b, c = np.zeros(self.K), np.zeros(self.K), np.zeros(self.K)
+        self._L.oracle_state_weights(self.h, a, b, c)
+        return a, b, c
+
+    def grid_terms(self, x):
+        x = _f64(x)
+        psi = np.zeros(2)
+        gs, gg = np.zeros(x.size), np.zeros(x.size)
+        self._L.oracle_grid_terms(self.h, x, psi, _ptr(gs), _ptr(gg))
+        return psi, gs.reshape(-1, 3), gg.reshape(-1, 3)
+
+    def restraint(self, x):
+        x = _f64(x)
+        F = np.zeros(x.size)
+        e = self._L.oracle_restraint(self.h, x, _ptr(F))
+        return e, F.reshape(-1, 3)
+
+    def ligand_ff(self, x):
+        x = _f64(x)
+        F = np.zeros(x.size)
+        terms = np.zeros(4)
+        e = self._L.oracle_ligand_ff(self.h, x, _ptr(F), _ptr(terms))
+        return e, F.reshape(-1, 3), terms
+
+    def energy_force(self, x, w_sg=0.0, w_g=0.0):
+        """Components {U_L, U_I, Psi_sg, Psi_g} and the force of grid weights (w_sg, w_g)."""
+        x = _f64(x)
+        F = np.zeros(x.size)
+        comps = np.zeros(4)
+        self._L.oracle_energy_force(self.h, x, float(w_sg), float(w_g), _ptr(F), comps)
+        return comps, F.reshape(-1, 3)
+
+    def vv(self, x, v, w_sg, w_g, dt, n_steps):
+        """Velocity Verlet at fixed weights.  Returns (x, v, H[0..n_steps])."""
+        x = np.array(x, dtype=np.float64, order="C")
+        v = np.array(v, dtype=np.float64, order="C")
+        H = np.zeros(n_steps + 1)
+        self._L.oracle_vv(self.h, x, v, float(w_sg), float(w_g), float(dt), int(n_steps), _ptr(H))
+        return x, v, H
+
+    def hmc(self, x, state_of, n_steps, seed, cycle, rep_offset=0, n_threads=0):
+        """One HMC trial per replica (in place on a float64 copy).  Returns
+        (x_new, comps [R,4], dH [R], accepted [R] uint8, threads used)."""
+        x = np.array(x, dtype=np.float64, order="C").reshape(-1, self.na, 3)
+        R = x.shape[0]
+        comps, dH, acc = np.zeros((R, 4)), np.zeros(R), np.zeros(R, dtype=np.uint8)
+        nt = self._L.oracle_hmc(self.h, R, _i32(state_of), int(rep_offset), x, comps, dH, acc, int(n_steps),
+                                int(seed), int(cycle), int(n_threads))
+        return x, comps, dH, acc, nt
+
+    def reduced_energies(self, x):
+        x = _f64(x).reshape(-1, self.na, 3)
+        N = x.shape[0]
+        u = np.zeros((self.K, N))
+        comps = np.zeros((N, 4))
+        self._L.oracle_reduced_energies(self.h, N, x, _ptr(u), _ptr(comps))
+        return u, comps
+
+
+def exchange(T, alpha, comps, config_of, n_sweeps, max_sep, seed, cycle, ladder_offset=0):
+    """Replica-exchange sweeps on each ladder.  comps [L, K, 4], config_of [L, K] int32 (copied).
+    Returns (config_of_new, attempts [max_sep, K], accepts [max_sep, K])."""
+    comps = _f64(comps)
+    L_, K = comps.shape[0], comps.shape[1]
+    cfg = np.array(config_of, dtype=np.int32, order="C").reshape(L_, K)
+    att = np.zeros((max_sep, K), dtype=np.int64)
+    acc = np.zeros((max_sep, K), dtype=np.int64)
+    _load().oracle_exchange(L_, K, _f64(T), _f64(alpha), comps, cfg, int(n_sweeps), int(max_sep), int(seed),
+                            int(cycle), int(ladder_offset), att, acc)
+    return cfg, att, acc
+
+
+def ukn_from_comps(T, alpha, comps):
+    comps = _f64(comps).reshape(-1, 4)
+    T = _f64(T)
+    u = np.zeros((T.size, comps.shape[0]))
+    _load().oracle_ukn_from_comps(T.size, T, _f64(alpha), comps.shape[0], comps, u)
+    return u
+
+
+def mbar(u_kn, N_k, tol=1e-10, max_iter=10000):
+    """Returns (f_k, iterations); iterations = -1 if not converged."""
+    u_kn = _f64(u_kn)
+    K, N = u_kn.shape
+    f = np.zeros(K)
+    it = _load().oracle_mbar(K, N, u_kn, np.ascontiguousarray(N_k, dtype=np.int64), float(tol), int(max_iter), f)
+    return f, it
+
+
+def statistical_inefficiency(a):
+    a = _f64(a)
+    return _load().oracle_statistical_inefficiency(a.size, a)
+
+
+def bpmf_kT(f_bc, f_cd):
+    """beta_T B = f_BC,L + f'_CD, each the last-minus-first free energy of its ladder (Estimation)."""
+    return (f_bc[-1] - f_bc[0]) + (f_cd[-1] - f_cd[0])
+
+
+def run_ladder(osys, x0, n_chains, n_cycles, n_steps, seed, n_sweeps=25, max_sep=5, rep_offset=0,
+               ladder_offset=0, burn_in=0, n_threads=0):
+    """Replica-exchange HMC on one ladder (the oracle's own driver of the sampling loop).
+
+    Slot r = c*K + i holds one configuration of chain c; config_of[c, k] is the slot index (within
+    the chain) of the configuration at state k.  Each cycle: one HMC trial per slot at its state,
+    then ``n_sweeps`` exchange sweeps per chain.  After ``burn_in`` cycles every slot's components
+    are recorded with its state.  Returns (comps [S, 4], state [S], acceptance per state [K],
+    exchange accepts / attempts [max_sep, K], final x).
+    """
+    K = osys.K
+    x = np.array(x0, dtype=np.float64).reshape(n_chains * K, osys.na, 3)
+    config_of = np.tile(np.arange(K, dtype=np.int32), (n_chains, 1))
+    samples, states = [], []
+    hmc_acc = np.zeros(K)
+    hmc_n = np.zeros(K)
+    ex_att = np.zeros((max_sep, K), dtype=np.int64)
+    ex_acc = np.zeros((max_sep, K), dtype=np.int64)
+    for cyc in range(n_cycles):
+        state_of = np.empty(n_chains * K, dtype=np.int32)
+        for c in range(n_chains):
+            state_of[c * K + config_of[c]] = np.arange(K, dtype=np.int32)
+        x, comps, dH, acc, _ = osys.hmc(x, state_of, n_steps, seed, cyc, rep_offset=rep_offset,
+                                        n_threads=n_threads)
+        np.add.at(hmc_acc, state_of, acc)
+        np.add.at(hmc_n, state_of, 1)
+        config_of, att, ac = exchange(osys.T, osys.alpha, comps.reshape(n_chains, K, 4), config_of, n_sweeps,
+                                      max_sep, seed, cyc, ladder_offset=ladder_offset)
+        ex_att += att
+        ex_acc += ac
+        if cyc >= burn_in:
+            st = np.empty(n_chains * K, dtype=np.int32)
+            for c in range(n_chains):
+                st[c * K + config_of[c]] = np.arange(K, dtype=np.int32)
+            samples.append(comps.copy())
+            states.append(st)
+    comps = np.concatenate(samples, 0) if samples else np.zeros((0, 4))
+    states = np.concatenate(states, 0) if states else np.zeros(0, dtype=np.int32)
+    return comps, states, hmc_acc / np.maximum(hmc_n, 1), (ex_acc, ex_att), x
+
+
+def ladder_free_energies(T, alpha, comps, states, tol=1e-10, max_iter=10000):
+    """MBAR over all recorded samples of one ladder; f_k with f_0 = 0."""
+    K = len(T)
+    order = np.argsort(states, kind="stable")
+    u = ukn_from_comps(T, alpha, comps[order])
+    N_k = np.bincount(states, minlength=K).astype(np.int64)
+    return mbar(u, N_k, tol=tol, max_iter=max_iter)
