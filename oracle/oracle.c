@@ -115,9 +115,11 @@ static void grid_point(const grid_job* J, const double p[3], double* vr, double*
     double r = sqrt(dx * dx + dy * dy + dz * dz);
     double rr = r < O_R_MIN ? O_R_MIN : r;
     double ra = r < O_R_MIN_ATT ? O_R_MIN_ATT : r;
-    sr += J->sA[j] / pow(rr, 12.0);
-    sa -= J->sB[j] / pow(ra, 6.0);
-    se += J->q[j] / (4.0 * ra * ra); /* distance-dependent dielectric eps(r) = 4 r */
+    double ir2 = 1.0 / (rr * rr), ia2 = 1.0 / (ra * ra);
+    double ir6 = ir2 * ir2 * ir2, ia6 = ia2 * ia2 * ia2;
+    sr += J->sA[j] * (ir6 * ir6); /* 1/r^12 */
+    sa -= J->sB[j] * ia6;         /* 1/r^6 */
+    se += J->q[j] * ia2 / 4.0;    /* distance-dependent dielectric eps(r) = 4 r */
   }
   *vr = sr;
   *va = sa;
