@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the plain BPMF hot path at paper scale on GB300.
+
+Workload (one GPU): a 48-atom synthetic ligand (seed 2), a 4000-atom receptor, three 129^3 grids at
+0.25 A, 32 warming + 96 coupling states, 64 independent chains (8192 replicas).  One step = one HMC
+trial of 50 velocity-Verlet steps for every replica, 25 replica-exchange sweeps on each of the 128
+ladders, and the energy re-evaluation + u_kn of the step's snapshot.  Metric: ligand atom-force
+evaluations per second (replicas x atoms x VV steps / time).  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ligand atom-force evals/s"
+N_STATES_BC, N_STATES_CD, N_CHAINS, N_VV = 32, 96, 64, 50
+FP32_LANES_PER_SM, N_SM = 128, 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-mbar", action="store_true")
+    return p.parse_args()
+
+
+def workload():
+    from paper_1507_03703_gb300 import synthetic as S
+    sys_ = S.config_paper_scale(2)
+    return sys_
+
+
+def workload_config(sys_, n_gpus):
+    lig = sys_.ligand
+    return {"workload": "plain BPMF hot path, paper scale",
+            "ligand_atoms": lig.n_atoms, "receptor_atoms": sys_.receptor.n_atoms,
+            "grid": "3 x 129^3 at 0.25 A (+2 soft)", "states": N_STATES_BC + N_STATES_CD,
+            "chains_per_gpu": N_CHAINS, "replicas_per_gpu": N_CHAINS * (N_STATES_BC + N_STATES_CD),
+            "vv_steps": N_VV, "exchange_sweeps": 25, "max_sep": 5, "parallelism": "chains sharded, dp%d" % n_gpus,
+            "l2": "flushed between steps (256 MB write); steps timed individually"}
+
+
+def flops_per_replica_eval(lig):
+    """Algorithmic FP32 work of one force evaluation of one replica (the roofline's unit):
+    26 per unique nonbonded pair (LJ + Coulomb energy and force on both atoms), 20 per bond,
+    60 per angle, 100 per torsion, 170 per atom for the five interpolated channels and 12 per
+    atom for the velocity-Verlet update."""
+    na = lig.n_atoms
+    nbr = [[] for _ in range(na)]
+    for a, b in lig.bonds:
+        nbr[a].append(b)
+        nbr[b].append(a)
+    n_pairs = 0
+    for i in range(na):
+        dist = {i: 0}
+        frontier = [i]
+        for d in (1, 2):
+            nxt = []
+            for u in frontier:
+                for v in nbr[u]:
+                    if v not in dist:
+                        dist[v] = d
+                        nxt.append(v)
+            frontier = nxt
+        n_pairs += sum(1 for j in range(i + 1, na) if j not in dist)
+    return 26 * n_pairs + 20 * len(lig.bonds) + 60 * len(lig.angles) + 100 * len(lig.torsions) + 182 * na
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            w = [t.strip() for t in line.split(",")]
+            if len(w) < 9:
+                continue
+            try:
+                sm.append(float(w[1]))
+                mx = float(w[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, w[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def oracle_cpu_baseline(sys_, n_rep=256, n_threads=0):
+    """The FP64 oracle as it stands on this host's cores: one HMC trial of 50 VV steps for a
+    bounded sample of replicas spread over all states."""
+    import oracle
+    T = np.concatenate([l.T for l in sys_.legs])
+    alpha = np.concatenate([l.alpha for l in sys_.legs])
+    dt = np.concatenate([l.dt_fs for l in sys_.legs])
+    ljr, lja, elec = oracle.grid_direct_sum(sys_.receptor, sys_.grid)
+    osys = oracle.OracleSystem(sys_.grid, ljr, lja, elec, sys_.ligand, T, alpha, dt, site=sys_.site)
+    from paper_1507_03703_gb300 import synthetic as S
+    x = S.place_ligand(sys_.ligand, sys_.receptor, sys_.site, n_rep, seed=9, n_tries=4).astype(np.float64)
+    states = (np.arange(n_rep) % len(T)).astype(np.int32)
+    t = time.perf_counter()
+    _, _, _, _, used = osys.hmc(x, states, N_VV, 1, 0, n_threads=n_threads)
+    el = time.perf_counter() - t
+    evals = n_rep * sys_.ligand.n_atoms * N_VV
+    return {"value": evals / el, "unit": METRIC, "cores": int(used), "kind": "oracle",
+            "sample": "%d replicas x 1 HMC trial of %d VV steps (all 128 states), %.1f s" % (n_rep, N_VV, el)}
+
+
+def run_reference(args):
+    """The oracle timed as the reference arm: each step is one bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sys_ = workload()
+    import oracle
+    T = np.concatenate([l.T for l in sys_.legs])
+    alpha = np.concatenate([l.alpha for l in sys_.legs])
+    dt = np.concatenate([l.dt_fs for l in sys_.legs])
+    ljr, lja, elec = oracle.grid_direct_sum(sys_.receptor, sys_.grid)
+    osys = oracle.OracleSystem(sys_.grid, ljr, lja, elec, sys_.ligand, T, alpha, dt, site=sys_.site)
+    from paper_1507_03703_gb300 import synthetic as S
+    n_rep = 128
+    x = S.place_ligand(sys_.ligand, sys_.receptor, sys_.site, n_rep, seed=9, n_tries=4).astype(np.float64)
+    states = (np.arange(n_rep) % len(T)).astype(np.int32)
+    used = 1
+    for w in range(args.warmup):
+        x, _, _, _, used = osys.hmc(x, states, N_VV, 1, w)
+    t = time.perf_counter()
+    for s in range(args.steps):
+        x, _, _, _, used = osys.hmc(x, states, N_VV, 1, 1000 + s)
+    el = time.perf_counter() - t
+    evals = n_rep * sys_.ligand.n_atoms * N_VV * args.steps
+    v = evals / el
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_config(sys_, 1), sample="%d replicas per step (all states)" % n_rep),
+        "cpu_baseline": {"value": v, "unit": "evals/s", "cores": int(used), "kind": "oracle",
+                         "sample": "%d replicas x 1 HMC trial of %d VV steps per step" % (n_rep, N_VV)},
+        "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_1507_03703_gb300 import build as B
+    B.build()
+    from paper_1507_03703_gb300 import synthetic as S
+    from paper_1507_03703_gb300.algdock import Context
+    from paper_1507_03703_gb300.sampler import Leg, ReplicaExchange
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sys_ = workload()
+    lig = sys_.ligand
+    T = np.concatenate([l.T for l in sys_.legs])
+    alpha = np.concatenate([l.alpha for l in sys_.legs])
+    dt = np.concatenate([l.dt_fs for l in sys_.legs])
+
+    stream = torch.cuda.current_stream(dev)
+    ctx = Context(local)
+    ctx.set_stream(stream)
+    nx, ny, nz = sys_.grid.n
+    raw = [torch.empty((nz, ny, nx), dtype=torch.float32, device=dev) for _ in range(3)]
+    ctx.grids_build(sys_.grid, sys_.receptor, *raw)
+    ctx.grids_load(sys_.grid, *raw, ligand=lig)
+    ctx.ligand_load(lig, sys_.site)
+    ctx.states_set(T, alpha, dt)
+    del raw
+    legs = [Leg(N_STATES_BC, 0), Leg(N_STATES_CD, N_STATES_BC)]
+    R = N_CHAINS * (N_STATES_BC + N_STATES_CD)
+    base = S.place_ligand(lig, sys_.receptor, sys_.site, 128, seed=100 + rank, n_tries=8).astype(np.float32)
+    x0 = base[np.arange(R) % base.shape[0]]
+    run = ReplicaExchange(ctx, legs, N_CHAINS, x0, seed=1000 + rank)
+    snap = torch.empty((R, 4), dtype=torch.float64, device=dev)
+    u_leg = [torch.empty((l.K, N_CHAINS * l.K), dtype=torch.float64, device=dev) for l in legs]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step(cyc, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        run.hmc(cyc, N_VV)
+        if ev is not None:
+            ev[1].record(stream)
+        run.exchange(cyc)
+        if ev is not None:
+            ev[2].record(stream)
+        for li, leg in enumerate(legs):
+            sl = run.leg_slice(li)
+            ctx.reduced_energies(N_CHAINS * leg.K, x=run.x[sl], comps=snap[sl], k_begin=leg.state_offset,
+                                 k_count=leg.K, u_kn=u_leg[li])
+        if ev is not None:
+            ev[3].record(stream)
+
+    launches_per_step = 1 + len(legs) + 2 * len(legs)  # hmc, exchange per leg, evaluate + u_kn per leg
+    for w in range(args.warmup):
+        step(w)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        step(args.warmup + s, evs[s])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    hmc_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    ex_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    ukn_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    ms_per_step = sum(step_ms) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_per_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    evals_per_step = world * R * lig.n_atoms * N_VV
+    value = evals_per_step / (ms_per_step * 1e-3)
+
+    # roofline of the dominant kernel (the fused HMC trial), FP32 ALU bound
+    peaks = measured_peaks()
+    sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fl = flops_per_replica_eval(lig) * R * (N_VV + 1)
+    hmc_avg = sum(hmc_ms) / len(hmc_ms)
+    achieved = fl / (hmc_avg * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "hmc_kernel", "kernel_ms": hmc_avg,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_max,
+                "flops_per_launch": fl}
+
+    # end to end through the C ABI with host buffers: pinned host -> device, step, device -> host
+    h_x = torch.empty((R, lig.n_atoms, 3), dtype=torch.float32, pin_memory=True)
+    h_x.copy_(run.x.cpu())
+    h_out = torch.empty_like(h_x).pin_memory()
+    h_c = torch.empty((R, 4), dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    es.record(stream)
+    for s in range(e2e_steps):
+        run.x.copy_(h_x, non_blocking=True)
+        step(10_000 + s)
+        h_out.copy_(run.x, non_blocking=True)
+        h_c.copy_(run.comps, non_blocking=True)
+    ee.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = es.elapsed_time(ee) / e2e_steps
+    e2e = {"value": world * R * lig.n_atoms * N_VV / (e2e_ms * 1e-3), "unit": "evals/s",
+           "h2d_bytes_per_step": int(h_x.numel() * 4), "d2h_bytes_per_step": int(h_out.numel() * 4 + h_c.numel() * 8)}
+
+    extra = {}
+    if not args.no_mbar and rank == 0:
+        # MBAR over K = 128 states and ~1e5 samples recorded from the run
+        n_snap = (100_000 + R - 1) // R
+        comps_hist = torch.empty((n_snap, R, 4), dtype=torch.float64, device=dev)
+        for s in range(n_snap):
+            run.cycle(20_000 + s, N_VV)
+            comps_hist[s].copy_(run.comps)
+        N = n_snap * R
+        u = torch.empty((len(T), N), dtype=torch.float64, device=dev)
+        ctx.reduced_energies(N, comps=comps_hist.reshape(N, 4), k_begin=0, k_count=len(T), u_kn=u)
+        N_k = np.full(len(T), N // len(T), dtype=np.int64)
+        for mode, key in ((0, "fp64"), (1, "fp32exp")):
+            ctx.mbar(u, N_k, tol=1e-300, max_iter=2, precision_mode=mode, raise_on_nonconvergence=False)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ctx.mbar(u, N_k, tol=1e-300, max_iter=50, precision_mode=mode, raise_on_nonconvergence=False)
+            el = time.perf_counter() - t
+            extra["mbar_%s_iters_per_s" % key] = 50 / el
+        f, it = ctx.mbar(u, N_k, tol=1e-10, max_iter=20000)
+        extra["mbar_K"], extra["mbar_N"], extra["mbar_iters_to_1e-10"] = len(T), N, it
+
+    acc = run.counters.cpu().numpy()
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(sys_, world),
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk, "breakdown_ms": {"hmc": hmc_avg, "exchange": sum(ex_ms) / len(ex_ms),
+                                        "snapshot_ukn": sum(ukn_ms) / len(ukn_ms), "wall_per_step_incl_flush":
+                                        1e3 * wall / args.steps},
+        "hmc_cycles_per_s": 1e3 / ms_per_step,
+        "hmc_acceptance": float(acc[0]) / max(1, R * (args.warmup + args.steps + e2e_steps)),
+    }
+    line.update(extra)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_cpu_baseline(sys_)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

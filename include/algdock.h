@@ -1,0 +1,206 @@
+/*
+ * algdock.h - C ABI of the GB300 (sm_103a) library for the hot path of AlGDock's binding potential
+ * of mean force (BPMF) method: Hamiltonian Monte Carlo of a flexible ligand against a rigid
+ * receptor represented by interpolation grids, over many thermodynamic states at once, with
+ * Hamiltonian replica exchange, reduced-energy (u_kn) evaluation and MBAR.
+ * Paper: D. D. L. Minh, "Alchemical Grid Dock (AlGDock): Binding Free Energy Calculations between
+ * Flexible Ligands and Rigid Receptors", arXiv:1507.03703.
+ *
+ * Conventions for every call:
+ *  - Units: A, kcal/mol, amu, fs, K, elementary charge.
+ *  - Every call returns algdock_status (ALGDOCK_OK = 0).  No C++ exception crosses the ABI.
+ *    On failure algdock_last_error(ctx) returns a message owned by the context, valid until the
+ *    next call on that context.
+ *  - Array arguments are owned by the caller.  Unless stated otherwise they must be DEVICE
+ *    pointers on the context's device (e.g. torch CUDA tensors' data_ptr()); arguments marked
+ *    "host or device" are detected with cudaPointerGetAttributes.  Arrays are C-contiguous.
+ *  - Work is enqueued on the stream set by algdock_set_stream (default: the legacy stream) and is
+ *    asynchronous unless a call returns host scalars (then it synchronises that stream).
+ *  - The context copies grids, ligand and state tables into device memory it owns.
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef ALGDOCK_H
+#define ALGDOCK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ALGDOCK_OK = 0,
+  ALGDOCK_E_INVALID = 1,       /* bad argument: null pointer, size, shape, missing setup */
+  ALGDOCK_E_CUDA = 2,          /* a CUDA runtime call failed */
+  ALGDOCK_E_OOM = 3,           /* device allocation failed */
+  ALGDOCK_E_NUMERIC = 4,       /* non-finite input where a finite one is required */
+  ALGDOCK_E_NOT_CONVERGED = 5, /* MBAR reached max_iter */
+  ALGDOCK_E_STATE = 6          /* call order: grids, ligand or states not loaded */
+} algdock_status;
+
+typedef struct algdock_ctx algdock_ctx;
+
+/* A regular lattice: node (i, j, k) at origin + spacing * (i, j, k); arrays are [nz][ny][nx]
+ * (x fastest).  Each n >= 2. */
+typedef struct {
+  double origin[3];
+  double spacing;
+  int32_t n[3];
+} algdock_grid_desc;
+
+/* Ligand topology and parameters (host pointers; copied by algdock_ligand_load).
+ * Sampling force field ("Thermodynamic Cycle"; GAFF-like):
+ *   bonds     k (r - r0)^2;   angles  k (theta - theta0)^2 (theta0 in rad);
+ *   torsions  sum_{n=1..3} V_n/2 (1 + cos(n phi - gamma_n)), V and gamma [n_torsions][3];
+ *   nonbonded pairs more than two bonds apart, no cutoff: eps_ij [(R_ij/r)^12 - 2 (R_ij/r)^6]
+ *     + 332.0637 q_i q_j / r with eps_ij = sqrt(eps_i eps_j), R_ij = R*_i + R*_j; pairs exactly
+ *     three bonds apart (1-4) scaled by 1/2 (LJ) and 1/1.2 (Coulomb).
+ * Receptor-ligand grid factors per atom: sqrt(A_i) = sqrt(eps_i) (2 R*_i)^6 for the repulsive
+ * grid, sqrt(B_i) = sqrt(2 eps_i) (2 R*_i)^3 for the attractive grid, q_i for the electrostatic.
+ * Index arrays are 0-based int32: bonds [n][2], angles [n][3] (centre in the middle),
+ * torsions [n][4].  1 <= n_atoms <= 96. */
+typedef struct {
+  int32_t n_atoms;
+  const double* mass;
+  const double* charge;
+  const double* rstar;
+  const double* eps;
+  int32_t n_bonds;
+  const int32_t* bonds;
+  const double* bond_k;
+  const double* bond_r0;
+  int32_t n_angles;
+  const int32_t* angles;
+  const double* angle_k;
+  const double* angle_theta0;
+  int32_t n_torsions;
+  const int32_t* torsions;
+  const double* torsion_V;
+  const double* torsion_gamma;
+} algdock_ligand;
+
+/* Flat-bottom harmonic restraint on the ligand centre of mass, Eq. (binding_site):
+ * U_I = 0 if d <= d0, else k/2 (d - d0)^2, d = |COM - site|.  The paper's k = 10000 kJ/(mol nm^2)
+ * is 23.9006 kcal/(mol A^2); d0 = 6 A. */
+typedef struct {
+  double site[3];
+  double k;
+  double d0;
+} algdock_restraint;
+
+/* Counters written by algdock_hmc_cycle (added to, not overwritten). */
+enum {
+  ALGDOCK_CNT_ACCEPTED = 0,  /* HMC trials accepted */
+  ALGDOCK_CNT_NONFINITE = 1, /* trials whose total energy change was not finite (rejected) */
+  ALGDOCK_CNT_OUTSIDE = 2,   /* atom evaluations clamped to the lattice boundary */
+  ALGDOCK_N_COUNTERS = 4
+};
+
+/* ---------------------------------------------------------------- lifecycle */
+algdock_status algdock_create(int device, algdock_ctx** out);
+void algdock_destroy(algdock_ctx* ctx);
+/* stream: a cudaStream_t (NULL = legacy default stream). */
+algdock_status algdock_set_stream(algdock_ctx* ctx, void* stream);
+const char* algdock_last_error(const algdock_ctx* ctx);
+
+/* ---------------------------------------------------------------- grids */
+/* Raw receptor grids by direct summation over receptor atoms j at every node p (the paper solves
+ * the electrostatic grid with APBS; here a direct Coulomb sum with a distance-dependent
+ * dielectric 4r stands in for it) - "Thermodynamic Cycle", electrostatic and van der Waals grids:
+ *   LJr(p)  = sum_j sqrt(A_j) / r^12          (r >= 0.01 A)
+ *   LJa(p)  = -sum_j sqrt(B_j) / r^6          (r >= 2 A)
+ *   elec(p) = 332.0637 sum_j q_j / (4 r^2)    (r >= 2 A)
+ * Receptor arrays (host or device, double): xyz [n_rec][3], rstar, eps, q [n_rec].
+ * Outputs ljr, lja, elec: device float [nz][ny][nx].  Terms in FP32, sums in FP64. */
+algdock_status algdock_grids_build(algdock_ctx* ctx, const algdock_grid_desc* desc, int32_t n_rec,
+                                   const double* rec_xyz, const double* rec_rstar, const double* rec_eps,
+                                   const double* rec_q, float* ljr, float* lja, float* elec);
+
+/* Soft electrostatic cap for a ligand ("Thermodynamic Cycle", soft grids):
+ * v_e = vmax_r * min over charged atoms of sqrt(A_i)/|q_i|, so that every atom's electrostatic
+ * energy on the soft grid is bounded by its soft repulsive cap.  +inf if no atom is charged.
+ * Host-only arithmetic; needs no context. */
+algdock_status algdock_soft_elec_cap(const algdock_ligand* lig, double vmax_r, double* vmax_e);
+
+/* Load raw grids (host or device float [nz][ny][nx], energies per unit scale factor) and derive
+ * the interpolated lattices ("Thermodynamic Cycle"): the repulsive grid stored as its 4th root
+ * (values capped at 1e10 first), the attractive and electrostatic grids as given, and the soft
+ * grids vmax_r tanh(LJr/vmax_r) (stored as its 4th root) and vmax_e tanh(elec/vmax_e).  The
+ * paper's vmax_r is 10 kJ/mol = 2.3901 kcal/mol per unit factor; vmax_e from
+ * algdock_soft_elec_cap (infinite = no cap).  The derivation runs in FP64; lattices are FP32. */
+algdock_status algdock_grids_load(algdock_ctx* ctx, const algdock_grid_desc* desc, const float* ljr,
+                                  const float* lja, const float* elec, double vmax_r, double vmax_e);
+
+/* ---------------------------------------------------------------- ligand and states */
+algdock_status algdock_ligand_load(algdock_ctx* ctx, const algdock_ligand* lig, const algdock_restraint* rest);
+
+/* K thermodynamic states (host arrays): temperature T (K), alchemical progress alpha, and the
+ * velocity-Verlet time step dt (fs).  Eq. (protocol): the grid weights are
+ *   alpha_sg = 1 - (2 alpha - 1)^2,  alpha_g = (2 alpha - 1)^2 / (1 + exp(-1000 (alpha - 1/2))),
+ * and u_k(x) = (U_L + U_I + alpha_sg Psi_sg + alpha_g Psi_g) / (k_B T_k).  alpha = NaN marks a
+ * state without receptor grids (the warming leg B -> C). */
+algdock_status algdock_states_set(algdock_ctx* ctx, int32_t K, const double* T, const double* alpha,
+                                  const double* dt_fs);
+
+/* ---------------------------------------------------------------- sampling */
+/* One HMC trial for each of n_rep replicas ("Sampling": HMC with n_steps of velocity Verlet and
+ * the Metropolis criterion on H = kinetic + U_k).  Replica r is at state state_of[r] (int32,
+ * index into the state table).  Momenta are drawn from N(0, k_B T / m) with Philox4x32-10 keyed
+ * by seed, counter {atom, rep_offset + r, cycle, 1}; the acceptance uniform from counter
+ * {0, rep_offset + r, cycle, 2}.  Energies are FP32 per term and summed in FP64; the energy
+ * change and the accept test are FP64.
+ *   x        [n_rep][n_atoms][3] float, in/out: the new configuration, or the old one if rejected
+ *   comps    [n_rep][4] double out: {U_L, U_I, Psi_sg, Psi_g} of the returned configuration
+ *   dH       [n_rep] double out (may be NULL): total energy change of the trial (kcal/mol)
+ *   accepted [n_rep] uint8 out (may be NULL)
+ *   counters [ALGDOCK_N_COUNTERS] int64 (may be NULL): accumulated, see ALGDOCK_CNT_*  */
+algdock_status algdock_hmc_cycle(algdock_ctx* ctx, int64_t n_rep, const int32_t* state_of, float* x,
+                                 double* comps, double* dH, uint8_t* accepted, int32_t n_steps, uint64_t seed,
+                                 uint64_t cycle, int64_t rep_offset, int64_t* counters);
+
+/* Energy and force of N configurations, each at its state ("Thermodynamic Cycle": grid
+ * interaction energy and sampling force field; Eq. (binding_site); Eq. (protocol) weights), with
+ * the arithmetic of one velocity-Verlet force evaluation inside algdock_hmc_cycle.
+ *   state_of [N] int32, x [N][n_atoms][3] float (device)
+ *   force    [N][n_atoms][3] float out: -dU_k/dx, U_k = U_L + U_I + alpha_sg Psi_sg + alpha_g Psi_g
+ *   comps    [N][4] double out (may be NULL): {U_L, U_I, Psi_sg, Psi_g} */
+algdock_status algdock_energy_force(algdock_ctx* ctx, int64_t N, const int32_t* state_of, const float* x,
+                                    float* force, double* comps);
+
+/* Hamiltonian replica exchange ("Sampling", Eq. (repXacc)) on n_ladders independent ladders of K
+ * consecutive states [state_offset, state_offset + K).  config_of [n_ladders][K] int32 (in/out):
+ * the slot (0..K-1) holding the configuration at each state; comps [n_ladders][K][4] double: the
+ * components of each slot; state_of [n_ladders][K] int32 (out, may be NULL): the new state of each
+ * slot, state_offset + k, in the form algdock_hmc_cycle reads.  One sweep attempts, for s = 1..min(max_sep, K-1) and colour 0 then 1,
+ * every pair (a, a+s) with floor(a/s) % 2 == colour, accepting if
+ * u < exp(-[u_a(y) + u_b(x) - u_a(x) - u_b(y)]) in FP64, u from Philox counter
+ * {(sweep*max_sep + s-1)*65536 + a, ladder_offset + l, cycle, 3}.  Requires K <= 1024 and
+ * n_sweeps*max_sep < 65536.  attempts / accepts [max_sep][K] int64 (may be NULL) are added to. */
+algdock_status algdock_exchange(algdock_ctx* ctx, int32_t n_ladders, int32_t K, int32_t state_offset,
+                                const double* comps, int32_t* config_of, int32_t* state_of, int32_t n_sweeps,
+                                int32_t max_sep, uint64_t seed, uint64_t cycle, int64_t ladder_offset,
+                                int64_t* attempts, int64_t* accepts);
+
+/* ---------------------------------------------------------------- estimation */
+/* Reduced energies for MBAR ("Estimation").  If x ([N][n_atoms][3] float) is given, the energy
+ * path evaluates each configuration's components into comps ([N][4] double, may then be NULL);
+ * if x is NULL, comps is read.  If u_kn is given it receives, for the k_count states starting at
+ * k_begin, u_kn[k][n] = (((U_L + U_I) + alpha_sg Psi_sg) + alpha_g Psi_g) / (k_B T_k) in FP64
+ * ([k_count][N] double). */
+algdock_status algdock_reduced_energies(algdock_ctx* ctx, int64_t N, const float* x, double* comps,
+                                        int32_t k_begin, int32_t k_count, double* u_kn);
+
+/* MBAR (Shirts & Chodera 2008, cited in "Estimation") by self-consistent iteration in log-sum-exp
+ * form from f = 0, with gauge f_0 = 0:
+ *   f_i <- -ln sum_n exp(-u_in) / sum_k N_k exp(f_k - u_kn)
+ * until max_i |change| < tol or max_iter iterations.  u_kn [K][N] double (device), N_k [K] int64
+ * (host).  precision_mode 0: FP64 throughout; 1: exponentials in FP32 of FP64 arguments, sums in
+ * FP64.  f_k [K] (host) and iters (host) receive the result.  Synchronises.  Returns
+ * ALGDOCK_E_NOT_CONVERGED (with the last iterate in f_k) if max_iter is reached. */
+algdock_status algdock_mbar(algdock_ctx* ctx, int32_t K, int64_t N, const double* u_kn, const int64_t* N_k,
+                            double tol, int32_t max_iter, int32_t precision_mode, double* f_k, int32_t* iters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ALGDOCK_H */

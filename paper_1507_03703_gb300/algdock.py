@@ -1,0 +1,294 @@
+"""Thin ctypes binding of libalgdock (include/algdock.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  Arrays are torch CUDA
+tensors (device pointers) or, where the C call accepts host memory, numpy arrays.  The library must
+have been built (``paper_1507_03703_gb300.build.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libalgdock.so")
+
+OK, E_INVALID, E_CUDA, E_OOM, E_NUMERIC, E_NOT_CONVERGED, E_STATE = range(7)
+CNT_ACCEPTED, CNT_NONFINITE, CNT_OUTSIDE = 0, 1, 2
+N_COUNTERS = 4
+
+# Unit conventions of the C ABI: A, kcal/mol, amu, fs, K.
+K_RESTRAINT = 10000.0 / 4.184 / 100.0  # 10000 kJ/(mol nm^2) in kcal/(mol A^2)
+D0 = 6.0
+VMAX_R = 10.0 / 4.184                  # 10 kJ/mol per unit scale factor, in kcal/mol
+
+EXPORTS = [
+    "algdock_create", "algdock_destroy", "algdock_set_stream", "algdock_last_error", "algdock_grids_build",
+    "algdock_soft_elec_cap", "algdock_grids_load", "algdock_ligand_load", "algdock_states_set",
+    "algdock_hmc_cycle", "algdock_energy_force", "algdock_exchange", "algdock_reduced_energies", "algdock_mbar",
+]
+
+
+class AlgdockError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("algdock status %d: %s" % (status, msg))
+        self.status = status
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("spacing", C.c_double), ("n", C.c_int32 * 3)]
+
+
+class LigandC(C.Structure):
+    _fields_ = [("n_atoms", C.c_int32), ("mass", C.c_void_p), ("charge", C.c_void_p), ("rstar", C.c_void_p),
+                ("eps", C.c_void_p), ("n_bonds", C.c_int32), ("bonds", C.c_void_p), ("bond_k", C.c_void_p),
+                ("bond_r0", C.c_void_p), ("n_angles", C.c_int32), ("angles", C.c_void_p),
+                ("angle_k", C.c_void_p), ("angle_theta0", C.c_void_p), ("n_torsions", C.c_int32),
+                ("torsions", C.c_void_p), ("torsion_V", C.c_void_p), ("torsion_gamma", C.c_void_p)]
+
+
+class RestraintC(C.Structure):
+    _fields_ = [("site", C.c_double * 3), ("k", C.c_double), ("d0", C.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libalgdock.so and declare its signatures.  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libalgdock.so not built: run paper_1507_03703_gb300.build.build() (needs nvcc)")
+    L = C.CDLL(path)
+    vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+    sig = {
+        "algdock_create": ([C.c_int, C.POINTER(vp)], C.c_int),
+        "algdock_destroy": ([vp], None),
+        "algdock_set_stream": ([vp, vp], C.c_int),
+        "algdock_last_error": ([vp], C.c_char_p),
+        "algdock_grids_build": ([vp, C.POINTER(GridDesc), i32, vp, vp, vp, vp, vp, vp, vp], C.c_int),
+        "algdock_soft_elec_cap": ([C.POINTER(LigandC), dbl, C.POINTER(dbl)], C.c_int),
+        "algdock_grids_load": ([vp, C.POINTER(GridDesc), vp, vp, vp, dbl, dbl], C.c_int),
+        "algdock_ligand_load": ([vp, C.POINTER(LigandC), C.POINTER(RestraintC)], C.c_int),
+        "algdock_states_set": ([vp, i32, vp, vp, vp], C.c_int),
+        "algdock_hmc_cycle": ([vp, i64, vp, vp, vp, vp, vp, i32, u64, u64, i64, vp], C.c_int),
+        "algdock_energy_force": ([vp, i64, vp, vp, vp, vp], C.c_int),
+        "algdock_exchange": ([vp, i32, i32, i32, vp, vp, vp, i32, i32, u64, u64, i64, vp, vp], C.c_int),
+        "algdock_reduced_energies": ([vp, i64, vp, vp, i32, i32, vp], C.c_int),
+        "algdock_mbar": ([vp, i32, i64, vp, vp, dbl, i32, i32, vp, C.POINTER(i32)], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _dev(t, dtype=None, name="array"):
+    """Device pointer of a contiguous torch CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a torch CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
+    return t.data_ptr()
+
+
+def _any(a, np_dtype, torch_dtype, name):
+    """Pointer to a host numpy array or a device tensor; returns (ptr, keepalive)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda:
+                return _dev(a, torch_dtype, name), a
+            a = a.numpy()
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a, dtype=np_dtype)
+    return arr.ctypes.data, arr
+
+
+def ligand_struct(lig):
+    """Build the C ligand description from any object with the fields of algdock_ligand."""
+    keep = []
+
+    def f64(a):
+        arr = np.ascontiguousarray(a, dtype=np.float64)
+        keep.append(arr)
+        return arr.ctypes.data
+
+    def i32(a, w):
+        arr = np.ascontiguousarray(np.asarray(a).reshape(-1, w), dtype=np.int32)
+        keep.append(arr)
+        return arr.ctypes.data
+
+    s = LigandC()
+    s.n_atoms = int(len(lig.mass))
+    s.mass, s.charge, s.rstar, s.eps = f64(lig.mass), f64(lig.charge), f64(lig.rstar), f64(lig.eps)
+    s.n_bonds = int(np.asarray(lig.bonds).reshape(-1, 2).shape[0])
+    s.bonds, s.bond_k, s.bond_r0 = i32(lig.bonds, 2), f64(lig.bond_k), f64(lig.bond_r0)
+    s.n_angles = int(np.asarray(lig.angles).reshape(-1, 3).shape[0])
+    s.angles, s.angle_k, s.angle_theta0 = i32(lig.angles, 3), f64(lig.angle_k), f64(lig.angle_theta0)
+    s.n_torsions = int(np.asarray(lig.torsions).reshape(-1, 4).shape[0])
+    s.torsions, s.torsion_V, s.torsion_gamma = i32(lig.torsions, 4), f64(lig.torsion_V), f64(lig.torsion_gamma)
+    return s, keep
+
+
+def soft_elec_cap(lig, vmax_r: float = VMAX_R) -> float:
+    L = load_library()
+    s, keep = ligand_struct(lig)
+    out = C.c_double()
+    st = L.algdock_soft_elec_cap(C.byref(s), float(vmax_r), C.byref(out))
+    if st != OK:
+        raise AlgdockError(st, "soft_elec_cap: invalid ligand")
+    return out.value
+
+
+def grid_desc(grid) -> GridDesc:
+    d = GridDesc()
+    for k in range(3):
+        d.origin[k] = float(grid.origin[k])
+        d.n[k] = int(grid.n[k])
+    d.spacing = float(grid.spacing)
+    return d
+
+
+class Context:
+    """One algdock_ctx on a CUDA device.  Method names follow the C calls without the prefix."""
+
+    def __init__(self, device: int = 0):
+        self._L = load_library()
+        h = C.c_void_p()
+        st = self._L.algdock_create(int(device), C.byref(h))
+        if st != OK:
+            raise AlgdockError(st, "algdock_create(%d) failed" % device)
+        self.h = h
+        self.device = device
+        self.n_atoms = None
+        self.K = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.algdock_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            raise AlgdockError(st, self._L.algdock_last_error(self.h).decode())
+        return st
+
+    def last_error(self) -> str:
+        return self._L.algdock_last_error(self.h).decode()
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream (or None for the legacy default stream)."""
+        ptr = None if stream is None else C.c_void_p(stream.cuda_stream)
+        self._check(self._L.algdock_set_stream(self.h, ptr))
+
+    # ---------------------------------------------------------------- grids
+    def grids_build(self, grid, receptor, ljr, lja, elec):
+        """Direct-sum raw grids into device float tensors [nz, ny, nx]."""
+        d = grid_desc(grid)
+        px, kx = _any(receptor.xyz, np.float64, None, "xyz")
+        pr, kr = _any(receptor.rstar, np.float64, None, "rstar")
+        pe, ke = _any(receptor.eps, np.float64, None, "eps")
+        pq, kq = _any(receptor.charge, np.float64, None, "q")
+        import torch
+        n = int(np.asarray(receptor.rstar).shape[0])
+        self._check(self._L.algdock_grids_build(self.h, C.byref(d), n, px, pr, pe, pq,
+                                                _dev(ljr, torch.float32, "ljr"), _dev(lja, torch.float32, "lja"),
+                                                _dev(elec, torch.float32, "elec")))
+
+    def grids_load(self, grid, ljr, lja, elec, vmax_r=VMAX_R, vmax_e=None, ligand=None):
+        """Raw grids (numpy float32 host arrays or CUDA float32 tensors).  vmax_e defaults to the
+        soft electrostatic cap of `ligand`."""
+        import torch
+        if vmax_e is None:
+            vmax_e = soft_elec_cap(ligand, vmax_r) if ligand is not None else math.inf
+        d = grid_desc(grid)
+        p1, k1 = _any(ljr, np.float32, torch.float32, "ljr")
+        p2, k2 = _any(lja, np.float32, torch.float32, "lja")
+        p3, k3 = _any(elec, np.float32, torch.float32, "elec")
+        self._check(self._L.algdock_grids_load(self.h, C.byref(d), p1, p2, p3, float(vmax_r), float(vmax_e)))
+
+    # ---------------------------------------------------------------- ligand and states
+    def ligand_load(self, lig, site, k=K_RESTRAINT, d0=D0):
+        s, keep = ligand_struct(lig)
+        r = RestraintC()
+        for i in range(3):
+            r.site[i] = float(site[i])
+        r.k, r.d0 = float(k), float(d0)
+        self._check(self._L.algdock_ligand_load(self.h, C.byref(s), C.byref(r)))
+        self.n_atoms = s.n_atoms
+
+    def states_set(self, T, alpha, dt_fs):
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        a = np.ascontiguousarray(alpha, dtype=np.float64)
+        dt = np.ascontiguousarray(dt_fs, dtype=np.float64)
+        if not (T.shape == a.shape == dt.shape) or T.ndim != 1:
+            raise ValueError("T, alpha, dt must be 1-D of equal length")
+        self._check(self._L.algdock_states_set(self.h, T.size, T.ctypes.data, a.ctypes.data, dt.ctypes.data))
+        self.K = int(T.size)
+
+    # ---------------------------------------------------------------- sampling
+    def hmc_cycle(self, state_of, x, comps, dH=None, accepted=None, n_steps=50, seed=0, cycle=0, rep_offset=0,
+                  counters=None):
+        import torch
+        n_rep = int(state_of.numel())
+        self._check(self._L.algdock_hmc_cycle(
+            self.h, n_rep, _dev(state_of, torch.int32, "state_of"), _dev(x, torch.float32, "x"),
+            _dev(comps, torch.float64, "comps"), _dev(dH, torch.float64, "dH"),
+            _dev(accepted, torch.uint8, "accepted"), int(n_steps), int(seed), int(cycle), int(rep_offset),
+            _dev(counters, torch.int64, "counters")))
+
+    def energy_force(self, state_of, x, force, comps=None):
+        import torch
+        self._check(self._L.algdock_energy_force(
+            self.h, int(state_of.numel()), _dev(state_of, torch.int32, "state_of"), _dev(x, torch.float32, "x"),
+            _dev(force, torch.float32, "force"), _dev(comps, torch.float64, "comps")))
+
+    def exchange(self, K, state_offset, comps, config_of, state_of=None, n_sweeps=25, max_sep=5, seed=0, cycle=0,
+                 ladder_offset=0, attempts=None, accepts=None):
+        import torch
+        n_ladders = int(config_of.numel()) // int(K)
+        self._check(self._L.algdock_exchange(
+            self.h, n_ladders, int(K), int(state_offset), _dev(comps, torch.float64, "comps"),
+            _dev(config_of, torch.int32, "config_of"), _dev(state_of, torch.int32, "state_of"), int(n_sweeps),
+            int(max_sep), int(seed), int(cycle), int(ladder_offset), _dev(attempts, torch.int64, "attempts"),
+            _dev(accepts, torch.int64, "accepts")))
+
+    # ---------------------------------------------------------------- estimation
+    def reduced_energies(self, N, x=None, comps=None, k_begin=0, k_count=0, u_kn=None):
+        import torch
+        self._check(self._L.algdock_reduced_energies(
+            self.h, int(N), _dev(x, torch.float32, "x"), _dev(comps, torch.float64, "comps"), int(k_begin),
+            int(k_count), _dev(u_kn, torch.float64, "u_kn")))
+
+    def mbar(self, u_kn, N_k, tol=1e-10, max_iter=10000, precision_mode=0, raise_on_nonconvergence=True):
+        """Returns (f_k numpy [K], iterations)."""
+        import torch
+        K, N = int(u_kn.shape[0]), int(u_kn.shape[1])
+        Nk = np.ascontiguousarray(N_k, dtype=np.int64)
+        f = np.zeros(K)
+        it = C.c_int32()
+        st = self._L.algdock_mbar(self.h, K, N, _dev(u_kn, torch.float64, "u_kn"), Nk.ctypes.data, float(tol),
+                                  int(max_iter), int(precision_mode), f.ctypes.data, C.byref(it))
+        if st == E_NOT_CONVERGED and not raise_on_nonconvergence:
+            return f, -1
+        self._check(st)
+        return f, it.value

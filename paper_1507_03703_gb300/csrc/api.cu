@@ -1,0 +1,581 @@
+// C ABI of libalgdock: argument checking, device-memory ownership, host-side preparation of the
+// ligand tables and state weights, and dispatch to the kernels.  See include/algdock.h.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace algdock {
+size_t mbar_scratch_bytes(int K, int64_t N);
+int mbar_run(cudaStream_t s, void* scratch, int K, int64_t N, const double* u_kn, const int64_t* Nk_host,
+             double tol, int max_iter, int mode, double* f_host, int* iters, int* h_flag, cudaError_t* err);
+}  // namespace algdock
+
+using namespace algdock;
+
+namespace {
+
+algdock_status fail(algdock_ctx* c, algdock_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+algdock_status cuda_fail(algdock_ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation) return fail(c, ALGDOCK_E_OOM, std::string(where) + ": out of device memory");
+  return fail(c, ALGDOCK_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define ALGDOCK_TRY(c) \
+  if (!(c)) return ALGDOCK_E_INVALID; \
+  try {
+#define ALGDOCK_CATCH(c)                                                   \
+  }                                                                        \
+  catch (const std::bad_alloc&) {                                          \
+    return fail(c, ALGDOCK_E_OOM, "host allocation failed");               \
+  }                                                                        \
+  catch (...) {                                                            \
+    return fail(c, ALGDOCK_E_INVALID, "unexpected exception");             \
+  }
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Device {
+  int prev = -1;
+  explicit Device(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~Device() {
+    int cur;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// A device copy of `bytes` from p (host or device); returns the device pointer to use and fills
+// `owned` if a temporary was allocated (freed by the caller after the stream is synchronised).
+cudaError_t device_view(cudaStream_t s, const void* p, size_t bytes, const void** out, void** owned) {
+  *owned = nullptr;
+  if (is_device_ptr(p)) {
+    *out = p;
+    return cudaSuccess;
+  }
+  void* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, bytes ? bytes : 1);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return e;
+  }
+  *owned = d;
+  *out = d;
+  return cudaSuccess;
+}
+
+// Host copy of a (host or device) double array.
+cudaError_t host_view(cudaStream_t s, const double* p, size_t n, std::vector<double>& out) {
+  out.resize(n);
+  if (n == 0) return cudaSuccess;
+  if (is_device_ptr(p)) {
+    cudaError_t e = cudaMemcpyAsync(out.data(), p, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+  }
+  memcpy(out.data(), p, n * sizeof(double));
+  return cudaSuccess;
+}
+
+double alpha_sg_of(double a) {
+  if (isnan(a)) return 0.0;
+  const double s = 2.0 * a - 1.0;
+  return 1.0 - s * s;
+}
+double alpha_g_of(double a) {
+  if (isnan(a)) return 0.0;
+  const double s = 2.0 * a - 1.0;
+  const double z = 1000.0 * (a - 0.5);
+  // logistic 1/(1 + e^{-z}) in the form that cannot overflow
+  const double logistic = z >= 0.0 ? 1.0 / (1.0 + exp(-z)) : exp(z) / (1.0 + exp(z));
+  return s * s * logistic;
+}
+
+double sqrtA(double rstar, double eps) {
+  const double t = 2.0 * rstar;
+  return sqrt(eps) * (t * t * t * t * t * t);
+}
+
+}  // namespace
+
+extern "C" {
+
+algdock_status algdock_create(int device, algdock_ctx** out) {
+  if (!out) return ALGDOCK_E_INVALID;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return ALGDOCK_E_CUDA;
+  }
+  algdock_ctx* c = new (std::nothrow) algdock_ctx();
+  if (!c) return ALGDOCK_E_OOM;
+  c->device = device;
+  Device g(device);
+  if (cudaMallocHost(&c->h_flag, sizeof(int)) != cudaSuccess) {
+    delete c;
+    return ALGDOCK_E_CUDA;
+  }
+  *out = c;
+  return ALGDOCK_OK;
+}
+
+void algdock_destroy(algdock_ctx* c) {
+  if (!c) return;
+  Device g(c->device);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->d_hard);
+  cudaFree(c->d_soft);
+  cudaFree(c->d_blob);
+  cudaFree(c->d_states);
+  cudaFree(c->d_mbar);
+  cudaFreeHost(c->h_flag);
+  delete c;
+}
+
+algdock_status algdock_set_stream(algdock_ctx* c, void* stream) {
+  if (!c) return ALGDOCK_E_INVALID;
+  c->stream = (cudaStream_t)stream;
+  return ALGDOCK_OK;
+}
+
+const char* algdock_last_error(const algdock_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+algdock_status algdock_soft_elec_cap(const algdock_ligand* lig, double vmax_r, double* vmax_e) {
+  if (!lig || !vmax_e || lig->n_atoms < 1 || !lig->rstar || !lig->eps || !lig->charge) return ALGDOCK_E_INVALID;
+  double best = INFINITY;
+  for (int i = 0; i < lig->n_atoms; ++i) {
+    if (lig->charge[i] == 0.0) continue;
+    const double r = sqrtA(lig->rstar[i], lig->eps[i]) / fabs(lig->charge[i]);
+    if (r < best) best = r;
+  }
+  *vmax_e = vmax_r * best;
+  return ALGDOCK_OK;
+}
+
+algdock_status algdock_grids_build(algdock_ctx* c, const algdock_grid_desc* d, int32_t n_rec, const double* xyz,
+                                   const double* rstar, const double* eps, const double* q, float* ljr, float* lja,
+                                   float* elec) {
+  ALGDOCK_TRY(c)
+  if (!d || n_rec < 0 || (n_rec > 0 && (!xyz || !rstar || !eps || !q)) || !ljr || !lja || !elec)
+    return fail(c, ALGDOCK_E_INVALID, "grids_build: null argument");
+  if (d->n[0] < 2 || d->n[1] < 2 || d->n[2] < 2 || !(d->spacing > 0))
+    return fail(c, ALGDOCK_E_INVALID, "grids_build: lattice needs n >= 2 and spacing > 0");
+  if (!is_device_ptr(ljr) || !is_device_ptr(lja) || !is_device_ptr(elec))
+    return fail(c, ALGDOCK_E_INVALID, "grids_build: outputs must be device pointers");
+  Device g(c->device);
+  std::vector<double> hx, hr, he, hq;
+  cudaError_t e = host_view(c->stream, xyz, 3 * (size_t)n_rec, hx);
+  if (e == cudaSuccess) e = host_view(c->stream, rstar, n_rec, hr);
+  if (e == cudaSuccess) e = host_view(c->stream, eps, n_rec, he);
+  if (e == cudaSuccess) e = host_view(c->stream, q, n_rec, hq);
+  if (e != cudaSuccess) return cuda_fail(c, e, "grids_build");
+  for (int j = 0; j < n_rec; ++j)
+    if (!isfinite(hx[3 * j]) || !isfinite(hx[3 * j + 1]) || !isfinite(hx[3 * j + 2]) || !isfinite(hr[j]) ||
+        !isfinite(he[j]) || !isfinite(hq[j]) || he[j] < 0)
+      return fail(c, ALGDOCK_E_NUMERIC, "grids_build: non-finite or negative receptor parameter");
+  e = launch_grid_build(c->stream, *d, n_rec, hx.data(), hr.data(), he.data(), hq.data(), ljr, lja, elec);
+  if (e != cudaSuccess) return cuda_fail(c, e, "grids_build");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_grids_load(algdock_ctx* c, const algdock_grid_desc* d, const float* ljr, const float* lja,
+                                  const float* elec, double vmax_r, double vmax_e) {
+  ALGDOCK_TRY(c)
+  if (!d || !ljr || !lja || !elec) return fail(c, ALGDOCK_E_INVALID, "grids_load: null argument");
+  if (d->n[0] < 2 || d->n[1] < 2 || d->n[2] < 2 || !(d->spacing > 0))
+    return fail(c, ALGDOCK_E_INVALID, "grids_load: lattice needs n >= 2 and spacing > 0");
+  if (!(vmax_r > 0) || !(vmax_e > 0)) return fail(c, ALGDOCK_E_INVALID, "grids_load: caps must be > 0");
+  for (int k = 0; k < 3; ++k)
+    if ((float)d->origin[k] != d->origin[k])
+      return fail(c, ALGDOCK_E_INVALID, "grids_load: origin must be exactly representable in FP32");
+  const size_t n = (size_t)d->n[0] * d->n[1] * d->n[2];
+  if (n > ((size_t)1 << 31)) return fail(c, ALGDOCK_E_INVALID, "grids_load: lattice too large");
+  Device g(c->device);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "grids_load");
+  if (n != c->grid_nodes) {
+    cudaFree(c->d_hard);
+    cudaFree(c->d_soft);
+    c->d_hard = nullptr;
+    c->d_soft = nullptr;
+    c->has_grid = false;
+    e = cudaMalloc(&c->d_hard, n * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_soft, n * sizeof(float2));
+    if (e != cudaSuccess) return cuda_fail(c, e, "grids_load");
+    c->grid_nodes = n;
+  }
+  const void *pr, *pa, *pe;
+  void *or_ = nullptr, *oa = nullptr, *oe = nullptr;
+  e = device_view(c->stream, ljr, n * 4, &pr, &or_);
+  if (e == cudaSuccess) e = device_view(c->stream, lja, n * 4, &pa, &oa);
+  if (e == cudaSuccess) e = device_view(c->stream, elec, n * 4, &pe, &oe);
+  if (e == cudaSuccess)
+    e = launch_grid_prepare(c->stream, n, (const float*)pr, (const float*)pa, (const float*)pe, vmax_r, vmax_e,
+                            c->d_hard, c->d_soft);
+  if (or_ || oa || oe) {
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = e2;
+    cudaFree(or_);
+    cudaFree(oa);
+    cudaFree(oe);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "grids_load");
+  GridDev G;
+  G.hard = c->d_hard;
+  G.soft = c->d_soft;
+  G.nx = d->n[0];
+  G.ny = d->n[1];
+  G.nz = d->n[2];
+  G.ox = (float)d->origin[0];
+  G.oy = (float)d->origin[1];
+  G.oz = (float)d->origin[2];
+  G.inv_h = (float)(1.0 / d->spacing);
+  c->grid = G;
+  c->has_grid = true;
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, const algdock_restraint* R) {
+  ALGDOCK_TRY(c)
+  if (!L || !R) return fail(c, ALGDOCK_E_INVALID, "ligand_load: null argument");
+  const int na = L->n_atoms, nb = L->n_bonds, nang = L->n_angles, ntor = L->n_torsions;
+  if (na < 1 || na > kMaxAtoms) return fail(c, ALGDOCK_E_INVALID, "ligand_load: need 1 <= n_atoms <= 96");
+  if (nb < 0 || nang < 0 || ntor < 0) return fail(c, ALGDOCK_E_INVALID, "ligand_load: negative term count");
+  if (!L->mass || !L->charge || !L->rstar || !L->eps || (nb && (!L->bonds || !L->bond_k || !L->bond_r0)) ||
+      (nang && (!L->angles || !L->angle_k || !L->angle_theta0)) ||
+      (ntor && (!L->torsions || !L->torsion_V || !L->torsion_gamma)))
+    return fail(c, ALGDOCK_E_INVALID, "ligand_load: null array");
+  auto bad_idx = [&](const int32_t* idx, int n, int w) {
+    for (int t = 0; t < n * w; ++t)
+      if (idx[t] < 0 || idx[t] >= na) return true;
+    return false;
+  };
+  if (bad_idx(L->bonds, nb, 2) || bad_idx(L->angles, nang, 3) || bad_idx(L->torsions, ntor, 4))
+    return fail(c, ALGDOCK_E_INVALID, "ligand_load: atom index out of range");
+  double M = 0.0;
+  for (int i = 0; i < na; ++i) {
+    if (!(L->mass[i] > 0) || !isfinite(L->mass[i]) || !isfinite(L->charge[i]) || !isfinite(L->rstar[i]) ||
+        !(L->eps[i] >= 0) || !isfinite(L->eps[i]))
+      return fail(c, ALGDOCK_E_NUMERIC, "ligand_load: non-finite or invalid atom parameter");
+    M += L->mass[i];
+  }
+  for (int t = 0; t < nb; ++t)
+    if (!isfinite(L->bond_k[t]) || !isfinite(L->bond_r0[t])) return fail(c, ALGDOCK_E_NUMERIC, "ligand_load: bond");
+  for (int t = 0; t < nang; ++t)
+    if (!isfinite(L->angle_k[t]) || !isfinite(L->angle_theta0[t]))
+      return fail(c, ALGDOCK_E_NUMERIC, "ligand_load: angle");
+  for (int t = 0; t < 3 * ntor; ++t)
+    if (!isfinite(L->torsion_V[t]) || !isfinite(L->torsion_gamma[t]))
+      return fail(c, ALGDOCK_E_NUMERIC, "ligand_load: torsion");
+  if (!isfinite(R->k) || !isfinite(R->d0) || !isfinite(R->site[0]) || !isfinite(R->site[1]) || !isfinite(R->site[2]))
+    return fail(c, ALGDOCK_E_NUMERIC, "ligand_load: restraint");
+
+  // graph distances (breadth-first over the bonds): exclusions within two bonds, 1-4 at three
+  std::vector<std::vector<int>> nbr(na);
+  for (int t = 0; t < nb; ++t) {
+    nbr[L->bonds[2 * t]].push_back(L->bonds[2 * t + 1]);
+    nbr[L->bonds[2 * t + 1]].push_back(L->bonds[2 * t]);
+  }
+  std::vector<uint32_t> excl(4 * na, 0u), one4(4 * na, 0u);
+  std::vector<int> dist(na), queue(na);
+  for (int i = 0; i < na; ++i) {
+    std::fill(dist.begin(), dist.end(), -1);
+    dist[i] = 0;
+    int h = 0, t = 0;
+    queue[t++] = i;
+    while (h < t) {
+      const int u = queue[h++];
+      if (dist[u] >= 3) continue;
+      for (int v : nbr[u])
+        if (dist[v] < 0) {
+          dist[v] = dist[u] + 1;
+          queue[t++] = v;
+        }
+    }
+    for (int j = 0; j < na; ++j) {
+      if (dist[j] >= 0 && dist[j] <= 2) excl[4 * i + j / 32] |= 1u << (j % 32);
+      else if (dist[j] == 3) one4[4 * i + j / 32] |= 1u << (j % 32);
+    }
+  }
+  // per-atom incidence lists of bonded terms (type << 30 | role << 28 | term)
+  std::vector<std::vector<uint32_t>> inc(na);
+  for (int t = 0; t < nb; ++t)
+    for (int r = 0; r < 2; ++r) inc[L->bonds[2 * t + r]].push_back((0u << 30) | ((uint32_t)r << 28) | (uint32_t)t);
+  for (int t = 0; t < nang; ++t)
+    for (int r = 0; r < 3; ++r) inc[L->angles[3 * t + r]].push_back((1u << 30) | ((uint32_t)r << 28) | (uint32_t)t);
+  for (int t = 0; t < ntor; ++t)
+    for (int r = 0; r < 4; ++r)
+      inc[L->torsions[4 * t + r]].push_back((2u << 30) | ((uint32_t)r << 28) | (uint32_t)t);
+  int ninc = 0;
+  for (auto& v : inc) ninc += (int)v.size();
+
+  LigandLayout Y;
+  memset(&Y, 0, sizeof(Y));
+  Y.na = na;
+  Y.nb = nb;
+  Y.nang = nang;
+  Y.ntor = ntor;
+  Y.ninc = ninc;
+  int w = 0;
+  auto take = [&](int words) {
+    const int o = w;
+    w += (words + 3) & ~3;
+    return o;
+  };
+  Y.off_atom_a = take(4 * na);
+  Y.off_atom_b = take(4 * na);
+  Y.off_excl = take(4 * na);
+  Y.off_one4 = take(4 * na);
+  Y.off_bond = take(4 * nb);
+  Y.off_ang = take(8 * nang);
+  Y.off_tor = take(16 * ntor);
+  Y.off_inc_start = take(na + 1);
+  Y.off_inc = take(ninc);
+  Y.words = w;
+  if ((size_t)w * 4 > 120 * 1024) return fail(c, ALGDOCK_E_INVALID, "ligand_load: topology too large");
+  std::vector<uint32_t> blob(w, 0u);
+  float* bf = (float*)blob.data();
+  int32_t* bi = (int32_t*)blob.data();
+  for (int i = 0; i < na; ++i) {
+    const double m = L->mass[i];
+    const double two_r = 2.0 * L->rstar[i];
+    bf[Y.off_atom_a + 4 * i + 0] = (float)(kForceToAccel / m);
+    bf[Y.off_atom_a + 4 * i + 1] = (float)L->charge[i];
+    bf[Y.off_atom_a + 4 * i + 2] = (float)sqrtA(L->rstar[i], L->eps[i]);
+    bf[Y.off_atom_a + 4 * i + 3] = (float)(sqrt(2.0 * L->eps[i]) * two_r * two_r * two_r);
+    bf[Y.off_atom_b + 4 * i + 0] = (float)L->rstar[i];
+    bf[Y.off_atom_b + 4 * i + 1] = (float)sqrt(L->eps[i]);
+    bf[Y.off_atom_b + 4 * i + 2] = (float)m;
+    bf[Y.off_atom_b + 4 * i + 3] = (float)sqrt(kForceToAccel / m);
+    for (int k = 0; k < 4; ++k) {
+      blob[Y.off_excl + 4 * i + k] = excl[4 * i + k];
+      blob[Y.off_one4 + 4 * i + k] = one4[4 * i + k];
+    }
+  }
+  for (int t = 0; t < nb; ++t) {
+    bi[Y.off_bond + 4 * t + 0] = L->bonds[2 * t];
+    bi[Y.off_bond + 4 * t + 1] = L->bonds[2 * t + 1];
+    bf[Y.off_bond + 4 * t + 2] = (float)L->bond_k[t];
+    bf[Y.off_bond + 4 * t + 3] = (float)L->bond_r0[t];
+  }
+  for (int t = 0; t < nang; ++t) {
+    for (int k = 0; k < 3; ++k) bi[Y.off_ang + 4 * t + k] = L->angles[3 * t + k];
+    bf[Y.off_ang + 4 * nang + 4 * t + 0] = (float)L->angle_k[t];
+    bf[Y.off_ang + 4 * nang + 4 * t + 1] = (float)L->angle_theta0[t];
+  }
+  for (int t = 0; t < ntor; ++t) {
+    for (int k = 0; k < 4; ++k) bi[Y.off_tor + 4 * t + k] = L->torsions[4 * t + k];
+    for (int n = 0; n < 3; ++n) {
+      const double g = L->torsion_gamma[3 * t + n];
+      bf[Y.off_tor + 4 * ntor + 4 * t + n] = (float)(0.5 * L->torsion_V[3 * t + n]);
+      bf[Y.off_tor + 8 * ntor + 4 * t + n] = (float)cos(g);
+      bf[Y.off_tor + 12 * ntor + 4 * t + n] = (float)sin(g);
+    }
+  }
+  int pos = 0;
+  for (int i = 0; i < na; ++i) {
+    bi[Y.off_inc_start + i] = pos;
+    for (uint32_t code : inc[i]) blob[Y.off_inc + pos++] = code;
+  }
+  bi[Y.off_inc_start + na] = pos;
+  Y.total_mass = (float)M;
+  for (int k = 0; k < 3; ++k) Y.site[k] = (float)R->site[k];
+  Y.k_rest = (float)R->k;
+  Y.d0 = (float)R->d0;
+
+  Device g(c->device);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ligand_load");
+  cudaFree(c->d_blob);
+  c->d_blob = nullptr;
+  c->has_ligand = false;
+  e = cudaMalloc(&c->d_blob, (size_t)w * 4);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_blob, blob.data(), (size_t)w * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ligand_load");
+  c->lig = Y;
+  c->has_ligand = true;
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_states_set(algdock_ctx* c, int32_t K, const double* T, const double* alpha,
+                                  const double* dt_fs) {
+  ALGDOCK_TRY(c)
+  if (K < 1 || !T || !alpha || !dt_fs) return fail(c, ALGDOCK_E_INVALID, "states_set: bad arguments");
+  std::vector<StateDev> h(K);
+  for (int k = 0; k < K; ++k) {
+    if (!(T[k] > 0) || !isfinite(T[k]) || !(dt_fs[k] >= 0) || !isfinite(dt_fs[k]) ||
+        (!isnan(alpha[k]) && !isfinite(alpha[k])))
+      return fail(c, ALGDOCK_E_INVALID, "states_set: need T > 0, dt >= 0, finite alpha or NaN");
+    StateDev s;
+    s.kT = kBoltzmann * T[k];
+    s.beta = 1.0 / (kBoltzmann * T[k]);
+    s.w_sg = alpha_sg_of(alpha[k]);
+    s.w_g = alpha_g_of(alpha[k]);
+    s.w_sg_f = (float)s.w_sg;
+    s.w_g_f = (float)s.w_g;
+    s.dt = (float)dt_fs[k];
+    s.sqrt_kT = (float)sqrt(s.kT);
+    h[k] = s;
+  }
+  Device g(c->device);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "states_set");
+  cudaFree(c->d_states);
+  c->d_states = nullptr;
+  c->K = 0;
+  e = cudaMalloc(&c->d_states, sizeof(StateDev) * K);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_states, h.data(), sizeof(StateDev) * K, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(c, e, "states_set");
+  c->K = K;
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_hmc_cycle(algdock_ctx* c, int64_t n_rep, const int32_t* state_of, float* x, double* comps,
+                                 double* dH, uint8_t* accepted, int32_t n_steps, uint64_t seed, uint64_t cycle,
+                                 int64_t rep_offset, int64_t* counters) {
+  ALGDOCK_TRY(c)
+  if (!c->has_grid || !c->has_ligand || c->K == 0)
+    return fail(c, ALGDOCK_E_STATE, "hmc_cycle: load grids, ligand and states first");
+  if (n_rep < 0 || n_steps < 0 || rep_offset < 0) return fail(c, ALGDOCK_E_INVALID, "hmc_cycle: negative size");
+  if (n_rep == 0) return ALGDOCK_OK;
+  if (!is_device_ptr(state_of) || !is_device_ptr(x) || !is_device_ptr(comps) || (dH && !is_device_ptr(dH)) ||
+      (accepted && !is_device_ptr(accepted)) || (counters && !is_device_ptr(counters)))
+    return fail(c, ALGDOCK_E_INVALID, "hmc_cycle: arrays must be device pointers");
+  Device g(c->device);
+  cudaError_t e = launch_hmc(c->stream, *c, n_rep, state_of, x, comps, dH, accepted, n_steps, seed, cycle,
+                             rep_offset, counters);
+  if (e != cudaSuccess) return cuda_fail(c, e, "hmc_cycle");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_energy_force(algdock_ctx* c, int64_t N, const int32_t* state_of, const float* x, float* force,
+                                    double* comps) {
+  ALGDOCK_TRY(c)
+  if (!c->has_grid || !c->has_ligand || c->K == 0)
+    return fail(c, ALGDOCK_E_STATE, "energy_force: load grids, ligand and states first");
+  if (N < 0) return fail(c, ALGDOCK_E_INVALID, "energy_force: N < 0");
+  if (N == 0) return ALGDOCK_OK;
+  if (!is_device_ptr(state_of) || !is_device_ptr(x) || !is_device_ptr(force) || (comps && !is_device_ptr(comps)))
+    return fail(c, ALGDOCK_E_INVALID, "energy_force: arrays must be device pointers");
+  Device g(c->device);
+  cudaError_t e = launch_energy_force(c->stream, *c, N, state_of, x, force, comps);
+  if (e != cudaSuccess) return cuda_fail(c, e, "energy_force");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_exchange(algdock_ctx* c, int32_t n_ladders, int32_t K, int32_t state_offset,
+                                const double* comps, int32_t* config_of, int32_t* state_of, int32_t n_sweeps,
+                                int32_t max_sep, uint64_t seed, uint64_t cycle, int64_t ladder_offset,
+                                int64_t* attempts, int64_t* accepts) {
+  ALGDOCK_TRY(c)
+  if (c->K == 0) return fail(c, ALGDOCK_E_STATE, "exchange: set states first");
+  if (n_ladders < 0 || K < 1 || K > kMaxLadder || state_offset < 0 || state_offset + K > c->K || n_sweeps < 0 ||
+      max_sep < 1 || (int64_t)n_sweeps * max_sep >= 65536 || ladder_offset < 0)
+    return fail(c, ALGDOCK_E_INVALID, "exchange: bad sizes");
+  if (n_ladders == 0) return ALGDOCK_OK;
+  if (!is_device_ptr(comps) || !is_device_ptr(config_of) || (state_of && !is_device_ptr(state_of)) ||
+      (attempts && !is_device_ptr(attempts)) ||
+      (accepts && !is_device_ptr(accepts)))
+    return fail(c, ALGDOCK_E_INVALID, "exchange: arrays must be device pointers");
+  Device g(c->device);
+  cudaError_t e = launch_exchange(c->stream, *c, n_ladders, K, state_offset, comps, config_of, state_of, n_sweeps,
+                                  max_sep, seed, cycle, ladder_offset, attempts, accepts);
+  if (e != cudaSuccess) return cuda_fail(c, e, "exchange");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_reduced_energies(algdock_ctx* c, int64_t N, const float* x, double* comps, int32_t k_begin,
+                                        int32_t k_count, double* u_kn) {
+  ALGDOCK_TRY(c)
+  if (N < 0) return fail(c, ALGDOCK_E_INVALID, "reduced_energies: N < 0");
+  if (N == 0) return ALGDOCK_OK;
+  if (!x && !comps) return fail(c, ALGDOCK_E_INVALID, "reduced_energies: need x or comps");
+  if (u_kn && (k_begin < 0 || k_count < 0 || k_begin + k_count > c->K))
+    return fail(c, ALGDOCK_E_INVALID, "reduced_energies: state range outside the state table");
+  if (x && (!c->has_grid || !c->has_ligand)) return fail(c, ALGDOCK_E_STATE, "reduced_energies: load grids and ligand");
+  if ((x && !is_device_ptr(x)) || (comps && !is_device_ptr(comps)) || (u_kn && !is_device_ptr(u_kn)))
+    return fail(c, ALGDOCK_E_INVALID, "reduced_energies: arrays must be device pointers");
+  Device g(c->device);
+  cudaError_t e = cudaSuccess;
+  double* tmp = nullptr;
+  double* cp = comps;
+  if (x) {
+    if (!cp) {
+      e = cudaMallocAsync(&tmp, (size_t)N * 4 * sizeof(double), c->stream);
+      cp = tmp;
+    }
+    if (e == cudaSuccess) e = launch_evaluate(c->stream, *c, N, x, cp);
+  }
+  if (e == cudaSuccess && u_kn) e = launch_ukn(c->stream, *c, N, cp, k_begin, k_count, u_kn);
+  if (tmp) cudaFreeAsync(tmp, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reduced_energies");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_mbar(algdock_ctx* c, int32_t K, int64_t N, const double* u_kn, const int64_t* N_k, double tol,
+                            int32_t max_iter, int32_t precision_mode, double* f_k, int32_t* iters) {
+  ALGDOCK_TRY(c)
+  if (K < 1 || N < 1 || !u_kn || !N_k || !f_k || !iters || max_iter < 1 || !(tol > 0) ||
+      (precision_mode != 0 && precision_mode != 1))
+    return fail(c, ALGDOCK_E_INVALID, "mbar: bad arguments");
+  if (!is_device_ptr(u_kn)) return fail(c, ALGDOCK_E_INVALID, "mbar: u_kn must be a device pointer");
+  int64_t total = 0;
+  for (int k = 0; k < K; ++k) {
+    if (N_k[k] < 0) return fail(c, ALGDOCK_E_INVALID, "mbar: negative N_k");
+    total += N_k[k];
+  }
+  if (total != N) return fail(c, ALGDOCK_E_INVALID, "mbar: sum of N_k must equal N");
+  Device g(c->device);
+  const size_t need = mbar_scratch_bytes(K, N);
+  if (need > c->mbar_bytes) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mbar");
+    cudaFree(c->d_mbar);
+    c->d_mbar = nullptr;
+    c->mbar_bytes = 0;
+    e = cudaMalloc(&c->d_mbar, need);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mbar");
+    c->mbar_bytes = need;
+  }
+  cudaError_t err = cudaSuccess;
+  int it = 0;
+  const int r = mbar_run(c->stream, c->d_mbar, K, N, u_kn, N_k, tol, max_iter, precision_mode, f_k, &it, c->h_flag,
+                         &err);
+  *iters = it;
+  if (r < 0) return cuda_fail(c, err, "mbar");
+  if (r == 1) return fail(c, ALGDOCK_E_NOT_CONVERGED, "mbar: max_iter reached");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+}  // extern "C"

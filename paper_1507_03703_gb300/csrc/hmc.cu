@@ -1,0 +1,768 @@
+// The fused HMC trial ("Sampling"): momentum draw, n_steps of velocity Verlet over the grid
+// interaction energy ("Thermodynamic Cycle"), the ligand force field and the flat-bottom
+// restraint (Eq. (binding_site)), then the Metropolis test on the total energy change.
+//
+// Layout: one warp per replica; lane l owns atoms l, l+32, l+64 (APL = atoms per lane).  Positions,
+// velocities and forces of owned atoms stay in registers for the whole trajectory; the current
+// positions are mirrored in a per-warp shared-memory array so that every lane can read every atom.
+// The ligand's parameters and topology are staged once per CTA in shared memory.  Every force
+// is accumulated by the lane that owns the atom (no atomics), so results are deterministic.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace algdock {
+namespace {
+
+constexpr int kWarpsPerBlock = 4;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct Lig {
+  const float4* atom_a;  // (accel factor 4.184e-4/m, q, sqrt(A), sqrt(B))
+  const float4* atom_b;  // (R*, sqrt(eps), m, sqrt(accel factor))
+  const uint4* excl;
+  const uint4* one4;
+  const float4* bond;
+  const int4* ang_i;
+  const float4* ang_p;
+  const int4* tor_i;
+  const float4* tor_v;
+  const float4* tor_c;
+  const float4* tor_s;
+  const int* inc_start;
+  const uint32_t* inc;
+};
+
+__device__ inline Lig bind_ligand(const uint32_t* s, const LigandLayout& L) {
+  Lig g;
+  g.atom_a = (const float4*)(s + L.off_atom_a);
+  g.atom_b = (const float4*)(s + L.off_atom_b);
+  g.excl = (const uint4*)(s + L.off_excl);
+  g.one4 = (const uint4*)(s + L.off_one4);
+  g.bond = (const float4*)(s + L.off_bond);
+  g.ang_i = (const int4*)(s + L.off_ang);
+  g.ang_p = (const float4*)(s + L.off_ang + 4 * L.nang);
+  g.tor_i = (const int4*)(s + L.off_tor);
+  g.tor_v = (const float4*)(s + L.off_tor + 4 * L.ntor);
+  g.tor_c = (const float4*)(s + L.off_tor + 8 * L.ntor);
+  g.tor_s = (const float4*)(s + L.off_tor + 12 * L.ntor);
+  g.inc_start = (const int*)(s + L.off_inc_start);
+  g.inc = (const uint32_t*)(s + L.off_inc);
+  return g;
+}
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ inline float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Lattice coordinate of x along one axis.  x - o is formed exactly as s + e (two-sum), so the
+// fractional offset keeps FP32 precision relative to the cell even far from the origin.
+__device__ inline void axis_coord(float x, float o, float inv_h, int n, int& c, float& t, bool& inside) {
+  const float a = x, b = -o;
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  float u = s * inv_h;
+  const float ue = e * inv_h;
+  inside = true;
+  float fl = floorf(u);
+  float frac = (u - fl) + ue;
+  if (!(u + ue >= 0.f)) {  // below the lattice, or NaN
+    fl = 0.f;
+    frac = 0.f;
+    inside = false;
+  } else if (fl + frac >= (float)(n - 1)) {
+    fl = (float)(n - 2);
+    frac = 1.f;
+    if (u + ue > (float)(n - 1)) inside = false;
+  } else if (frac >= 1.f) {  // ue pushed the offset into the next cell
+    fl += 1.f;
+    frac -= 1.f;
+  } else if (frac < 0.f) {
+    fl -= 1.f;
+    frac += 1.f;
+  }
+  c = (int)fl;
+  t = frac;
+}
+
+// Trilinear value and gradient (in lattice units) of one channel from 8 corner values,
+// c[dz][dy][dx].
+struct Tri {
+  float v, gx, gy, gz;
+};
+__device__ inline Tri tri(const float c000, const float c001, const float c010, const float c011, const float c100,
+                          const float c101, const float c110, const float c111, float tx, float ty, float tz) {
+  // along x
+  const float a00 = fmaf(tx, c001 - c000, c000), d00 = c001 - c000;
+  const float a01 = fmaf(tx, c011 - c010, c010), d01 = c011 - c010;
+  const float a10 = fmaf(tx, c101 - c100, c100), d10 = c101 - c100;
+  const float a11 = fmaf(tx, c111 - c110, c110), d11 = c111 - c110;
+  // along y
+  const float b0 = fmaf(ty, a01 - a00, a00), bx0 = fmaf(ty, d01 - d00, d00), by0 = a01 - a00;
+  const float b1 = fmaf(ty, a11 - a10, a10), bx1 = fmaf(ty, d11 - d10, d10), by1 = a11 - a10;
+  Tri r;
+  r.v = fmaf(tz, b1 - b0, b0);
+  r.gx = fmaf(tz, bx1 - bx0, bx0);
+  r.gy = fmaf(tz, by1 - by0, by0);
+  r.gz = b1 - b0;
+  return r;
+}
+
+struct GridOut {
+  float e_g, e_sg;         // Psi_g, Psi_sg contributions of this atom
+  float fx, fy, fz;        // -(w_sg dPsi_sg + w_g dPsi_g)/dx
+  bool outside;
+};
+
+// Grid energies and forces of one atom.  hard / soft select which lattices are read.
+__device__ inline GridOut grid_atom(const GridDev& G, float x, float y, float z, float sA, float sB, float q,
+                                    bool hard, bool soft, float w_sg, float w_g) {
+  GridOut o{0.f, 0.f, 0.f, 0.f, 0.f, false};
+  int cx, cy, cz;
+  float tx, ty, tz;
+  bool ix, iy, iz;
+  axis_coord(x, G.ox, G.inv_h, G.nx, cx, tx, ix);
+  axis_coord(y, G.oy, G.inv_h, G.ny, cy, ty, iy);
+  axis_coord(z, G.oz, G.inv_h, G.nz, cz, tz, iz);
+  o.outside = !(ix && iy && iz);
+  const float mx = ix ? G.inv_h : 0.f, my = iy ? G.inv_h : 0.f, mz = iz ? G.inv_h : 0.f;
+  const int64_t sx = 1, sy = G.nx, sz = (int64_t)G.nx * G.ny;
+  const int64_t b = (int64_t)cz * sz + (int64_t)cy * sy + cx;
+  float gxs = 0.f, gys = 0.f, gzs = 0.f;
+  if (hard) {
+    const float4 c000 = __ldg(G.hard + b), c001 = __ldg(G.hard + b + sx);
+    const float4 c010 = __ldg(G.hard + b + sy), c011 = __ldg(G.hard + b + sy + sx);
+    const float4 c100 = __ldg(G.hard + b + sz), c101 = __ldg(G.hard + b + sz + sx);
+    const float4 c110 = __ldg(G.hard + b + sz + sy), c111 = __ldg(G.hard + b + sz + sy + sx);
+    const Tri r = tri(c000.x, c001.x, c010.x, c011.x, c100.x, c101.x, c110.x, c111.x, tx, ty, tz);
+    const Tri a = tri(c000.y, c001.y, c010.y, c011.y, c100.y, c101.y, c110.y, c111.y, tx, ty, tz);
+    const Tri e = tri(c000.z, c001.z, c010.z, c011.z, c100.z, c101.z, c110.z, c111.z, tx, ty, tz);
+    const float r2 = r.v * r.v;
+    o.e_g = sA * (r2 * r2) + sB * a.v + q * e.v;
+    const float cr = 4.f * sA * r2 * r.v;
+    if (w_g != 0.f) {
+      gxs += w_g * (cr * r.gx + sB * a.gx + q * e.gx);
+      gys += w_g * (cr * r.gy + sB * a.gy + q * e.gy);
+      gzs += w_g * (cr * r.gz + sB * a.gz + q * e.gz);
+    }
+  }
+  if (soft) {
+    const float2 c000 = __ldg(G.soft + b), c001 = __ldg(G.soft + b + sx);
+    const float2 c010 = __ldg(G.soft + b + sy), c011 = __ldg(G.soft + b + sy + sx);
+    const float2 c100 = __ldg(G.soft + b + sz), c101 = __ldg(G.soft + b + sz + sx);
+    const float2 c110 = __ldg(G.soft + b + sz + sy), c111 = __ldg(G.soft + b + sz + sy + sx);
+    const Tri r = tri(c000.x, c001.x, c010.x, c011.x, c100.x, c101.x, c110.x, c111.x, tx, ty, tz);
+    const Tri e = tri(c000.y, c001.y, c010.y, c011.y, c100.y, c101.y, c110.y, c111.y, tx, ty, tz);
+    const float r2 = r.v * r.v;
+    o.e_sg = sA * (r2 * r2) + q * e.v;
+    const float cr = 4.f * sA * r2 * r.v;
+    if (w_sg != 0.f) {
+      gxs += w_sg * (cr * r.gx + q * e.gx);
+      gys += w_sg * (cr * r.gy + q * e.gy);
+      gzs += w_sg * (cr * r.gz + q * e.gz);
+    }
+  }
+  o.fx = -gxs * mx;
+  o.fy = -gys * my;
+  o.fz = -gzs * mz;
+  return o;
+}
+
+struct Energies {
+  float lig;   // bonded + nonbonded (each pair counted from both ends, halved)
+  float rest;  // restraint
+  float sg, g; // grid terms
+};
+
+__device__ inline float3 sub(float4 a, float4 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ inline float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ inline float3 cross(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// Force on atom `self` (role `role`) from one bonded term, and the term's energy (counted by role 0).
+__device__ inline float3 bonded_force(const Lig& L, const float4* xs, uint32_t code, float& energy) {
+  const uint32_t type = code >> 30, role = (code >> 28) & 3u, t = code & 0x0fffffffu;
+  float3 f = make_float3(0.f, 0.f, 0.f);
+  float e = 0.f;
+  if (type == 0) {  // bond k (r - r0)^2
+    const float4 bp = L.bond[t];
+    const int i = __float_as_int(bp.x), j = __float_as_int(bp.y);
+    const float3 d = sub(xs[i], xs[j]);
+    const float r = sqrtf(dot(d, d));
+    const float dr = r - bp.w;
+    e = bp.z * dr * dr;
+    const float c = (role == 0 ? -2.f : 2.f) * bp.z * dr / r;
+    f = make_float3(c * d.x, c * d.y, c * d.z);
+  } else if (type == 1) {  // angle k (theta - theta0)^2
+    const int4 id = L.ang_i[t];
+    const float4 ap = L.ang_p[t];
+    const float3 u = sub(xs[id.x], xs[id.y]);
+    const float3 w = sub(xs[id.z], xs[id.y]);
+    const float lu2 = dot(u, u), lw2 = dot(w, w);
+    const float inv_luw = rsqrtf(lu2 * lw2);
+    float c = dot(u, w) * inv_luw;
+    c = fminf(1.f, fmaxf(-1.f, c));
+    const float th = acosf(c);
+    const float dth = th - ap.y;
+    e = ap.x * dth * dth;
+    const float sn = fmaxf(sqrtf(1.f - c * c), 1e-6f);
+    const float coef = 2.f * ap.x * dth / sn;
+    const float3 fa = make_float3(coef * (w.x * inv_luw - c * u.x / lu2), coef * (w.y * inv_luw - c * u.y / lu2),
+                                  coef * (w.z * inv_luw - c * u.z / lu2));
+    const float3 fc = make_float3(coef * (u.x * inv_luw - c * w.x / lw2), coef * (u.y * inv_luw - c * w.y / lw2),
+                                  coef * (u.z * inv_luw - c * w.z / lw2));
+    if (role == 0) f = fa;
+    else if (role == 2) f = fc;
+    else f = make_float3(-(fa.x + fc.x), -(fa.y + fc.y), -(fa.z + fc.z));
+  } else {  // torsion sum_n V_n/2 (1 + cos(n phi - gamma_n))
+    const int4 id = L.tor_i[t];
+    const float4 V = L.tor_v[t], cg = L.tor_c[t], sg = L.tor_s[t];
+    const float3 b1 = sub(xs[id.y], xs[id.x]);
+    const float3 b2 = sub(xs[id.z], xs[id.y]);
+    const float3 b3 = sub(xs[id.w], xs[id.z]);
+    const float3 n1 = cross(b1, b2), n2 = cross(b2, b3);
+    const float lb22 = dot(b2, b2);
+    const float lb2 = sqrtf(lb22);
+    const float n1s = fmaxf(dot(n1, n1), 1e-20f), n2s = fmaxf(dot(n2, n2), 1e-20f);
+    const float inv = rsqrtf(n1s * n2s);
+    const float cp = dot(n1, n2) * inv;           // cos phi
+    const float sp = lb2 * dot(b1, n2) * inv;     // sin phi
+    const float c2 = 2.f * cp * cp - 1.f, s2 = 2.f * sp * cp;
+    const float c3 = cp * (4.f * cp * cp - 3.f), s3 = sp * (3.f - 4.f * sp * sp);
+    // V/2 (1 + cos(n phi) cos g + sin(n phi) sin g);  dE/dphi = V/2 n (cos(n phi) sin g - sin(n phi) cos g)
+    e = V.x * (1.f + cp * cg.x + sp * sg.x) + V.y * (1.f + c2 * cg.y + s2 * sg.y) + V.z * (1.f + c3 * cg.z + s3 * sg.z);
+    const float dE = V.x * (cp * sg.x - sp * cg.x) + 2.f * V.y * (c2 * sg.y - s2 * cg.y) +
+                     3.f * V.z * (c3 * sg.z - s3 * cg.z);
+    const float ai = -lb2 / n1s, al = lb2 / n2s;
+    const float p = dot(b1, b2) / lb22, q = dot(b3, b2) / lb22;
+    float3 d;
+    if (role == 0) d = make_float3(ai * n1.x, ai * n1.y, ai * n1.z);
+    else if (role == 3) d = make_float3(al * n2.x, al * n2.y, al * n2.z);
+    else if (role == 1) {
+      const float ci = -(1.f + p) * ai, cl = q * al;
+      d = make_float3(ci * n1.x + cl * n2.x, ci * n1.y + cl * n2.y, ci * n1.z + cl * n2.z);
+    } else {
+      const float ci = p * ai, cl = -(1.f + q) * al;
+      d = make_float3(ci * n1.x + cl * n2.x, ci * n1.y + cl * n2.y, ci * n1.z + cl * n2.z);
+    }
+    f = make_float3(-dE * d.x, -dE * d.y, -dE * d.z);
+  }
+  energy = (role == 0) ? e : 0.f;
+  return f;
+}
+
+// Forces on the lane's atoms (and, if ENERGY, the lane's partial energies).  xs holds all
+// positions (x, y, z, q).
+template <int APL, bool ENERGY>
+__device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const GridDev& G, const float4* xs,
+                                const float (&x)[APL][3], float (&F)[APL][3], float w_sg, float w_g, bool all_grids,
+                                Energies& en, int& outside) {
+  const int lane = threadIdx.x & 31;
+  const int na = LL.na;
+  const bool hard = all_grids || w_g != 0.f;
+  const bool soft = all_grids || w_sg != 0.f;
+  float el = 0.f, eg = 0.f, esg = 0.f;
+  float mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+  for (int a = 0; a < APL; ++a) {
+    const int i = lane + 32 * a;
+    F[a][0] = F[a][1] = F[a][2] = 0.f;
+    if (i >= na) continue;
+    const float4 pa = L.atom_a[i];
+    const float4 pb = L.atom_b[i];
+    mx += pb.z * x[a][0];
+    my += pb.z * x[a][1];
+    mz += pb.z * x[a][2];
+    if (hard || soft) {
+      const GridOut go = grid_atom(G, x[a][0], x[a][1], x[a][2], pa.z, pa.w, pa.y, hard, soft, w_sg, w_g);
+      F[a][0] += go.fx;
+      F[a][1] += go.fy;
+      F[a][2] += go.fz;
+      eg += go.e_g;
+      esg += go.e_sg;
+      outside += go.outside ? 1 : 0;
+    }
+    // nonbonded pairs: every j, masked by the exclusion and 1-4 bits (branch-free)
+    const uint4 ex = L.excl[i], o4 = L.one4[i];
+    const float xi = x[a][0], yi = x[a][1], zi = x[a][2];
+    const float qi = (float)kCoulomb * pa.y, ri = pb.x, si = pb.y;
+    float fx = 0.f, fy = 0.f, fz = 0.f, e2 = 0.f;
+#pragma unroll
+    for (int w = 0; w < APL; ++w) {
+      const uint32_t exw = w == 0 ? ex.x : (w == 1 ? ex.y : ex.z);
+      const uint32_t o4w = w == 0 ? o4.x : (w == 1 ? o4.y : o4.z);
+      const int jmax = min(32, na - 32 * w);
+      for (int jj = 0; jj < jmax; ++jj) {
+        const int j = 32 * w + jj;
+        const float4 pj = xs[j];
+        const float4 bj = L.atom_b[j];
+        const bool excluded = (exw >> jj) & 1u;
+        const bool is14 = (o4w >> jj) & 1u;
+        const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        r2 = excluded ? 1.f : r2;
+        const float inv_r = rsqrtf(r2);
+        const float inv_r2 = inv_r * inv_r;
+        const float R = ri + bj.x;
+        const float s2 = R * R * inv_r2;
+        const float s6 = s2 * s2 * s2;
+        const float eps = excluded ? 0.f : (is14 ? 0.5f : 1.f) * si * bj.y;
+        const float qq = excluded ? 0.f : (is14 ? (float)(1.0 / 1.2) : 1.f) * qi * pj.w;
+        const float elj = eps * (s6 * s6 - 2.f * s6);
+        const float eel = qq * inv_r;
+        const float fr = (12.f * eps * (s6 * s6 - s6) + eel) * inv_r2;
+        fx = fmaf(fr, dx, fx);
+        fy = fmaf(fr, dy, fy);
+        fz = fmaf(fr, dz, fz);
+        if (ENERGY) e2 += elj + eel;
+      }
+    }
+    F[a][0] += fx;
+    F[a][1] += fy;
+    F[a][2] += fz;
+    if (ENERGY) el += 0.5f * e2;
+    // bonded terms through the atom's incidence list
+    const int b0 = L.inc_start[i], b1 = L.inc_start[i + 1];
+    for (int b = b0; b < b1; ++b) {
+      float e1;
+      const float3 f = bonded_force(L, xs, L.inc[b], e1);
+      F[a][0] += f.x;
+      F[a][1] += f.y;
+      F[a][2] += f.z;
+      if (ENERGY) el += e1;
+    }
+  }
+  // restraint on the centre of mass
+  mx = warp_sumf(mx);
+  my = warp_sumf(my);
+  mz = warp_sumf(mz);
+  const float invM = 1.f / LL.total_mass;
+  const float dx = mx * invM - LL.site[0], dy = my * invM - LL.site[1], dz = mz * invM - LL.site[2];
+  const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+  float er = 0.f;
+  if (d > LL.d0) {
+    const float ex = d - LL.d0;
+    er = 0.5f * LL.k_rest * ex * ex;
+    const float c = -LL.k_rest * ex / d * invM;
+#pragma unroll
+    for (int a = 0; a < APL; ++a) {
+      const int i = lane + 32 * a;
+      if (i >= na) continue;
+      const float m = L.atom_b[i].z;
+      F[a][0] += c * m * dx;
+      F[a][1] += c * m * dy;
+      F[a][2] += c * m * dz;
+    }
+  } else if (!(d <= LL.d0)) {  // NaN centre of mass: make the energy NaN
+    er = d;
+  }
+  en.lig = el;
+  en.rest = lane == 0 ? er : 0.f;
+  en.sg = esg;
+  en.g = eg;
+}
+
+__device__ inline void reduce_components(const Energies& e, double c[4]) {
+  c[0] = warp_sum((double)e.lig);
+  c[1] = warp_sum((double)e.rest);
+  c[2] = warp_sum((double)e.sg);
+  c[3] = warp_sum((double)e.g);
+}
+
+// U_k = ((U_L + U_I) + w_sg Psi_sg) + w_g Psi_g, a zero weight dropping its term.
+__device__ inline double weighted(const double c[4], double w_sg, double w_g) {
+  double e = __dadd_rn(c[0], c[1]);
+  if (w_sg != 0.0) e = __dadd_rn(e, __dmul_rn(w_sg, c[2]));
+  if (w_g != 0.0) e = __dadd_rn(e, __dmul_rn(w_g, c[3]));
+  return e;
+}
+
+__device__ inline void stage_ligand(uint32_t* s, const uint32_t* __restrict__ blob, int words) {
+  const uint4* src = (const uint4*)blob;
+  uint4* dst = (uint4*)s;
+  for (int i = threadIdx.x; i < words / 4; i += blockDim.x) dst[i] = src[i];
+}
+
+struct HmcArgs {
+  GridDev G;
+  LigandLayout LL;
+  const uint32_t* blob;
+  const StateDev* states;
+  int64_t n_rep;
+  const int32_t* state_of;
+  float* x;
+  double* comps;
+  double* dH;
+  uint8_t* acc;
+  int n_steps;
+  uint64_t seed;
+  uint32_t cycle;
+  int64_t rep_offset;
+  int64_t* counters;
+  int n_states;
+};
+
+template <int APL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) hmc_kernel(const HmcArgs A) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  stage_ligand(smem, A.blob, A.LL.words);
+  float4* xs_all = (float4*)(smem + A.LL.words);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (r >= A.n_rep) return;
+  const Lig L = bind_ligand(smem, A.LL);
+  float4* xs = xs_all + warp * (32 * APL);
+  const int na = A.LL.na;
+  const int k = A.state_of[r];
+  if ((unsigned)k >= (unsigned)A.n_states) {  // invalid state index: leave the replica untouched
+    if (lane == 0) {
+      if (A.dH) A.dH[r] = __longlong_as_double(0x7ff8000000000000ll);
+      if (A.acc) A.acc[r] = 0;
+    }
+    return;
+  }
+  const StateDev st = A.states[k];
+  const float dt = st.dt, hdt = 0.5f * st.dt;
+  const uint32_t rid = (uint32_t)(A.rep_offset + r);
+
+  float x[APL][3], v[APL][3], F[APL][3], x0[APL][3];
+  float kin = 0.f;
+#pragma unroll
+  for (int a = 0; a < APL; ++a) {
+    const int i = lane + 32 * a;
+    if (i < na) {
+      const float* src = A.x + (r * na + i) * 3;
+      x[a][0] = src[0];
+      x[a][1] = src[1];
+      x[a][2] = src[2];
+      const U4 o = philox(A.seed, (uint32_t)i, rid, A.cycle, kPurposeMomentum);
+      // Box-Muller: u1 in (0, 1] from 23 bits + 1/2, u2 in [0, 1) from 23 bits (exact in FP32)
+      const float u1 = ((float)(o.x >> 9) + 0.5f) * (1.0f / 8388608.0f);
+      const float u2 = (float)(o.y >> 9) * (1.0f / 8388608.0f);
+      const float u3 = ((float)(o.z >> 9) + 0.5f) * (1.0f / 8388608.0f);
+      const float u4 = (float)(o.w >> 9) * (1.0f / 8388608.0f);
+      const float rr1 = sqrtf(-2.f * logf(u1)), rr2 = sqrtf(-2.f * logf(u3));
+      float s1, c1, s2, c2;
+      sincospif(2.f * u2, &s1, &c1);
+      sincospif(2.f * u4, &s2, &c2);
+      const float4 pb = L.atom_b[i];
+      const float sd = st.sqrt_kT * pb.w;  // sqrt(kT * 4.184e-4 / m)
+      v[a][0] = rr1 * c1 * sd;
+      v[a][1] = rr1 * s1 * sd;
+      v[a][2] = rr2 * c2 * sd;
+      kin += pb.z * (v[a][0] * v[a][0] + v[a][1] * v[a][1] + v[a][2] * v[a][2]);
+      xs[i] = make_float4(x[a][0], x[a][1], x[a][2], L.atom_a[i].y);
+    } else {
+      x[a][0] = x[a][1] = x[a][2] = 0.f;
+      v[a][0] = v[a][1] = v[a][2] = 0.f;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) x0[a][d] = x[a][d];
+  }
+  __syncwarp();
+  int outside = 0;
+  Energies en;
+  double c0[4], c1[4];
+  evaluate<APL, true>(A.LL, L, A.G, xs, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
+  reduce_components(en, c0);
+  const double K0 = 0.5 * kKineticToKcal * warp_sum((double)kin);
+  for (int s = 0; s < A.n_steps; ++s) {
+#pragma unroll
+    for (int a = 0; a < APL; ++a) {
+      const int i = lane + 32 * a;
+      if (i < na) {
+        const float acc = L.atom_a[i].x;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          v[a][d] = fmaf(hdt * acc, F[a][d], v[a][d]);
+          x[a][d] = fmaf(dt, v[a][d], x[a][d]);
+        }
+      }
+    }
+    __syncwarp();  // all lanes finished reading the previous positions
+#pragma unroll
+    for (int a = 0; a < APL; ++a) {
+      const int i = lane + 32 * a;
+      if (i < na) {
+        float4 p = xs[i];
+        p.x = x[a][0];
+        p.y = x[a][1];
+        p.z = x[a][2];
+        xs[i] = p;
+      }
+    }
+    __syncwarp();
+    if (s + 1 < A.n_steps) {
+      evaluate<APL, false>(A.LL, L, A.G, xs, x, F, st.w_sg_f, st.w_g_f, false, en, outside);
+    } else {
+      evaluate<APL, true>(A.LL, L, A.G, xs, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
+      reduce_components(en, c1);
+    }
+#pragma unroll
+    for (int a = 0; a < APL; ++a) {
+      const int i = lane + 32 * a;
+      if (i < na) {
+        const float acc = L.atom_a[i].x;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[a][d] = fmaf(hdt * acc, F[a][d], v[a][d]);
+      }
+    }
+  }
+  if (A.n_steps == 0) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) c1[c] = c0[c];
+  }
+  kin = 0.f;
+#pragma unroll
+  for (int a = 0; a < APL; ++a) {
+    const int i = lane + 32 * a;
+    if (i < na) kin += L.atom_b[i].z * (v[a][0] * v[a][0] + v[a][1] * v[a][1] + v[a][2] * v[a][2]);
+  }
+  const double K1 = 0.5 * kKineticToKcal * warp_sum((double)kin);
+  const double U0 = weighted(c0, st.w_sg, st.w_g), U1 = weighted(c1, st.w_sg, st.w_g);
+  const double dH = (K1 + U1) - (K0 + U0);
+  const U4 o = philox(A.seed, 0u, rid, A.cycle, kPurposeAccept);
+  const double u = uniform53(o.x, o.y);
+  const bool accept = u < exp(-dH / st.kT);
+#pragma unroll
+  for (int a = 0; a < APL; ++a) {
+    const int i = lane + 32 * a;
+    if (i < na) {
+      float* dst = A.x + (r * na + i) * 3;
+      dst[0] = accept ? x[a][0] : x0[a][0];
+      dst[1] = accept ? x[a][1] : x0[a][1];
+      dst[2] = accept ? x[a][2] : x0[a][2];
+    }
+  }
+  if (lane < 4) A.comps[r * 4 + lane] = accept ? c1[lane] : c0[lane];
+  if (lane == 0) {
+    if (A.dH) A.dH[r] = dH;
+    if (A.acc) A.acc[r] = accept ? 1 : 0;
+  }
+  if (A.counters) {
+    int out_total = __reduce_add_sync(kFull, outside);
+    if (lane == 0) {
+      if (accept) atomicAdd((unsigned long long*)&A.counters[ALGDOCK_CNT_ACCEPTED], 1ull);
+      if (!isfinite(dH)) atomicAdd((unsigned long long*)&A.counters[ALGDOCK_CNT_NONFINITE], 1ull);
+      if (out_total) atomicAdd((unsigned long long*)&A.counters[ALGDOCK_CNT_OUTSIDE], (unsigned long long)out_total);
+    }
+  }
+}
+
+// Energy-only evaluation of stored configurations (one warp each): components for u_kn.
+template <int APL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) evaluate_kernel(GridDev G, LigandLayout LL,
+                                                                       const uint32_t* blob, int64_t N,
+                                                                       const float* __restrict__ xin,
+                                                                       double* comps) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  stage_ligand(smem, blob, LL.words);
+  float4* xs_all = (float4*)(smem + LL.words);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (n >= N) return;
+  const Lig L = bind_ligand(smem, LL);
+  float4* xs = xs_all + warp * (32 * APL);
+  const int na = LL.na;
+  float x[APL][3], F[APL][3];
+#pragma unroll
+  for (int a = 0; a < APL; ++a) {
+    const int i = lane + 32 * a;
+    if (i < na) {
+      const float* src = xin + (n * na + i) * 3;
+      x[a][0] = src[0];
+      x[a][1] = src[1];
+      x[a][2] = src[2];
+      xs[i] = make_float4(x[a][0], x[a][1], x[a][2], L.atom_a[i].y);
+    } else {
+      x[a][0] = x[a][1] = x[a][2] = 0.f;
+    }
+  }
+  __syncwarp();
+  Energies en;
+  int outside = 0;
+  evaluate<APL, true>(LL, L, G, xs, x, F, 0.f, 0.f, true, en, outside);
+  double c[4];
+  reduce_components(en, c);
+  if (lane < 4) comps[n * 4 + lane] = c[lane];
+}
+
+// Energy and force of configurations at given states (one warp each).
+template <int APL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) force_kernel(GridDev G, LigandLayout LL, const uint32_t* blob,
+                                                                    const StateDev* __restrict__ states, int n_states,
+                                                                    int64_t N,
+                                                                    const int32_t* __restrict__ state_of,
+                                                                    const float* __restrict__ xin, float* fout,
+                                                                    double* comps) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  stage_ligand(smem, blob, LL.words);
+  float4* xs_all = (float4*)(smem + LL.words);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (n >= N) return;
+  const Lig L = bind_ligand(smem, LL);
+  float4* xs = xs_all + warp * (32 * APL);
+  const int na = LL.na;
+  const int k = state_of[n];
+  if ((unsigned)k >= (unsigned)n_states) return;  // invalid state index: no output
+  const StateDev st = states[k];
+  float x[APL][3], F[APL][3];
+#pragma unroll
+  for (int a = 0; a < APL; ++a) {
+    const int i = lane + 32 * a;
+    if (i < na) {
+      const float* src = xin + (n * na + i) * 3;
+      x[a][0] = src[0];
+      x[a][1] = src[1];
+      x[a][2] = src[2];
+      xs[i] = make_float4(x[a][0], x[a][1], x[a][2], L.atom_a[i].y);
+    } else {
+      x[a][0] = x[a][1] = x[a][2] = 0.f;
+    }
+  }
+  __syncwarp();
+  Energies en;
+  int outside = 0;
+  evaluate<APL, true>(LL, L, G, xs, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
+  double c[4];
+  reduce_components(en, c);
+#pragma unroll
+  for (int a = 0; a < APL; ++a) {
+    const int i = lane + 32 * a;
+    if (i < na) {
+      float* dst = fout + (n * na + i) * 3;
+      dst[0] = F[a][0];
+      dst[1] = F[a][1];
+      dst[2] = F[a][2];
+    }
+  }
+  if (comps && lane < 4) comps[n * 4 + lane] = c[lane];
+}
+
+// u_kn[k][n] from stored components (k over k_count states from k_begin).
+__global__ void ukn_kernel(const StateDev* __restrict__ states, int k_begin, int k_count, int64_t N,
+                           const double* __restrict__ comps, double* u_kn) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double c[4];
+  const double2 c01 = *(const double2*)(comps + 4 * n), c23 = *(const double2*)(comps + 4 * n + 2);
+  c[0] = c01.x;
+  c[1] = c01.y;
+  c[2] = c23.x;
+  c[3] = c23.y;
+  for (int k = blockIdx.y; k < k_count; k += gridDim.y) {
+    const StateDev st = states[k_begin + k];
+    u_kn[(int64_t)k * N + n] = __dmul_rn(st.beta, weighted(c, st.w_sg, st.w_g));
+  }
+}
+
+int atoms_per_lane(int na) { return na <= 32 ? 1 : (na <= 64 ? 2 : 3); }
+
+}  // namespace
+
+cudaError_t launch_hmc(cudaStream_t s, const algdock_ctx& c, int64_t n_rep, const int32_t* state_of, float* x,
+                       double* comps, double* dH, uint8_t* acc, int n_steps, uint64_t seed, uint64_t cycle,
+                       int64_t rep_offset, int64_t* counters) {
+  if (n_rep == 0) return cudaSuccess;
+  HmcArgs A{c.grid, c.lig, c.d_blob, c.d_states, n_rep, state_of, x, comps, dH, acc, n_steps, seed,
+            (uint32_t)cycle, rep_offset, counters, c.K};
+  const int apl = atoms_per_lane(c.lig.na);
+  const size_t smem = (size_t)c.lig.words * 4 + (size_t)kWarpsPerBlock * 32 * apl * sizeof(float4);
+  const int64_t blocks = (n_rep + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  cudaError_t e = cudaSuccess;
+  switch (apl) {
+    case 1:
+      e = cudaFuncSetAttribute(hmc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) hmc_kernel<1><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(A);
+      break;
+    case 2:
+      e = cudaFuncSetAttribute(hmc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) hmc_kernel<2><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(A);
+      break;
+    default:
+      e = cudaFuncSetAttribute(hmc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) hmc_kernel<3><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(A);
+      break;
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_evaluate(cudaStream_t s, const algdock_ctx& c, int64_t N, const float* x, double* comps) {
+  if (N == 0) return cudaSuccess;
+  const int apl = atoms_per_lane(c.lig.na);
+  const size_t smem = (size_t)c.lig.words * 4 + (size_t)kWarpsPerBlock * 32 * apl * sizeof(float4);
+  const int64_t blocks = (N + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  cudaError_t e = cudaSuccess;
+  switch (apl) {
+    case 1:
+      e = cudaFuncSetAttribute(evaluate_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess)
+        evaluate_kernel<1><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(c.grid, c.lig, c.d_blob, N, x, comps);
+      break;
+    case 2:
+      e = cudaFuncSetAttribute(evaluate_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess)
+        evaluate_kernel<2><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(c.grid, c.lig, c.d_blob, N, x, comps);
+      break;
+    default:
+      e = cudaFuncSetAttribute(evaluate_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess)
+        evaluate_kernel<3><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(c.grid, c.lig, c.d_blob, N, x, comps);
+      break;
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_energy_force(cudaStream_t s, const algdock_ctx& c, int64_t N, const int32_t* state_of,
+                                const float* x, float* force, double* comps) {
+  if (N == 0) return cudaSuccess;
+  const int apl = atoms_per_lane(c.lig.na);
+  const size_t smem = (size_t)c.lig.words * 4 + (size_t)kWarpsPerBlock * 32 * apl * sizeof(float4);
+  const int64_t blocks = (N + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  cudaError_t e = cudaSuccess;
+  switch (apl) {
+    case 1:
+      e = cudaFuncSetAttribute(force_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess)
+        force_kernel<1><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(c.grid, c.lig, c.d_blob, c.d_states, c.K, N,
+                                                                             state_of, x, force, comps);
+      break;
+    case 2:
+      e = cudaFuncSetAttribute(force_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess)
+        force_kernel<2><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(c.grid, c.lig, c.d_blob, c.d_states, c.K, N,
+                                                                             state_of, x, force, comps);
+      break;
+    default:
+      e = cudaFuncSetAttribute(force_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess)
+        force_kernel<3><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(c.grid, c.lig, c.d_blob, c.d_states, c.K, N,
+                                                                             state_of, x, force, comps);
+      break;
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_ukn(cudaStream_t s, const algdock_ctx& c, int64_t N, const double* comps, int k_begin,
+                       int k_count, double* u_kn) {
+  if (N == 0 || k_count == 0) return cudaSuccess;
+  const int threads = 256;
+  dim3 grid((unsigned)((N + threads - 1) / threads), (unsigned)min(k_count, 64));
+  ukn_kernel<<<grid, threads, 0, s>>>(c.d_states, k_begin, k_count, N, comps, u_kn);
+  return cudaGetLastError();
+}
+
+}  // namespace algdock

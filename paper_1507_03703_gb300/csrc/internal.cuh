@@ -1,0 +1,140 @@
+// Internal declarations shared by the CUDA sources of libalgdock (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "algdock.h"
+
+namespace algdock {
+
+// Unit conventions: A, kcal/mol, amu, fs.
+constexpr double kBoltzmann = 0.0019872043;        // kcal / (mol K)
+constexpr double kCoulomb = 332.0637;              // kcal A / (mol e^2)
+constexpr double kForceToAccel = 4.184e-4;         // (kcal/mol/A) / amu -> A / fs^2
+constexpr double kKineticToKcal = 1.0 / 4.184e-4;  // amu A^2 / fs^2 -> kcal/mol
+constexpr double kRepulsiveNodeCap = 1.0e10;
+constexpr double kRepulsiveMinDist = 0.01;         // A
+constexpr double kAttractiveMinDist = 2.0;         // A
+constexpr int kMaxAtoms = 96;                      // 3 atoms per lane of one warp
+constexpr int kMaxLadder = 1024;
+
+enum : uint32_t { kPurposeMomentum = 1, kPurposeAccept = 2, kPurposeExchange = 3 };
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, SC'11: ten rounds of two 32x32->64 multiplies with a Weyl key
+// schedule.  Written from the published definition.
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__host__ __device__ inline U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__host__ __device__ inline U4 philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
+  return philox4x32_10(U4{c0, c1, c2, c3}, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// Uniform double in [0, 1) from 27 + 26 random bits (exact integer arithmetic).
+__host__ __device__ inline double uniform53(uint32_t a, uint32_t b) {
+  return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+// ------------------------------------------------------------------ device-side tables
+// Interpolation lattices.  hard: (LJr^(1/4), LJa, elec, 0) per node; soft: (sLJr^(1/4), selec).
+struct GridDev {
+  const float4* hard;
+  const float2* soft;
+  int nx, ny, nz;
+  float ox, oy, oz;  // origin, exactly the FP32 value used by the split subtraction
+  float inv_h;
+};
+
+// One thermodynamic state as the kernels read it.
+struct StateDev {
+  double kT;       // k_B T
+  double beta;     // 1 / (k_B T)
+  double w_sg;     // alpha_sg
+  double w_g;      // alpha_g
+  float w_sg_f, w_g_f;
+  float dt, sqrt_kT;
+};
+
+// Ligand blob header: word offsets (4-byte words, each section 16-byte aligned) into one
+// contiguous buffer that a CTA copies into shared memory.
+struct LigandLayout {
+  int na, nb, nang, ntor, ninc;
+  int off_atom_a;  // float4[na]: (accel factor 4.184e-4/m, q, sqrt(A), sqrt(B))
+  int off_atom_b;  // float4[na]: (R*, sqrt(eps), m, sqrt(4.184e-4/m))
+  int off_excl;    // uint4[na]: bit j of word j/32 set if pair (i, j) is excluded (incl. i == j)
+  int off_one4;    // uint4[na]: bit j set if (i, j) is a 1-4 pair
+  int off_bond;    // float4[nb]: (i, j as int bits, k, r0)
+  int off_ang;     // int4[nang] (i, j, k, 0) then float4[nang] (k, theta0, 0, 0)
+  int off_tor;     // int4[ntor] (i, j, k, l), float4 (V1/2, V2/2, V3/2, 0), float4 cos(gamma), float4 sin(gamma)
+  int off_inc_start;  // int[na + 1]
+  int off_inc;        // uint32[ninc]: type << 30 | role << 28 | term
+  int words;          // total (multiple of 4)
+  float total_mass;
+  float site[3];
+  float k_rest, d0;
+};
+
+}  // namespace algdock
+
+// The context (opaque to callers).
+struct algdock_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // grids
+  bool has_grid = false;
+  algdock::GridDev grid{};
+  float4* d_hard = nullptr;
+  float2* d_soft = nullptr;
+  size_t grid_nodes = 0;
+  // ligand
+  bool has_ligand = false;
+  algdock::LigandLayout lig{};
+  uint32_t* d_blob = nullptr;
+  // states
+  int K = 0;
+  algdock::StateDev* d_states = nullptr;
+  // scratch owned by the MBAR solver, grown on demand
+  void* d_mbar = nullptr;
+  size_t mbar_bytes = 0;
+  // pinned host word for convergence polling
+  int* h_flag = nullptr;
+};
+
+namespace algdock {
+// launchers implemented in the .cu files
+cudaError_t launch_grid_build(cudaStream_t s, const algdock_grid_desc& d, int n_rec, const double* xyz,
+                              const double* rstar, const double* eps, const double* q, float* ljr, float* lja,
+                              float* elec);
+cudaError_t launch_grid_prepare(cudaStream_t s, size_t n_nodes, const float* ljr, const float* lja,
+                                const float* elec, double vmax_r, double vmax_e, float4* hard, float2* soft);
+cudaError_t launch_hmc(cudaStream_t s, const algdock_ctx& c, int64_t n_rep, const int32_t* state_of, float* x,
+                       double* comps, double* dH, uint8_t* acc, int n_steps, uint64_t seed, uint64_t cycle,
+                       int64_t rep_offset, int64_t* counters);
+cudaError_t launch_evaluate(cudaStream_t s, const algdock_ctx& c, int64_t N, const float* x, double* comps);
+cudaError_t launch_energy_force(cudaStream_t s, const algdock_ctx& c, int64_t N, const int32_t* state_of,
+                                const float* x, float* force, double* comps);
+cudaError_t launch_ukn(cudaStream_t s, const algdock_ctx& c, int64_t N, const double* comps, int k_begin,
+                       int k_count, double* u_kn);
+cudaError_t launch_exchange(cudaStream_t s, const algdock_ctx& c, int n_ladders, int K, int state_offset,
+                            const double* comps, int32_t* config_of, int32_t* state_of, int n_sweeps, int max_sep,
+                            uint64_t seed, uint64_t cycle, int64_t ladder_offset, int64_t* attempts,
+                            int64_t* accepts);
+}  // namespace algdock

@@ -1,0 +1,184 @@
+// MBAR (Shirts & Chodera 2008; "Estimation") by self-consistent iteration in log-sum-exp form.
+//
+// One iteration is three kernels on the stream:
+//   1. log_denominators: for every sample n, log D_n = ln sum_k N_k exp(f_k - u_kn)   (one thread per n)
+//   2. state_partials:   for every state i and a chunk of samples, the (max, sum) pair of
+//                        exp(-u_in - log D_n)                                       (block per (chunk, i))
+//   3. finalize:         f_i <- -ln sum_n ..., gauge f_0 = 0, convergence flag       (one block)
+// Every kernel returns at once when the device flag says the iteration has converged, so the host
+// can enqueue iterations in batches and poll the flag between batches.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace algdock {
+namespace {
+
+constexpr int kPartialThreads = 256;
+constexpr int kChunk = 8192;  // samples per state_partials block
+
+struct MbarState {
+  int converged;
+  int iters;
+  int _pad[2];
+};
+
+// Online log-sum-exp accumulator: value = m + log(s).
+struct Lse {
+  double m, s;
+};
+__device__ inline void lse_add(Lse& a, double x, int mode) {
+  if (x == -INFINITY) return;
+  if (x <= a.m) {
+    a.s += mode ? (double)__expf((float)(x - a.m)) : exp(x - a.m);
+  } else {
+    a.s = a.s * (mode ? (double)__expf((float)(a.m - x)) : exp(a.m - x)) + 1.0;
+    a.m = x;
+  }
+}
+__device__ inline Lse lse_merge(Lse a, Lse b) {
+  if (b.m == -INFINITY) return a;
+  if (a.m == -INFINITY) return b;
+  if (a.m >= b.m) return Lse{a.m, a.s + b.s * exp(b.m - a.m)};
+  return Lse{b.m, b.s + a.s * exp(a.m - b.m)};
+}
+
+__global__ void log_denominators(int K, int64_t N, const double* __restrict__ u, const double* __restrict__ logNk,
+                                 const double* __restrict__ f, double* logD, const MbarState* st, int mode) {
+  if (st->converged) return;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  Lse a{-INFINITY, 0.0};
+  for (int k = 0; k < K; ++k) lse_add(a, logNk[k] + f[k] - u[(int64_t)k * N + n], mode);
+  logD[n] = a.m + log(a.s);
+}
+
+__global__ void __launch_bounds__(kPartialThreads) state_partials(int64_t N, const double* __restrict__ u,
+                                                                  const double* __restrict__ logD, double2* part,
+                                                                  int n_chunks, const MbarState* st, int mode) {
+  if (st->converged) return;
+  const int i = blockIdx.y, chunk = blockIdx.x;
+  const int64_t begin = (int64_t)chunk * kChunk;
+  const int64_t end = min(N, begin + kChunk);
+  Lse a{-INFINITY, 0.0};
+  const double* ui = u + (int64_t)i * N;
+  for (int64_t n = begin + threadIdx.x; n < end; n += blockDim.x) lse_add(a, -ui[n] - logD[n], mode);
+  __shared__ double sm[kPartialThreads], ss[kPartialThreads];
+  sm[threadIdx.x] = a.m;
+  ss[threadIdx.x] = a.s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      const Lse r = lse_merge(Lse{sm[threadIdx.x], ss[threadIdx.x]}, Lse{sm[threadIdx.x + w], ss[threadIdx.x + w]});
+      sm[threadIdx.x] = r.m;
+      ss[threadIdx.x] = r.s;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(int64_t)i * n_chunks + chunk] = make_double2(sm[0], ss[0]);
+}
+
+__global__ void finalize(int K, int n_chunks, const double2* __restrict__ part, double* f, double* fnew,
+                         MbarState* st, double tol, int max_iter) {
+  if (st->converged) return;
+  __shared__ double s_delta[256];
+  // new free energies, one state per thread (strided)
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    Lse a{-INFINITY, 0.0};
+    for (int c = 0; c < n_chunks; ++c) {
+      const double2 p = part[(int64_t)i * n_chunks + c];
+      a = lse_merge(a, Lse{p.x, p.y});
+    }
+    fnew[i] = -(a.m + log(a.s));
+  }
+  __syncthreads();
+  const double f0 = fnew[0];
+  double dmax = 0.0;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    const double v = fnew[i] - f0;
+    const double d = fabs(v - f[i]);
+    dmax = (d > dmax || isnan(d)) ? d : dmax;
+  }
+  s_delta[threadIdx.x] = dmax;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      const double o = s_delta[threadIdx.x + w];
+      if (o > s_delta[threadIdx.x] || isnan(o)) s_delta[threadIdx.x] = o;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < K; i += blockDim.x) f[i] = fnew[i] - f0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->iters += 1;
+    if (s_delta[0] < tol) st->converged = 1;
+    else if (st->iters >= max_iter) st->converged = 2;  // stop: not converged
+  }
+}
+
+__global__ void init_state(int K, const int64_t* Nk, double* logNk, double* f, MbarState* st) {
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    logNk[k] = Nk[k] > 0 ? log((double)Nk[k]) : -INFINITY;
+    f[k] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    st->converged = 0;
+    st->iters = 0;
+  }
+}
+
+}  // namespace
+
+// Scratch layout (bytes): MbarState | logNk[K] | f[K] | fnew[K] | Nk[K] (int64) | part[K][n_chunks] | logD[N]
+size_t mbar_scratch_bytes(int K, int64_t N) {
+  const int64_t n_chunks = (N + kChunk - 1) / kChunk;
+  return 64 + 4 * (size_t)K * 8 + (size_t)K * n_chunks * 16 + (size_t)N * 8 + 256;
+}
+
+// Runs the solver on caller-provided scratch (mbar_scratch_bytes(K, N) bytes, 256-byte aligned).
+// h_flag: pinned host int used to poll the device flag.  Returns 0 converged, 1 not converged,
+// -1 on a CUDA error (then *err is set).
+int mbar_run(cudaStream_t s, void* scratch, int K, int64_t N, const double* u_kn, const int64_t* Nk_host,
+             double tol, int max_iter, int mode, double* f_host, int* iters, int* h_flag, cudaError_t* err) {
+  const int64_t n_chunks = (N + kChunk - 1) / kChunk;
+  char* p = (char*)scratch;
+  MbarState* st = (MbarState*)p;
+  double* logNk = (double*)(p + 64);
+  double* f = logNk + K;
+  double* fnew = f + K;
+  int64_t* Nk = (int64_t*)(fnew + K);
+  double2* part = (double2*)(Nk + K);
+  double* logD = (double*)(part + (size_t)K * n_chunks);
+  cudaError_t e = cudaMemcpyAsync(Nk, Nk_host, sizeof(int64_t) * K, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) { *err = e; return -1; }
+  init_state<<<1, 256, 0, s>>>(K, Nk, logNk, f, st);
+  const int threads = 256;
+  const unsigned blocks_n = (unsigned)((N + threads - 1) / threads);
+  const dim3 grid_p((unsigned)n_chunks, (unsigned)K);
+  int done = 0;
+  int issued = 0;
+  int batch = 4;
+  while (!done) {
+    for (int b = 0; b < batch && issued < max_iter; ++b, ++issued) {
+      log_denominators<<<blocks_n, threads, 0, s>>>(K, N, u_kn, logNk, f, logD, st, mode);
+      state_partials<<<grid_p, kPartialThreads, 0, s>>>(N, u_kn, logD, part, (int)n_chunks, st, mode);
+      finalize<<<1, 256, 0, s>>>(K, (int)n_chunks, part, f, fnew, st, tol, max_iter);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_flag, &st->converged, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { *err = e; return -1; }
+    done = (*h_flag != 0) || issued >= max_iter;
+    if (batch < 64) batch *= 2;
+  }
+  MbarState hs;
+  e = cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f_host, f, sizeof(double) * K, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { *err = e; return -1; }
+  *iters = hs.iters;
+  return hs.converged == 1 ? 0 : 1;
+}
+
+}  // namespace algdock

@@ -1,0 +1,156 @@
+"""GPU parity: receptor grids, energy components and forces against the FP64 oracle
+("Thermodynamic Cycle"; Eq. (binding_site); Eq. (protocol)).
+
+Tolerances (derived from the arithmetic):
+- grids_build: terms in FP32 from FP64 differences, sums in FP64, so each node carries at most a
+  few FP32 roundings of its largest terms: |err| <= 2e-6 * sum_j |term_j| (for LJr and LJa the
+  terms share a sign, so this is 2e-6 relative).
+- forces: 1e-5 relative per configuration, ||F_gpu - F_ref|| / ||F_ref|| (FP32 per term).
+- energy components: FP32 per term, FP64 sums: 1e-5 relative of the component's scale plus
+  1e-4 kcal/mol.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1507_03703_gb300 import synthetic as S
+
+from systems import configurations, gpu_context, oracle_system, raw_grids32, state_table
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def small():
+    sys_ = S.config_small(1)
+    g32 = raw_grids32(sys_)
+    T, alpha, dt = state_table(sys_)
+    ctx = gpu_context(sys_, g32, T, alpha, dt)
+    osys = oracle_system(sys_, g32, T, alpha, dt)
+    return sys_, g32, T, alpha, dt, ctx, osys
+
+
+def _abs_receptor(rec):
+    return S.Receptor(xyz=rec.xyz, rstar=rec.rstar, eps=rec.eps, charge=np.abs(rec.charge))
+
+
+def test_grids_build_matches_direct_sum(small):
+    from paper_1507_03703_gb300.algdock import Context
+    sys_ = small[0]
+    ctx = Context(0)
+    shape = tuple(reversed(sys_.grid.n))
+    out = [torch.empty(shape, dtype=torch.float32, device="cuda") for _ in range(3)]
+    ctx.grids_build(sys_.grid, sys_.receptor, *out)
+    torch.cuda.synchronize()
+    g = [o.cpu().numpy().astype(np.float64) for o in out]
+    o_ljr, o_lja, o_elec = oracle.grid_direct_sum(sys_.receptor, sys_.grid)
+    _, _, abs_elec = oracle.grid_direct_sum(_abs_receptor(sys_.receptor), sys_.grid)
+    assert np.all(np.abs(g[0] - o_ljr) <= 2e-6 * o_ljr)
+    assert np.all(np.abs(g[1] - o_lja) <= 2e-6 * np.abs(o_lja))
+    assert np.all(np.abs(g[2] - o_elec) <= 2e-6 * abs_elec + 1e-30)
+
+
+def test_grids_build_paper_scale_sampled_nodes():
+    """129^3 lattice, 4000 receptor atoms: 4000 sampled nodes including the corners."""
+    from paper_1507_03703_gb300.algdock import Context
+    sys_ = S.config_paper_scale(2)
+    ctx = Context(0)
+    nx, ny, nz = sys_.grid.n
+    out = [torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda") for _ in range(3)]
+    ctx.grids_build(sys_.grid, sys_.receptor, *out)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    idx = rng.integers(0, [nx, ny, nz], size=(4000, 3))
+    idx[:8] = [[i * (nx - 1), j * (ny - 1), k * (nz - 1)] for i in (0, 1) for j in (0, 1) for k in (0, 1)]
+    pts = sys_.grid.origin + sys_.grid.spacing * idx
+    o = oracle.grid_points(sys_.receptor, pts)
+    a = oracle.grid_points(_abs_receptor(sys_.receptor), pts)
+    gv = [out[c][idx[:, 2], idx[:, 1], idx[:, 0]].cpu().numpy().astype(np.float64) for c in range(3)]
+    assert np.all(np.abs(gv[0] - o[0]) <= 2e-6 * o[0])
+    assert np.all(np.abs(gv[1] - o[1]) <= 2e-6 * np.abs(o[1]))
+    assert np.all(np.abs(gv[2] - o[2]) <= 2e-6 * a[2] + 1e-30)
+
+
+def _check_forces(ctx, osys, x, states, w_sg, w_g):
+    N = x.shape[0]
+    xd = torch.from_numpy(x).cuda()
+    sd = torch.from_numpy(states.astype(np.int32)).cuda()
+    F = torch.empty_like(xd)
+    comps = torch.empty((N, 4), dtype=torch.float64, device="cuda")
+    ctx.energy_force(sd, xd, F, comps)
+    torch.cuda.synchronize()
+    F, comps = F.cpu().numpy().astype(np.float64), comps.cpu().numpy()
+    worst = 0.0
+    for n in range(N):
+        k = states[n]
+        c_o, F_o = osys.energy_force(x[n].astype(np.float64), w_sg[k], w_g[k])
+        rel = np.linalg.norm(F[n] - F_o) / np.linalg.norm(F_o)
+        worst = max(worst, rel)
+        assert rel <= 1e-5, (n, k, rel)
+        scale = np.maximum(np.abs(c_o), 1.0)
+        assert np.all(np.abs(comps[n] - c_o) <= 1e-5 * scale + 1e-4), (n, comps[n], c_o)
+    return worst
+
+
+def test_forces_and_components_every_state_small(small):
+    sys_, g32, T, alpha, dt, ctx, osys = small
+    K = len(T)
+    x = configurations(sys_, 8 * K, seed=3)
+    states = np.arange(8 * K) % K
+    w_sg, w_g, _ = osys.state_weights()
+    _check_forces(ctx, osys, x, states, w_sg, w_g)
+
+
+def test_forces_with_atoms_outside_the_lattice(small):
+    sys_, g32, T, alpha, dt, ctx, osys = small
+    x = configurations(sys_, 16, seed=4)
+    x[:, :3, 0] += 9.0  # push a few atoms past the +x face (16 A cube, half-width 8 A)
+    x[8:, 3:6, 2] -= 12.0
+    states = np.full(16, len(T) - 1)
+    w_sg, w_g, _ = osys.state_weights()
+    _check_forces(ctx, osys, x, states, w_sg, w_g)
+
+
+def test_reduced_energies_and_ukn(small):
+    sys_, g32, T, alpha, dt, ctx, osys = small
+    N = 300  # several warps per block and a ragged tail
+    x = configurations(sys_, N, seed=5)
+    xd = torch.from_numpy(x).cuda()
+    comps = torch.empty((N, 4), dtype=torch.float64, device="cuda")
+    u = torch.empty((len(T), N), dtype=torch.float64, device="cuda")
+    ctx.reduced_energies(N, x=xd, comps=comps, k_begin=0, k_count=len(T), u_kn=u)
+    torch.cuda.synchronize()
+    u_o, c_o = osys.reduced_energies(x.astype(np.float64))
+    c = comps.cpu().numpy()
+    assert np.all(np.abs(c - c_o) <= 1e-5 * np.maximum(np.abs(c_o), 1.0) + 1e-4)
+    # u_kn from the GPU's own components is exact FP64 arithmetic: compare with the oracle's
+    # formula applied to the same components, bit for bit
+    u_same = oracle.ukn_from_comps(T, alpha, c)
+    assert np.array_equal(u.cpu().numpy(), u_same)
+    # a sub-range of states, from stored components
+    u2 = torch.empty((5, N), dtype=torch.float64, device="cuda")
+    ctx.reduced_energies(N, comps=comps, k_begin=7, k_count=5, u_kn=u2)
+    assert np.array_equal(u2.cpu().numpy(), u_same[7:12])
+
+
+@pytest.fixture(scope="module")
+def paper_scale():
+    sys_ = S.config_paper_scale(2)
+    g32 = raw_grids32(sys_)
+    T, alpha, dt = state_table(sys_)
+    ctx = gpu_context(sys_, g32, T, alpha, dt)
+    osys = oracle_system(sys_, g32, T, alpha, dt)
+    return sys_, g32, T, alpha, dt, ctx, osys
+
+
+def test_forces_paper_scale_sampled(paper_scale):
+    """Paper-scale system (129^3 lattices, 30-60 atom ligand): sampled configurations at sampled
+    states, including both legs and the alpha range where both grid sets are active."""
+    sys_, g32, T, alpha, dt, ctx, osys = paper_scale
+    K = len(T)
+    x = configurations(sys_, 96, seed=6)
+    states = np.random.default_rng(7).integers(0, K, size=96)
+    states[:4] = [0, 31, 32 + 48, K - 1]
+    w_sg, w_g, _ = osys.state_weights()
+    _check_forces(ctx, osys, x, states, w_sg, w_g)

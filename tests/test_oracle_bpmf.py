@@ -6,35 +6,10 @@ replica-exchange HMC samples): for a one-atom ligand the BPMF has a closed quadr
 with the numerator summed on a sub-lattice of the receptor grid (scipy's trilinear interpolator,
 an implementation independent of the oracle's) and the denominator in closed form."""
 import numpy as np
-from scipy.interpolate import RegularGridInterpolator
-
 import oracle
 from paper_1507_03703_gb300 import synthetic as S
 
-
-def _quadrature_bpmf(grid, ljr, lja, elec, lig, T=300.0, d0=6.0, k=oracle.K_RESTRAINT):
-    b = oracle.beta(T)
-    ax = tuple(grid.origin[d] + grid.spacing * np.arange(grid.n[d]) for d in range(3))
-    rgi = lambda L: RegularGridInterpolator(ax, np.transpose(L, (2, 1, 0)), method="linear")
-    root = np.minimum(ljr, 1e10) ** 0.25
-    sA = np.sqrt(lig.eps[0] * (2 * lig.rstar[0]) ** 12)
-    sB = np.sqrt(2 * lig.eps[0] * (2 * lig.rstar[0]) ** 6)
-    q = lig.charge[0]
-    hq = grid.spacing / 8
-    R = d0 + 1.0
-    s = np.arange(-R + hq / 2, R, hq)
-    X, Y, Z = np.meshgrid(s, s, s, indexing="ij")
-    P = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
-    d = np.linalg.norm(P, axis=1)
-    keep = d < R
-    P, d = P[keep] + grid.center, d[keep]
-    UI = np.where(d > d0, 0.5 * k * (d - d0) ** 2, 0.0)
-    psi = sA * rgi(root)(P) ** 4 + sB * rgi(lja)(P) + q * rgi(elec)(P)
-    num = np.sum(np.exp(-b * (psi + UI))) * hq ** 3
-    a = b * k / 2
-    den = 4 / 3 * np.pi * d0 ** 3 + 4 * np.pi * (d0 ** 2 * np.sqrt(np.pi) / (2 * np.sqrt(a)) + d0 / a
-                                                + np.sqrt(np.pi) / (4 * a ** 1.5))
-    return -np.log(num / den)
+from systems import quadrature_bpmf
 
 
 def test_one_atom_bpmf_matches_quadrature():
@@ -42,7 +17,7 @@ def test_one_atom_bpmf_matches_quadrature():
     g = sys_.grid
     lig = S.one_atom_ligand()
     ljr, lja, elec = oracle.grid_direct_sum(sys_.receptor, g)
-    target = _quadrature_bpmf(g, ljr, lja, elec, lig)
+    target = quadrature_bpmf(g, ljr, lja, elec, lig)
     C, K, ncyc, nsteps, dt = 64, 8, 400, 40, 4.0
     rng = np.random.default_rng(5)
     legs = [S.bc_ladder(K, dt_fs=dt), S.cd_ladder(K, dt_fs=dt)]
