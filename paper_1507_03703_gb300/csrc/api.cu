@@ -300,7 +300,8 @@ algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, cons
     nbr[L->bonds[2 * t]].push_back(L->bonds[2 * t + 1]);
     nbr[L->bonds[2 * t + 1]].push_back(L->bonds[2 * t]);
   }
-  std::vector<uint32_t> excl(4 * na, 0u), one4(4 * na, 0u);
+  // pair type [j][i]: 0 nonbonded, 1 1-4 (three bonds apart), 2 excluded (within two bonds, or i == j)
+  std::vector<uint8_t> ptype((size_t)na * na, 0);
   std::vector<int> dist(na), queue(na);
   for (int i = 0; i < na; ++i) {
     std::fill(dist.begin(), dist.end(), -1);
@@ -317,19 +318,20 @@ algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, cons
         }
     }
     for (int j = 0; j < na; ++j) {
-      if (dist[j] >= 0 && dist[j] <= 2) excl[4 * i + j / 32] |= 1u << (j % 32);
-      else if (dist[j] == 3) one4[4 * i + j / 32] |= 1u << (j % 32);
+      if (dist[j] >= 0 && dist[j] <= 2) ptype[(size_t)j * na + i] = 2;
+      else if (dist[j] == 3) ptype[(size_t)j * na + i] = 1;
     }
   }
-  // per-atom incidence lists of bonded terms (type << 30 | role << 28 | term)
+  // per-atom lists of the bonded force slots that act on it (role-major slot numbering:
+  // bond t role r -> r nb + t; angle -> 2 nb + r nang + t; torsion -> 2 nb + 3 nang + r ntor + t)
   std::vector<std::vector<uint32_t>> inc(na);
   for (int t = 0; t < nb; ++t)
-    for (int r = 0; r < 2; ++r) inc[L->bonds[2 * t + r]].push_back((0u << 30) | ((uint32_t)r << 28) | (uint32_t)t);
+    for (int r = 0; r < 2; ++r) inc[L->bonds[2 * t + r]].push_back((uint32_t)(r * nb + t));
   for (int t = 0; t < nang; ++t)
-    for (int r = 0; r < 3; ++r) inc[L->angles[3 * t + r]].push_back((1u << 30) | ((uint32_t)r << 28) | (uint32_t)t);
+    for (int r = 0; r < 3; ++r) inc[L->angles[3 * t + r]].push_back((uint32_t)(2 * nb + r * nang + t));
   for (int t = 0; t < ntor; ++t)
     for (int r = 0; r < 4; ++r)
-      inc[L->torsions[4 * t + r]].push_back((2u << 30) | ((uint32_t)r << 28) | (uint32_t)t);
+      inc[L->torsions[4 * t + r]].push_back((uint32_t)(2 * nb + 3 * nang + r * ntor + t));
   int ninc = 0;
   for (auto& v : inc) ninc += (int)v.size();
 
@@ -340,6 +342,7 @@ algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, cons
   Y.nang = nang;
   Y.ntor = ntor;
   Y.ninc = ninc;
+  Y.n_slots = 2 * nb + 3 * nang + 4 * ntor;
   int w = 0;
   auto take = [&](int words) {
     const int o = w;
@@ -348,8 +351,7 @@ algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, cons
   };
   Y.off_atom_a = take(4 * na);
   Y.off_atom_b = take(4 * na);
-  Y.off_excl = take(4 * na);
-  Y.off_one4 = take(4 * na);
+  Y.off_ptype = take((na * na + 3) / 4);
   Y.off_bond = take(4 * nb);
   Y.off_ang = take(8 * nang);
   Y.off_tor = take(16 * ntor);
@@ -371,11 +373,8 @@ algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, cons
     bf[Y.off_atom_b + 4 * i + 1] = (float)sqrt(L->eps[i]);
     bf[Y.off_atom_b + 4 * i + 2] = (float)m;
     bf[Y.off_atom_b + 4 * i + 3] = (float)sqrt(kForceToAccel / m);
-    for (int k = 0; k < 4; ++k) {
-      blob[Y.off_excl + 4 * i + k] = excl[4 * i + k];
-      blob[Y.off_one4 + 4 * i + k] = one4[4 * i + k];
-    }
   }
+  memcpy((uint8_t*)(blob.data() + Y.off_ptype), ptype.data(), ptype.size());
   for (int t = 0; t < nb; ++t) {
     bi[Y.off_bond + 4 * t + 0] = L->bonds[2 * t];
     bi[Y.off_bond + 4 * t + 1] = L->bonds[2 * t + 1];

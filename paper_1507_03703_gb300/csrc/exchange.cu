@@ -89,8 +89,22 @@ __global__ void __launch_bounds__(kExMaxWarps * 32) exchange_kernel(const ExArgs
           const U4 o = philox(A.seed, (uint32_t)((sw * A.max_sep + s - 1) * 65536 + a), lid, A.cycle,
                               kPurposeExchange);
           const double u = uniform53(o.x, o.y);
-          // exp(-d) >= 1 > u whenever d <= 0, so the exponential is only needed for d > 0
-          const bool acc = (d <= 0.0) || (u < exp(-d));
+          // The test u < exp(-d) in FP64.  exp(-d) >= 1 > u whenever d <= 0.  Otherwise an FP32
+          // estimate of ln u (error < 1e-5 absolute) decides every case more than 1e-3 away from
+          // the boundary ln u = -d; the rest takes the FP64 exponential.  The decision is the FP64
+          // one either way.
+          bool acc;
+          if (d <= 0.0) {
+            acc = true;
+          } else if (u == 0.0) {
+            acc = 0.0 < exp(-d);
+          } else {
+            const float lu = __logf((float)u);
+            const float md = (float)(-d);
+            if (lu < md - 1e-3f) acc = true;
+            else if (lu > md + 1e-3f) acc = false;
+            else acc = u < exp(-d);
+          }
           s_cnt[(s - 1) * K + a] += 1u;
           if (acc) {
             s_cfg[a] = yi;
@@ -125,7 +139,10 @@ cudaError_t launch_exchange(cudaStream_t s, const algdock_ctx& c, int n_ladders,
   const size_t fixed = (size_t)3 * K * sizeof(double);
   const size_t per_warp = (size_t)K * (sizeof(SlotE) + sizeof(int)) + (size_t)2 * max_sep * K * sizeof(unsigned);
   const size_t budget = 200 * 1024;
-  int warps = kExMaxWarps;
+  // Each ladder is a chain of dependent phases, so the launch is latency-bound: spread the
+  // ladders over all SMs first (one warp per block until there are two blocks per SM).
+  int warps = n_ladders / (2 * 152);
+  warps = warps < 1 ? 1 : (warps > kExMaxWarps ? kExMaxWarps : warps);
   while (warps > 1 && fixed + warps * per_warp > budget) --warps;
   if (fixed + warps * per_warp > budget) return cudaErrorInvalidValue;
   const size_t smem = fixed + warps * per_warp;

@@ -5,8 +5,19 @@
 // Layout: one warp per replica; lane l owns atoms l, l+32, l+64 (APL = atoms per lane).  Positions,
 // velocities and forces of owned atoms stay in registers for the whole trajectory; the current
 // positions are mirrored in a per-warp shared-memory array so that every lane can read every atom.
-// The ligand's parameters and topology are staged once per CTA in shared memory.  Every force
-// is accumulated by the lane that owns the atom (no atomics), so results are deterministic.
+// The ligand's parameters and topology are staged once per CTA in shared memory.
+//
+// One force evaluation:
+//   1. bonded terms, one term per lane: each term's forces on its 2-4 atoms go to per-warp
+//      shared-memory slots (role-major, so consecutive lanes write consecutive words);
+//   2. per owned atom: the 8-corner gathers of the grid lattices and the sum of its bonded slots
+//      in a fixed order;
+//   3. nonbonded pairs, each owned atom against every other atom (the pair type table marks
+//      excluded and 1-4 pairs); when the last pass has at most 16 atoms, two lanes share an atom
+//      and split the partner range;
+//   4. the restraint on the warp-reduced centre of mass.
+// Every force is accumulated by one lane in a fixed order (no atomics), so results are
+// deterministic.
 #include <math.h>
 
 #include "internal.cuh"
@@ -20,8 +31,7 @@ constexpr unsigned kFull = 0xffffffffu;
 struct Lig {
   const float4* atom_a;  // (accel factor 4.184e-4/m, q, sqrt(A), sqrt(B))
   const float4* atom_b;  // (R*, sqrt(eps), m, sqrt(accel factor))
-  const uint4* excl;
-  const uint4* one4;
+  const uint8_t* ptype;  // [j][i]: 0 nonbonded, 1 1-4, 2 excluded (and i == j)
   const float4* bond;
   const int4* ang_i;
   const float4* ang_p;
@@ -30,15 +40,14 @@ struct Lig {
   const float4* tor_c;
   const float4* tor_s;
   const int* inc_start;
-  const uint32_t* inc;
+  const uint32_t* inc;  // slot indices
 };
 
 __device__ inline Lig bind_ligand(const uint32_t* s, const LigandLayout& L) {
   Lig g;
   g.atom_a = (const float4*)(s + L.off_atom_a);
   g.atom_b = (const float4*)(s + L.off_atom_b);
-  g.excl = (const uint4*)(s + L.off_excl);
-  g.one4 = (const uint4*)(s + L.off_one4);
+  g.ptype = (const uint8_t*)(s + L.off_ptype);
   g.bond = (const float4*)(s + L.off_bond);
   g.ang_i = (const int4*)(s + L.off_ang);
   g.ang_p = (const float4*)(s + L.off_ang + 4 * L.nang);
@@ -93,19 +102,16 @@ __device__ inline void axis_coord(float x, float o, float inv_h, int n, int& c, 
   t = frac;
 }
 
-// Trilinear value and gradient (in lattice units) of one channel from 8 corner values,
-// c[dz][dy][dx].
+// Trilinear value and gradient (in lattice units) of one channel from 8 corner values c_zyx.
 struct Tri {
   float v, gx, gy, gz;
 };
 __device__ inline Tri tri(const float c000, const float c001, const float c010, const float c011, const float c100,
                           const float c101, const float c110, const float c111, float tx, float ty, float tz) {
-  // along x
   const float a00 = fmaf(tx, c001 - c000, c000), d00 = c001 - c000;
   const float a01 = fmaf(tx, c011 - c010, c010), d01 = c011 - c010;
   const float a10 = fmaf(tx, c101 - c100, c100), d10 = c101 - c100;
   const float a11 = fmaf(tx, c111 - c110, c110), d11 = c111 - c110;
-  // along y
   const float b0 = fmaf(ty, a01 - a00, a00), bx0 = fmaf(ty, d01 - d00, d00), by0 = a01 - a00;
   const float b1 = fmaf(ty, a11 - a10, a10), bx1 = fmaf(ty, d11 - d10, d10), by1 = a11 - a10;
   Tri r;
@@ -117,8 +123,8 @@ __device__ inline Tri tri(const float c000, const float c001, const float c010, 
 }
 
 struct GridOut {
-  float e_g, e_sg;         // Psi_g, Psi_sg contributions of this atom
-  float fx, fy, fz;        // -(w_sg dPsi_sg + w_g dPsi_g)/dx
+  float e_g, e_sg;   // Psi_g, Psi_sg contributions of this atom
+  float fx, fy, fz;  // -(w_sg dPsi_sg + w_g dPsi_g)/dx
   bool outside;
 };
 
@@ -177,9 +183,9 @@ __device__ inline GridOut grid_atom(const GridDev& G, float x, float y, float z,
 }
 
 struct Energies {
-  float lig;   // bonded + nonbonded (each pair counted from both ends, halved)
-  float rest;  // restraint
-  float sg, g; // grid terms
+  float lig;    // bonded + nonbonded (pairs counted from both ends, halved)
+  float rest;   // restraint
+  float sg, g;  // grid terms
 };
 
 __device__ inline float3 sub(float4 a, float4 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
@@ -187,43 +193,51 @@ __device__ inline float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y +
 __device__ inline float3 cross(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
+__device__ inline void put(float* sx, float* sy, float* sz, int s, float3 f) {
+  sx[s] = f.x;
+  sy[s] = f.y;
+  sz[s] = f.z;
+}
 
-// Force on atom `self` (role `role`) from one bonded term, and the term's energy (counted by role 0).
-__device__ inline float3 bonded_force(const Lig& L, const float4* xs, uint32_t code, float& energy) {
-  const uint32_t type = code >> 30, role = (code >> 28) & 3u, t = code & 0x0fffffffu;
-  float3 f = make_float3(0.f, 0.f, 0.f);
+// Step 1: every bonded term once, one per lane; per-role forces to the slot arrays.
+// Slots: bond t role r -> r*nb + t; angle -> 2nb + r*nang + t; torsion -> 2nb + 3nang + r*ntor + t.
+template <bool ENERGY>
+__device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const float4* xs, float* sx, float* sy,
+                                     float* sz) {
+  const int lane = threadIdx.x & 31;
   float e = 0.f;
-  if (type == 0) {  // bond k (r - r0)^2
+  const int nb = LL.nb, nang = LL.nang, ntor = LL.ntor;
+  for (int t = lane; t < nb; t += 32) {  // k (r - r0)^2
     const float4 bp = L.bond[t];
-    const int i = __float_as_int(bp.x), j = __float_as_int(bp.y);
-    const float3 d = sub(xs[i], xs[j]);
+    const float3 d = sub(xs[__float_as_int(bp.x)], xs[__float_as_int(bp.y)]);
     const float r = sqrtf(dot(d, d));
     const float dr = r - bp.w;
-    e = bp.z * dr * dr;
-    const float c = (role == 0 ? -2.f : 2.f) * bp.z * dr / r;
-    f = make_float3(c * d.x, c * d.y, c * d.z);
-  } else if (type == 1) {  // angle k (theta - theta0)^2
+    if (ENERGY) e += bp.z * dr * dr;
+    const float c = -2.f * bp.z * dr / r;
+    put(sx, sy, sz, t, make_float3(c * d.x, c * d.y, c * d.z));
+    put(sx, sy, sz, nb + t, make_float3(-c * d.x, -c * d.y, -c * d.z));
+  }
+  const int ab = 2 * nb;
+  for (int t = lane; t < nang; t += 32) {  // k (theta - theta0)^2
     const int4 id = L.ang_i[t];
     const float4 ap = L.ang_p[t];
     const float3 u = sub(xs[id.x], xs[id.y]);
     const float3 w = sub(xs[id.z], xs[id.y]);
     const float lu2 = dot(u, u), lw2 = dot(w, w);
     const float inv_luw = rsqrtf(lu2 * lw2);
-    float c = dot(u, w) * inv_luw;
-    c = fminf(1.f, fmaxf(-1.f, c));
-    const float th = acosf(c);
-    const float dth = th - ap.y;
-    e = ap.x * dth * dth;
-    const float sn = fmaxf(sqrtf(1.f - c * c), 1e-6f);
-    const float coef = 2.f * ap.x * dth / sn;
-    const float3 fa = make_float3(coef * (w.x * inv_luw - c * u.x / lu2), coef * (w.y * inv_luw - c * u.y / lu2),
-                                  coef * (w.z * inv_luw - c * u.z / lu2));
-    const float3 fc = make_float3(coef * (u.x * inv_luw - c * w.x / lw2), coef * (u.y * inv_luw - c * w.y / lw2),
-                                  coef * (u.z * inv_luw - c * w.z / lw2));
-    if (role == 0) f = fa;
-    else if (role == 2) f = fc;
-    else f = make_float3(-(fa.x + fc.x), -(fa.y + fc.y), -(fa.z + fc.z));
-  } else {  // torsion sum_n V_n/2 (1 + cos(n phi - gamma_n))
+    const float c = fminf(1.f, fmaxf(-1.f, dot(u, w) * inv_luw));
+    const float dth = acosf(c) - ap.y;
+    if (ENERGY) e += ap.x * dth * dth;
+    const float coef = 2.f * ap.x * dth / fmaxf(sqrtf(1.f - c * c), 1e-6f);
+    const float cu = coef * c / lu2, cw = coef * c / lw2, cx = coef * inv_luw;
+    const float3 fa = make_float3(cx * w.x - cu * u.x, cx * w.y - cu * u.y, cx * w.z - cu * u.z);
+    const float3 fc = make_float3(cx * u.x - cw * w.x, cx * u.y - cw * w.y, cx * u.z - cw * w.z);
+    put(sx, sy, sz, ab + t, fa);
+    put(sx, sy, sz, ab + nang + t, make_float3(-(fa.x + fc.x), -(fa.y + fc.y), -(fa.z + fc.z)));
+    put(sx, sy, sz, ab + 2 * nang + t, fc);
+  }
+  const int tb = ab + 3 * nang;
+  for (int t = lane; t < ntor; t += 32) {  // sum_n V_n/2 (1 + cos(n phi - gamma_n))
     const int4 id = L.tor_i[t];
     const float4 V = L.tor_v[t], cg = L.tor_c[t], sg = L.tor_s[t];
     const float3 b1 = sub(xs[id.y], xs[id.x]);
@@ -234,43 +248,111 @@ __device__ inline float3 bonded_force(const Lig& L, const float4* xs, uint32_t c
     const float lb2 = sqrtf(lb22);
     const float n1s = fmaxf(dot(n1, n1), 1e-20f), n2s = fmaxf(dot(n2, n2), 1e-20f);
     const float inv = rsqrtf(n1s * n2s);
-    const float cp = dot(n1, n2) * inv;           // cos phi
-    const float sp = lb2 * dot(b1, n2) * inv;     // sin phi
+    const float cp = dot(n1, n2) * inv;        // cos phi
+    const float sp = lb2 * dot(b1, n2) * inv;  // sin phi
     const float c2 = 2.f * cp * cp - 1.f, s2 = 2.f * sp * cp;
     const float c3 = cp * (4.f * cp * cp - 3.f), s3 = sp * (3.f - 4.f * sp * sp);
-    // V/2 (1 + cos(n phi) cos g + sin(n phi) sin g);  dE/dphi = V/2 n (cos(n phi) sin g - sin(n phi) cos g)
-    e = V.x * (1.f + cp * cg.x + sp * sg.x) + V.y * (1.f + c2 * cg.y + s2 * sg.y) + V.z * (1.f + c3 * cg.z + s3 * sg.z);
+    if (ENERGY)
+      e += V.x * (1.f + cp * cg.x + sp * sg.x) + V.y * (1.f + c2 * cg.y + s2 * sg.y) +
+           V.z * (1.f + c3 * cg.z + s3 * sg.z);
+    // dE/dphi = sum_n V_n/2 n (cos(n phi) sin g - sin(n phi) cos g)
     const float dE = V.x * (cp * sg.x - sp * cg.x) + 2.f * V.y * (c2 * sg.y - s2 * cg.y) +
                      3.f * V.z * (c3 * sg.z - s3 * cg.z);
-    const float ai = -lb2 / n1s, al = lb2 / n2s;
+    const float ai = dE * lb2 / n1s, al = -dE * lb2 / n2s;  // F_i = ai n1, F_l = al n2
     const float p = dot(b1, b2) / lb22, q = dot(b3, b2) / lb22;
-    float3 d;
-    if (role == 0) d = make_float3(ai * n1.x, ai * n1.y, ai * n1.z);
-    else if (role == 3) d = make_float3(al * n2.x, al * n2.y, al * n2.z);
-    else if (role == 1) {
-      const float ci = -(1.f + p) * ai, cl = q * al;
-      d = make_float3(ci * n1.x + cl * n2.x, ci * n1.y + cl * n2.y, ci * n1.z + cl * n2.z);
-    } else {
-      const float ci = p * ai, cl = -(1.f + q) * al;
-      d = make_float3(ci * n1.x + cl * n2.x, ci * n1.y + cl * n2.y, ci * n1.z + cl * n2.z);
-    }
-    f = make_float3(-dE * d.x, -dE * d.y, -dE * d.z);
+    const float3 fi = make_float3(ai * n1.x, ai * n1.y, ai * n1.z);
+    const float3 fl = make_float3(al * n2.x, al * n2.y, al * n2.z);
+    const float3 fj = make_float3(-(1.f + p) * fi.x + q * fl.x, -(1.f + p) * fi.y + q * fl.y,
+                                  -(1.f + p) * fi.z + q * fl.z);
+    const float3 fk = make_float3(p * fi.x - (1.f + q) * fl.x, p * fi.y - (1.f + q) * fl.y,
+                                  p * fi.z - (1.f + q) * fl.z);
+    put(sx, sy, sz, tb + t, fi);
+    put(sx, sy, sz, tb + ntor + t, fj);
+    put(sx, sy, sz, tb + 2 * ntor + t, fk);
+    put(sx, sy, sz, tb + 3 * ntor + t, fl);
   }
-  energy = (role == 0) ? e : 0.f;
-  return f;
+  return e;
+}
+
+// Step 3: nonbonded pairs.  Pass a covers atoms 32a .. 32a+31; a pass with at most 16 atoms gives
+// each atom two lanes, which split the partner range and combine with one shuffle.
+template <int APL, bool ENERGY>
+__device__ inline void nonbonded(const Lig& L, int na, const float4* xs, float (&F)[APL][3], float& el) {
+  const int lane = threadIdx.x & 31;
+  float e2 = 0.f;
+#pragma unroll
+  for (int a = 0; a < APL; ++a) {
+    const int base = 32 * a;
+    const int m = na - base;
+    if (m <= 0) break;
+    const bool split = m <= 16;
+    const int il = split ? (lane & 15) : lane;
+    const int i = base + il;
+    const bool act = il < m;
+    int jb = 0, je = na;
+    if (split) {
+      const int h = (na + 1) >> 1;
+      jb = lane < 16 ? 0 : h;
+      je = lane < 16 ? h : na;
+    }
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    if (act) {
+      const float4 pi = xs[i];
+      const float4 bi = L.atom_b[i];
+      const float qi = (float)kCoulomb * pi.w, ri = bi.x, si = bi.y;
+      const uint8_t* ty_col = L.ptype + i;
+      for (int j = jb; j < je; ++j) {
+        const float4 pj = xs[j];
+        const float2 bj = *(const float2*)&L.atom_b[j];
+        const uint32_t ty = ty_col[j * na];
+        const bool excluded = ty == 2u;
+        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        const float r2 = excluded ? 1.f : fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float inv_r = rsqrtf(r2);
+        const float inv_r2 = inv_r * inv_r;
+        const float R = ri + bj.x;
+        const float s2 = R * R * inv_r2;
+        const float s6 = s2 * s2 * s2;
+        const float eps = excluded ? 0.f : (ty == 1u ? 0.5f : 1.f) * (si * bj.y);
+        const float qq = excluded ? 0.f : (ty == 1u ? (float)(1.0 / 1.2) : 1.f) * (qi * pj.w);
+        const float eel = qq * inv_r;
+        const float fr = fmaf(12.f * eps, s6 * s6 - s6, eel) * inv_r2;
+        fx = fmaf(fr, dx, fx);
+        fy = fmaf(fr, dy, fy);
+        fz = fmaf(fr, dz, fz);
+        if (ENERGY) e2 += fmaf(eps, s6 * s6 - 2.f * s6, eel);
+      }
+    }
+    if (split) {
+      fx += __shfl_xor_sync(kFull, fx, 16);
+      fy += __shfl_xor_sync(kFull, fy, 16);
+      fz += __shfl_xor_sync(kFull, fz, 16);
+    }
+    if (lane < m && (!split || lane < 16)) {
+      F[a][0] += fx;
+      F[a][1] += fy;
+      F[a][2] += fz;
+    }
+  }
+  if (ENERGY) el += 0.5f * e2;
 }
 
 // Forces on the lane's atoms (and, if ENERGY, the lane's partial energies).  xs holds all
-// positions (x, y, z, q).
+// positions (x, y, z, q); sf is the warp's bonded-slot scratch (3 * n_slots floats).
 template <int APL, bool ENERGY>
-__device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const GridDev& G, const float4* xs,
+__device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const GridDev& G, const float4* xs, float* sf,
                                 const float (&x)[APL][3], float (&F)[APL][3], float w_sg, float w_g, bool all_grids,
                                 Energies& en, int& outside) {
   const int lane = threadIdx.x & 31;
-  const int na = LL.na;
+  const int na = LL.na, ns = LL.n_slots;
+  float* sx = sf;
+  float* sy = sf + ns;
+  float* sz = sf + 2 * ns;
+  float el = bonded_terms<ENERGY>(L, LL, xs, sx, sy, sz);
+  __syncwarp();
   const bool hard = all_grids || w_g != 0.f;
   const bool soft = all_grids || w_sg != 0.f;
-  float el = 0.f, eg = 0.f, esg = 0.f;
+  float eg = 0.f, esg = 0.f;
   float mx = 0.f, my = 0.f, mz = 0.f;
 #pragma unroll
   for (int a = 0; a < APL; ++a) {
@@ -278,10 +360,10 @@ __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const Grid
     F[a][0] = F[a][1] = F[a][2] = 0.f;
     if (i >= na) continue;
     const float4 pa = L.atom_a[i];
-    const float4 pb = L.atom_b[i];
-    mx += pb.z * x[a][0];
-    my += pb.z * x[a][1];
-    mz += pb.z * x[a][2];
+    const float m = L.atom_b[i].z;
+    mx += m * x[a][0];
+    my += m * x[a][1];
+    mz += m * x[a][2];
     if (hard || soft) {
       const GridOut go = grid_atom(G, x[a][0], x[a][1], x[a][2], pa.z, pa.w, pa.y, hard, soft, w_sg, w_g);
       F[a][0] += go.fx;
@@ -291,56 +373,15 @@ __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const Grid
       esg += go.e_sg;
       outside += go.outside ? 1 : 0;
     }
-    // nonbonded pairs: every j, masked by the exclusion and 1-4 bits (branch-free)
-    const uint4 ex = L.excl[i], o4 = L.one4[i];
-    const float xi = x[a][0], yi = x[a][1], zi = x[a][2];
-    const float qi = (float)kCoulomb * pa.y, ri = pb.x, si = pb.y;
-    float fx = 0.f, fy = 0.f, fz = 0.f, e2 = 0.f;
-#pragma unroll
-    for (int w = 0; w < APL; ++w) {
-      const uint32_t exw = w == 0 ? ex.x : (w == 1 ? ex.y : ex.z);
-      const uint32_t o4w = w == 0 ? o4.x : (w == 1 ? o4.y : o4.z);
-      const int jmax = min(32, na - 32 * w);
-      for (int jj = 0; jj < jmax; ++jj) {
-        const int j = 32 * w + jj;
-        const float4 pj = xs[j];
-        const float4 bj = L.atom_b[j];
-        const bool excluded = (exw >> jj) & 1u;
-        const bool is14 = (o4w >> jj) & 1u;
-        const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        r2 = excluded ? 1.f : r2;
-        const float inv_r = rsqrtf(r2);
-        const float inv_r2 = inv_r * inv_r;
-        const float R = ri + bj.x;
-        const float s2 = R * R * inv_r2;
-        const float s6 = s2 * s2 * s2;
-        const float eps = excluded ? 0.f : (is14 ? 0.5f : 1.f) * si * bj.y;
-        const float qq = excluded ? 0.f : (is14 ? (float)(1.0 / 1.2) : 1.f) * qi * pj.w;
-        const float elj = eps * (s6 * s6 - 2.f * s6);
-        const float eel = qq * inv_r;
-        const float fr = (12.f * eps * (s6 * s6 - s6) + eel) * inv_r2;
-        fx = fmaf(fr, dx, fx);
-        fy = fmaf(fr, dy, fy);
-        fz = fmaf(fr, dz, fz);
-        if (ENERGY) e2 += elj + eel;
-      }
-    }
-    F[a][0] += fx;
-    F[a][1] += fy;
-    F[a][2] += fz;
-    if (ENERGY) el += 0.5f * e2;
-    // bonded terms through the atom's incidence list
-    const int b0 = L.inc_start[i], b1 = L.inc_start[i + 1];
-    for (int b = b0; b < b1; ++b) {
-      float e1;
-      const float3 f = bonded_force(L, xs, L.inc[b], e1);
-      F[a][0] += f.x;
-      F[a][1] += f.y;
-      F[a][2] += f.z;
-      if (ENERGY) el += e1;
+    const int b1 = L.inc_start[i + 1];
+    for (int b = L.inc_start[i]; b < b1; ++b) {
+      const uint32_t s = L.inc[b];
+      F[a][0] += sx[s];
+      F[a][1] += sy[s];
+      F[a][2] += sz[s];
     }
   }
+  nonbonded<APL, ENERGY>(L, na, xs, F, el);
   // restraint on the centre of mass
   mx = warp_sumf(mx);
   my = warp_sumf(my);
@@ -392,11 +433,26 @@ __device__ inline void stage_ligand(uint32_t* s, const uint32_t* __restrict__ bl
   for (int i = threadIdx.x; i < words / 4; i += blockDim.x) dst[i] = src[i];
 }
 
+// Shared memory of one block: ligand blob, then per warp 32*APL float4 positions and the
+// bonded-slot scratch (3 * n_slots floats, rounded up to 16 bytes).
+__host__ __device__ inline int scratch_words(const LigandLayout& L) { return (3 * L.n_slots + 3) & ~3; }
+
+struct WarpSmem {
+  float4* xs;
+  float* sf;
+};
+template <int APL>
+__device__ inline WarpSmem warp_smem(uint32_t* smem, const LigandLayout& LL, int warp) {
+  uint32_t* p = smem + LL.words + warp * (4 * 32 * APL + scratch_words(LL));
+  return WarpSmem{(float4*)p, (float*)(p + 4 * 32 * APL)};
+}
+
 struct HmcArgs {
   GridDev G;
   LigandLayout LL;
   const uint32_t* blob;
   const StateDev* states;
+  int n_states;
   int64_t n_rep;
   const int32_t* state_of;
   float* x;
@@ -408,20 +464,19 @@ struct HmcArgs {
   uint32_t cycle;
   int64_t rep_offset;
   int64_t* counters;
-  int n_states;
 };
 
 template <int APL>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) hmc_kernel(const HmcArgs A) {
   extern __shared__ __align__(16) uint32_t smem[];
   stage_ligand(smem, A.blob, A.LL.words);
-  float4* xs_all = (float4*)(smem + A.LL.words);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
   if (r >= A.n_rep) return;
   const Lig L = bind_ligand(smem, A.LL);
-  float4* xs = xs_all + warp * (32 * APL);
+  const WarpSmem ws = warp_smem<APL>(smem, A.LL, warp);
+  float4* xs = ws.xs;
   const int na = A.LL.na;
   const int k = A.state_of[r];
   if ((unsigned)k >= (unsigned)A.n_states) {  // invalid state index: leave the replica untouched
@@ -473,7 +528,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) hmc_kernel(const HmcArgs 
   int outside = 0;
   Energies en;
   double c0[4], c1[4];
-  evaluate<APL, true>(A.LL, L, A.G, xs, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
+  evaluate<APL, true>(A.LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
   reduce_components(en, c0);
   const double K0 = 0.5 * kKineticToKcal * warp_sum((double)kin);
   for (int s = 0; s < A.n_steps; ++s) {
@@ -489,7 +544,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) hmc_kernel(const HmcArgs 
         }
       }
     }
-    __syncwarp();  // all lanes finished reading the previous positions
+    __syncwarp();  // all lanes finished reading the previous positions and bonded slots
 #pragma unroll
     for (int a = 0; a < APL; ++a) {
       const int i = lane + 32 * a;
@@ -503,9 +558,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) hmc_kernel(const HmcArgs 
     }
     __syncwarp();
     if (s + 1 < A.n_steps) {
-      evaluate<APL, false>(A.LL, L, A.G, xs, x, F, st.w_sg_f, st.w_g_f, false, en, outside);
+      evaluate<APL, false>(A.LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, false, en, outside);
     } else {
-      evaluate<APL, true>(A.LL, L, A.G, xs, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
+      evaluate<APL, true>(A.LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
       reduce_components(en, c1);
     }
 #pragma unroll
@@ -550,7 +605,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) hmc_kernel(const HmcArgs 
     if (A.acc) A.acc[r] = accept ? 1 : 0;
   }
   if (A.counters) {
-    int out_total = __reduce_add_sync(kFull, outside);
+    const int out_total = __reduce_add_sync(kFull, outside);
     if (lane == 0) {
       if (accept) atomicAdd((unsigned long long*)&A.counters[ALGDOCK_CNT_ACCEPTED], 1ull);
       if (!isfinite(dH)) atomicAdd((unsigned long long*)&A.counters[ALGDOCK_CNT_NONFINITE], 1ull);
@@ -559,76 +614,49 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) hmc_kernel(const HmcArgs 
   }
 }
 
-// Energy-only evaluation of stored configurations (one warp each): components for u_kn.
-template <int APL>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) evaluate_kernel(GridDev G, LigandLayout LL,
-                                                                       const uint32_t* blob, int64_t N,
-                                                                       const float* __restrict__ xin,
-                                                                       double* comps) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  stage_ligand(smem, blob, LL.words);
-  float4* xs_all = (float4*)(smem + LL.words);
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t n = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-  if (n >= N) return;
-  const Lig L = bind_ligand(smem, LL);
-  float4* xs = xs_all + warp * (32 * APL);
-  const int na = LL.na;
-  float x[APL][3], F[APL][3];
-#pragma unroll
-  for (int a = 0; a < APL; ++a) {
-    const int i = lane + 32 * a;
-    if (i < na) {
-      const float* src = xin + (n * na + i) * 3;
-      x[a][0] = src[0];
-      x[a][1] = src[1];
-      x[a][2] = src[2];
-      xs[i] = make_float4(x[a][0], x[a][1], x[a][2], L.atom_a[i].y);
-    } else {
-      x[a][0] = x[a][1] = x[a][2] = 0.f;
-    }
-  }
-  __syncwarp();
-  Energies en;
-  int outside = 0;
-  evaluate<APL, true>(LL, L, G, xs, x, F, 0.f, 0.f, true, en, outside);
-  double c[4];
-  reduce_components(en, c);
-  if (lane < 4) comps[n * 4 + lane] = c[lane];
-}
+// Energy (and, with force != NULL, force) of stored configurations, one warp each.  With
+// state_of == NULL the grid weights are zero (components only).
+struct EvalArgs {
+  GridDev G;
+  LigandLayout LL;
+  const uint32_t* blob;
+  const StateDev* states;
+  int n_states;
+  int64_t N;
+  const int32_t* state_of;
+  const float* x;
+  float* force;
+  double* comps;
+};
 
-// Energy and force of configurations at given states (one warp each).
 template <int APL>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) force_kernel(GridDev G, LigandLayout LL, const uint32_t* blob,
-                                                                    const StateDev* __restrict__ states, int n_states,
-                                                                    int64_t N,
-                                                                    const int32_t* __restrict__ state_of,
-                                                                    const float* __restrict__ xin, float* fout,
-                                                                    double* comps) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) eval_kernel(const EvalArgs A) {
   extern __shared__ __align__(16) uint32_t smem[];
-  stage_ligand(smem, blob, LL.words);
-  float4* xs_all = (float4*)(smem + LL.words);
+  stage_ligand(smem, A.blob, A.LL.words);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-  if (n >= N) return;
-  const Lig L = bind_ligand(smem, LL);
-  float4* xs = xs_all + warp * (32 * APL);
-  const int na = LL.na;
-  const int k = state_of[n];
-  if ((unsigned)k >= (unsigned)n_states) return;  // invalid state index: no output
-  const StateDev st = states[k];
+  if (n >= A.N) return;
+  const Lig L = bind_ligand(smem, A.LL);
+  const WarpSmem ws = warp_smem<APL>(smem, A.LL, warp);
+  const int na = A.LL.na;
+  float w_sg = 0.f, w_g = 0.f;
+  if (A.state_of) {
+    const int k = A.state_of[n];
+    if ((unsigned)k >= (unsigned)A.n_states) return;  // invalid state index: no output
+    w_sg = A.states[k].w_sg_f;
+    w_g = A.states[k].w_g_f;
+  }
   float x[APL][3], F[APL][3];
 #pragma unroll
   for (int a = 0; a < APL; ++a) {
     const int i = lane + 32 * a;
     if (i < na) {
-      const float* src = xin + (n * na + i) * 3;
+      const float* src = A.x + (n * na + i) * 3;
       x[a][0] = src[0];
       x[a][1] = src[1];
       x[a][2] = src[2];
-      xs[i] = make_float4(x[a][0], x[a][1], x[a][2], L.atom_a[i].y);
+      ws.xs[i] = make_float4(x[a][0], x[a][1], x[a][2], L.atom_a[i].y);
     } else {
       x[a][0] = x[a][1] = x[a][2] = 0.f;
     }
@@ -636,20 +664,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) force_kernel(GridDev G, L
   __syncwarp();
   Energies en;
   int outside = 0;
-  evaluate<APL, true>(LL, L, G, xs, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
+  evaluate<APL, true>(A.LL, L, A.G, ws.xs, ws.sf, x, F, w_sg, w_g, true, en, outside);
   double c[4];
   reduce_components(en, c);
+  if (A.force) {
 #pragma unroll
-  for (int a = 0; a < APL; ++a) {
-    const int i = lane + 32 * a;
-    if (i < na) {
-      float* dst = fout + (n * na + i) * 3;
-      dst[0] = F[a][0];
-      dst[1] = F[a][1];
-      dst[2] = F[a][2];
+    for (int a = 0; a < APL; ++a) {
+      const int i = lane + 32 * a;
+      if (i < na) {
+        float* dst = A.force + (n * na + i) * 3;
+        dst[0] = F[a][0];
+        dst[1] = F[a][1];
+        dst[2] = F[a][2];
+      }
     }
   }
-  if (comps && lane < 4) comps[n * 4 + lane] = c[lane];
+  if (A.comps && lane < 4) A.comps[n * 4 + lane] = c[lane];
 }
 
 // u_kn[k][n] from stored components (k over k_count states from k_begin).
@@ -671,89 +701,48 @@ __global__ void ukn_kernel(const StateDev* __restrict__ states, int k_begin, int
 
 int atoms_per_lane(int na) { return na <= 32 ? 1 : (na <= 64 ? 2 : 3); }
 
+size_t block_smem(const LigandLayout& L, int apl) {
+  return ((size_t)L.words + (size_t)kWarpsPerBlock * (4 * 32 * apl + scratch_words(L))) * 4;
+}
+
+template <typename Kernel, typename Args>
+cudaError_t launch_templated(Kernel k1, Kernel k2, Kernel k3, int apl, size_t smem, int64_t items, cudaStream_t s,
+                             const Args& A) {
+  Kernel k = apl == 1 ? k1 : (apl == 2 ? k2 : k3);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  k<<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_hmc(cudaStream_t s, const algdock_ctx& c, int64_t n_rep, const int32_t* state_of, float* x,
                        double* comps, double* dH, uint8_t* acc, int n_steps, uint64_t seed, uint64_t cycle,
                        int64_t rep_offset, int64_t* counters) {
   if (n_rep == 0) return cudaSuccess;
-  HmcArgs A{c.grid, c.lig, c.d_blob, c.d_states, n_rep, state_of, x, comps, dH, acc, n_steps, seed,
-            (uint32_t)cycle, rep_offset, counters, c.K};
+  HmcArgs A{c.grid, c.lig, c.d_blob, c.d_states, c.K, n_rep, state_of, x, comps, dH, acc, n_steps, seed,
+            (uint32_t)cycle, rep_offset, counters};
   const int apl = atoms_per_lane(c.lig.na);
-  const size_t smem = (size_t)c.lig.words * 4 + (size_t)kWarpsPerBlock * 32 * apl * sizeof(float4);
-  const int64_t blocks = (n_rep + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  cudaError_t e = cudaSuccess;
-  switch (apl) {
-    case 1:
-      e = cudaFuncSetAttribute(hmc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) hmc_kernel<1><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(A);
-      break;
-    case 2:
-      e = cudaFuncSetAttribute(hmc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) hmc_kernel<2><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(A);
-      break;
-    default:
-      e = cudaFuncSetAttribute(hmc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) hmc_kernel<3><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(A);
-      break;
-  }
-  return e != cudaSuccess ? e : cudaGetLastError();
+  return launch_templated(hmc_kernel<1>, hmc_kernel<2>, hmc_kernel<3>, apl, block_smem(c.lig, apl), n_rep, s, A);
+}
+
+static cudaError_t launch_eval(cudaStream_t s, const algdock_ctx& c, int64_t N, const int32_t* state_of,
+                               const float* x, float* force, double* comps) {
+  if (N == 0) return cudaSuccess;
+  EvalArgs A{c.grid, c.lig, c.d_blob, c.d_states, c.K, N, state_of, x, force, comps};
+  const int apl = atoms_per_lane(c.lig.na);
+  return launch_templated(eval_kernel<1>, eval_kernel<2>, eval_kernel<3>, apl, block_smem(c.lig, apl), N, s, A);
 }
 
 cudaError_t launch_evaluate(cudaStream_t s, const algdock_ctx& c, int64_t N, const float* x, double* comps) {
-  if (N == 0) return cudaSuccess;
-  const int apl = atoms_per_lane(c.lig.na);
-  const size_t smem = (size_t)c.lig.words * 4 + (size_t)kWarpsPerBlock * 32 * apl * sizeof(float4);
-  const int64_t blocks = (N + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  cudaError_t e = cudaSuccess;
-  switch (apl) {
-    case 1:
-      e = cudaFuncSetAttribute(evaluate_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess)
-        evaluate_kernel<1><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(c.grid, c.lig, c.d_blob, N, x, comps);
-      break;
-    case 2:
-      e = cudaFuncSetAttribute(evaluate_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess)
-        evaluate_kernel<2><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(c.grid, c.lig, c.d_blob, N, x, comps);
-      break;
-    default:
-      e = cudaFuncSetAttribute(evaluate_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess)
-        evaluate_kernel<3><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(c.grid, c.lig, c.d_blob, N, x, comps);
-      break;
-  }
-  return e != cudaSuccess ? e : cudaGetLastError();
+  return launch_eval(s, c, N, nullptr, x, nullptr, comps);
 }
 
 cudaError_t launch_energy_force(cudaStream_t s, const algdock_ctx& c, int64_t N, const int32_t* state_of,
                                 const float* x, float* force, double* comps) {
-  if (N == 0) return cudaSuccess;
-  const int apl = atoms_per_lane(c.lig.na);
-  const size_t smem = (size_t)c.lig.words * 4 + (size_t)kWarpsPerBlock * 32 * apl * sizeof(float4);
-  const int64_t blocks = (N + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  cudaError_t e = cudaSuccess;
-  switch (apl) {
-    case 1:
-      e = cudaFuncSetAttribute(force_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess)
-        force_kernel<1><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(c.grid, c.lig, c.d_blob, c.d_states, c.K, N,
-                                                                             state_of, x, force, comps);
-      break;
-    case 2:
-      e = cudaFuncSetAttribute(force_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess)
-        force_kernel<2><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(c.grid, c.lig, c.d_blob, c.d_states, c.K, N,
-                                                                             state_of, x, force, comps);
-      break;
-    default:
-      e = cudaFuncSetAttribute(force_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess)
-        force_kernel<3><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(c.grid, c.lig, c.d_blob, c.d_states, c.K, N,
-                                                                             state_of, x, force, comps);
-      break;
-  }
-  return e != cudaSuccess ? e : cudaGetLastError();
+  return launch_eval(s, c, N, state_of, x, force, comps);
 }
 
 cudaError_t launch_ukn(cudaStream_t s, const algdock_ctx& c, int64_t N, const double* comps, int k_begin,

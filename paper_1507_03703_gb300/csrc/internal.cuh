@@ -76,15 +76,15 @@ struct StateDev {
 // contiguous buffer that a CTA copies into shared memory.
 struct LigandLayout {
   int na, nb, nang, ntor, ninc;
+  int n_slots;     // bonded force slots: 2 nb + 3 nang + 4 ntor
   int off_atom_a;  // float4[na]: (accel factor 4.184e-4/m, q, sqrt(A), sqrt(B))
   int off_atom_b;  // float4[na]: (R*, sqrt(eps), m, sqrt(4.184e-4/m))
-  int off_excl;    // uint4[na]: bit j of word j/32 set if pair (i, j) is excluded (incl. i == j)
-  int off_one4;    // uint4[na]: bit j set if (i, j) is a 1-4 pair
+  int off_ptype;   // uint8[na][na], [j][i]: 0 nonbonded pair, 1 1-4 pair, 2 excluded (incl. i == j)
   int off_bond;    // float4[nb]: (i, j as int bits, k, r0)
   int off_ang;     // int4[nang] (i, j, k, 0) then float4[nang] (k, theta0, 0, 0)
   int off_tor;     // int4[ntor] (i, j, k, l), float4 (V1/2, V2/2, V3/2, 0), float4 cos(gamma), float4 sin(gamma)
   int off_inc_start;  // int[na + 1]
-  int off_inc;        // uint32[ninc]: type << 30 | role << 28 | term
+  int off_inc;        // uint32[ninc]: the bonded slots of each atom, in a fixed order
   int words;          // total (multiple of 4)
   float total_mass;
   float site[3];

@@ -95,4 +95,8 @@ def test_forces_at_layout_boundaries(base, n_atoms):
     w_sg, w_g, _ = osys.state_weights()
     for n in range(2 * K):
         c_o, F_o = osys.energy_force(x[n].astype(np.float64), w_sg[states[n]], w_g[states[n]])
-        assert np.linalg.norm(F[n] - F_o) / np.linalg.norm(F_o) <= 1e-5
+        ref = np.linalg.norm(F_o)
+        if ref == 0.0:  # e.g. one atom, no grid weight, inside the flat bottom: no force at all
+            assert np.all(F[n] == 0.0)
+        else:
+            assert np.linalg.norm(F[n] - F_o) / ref <= 1e-5
