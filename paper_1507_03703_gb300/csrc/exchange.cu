@@ -1,10 +1,13 @@
 // Hamiltonian replica exchange ("Sampling", Eq. (repXacc)): sweeps of swap attempts between
 // states 1..min(max_sep, K-1) apart, with the FP64 acceptance test.
 //
-// One warp per ladder.  Within one (separation, colour) phase the pairs (a, a+s) with
-// floor(a/s) % 2 == colour are disjoint, so the lanes attempt them concurrently; phases follow
-// one another in a fixed order, which is what makes the result a deterministic function of the
-// components and the Philox counters.
+// Within one (separation, colour) phase the pairs (a, a+s) with floor(a/s) % 2 == colour are
+// disjoint, so a warp's lanes attempt them concurrently; phases follow one another in a fixed
+// order, which makes the result a deterministic function of the components and the Philox
+// counters.  The slot components do not change during the sweeps, so for K <= 160 the reduced
+// energies u_k(x_i) of every state and slot are computed once per ladder into shared memory
+// (by all four warps of the ladder's block) before one warp runs the sweeps; larger ladders
+// evaluate them per attempt.  Both give bit-identical decisions: the same FP64 expression.
 #include <math.h>
 
 #include "internal.cuh"
@@ -13,6 +16,7 @@ namespace algdock {
 namespace {
 
 constexpr int kExMaxWarps = 4;
+constexpr int kMatrixMaxK = 160;  // K^2 doubles of shared memory
 
 struct SlotE {
   double e, psg, pg;  // U_L + U_I, Psi_sg, Psi_g of one slot
@@ -25,6 +29,19 @@ __device__ inline double reduced(double beta, double w_sg, double w_g, const Slo
   if (w_sg != 0.0) e = __dadd_rn(e, __dmul_rn(w_sg, c.psg));
   if (w_g != 0.0) e = __dadd_rn(e, __dmul_rn(w_g, c.pg));
   return __dmul_rn(beta, e);
+}
+
+// The test u < exp(-d) in FP64.  exp(-d) >= 1 > u whenever d <= 0.  Otherwise an FP32 estimate of
+// ln u (error < 1e-5 absolute) decides every case more than 1e-3 away from the boundary ln u = -d;
+// the rest (and u = 0) takes the FP64 exponential.  The decision is the FP64 one either way.
+__device__ inline bool accept_swap(double d, double u) {
+  if (d <= 0.0) return true;
+  if (u == 0.0) return 0.0 < exp(-d);
+  const float lu = __logf((float)u);
+  const float md = (float)(-d);
+  if (lu < md - 1e-3f) return true;
+  if (lu > md + 1e-3f) return false;
+  return u < exp(-d);
 }
 
 struct ExArgs {
@@ -41,16 +58,105 @@ struct ExArgs {
   int64_t* accepts;
 };
 
-__global__ void __launch_bounds__(kExMaxWarps * 32) exchange_kernel(const ExArgs A) {
+__device__ inline SlotE load_slot(const double* c) { return SlotE{__dadd_rn(c[0], c[1]), c[2], c[3]}; }
+
+// The sweeps of one ladder by one warp.  U(a, i) returns u_a(x_i).
+template <typename UFn>
+__device__ inline void sweeps(const ExArgs& A, int64_t l, int* s_cfg, unsigned* s_cnt, UFn U) {
+  const int K = A.K, lane = threadIdx.x & 31;
+  const int smax = min(A.max_sep, K - 1);
+  const uint32_t lid = (uint32_t)(A.ladder_offset + l);
+  for (int sw = 0; sw < A.n_sweeps; ++sw) {
+    for (int s = 1; s <= smax; ++s) {
+      for (int colour = 0; colour < 2; ++colour) {
+        for (int a = lane; a + s < K; a += 32) {
+          if ((a / s) % 2 != colour) continue;
+          const int b = a + s;
+          const int xi = s_cfg[a], yi = s_cfg[b];
+          const U4 o = philox(A.seed, (uint32_t)((sw * A.max_sep + s - 1) * 65536 + a), lid, A.cycle,
+                              kPurposeExchange);
+          double d = __dadd_rn(U(a, yi), U(b, xi));
+          d = __dsub_rn(d, U(a, xi));
+          d = __dsub_rn(d, U(b, yi));
+          const bool acc = accept_swap(d, uniform53(o.x, o.y));
+          s_cnt[(s - 1) * K + a] += 1u;
+          if (acc) {
+            s_cfg[a] = yi;
+            s_cfg[b] = xi;
+            s_cnt[(A.max_sep + s - 1) * K + a] += 1u;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
+__device__ inline void write_back(const ExArgs& A, int64_t l, const int* s_cfg, const unsigned* s_cnt) {
+  const int K = A.K, lane = threadIdx.x & 31;
+  for (int k = lane; k < K; k += 32) {
+    A.config_of[l * K + k] = s_cfg[k];
+    if (A.state_of) A.state_of[l * K + s_cfg[k]] = A.state_offset + k;
+  }
+  for (int i = lane; i < A.max_sep * K; i += 32) {
+    if (A.attempts && s_cnt[i]) atomicAdd((unsigned long long*)&A.attempts[i], (unsigned long long)s_cnt[i]);
+    const unsigned ac = s_cnt[A.max_sep * K + i];
+    if (A.accepts && ac) atomicAdd((unsigned long long*)&A.accepts[i], (unsigned long long)ac);
+  }
+}
+
+// Loads the ladder's configuration and clears its counters; false if config_of is not a list of
+// slots 0..K-1 (then the ladder is left untouched).
+__device__ inline bool load_ladder(const ExArgs& A, int64_t l, int* s_cfg, unsigned* s_cnt) {
+  const int K = A.K, lane = threadIdx.x & 31;
+  bool bad = false;
+  for (int i = lane; i < K; i += 32) {
+    s_cfg[i] = A.config_of[l * K + i];
+    bad |= (unsigned)s_cfg[i] >= (unsigned)K;
+  }
+  for (int i = lane; i < 2 * A.max_sep * K; i += 32) s_cnt[i] = 0u;
+  __syncwarp();
+  return !__any_sync(0xffffffffu, bad);
+}
+
+// One ladder per block: all warps fill u[k][i], warp 0 sweeps.
+__global__ void __launch_bounds__(kExMaxWarps * 32) exchange_matrix_kernel(const ExArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int K = A.K;
-  // per block: state table (beta, w_sg, w_g) then per warp: slots, config, counters
+  double* s_u = (double*)smem_raw;  // [K][K]
+  double* s_st = s_u + (size_t)K * K;  // [K][3]: beta, w_sg, w_g
+  SlotE* s_slot = (SlotE*)(s_st + 3 * K);
+  int* s_cfg = (int*)(s_slot + K);
+  unsigned* s_cnt = (unsigned*)(s_cfg + K);
+  const int64_t l = blockIdx.x;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const StateDev st = A.states[A.state_offset + k];
+    s_st[3 * k] = st.beta;
+    s_st[3 * k + 1] = st.w_sg;
+    s_st[3 * k + 2] = st.w_g;
+    s_slot[k] = load_slot(A.comps + (l * K + k) * 4);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int k = e / K, i = e - k * K;
+    s_u[e] = reduced(s_st[3 * k], s_st[3 * k + 1], s_st[3 * k + 2], s_slot[i]);
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  if (!load_ladder(A, l, s_cfg, s_cnt)) return;
+  sweeps(A, l, s_cfg, s_cnt, [&](int k, int i) { return s_u[k * K + i]; });
+  write_back(A, l, s_cfg, s_cnt);
+}
+
+// Several ladders per block, one warp each, reduced energies per attempt (any K up to 1024).
+__global__ void __launch_bounds__(kExMaxWarps * 32) exchange_direct_kernel(const ExArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = A.K;
   double* s_beta = (double*)smem_raw;
   double* s_wsg = s_beta + K;
   double* s_wg = s_wsg + K;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_warps = blockDim.x >> 5;
-  const int smax = min(A.max_sep, K - 1);
   SlotE* s_slot = (SlotE*)(s_wg + K) + (size_t)warp * K;
   int* s_cfg = (int*)((SlotE*)(s_wg + K) + (size_t)n_warps * K) + (size_t)warp * K;
   unsigned* s_cnt = (unsigned*)((int*)((SlotE*)(s_wg + K) + (size_t)n_warps * K) + (size_t)n_warps * K) +
@@ -64,67 +170,11 @@ __global__ void __launch_bounds__(kExMaxWarps * 32) exchange_kernel(const ExArgs
   __syncthreads();
   const int64_t l = (int64_t)blockIdx.x * n_warps + warp;
   if (l >= A.n_ladders) return;
-  for (int i = lane; i < K; i += 32) {
-    const double* c = A.comps + (l * K + i) * 4;
-    s_slot[i] = SlotE{__dadd_rn(c[0], c[1]), c[2], c[3]};
-    s_cfg[i] = A.config_of[l * K + i];
-  }
-  for (int i = lane; i < 2 * A.max_sep * K; i += 32) s_cnt[i] = 0u;
-  bool bad = false;
-  for (int i = lane; i < K; i += 32) bad |= (unsigned)s_cfg[i] >= (unsigned)K;
-  if (__any_sync(0xffffffffu, bad)) return;  // not a permutation of 0..K-1: leave the ladder untouched
-  __syncwarp();
-  const uint32_t lid = (uint32_t)(A.ladder_offset + l);
-  for (int sw = 0; sw < A.n_sweeps; ++sw) {
-    for (int s = 1; s <= smax; ++s) {
-      for (int colour = 0; colour < 2; ++colour) {
-        for (int a = lane; a + s < K; a += 32) {
-          if ((a / s) % 2 != colour) continue;
-          const int b = a + s;
-          const int xi = s_cfg[a], yi = s_cfg[b];
-          const SlotE X = s_slot[xi], Y = s_slot[yi];
-          double d = __dadd_rn(reduced(s_beta[a], s_wsg[a], s_wg[a], Y), reduced(s_beta[b], s_wsg[b], s_wg[b], X));
-          d = __dsub_rn(d, reduced(s_beta[a], s_wsg[a], s_wg[a], X));
-          d = __dsub_rn(d, reduced(s_beta[b], s_wsg[b], s_wg[b], Y));
-          const U4 o = philox(A.seed, (uint32_t)((sw * A.max_sep + s - 1) * 65536 + a), lid, A.cycle,
-                              kPurposeExchange);
-          const double u = uniform53(o.x, o.y);
-          // The test u < exp(-d) in FP64.  exp(-d) >= 1 > u whenever d <= 0.  Otherwise an FP32
-          // estimate of ln u (error < 1e-5 absolute) decides every case more than 1e-3 away from
-          // the boundary ln u = -d; the rest takes the FP64 exponential.  The decision is the FP64
-          // one either way.
-          bool acc;
-          if (d <= 0.0) {
-            acc = true;
-          } else if (u == 0.0) {
-            acc = 0.0 < exp(-d);
-          } else {
-            const float lu = __logf((float)u);
-            const float md = (float)(-d);
-            if (lu < md - 1e-3f) acc = true;
-            else if (lu > md + 1e-3f) acc = false;
-            else acc = u < exp(-d);
-          }
-          s_cnt[(s - 1) * K + a] += 1u;
-          if (acc) {
-            s_cfg[a] = yi;
-            s_cfg[b] = xi;
-            s_cnt[(A.max_sep + s - 1) * K + a] += 1u;
-          }
-        }
-        __syncwarp();
-      }
-    }
-  }
-  for (int k = lane; k < K; k += 32) {
-    A.config_of[l * K + k] = s_cfg[k];
-    if (A.state_of) A.state_of[l * K + s_cfg[k]] = A.state_offset + k;
-  }
-  for (int i = lane; i < A.max_sep * K; i += 32) {
-    if (A.attempts && s_cnt[i]) atomicAdd((unsigned long long*)&A.attempts[i], (unsigned long long)s_cnt[i]);
-    const unsigned ac = s_cnt[A.max_sep * K + i];
-    if (A.accepts && ac) atomicAdd((unsigned long long*)&A.accepts[i], (unsigned long long)ac);
-  }
+  for (int i = lane; i < K; i += 32) s_slot[i] = load_slot(A.comps + (l * K + i) * 4);
+  if (!load_ladder(A, l, s_cfg, s_cnt)) return;
+  sweeps(A, l, s_cfg, s_cnt,
+         [&](int k, int i) { return reduced(s_beta[k], s_wsg[k], s_wg[k], s_slot[i]); });
+  write_back(A, l, s_cfg, s_cnt);
 }
 
 }  // namespace
@@ -136,20 +186,29 @@ cudaError_t launch_exchange(cudaStream_t s, const algdock_ctx& c, int n_ladders,
   if (n_ladders == 0) return cudaSuccess;
   ExArgs A{c.d_states, n_ladders, K, state_offset, comps, config_of, state_of, n_sweeps, max_sep, seed,
            (uint32_t)cycle, ladder_offset, attempts, accepts};
+  const size_t counters = (size_t)2 * max_sep * K * sizeof(unsigned);
+  if (K <= kMatrixMaxK) {
+    const size_t smem = (size_t)K * K * sizeof(double) + (size_t)K * (3 * sizeof(double) + sizeof(SlotE) + sizeof(int)) +
+                        counters;
+    cudaError_t e = cudaFuncSetAttribute(exchange_matrix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    exchange_matrix_kernel<<<n_ladders, kExMaxWarps * 32, smem, s>>>(A);
+    return cudaGetLastError();
+  }
   const size_t fixed = (size_t)3 * K * sizeof(double);
-  const size_t per_warp = (size_t)K * (sizeof(SlotE) + sizeof(int)) + (size_t)2 * max_sep * K * sizeof(unsigned);
+  const size_t per_warp = (size_t)K * (sizeof(SlotE) + sizeof(int)) + counters;
   const size_t budget = 200 * 1024;
-  // Each ladder is a chain of dependent phases, so the launch is latency-bound: spread the
-  // ladders over all SMs first (one warp per block until there are two blocks per SM).
+  // each ladder is a chain of dependent phases: spread the ladders over all SMs first
   int warps = n_ladders / (2 * 152);
   warps = warps < 1 ? 1 : (warps > kExMaxWarps ? kExMaxWarps : warps);
   while (warps > 1 && fixed + warps * per_warp > budget) --warps;
   if (fixed + warps * per_warp > budget) return cudaErrorInvalidValue;
   const size_t smem = fixed + warps * per_warp;
-  cudaError_t e = cudaFuncSetAttribute(exchange_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(exchange_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int blocks = (n_ladders + warps - 1) / warps;
-  exchange_kernel<<<blocks, warps * 32, smem, s>>>(A);
+  exchange_direct_kernel<<<blocks, warps * 32, smem, s>>>(A);
   return cudaGetLastError();
 }
 

@@ -210,10 +210,11 @@ __device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const
   for (int t = lane; t < nb; t += 32) {  // k (r - r0)^2
     const float4 bp = L.bond[t];
     const float3 d = sub(xs[__float_as_int(bp.x)], xs[__float_as_int(bp.y)]);
-    const float r = sqrtf(dot(d, d));
-    const float dr = r - bp.w;
+    const float r2 = dot(d, d);
+    const float inv_r = rsqrtf(r2);
+    const float dr = r2 * inv_r - bp.w;
     if (ENERGY) e += bp.z * dr * dr;
-    const float c = -2.f * bp.z * dr / r;
+    const float c = -2.f * bp.z * dr * inv_r;
     put(sx, sy, sz, t, make_float3(c * d.x, c * d.y, c * d.z));
     put(sx, sy, sz, nb + t, make_float3(-c * d.x, -c * d.y, -c * d.z));
   }
@@ -228,8 +229,8 @@ __device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const
     const float c = fminf(1.f, fmaxf(-1.f, dot(u, w) * inv_luw));
     const float dth = acosf(c) - ap.y;
     if (ENERGY) e += ap.x * dth * dth;
-    const float coef = 2.f * ap.x * dth / fmaxf(sqrtf(1.f - c * c), 1e-6f);
-    const float cu = coef * c / lu2, cw = coef * c / lw2, cx = coef * inv_luw;
+    const float coef = 2.f * ap.x * dth * rsqrtf(fmaxf(1.f - c * c, 1e-12f));
+    const float cu = __fdividef(coef * c, lu2), cw = __fdividef(coef * c, lw2), cx = coef * inv_luw;
     const float3 fa = make_float3(cx * w.x - cu * u.x, cx * w.y - cu * u.y, cx * w.z - cu * u.z);
     const float3 fc = make_float3(cx * u.x - cw * w.x, cx * u.y - cw * w.y, cx * u.z - cw * w.z);
     put(sx, sy, sz, ab + t, fa);
@@ -245,7 +246,8 @@ __device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const
     const float3 b3 = sub(xs[id.w], xs[id.z]);
     const float3 n1 = cross(b1, b2), n2 = cross(b2, b3);
     const float lb22 = dot(b2, b2);
-    const float lb2 = sqrtf(lb22);
+    const float inv_lb2 = rsqrtf(lb22);
+    const float lb2 = lb22 * inv_lb2;
     const float n1s = fmaxf(dot(n1, n1), 1e-20f), n2s = fmaxf(dot(n2, n2), 1e-20f);
     const float inv = rsqrtf(n1s * n2s);
     const float cp = dot(n1, n2) * inv;        // cos phi
@@ -258,8 +260,9 @@ __device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const
     // dE/dphi = sum_n V_n/2 n (cos(n phi) sin g - sin(n phi) cos g)
     const float dE = V.x * (cp * sg.x - sp * cg.x) + 2.f * V.y * (c2 * sg.y - s2 * cg.y) +
                      3.f * V.z * (c3 * sg.z - s3 * cg.z);
-    const float ai = dE * lb2 / n1s, al = -dE * lb2 / n2s;  // F_i = ai n1, F_l = al n2
-    const float p = dot(b1, b2) / lb22, q = dot(b3, b2) / lb22;
+    const float ai = __fdividef(dE * lb2, n1s), al = -__fdividef(dE * lb2, n2s);  // F_i = ai n1, F_l = al n2
+    const float inv_lb22 = inv_lb2 * inv_lb2;
+    const float p = dot(b1, b2) * inv_lb22, q = dot(b3, b2) * inv_lb22;
     const float3 fi = make_float3(ai * n1.x, ai * n1.y, ai * n1.z);
     const float3 fl = make_float3(al * n2.x, al * n2.y, al * n2.z);
     const float3 fj = make_float3(-(1.f + p) * fi.x + q * fl.x, -(1.f + p) * fi.y + q * fl.y,
@@ -289,11 +292,15 @@ __device__ inline void nonbonded(const Lig& L, int na, const float4* xs, float (
     const int il = split ? (lane & 15) : lane;
     const int i = base + il;
     const bool act = il < m;
-    int jb = 0, je = na;
+    // partners: all j; split: the low half-warp takes j = 0 .. h-1 upwards, the high half-warp
+    // j = na-1 .. h downwards (opposite directions keep the two rows read per step in different
+    // shared-memory banks)
+    int jb = 0, cnt = na, dir = 1;
     if (split) {
       const int h = (na + 1) >> 1;
-      jb = lane < 16 ? 0 : h;
-      je = lane < 16 ? h : na;
+      jb = lane < 16 ? 0 : na - 1;
+      cnt = lane < 16 ? h : na - h;
+      dir = lane < 16 ? 1 : -1;
     }
     float fx = 0.f, fy = 0.f, fz = 0.f;
     if (act) {
@@ -301,7 +308,8 @@ __device__ inline void nonbonded(const Lig& L, int na, const float4* xs, float (
       const float4 bi = L.atom_b[i];
       const float qi = (float)kCoulomb * pi.w, ri = bi.x, si = bi.y;
       const uint8_t* ty_col = L.ptype + i;
-      for (int j = jb; j < je; ++j) {
+      for (int jj = 0; jj < cnt; ++jj) {
+        const int j = jb + dir * jj;
         const float4 pj = xs[j];
         const float2 bj = *(const float2*)&L.atom_b[j];
         const uint32_t ty = ty_col[j * na];

@@ -28,7 +28,7 @@ def _comps(rng, L, K, spread=1.0):
 
 
 @pytest.mark.parametrize("K,L,max_sep,n_sweeps", [(2, 3, 5, 25), (8, 64, 5, 25), (33, 5, 5, 25), (96, 64, 5, 25),
-                                                  (130, 2, 3, 7), (1, 4, 5, 3)])
+                                                  (130, 2, 3, 7), (200, 3, 5, 4), (1, 4, 5, 3)])
 def test_exchange_bit_exact(K, L, max_sep, n_sweeps):
     rng = np.random.default_rng(K * 1000 + L)
     # a table with a warming leg (alpha NaN) first, then the coupling leg under test
