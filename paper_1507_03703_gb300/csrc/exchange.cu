@@ -119,6 +119,127 @@ __device__ inline bool load_ladder(const ExArgs& A, int64_t l, int* s_cfg, unsig
   return !__any_sync(0xffffffffu, bad);
 }
 
+// Shared-memory bytes of the fast kernel for a ladder of K states.
+__host__ __device__ inline size_t fast_smem_bytes(int K, int n_sweeps, int max_sep) {
+  const int smax = max_sep < K - 1 ? max_sep : K - 1;
+  return (size_t)K * K * (sizeof(double) + sizeof(float)) +  // u in FP64 and FP32
+         (size_t)n_sweeps * (smax > 0 ? smax : 1) * K * sizeof(float) +  // log-uniforms
+         (size_t)2 * (smax > 0 ? smax : 1) * K * sizeof(int) +           // pair lists
+         (size_t)K * (3 * sizeof(double) + sizeof(SlotE) + sizeof(int)) +   // states, slots, config
+         (size_t)max_sep * K * sizeof(unsigned) + 64;                    // accept counters
+}
+
+// One ladder per block.  All warps fill u_k(x_i) (FP64, and its FP32 rounding), the pair list of
+// every (separation, colour) phase and the FP32 log-uniform of every attempt; warp 0 then sweeps,
+// deciding each attempt from the FP32 values when the margin to the boundary exceeds a bound on
+// their rounding error, and otherwise exactly as the FP64 test.
+__global__ void __launch_bounds__(kExMaxWarps * 32) exchange_fast_kernel(const ExArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = A.K;
+  const int smax = min(A.max_sep, K - 1);
+  const int sm1 = smax > 0 ? smax : 1;
+  double* s_u = (double*)smem_raw;                       // [K][K]
+  double* s_st = s_u + (size_t)K * K;                     // [K][3]
+  SlotE* s_slot = (SlotE*)(s_st + 3 * K);                 // [K]
+  float* s_uf = (float*)(s_slot + K);                     // [K][K]
+  float* s_lu = s_uf + (size_t)K * K;                     // [n_sweeps][smax][K]
+  int* s_pairs = (int*)(s_lu + (size_t)A.n_sweeps * sm1 * K);  // [smax][2][K/2+1]... stored [smax][2][K]
+  int* s_cfg = s_pairs + 2 * sm1 * K;
+  unsigned* s_acc = (unsigned*)(s_cfg + K);               // [max_sep][K]
+  __shared__ int s_npairs[2 * 8];
+  const int64_t l = blockIdx.x;
+  const uint32_t lid = (uint32_t)(A.ladder_offset + l);
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const StateDev st = A.states[A.state_offset + k];
+    s_st[3 * k] = st.beta;
+    s_st[3 * k + 1] = st.w_sg;
+    s_st[3 * k + 2] = st.w_g;
+    s_slot[k] = load_slot(A.comps + (l * K + k) * 4);
+  }
+  if (threadIdx.x < 2 * smax) {  // pair list of phase (s, colour), ascending a
+    const int s = threadIdx.x / 2 + 1, colour = threadIdx.x % 2;
+    int n = 0;
+    for (int a = 0; a + s < K; ++a)
+      if ((a / s) % 2 == colour) s_pairs[(2 * (s - 1) + colour) * K + n++] = a;
+    s_npairs[threadIdx.x] = n;
+  }
+  const int n_att = A.n_sweeps * smax * K;
+  for (int idx = threadIdx.x; idx < n_att; idx += blockDim.x) {
+    const int a = idx % K, ss = idx / K;
+    const int s = ss % smax + 1, sw = ss / smax;
+    float lu = 0.f;
+    if (a + s < K) {
+      const U4 o = philox(A.seed, (uint32_t)((sw * A.max_sep + s - 1) * 65536 + a), lid, A.cycle, kPurposeExchange);
+      const double u = uniform53(o.x, o.y);
+      lu = u == 0.0 ? -INFINITY : __logf((float)u);
+    }
+    s_lu[idx] = lu;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int k = e / K, i = e - k * K;
+    const double v = reduced(s_st[3 * k], s_st[3 * k + 1], s_st[3 * k + 2], s_slot[i]);
+    s_u[e] = v;
+    s_uf[e] = (float)v;
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  bool bad = false;
+  for (int i = lane; i < K; i += 32) {
+    s_cfg[i] = A.config_of[l * K + i];
+    bad |= (unsigned)s_cfg[i] >= (unsigned)K;
+  }
+  for (int i = lane; i < A.max_sep * K; i += 32) s_acc[i] = 0u;
+  __syncwarp();
+  if (__any_sync(0xffffffffu, bad)) return;  // not a list of slots 0..K-1: leave the ladder untouched
+  for (int sw = 0; sw < A.n_sweeps; ++sw) {
+    for (int s = 1; s <= smax; ++s) {
+      for (int colour = 0; colour < 2; ++colour) {
+        const int ph = 2 * (s - 1) + colour;
+        const int np = s_npairs[ph];
+        for (int p = lane; p < np; p += 32) {
+          const int a = s_pairs[ph * K + p], b = a + s;
+          const int xi = s_cfg[a], yi = s_cfg[b];
+          const float f1 = s_uf[a * K + yi], f2 = s_uf[b * K + xi], f3 = s_uf[a * K + xi], f4 = s_uf[b * K + yi];
+          const float df = ((f1 + f2) - f3) - f4;
+          // |df - d| <= 2^-22 (|f1| + |f2| + |f3| + |f4|) from the roundings; ln-uniform error < 2e-5
+          const float band = 1e-3f + 1e-6f * (fabsf(f1) + fabsf(f2) + fabsf(f3) + fabsf(f4));
+          const float lu = s_lu[((sw * smax) + (s - 1)) * K + a];
+          bool acc;
+          if (lu != -INFINITY && lu < -df - band) {
+            acc = true;
+          } else if (lu != -INFINITY && lu > -df + band) {
+            acc = false;
+          } else {  // close to the boundary, or not finite: the FP64 test itself
+            double d = __dadd_rn(s_u[a * K + yi], s_u[b * K + xi]);
+            d = __dsub_rn(d, s_u[a * K + xi]);
+            d = __dsub_rn(d, s_u[b * K + yi]);
+            const U4 o = philox(A.seed, (uint32_t)((sw * A.max_sep + s - 1) * 65536 + a), lid, A.cycle,
+                                kPurposeExchange);
+            acc = (d <= 0.0) || (uniform53(o.x, o.y) < exp(-d));
+          }
+          if (acc) {
+            s_cfg[a] = yi;
+            s_cfg[b] = xi;
+            s_acc[(s - 1) * K + a] += 1u;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  for (int k = lane; k < K; k += 32) {
+    A.config_of[l * K + k] = s_cfg[k];
+    if (A.state_of) A.state_of[l * K + s_cfg[k]] = A.state_offset + k;
+  }
+  for (int i = lane; i < A.max_sep * K; i += 32) {
+    const int s = i / K + 1, a = i % K;
+    if (A.attempts && s <= smax && a + s < K) atomicAdd((unsigned long long*)&A.attempts[i], (unsigned long long)A.n_sweeps);
+    if (A.accepts && s_acc[i]) atomicAdd((unsigned long long*)&A.accepts[i], (unsigned long long)s_acc[i]);
+  }
+}
+
 // One ladder per block: all warps fill u[k][i], warp 0 sweeps.
 __global__ void __launch_bounds__(kExMaxWarps * 32) exchange_matrix_kernel(const ExArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -187,6 +308,13 @@ cudaError_t launch_exchange(cudaStream_t s, const algdock_ctx& c, int n_ladders,
   ExArgs A{c.d_states, n_ladders, K, state_offset, comps, config_of, state_of, n_sweeps, max_sep, seed,
            (uint32_t)cycle, ladder_offset, attempts, accepts};
   const size_t counters = (size_t)2 * max_sep * K * sizeof(unsigned);
+  const size_t fast = fast_smem_bytes(K, n_sweeps, max_sep);
+  if (max_sep <= 8 && fast <= 200 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(exchange_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast);
+    if (e != cudaSuccess) return e;
+    exchange_fast_kernel<<<n_ladders, kExMaxWarps * 32, fast, s>>>(A);
+    return cudaGetLastError();
+  }
   if (K <= kMatrixMaxK) {
     const size_t smem = (size_t)K * K * sizeof(double) + (size_t)K * (3 * sizeof(double) + sizeof(SlotE) + sizeof(int)) +
                         counters;
