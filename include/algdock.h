@@ -200,6 +200,25 @@ algdock_status algdock_reduced_energies(algdock_ctx* ctx, int64_t N, const float
 algdock_status algdock_mbar(algdock_ctx* ctx, int32_t K, int64_t N, const double* u_kn, const int64_t* N_k,
                             double tol, int32_t max_iter, int32_t precision_mode, double* f_k, int32_t* iters);
 
+/* MBAR without any device allocation.  The paper has no counterpart: this is a service of this
+ * library for callers that cannot call cudaMalloc - for example a host framework whose caching
+ * allocator owns all device memory and forbids direct allocations, or a service that reserves its
+ * whole memory budget at start-up.  Same arguments, arithmetic and results as algdock_mbar, but
+ * the solver's scratch is a fixed 8 MiB array in the library's own device memory (every GPU that
+ * loads the library holds it until the process exits); the call itself allocates nothing and
+ * does not use the context's own MBAR scratch.
+ *  - Sizes whose scratch exceeds 8 MiB (about 8 bytes per sample plus 16 bytes per state and
+ *    8192-sample chunk, e.g. N up to ~1e6 samples for K = 128) are rejected with
+ *    ALGDOCK_E_INVALID and a message naming the bytes needed.
+ *  - The first call on a device looks up the array's device address (once per device, with that
+ *    device current); make that first call before any stream capture.
+ *  - Every call on a device shares the one array, which keeps the last call's contents (each call
+ *    re-initialises what it reads).  Calls whose work overlaps on the GPU (from several host
+ *    threads or streams) race on it: serialise them. */
+algdock_status algdock_mbar_noalloc(algdock_ctx* ctx, int32_t K, int64_t N, const double* u_kn, const int64_t* N_k,
+                                    double tol, int32_t max_iter, int32_t precision_mode, double* f_k,
+                                    int32_t* iters);
+
 #ifdef __cplusplus
 }
 #endif

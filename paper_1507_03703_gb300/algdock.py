@@ -28,6 +28,7 @@ EXPORTS = [
     "algdock_create", "algdock_destroy", "algdock_set_stream", "algdock_last_error", "algdock_grids_build",
     "algdock_soft_elec_cap", "algdock_grids_load", "algdock_ligand_load", "algdock_states_set",
     "algdock_hmc_cycle", "algdock_energy_force", "algdock_exchange", "algdock_reduced_energies", "algdock_mbar",
+    "algdock_mbar_noalloc",
 ]
 
 
@@ -80,6 +81,7 @@ def load_library(path: str = LIB_PATH):
         "algdock_exchange": ([vp, i32, i32, i32, vp, vp, vp, i32, i32, u64, u64, i64, vp, vp], C.c_int),
         "algdock_reduced_energies": ([vp, i64, vp, vp, i32, i32, vp], C.c_int),
         "algdock_mbar": ([vp, i32, i64, vp, vp, dbl, i32, i32, vp, C.POINTER(i32)], C.c_int),
+        "algdock_mbar_noalloc": ([vp, i32, i64, vp, vp, dbl, i32, i32, vp, C.POINTER(i32)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -291,4 +293,17 @@ class Context:
         if st == E_NOT_CONVERGED and not raise_on_nonconvergence:
             return f, -1
         self._check(st)
+        return f, it.value
+
+    def mbar_noalloc(self, u_kn, N_k, tol=1e-10, max_iter=10000, precision_mode=0):
+        """algdock_mbar_noalloc: MBAR whose scratch is the library's fixed device array (for callers
+        that cannot allocate device memory).  Returns (f_k numpy [K], iterations)."""
+        import torch
+        K, N = int(u_kn.shape[0]), int(u_kn.shape[1])
+        Nk = np.ascontiguousarray(N_k, dtype=np.int64)
+        f = np.zeros(K)
+        it = C.c_int32()
+        self._check(self._L.algdock_mbar_noalloc(self.h, K, N, _dev(u_kn, torch.float64, "u_kn"), Nk.ctypes.data,
+                                                 float(tol), int(max_iter), int(precision_mode), f.ctypes.data,
+                                                 C.byref(it)))
         return f, it.value

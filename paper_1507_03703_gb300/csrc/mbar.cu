@@ -9,6 +9,9 @@
 // can enqueue iterations in batches and poll the flag between batches.
 #include <math.h>
 
+#include <mutex>
+#include <string>
+
 #include "internal.cuh"
 
 namespace algdock {
@@ -182,3 +185,100 @@ int mbar_run(cudaStream_t s, void* scratch, int K, int64_t N, const double* u_kn
 }
 
 }  // namespace algdock
+
+// ------------------------------------------------------------------ allocation-free MBAR
+// Callers that must not allocate device memory - a host framework whose caching allocator owns
+// all device memory and forbids direct cudaMalloc, or a service that reserves its whole memory
+// budget at start-up - use algdock_mbar_noalloc.  Its scratch is this fixed array in the
+// library's own device memory, present on every GPU that loads the library until the process
+// exits.
+namespace {
+
+constexpr size_t kNoallocScratchBytes = (size_t)8 << 20;  // 8 MiB
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_mbar_noalloc_scratch[kNoallocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code the array's name is
+// only a host-side stand-in, so the address is looked up once per device (with that device
+// current) and cached.
+cudaError_t noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_mbar_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[device] = p;
+  }
+  *out = g_noalloc_ptr[device];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" algdock_status algdock_mbar_noalloc(algdock_ctx* c, int32_t K, int64_t N, const double* u_kn,
+                                               const int64_t* N_k, double tol, int32_t max_iter,
+                                               int32_t precision_mode, double* f_k, int32_t* iters) {
+  if (!c) return ALGDOCK_E_INVALID;
+  try {
+    if (K < 1 || N < 1 || !u_kn || !N_k || !f_k || !iters || max_iter < 1 || !(tol > 0) ||
+        (precision_mode != 0 && precision_mode != 1)) {
+      c->err = "mbar_noalloc: bad arguments";
+      return ALGDOCK_E_INVALID;
+    }
+    int64_t total = 0;
+    for (int k = 0; k < K; ++k) {
+      if (N_k[k] < 0) {
+        c->err = "mbar_noalloc: negative N_k";
+        return ALGDOCK_E_INVALID;
+      }
+      total += N_k[k];
+    }
+    if (total != N) {
+      c->err = "mbar_noalloc: sum of N_k must equal N";
+      return ALGDOCK_E_INVALID;
+    }
+    const size_t need = algdock::mbar_scratch_bytes(K, N);
+    if (need > kNoallocScratchBytes) {
+      c->err = "mbar_noalloc: K = " + std::to_string(K) + ", N = " + std::to_string(N) + " needs " +
+               std::to_string(need) + " bytes of scratch, more than the fixed " +
+               std::to_string(kNoallocScratchBytes) + "-byte buffer; use algdock_mbar";
+      return ALGDOCK_E_INVALID;
+    }
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, u_kn) != cudaSuccess ||
+        (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
+      cudaGetLastError();
+      c->err = "mbar_noalloc: u_kn must be a device pointer";
+      return ALGDOCK_E_INVALID;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != c->device) cudaSetDevice(c->device);
+    void* scratch = nullptr;
+    cudaError_t e = noalloc_scratch(c->device, &scratch);
+    cudaError_t err = cudaSuccess;
+    int it = 0;
+    int r = -1;
+    if (e == cudaSuccess) r = algdock::mbar_run(c->stream, scratch, K, N, u_kn, N_k, tol, max_iter, precision_mode,
+                                                f_k, &it, c->h_flag, &err);
+    else err = e;
+    if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
+    *iters = it;
+    if (r < 0) {
+      c->err = std::string("mbar_noalloc: ") + cudaGetErrorString(err);
+      return err == cudaErrorMemoryAllocation ? ALGDOCK_E_OOM : ALGDOCK_E_CUDA;
+    }
+    if (r == 1) {
+      c->err = "mbar_noalloc: max_iter reached";
+      return ALGDOCK_E_NOT_CONVERGED;
+    }
+    return ALGDOCK_OK;
+  } catch (...) {
+    return ALGDOCK_E_INVALID;
+  }
+}
