@@ -132,6 +132,22 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def profiled_traffic():
+    """DRAM bytes per HMC launch from the committed ncu summary, if it was taken on the current
+    source of the kernel (else None)."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", "hmc_kernel_paper_scale.md")).read()
+        vals = dict(l.strip().split(": ", 1) for l in text.splitlines() if l.strip().startswith(
+            ("traffic_bytes_per_launch:", "hmc_cu_sha256:")))
+        src = open(os.path.join(ROOT, "paper_1507_03703_gb300", "csrc", "hmc.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != vals["hmc_cu_sha256"]:
+            return None
+        return int(vals["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -295,7 +311,7 @@ def main():
     hmc_avg = sum(hmc_ms) / len(hmc_ms)
     achieved = fl / (hmc_avg * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
+                "frac": achieved / peak_tflops, "traffic": profiled_traffic(),
                 "kernel": "hmc_kernel", "kernel_ms": hmc_avg,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_max,
                 "flops_per_launch": fl}
