@@ -365,3 +365,111 @@ def ladder_free_energies(T, alpha, comps, states, tol=1e-10, max_iter=10000):
     u = ukn_from_comps(T, alpha, comps[order])
     N_k = np.bincount(states, minlength=K).astype(np.int64)
     return mbar(u, N_k, tol=tol, max_iter=max_iter)
+
+
+# ------------------------------------------------------------------ learned pose proposal
+NFEAT, NHID, NCOMP, DMAX, NOUT = 64, 256, 8, 22, 8 * (1 + 2 * 22)
+_MLP_KEYS = ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")
+
+
+def _learned_sigs(L):
+    if getattr(L, "_learned", False):
+        return
+    L.oracle_learned_ntorsions.argtypes = [C.c_void_p]
+    L.oracle_learned_ntorsions.restype = C.c_int
+    L.oracle_features.argtypes = [C.c_void_p, _d, _d, C.c_int, _d]
+    L.oracle_apply.argtypes = [C.c_void_p, _d, _d, _d]
+    L.oracle_pose_delta.argtypes = [C.c_void_p, _d, _d, _d]
+    L.oracle_mlp_forward.argtypes = [_d] * 8 + [C.c_int, _d, _d, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.oracle_mlp_backward.argtypes = [_d, _d, _d, C.c_int, _d, _d, _d, _d, _d] + [_d] * 8
+    L.oracle_mixture_logq.argtypes = [_d, C.c_int, _d, C.c_void_p]
+    L.oracle_mixture_logq.restype = C.c_double
+    L.oracle_mixture_sample.argtypes = [_d, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, _d]
+    L.oracle_learned_mh.argtypes = ([C.c_void_p] + [_d] * 8 + [C.c_int64, _i, C.c_int64, _d, _d, C.c_int, C.c_uint64,
+                                    C.c_uint64, _i, C.c_void_p])
+    L._learned = True
+
+
+def _p(params):
+    return [_f64(params[k]).ravel() for k in _MLP_KEYS]
+
+
+def mlp_forward(params, X):
+    """FP64 forward pass: returns (out [B, 360], h1, h2, h3)."""
+    L = _load()
+    _learned_sigs(L)
+    X = _f64(X).reshape(-1, NFEAT)
+    B = X.shape[0]
+    out, h1, h2, h3 = np.zeros((B, NOUT)), np.zeros((B, NHID)), np.zeros((B, NHID)), np.zeros((B, NHID))
+    L.oracle_mlp_forward(*_p(params), B, X, out, _ptr(h1), _ptr(h2), _ptr(h3))
+    return out, h1, h2, h3
+
+
+def mlp_backward(params, X, h1, h2, h3, dout):
+    """Gradients of sum <dout, out> with respect to every parameter (dict like params)."""
+    L = _load()
+    _learned_sigs(L)
+    X = _f64(X).reshape(-1, NFEAT)
+    B = X.shape[0]
+    g = {k: np.zeros_like(_f64(params[k])) for k in _MLP_KEYS}
+    L.oracle_mlp_backward(_f64(params["W2"]).ravel(), _f64(params["W3"]).ravel(), _f64(params["W4"]).ravel(), B, X,
+                          _f64(h1), _f64(h2), _f64(h3), _f64(dout), *[g[k] for k in _MLP_KEYS])
+    return g
+
+
+def mixture_logq(o, D, delta, grad=False):
+    L = _load()
+    _learned_sigs(L)
+    g = np.zeros(NOUT) if grad else None
+    lq = L.oracle_mixture_logq(_f64(o), int(D), _f64(np.resize(np.asarray(delta, dtype=np.float64), DMAX)), _ptr(g))
+    return (lq, g) if grad else lq
+
+
+def mixture_sample(o, D, seed, rep, ctr):
+    L = _load()
+    _learned_sigs(L)
+    out = np.zeros(DMAX)
+    L.oracle_mixture_sample(_f64(o), int(D), int(seed), int(rep), int(ctr), out)
+    return out[:D]
+
+
+class _LearnedMixin:
+    def learned_ntorsions(self):
+        _learned_sigs(self._L)
+        return self._L.oracle_learned_ntorsions(self.h)
+
+    def features(self, x, comps, k):
+        _learned_sigs(self._L)
+        f = np.zeros(NFEAT)
+        self._L.oracle_features(self.h, _f64(x).ravel(), _f64(comps), int(k), f)
+        return f
+
+    def apply(self, x, delta):
+        _learned_sigs(self._L)
+        y = np.zeros(3 * self.na)
+        d = np.zeros(DMAX)
+        d[:len(delta)] = delta
+        self._L.oracle_apply(self.h, _f64(x).ravel(), d, y)
+        return y.reshape(-1, 3)
+
+    def pose_delta(self, x, y):
+        _learned_sigs(self._L)
+        d = np.zeros(DMAX)
+        self._L.oracle_pose_delta(self.h, _f64(x).ravel(), _f64(y).ravel(), d)
+        return d[:6 + self.learned_ntorsions()]
+
+    def learned_mh(self, params, x, comps, state_of, n_moves, seed, cycle, rep_offset=0):
+        """n_moves learned proposals per replica.  Returns (x, comps, accepts [R], last log-ratio [R])."""
+        _learned_sigs(self._L)
+        x = np.array(x, dtype=np.float64, order="C").reshape(-1, self.na, 3)
+        comps = np.array(comps, dtype=np.float64, order="C").reshape(-1, 4)
+        R = x.shape[0]
+        acc = np.zeros(R, dtype=np.int32)
+        lr = np.zeros(R)
+        self._L.oracle_learned_mh(self.h, *_p(params), R, _i32(state_of), int(rep_offset), x, comps, int(n_moves),
+                                  int(seed), int(cycle), acc, _ptr(lr))
+        return x, comps, acc, lr
+
+
+for _name in ("learned_ntorsions", "features", "apply", "pose_delta", "learned_mh"):
+    setattr(OracleSystem, _name, getattr(_LearnedMixin, _name))

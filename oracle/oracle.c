@@ -878,3 +878,443 @@ double oracle_statistical_inefficiency(int64_t N, const double* a) {
   }
   return g < 1.0 ? 1.0 : g;
 }
+
+/* ================================================================ learned pose proposal
+ * Not a step of the paper: a learned proposal of rigid-body and torsion moves, made exact by the
+ * Metropolis-Hastings test of an involution.  It generalises the paper's external-coordinate moves
+ * ("Sampling": a random rotation about the centre of mass and a Gaussian translation).
+ *
+ *  torsion tree   root atom 0; a bond is rotatable if both its atoms have two or more neighbours;
+ *                 the first 16 rotatable bonds (bond-list order) are moved; each moves the atoms
+ *                 on its side away from the root, about the axis proximal -> distal atom.
+ *  move           Apply(x, d) = Rigid(d_r / 2) o Tor(d_tau) o Rigid(d_r / 2), Rigid(t, w) = rotate
+ *                 about the centre of mass by exp(w) (axis-angle), then translate by t.  Torsion
+ *                 rotations commute (each changes one dihedral, the root side fixed), so
+ *                 Apply(Apply(x, d), -d) = x; every factor preserves volume (unit Jacobian).
+ *  network        64 features -> 256 -> 256 -> 256 (ReLU) -> 360 outputs: an 8-component diagonal
+ *                 Gaussian mixture over d = (t[3] A, w[3] rad, d_tau[T] rad); log sigma =
+ *                 -2 + 4 tanh(raw / 4).
+ *  acceptance     min(1, exp(-(u(x') - u(x))) q(-d | x') / q(d | x)).
+ * Random numbers: Philox counter {draw, replica, cycle * n_moves + move, 4}: draw d < 22 gives the
+ * normal of dimension d (first Box-Muller output), draw 100 the component uniform, draw 101 the
+ * acceptance uniform. */
+#define O_TMAX 16
+#define O_NFEAT 64
+#define O_NCOMP 8
+#define O_DMAX (6 + O_TMAX)
+#define O_NOUT (O_NCOMP * (1 + 2 * O_DMAX))
+#define O_HID 256
+enum { O_PURPOSE_LEARNED = 4 };
+
+typedef struct {
+  int T;
+  int prox[O_TMAX], dist[O_TMAX];
+  int dih[O_TMAX][4];
+  unsigned char* moved; /* [T][na] */
+} o_tree;
+
+static void o_tree_build(const oracle_system* s, o_tree* t) {
+  int na = s->na;
+  int* deg = (int*)calloc((size_t)(na > 0 ? na : 1), sizeof(int));
+  for (int b = 0; b < s->nb; ++b) { deg[s->bonds[2 * b]]++; deg[s->bonds[2 * b + 1]]++; }
+  t->T = 0;
+  t->moved = (unsigned char*)calloc((size_t)O_TMAX * (size_t)(na > 0 ? na : 1), 1);
+  int* seen = (int*)malloc(sizeof(int) * (size_t)(na > 0 ? na : 1));
+  int* queue = (int*)malloc(sizeof(int) * (size_t)(na > 0 ? na : 1));
+  for (int b = 0; b < s->nb && t->T < O_TMAX; ++b) {
+    int j = s->bonds[2 * b], k = s->bonds[2 * b + 1];
+    if (deg[j] < 2 || deg[k] < 2) continue;
+    /* atoms reachable from the root without crossing bond b */
+    for (int i = 0; i < na; ++i) seen[i] = 0;
+    int h = 0, tl = 0;
+    seen[0] = 1;
+    queue[tl++] = 0;
+    while (h < tl) {
+      int u = queue[h++];
+      for (int c = 0; c < s->nb; ++c) {
+        if (c == b) continue;
+        int v = -1;
+        if (s->bonds[2 * c] == u) v = s->bonds[2 * c + 1];
+        else if (s->bonds[2 * c + 1] == u) v = s->bonds[2 * c];
+        if (v >= 0 && !seen[v]) { seen[v] = 1; queue[tl++] = v; }
+      }
+    }
+    int prox = seen[j] ? j : k, dist = seen[j] ? k : j;
+    int T = t->T;
+    t->prox[T] = prox;
+    t->dist[T] = dist;
+    for (int i = 0; i < na; ++i) t->moved[(size_t)T * na + i] = (unsigned char)(seen[i] ? 0 : 1);
+    t->moved[(size_t)T * na + dist] = 0; /* on the axis */
+    int ii = -1, ll = -1;
+    for (int c = 0; c < s->nb; ++c) {
+      int a0 = s->bonds[2 * c], a1 = s->bonds[2 * c + 1];
+      int v;
+      if (a0 == prox || a1 == prox) {
+        v = a0 == prox ? a1 : a0;
+        if (v != dist && (ii < 0 || v < ii)) ii = v;
+      }
+      if (a0 == dist || a1 == dist) {
+        v = a0 == dist ? a1 : a0;
+        if (v != prox && (ll < 0 || v < ll)) ll = v;
+      }
+    }
+    t->dih[T][0] = ii; t->dih[T][1] = prox; t->dih[T][2] = dist; t->dih[T][3] = ll;
+    t->T++;
+  }
+  free(deg); free(seen); free(queue);
+}
+
+int oracle_learned_ntorsions(const oracle_system* s) {
+  o_tree t;
+  o_tree_build(s, &t);
+  free(t.moved);
+  return t.T;
+}
+
+static double o_dihedral(const double* x, const int* a) {
+  double b1[3], b2[3], b3[3], n1[3], n2[3];
+  sub3(x + 3 * a[1], x + 3 * a[0], b1);
+  sub3(x + 3 * a[2], x + 3 * a[1], b2);
+  sub3(x + 3 * a[3], x + 3 * a[2], b3);
+  cross3(b1, b2, n1);
+  cross3(b2, b3, n2);
+  return atan2(sqrt(dot3(b2, b2)) * dot3(b1, n2), dot3(n1, n2));
+}
+
+static void o_com(const oracle_system* s, const double* x, double c[3]) {
+  double M = 0.0;
+  c[0] = c[1] = c[2] = 0.0;
+  for (int i = 0; i < s->na; ++i) {
+    M += s->mass[i];
+    for (int d = 0; d < 3; ++d) c[d] += s->mass[i] * x[3 * i + d];
+  }
+  for (int d = 0; d < 3; ++d) c[d] /= M;
+}
+
+/* Features of a pose at state k (comps = {U_L, U_I, Psi_sg, Psi_g} of x). */
+void oracle_features(const oracle_system* s, const double* x, const double comps[4], int k, double* f) {
+  o_tree t;
+  o_tree_build(s, &t);
+  for (int i = 0; i < O_NFEAT; ++i) f[i] = 0.0;
+  double c[3];
+  o_com(s, x, c);
+  for (int d = 0; d < 3; ++d) f[d] = (c[d] - s->site[d]) / s->d0;
+  int ref[2] = {0, s->na - 1};
+  for (int r = 0; r < 2; ++r) {
+    double v[3];
+    sub3(x + 3 * ref[r], c, v);
+    double n = sqrt(dot3(v, v));
+    if (n < 1e-6) n = 1e-6;
+    for (int d = 0; d < 3; ++d) f[3 + 3 * r + d] = v[d] / n;
+  }
+  for (int q = 0; q < t.T; ++q) {
+    double tau = o_dihedral(x, t.dih[q]);
+    f[9 + 2 * q] = cos(tau);
+    f[10 + 2 * q] = sin(tau);
+  }
+  f[41] = s->w_sg[k];
+  f[42] = s->w_g[k];
+  f[43] = 300.0 / s->T[k];
+  for (int i = 0; i < 4; ++i) f[44 + i] = asinh(comps[i] / 10.0);
+  free(t.moved);
+}
+
+static void o_rotate(double* v, const double w[3]) {
+  /* v <- exp([w]x) v (Rodrigues) */
+  double th = sqrt(dot3(w, w));
+  double a, b;
+  if (th < 1e-8) { a = 1.0 - th * th / 6.0; b = 0.5 - th * th / 24.0; }
+  else { a = sin(th) / th; b = (1.0 - cos(th)) / (th * th); }
+  double wv[3], wwv[3];
+  cross3(w, v, wv);
+  cross3(w, wv, wwv);
+  for (int d = 0; d < 3; ++d) v[d] = v[d] + a * wv[d] + b * wwv[d];
+}
+
+static void o_rigid(const oracle_system* s, double* x, const double t[3], const double w[3]) {
+  double c[3];
+  o_com(s, x, c);
+  for (int i = 0; i < s->na; ++i) {
+    double v[3];
+    sub3(x + 3 * i, c, v);
+    o_rotate(v, w);
+    for (int d = 0; d < 3; ++d) x[3 * i + d] = c[d] + v[d] + t[d];
+  }
+}
+
+/* y = Apply(x, d), d = (t[3], w[3], d_tau[T]). */
+void oracle_apply(const oracle_system* s, const double* x, const double* dl, double* y) {
+  o_tree t;
+  o_tree_build(s, &t);
+  memcpy(y, x, sizeof(double) * 3 * (size_t)s->na);
+  double ht[3] = {0.5 * dl[0], 0.5 * dl[1], 0.5 * dl[2]}, hw[3] = {0.5 * dl[3], 0.5 * dl[4], 0.5 * dl[5]};
+  o_rigid(s, y, ht, hw);
+  for (int q = 0; q < t.T; ++q) {
+    double ax[3];
+    sub3(y + 3 * t.dist[q], y + 3 * t.prox[q], ax);
+    double n = sqrt(dot3(ax, ax));
+    double w[3] = {ax[0] / n * dl[6 + q], ax[1] / n * dl[6 + q], ax[2] / n * dl[6 + q]};
+    const double* p = y + 3 * t.prox[q];
+    double pc[3] = {p[0], p[1], p[2]};
+    for (int i = 0; i < s->na; ++i) {
+      if (!t.moved[(size_t)q * s->na + i]) continue;
+      double v[3];
+      sub3(y + 3 * i, pc, v);
+      o_rotate(v, w);
+      for (int d = 0; d < 3; ++d) y[3 * i + d] = pc[d] + v[d];
+    }
+  }
+  o_rigid(s, y, ht, hw);
+  free(t.moved);
+}
+
+/* Training target: the move taking pose x to pose y (translation of the centre of mass, rotation
+ * of the frame of reference atoms 0 and n-1, wrapped torsion differences). */
+void oracle_pose_delta(const oracle_system* s, const double* x, const double* y, double* dl) {
+  o_tree t;
+  o_tree_build(s, &t);
+  double cx[3], cy[3];
+  o_com(s, x, cx);
+  o_com(s, y, cy);
+  for (int d = 0; d < 3; ++d) dl[d] = cy[d] - cx[d];
+  double F[2][3][3];
+  const double* P[2] = {x, y};
+  const double* C[2] = {cx, cy};
+  for (int p = 0; p < 2; ++p) {
+    double e1[3], e2[3], e3[3];
+    sub3(P[p] + 0, C[p], e1);
+    double n = sqrt(dot3(e1, e1));
+    if (n < 1e-9) { e1[0] = 1; e1[1] = 0; e1[2] = 0; n = 1; }
+    for (int d = 0; d < 3; ++d) e1[d] /= n;
+    sub3(P[p] + 3 * (s->na - 1), C[p], e2);
+    double pr = dot3(e2, e1);
+    for (int d = 0; d < 3; ++d) e2[d] -= pr * e1[d];
+    n = sqrt(dot3(e2, e2));
+    if (n < 1e-9) { double a[3] = {0, 0, 1}; if (fabs(e1[2]) > 0.9) { a[1] = 1; a[2] = 0; } cross3(e1, a, e2); n = sqrt(dot3(e2, e2)); }
+    for (int d = 0; d < 3; ++d) e2[d] /= n;
+    cross3(e1, e2, e3);
+    for (int d = 0; d < 3; ++d) { F[p][d][0] = e1[d]; F[p][d][1] = e2[d]; F[p][d][2] = e3[d]; }
+  }
+  double R[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      R[a][b] = 0.0;
+      for (int c = 0; c < 3; ++c) R[a][b] += F[1][a][c] * F[0][b][c];
+    }
+  double tr = R[0][0] + R[1][1] + R[2][2];
+  double ct = 0.5 * (tr - 1.0);
+  if (ct > 1.0) ct = 1.0;
+  if (ct < -1.0) ct = -1.0;
+  double th = acos(ct);
+  double v[3] = {R[2][1] - R[1][2], R[0][2] - R[2][0], R[1][0] - R[0][1]};
+  double sn = sin(th);
+  double f = th < 1e-8 ? 0.5 : (sn > 1e-8 ? th / (2.0 * sn) : 0.0);
+  if (th > 1e-8 && sn <= 1e-8) { /* rotation by pi: axis from the symmetric part */
+    double ax[3] = {sqrt(fmax(0.0, 0.5 * (R[0][0] + 1))), sqrt(fmax(0.0, 0.5 * (R[1][1] + 1))),
+                    sqrt(fmax(0.0, 0.5 * (R[2][2] + 1)))};
+    if (R[0][1] < 0) ax[1] = -ax[1];
+    if (R[0][2] < 0) ax[2] = -ax[2];
+    for (int d = 0; d < 3; ++d) dl[3 + d] = th * ax[d];
+  } else {
+    for (int d = 0; d < 3; ++d) dl[3 + d] = f * v[d];
+  }
+  for (int q = 0; q < t.T; ++q) {
+    double d = o_dihedral(y, t.dih[q]) - o_dihedral(x, t.dih[q]);
+    while (d > M_PI) d -= 2.0 * M_PI;
+    while (d <= -M_PI) d += 2.0 * M_PI;
+    dl[6 + q] = d;
+  }
+  free(t.moved);
+}
+
+/* ---------------- MLP (weights row-major [out][in]); activations kept for the backward pass */
+static void o_dense(int B, int nin, int nout, const double* W, const double* b, const double* X, double* Y, int relu) {
+  for (int r = 0; r < B; ++r)
+    for (int o = 0; o < nout; ++o) {
+      double acc = b[o];
+      for (int i = 0; i < nin; ++i) acc += W[(size_t)o * nin + i] * X[(size_t)r * nin + i];
+      Y[(size_t)r * nout + o] = relu ? (acc > 0.0 ? acc : 0.0) : acc;
+    }
+}
+
+void oracle_mlp_forward(const double* W1, const double* b1, const double* W2, const double* b2, const double* W3,
+                        const double* b3, const double* W4, const double* b4, int B, const double* X, double* out,
+                        double* h1, double* h2, double* h3) {
+  double* a1 = h1 ? h1 : (double*)malloc(sizeof(double) * (size_t)B * O_HID);
+  double* a2 = h2 ? h2 : (double*)malloc(sizeof(double) * (size_t)B * O_HID);
+  double* a3 = h3 ? h3 : (double*)malloc(sizeof(double) * (size_t)B * O_HID);
+  o_dense(B, O_NFEAT, O_HID, W1, b1, X, a1, 1);
+  o_dense(B, O_HID, O_HID, W2, b2, a1, a2, 1);
+  o_dense(B, O_HID, O_HID, W3, b3, a2, a3, 1);
+  o_dense(B, O_HID, O_NOUT, W4, b4, a3, out, 0);
+  if (!h1) free(a1);
+  if (!h2) free(a2);
+  if (!h3) free(a3);
+}
+
+/* Gradients (summed over the batch) of sum_r <dout_r, out_r> with respect to all parameters. */
+void oracle_mlp_backward(const double* W2, const double* W3, const double* W4, int B, const double* X,
+                         const double* h1, const double* h2, const double* h3, const double* dout, double* gW1,
+                         double* gb1, double* gW2, double* gb2, double* gW3, double* gb3, double* gW4,
+                         double* gb4) {
+  double* d3 = (double*)calloc((size_t)B * O_HID, sizeof(double));
+  double* d2 = (double*)calloc((size_t)B * O_HID, sizeof(double));
+  double* d1 = (double*)calloc((size_t)B * O_HID, sizeof(double));
+  memset(gW1, 0, sizeof(double) * O_HID * O_NFEAT); memset(gb1, 0, sizeof(double) * O_HID);
+  memset(gW2, 0, sizeof(double) * O_HID * O_HID); memset(gb2, 0, sizeof(double) * O_HID);
+  memset(gW3, 0, sizeof(double) * O_HID * O_HID); memset(gb3, 0, sizeof(double) * O_HID);
+  memset(gW4, 0, sizeof(double) * O_NOUT * O_HID); memset(gb4, 0, sizeof(double) * O_NOUT);
+  for (int r = 0; r < B; ++r) {
+    const double* g = dout + (size_t)r * O_NOUT;
+    for (int o = 0; o < O_NOUT; ++o) {
+      gb4[o] += g[o];
+      for (int i = 0; i < O_HID; ++i) gW4[(size_t)o * O_HID + i] += g[o] * h3[(size_t)r * O_HID + i];
+    }
+    for (int i = 0; i < O_HID; ++i) {
+      double acc = 0.0;
+      for (int o = 0; o < O_NOUT; ++o) acc += g[o] * W4[(size_t)o * O_HID + i];
+      d3[(size_t)r * O_HID + i] = h3[(size_t)r * O_HID + i] > 0.0 ? acc : 0.0;
+    }
+    const double* g3 = d3 + (size_t)r * O_HID;
+    for (int o = 0; o < O_HID; ++o) {
+      gb3[o] += g3[o];
+      for (int i = 0; i < O_HID; ++i) gW3[(size_t)o * O_HID + i] += g3[o] * h2[(size_t)r * O_HID + i];
+    }
+    for (int i = 0; i < O_HID; ++i) {
+      double acc = 0.0;
+      for (int o = 0; o < O_HID; ++o) acc += g3[o] * W3[(size_t)o * O_HID + i];
+      d2[(size_t)r * O_HID + i] = h2[(size_t)r * O_HID + i] > 0.0 ? acc : 0.0;
+    }
+    const double* g2 = d2 + (size_t)r * O_HID;
+    for (int o = 0; o < O_HID; ++o) {
+      gb2[o] += g2[o];
+      for (int i = 0; i < O_HID; ++i) gW2[(size_t)o * O_HID + i] += g2[o] * h1[(size_t)r * O_HID + i];
+    }
+    for (int i = 0; i < O_HID; ++i) {
+      double acc = 0.0;
+      for (int o = 0; o < O_HID; ++o) acc += g2[o] * W2[(size_t)o * O_HID + i];
+      d1[(size_t)r * O_HID + i] = h1[(size_t)r * O_HID + i] > 0.0 ? acc : 0.0;
+    }
+    const double* g1 = d1 + (size_t)r * O_HID;
+    for (int o = 0; o < O_HID; ++o) {
+      gb1[o] += g1[o];
+      for (int i = 0; i < O_NFEAT; ++i) gW1[(size_t)o * O_NFEAT + i] += g1[o] * X[(size_t)r * O_NFEAT + i];
+    }
+  }
+  free(d1); free(d2); free(d3);
+}
+
+/* log q(d) of the mixture encoded by one output row o[360], over the first D dimensions; g (may be
+ * NULL) receives d log q / d o. */
+double oracle_mixture_logq(const double* o, int D, const double* dl, double* g) {
+  double lw[O_NCOMP], lp[O_NCOMP];
+  double m = -INFINITY;
+  for (int c = 0; c < O_NCOMP; ++c) if (o[c] > m) m = o[c];
+  double z = 0.0;
+  for (int c = 0; c < O_NCOMP; ++c) z += exp(o[c] - m);
+  double lz = m + log(z);
+  for (int c = 0; c < O_NCOMP; ++c) {
+    lw[c] = o[c] - lz;
+    double s = lw[c];
+    for (int d = 0; d < D; ++d) {
+      double mu = o[O_NCOMP + c * O_DMAX + d];
+      double ls = -2.0 + 4.0 * tanh(o[O_NCOMP + O_NCOMP * O_DMAX + c * O_DMAX + d] / 4.0);
+      double zz = (dl[d] - mu) / exp(ls);
+      s += -0.5 * zz * zz - ls - 0.5 * log(2.0 * M_PI);
+    }
+    lp[c] = s;
+  }
+  double mm = -INFINITY;
+  for (int c = 0; c < O_NCOMP; ++c) if (lp[c] > mm) mm = lp[c];
+  double ss = 0.0;
+  for (int c = 0; c < O_NCOMP; ++c) ss += exp(lp[c] - mm);
+  double lq = mm + log(ss);
+  if (g) {
+    for (int i = 0; i < O_NOUT; ++i) g[i] = 0.0;
+    for (int c = 0; c < O_NCOMP; ++c) {
+      double r = exp(lp[c] - lq);
+      g[c] += r;
+      for (int c2 = 0; c2 < O_NCOMP; ++c2) g[c2] -= r * exp(lw[c2]);
+      for (int d = 0; d < D; ++d) {
+        double mu = o[O_NCOMP + c * O_DMAX + d];
+        double raw = o[O_NCOMP + O_NCOMP * O_DMAX + c * O_DMAX + d];
+        double th = tanh(raw / 4.0);
+        double ls = -2.0 + 4.0 * th;
+        double sg = exp(ls);
+        double zz = (dl[d] - mu) / sg;
+        g[O_NCOMP + c * O_DMAX + d] += r * zz / sg;
+        g[O_NCOMP + O_NCOMP * O_DMAX + c * O_DMAX + d] += r * (zz * zz - 1.0) * (1.0 - th * th);
+      }
+    }
+  }
+  return lq;
+}
+
+/* Draw d ~ q(. | o) with the replica's Philox stream. */
+void oracle_mixture_sample(const double* o, int D, uint64_t seed, uint32_t rep, uint32_t ctr, double* dl) {
+  double m = -INFINITY;
+  for (int c = 0; c < O_NCOMP; ++c) if (o[c] > m) m = o[c];
+  double w[O_NCOMP], z = 0.0;
+  for (int c = 0; c < O_NCOMP; ++c) { w[c] = exp(o[c] - m); z += w[c]; }
+  uint32_t r4[4];
+  philox(seed, 100u, rep, ctr, O_PURPOSE_LEARNED, r4);
+  double u = oracle_u53(r4[0], r4[1]) * z;
+  int comp = O_NCOMP - 1;
+  double cum = 0.0;
+  for (int c = 0; c < O_NCOMP; ++c) {
+    cum += w[c];
+    if (u < cum) { comp = c; break; }
+  }
+  for (int d = 0; d < D; ++d) {
+    philox(seed, (uint32_t)d, rep, ctr, O_PURPOSE_LEARNED, r4);
+    double z0, z1;
+    box_muller(r4[0], r4[1], &z0, &z1);
+    double mu = o[O_NCOMP + comp * O_DMAX + d];
+    double ls = -2.0 + 4.0 * tanh(o[O_NCOMP + O_NCOMP * O_DMAX + comp * O_DMAX + d] / 4.0);
+    dl[d] = mu + exp(ls) * z0;
+  }
+}
+
+/* n_moves learned proposals per replica at its state, each accepted with the involutive MH test.
+ * x [R][na][3] and comps [R][4] (components of x) are updated in place; acc [R] counts accepts;
+ * logratio [R] (may be NULL) receives the last move's log acceptance ratio. */
+void oracle_learned_mh(const oracle_system* s, const double* W1, const double* b1, const double* W2, const double* b2,
+                       const double* W3, const double* b3, const double* W4, const double* b4, int64_t n_rep,
+                       const int* state_of, int64_t rep_offset, double* x, double* comps, int n_moves, uint64_t seed,
+                       uint64_t cycle, int* acc, double* logratio) {
+  int na = s->na, T = oracle_learned_ntorsions(s), D = 6 + T;
+  double f[O_NFEAT], o[O_NOUT], dl[O_DMAX], ndl[O_DMAX], c1[4];
+  double* y = (double*)malloc(sizeof(double) * 3 * (size_t)na);
+  for (int64_t r = 0; r < n_rep; ++r) {
+    int k = state_of[r];
+    double* xr = x + (size_t)3 * na * r;
+    double* cr = comps + 4 * r;
+    uint32_t rid = (uint32_t)(rep_offset + r);
+    acc[r] = 0;
+    for (int mv = 0; mv < n_moves; ++mv) {
+      uint32_t ctr = (uint32_t)(cycle * (uint64_t)n_moves + (uint64_t)mv);
+      oracle_features(s, xr, cr, k, f);
+      oracle_mlp_forward(W1, b1, W2, b2, W3, b3, W4, b4, 1, f, o, NULL, NULL, NULL);
+      oracle_mixture_sample(o, D, seed, rid, ctr, dl);
+      double lqf = oracle_mixture_logq(o, D, dl, NULL);
+      oracle_apply(s, xr, dl, y);
+      oracle_energy_force(s, y, 0.0, 0.0, NULL, c1);
+      oracle_features(s, y, c1, k, f);
+      oracle_mlp_forward(W1, b1, W2, b2, W3, b3, W4, b4, 1, f, o, NULL, NULL, NULL);
+      for (int d = 0; d < D; ++d) ndl[d] = -dl[d];
+      double lqr = oracle_mixture_logq(o, D, ndl, NULL);
+      double du = s->beta[k] * (weighted_energy(s->w_sg[k], s->w_g[k], c1) - weighted_energy(s->w_sg[k], s->w_g[k], cr));
+      double lr = (lqr - lqf) - du;
+      uint32_t r4[4];
+      philox(seed, 101u, rid, ctr, O_PURPOSE_LEARNED, r4);
+      double u = oracle_u53(r4[0], r4[1]);
+      if (logratio) logratio[r] = lr;
+      if (u < exp(lr)) {
+        memcpy(xr, y, sizeof(double) * 3 * (size_t)na);
+        memcpy(cr, c1, sizeof(c1));
+        acc[r] += 1;
+      }
+    }
+  }
+  free(y);
+}

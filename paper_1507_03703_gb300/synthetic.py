@@ -336,3 +336,16 @@ def harmonic_oscillator_samples(K: int, N_per: int, seed: int, D: int = 1):
     mu = rng.uniform(-1.0, 1.0, size=(K, D))
     xs = [mu[k] + rng.normal(size=(N_per, D)) / np.sqrt(bk[k]) for k in range(K)]
     return bk, mu, np.concatenate(xs, 0), np.full(K, N_per, dtype=np.int64)
+
+
+def mlp_init(seed: int, n_feat: int = 64, n_hid: int = 256, n_out: int = 360, out_scale: float = 0.01):
+    """Random initial weights of the proposal network (He-normal hidden layers, a small output
+    layer, zero biases); row-major [out][in], float64."""
+    rng = np.random.default_rng(np.random.SeedSequence([0x3E7, seed]))
+    sizes = [(n_hid, n_feat), (n_hid, n_hid), (n_hid, n_hid), (n_out, n_hid)]
+    p = {}
+    for i, (o, n) in enumerate(sizes, 1):
+        scale = np.sqrt(2.0 / n) if i < 4 else out_scale / np.sqrt(n)
+        p["W%d" % i] = rng.normal(scale=scale, size=(o, n))
+        p["b%d" % i] = np.zeros(o)
+    return p
