@@ -200,6 +200,71 @@ algdock_status algdock_reduced_energies(algdock_ctx* ctx, int64_t N, const float
 algdock_status algdock_mbar(algdock_ctx* ctx, int32_t K, int64_t N, const double* u_kn, const int64_t* N_k,
                             double tol, int32_t max_iter, int32_t precision_mode, double* f_k, int32_t* iters);
 
+/* ---------------------------------------------------------------- learned pose proposal
+ * An extension of the paper's external-coordinate moves ("Sampling": a random rotation about the
+ * centre of mass and a Gaussian translation, Metropolis-tested): a network proposes rigid-body and
+ * torsion increments d = (t[3] A, w[3] rad axis-angle, d_tau[T] rad), the move
+ * Apply(x, d) = Rigid(d_r/2) . Tor(d_tau) . Rigid(d_r/2) satisfies Apply(Apply(x, d), -d) = x with
+ * unit Jacobian, and the move is accepted with min(1, exp(-(u_k(x') - u_k(x))) q(-d|x') / q(d|x)),
+ * which keeps every state's Boltzmann distribution exact whatever the network.
+ *  - Torsions: root atom 0; a bond is rotatable if both atoms have >= 2 neighbours; the first
+ *    T = min(16, #rotatable) in bond order are moved (the side away from the root).
+ *  - Features (64): (COM - site)/d0; unit vectors COM -> atom 0 and COM -> atom n-1; (cos, sin) of
+ *    the T dihedrals; alpha_sg, alpha_g, 300/T_k; asinh(component/10) of the four components; 0.
+ *  - Network: 64 -> 256 -> 256 -> 256 (ReLU) -> 360 = an 8-component diagonal Gaussian mixture over
+ *    the 22 (= 6 + 16) dimensions: [0,8) logits, [8,184) means [c][22], [184,360) raw log-sigma
+ *    [c][22], log sigma = -2 + 4 tanh(raw / 4); only the first 6 + T dimensions are used.
+ *  - Parameters: one FP32 buffer of ALGDOCK_MLP_NPARAMS floats, W1 [256][64], b1 [256], W2
+ *    [256][256], b2, W3 [256][256], b3, W4 [360][256], b4 [360] (weights row-major [out][in]), and
+ *    a BF16 copy of the four weight matrices (ALGDOCK_MLP_NWEIGHTS, same order).  Matrix products
+ *    run on the tensor cores in BF16 with FP32 accumulation; hidden activations are stored in BF16.
+ *  - Random numbers: Philox counter {draw, replica, cycle * n_moves + move, 4}: draw d < 22 the
+ *    normal of dimension d, draw 100 the mixture component, draw 101 the acceptance uniform. */
+enum {
+  ALGDOCK_MLP_NFEAT = 64,
+  ALGDOCK_MLP_NHID = 256,
+  ALGDOCK_MLP_NOUT = 360,
+  ALGDOCK_MLP_DMAX = 22,
+  ALGDOCK_MLP_NWEIGHTS = 64 * 256 + 256 * 256 + 256 * 256 + 256 * 360,
+  ALGDOCK_MLP_NPARAMS = 64 * 256 + 256 + 256 * 256 + 256 + 256 * 256 + 256 + 256 * 360 + 360
+};
+
+/* Number of moved torsions T of the loaded ligand (host call). */
+algdock_status algdock_learned_ntorsions(algdock_ctx* ctx, int32_t* T);
+
+/* Features of N poses: state_of [N] int32, x [N][n_atoms][3] float, comps [N][4] double (the
+ * components of x); feat [N][64] float out. */
+algdock_status algdock_learned_features(algdock_ctx* ctx, int64_t N, const int32_t* state_of, const float* x,
+                                        const double* comps, float* feat);
+
+/* Training targets: the move taking pose x to pose y (translation of the centre of mass, rotation
+ * of the frame of atoms 0 and n-1, wrapped torsion differences).  x, y [N][n_atoms][3] float;
+ * delta [N][22] float out (unused dimensions 0). */
+algdock_status algdock_pose_delta(algdock_ctx* ctx, int64_t N, const float* x, const float* y, float* delta);
+
+/* Network outputs for N feature rows: params FP32 [NPARAMS] (biases read from it), wbf16 [NWEIGHTS]
+ * (uint16 BF16 bits); feat [N][64] float; out [N][360] float. */
+algdock_status algdock_mlp_forward(algdock_ctx* ctx, const float* params, const uint16_t* wbf16, int64_t N,
+                                   const float* feat, float* out);
+
+/* Gradient of the mean negative log-density of the targets, -(1/N) sum_n log q(delta_n | feat_n),
+ * over the first D dimensions: grad [NPARAMS] float out (FP32), loss (device float, may be NULL). */
+algdock_status algdock_mlp_grad(algdock_ctx* ctx, const float* params, const uint16_t* wbf16, int64_t N,
+                                const float* feat, const float* delta, int32_t D, float* grad, float* loss);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on params from grad; m, v [NPARAMS] moments;
+ * step >= 1; refreshes the BF16 copy wbf16. */
+algdock_status algdock_mlp_adam(algdock_ctx* ctx, float* params, uint16_t* wbf16, const float* grad, float* m, float* v,
+                                int32_t step, float lr);
+
+/* n_moves learned proposals for each of n_rep replicas at its state (state_of), each accepted or
+ * rejected as above in FP64.  x and comps (the components of x) are updated in place; accepted
+ * [n_rep] int32 (may be NULL) is added to; counters as for algdock_hmc_cycle (may be NULL). */
+algdock_status algdock_propose_learned(algdock_ctx* ctx, const float* params, const uint16_t* wbf16, int64_t n_rep,
+                                       const int32_t* state_of, float* x, double* comps, int32_t n_moves,
+                                       uint64_t seed, uint64_t cycle, int64_t rep_offset, int32_t* accepted,
+                                       int64_t* counters);
+
 /* MBAR without any device allocation.  The paper has no counterpart: this is a service of this
  * library for callers that cannot call cudaMalloc - for example a host framework whose caching
  * allocator owns all device memory and forbids direct allocations, or a service that reserves its

@@ -375,6 +375,7 @@ _MLP_KEYS = ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")
 def _learned_sigs(L):
     if getattr(L, "_learned", False):
         return
+    L.oracle_set_bf16_activations.argtypes = [C.c_int]
     L.oracle_learned_ntorsions.argtypes = [C.c_void_p]
     L.oracle_learned_ntorsions.restype = C.c_int
     L.oracle_features.argtypes = [C.c_void_p, _d, _d, C.c_int, _d]
@@ -392,6 +393,14 @@ def _learned_sigs(L):
 
 def _p(params):
     return [_f64(params[k]).ravel() for k in _MLP_KEYS]
+
+
+def set_bf16_activations(on: bool):
+    """Round the network's input and hidden activations to BF16 (as a BF16 tensor-core
+    implementation stores them) in every later forward pass; default off (FP64)."""
+    L = _load()
+    _learned_sigs(L)
+    L.oracle_set_bf16_activations(1 if on else 0)
 
 
 def mlp_forward(params, X):

@@ -1137,16 +1137,44 @@ static void o_dense(int B, int nin, int nout, const double* W, const double* b, 
     }
 }
 
+/* With BF16 emulation on, the network's input and hidden activations are rounded to BF16 (round
+ * to nearest even), as a BF16 tensor-core implementation stores them; off (the default), FP64. */
+static int o_bf16_act = 0;
+void oracle_set_bf16_activations(int on) { o_bf16_act = on; }
+
+static double o_bf16(double v) {
+  float f = (float)v;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0x7fffu + ((u >> 16) & 1u);
+    u &= 0xffff0000u;
+  }
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
 void oracle_mlp_forward(const double* W1, const double* b1, const double* W2, const double* b2, const double* W3,
                         const double* b3, const double* W4, const double* b4, int B, const double* X, double* out,
                         double* h1, double* h2, double* h3) {
   double* a1 = h1 ? h1 : (double*)malloc(sizeof(double) * (size_t)B * O_HID);
   double* a2 = h2 ? h2 : (double*)malloc(sizeof(double) * (size_t)B * O_HID);
   double* a3 = h3 ? h3 : (double*)malloc(sizeof(double) * (size_t)B * O_HID);
-  o_dense(B, O_NFEAT, O_HID, W1, b1, X, a1, 1);
+  const double* in = X;
+  double* xr = NULL;
+  if (o_bf16_act) {
+    xr = (double*)malloc(sizeof(double) * (size_t)B * O_NFEAT);
+    for (size_t i = 0; i < (size_t)B * O_NFEAT; ++i) xr[i] = o_bf16(X[i]);
+    in = xr;
+  }
+  o_dense(B, O_NFEAT, O_HID, W1, b1, in, a1, 1);
+  if (o_bf16_act) for (size_t i = 0; i < (size_t)B * O_HID; ++i) a1[i] = o_bf16(a1[i]);
   o_dense(B, O_HID, O_HID, W2, b2, a1, a2, 1);
+  if (o_bf16_act) for (size_t i = 0; i < (size_t)B * O_HID; ++i) a2[i] = o_bf16(a2[i]);
   o_dense(B, O_HID, O_HID, W3, b3, a2, a3, 1);
+  if (o_bf16_act) for (size_t i = 0; i < (size_t)B * O_HID; ++i) a3[i] = o_bf16(a3[i]);
   o_dense(B, O_HID, O_NOUT, W4, b4, a3, out, 0);
+  free(xr);
   if (!h1) free(a1);
   if (!h2) free(a2);
   if (!h3) free(a3);

@@ -28,8 +28,47 @@ EXPORTS = [
     "algdock_create", "algdock_destroy", "algdock_set_stream", "algdock_last_error", "algdock_grids_build",
     "algdock_soft_elec_cap", "algdock_grids_load", "algdock_ligand_load", "algdock_states_set",
     "algdock_hmc_cycle", "algdock_energy_force", "algdock_exchange", "algdock_reduced_energies", "algdock_mbar",
-    "algdock_mbar_noalloc",
+    "algdock_mbar_noalloc", "algdock_learned_ntorsions", "algdock_learned_features", "algdock_pose_delta",
+    "algdock_mlp_forward", "algdock_mlp_grad", "algdock_mlp_adam", "algdock_propose_learned",
 ]
+MLP_NFEAT, MLP_NHID, MLP_NOUT, MLP_DMAX = 64, 256, 360, 22
+MLP_KEYS = ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")
+MLP_NPARAMS = 64 * 256 + 256 + 256 * 256 + 256 + 256 * 256 + 256 + 256 * 360 + 360
+MLP_NWEIGHTS = 64 * 256 + 256 * 256 + 256 * 256 + 256 * 360
+
+
+def bf16_bits(a):
+    """Round float32 values to BF16 (nearest even) and return the 16-bit patterns."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    finite = (u & 0x7F800000) != 0x7F800000
+    r = np.where(finite, u + 0x7FFF + ((u >> 16) & 1), u)
+    return ((r >> 16) & 0xFFFF).astype(np.uint16)
+
+
+def bf16_values(a):
+    """The float32 values of the BF16 rounding of a."""
+    return (bf16_bits(a).astype(np.uint32) << 16).view(np.float32)
+
+
+def pack_mlp(params):
+    """Flatten a parameter dict (W1 [256][64], b1, ..., W4 [360][256], b4) into the library's FP32
+    parameter vector and the BF16 copy of its weight matrices (numpy)."""
+    flat = np.concatenate([np.asarray(params[k], dtype=np.float32).ravel() for k in MLP_KEYS])
+    w = np.concatenate([np.asarray(params[k], dtype=np.float32).ravel() for k in ("W1", "W2", "W3", "W4")])
+    assert flat.size == MLP_NPARAMS and w.size == MLP_NWEIGHTS
+    return flat, bf16_bits(w)
+
+
+def unpack_mlp(flat):
+    """Inverse of the FP32 part of pack_mlp."""
+    shapes = {"W1": (256, 64), "b1": (256,), "W2": (256, 256), "b2": (256,), "W3": (256, 256), "b3": (256,),
+              "W4": (360, 256), "b4": (360,)}
+    out, o = {}, 0
+    for k in MLP_KEYS:
+        n = int(np.prod(shapes[k]))
+        out[k] = np.asarray(flat[o:o + n], dtype=np.float64).reshape(shapes[k])
+        o += n
+    return out
 
 
 class AlgdockError(RuntimeError):
@@ -82,6 +121,13 @@ def load_library(path: str = LIB_PATH):
         "algdock_reduced_energies": ([vp, i64, vp, vp, i32, i32, vp], C.c_int),
         "algdock_mbar": ([vp, i32, i64, vp, vp, dbl, i32, i32, vp, C.POINTER(i32)], C.c_int),
         "algdock_mbar_noalloc": ([vp, i32, i64, vp, vp, dbl, i32, i32, vp, C.POINTER(i32)], C.c_int),
+        "algdock_learned_ntorsions": ([vp, C.POINTER(i32)], C.c_int),
+        "algdock_learned_features": ([vp, i64, vp, vp, vp, vp], C.c_int),
+        "algdock_pose_delta": ([vp, i64, vp, vp, vp], C.c_int),
+        "algdock_mlp_forward": ([vp, vp, vp, i64, vp, vp], C.c_int),
+        "algdock_mlp_grad": ([vp, vp, vp, i64, vp, vp, i32, vp, vp], C.c_int),
+        "algdock_mlp_adam": ([vp, vp, vp, vp, vp, vp, i32, C.c_float], C.c_int),
+        "algdock_propose_learned": ([vp, vp, vp, i64, vp, vp, vp, i32, u64, u64, i64, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -294,6 +340,53 @@ class Context:
             return f, -1
         self._check(st)
         return f, it.value
+
+    # ---------------------------------------------------------------- learned proposal
+    def learned_ntorsions(self):
+        T = C.c_int32()
+        self._check(self._L.algdock_learned_ntorsions(self.h, C.byref(T)))
+        return T.value
+
+    def learned_features(self, state_of, x, comps, feat):
+        import torch
+        self._check(self._L.algdock_learned_features(
+            self.h, int(state_of.numel()), _dev(state_of, torch.int32, "state_of"), _dev(x, torch.float32, "x"),
+            _dev(comps, torch.float64, "comps"), _dev(feat, torch.float32, "feat")))
+
+    def pose_delta(self, x, y, delta):
+        import torch
+        self._check(self._L.algdock_pose_delta(self.h, int(x.shape[0]), _dev(x, torch.float32, "x"),
+                                               _dev(y, torch.float32, "y"), _dev(delta, torch.float32, "delta")))
+
+    def mlp_forward(self, params, wbf16, feat, out):
+        import torch
+        self._check(self._L.algdock_mlp_forward(self.h, _dev(params, torch.float32, "params"),
+                                                _dev(wbf16, torch.int16, "wbf16"), int(feat.shape[0]),
+                                                _dev(feat, torch.float32, "feat"), _dev(out, torch.float32, "out")))
+
+    def mlp_grad(self, params, wbf16, feat, delta, D, grad, loss=None):
+        import torch
+        self._check(self._L.algdock_mlp_grad(self.h, _dev(params, torch.float32, "params"),
+                                             _dev(wbf16, torch.int16, "wbf16"), int(feat.shape[0]),
+                                             _dev(feat, torch.float32, "feat"), _dev(delta, torch.float32, "delta"),
+                                             int(D), _dev(grad, torch.float32, "grad"),
+                                             _dev(loss, torch.float32, "loss")))
+
+    def mlp_adam(self, params, wbf16, grad, m, v, step, lr):
+        import torch
+        self._check(self._L.algdock_mlp_adam(self.h, _dev(params, torch.float32, "params"),
+                                             _dev(wbf16, torch.int16, "wbf16"), _dev(grad, torch.float32, "grad"),
+                                             _dev(m, torch.float32, "m"), _dev(v, torch.float32, "v"), int(step),
+                                             float(lr)))
+
+    def propose_learned(self, params, wbf16, state_of, x, comps, n_moves, seed=0, cycle=0, rep_offset=0,
+                        accepted=None, counters=None):
+        import torch
+        self._check(self._L.algdock_propose_learned(
+            self.h, _dev(params, torch.float32, "params"), _dev(wbf16, torch.int16, "wbf16"), int(state_of.numel()),
+            _dev(state_of, torch.int32, "state_of"), _dev(x, torch.float32, "x"), _dev(comps, torch.float64, "comps"),
+            int(n_moves), int(seed), int(cycle), int(rep_offset), _dev(accepted, torch.int32, "accepted"),
+            _dev(counters, torch.int64, "counters")))
 
     def mbar_noalloc(self, u_kn, N_k, tol=1e-10, max_iter=10000, precision_mode=0):
         """algdock_mbar_noalloc: MBAR whose scratch is the library's fixed device array (for callers

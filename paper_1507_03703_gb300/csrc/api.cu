@@ -150,6 +150,7 @@ void algdock_destroy(algdock_ctx* c) {
   cudaFree(c->d_blob);
   cudaFree(c->d_states);
   cudaFree(c->d_mbar);
+  cudaFree(c->d_learn);
   cudaFreeHost(c->h_flag);
   delete c;
 }
@@ -416,6 +417,7 @@ algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, cons
   if (e == cudaSuccess) e = cudaMemcpy(c->d_blob, blob.data(), (size_t)w * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(c, e, "ligand_load");
   c->lig = Y;
+  build_learned_topo(na, nb, L->bonds, &c->ltopo);
   c->has_ligand = true;
   return ALGDOCK_OK;
   ALGDOCK_CATCH(c)
@@ -537,6 +539,128 @@ algdock_status algdock_reduced_energies(algdock_ctx* c, int64_t N, const float* 
   if (e == cudaSuccess && u_kn) e = launch_ukn(c->stream, *c, N, cp, k_begin, k_count, u_kn);
   if (tmp) cudaFreeAsync(tmp, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "reduced_energies");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+// ------------------------------------------------------------------ learned proposal
+static algdock_status learn_scratch(algdock_ctx* c, size_t need, const char* where) {
+  if (need <= c->learn_bytes) return ALGDOCK_OK;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  cudaFree(c->d_learn);
+  c->d_learn = nullptr;
+  c->learn_bytes = 0;
+  e = cudaMalloc(&c->d_learn, need);
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  c->learn_bytes = need;
+  return ALGDOCK_OK;
+}
+
+algdock_status algdock_learned_ntorsions(algdock_ctx* c, int32_t* T) {
+  ALGDOCK_TRY(c)
+  if (!T) return fail(c, ALGDOCK_E_INVALID, "learned_ntorsions: null argument");
+  if (!c->has_ligand) return fail(c, ALGDOCK_E_STATE, "learned_ntorsions: load the ligand first");
+  *T = c->ltopo.T;
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_learned_features(algdock_ctx* c, int64_t N, const int32_t* state_of, const float* x,
+                                        const double* comps, float* feat) {
+  ALGDOCK_TRY(c)
+  if (!c->has_ligand || c->K == 0) return fail(c, ALGDOCK_E_STATE, "learned_features: load ligand and states first");
+  if (N < 0) return fail(c, ALGDOCK_E_INVALID, "learned_features: N < 0");
+  if (N == 0) return ALGDOCK_OK;
+  if (!is_device_ptr(state_of) || !is_device_ptr(x) || !is_device_ptr(comps) || !is_device_ptr(feat))
+    return fail(c, ALGDOCK_E_INVALID, "learned_features: arrays must be device pointers");
+  Device g(c->device);
+  cudaError_t e = learned_features(c->stream, *c, N, state_of, x, comps, feat);
+  if (e != cudaSuccess) return cuda_fail(c, e, "learned_features");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_pose_delta(algdock_ctx* c, int64_t N, const float* x, const float* y, float* delta) {
+  ALGDOCK_TRY(c)
+  if (!c->has_ligand) return fail(c, ALGDOCK_E_STATE, "pose_delta: load the ligand first");
+  if (N < 0) return fail(c, ALGDOCK_E_INVALID, "pose_delta: N < 0");
+  if (N == 0) return ALGDOCK_OK;
+  if (!is_device_ptr(x) || !is_device_ptr(y) || !is_device_ptr(delta))
+    return fail(c, ALGDOCK_E_INVALID, "pose_delta: arrays must be device pointers");
+  Device g(c->device);
+  cudaError_t e = learned_pose_delta(c->stream, *c, N, x, y, delta);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pose_delta");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_mlp_forward(algdock_ctx* c, const float* params, const uint16_t* wbf16, int64_t N,
+                                   const float* feat, float* out) {
+  ALGDOCK_TRY(c)
+  if (N < 0 || N > (int64_t)1 << 30) return fail(c, ALGDOCK_E_INVALID, "mlp_forward: bad N");
+  if (N == 0) return ALGDOCK_OK;
+  if (!is_device_ptr(params) || !is_device_ptr(wbf16) || !is_device_ptr(feat) || !is_device_ptr(out))
+    return fail(c, ALGDOCK_E_INVALID, "mlp_forward: arrays must be device pointers");
+  Device g(c->device);
+  algdock_status st = learn_scratch(c, learned_forward_scratch(N), "mlp_forward");
+  if (st != ALGDOCK_OK) return st;
+  cudaError_t e = learned_forward(c->stream, params, wbf16, N, feat, out, c->d_learn);
+  if (e != cudaSuccess) return cuda_fail(c, e, "mlp_forward");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_mlp_grad(algdock_ctx* c, const float* params, const uint16_t* wbf16, int64_t N, const float* feat,
+                                const float* delta, int32_t D, float* grad, float* loss) {
+  ALGDOCK_TRY(c)
+  if (N < 1 || N > (int64_t)1 << 30 || D < 1 || D > ALGDOCK_MLP_DMAX)
+    return fail(c, ALGDOCK_E_INVALID, "mlp_grad: bad N or D");
+  if (!is_device_ptr(params) || !is_device_ptr(wbf16) || !is_device_ptr(feat) || !is_device_ptr(delta) ||
+      !is_device_ptr(grad) || (loss && !is_device_ptr(loss)))
+    return fail(c, ALGDOCK_E_INVALID, "mlp_grad: arrays must be device pointers");
+  Device g(c->device);
+  algdock_status st = learn_scratch(c, learned_grad_scratch(N), "mlp_grad");
+  if (st != ALGDOCK_OK) return st;
+  cudaError_t e = learned_grad(c->stream, params, wbf16, N, feat, delta, D, grad, loss, c->d_learn);
+  if (e != cudaSuccess) return cuda_fail(c, e, "mlp_grad");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_mlp_adam(algdock_ctx* c, float* params, uint16_t* wbf16, const float* grad, float* m, float* v,
+                                int32_t step, float lr) {
+  ALGDOCK_TRY(c)
+  if (step < 1 || !(lr >= 0.f)) return fail(c, ALGDOCK_E_INVALID, "mlp_adam: step >= 1 and lr >= 0");
+  if (!is_device_ptr(params) || !is_device_ptr(wbf16) || !is_device_ptr(grad) || !is_device_ptr(m) ||
+      !is_device_ptr(v))
+    return fail(c, ALGDOCK_E_INVALID, "mlp_adam: arrays must be device pointers");
+  Device g(c->device);
+  cudaError_t e = learned_adam(c->stream, params, wbf16, grad, m, v, step, lr);
+  if (e != cudaSuccess) return cuda_fail(c, e, "mlp_adam");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_propose_learned(algdock_ctx* c, const float* params, const uint16_t* wbf16, int64_t n_rep,
+                                       const int32_t* state_of, float* x, double* comps, int32_t n_moves,
+                                       uint64_t seed, uint64_t cycle, int64_t rep_offset, int32_t* accepted,
+                                       int64_t* counters) {
+  ALGDOCK_TRY(c)
+  if (!c->has_grid || !c->has_ligand || c->K == 0)
+    return fail(c, ALGDOCK_E_STATE, "propose_learned: load grids, ligand and states first");
+  if (n_rep < 0 || n_rep > (int64_t)1 << 30 || n_moves < 0 || rep_offset < 0)
+    return fail(c, ALGDOCK_E_INVALID, "propose_learned: bad sizes");
+  if (n_rep == 0 || n_moves == 0) return ALGDOCK_OK;
+  if (!is_device_ptr(params) || !is_device_ptr(wbf16) || !is_device_ptr(state_of) || !is_device_ptr(x) ||
+      !is_device_ptr(comps) || (accepted && !is_device_ptr(accepted)) || (counters && !is_device_ptr(counters)))
+    return fail(c, ALGDOCK_E_INVALID, "propose_learned: arrays must be device pointers");
+  Device g(c->device);
+  algdock_status st = learn_scratch(c, learned_propose_scratch(n_rep, c->lig.na), "propose_learned");
+  if (st != ALGDOCK_OK) return st;
+  cudaError_t e = learned_propose(c->stream, *c, params, wbf16, n_rep, state_of, x, comps, n_moves, seed, cycle,
+                                  rep_offset, accepted, counters, c->d_learn);
+  if (e != cudaSuccess) return cuda_fail(c, e, "propose_learned");
   return ALGDOCK_OK;
   ALGDOCK_CATCH(c)
 }

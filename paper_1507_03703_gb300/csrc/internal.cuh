@@ -91,6 +91,15 @@ struct LigandLayout {
   float k_rest, d0;
 };
 
+// Torsion tree of the learned proposal: root atom 0, the first 16 rotatable bonds in bond order.
+constexpr int kLearnTmax = 16;
+struct LearnedTopo {
+  int T;
+  int prox[kLearnTmax], dist[kLearnTmax];  // bond atoms on the root side / away from the root
+  int dih[kLearnTmax][4];                  // dihedral atoms (features)
+  uint32_t moved[kLearnTmax][3];           // bit i: atom i turns with torsion k
+};
+
 }  // namespace algdock
 
 // The context (opaque to callers).
@@ -116,6 +125,10 @@ struct algdock_ctx {
   size_t mbar_bytes = 0;
   // pinned host word for convergence polling
   int* h_flag = nullptr;
+  // learned proposal: torsion tree and scratch grown on demand
+  algdock::LearnedTopo ltopo{};
+  void* d_learn = nullptr;
+  size_t learn_bytes = 0;
 };
 
 namespace algdock {
@@ -133,6 +146,24 @@ cudaError_t launch_energy_force(cudaStream_t s, const algdock_ctx& c, int64_t N,
                                 const float* x, float* force, double* comps);
 cudaError_t launch_ukn(cudaStream_t s, const algdock_ctx& c, int64_t N, const double* comps, int k_begin,
                        int k_count, double* u_kn);
+void build_learned_topo(int na, int nb, const int32_t* bonds, LearnedTopo* t);
+cudaError_t learned_features(cudaStream_t s, const algdock_ctx& c, int64_t N, const int32_t* state_of,
+                             const float* x, const double* comps, float* feat);
+cudaError_t learned_pose_delta(cudaStream_t s, const algdock_ctx& c, int64_t N, const float* x, const float* y,
+                               float* delta);
+size_t learned_forward_scratch(int64_t N);
+cudaError_t learned_forward(cudaStream_t s, const float* params, const uint16_t* wbf16, int64_t N, const float* feat,
+                            float* out, void* scratch);
+size_t learned_grad_scratch(int64_t N);
+cudaError_t learned_grad(cudaStream_t s, const float* params, const uint16_t* wbf16, int64_t N, const float* feat,
+                         const float* delta, int D, float* grad, float* loss, void* scratch);
+cudaError_t learned_adam(cudaStream_t s, float* params, uint16_t* wbf16, const float* grad, float* m, float* v, int step,
+                         float lr);
+size_t learned_propose_scratch(int64_t n_rep, int na);
+cudaError_t learned_propose(cudaStream_t s, const algdock_ctx& c, const float* params, const uint16_t* wbf16,
+                            int64_t n_rep, const int32_t* state_of, float* x, double* comps, int n_moves,
+                            uint64_t seed, uint64_t cycle, int64_t rep_offset, int32_t* accepted, int64_t* counters,
+                            void* scratch);
 cudaError_t launch_exchange(cudaStream_t s, const algdock_ctx& c, int n_ladders, int K, int state_offset,
                             const double* comps, int32_t* config_of, int32_t* state_of, int n_sweeps, int max_sep,
                             uint64_t seed, uint64_t cycle, int64_t ladder_offset, int64_t* attempts,
