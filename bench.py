@@ -37,6 +37,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-mbar", action="store_true")
+    p.add_argument("--no-learned", action="store_true")
     return p.parse_args()
 
 
@@ -153,6 +154,67 @@ def measured_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=40, train_iter=300, cmp_cycles=200,
+                     n_moves=4, lag=4, seed=7):
+    """Effective samples per second at the target state (alpha = 1, 300 K) of plain HMC and of HMC
+    plus learned proposals, after training the proposal on the plain run's own samples (moves
+    between poses of the same chain `lag` cycles apart).  ESS: sum over chains of N / g of the
+    Psi_g series."""
+    import torch
+
+    from paper_1507_03703_gb300 import synthetic as S
+    from paper_1507_03703_gb300.learned import LearnedProposal, effective_samples
+    target = N_STATES_BC + N_STATES_CD - 1
+    lig = sys_.ligand
+    base = S.place_ligand(lig, sys_.receptor, sys_.site, 128, seed=seed, n_tries=8).astype(np.float32)
+    x = torch.from_numpy(base[np.arange(chains) % 128]).to(dev)
+    comps = torch.empty((chains, 4), dtype=torch.float64, device=dev)
+    st = torch.full((chains,), target, dtype=torch.int32, device=dev)
+    ctx.reduced_energies(chains, x=x, comps=comps)
+    xs, cs = [], []
+    for cyc in range(burn + data_cycles):
+        ctx.hmc_cycle(st, x, comps, n_steps=N_VV, seed=seed, cycle=cyc)
+        if cyc >= burn:
+            xs.append(x.clone())
+            cs.append(comps.clone())
+    X = torch.cat(xs)
+    Cm = torch.cat(cs)
+    lp = LearnedProposal(ctx, seed=seed)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    t_idx = np.arange(data_cycles - lag)
+    I = (t_idx[:, None] * chains + np.arange(chains)[None, :]).ravel()
+    losses = lp.train(X, Cm, target, n_iter=train_iter, batch=4096, lr=1e-3, seed=seed, pairs=(I, I + lag * chains))
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    train_ms = ev[0].elapsed_time(ev[1])
+    x0, c0 = x.clone(), comps.clone()
+    out = {"state": "alpha=1, 300 K", "chains": chains, "training_poses": int(X.shape[0]), "train_iters": train_iter,
+           "train_ms": train_ms, "loss_first": losses[0], "loss_last": losses[-1], "moves_per_cycle": n_moves,
+           "training_pairs": "same chain, %d cycles apart" % lag}
+    for mode in ("plain", "learned"):
+        x.copy_(x0)
+        comps.copy_(c0)
+        acc = torch.zeros(chains, dtype=torch.int32, device=dev)
+        series = []
+        t = 0.0
+        for cyc in range(cmp_cycles):
+            ev[0].record(stream)
+            ctx.hmc_cycle(st, x, comps, n_steps=N_VV, seed=seed + 1, cycle=1000 + cyc)
+            if mode == "learned":
+                lp.propose(st, x, comps, n_moves, seed=seed + 2, cycle=cyc, accepted=acc)
+            ev[1].record(stream)
+            series.append(comps[:, 3].clone())
+            torch.cuda.synchronize()
+            t += ev[0].elapsed_time(ev[1])
+        ess = effective_samples(torch.stack(series).cpu().numpy())
+        out[mode] = {"ess": ess, "ms": t, "ess_per_s": ess / (t * 1e-3)}
+        if mode == "learned":
+            out[mode]["move_acceptance"] = float(acc.sum().item()) / (chains * cmp_cycles * n_moves)
+    out["ess_per_s_ratio"] = out["learned"]["ess_per_s"] / out["plain"]["ess_per_s"]
+    return out
 
 
 def oracle_cpu_baseline(sys_, n_rep=4096, n_threads=0):
@@ -359,6 +421,9 @@ def main():
             extra["mbar_%s_iters_per_s" % key] = 50 / el
         f, it = ctx.mbar(u, N_k, tol=1e-10, max_iter=20000)
         extra["mbar_K"], extra["mbar_N"], extra["mbar_iters_to_1e-10"] = len(T), N, it
+        del u, comps_hist
+    if not args.no_learned and rank == 0:
+        extra["learned_vs_plain"] = learned_vs_plain(ctx, sys_, stream, dev)
 
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,

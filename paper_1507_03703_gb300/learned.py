@@ -1,0 +1,95 @@
+"""Training and use of the learned pose proposal through the C ABI.
+
+The proposal network is trained on poses that plain HMC itself sampled: for random pairs (x_i,
+x_j) of samples at one state, the target is the move that takes x_i to x_j, and the loss is the
+mean negative log-density of those moves under the network's mixture.  Every step (features,
+targets, forward and backward passes, Adam) runs in the library; this module only picks pairs and
+orders the calls.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import synthetic
+from .algdock import MLP_DMAX, MLP_NFEAT, MLP_NPARAMS, pack_mlp
+
+
+class LearnedProposal:
+    """Device-resident network parameters (FP32 master + BF16 copy) and Adam moments."""
+
+    def __init__(self, ctx, seed: int = 0, device="cuda"):
+        self.ctx = ctx
+        flat, w = pack_mlp(synthetic.mlp_init(seed))
+        dev = torch.device(device)
+        self.params = torch.from_numpy(flat).to(dev)
+        self.wbf16 = torch.from_numpy(w.view(np.int16)).to(dev)
+        self.m = torch.zeros(MLP_NPARAMS, dtype=torch.float32, device=dev)
+        self.v = torch.zeros_like(self.m)
+        self.grad = torch.zeros_like(self.m)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.step = 0
+        self.T = ctx.learned_ntorsions()
+
+    def train(self, x, comps, state: int, n_iter: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
+              pairs=None):
+        """Adam on the mean negative log-density of moves between pairs of the samples
+        x [S][n_atoms][3] (float32, device) with components comps [S][4] at one state: random pairs,
+        or the given (I, J) index arrays (e.g. the same chain a few cycles apart).  Returns the loss
+        after each iteration."""
+        S = x.shape[0]
+        dev = x.device
+        rng = np.random.default_rng(seed)
+        if pairs is not None:
+            PI = torch.as_tensor(np.asarray(pairs[0]), device=dev)
+            PJ = torch.as_tensor(np.asarray(pairs[1]), device=dev)
+        st = torch.full((batch,), int(state), dtype=torch.int32, device=dev)
+        feat = torch.empty((batch, MLP_NFEAT), dtype=torch.float32, device=dev)
+        delta = torch.empty((batch, MLP_DMAX), dtype=torch.float32, device=dev)
+        losses = []
+        D = 6 + self.T
+        for _ in range(n_iter):
+            if pairs is None:
+                i = torch.from_numpy(rng.integers(0, S, size=batch)).to(dev)
+                j = torch.from_numpy(rng.integers(0, S, size=batch)).to(dev)
+            else:
+                sel = torch.from_numpy(rng.integers(0, PI.numel(), size=batch)).to(dev)
+                i, j = PI[sel], PJ[sel]
+            xi, xj = x[i].contiguous(), x[j].contiguous()
+            self.ctx.learned_features(st, xi, comps[i].contiguous(), feat)
+            self.ctx.pose_delta(xi, xj, delta)
+            self.ctx.mlp_grad(self.params, self.wbf16, feat, delta, D, self.grad, self.loss)
+            self.step += 1
+            self.ctx.mlp_adam(self.params, self.wbf16, self.grad, self.m, self.v, self.step, lr)
+            losses.append(self.loss.clone())
+        return [float(l.item()) for l in losses]
+
+    def propose(self, state_of, x, comps, n_moves, seed, cycle, accepted=None, counters=None, rep_offset=0):
+        self.ctx.propose_learned(self.params, self.wbf16, state_of, x, comps, n_moves, seed=seed, cycle=cycle,
+                                 rep_offset=rep_offset, accepted=accepted, counters=counters)
+
+
+def statistical_inefficiency(a):
+    """g = 1 + 2 sum_t (1 - t/N) C(t), summed until the normalised autocorrelation first drops to
+    zero (used to report effective sample sizes)."""
+    a = np.asarray(a, dtype=np.float64)
+    N = a.size
+    if N < 2:
+        return 1.0
+    d = a - a.mean()
+    var = np.dot(d, d) / N
+    if var == 0.0:
+        return 1.0
+    g = 1.0
+    for t in range(1, N):
+        c = np.dot(d[:-t], d[t:]) / ((N - t) * var)
+        if c <= 0.0:
+            break
+        g += 2.0 * c * (1.0 - t / N)
+    return max(g, 1.0)
+
+
+def effective_samples(series):
+    """Sum over chains of N / g for series [cycles][chains]."""
+    s = np.asarray(series)
+    return float(sum(s.shape[0] / statistical_inefficiency(s[:, c]) for c in range(s.shape[1])))

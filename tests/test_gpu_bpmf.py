@@ -48,6 +48,44 @@ def test_one_atom_bpmf_matches_quadrature():
     assert int(run.counters[1].item()) == 0  # no non-finite trial
 
 
+def test_one_atom_bpmf_with_learned_moves_matches_quadrature():
+    """The same estimate with four learned proposals (random network) per replica and cycle at
+    every state between HMC and exchange: the Metropolis-Hastings test keeps each state's
+    distribution exact, so the BPMF still matches quadrature (bound 0.2 kT or 4 standard errors)."""
+    from paper_1507_03703_gb300.learned import LearnedProposal
+    from paper_1507_03703_gb300.sampler import Leg, ReplicaExchange, bpmf_kT
+    sys_ = S.config_small(1)
+    lig = S.one_atom_ligand()
+    g32 = raw_grids32(sys_)
+    K, C, dt = 8, 64, 4.0
+    bc, cd = S.bc_ladder(K, dt_fs=dt), S.cd_ladder(K, dt_fs=dt)
+    T = np.concatenate([bc.T, cd.T])
+    alpha = np.concatenate([bc.alpha, cd.alpha])
+    ctx = gpu_context(sys_, g32, T, alpha, np.full(2 * K, dt), ligand=lig)
+    lp = LearnedProposal(ctx, seed=3)
+    rng = np.random.default_rng(6)
+    x0 = uniform_in_sphere(rng, 2 * C * K, 6.0, sys_.grid.center).astype(np.float32)
+    run = ReplicaExchange(ctx, [Leg(K, 0), Leg(K, K)], C, x0, seed=31)
+    acc = torch.zeros(run.R, dtype=torch.int32, device="cuda")
+    for cyc in range(300):
+        run.hmc(cyc, 40)
+        lp.propose(run.state_of, run.x, run.comps, 4, seed=32, cycle=cyc, accepted=acc)
+        run.exchange(cyc)
+        if cyc >= 40:
+            run.history.append(run.comps.clone())
+    groups = []
+    for g in range(8):
+        ch = np.arange(g, C, 8)
+        groups.append(bpmf_kT(run.free_energies(0, chains=ch)[0], run.free_energies(1, chains=ch)[0]))
+    B = bpmf_kT(run.free_energies(0)[0], run.free_energies(1)[0])
+    se = np.std(groups, ddof=1) / np.sqrt(8)
+    target = quadrature_bpmf(sys_.grid, *[a.astype(np.float64) for a in g32], lig)
+    rate = float(acc.sum().item()) / (run.R * 300 * 4)
+    print("one-atom BPMF with learned moves", B, "quadrature", target, "se", se, "move acceptance", rate)
+    assert 0.01 < rate < 0.999
+    assert abs(B - target) < max(0.2, 4 * se), (B, target, se)
+
+
 def test_small_ligand_bpmf_matches_oracle():
     """20-atom ligand, 8 + 8 states, 2 fs: the GPU estimate against the oracle's estimate from
     its own FP64 run with the same inputs and seeds."""
