@@ -157,16 +157,16 @@ def measured_peaks():
 
 
 def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=40, train_iter=300, cmp_cycles=200,
-                     n_moves=4, lag=4, seed=7):
-    """Effective samples per second at the target state (alpha = 1, 300 K) of plain HMC and of HMC
-    plus learned proposals, after training the proposal on the plain run's own samples (moves
-    between poses of the same chain `lag` cycles apart).  ESS: sum over chains of N / g of the
-    Psi_g series."""
+                     n_moves=4, lag=None, seed=7, target=N_STATES_BC, n_torsions=0):
+    """Effective samples per second at one state of plain HMC and of HMC plus learned proposals,
+    after training the proposal on the plain run's own samples: moves between random pairs of
+    samples (lag None) or between poses of the same chain `lag` cycles apart.  The default state
+    is the decoupled end of the coupling leg (alpha = 0, 600 K), where the paper applies its own
+    external-coordinate moves.  ESS: sum over chains of N / g of the Psi_g series."""
     import torch
 
     from paper_1507_03703_gb300 import synthetic as S
     from paper_1507_03703_gb300.learned import LearnedProposal, effective_samples
-    target = N_STATES_BC + N_STATES_CD - 1
     lig = sys_.ligand
     base = S.place_ligand(lig, sys_.receptor, sys_.site, 128, seed=seed, n_tries=8).astype(np.float32)
     x = torch.from_numpy(base[np.arange(chains) % 128]).to(dev)
@@ -181,19 +181,25 @@ def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=4
             cs.append(comps.clone())
     X = torch.cat(xs)
     Cm = torch.cat(cs)
-    lp = LearnedProposal(ctx, seed=seed)
+    lp = LearnedProposal(ctx, seed=seed, n_torsions=n_torsions)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record(stream)
-    t_idx = np.arange(data_cycles - lag)
-    I = (t_idx[:, None] * chains + np.arange(chains)[None, :]).ravel()
-    losses = lp.train(X, Cm, target, n_iter=train_iter, batch=4096, lr=1e-3, seed=seed, pairs=(I, I + lag * chains))
+    pairs = None
+    if lag is not None:
+        t_idx = np.arange(data_cycles - lag)
+        I = (t_idx[:, None] * chains + np.arange(chains)[None, :]).ravel()
+        pairs = (I, I + lag * chains)
+    losses = lp.train(X, Cm, target, n_iter=train_iter, batch=4096, lr=1e-3, seed=seed, pairs=pairs)
     ev[1].record(stream)
     torch.cuda.synchronize()
     train_ms = ev[0].elapsed_time(ev[1])
     x0, c0 = x.clone(), comps.clone()
-    out = {"state": "alpha=1, 300 K", "chains": chains, "training_poses": int(X.shape[0]), "train_iters": train_iter,
-           "train_ms": train_ms, "loss_first": losses[0], "loss_last": losses[-1], "moves_per_cycle": n_moves,
-           "training_pairs": "same chain, %d cycles apart" % lag}
+    st_tab = np.concatenate([[(l.T[k], l.alpha[k]) for k in range(l.K)] for l in sys_.legs])
+    out = {"state": "index %d: T %.0f K, alpha %s" % (target, st_tab[target][0], st_tab[target][1]),
+           "chains": chains, "training_poses": int(X.shape[0]), "train_iters": train_iter, "train_ms": train_ms,
+           "loss_first": losses[0], "loss_last": losses[-1], "moves_per_cycle": n_moves,
+           "moved_torsions": lp.T,
+           "training_pairs": "random pairs" if lag is None else "same chain, %d cycles apart" % lag}
     for mode in ("plain", "learned"):
         x.copy_(x0)
         comps.copy_(c0)
@@ -423,7 +429,10 @@ def main():
         extra["mbar_K"], extra["mbar_N"], extra["mbar_iters_to_1e-10"] = len(T), N, it
         del u, comps_hist
     if not args.no_learned and rank == 0:
-        extra["learned_vs_plain"] = learned_vs_plain(ctx, sys_, stream, dev)
+        # rigid-body learned moves (the paper's external-coordinate moves with a learned proposal) at
+        # the paper's own regime (alpha ~ 0.01), mid-leg, and the fully coupled end
+        extra["learned_vs_plain"] = [learned_vs_plain(ctx, sys_, stream, dev, target=k) for k in
+                                     (N_STATES_BC + 1, N_STATES_BC + 28, N_STATES_BC + N_STATES_CD - 1)]
 
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,

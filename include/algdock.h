@@ -258,12 +258,15 @@ algdock_status algdock_mlp_adam(algdock_ctx* ctx, float* params, uint16_t* wbf16
                                 int32_t step, float lr);
 
 /* n_moves learned proposals for each of n_rep replicas at its state (state_of), each accepted or
- * rejected as above in FP64.  x and comps (the components of x) are updated in place; accepted
- * [n_rep] int32 (may be NULL) is added to; counters as for algdock_hmc_cycle (may be NULL). */
+ * rejected as above in FP64.  n_torsions limits the moved torsions to the first
+ * min(T, n_torsions) (negative: all T); the mixture then covers 6 + that many dimensions, and
+ * n_torsions = 0 gives rigid-body moves only (the paper's external-coordinate moves, with a learned
+ * proposal).  x and comps (the components of x) are updated in place; accepted [n_rep] int32 (may
+ * be NULL) is added to; counters as for algdock_hmc_cycle (may be NULL). */
 algdock_status algdock_propose_learned(algdock_ctx* ctx, const float* params, const uint16_t* wbf16, int64_t n_rep,
                                        const int32_t* state_of, float* x, double* comps, int32_t n_moves,
-                                       uint64_t seed, uint64_t cycle, int64_t rep_offset, int32_t* accepted,
-                                       int64_t* counters);
+                                       int32_t n_torsions, uint64_t seed, uint64_t cycle, int64_t rep_offset,
+                                       int32_t* accepted, int64_t* counters);
 
 /* MBAR without any device allocation.  The paper has no counterpart: this is a service of this
  * library for callers that cannot call cudaMalloc - for example a host framework whose caching

@@ -386,8 +386,8 @@ def _learned_sigs(L):
     L.oracle_mixture_logq.argtypes = [_d, C.c_int, _d, C.c_void_p]
     L.oracle_mixture_logq.restype = C.c_double
     L.oracle_mixture_sample.argtypes = [_d, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, _d]
-    L.oracle_learned_mh.argtypes = ([C.c_void_p] + [_d] * 8 + [C.c_int64, _i, C.c_int64, _d, _d, C.c_int, C.c_uint64,
-                                    C.c_uint64, _i, C.c_void_p])
+    L.oracle_learned_mh.argtypes = ([C.c_void_p] + [_d] * 8 + [C.c_int64, _i, C.c_int64, _d, _d, C.c_int, C.c_int,
+                                    C.c_uint64, C.c_uint64, _i, C.c_void_p])
     L._learned = True
 
 
@@ -467,8 +467,9 @@ class _LearnedMixin:
         self._L.oracle_pose_delta(self.h, _f64(x).ravel(), _f64(y).ravel(), d)
         return d[:6 + self.learned_ntorsions()]
 
-    def learned_mh(self, params, x, comps, state_of, n_moves, seed, cycle, rep_offset=0):
-        """n_moves learned proposals per replica.  Returns (x, comps, accepts [R], last log-ratio [R])."""
+    def learned_mh(self, params, x, comps, state_of, n_moves, seed, cycle, rep_offset=0, n_torsions=-1):
+        """n_moves learned proposals per replica (moving the first n_torsions torsions; negative: all).
+        Returns (x, comps, accepts [R], last log-ratio [R])."""
         _learned_sigs(self._L)
         x = np.array(x, dtype=np.float64, order="C").reshape(-1, self.na, 3)
         comps = np.array(comps, dtype=np.float64, order="C").reshape(-1, 4)
@@ -476,7 +477,7 @@ class _LearnedMixin:
         acc = np.zeros(R, dtype=np.int32)
         lr = np.zeros(R)
         self._L.oracle_learned_mh(self.h, *_p(params), R, _i32(state_of), int(rep_offset), x, comps, int(n_moves),
-                                  int(seed), int(cycle), acc, _ptr(lr))
+                                  int(n_torsions), int(seed), int(cycle), acc, _ptr(lr))
         return x, comps, acc, lr
 
 

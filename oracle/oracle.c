@@ -1308,10 +1308,15 @@ void oracle_mixture_sample(const double* o, int D, uint64_t seed, uint32_t rep, 
  * logratio [R] (may be NULL) receives the last move's log acceptance ratio. */
 void oracle_learned_mh(const oracle_system* s, const double* W1, const double* b1, const double* W2, const double* b2,
                        const double* W3, const double* b3, const double* W4, const double* b4, int64_t n_rep,
-                       const int* state_of, int64_t rep_offset, double* x, double* comps, int n_moves, uint64_t seed,
-                       uint64_t cycle, int* acc, double* logratio) {
-  int na = s->na, T = oracle_learned_ntorsions(s), D = 6 + T;
+                       const int* state_of, int64_t rep_offset, double* x, double* comps, int n_moves,
+                       int n_torsions, uint64_t seed, uint64_t cycle, int* acc, double* logratio) {
+  /* n_torsions limits the moved torsions to the first min(T, n_torsions) (negative: all); the
+   * other increments are zero and the mixture uses 6 + that many dimensions. */
+  int na = s->na, T = oracle_learned_ntorsions(s);
+  if (n_torsions >= 0 && n_torsions < T) T = n_torsions;
+  int D = 6 + T;
   double f[O_NFEAT], o[O_NOUT], dl[O_DMAX], ndl[O_DMAX], c1[4];
+  for (int d = 0; d < O_DMAX; ++d) dl[d] = ndl[d] = 0.0;
   double* y = (double*)malloc(sizeof(double) * 3 * (size_t)na);
   for (int64_t r = 0; r < n_rep; ++r) {
     int k = state_of[r];

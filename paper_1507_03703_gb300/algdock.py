@@ -127,7 +127,7 @@ def load_library(path: str = LIB_PATH):
         "algdock_mlp_forward": ([vp, vp, vp, i64, vp, vp], C.c_int),
         "algdock_mlp_grad": ([vp, vp, vp, i64, vp, vp, i32, vp, vp], C.c_int),
         "algdock_mlp_adam": ([vp, vp, vp, vp, vp, vp, i32, C.c_float], C.c_int),
-        "algdock_propose_learned": ([vp, vp, vp, i64, vp, vp, vp, i32, u64, u64, i64, vp, vp], C.c_int),
+        "algdock_propose_learned": ([vp, vp, vp, i64, vp, vp, vp, i32, i32, u64, u64, i64, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -380,12 +380,12 @@ class Context:
                                              float(lr)))
 
     def propose_learned(self, params, wbf16, state_of, x, comps, n_moves, seed=0, cycle=0, rep_offset=0,
-                        accepted=None, counters=None):
+                        accepted=None, counters=None, n_torsions=-1):
         import torch
         self._check(self._L.algdock_propose_learned(
             self.h, _dev(params, torch.float32, "params"), _dev(wbf16, torch.int16, "wbf16"), int(state_of.numel()),
             _dev(state_of, torch.int32, "state_of"), _dev(x, torch.float32, "x"), _dev(comps, torch.float64, "comps"),
-            int(n_moves), int(seed), int(cycle), int(rep_offset), _dev(accepted, torch.int32, "accepted"),
+            int(n_moves), int(n_torsions), int(seed), int(cycle), int(rep_offset), _dev(accepted, torch.int32, "accepted"),
             _dev(counters, torch.int64, "counters")))
 
     def mbar_noalloc(self, u_kn, N_k, tol=1e-10, max_iter=10000, precision_mode=0):

@@ -644,8 +644,8 @@ algdock_status algdock_mlp_adam(algdock_ctx* c, float* params, uint16_t* wbf16, 
 
 algdock_status algdock_propose_learned(algdock_ctx* c, const float* params, const uint16_t* wbf16, int64_t n_rep,
                                        const int32_t* state_of, float* x, double* comps, int32_t n_moves,
-                                       uint64_t seed, uint64_t cycle, int64_t rep_offset, int32_t* accepted,
-                                       int64_t* counters) {
+                                       int32_t n_torsions, uint64_t seed, uint64_t cycle, int64_t rep_offset,
+                                       int32_t* accepted, int64_t* counters) {
   ALGDOCK_TRY(c)
   if (!c->has_grid || !c->has_ligand || c->K == 0)
     return fail(c, ALGDOCK_E_STATE, "propose_learned: load grids, ligand and states first");
@@ -658,8 +658,9 @@ algdock_status algdock_propose_learned(algdock_ctx* c, const float* params, cons
   Device g(c->device);
   algdock_status st = learn_scratch(c, learned_propose_scratch(n_rep, c->lig.na), "propose_learned");
   if (st != ALGDOCK_OK) return st;
-  cudaError_t e = learned_propose(c->stream, *c, params, wbf16, n_rep, state_of, x, comps, n_moves, seed, cycle,
-                                  rep_offset, accepted, counters, c->d_learn);
+  const int t_eff = (n_torsions < 0 || n_torsions > c->ltopo.T) ? c->ltopo.T : n_torsions;
+  cudaError_t e = learned_propose(c->stream, *c, params, wbf16, n_rep, state_of, x, comps, n_moves, t_eff, seed,
+                                  cycle, rep_offset, accepted, counters, c->d_learn);
   if (e != cudaSuccess) return cuda_fail(c, e, "propose_learned");
   return ALGDOCK_OK;
   ALGDOCK_CATCH(c)

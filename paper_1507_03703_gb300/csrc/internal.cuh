@@ -162,8 +162,8 @@ cudaError_t learned_adam(cudaStream_t s, float* params, uint16_t* wbf16, const f
 size_t learned_propose_scratch(int64_t n_rep, int na);
 cudaError_t learned_propose(cudaStream_t s, const algdock_ctx& c, const float* params, const uint16_t* wbf16,
                             int64_t n_rep, const int32_t* state_of, float* x, double* comps, int n_moves,
-                            uint64_t seed, uint64_t cycle, int64_t rep_offset, int32_t* accepted, int64_t* counters,
-                            void* scratch);
+                            int n_torsions, uint64_t seed, uint64_t cycle, int64_t rep_offset, int32_t* accepted,
+                            int64_t* counters, void* scratch);
 cudaError_t launch_exchange(cudaStream_t s, const algdock_ctx& c, int n_ladders, int K, int state_offset,
                             const double* comps, int32_t* config_of, int32_t* state_of, int n_sweeps, int max_sep,
                             uint64_t seed, uint64_t cycle, int64_t ladder_offset, int64_t* attempts,

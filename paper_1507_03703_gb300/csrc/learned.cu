@@ -48,6 +48,39 @@ constexpr int GT = 64;   // block tile in M and N
 constexpr int GK = 32;   // K step
 constexpr int GP = 40;   // padded row length of the shared tiles (bf16 elements)
 
+// Eight consecutive elements (from a 16-byte aligned address) as BF16 pairs.
+__device__ inline uint4 load8(const bf16* p) { return *(const uint4*)p; }
+__device__ inline uint4 load8(const float* p) {
+  const float4 a = *(const float4*)p, b = *(const float4*)(p + 4);
+  __nv_bfloat162 h0 = __floats2bfloat162_rn(a.x, a.y), h1 = __floats2bfloat162_rn(a.z, a.w);
+  __nv_bfloat162 h2 = __floats2bfloat162_rn(b.x, b.y), h3 = __floats2bfloat162_rn(b.z, b.w);
+  return make_uint4(*(uint32_t*)&h0, *(uint32_t*)&h1, *(uint32_t*)&h2, *(uint32_t*)&h3);
+}
+
+// Rows r0 .. r0+63, columns k0 .. k0+31 of a row-major matrix into a shared tile, 8 elements per
+// 16-byte load where the row stride allows it, element by element at the edges.
+template <typename T>
+__device__ inline void load_rows(bf16 (&S)[GT][GP], const T* __restrict__ X, int ld, int r0, int R, int k0, int K,
+                                 int tid) {
+  const bool vec = (ld % 8) == 0 && (((uintptr_t)X) & 15) == 0;
+  for (int e = tid; e < GT * (GK / 8); e += 128) {
+    const int rr = e / (GK / 8), kk = (e % (GK / 8)) * 8;
+    const int gr = r0 + rr, gk = k0 + kk;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (gr < R) {
+      if (vec && gk + 8 <= K) {
+        v = load8(X + (size_t)gr * ld + gk);
+      } else {
+        __nv_bfloat16 h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16(gk + j < K ? ld_f(X + (size_t)gr * ld + gk + j) : 0.f);
+        v = *(uint4*)h;
+      }
+    }
+    *(uint4*)&S[rr][kk] = v;
+  }
+}
+
 template <typename TA, bool A_T, typename TB, bool B_T, int EPI>
 __global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const TA* __restrict__ A, int lda,
                                                    const TB* __restrict__ B, int ldb, void* C, int ldc,
@@ -67,19 +100,25 @@ __global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const TA
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
   for (int k0 = 0; k0 < K; k0 += GK) {
-    for (int e = tid; e < GT * GK; e += 128) {
-      int mm, kk;
-      if (A_T) { kk = e / GT; mm = e % GT; } else { mm = e / GK; kk = e % GK; }
-      const int gm = m0 + mm, gk = k0 + kk;
-      float v = 0.f;
-      if (gm < M && gk < K) v = ld_f(A_T ? A + (size_t)gk * lda + gm : A + (size_t)gm * lda + gk);
-      As[mm][kk] = __float2bfloat16(v);
-      int nn;
-      if (B_T) { kk = e / GT; nn = e % GT; } else { nn = e / GK; kk = e % GK; }
-      const int gn = n0 + nn, gk2 = k0 + kk;
-      float w = 0.f;
-      if (gn < N && gk2 < K) w = ld_f(B_T ? B + (size_t)gk2 * ldb + gn : B + (size_t)gn * ldb + gk2);
-      Bs[nn][kk] = __float2bfloat16(w);
+    if (A_T) {
+      for (int e = tid; e < GT * GK; e += 128) {
+        const int kk = e / GT, mm = e % GT;
+        const int gm = m0 + mm, gk = k0 + kk;
+        const float v = (gm < M && gk < K) ? ld_f(A + (size_t)gk * lda + gm) : 0.f;
+        As[mm][kk] = __float2bfloat16(v);
+      }
+    } else {
+      load_rows(As, A, lda, m0, M, k0, K, tid);
+    }
+    if (B_T) {
+      for (int e = tid; e < GT * GK; e += 128) {
+        const int kk = e / GT, nn = e % GT;
+        const int gn = n0 + nn, gk = k0 + kk;
+        const float w = (gn < N && gk < K) ? ld_f(B + (size_t)gk * ldb + gn) : 0.f;
+        Bs[nn][kk] = __float2bfloat16(w);
+      }
+    } else {
+      load_rows(Bs, B, ldb, n0, N, k0, K, tid);
     }
     __syncthreads();
 #pragma unroll
@@ -462,6 +501,7 @@ struct MoveArgs {
   uint64_t seed;
   uint32_t ctr;
   int64_t rep_offset;
+  int t_eff;         // moved torsions (<= topo.T); the mixture uses 6 + t_eff dimensions
 };
 
 // Draw d ~ q(. | x), y = Apply(x, d), log q(d | x).  One warp per replica.
@@ -473,7 +513,7 @@ __global__ void sample_apply_kernel(const MoveArgs A, const float* __restrict__ 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * 4 + warp;
   if (r >= A.n_rep) return;
-  const int na = A.P.LL.na, T = A.P.topo.T, D = 6 + T;
+  const int na = A.P.LL.na, T = A.t_eff, D = 6 + T;
   const float* o = A.out + r * NOUT;
   const uint32_t rid = (uint32_t)(A.rep_offset + r);
   // component: cumulative softmax in FP64 against a 53-bit uniform
@@ -590,7 +630,7 @@ __global__ void accept_kernel(const MoveArgs A, const float* __restrict__ y, con
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * 4 + warp;
   if (r >= A.n_rep) return;
-  const int na = A.P.LL.na, D = 6 + A.P.topo.T;
+  const int na = A.P.LL.na, D = 6 + A.t_eff;
   const int k = A.state_of[r];
   if ((unsigned)k >= (unsigned)A.n_states) return;
   if (lane < DMAX) s_dl[warp][lane] = -delta[r * DMAX + lane];
@@ -803,8 +843,9 @@ size_t learned_propose_scratch(int64_t R, int na) {
 }
 
 cudaError_t learned_propose(cudaStream_t s, const algdock_ctx& c, const float* params, const uint16_t* wbf16,
-                            int64_t R, const int32_t* state_of, float* x, double* comps, int n_moves, uint64_t seed,
-                            uint64_t cycle, int64_t rep_offset, int32_t* accepted, int64_t* counters, void* scratch) {
+                            int64_t R, const int32_t* state_of, float* x, double* comps, int n_moves, int t_eff,
+                            uint64_t seed, uint64_t cycle, int64_t rep_offset, int32_t* accepted, int64_t* counters,
+                            void* scratch) {
   if (R == 0 || n_moves == 0) return cudaSuccess;
   const int na = c.lig.na;
   char* p = (char*)scratch;
@@ -826,7 +867,7 @@ cudaError_t learned_propose(cudaStream_t s, const algdock_ctx& c, const float* p
   cudaError_t e = cudaSuccess;
   for (int mv = 0; mv < n_moves && e == cudaSuccess; ++mv) {
     MoveArgs A{pose_args(c), c.d_states, c.K, R, state_of, out, seed, (uint32_t)(cycle * (uint64_t)n_moves + mv),
-               rep_offset};
+               rep_offset, t_eff};
     e = learned_features(s, c, R, state_of, x, comps, feat);
     if (e == cudaSuccess) e = learned_forward(s, params, wbf16, R, feat, out, fwd);
     if (e != cudaSuccess) break;

@@ -18,7 +18,8 @@ from .algdock import MLP_DMAX, MLP_NFEAT, MLP_NPARAMS, pack_mlp
 class LearnedProposal:
     """Device-resident network parameters (FP32 master + BF16 copy) and Adam moments."""
 
-    def __init__(self, ctx, seed: int = 0, device="cuda"):
+    def __init__(self, ctx, seed: int = 0, device="cuda", n_torsions: int = -1):
+        """n_torsions: moved torsions (negative: all the ligand's, 0: rigid-body moves only)."""
         self.ctx = ctx
         flat, w = pack_mlp(synthetic.mlp_init(seed))
         dev = torch.device(device)
@@ -29,7 +30,8 @@ class LearnedProposal:
         self.grad = torch.zeros_like(self.m)
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.step = 0
-        self.T = ctx.learned_ntorsions()
+        T = ctx.learned_ntorsions()
+        self.T = T if n_torsions < 0 else min(T, n_torsions)
 
     def train(self, x, comps, state: int, n_iter: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
               pairs=None):
@@ -66,7 +68,7 @@ class LearnedProposal:
 
     def propose(self, state_of, x, comps, n_moves, seed, cycle, accepted=None, counters=None, rep_offset=0):
         self.ctx.propose_learned(self.params, self.wbf16, state_of, x, comps, n_moves, seed=seed, cycle=cycle,
-                                 rep_offset=rep_offset, accepted=accepted, counters=counters)
+                                 rep_offset=rep_offset, accepted=accepted, counters=counters, n_torsions=self.T)
 
 
 def statistical_inefficiency(a):
