@@ -38,6 +38,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-mbar", action="store_true")
     p.add_argument("--no-learned", action="store_true")
+    p.add_argument("--learned-only", action="store_true",
+                   help="set up the workload and run only the learned-vs-plain comparison (for profiling)")
     return p.parse_args()
 
 
@@ -223,7 +225,7 @@ def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=4
     return out
 
 
-def oracle_cpu_baseline(sys_, n_rep=4096, n_threads=0):
+def oracle_cpu_baseline(sys_, n_rep=65536, n_threads=0):
     """The FP64 oracle as it stands on this host's cores: one HMC trial of 50 VV steps for a
     bounded sample of replicas spread over all states (about 10-30 s on a 16-core host)."""
     import oracle
@@ -340,6 +342,10 @@ def main():
         if ev is not None:
             ev[3].record(stream)
 
+    if args.learned_only:
+        r = learned_vs_plain(ctx, sys_, stream, dev, target=N_STATES_BC + 28, cmp_cycles=20, train_iter=20)
+        print(json.dumps({"learned_vs_plain": r}))
+        return
     launches_per_step = 1 + len(legs) + 2 * len(legs)  # hmc, exchange per leg, evaluate + u_kn per leg
     for w in range(args.warmup):
         step(w)
