@@ -292,6 +292,7 @@ def main():
     B.build()
     from paper_1507_03703_gb300 import synthetic as S
     from paper_1507_03703_gb300.algdock import Context
+    from paper_1507_03703_gb300.ranks import max_over_ranks, shard_per_rank
     from paper_1507_03703_gb300.sampler import Leg, ReplicaExchange
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -319,9 +320,12 @@ def main():
     del raw
     legs = [Leg(N_STATES_BC, 0), Leg(N_STATES_CD, N_STATES_BC)]
     R = N_CHAINS * (N_STATES_BC + N_STATES_CD)
+    # weak scaling: N_CHAINS chains per rank, numbered globally so that ranks draw disjoint streams
+    sh = shard_per_rank(N_CHAINS, world, rank)
     base = S.place_ligand(lig, sys_.receptor, sys_.site, 128, seed=100 + rank, n_tries=8).astype(np.float32)
     x0 = base[np.arange(R) % base.shape[0]]
-    run = ReplicaExchange(ctx, legs, N_CHAINS, x0, seed=1000 + rank)
+    run = ReplicaExchange(ctx, legs, N_CHAINS, x0, seed=1000, rep_offset=sh.rep_offset(N_STATES_BC + N_STATES_CD),
+                          ladder_offset=sh.ladder_offset(len(legs)))
     snap = torch.empty((R, 4), dtype=torch.float64, device=dev)
     u_leg = [torch.empty((l.K, N_CHAINS * l.K), dtype=torch.float64, device=dev) for l in legs]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -370,10 +374,7 @@ def main():
     ukn_ms = [e[2].elapsed_time(e[3]) for e in evs]
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
     ms_per_step = sum(step_ms) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_per_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step = float(t.item())
+    ms_per_step = max_over_ranks(ms_per_step, device=dev)
     evals_per_step = world * R * lig.n_atoms * N_VV
     value = evals_per_step / (ms_per_step * 1e-3)
 
@@ -406,7 +407,7 @@ def main():
         h_c.copy_(run.comps, non_blocking=True)
     ee.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = es.elapsed_time(ee) / e2e_steps
+    e2e_ms = max_over_ranks(es.elapsed_time(ee) / e2e_steps, device=dev)
     e2e = {"value": world * R * lig.n_atoms * N_VV / (e2e_ms * 1e-3), "unit": "evals/s",
            "h2d_bytes_per_step": int(h_x.numel() * 4), "d2h_bytes_per_step": int(h_out.numel() * 4 + h_c.numel() * 8)}
 

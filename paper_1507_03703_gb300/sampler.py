@@ -24,9 +24,12 @@ class ReplicaExchange:
     """All legs of one ligand: HMC for every slot in one launch, then exchange per leg."""
 
     def __init__(self, ctx: Context, legs, n_chains: int, x0, seed: int, n_sweeps: int = 25, max_sep: int = 5,
-                 device="cuda"):
+                 device="cuda", rep_offset: int = 0, ladder_offset: int = 0):
+        """rep_offset / ladder_offset: global index of this run's first replica slot and first
+        ladder in the Philox counters (a rank's share of a sharded run; see ranks.Shard)."""
         self.ctx, self.legs, self.C = ctx, list(legs), int(n_chains)
         self.seed, self.n_sweeps, self.max_sep = int(seed), int(n_sweeps), int(max_sep)
+        self.rep_offset, self.ladder_offset = int(rep_offset), int(ladder_offset)
         self.R = self.C * sum(l.K for l in self.legs)
         x0 = np.asarray(x0, dtype=np.float32)
         if x0.shape[0] != self.R:
@@ -59,14 +62,15 @@ class ReplicaExchange:
 
     def hmc(self, cycle: int, n_steps: int):
         self.ctx.hmc_cycle(self.state_of, self.x, self.comps, self.dH, self.acc, n_steps=n_steps, seed=self.seed,
-                           cycle=cycle, rep_offset=0, counters=self.counters)
+                           cycle=cycle, rep_offset=self.rep_offset, counters=self.counters)
 
     def exchange(self, cycle: int):
         for li, leg in enumerate(self.legs):
             sl = self.leg_slice(li)
             self.ctx.exchange(leg.K, leg.state_offset, self.comps[sl], self.config_of[li], self.state_of[sl],
                               n_sweeps=self.n_sweeps, max_sep=self.max_sep, seed=self.seed, cycle=cycle,
-                              ladder_offset=li * self.C, attempts=self.attempts[li], accepts=self.accepts[li])
+                              ladder_offset=self.ladder_offset + li * self.C, attempts=self.attempts[li],
+                              accepts=self.accepts[li])
 
     def cycle(self, cycle: int, n_steps: int, record: bool = False):
         self.hmc(cycle, n_steps)
