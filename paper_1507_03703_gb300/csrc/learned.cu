@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <atomic>
 #include <vector>
 
 #include "internal.cuh"
@@ -81,17 +82,48 @@ __device__ inline void load_rows(bf16 (&S)[GT][GP], const T* __restrict__ X, int
   }
 }
 
+// Columns k0 .. k0+31 of a matrix stored transposed (X[k * ld + r]), rows r0 .. r0+63, into a
+// shared tile: 8 consecutive r per 16-byte load where the stride allows it, scattered into the
+// tile's rows.
+template <typename T>
+__device__ inline void load_cols(bf16 (&S)[GT][GP], const T* __restrict__ X, int ld, int r0, int R, int k0, int K,
+                                 int tid) {
+  const bool vec = (ld % 8) == 0 && (((uintptr_t)X) & 15) == 0;
+  for (int e = tid; e < GK * (GT / 8); e += 128) {
+    const int kk = e / (GT / 8), rr = (e % (GT / 8)) * 8;
+    const int gk = k0 + kk, gr = r0 + rr;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (gk < K) {
+      if (vec && gr + 8 <= R) {
+        v = load8(X + (size_t)gk * ld + gr);
+      } else {
+        __nv_bfloat16 h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16(gr + j < R ? ld_f(X + (size_t)gk * ld + gr + j) : 0.f);
+        v = *(uint4*)h;
+      }
+    }
+    const bf16* h = (const bf16*)&v;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) S[rr + j][kk] = h[j];
+  }
+}
+
+// Block (blockIdx.z) of a split reduction dimension: k in [z * k_len, min(K, (z + 1) * k_len)),
+// its result at C + z * c_zstride (FP32 epilogue only).
 template <typename TA, bool A_T, typename TB, bool B_T, int EPI>
 __global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const TA* __restrict__ A, int lda,
                                                    const TB* __restrict__ B, int ldb, void* C, int ldc,
                                                    const float* __restrict__ bias, const bf16* __restrict__ mask,
-                                                   int ldm) {
+                                                   int ldm, int k_len, size_t c_zstride) {
   __shared__ __align__(16) bf16 As[GT][GP];
   __shared__ __align__(16) bf16 Bs[GT][GP];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
   const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
   const int g = lane >> 2, t = lane & 3;
+  const int kb = blockIdx.z * k_len, ke = min(K, kb + k_len);
+  if (EPI == EPI_F32) C = (float*)C + blockIdx.z * c_zstride;
   float acc[2][4][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -99,27 +131,11 @@ __global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const TA
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += GK) {
-    if (A_T) {
-      for (int e = tid; e < GT * GK; e += 128) {
-        const int kk = e / GT, mm = e % GT;
-        const int gm = m0 + mm, gk = k0 + kk;
-        const float v = (gm < M && gk < K) ? ld_f(A + (size_t)gk * lda + gm) : 0.f;
-        As[mm][kk] = __float2bfloat16(v);
-      }
-    } else {
-      load_rows(As, A, lda, m0, M, k0, K, tid);
-    }
-    if (B_T) {
-      for (int e = tid; e < GT * GK; e += 128) {
-        const int kk = e / GT, nn = e % GT;
-        const int gn = n0 + nn, gk = k0 + kk;
-        const float w = (gn < N && gk < K) ? ld_f(B + (size_t)gk * ldb + gn) : 0.f;
-        Bs[nn][kk] = __float2bfloat16(w);
-      }
-    } else {
-      load_rows(Bs, B, ldb, n0, N, k0, K, tid);
-    }
+  for (int k0 = kb; k0 < ke; k0 += GK) {
+    if (A_T) load_cols(As, A, lda, m0, M, k0, ke, tid);
+    else load_rows(As, A, lda, m0, M, k0, ke, tid);
+    if (B_T) load_cols(Bs, B, ldb, n0, N, k0, ke, tid);
+    else load_rows(Bs, B, ldb, n0, N, k0, ke, tid);
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; kk += 16) {
@@ -172,24 +188,308 @@ cudaError_t gemm(cudaStream_t s, int M, int N, int K, const TA* A, int lda, cons
                  const float* bias = nullptr, const bf16* mask = nullptr, int ldm = 0) {
   if (M == 0 || N == 0) return cudaSuccess;
   dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
-  gemm_kernel<TA, A_T, TB, B_T, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, ldm);
+  gemm_kernel<TA, A_T, TB, B_T, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, ldm, K, 0);
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ small kernels
-// Column sums of G [M][N] into out[n] (bias gradients), scaled.
-template <typename T>
-__global__ void colsum_kernel(int M, int N, const T* __restrict__ G, float scale, float* out) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
+// Sum of the split partial products part[z][M*N], z in fixed order, into C.
+__global__ void splitk_reduce_kernel(int MN, int nz, const float* __restrict__ part, float* C) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= MN) return;
   float s = 0.f;
-  for (int m = 0; m < M; ++m) s += ld_f(G + (size_t)m * N + n);
-  out[n] = scale * s;
+  for (int z = 0; z < nz; ++z) s += part[(size_t)z * MN + i];
+  C[i] = s;
 }
 
-__global__ void to_bf16_kernel(int64_t n, const float* __restrict__ in, bf16* out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = __float2bfloat16(in[i]);
+constexpr int kWgradSplit = 16;  // batch slices of a weight-gradient product
+
+// Weight gradient C[M][N] = sum_k A[k][M] B[k][N] over a long batch dimension K: the batch is
+// split into up to kWgradSplit slices (one CTA column each, so the 16-24 output tiles fill the
+// GPU), the partial products land in part and are summed in slice order.
+template <typename TA, typename TB>
+cudaError_t gemm_wgrad(cudaStream_t s, int M, int N, int K, const TA* A, int lda, const TB* B, int ldb, float* C,
+                       float* part) {
+  if (M == 0 || N == 0) return cudaSuccess;
+  const int k_len = ((K + kWgradSplit - 1) / kWgradSplit + GK - 1) / GK * GK;
+  const int nz = k_len > 0 ? (K + k_len - 1) / k_len : 0;
+  if (nz == 0) {
+    cudaError_t e = cudaMemsetAsync(C, 0, sizeof(float) * (size_t)M * N, s);
+    return e;
+  }
+  dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT, nz);
+  gemm_kernel<TA, true, TB, true, EPI_F32><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, part, N, nullptr, nullptr, 0,
+                                                                k_len, (size_t)M * N);
+  splitk_reduce_kernel<<<(M * N + 255) / 256, 256, 0, s>>>(M * N, nz, part, C);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ fused forward pass
+// One CTA takes 16 rows through all four layers.  The activations stay in shared memory as BF16.
+// The weights are first packed (once per call) into 13 chunks of 64 input columns, each a
+// contiguous [rows][72] BF16 block whose rows carry the 8-element padding that keeps ldmatrix free
+// of bank conflicts; one cp.async.bulk per chunk (the TMA engine, completion counted on an
+// mbarrier) streams them from L2 through a three-stage ring, so a CTA has up to ~100 KB of weights
+// in flight from two instructions instead of thousands of 16-byte requests.  The fragments reach
+// mma.sync m16n8k16 through ldmatrix.  Eight warps split the output columns: 32 each in the hidden
+// layers, 48 in the output layer.  Rounding is that of the layer-by-layer GEMMs: BF16 inputs and
+// hidden activations, FP32 accumulation.
+constexpr int FM = 16;               // rows per CTA
+constexpr int F_MT = FM / 16;        // m16 row tiles per warp
+constexpr int FKC = 64;              // input columns per weight chunk
+constexpr int FWS = FKC + 8;         // padded row of a weight chunk (bf16): conflict-free ldmatrix
+constexpr int FHS = NHID + 8;        // padded row of a hidden activation tile
+constexpr int FXS = NFEAT + 8;       // padded row of the input tile
+constexpr int F_WARPS = 8;
+constexpr int F_STAGES = 3;
+constexpr int F_NOUT_ROWS = 368;     // output-layer rows rounded up to the 16-row ldmatrix pair
+constexpr int F_CH0 = NFEAT / FKC;   // chunks of the input layer
+constexpr int F_CHH = NHID / FKC;    // chunks of each later layer
+constexpr int F_NCHUNK = F_CH0 + 3 * F_CHH;
+constexpr int F_STAGE_ELEMS = F_NOUT_ROWS * FWS;
+constexpr size_t F_SMEM = (size_t)(F_STAGES * F_STAGE_ELEMS + 2 * FM * FHS + FM * FXS) * sizeof(bf16);
+// packed weights: chunks of the three 256-row layers, then the four chunks of the 360-row layer
+constexpr int F_CHUNK_H = NHID * FWS;                // elements of a 256-row chunk
+constexpr int F_CHUNK_O = NOUT * FWS;                // elements of a 360-row chunk
+constexpr int F_NCHUNK_H = F_CH0 + 2 * F_CHH;        // chunks of 256 rows
+constexpr int F_PACKED = F_NCHUNK_H * F_CHUNK_H + F_CHH * F_CHUNK_O;
+static_assert(NFEAT % FKC == 0 && NHID % FKC == 0, "whole chunks");
+static_assert(F_SMEM <= 227 * 1024, "shared memory of one CTA");
+static_assert((F_CHUNK_H * 2) % 16 == 0 && (F_CHUNK_O * 2) % 16 == 0 && (F_STAGE_ELEMS * 2) % 16 == 0,
+              "bulk copies move multiples of 16 bytes between 16-byte aligned addresses");
+constexpr long long kMbarSpinLimit = 1ll << 22;      // bounded waits (well over a second in all)
+
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void ldsm_x4(uint32_t (&r)[4], const bf16* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ inline void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false if the limit ran out.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < kMbarSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// One bulk copy global -> this CTA's shared memory, its bytes counted on bar.
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+struct FusedArgs {
+  const float* params;
+  const bf16* Wp;      // packed weights (F_PACKED elements, 16-byte aligned)
+  int N;
+  const float* feat;
+  float* out;
+  bf16 *h1, *h2, *h3;  // optional copies of the hidden activations [N][256] (for the backward pass)
+};
+
+__device__ inline void f_layer_dims(int layer, int& n_out, int& k_in, int& woff, int& boff) {
+  if (layer == 0) { n_out = NHID; k_in = NFEAT; woff = WOFF_1; boff = OFF_B1; }
+  else if (layer == 1) { n_out = NHID; k_in = NHID; woff = WOFF_2; boff = OFF_B2; }
+  else if (layer == 2) { n_out = NHID; k_in = NHID; woff = WOFF_3; boff = OFF_B3; }
+  else { n_out = NOUT; k_in = NHID; woff = WOFF_4; boff = OFF_B4; }
+}
+
+__host__ __device__ inline void f_chunk(int c, int& layer, int& kc) {
+  layer = c < F_CH0 ? 0 : 1 + (c - F_CH0) / F_CHH;
+  kc = c < F_CH0 ? c : (c - F_CH0) % F_CHH;
+}
+
+// First element and element count of packed chunk c.
+__host__ __device__ inline int f_chunk_off(int c) {
+  return c < F_NCHUNK_H ? c * F_CHUNK_H : F_NCHUNK_H * F_CHUNK_H + (c - F_NCHUNK_H) * F_CHUNK_O;
+}
+__host__ __device__ inline int f_chunk_len(int c) { return c < F_NCHUNK_H ? F_CHUNK_H : F_CHUNK_O; }
+
+// Packed weights from the row-major BF16 copy: chunk c, row n, column k < 64 is W_layer[n][64 kc + k];
+// columns 64..71 are zero.
+__global__ void pack_weights_kernel(const bf16* __restrict__ W, bf16* Wp) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= F_PACKED) return;
+  const int c = e < F_NCHUNK_H * F_CHUNK_H ? e / F_CHUNK_H : F_NCHUNK_H + (e - F_NCHUNK_H * F_CHUNK_H) / F_CHUNK_O;
+  const int i = e - f_chunk_off(c), row = i / FWS, col = i % FWS;
+  int layer, kc, n_out, k_in, woff, boff;
+  f_chunk(c, layer, kc);
+  f_layer_dims(layer, n_out, k_in, woff, boff);
+  Wp[e] = col < FKC ? W[woff + row * k_in + kc * FKC + col] : __float2bfloat16(0.f);
+}
+
+__global__ void __launch_bounds__(F_WARPS * 32) mlp_fused_kernel(const FusedArgs P) {
+  extern __shared__ __align__(16) unsigned char f_smem[];
+  __shared__ __align__(8) uint64_t full[F_STAGES];
+  bf16* const Wst = (bf16*)f_smem;
+  bf16* const H0 = Wst + F_STAGES * F_STAGE_ELEMS;
+  bf16* const H1 = H0 + FM * FHS;
+  bf16* const Xs = H1 + FM * FHS;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = blockIdx.x * FM;
+  if (tid == 0) {
+    for (int st = 0; st < F_STAGES; ++st) mbar_init(&full[st], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int c) {  // thread 0: chunk c into its stage
+    // the stage's earlier reads (generic proxy, ordered before this thread by the barrier) come
+    // before the bulk copy's writes (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    uint64_t* bar = &full[c % F_STAGES];
+    const uint32_t bytes = (uint32_t)(f_chunk_len(c) * sizeof(bf16));
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(Wst + (c % F_STAGES) * F_STAGE_ELEMS, P.Wp + f_chunk_off(c), bytes, bar);
+  };
+  if (tid == 0)
+    for (int c = 0; c < F_STAGES - 1 && c < F_NCHUNK; ++c) issue(c);
+  int issued = min(F_STAGES - 1, F_NCHUNK);
+  // rows of every stage past the 360 output-layer weight rows: zero (their columns are dropped)
+  for (int e = tid; e < F_STAGES * (F_NOUT_ROWS - NOUT) * FWS; e += F_WARPS * 32) {
+    const int st = e / ((F_NOUT_ROWS - NOUT) * FWS), i = e % ((F_NOUT_ROWS - NOUT) * FWS);
+    Wst[st * F_STAGE_ELEMS + NOUT * FWS + i] = __float2bfloat16(0.f);
+  }
+  for (int e = tid; e < FM * NFEAT / 4; e += F_WARPS * 32) {
+    const int row = e / (NFEAT / 4), col = (e % (NFEAT / 4)) * 4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r0 + row < P.N) v = *(const float4*)(P.feat + (size_t)(r0 + row) * NFEAT + col);
+    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+    *(__nv_bfloat162*)(Xs + row * FXS + col) = lo;
+    *(__nv_bfloat162*)(Xs + row * FXS + col + 2) = hi;
+  }
+  float acc[F_MT][6][4];
+#pragma unroll
+  for (int mi = 0; mi < F_MT; ++mi)
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[mi][j][e] = 0.f;
+  for (int c = 0; c < F_NCHUNK; ++c) {
+    // chunk c has landed; after the barrier every warp is done with chunk c - 1, whose stage takes
+    // chunk c + F_STAGES - 1
+    const bool ok = mbar_wait(&full[c % F_STAGES], (uint32_t)((c / F_STAGES) & 1));
+    if (__syncthreads_or(!ok)) {
+      // a copy did not arrive in time: wait (bounded) for the copies still in flight, then mark
+      // this CTA's rows as failed (NaN outputs) and leave
+      if (tid == 0)
+        for (int cc = c; cc < issued; ++cc) mbar_wait(&full[cc % F_STAGES], (uint32_t)((cc / F_STAGES) & 1));
+      __syncthreads();
+      for (int e = tid; e < FM * NOUT; e += F_WARPS * 32)
+        if (r0 + e / NOUT < P.N) P.out[(size_t)r0 * NOUT + e] = __int_as_float(0x7fc00000);
+      return;
+    }
+    if (c + F_STAGES - 1 < F_NCHUNK) {
+      if (tid == 0) issue(c + F_STAGES - 1);
+      issued = c + F_STAGES;
+    }
+    int layer, kc, n_out, k_in, woff, boff;
+    f_chunk(c, layer, kc);
+    f_layer_dims(layer, n_out, k_in, woff, boff);
+    const bf16* Ain = layer == 0 ? Xs : (((layer - 1) & 1) ? H1 : H0);
+    const int as = layer == 0 ? FXS : FHS;
+    const bf16* Wc = Wst + (c % F_STAGES) * F_STAGE_ELEMS;
+    const int ntile = layer == 3 ? 6 : 4;            // n8 tiles per warp
+    const int nbase = warp * ntile * 8;
+    // pairs of n8 tiles this warp multiplies (warp-uniform): 2 in the hidden layers, up to 3 in
+    // the output layer (the last warp's third pair would start past the 360 outputs)
+    const int npair = min(ntile / 2, (n_out - nbase + 15) / 16);
+#pragma unroll
+    for (int kk = 0; kk < FKC; kk += 16) {
+      uint32_t a[F_MT][4];
+#pragma unroll
+      for (int mi = 0; mi < F_MT; ++mi) ldsm_x4(a[mi], Ain + (16 * mi + (lane & 15)) * as + kc * FKC + kk + (lane >> 4) * 8);
+#pragma unroll
+      for (int jp = 0; jp < 3; ++jp) {
+        if (jp < npair) {
+          uint32_t b[4];
+          ldsm_x4(b, Wc + (nbase + 16 * jp + (lane & 7) + ((lane >> 4) << 3)) * FWS + kk + ((lane >> 3) & 1) * 8);
+          const uint32_t b0[2] = {b[0], b[1]}, b1[2] = {b[2], b[3]};
+#pragma unroll
+          for (int mi = 0; mi < F_MT; ++mi) {
+            mma_bf16(acc[mi][2 * jp], a[mi], b0);
+            mma_bf16(acc[mi][2 * jp + 1], a[mi], b1);
+          }
+        }
+      }
+    }
+    const bool last = kc == (layer == 0 ? F_CH0 : F_CHH) - 1;
+    if (last) {
+#pragma unroll
+      for (int mi = 0; mi < F_MT; ++mi)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (j < ntile) {
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int row = 16 * mi + g + 8 * hh, col = nbase + 8 * j + 2 * t;
+            float v0 = acc[mi][j][2 * hh], v1 = acc[mi][j][2 * hh + 1];
+            acc[mi][j][2 * hh] = acc[mi][j][2 * hh + 1] = 0.f;
+            if (col >= n_out) continue;
+            v0 += P.params[boff + col];
+            v1 += P.params[boff + col + 1];
+            if (layer < 3) {
+              const __nv_bfloat162 hv = __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+              *(__nv_bfloat162*)(((layer & 1) ? H1 : H0) + row * FHS + col) = hv;
+              bf16* hk = layer == 0 ? P.h1 : (layer == 1 ? P.h2 : P.h3);
+              if (hk && r0 + row < P.N) *(__nv_bfloat162*)(hk + (size_t)(r0 + row) * NHID + col) = hv;
+            } else if (r0 + row < P.N) {
+              *(float2*)(P.out + (size_t)(r0 + row) * NOUT + col) = make_float2(v0, v1);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ small kernels
+// Column sums of G [M][N] (bias gradients) in two passes: block (x, y) sums 32 columns over the
+// y-th of kColsumSlices row slices (8 warps, then the warps' sums in fixed order) into
+// part[y][n]; the split reduction then adds the slices in order.
+constexpr int kColsumSlices = 16;
+
+template <typename T>
+__global__ void colsum_kernel(int M, int N, const T* __restrict__ G, float* part) {
+  __shared__ float ws[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n = blockIdx.x * 32 + lane;
+  const int len = (M + kColsumSlices - 1) / kColsumSlices;
+  const int mb = blockIdx.y * len, me = min(M, mb + len);
+  float s = 0.f;
+  if (n < N)
+    for (int m = mb + warp; m < me; m += 8) s += ld_f(G + (size_t)m * N + n);
+  ws[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && n < N) {
+    float t = 0.f;
+    for (int w = 0; w < 8; ++w) t += ws[w][lane];
+    part[(size_t)blockIdx.y * N + n] = t;
+  }
+}
+
+template <typename T>
+cudaError_t colsum(cudaStream_t s, int M, int N, const T* G, float* out, float* part) {
+  colsum_kernel<T><<<dim3((N + 31) / 32, kColsumSlices), 256, 0, s>>>(M, N, G, part);
+  splitk_reduce_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, kColsumSlices, part, out);
+  return cudaGetLastError();
 }
 
 // Weight entries (not biases) of the parameter vector, in the order of the BF16 copy.
@@ -216,65 +516,93 @@ __global__ void adam_kernel(float* params, bf16* wbf16, const float* __restrict_
   if (wi >= 0) wbf16[wi] = __float2bfloat16(w);
 }
 
-// log sigma of a mixture output
-__device__ inline double log_sigma(float raw) { return -2.0 + 4.0 * tanh((double)raw / 4.0); }
+// ------------------------------------------------------------------ the mixture density, one warp per row
+// The mixture is evaluated in FP32 across the warp: lane = c + 8 j takes component c = lane & 7 and
+// the dimensions j, j + 4, j + 8, ...; the four lanes of a component add their partial sums and a
+// log-sum-exp over the eight components follows.  (FP64 transcendentals run at a small fraction of
+// the FP32 rate on this part; the Metropolis decision itself stays FP64.)
+__device__ inline float log_sigma_f(float raw) { return -2.f + 4.f * tanhf(0.25f * raw); }
 
-// Per component c: log w_c + sum_d log N(delta_d; mu, sigma) over D dims (FP64).
-__device__ inline double component_logp(const float* o, int D, const float* dl, int c, double logz) {
-  double s = (double)o[c] - logz;
-  for (int d = 0; d < D; ++d) {
-    const double mu = o[NCOMP + c * DMAX + d];
-    const double ls = log_sigma(o[NCOMP + NCOMP * DMAX + c * DMAX + d]);
-    const double z = ((double)dl[d] - mu) * exp(-ls);
-    s += -0.5 * z * z - ls - 0.9189385332046728;  // 0.5 ln(2 pi)
+struct MixtureTerms {
+  float lq;   // log q(dl | o)
+  float lp;   // log w_c + log N(dl; mu_c, sigma_c) of this lane's component
+  float lw;   // log w_c (log-softmax of the logits)
+};
+
+__device__ inline float warp8_max(float v) {
+  v = fmaxf(v, __shfl_xor_sync(kFull, v, 1));
+  v = fmaxf(v, __shfl_xor_sync(kFull, v, 2));
+  return fmaxf(v, __shfl_xor_sync(kFull, v, 4));
+}
+
+__device__ inline float warp8_sum(float v) {
+  v += __shfl_xor_sync(kFull, v, 1);
+  v += __shfl_xor_sync(kFull, v, 2);
+  return v + __shfl_xor_sync(kFull, v, 4);
+}
+
+__device__ inline MixtureTerms mixture_terms(const float* o, int D, const float* dl, int lane) {
+  const int c = lane & 7;
+  const float lg = o[c];
+  const float m = warp8_max(lg);
+  const float lz = m + logf(warp8_sum(expf(lg - m)));
+  float s = 0.f;
+  for (int d = lane >> 3; d < D; d += 4) {
+    const float mu = o[NCOMP + c * DMAX + d];
+    const float ls = log_sigma_f(o[NCOMP + NCOMP * DMAX + c * DMAX + d]);
+    const float z = (dl[d] - mu) * expf(-ls);
+    s += -0.5f * z * z - ls;
   }
-  return s;
+  s += __shfl_xor_sync(kFull, s, 8);
+  s += __shfl_xor_sync(kFull, s, 16);
+  MixtureTerms t;
+  t.lw = lg - lz;
+  t.lp = s + t.lw - 0.9189385332f * (float)D;  // 0.5 ln(2 pi) per dimension
+  const float mx = warp8_max(t.lp);
+  t.lq = mx + logf(warp8_sum(expf(t.lp - mx)));
+  return t;
 }
 
-__device__ inline double logits_lse(const float* o) {
-  double m = -INFINITY;
-  for (int c = 0; c < NCOMP; ++c) m = fmax(m, (double)o[c]);
-  double z = 0.0;
-  for (int c = 0; c < NCOMP; ++c) z += exp((double)o[c] - m);
-  return m + log(z);
-}
-
-// Mean negative log-density of the targets: per row, the gradient -(1/N) dlogq/do (FP32) and
-// the row's -log q.
+// Mean negative log-density of the targets, one warp per row: the gradient -(1/N) dlogq/do (FP32
+// and its BF16 copy for the backward GEMMs) and the row's -log q.
 __global__ void nll_kernel(int64_t N, int D, const float* __restrict__ out, const float* __restrict__ delta,
-                           float* dout, float* loss_rows) {
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                           float* dout, bf16* dout16, float* loss_rows) {
+  __shared__ float s_dl[4][DMAX];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n = (int64_t)blockIdx.x * 4 + warp;
   if (n >= N) return;
   const float* o = out + n * NOUT;
-  const float* dl = delta + n * DMAX;
+  if (lane < DMAX) s_dl[warp][lane] = delta[n * DMAX + lane];
+  __syncwarp();
+  const float* dl = s_dl[warp];
+  const MixtureTerms t = mixture_terms(o, D, dl, lane);
+  const float scale = -1.f / (float)N;
+  const int c = lane & 7;
+  const float r = expf(t.lp - t.lq);  // responsibility of component c
   float* g = dout + n * NOUT;
-  const double logz = logits_lse(o);
-  double lp[NCOMP];
-  double m = -INFINITY;
-  for (int c = 0; c < NCOMP; ++c) {
-    lp[c] = component_logp(o, D, dl, c, logz);
-    m = fmax(m, lp[c]);
+  bf16* g16 = dout16 + n * NOUT;
+  if (lane < NCOMP) {
+    // d logq / d logit_c = r_c - softmax_c
+    const float v = scale * (r - expf(t.lw));
+    g[c] = v;
+    g16[c] = __float2bfloat16(v);
   }
-  double ss = 0.0;
-  for (int c = 0; c < NCOMP; ++c) ss += exp(lp[c] - m);
-  const double lq = m + log(ss);
-  const double scale = -1.0 / (double)N;
-  for (int i = 0; i < NOUT; ++i) g[i] = 0.f;
-  for (int c = 0; c < NCOMP; ++c) {
-    const double r = exp(lp[c] - lq);
-    // d logq / d logit_c' = r_c' - softmax_c' (summed over c below)
-    g[c] += (float)(scale * (r - exp((double)o[c] - logz)));
-    for (int d = 0; d < D; ++d) {
-      const double mu = o[NCOMP + c * DMAX + d];
-      const float raw = o[NCOMP + NCOMP * DMAX + c * DMAX + d];
-      const double th = tanh((double)raw / 4.0);
-      const double sg = exp(-2.0 + 4.0 * th);
-      const double z = ((double)dl[d] - mu) / sg;
-      g[NCOMP + c * DMAX + d] = (float)(scale * r * z / sg);
-      g[NCOMP + NCOMP * DMAX + c * DMAX + d] = (float)(scale * r * (z * z - 1.0) * (1.0 - th * th));
+  for (int d = lane >> 3; d < DMAX; d += 4) {
+    float gm = 0.f, gs = 0.f;
+    if (d < D) {
+      const float mu = o[NCOMP + c * DMAX + d];
+      const float th = tanhf(0.25f * o[NCOMP + NCOMP * DMAX + c * DMAX + d]);
+      const float inv_sg = expf(2.f - 4.f * th);
+      const float z = (dl[d] - mu) * inv_sg;
+      gm = scale * r * z * inv_sg;
+      gs = scale * r * (z * z - 1.f) * (1.f - th * th);
     }
+    g[NCOMP + c * DMAX + d] = gm;
+    g[NCOMP + NCOMP * DMAX + c * DMAX + d] = gs;
+    g16[NCOMP + c * DMAX + d] = __float2bfloat16(gm);
+    g16[NCOMP + NCOMP * DMAX + c * DMAX + d] = __float2bfloat16(gs);
   }
-  loss_rows[n] = (float)(-lq);
+  if (lane == 0) loss_rows[n] = -t.lq;
 }
 
 __global__ void sum_kernel(int64_t N, const float* __restrict__ x, float scale, float* out) {
@@ -299,38 +627,60 @@ struct PoseArgs {
 
 __device__ inline float atom_mass(const PoseArgs& P, int i) { return ((const float4*)(P.blob + P.LL.off_atom_b))[i].z; }
 
+// Pose features, one warp per replica: lanes share the centre-of-mass sums, lanes 3-4 take the two
+// reference directions, lanes 8.. one torsion each, and the row leaves through shared memory in two
+// coalesced stores.
 __global__ void features_kernel(int64_t N, const PoseArgs P, const StateDev* __restrict__ states, int n_states,
                                 const int32_t* __restrict__ state_of, const float* __restrict__ x,
                                 const double* __restrict__ comps, float* feat) {
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ float s_f[4][NFEAT];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n = (int64_t)blockIdx.x * 4 + warp;
   if (n >= N) return;
   const int na = P.LL.na;
   const float* xn = x + n * na * 3;
-  float* f = feat + n * NFEAT;
-  for (int i = 0; i < NFEAT; ++i) f[i] = 0.f;
+  float* f = s_f[warp];
+  f[lane] = 0.f;
+  f[lane + 32] = 0.f;
   float cx = 0.f, cy = 0.f, cz = 0.f;
-  for (int i = 0; i < na; ++i) {
+  for (int i = lane; i < na; i += 32) {
     const float m = atom_mass(P, i);
     cx += m * xn[3 * i];
     cy += m * xn[3 * i + 1];
     cz += m * xn[3 * i + 2];
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cx += __shfl_xor_sync(kFull, cx, o);
+    cy += __shfl_xor_sync(kFull, cy, o);
+    cz += __shfl_xor_sync(kFull, cz, o);
+  }
   const float invM = 1.f / P.LL.total_mass;
   cx *= invM;
   cy *= invM;
   cz *= invM;
-  f[0] = (cx - P.LL.site[0]) / P.LL.d0;
-  f[1] = (cy - P.LL.site[1]) / P.LL.d0;
-  f[2] = (cz - P.LL.site[2]) / P.LL.d0;
-  const int ref[2] = {0, na - 1};
-  for (int r = 0; r < 2; ++r) {
-    const float vx = xn[3 * ref[r]] - cx, vy = xn[3 * ref[r] + 1] - cy, vz = xn[3 * ref[r] + 2] - cz;
+  __syncwarp();
+  if (lane < 3) f[lane] = ((lane == 0 ? cx : (lane == 1 ? cy : cz)) - P.LL.site[lane]) / P.LL.d0;
+  if (lane == 3 || lane == 4) {
+    const int r = lane - 3, a = r ? na - 1 : 0;
+    const float vx = xn[3 * a] - cx, vy = xn[3 * a + 1] - cy, vz = xn[3 * a + 2] - cz;
     const float nn = fmaxf(sqrtf(vx * vx + vy * vy + vz * vz), 1e-6f);
     f[3 + 3 * r] = vx / nn;
     f[4 + 3 * r] = vy / nn;
     f[5 + 3 * r] = vz / nn;
   }
-  for (int q = 0; q < P.topo.T; ++q) {
+  if (lane == 5) {
+    const int k = state_of ? state_of[n] : 0;
+    if ((unsigned)k < (unsigned)n_states) {
+      const StateDev st = states[k];
+      f[41] = st.w_sg_f;
+      f[42] = st.w_g_f;
+      f[43] = (float)(300.0 * kBoltzmann / st.kT);
+    }
+  }
+  if (lane >= 24 && lane < 28) f[44 + lane - 24] = asinhf(0.1f * (float)comps[n * 4 + lane - 24]);
+  const int q = lane - 8;
+  if (q >= 0 && q < P.topo.T) {
     const int* a = P.topo.dih[q];
     float b1[3], b2[3], b3[3];
     for (int d = 0; d < 3; ++d) {
@@ -346,17 +696,12 @@ __global__ void features_kernel(int64_t N, const PoseArgs P, const StateDev* __r
     f[9 + 2 * q] = rr > 0.f ? xx / rr : 1.f;
     f[10 + 2 * q] = rr > 0.f ? yy / rr : 0.f;
   }
-  const int k = state_of ? state_of[n] : 0;
-  if ((unsigned)k < (unsigned)n_states) {
-    const StateDev st = states[k];
-    f[41] = st.w_sg_f;
-    f[42] = st.w_g_f;
-    f[43] = (float)(300.0 * kBoltzmann / st.kT);
-  }
-  for (int i = 0; i < 4; ++i) f[44 + i] = asinhf((float)(comps[n * 4 + i] / 10.0));
+  __syncwarp();
+  feat[n * NFEAT + lane] = f[lane];
+  feat[n * NFEAT + lane + 32] = f[lane + 32];
 }
 
-// The move from pose x to pose y, in FP64.
+// The move from pose x to pose y: the rigid-body part in FP64, the torsion increments in FP32.
 __global__ void pose_delta_kernel(int64_t N, const PoseArgs P, const float* __restrict__ x,
                                   const float* __restrict__ y, float* delta) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,25 +759,28 @@ __global__ void pose_delta_kernel(int64_t N, const PoseArgs P, const float* __re
     const double f = th < 1e-8 ? 0.5 : th / sv;
     for (int d = 0; d < 3; ++d) out[3 + d] = (float)(f * v[d]);
   }
+  // torsion increments in FP32 (FP64 transcendentals are slow on this part; the angles carry
+  // FP32-level error either way, the poses being FP32)
   for (int q = 0; q < P.topo.T; ++q) {
-    double tau[2];
+    float tau[2];
     for (int p = 0; p < 2; ++p) {
       const int* a = P.topo.dih[q];
-      double b1[3], b2[3], b3[3];
+      float b1[3], b2[3], b3[3];
       for (int d = 0; d < 3; ++d) {
-        b1[d] = (double)X[p][3 * a[1] + d] - X[p][3 * a[0] + d];
-        b2[d] = (double)X[p][3 * a[2] + d] - X[p][3 * a[1] + d];
-        b3[d] = (double)X[p][3 * a[3] + d] - X[p][3 * a[2] + d];
+        b1[d] = X[p][3 * a[1] + d] - X[p][3 * a[0] + d];
+        b2[d] = X[p][3 * a[2] + d] - X[p][3 * a[1] + d];
+        b3[d] = X[p][3 * a[3] + d] - X[p][3 * a[2] + d];
       }
-      const double n1[3] = {b1[1] * b2[2] - b1[2] * b2[1], b1[2] * b2[0] - b1[0] * b2[2], b1[0] * b2[1] - b1[1] * b2[0]};
-      const double n2[3] = {b2[1] * b3[2] - b2[2] * b3[1], b2[2] * b3[0] - b2[0] * b3[2], b2[0] * b3[1] - b2[1] * b3[0]};
-      tau[p] = atan2(sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]) * (b1[0] * n2[0] + b1[1] * n2[1] + b1[2] * n2[2]),
-                     n1[0] * n2[0] + n1[1] * n2[1] + n1[2] * n2[2]);
+      const float n1[3] = {b1[1] * b2[2] - b1[2] * b2[1], b1[2] * b2[0] - b1[0] * b2[2], b1[0] * b2[1] - b1[1] * b2[0]};
+      const float n2[3] = {b2[1] * b3[2] - b2[2] * b3[1], b2[2] * b3[0] - b2[0] * b3[2], b2[0] * b3[1] - b2[1] * b3[0]};
+      tau[p] = atan2f(sqrtf(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]) * (b1[0] * n2[0] + b1[1] * n2[1] + b1[2] * n2[2]),
+                      n1[0] * n2[0] + n1[1] * n2[1] + n1[2] * n2[2]);
     }
-    double d = tau[1] - tau[0];
-    while (d > M_PI) d -= 2.0 * M_PI;
-    while (d <= -M_PI) d += 2.0 * M_PI;
-    out[6 + q] = (float)d;
+    float d = tau[1] - tau[0];
+    const float pi = 3.14159265358979f;
+    if (d > pi) d -= 2.f * pi;
+    if (d <= -pi) d += 2.f * pi;
+    out[6 + q] = d;
   }
 }
 
@@ -516,28 +864,26 @@ __global__ void sample_apply_kernel(const MoveArgs A, const float* __restrict__ 
   const int na = A.P.LL.na, T = A.t_eff, D = 6 + T;
   const float* o = A.out + r * NOUT;
   const uint32_t rid = (uint32_t)(A.rep_offset + r);
-  // component: cumulative softmax in FP64 against a 53-bit uniform
+  // component: cumulative softmax in FP64 against a 53-bit uniform, the weights computed one per
+  // lane and summed in component order (every lane walks the same sum)
+  const float m8 = warp8_max(o[lane & 7]);
+  const double w = lane < NCOMP ? exp((double)o[lane] - (double)m8) : 0.0;
+  double z = 0.0;
+#pragma unroll
+  for (int c = 0; c < NCOMP; ++c) z += __shfl_sync(kFull, w, c);
+  const U4 ru = philox(A.seed, 100u, rid, A.ctr, kPurposeLearned);
+  const double u = uniform53(ru.x, ru.y) * z;
   int comp = NCOMP - 1;
-  if (lane == 0) {
-    double m = -INFINITY;
-    for (int c = 0; c < NCOMP; ++c) m = fmax(m, (double)o[c]);
-    double w[NCOMP], z = 0.0;
-    for (int c = 0; c < NCOMP; ++c) {
-      w[c] = exp((double)o[c] - m);
-      z += w[c];
-    }
-    const U4 rr = philox(A.seed, 100u, rid, A.ctr, kPurposeLearned);
-    const double u = uniform53(rr.x, rr.y) * z;
-    double cum = 0.0;
-    for (int c = 0; c < NCOMP; ++c) {
-      cum += w[c];
-      if (u < cum) {
-        comp = c;
-        break;
-      }
+  bool found = false;
+  double cum = 0.0;
+#pragma unroll
+  for (int c = 0; c < NCOMP; ++c) {
+    cum += __shfl_sync(kFull, w, c);
+    if (!found && u < cum) {
+      comp = c;
+      found = true;
     }
   }
-  comp = __shfl_sync(kFull, comp, 0);
   if (lane < D) {
     const U4 rr = philox(A.seed, (uint32_t)lane, rid, A.ctr, kPurposeLearned);
     const float u1 = ((float)(rr.x >> 9) + 0.5f) * (1.0f / 8388608.0f);
@@ -546,22 +892,15 @@ __global__ void sample_apply_kernel(const MoveArgs A, const float* __restrict__ 
     sincospif(2.f * u2, &sn, &cs);
     const float z0 = sqrtf(-2.f * logf(u1)) * cs;
     const float mu = o[NCOMP + comp * DMAX + lane];
-    const float sg = (float)exp(log_sigma(o[NCOMP + NCOMP * DMAX + comp * DMAX + lane]));
+    const float sg = expf(log_sigma_f(o[NCOMP + NCOMP * DMAX + comp * DMAX + lane]));
     s_dl[warp][lane] = mu + sg * z0;
   } else if (lane < DMAX) {
     s_dl[warp][lane] = 0.f;
   }
   __syncwarp();
-  // log q(d | x): component log-probabilities on lanes 0..7, log-sum-exp over the warp (FP64)
-  const double logz = logits_lse(o);
-  double lp = lane < NCOMP ? component_logp(o, D, s_dl[warp], lane, logz) : -INFINITY;
-  double mx = lp;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, off));
-  double e = lane < NCOMP ? exp(lp - mx) : 0.0;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(kFull, e, off);
-  if (lane == 0) logq[r] = mx + log(e);
+  // log q(d | x)
+  const MixtureTerms mt = mixture_terms(o, D, s_dl[warp], lane);
+  if (lane == 0) logq[r] = (double)mt.lq;
   if (lane < DMAX) delta[r * DMAX + lane] = s_dl[warp][lane];
   // Apply
   float xs[APL][3], mass[APL];
@@ -635,16 +974,7 @@ __global__ void accept_kernel(const MoveArgs A, const float* __restrict__ y, con
   if ((unsigned)k >= (unsigned)A.n_states) return;
   if (lane < DMAX) s_dl[warp][lane] = -delta[r * DMAX + lane];
   __syncwarp();
-  const float* o = A.out + r * NOUT;
-  const double logz = logits_lse(o);
-  const double lp = lane < NCOMP ? component_logp(o, D, s_dl[warp], lane, logz) : -INFINITY;
-  double mx = lp;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, off));
-  double e = lane < NCOMP ? exp(lp - mx) : 0.0;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(kFull, e, off);
-  const double lqr = mx + log(e);
+  const double lqr = (double)mixture_terms(A.out + r * NOUT, D, s_dl[warp], lane).lq;
   const StateDev st = A.states[k];
   const double du = st.beta * (weighted_u(comps_y + r * 4, st.w_sg, st.w_g) - weighted_u(comps + r * 4, st.w_sg, st.w_g));
   const double lr = (lqr - logq_f[r]) - du;
@@ -733,7 +1063,7 @@ void build_learned_topo(int na, int nb, const int32_t* bonds, LearnedTopo* t) {
 cudaError_t learned_features(cudaStream_t s, const algdock_ctx& c, int64_t N, const int32_t* state_of,
                              const float* x, const double* comps, float* feat) {
   if (N == 0) return cudaSuccess;
-  features_kernel<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(N, pose_args(c), c.d_states, c.K, state_of, x, comps,
+  features_kernel<<<(unsigned)((N + 3) / 4), 128, 0, s>>>(N, pose_args(c), c.d_states, c.K, state_of, x, comps,
                                                               feat);
   return cudaGetLastError();
 }
@@ -741,16 +1071,46 @@ cudaError_t learned_features(cudaStream_t s, const algdock_ctx& c, int64_t N, co
 cudaError_t learned_pose_delta(cudaStream_t s, const algdock_ctx& c, int64_t N, const float* x, const float* y,
                                float* delta) {
   if (N == 0) return cudaSuccess;
-  pose_delta_kernel<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(N, pose_args(c), x, y, delta);
+  pose_delta_kernel<<<(unsigned)((N + 31) / 32), 32, 0, s>>>(N, pose_args(c), x, y, delta);
   return cudaGetLastError();
 }
 
-// Scratch of the forward pass: h1, h2, h3 (BF16 [N][256]).
-size_t learned_forward_scratch(int64_t N) { return 3 * align256((size_t)N * NHID * sizeof(bf16)); }
+// Scratch of the forward pass: the packed weights, then h1, h2, h3 (BF16 [N][256]) for the
+// layer-by-layer path.
+static size_t packed_bytes() { return align256((size_t)F_PACKED * sizeof(bf16)); }
+size_t learned_forward_scratch(int64_t N) { return packed_bytes() + 3 * align256((size_t)N * NHID * sizeof(bf16)); }
 
-static cudaError_t forward_keep(cudaStream_t s, const float* params, const bf16* W, int64_t N, const float* feat,
-                                float* out, bf16* h1, bf16* h2, bf16* h3) {
+static cudaError_t pack_weights(cudaStream_t s, const bf16* W, bf16* Wp) {
+  pack_weights_kernel<<<(F_PACKED + 255) / 256, 256, 0, s>>>(W, Wp);
+  return cudaGetLastError();
+}
+
+// The fused kernel needs 16-byte aligned features (float4 loads) and the opt-in shared-memory
+// size, set once per device.
+static bool fused_ready(const float* feat) {
+  if ((((uintptr_t)feat) & 15) != 0) return false;
+  static std::atomic<int> done[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  if (done[dev].load(std::memory_order_acquire) == 1) return true;
+  if (cudaFuncSetAttribute(mlp_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  done[dev].store(1, std::memory_order_release);
+  return true;
+}
+
+// Forward pass: the fused kernel on the packed weights Wp, or (misaligned features) the four
+// layer GEMMs on the row-major copy W.  keep: also store h1..h3.
+static cudaError_t forward_run(cudaStream_t s, const float* params, const bf16* W, const bf16* Wp, int64_t N,
+                               const float* feat, float* out, bf16* h1, bf16* h2, bf16* h3, bool keep) {
   const int n = (int)N;
+  if (fused_ready(feat)) {
+    FusedArgs P{params, Wp, n, feat, out, keep ? h1 : nullptr, keep ? h2 : nullptr, keep ? h3 : nullptr};
+    mlp_fused_kernel<<<(unsigned)((N + FM - 1) / FM), F_WARPS * 32, F_SMEM, s>>>(P);
+    return cudaGetLastError();
+  }
   cudaError_t e = gemm<float, false, bf16, false, EPI_RELU_BF16>(s, n, NHID, NFEAT, feat, NFEAT, W + WOFF_1, NFEAT, h1,
                                                                   NHID, params + OFF_B1);
   if (e == cudaSuccess)
@@ -765,18 +1125,34 @@ static cudaError_t forward_keep(cudaStream_t s, const float* params, const bf16*
   return e;
 }
 
-cudaError_t learned_forward(cudaStream_t s, const float* params, const uint16_t* wbf16, int64_t N, const float* feat,
-                            float* out, void* scratch) {
+// Forward pass with its scratch laid out as learned_forward_scratch; pack: (re)pack the weights
+// first (false when an earlier call on the same scratch and weights already did).
+static cudaError_t forward_scratch(cudaStream_t s, const float* params, const uint16_t* wbf16, int64_t N,
+                                   const float* feat, float* out, void* scratch, bool pack) {
   if (N == 0) return cudaSuccess;
   char* p = (char*)scratch;
+  bf16* Wp = (bf16*)p;
+  p += packed_bytes();
   const size_t hb = align256((size_t)N * NHID * sizeof(bf16));
-  return forward_keep(s, params, (const bf16*)wbf16, N, feat, out, (bf16*)p, (bf16*)(p + hb), (bf16*)(p + 2 * hb));
+  if (pack) {
+    const cudaError_t e = pack_weights(s, (const bf16*)wbf16, Wp);
+    if (e != cudaSuccess) return e;
+  }
+  return forward_run(s, params, (const bf16*)wbf16, Wp, N, feat, out, (bf16*)p, (bf16*)(p + hb), (bf16*)(p + 2 * hb),
+                     false);
 }
 
-// Scratch of the gradient: h1..h3, out (FP32), dout (FP32 and BF16), dh (two BF16 buffers), loss rows.
+cudaError_t learned_forward(cudaStream_t s, const float* params, const uint16_t* wbf16, int64_t N, const float* feat,
+                            float* out, void* scratch) {
+  return forward_scratch(s, params, wbf16, N, feat, out, scratch, true);
+}
+
+// Scratch of the gradient: h1..h3, dh (two BF16 buffers), out and dout (FP32), dout (BF16), loss
+// rows, and the split partial products of the weight gradients.
 size_t learned_grad_scratch(int64_t N) {
   return 5 * align256((size_t)N * NHID * sizeof(bf16)) + 2 * align256((size_t)N * NOUT * sizeof(float)) +
-         align256((size_t)N * NOUT * sizeof(bf16)) + align256((size_t)N * sizeof(float));
+         align256((size_t)N * NOUT * sizeof(bf16)) + align256((size_t)N * sizeof(float)) +
+         align256((size_t)kWgradSplit * NOUT * NHID * sizeof(float)) + packed_bytes();
 }
 
 cudaError_t learned_grad(cudaStream_t s, const float* params, const uint16_t* wbf16, int64_t N, const float* feat,
@@ -795,34 +1171,35 @@ cudaError_t learned_grad(cudaStream_t s, const float* params, const uint16_t* wb
   float* dout = (float*)(p + 5 * hb + ob);
   bf16* dout16 = (bf16*)(p + 5 * hb + 2 * ob);
   float* lrow = (float*)(p + 5 * hb + 2 * ob + align256((size_t)N * NOUT * sizeof(bf16)));
+  float* part = (float*)((char*)lrow + align256((size_t)N * sizeof(float)));
+  bf16* Wp = (bf16*)((char*)part + align256((size_t)kWgradSplit * NOUT * NHID * sizeof(float)));
   const int n = (int)N;
-  cudaError_t e = forward_keep(s, params, W, N, feat, out, h1, h2, h3);
+  cudaError_t e = pack_weights(s, W, Wp);
+  if (e == cudaSuccess) e = forward_run(s, params, W, Wp, N, feat, out, h1, h2, h3, true);
   if (e != cudaSuccess) return e;
-  nll_kernel<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(N, D, out, delta, dout, lrow);
-  to_bf16_kernel<<<(unsigned)((N * NOUT + 255) / 256), 256, 0, s>>>(N * NOUT, dout, dout16);
+  nll_kernel<<<(unsigned)((N + 3) / 4), 128, 0, s>>>(N, D, out, delta, dout, dout16, lrow);
   if (loss) sum_kernel<<<1, 256, 0, s>>>(N, lrow, 1.f / (float)N, loss);
   // layer 4: dW4 = dout^T h3, db4 = colsum(dout), dh3 = (dout W4) * [h3 > 0]
-  e = gemm<bf16, true, bf16, true, EPI_F32>(s, NOUT, NHID, n, dout16, NOUT, h3, NHID, grad + OFF_W4, NHID);
-  colsum_kernel<float><<<(NOUT + 127) / 128, 128, 0, s>>>(n, NOUT, dout, 1.f, grad + OFF_B4);
+  e = gemm_wgrad<bf16, bf16>(s, NOUT, NHID, n, dout16, NOUT, h3, NHID, grad + OFF_W4, part);
+  if (e == cudaSuccess) e = colsum<float>(s, n, NOUT, dout, grad + OFF_B4, part);
   if (e == cudaSuccess)
     e = gemm<bf16, false, bf16, true, EPI_MASK_BF16>(s, n, NHID, NOUT, dout16, NOUT, W + WOFF_4, NHID, dA, NHID,
                                                       nullptr, h3, NHID);
   // layer 3
-  if (e == cudaSuccess) e = gemm<bf16, true, bf16, true, EPI_F32>(s, NHID, NHID, n, dA, NHID, h2, NHID, grad + OFF_W3, NHID);
-  colsum_kernel<bf16><<<(NHID + 127) / 128, 128, 0, s>>>(n, NHID, dA, 1.f, grad + OFF_B3);
+  if (e == cudaSuccess) e = gemm_wgrad<bf16, bf16>(s, NHID, NHID, n, dA, NHID, h2, NHID, grad + OFF_W3, part);
+  if (e == cudaSuccess) e = colsum<bf16>(s, n, NHID, dA, grad + OFF_B3, part);
   if (e == cudaSuccess)
     e = gemm<bf16, false, bf16, true, EPI_MASK_BF16>(s, n, NHID, NHID, dA, NHID, W + WOFF_3, NHID, dB, NHID, nullptr,
                                                       h2, NHID);
   // layer 2
-  if (e == cudaSuccess) e = gemm<bf16, true, bf16, true, EPI_F32>(s, NHID, NHID, n, dB, NHID, h1, NHID, grad + OFF_W2, NHID);
-  colsum_kernel<bf16><<<(NHID + 127) / 128, 128, 0, s>>>(n, NHID, dB, 1.f, grad + OFF_B2);
+  if (e == cudaSuccess) e = gemm_wgrad<bf16, bf16>(s, NHID, NHID, n, dB, NHID, h1, NHID, grad + OFF_W2, part);
+  if (e == cudaSuccess) e = colsum<bf16>(s, n, NHID, dB, grad + OFF_B2, part);
   if (e == cudaSuccess)
     e = gemm<bf16, false, bf16, true, EPI_MASK_BF16>(s, n, NHID, NHID, dB, NHID, W + WOFF_2, NHID, dA, NHID, nullptr,
                                                       h1, NHID);
   // layer 1
-  if (e == cudaSuccess)
-    e = gemm<bf16, true, float, true, EPI_F32>(s, NHID, NFEAT, n, dA, NHID, feat, NFEAT, grad + OFF_W1, NFEAT);
-  colsum_kernel<bf16><<<(NHID + 127) / 128, 128, 0, s>>>(n, NHID, dA, 1.f, grad + OFF_B1);
+  if (e == cudaSuccess) e = gemm_wgrad<bf16, float>(s, NHID, NFEAT, n, dA, NHID, feat, NFEAT, grad + OFF_W1, part);
+  if (e == cudaSuccess) e = colsum<bf16>(s, n, NHID, dA, grad + OFF_B1, part);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -834,7 +1211,8 @@ cudaError_t learned_adam(cudaStream_t s, float* params, uint16_t* wbf16, const f
   return cudaGetLastError();
 }
 
-// Scratch of one learned move: features, h1..h3, outputs, y, delta, log q, components of y.
+// Scratch of one learned move: features, packed weights and h1..h3, outputs, y, delta, log q,
+// components of y.
 size_t learned_propose_scratch(int64_t R, int na) {
   return align256((size_t)R * NFEAT * sizeof(float)) + learned_forward_scratch(R) +
          align256((size_t)R * NOUT * sizeof(float)) + align256((size_t)R * na * 3 * sizeof(float)) +
@@ -869,7 +1247,7 @@ cudaError_t learned_propose(cudaStream_t s, const algdock_ctx& c, const float* p
     MoveArgs A{pose_args(c), c.d_states, c.K, R, state_of, out, seed, (uint32_t)(cycle * (uint64_t)n_moves + mv),
                rep_offset, t_eff};
     e = learned_features(s, c, R, state_of, x, comps, feat);
-    if (e == cudaSuccess) e = learned_forward(s, params, wbf16, R, feat, out, fwd);
+    if (e == cudaSuccess) e = forward_scratch(s, params, wbf16, R, feat, out, fwd, mv == 0);
     if (e != cudaSuccess) break;
     if (apl == 1) sample_apply_kernel<1><<<blocks, 128, 0, s>>>(A, x, y, delta, logq);
     else if (apl == 2) sample_apply_kernel<2><<<blocks, 128, 0, s>>>(A, x, y, delta, logq);
@@ -877,7 +1255,7 @@ cudaError_t learned_propose(cudaStream_t s, const algdock_ctx& c, const float* p
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_evaluate(s, c, R, y, comps_y);
     if (e == cudaSuccess) e = learned_features(s, c, R, state_of, y, comps_y, feat);
-    if (e == cudaSuccess) e = learned_forward(s, params, wbf16, R, feat, out, fwd);
+    if (e == cudaSuccess) e = forward_scratch(s, params, wbf16, R, feat, out, fwd, false);
     if (e != cudaSuccess) break;
     if (apl == 1) accept_kernel<1><<<blocks, 128, 0, s>>>(A, y, comps_y, delta, logq, x, comps, accepted, counters);
     else if (apl == 2) accept_kernel<2><<<blocks, 128, 0, s>>>(A, y, comps_y, delta, logq, x, comps, accepted, counters);

@@ -107,6 +107,30 @@ def test_network_forward(small):
     assert np.median(rel) < 1e-3 and rel.max() < 2e-2, (np.median(rel), rel.max())
 
 
+def test_fused_forward_matches_layer_by_layer(small):
+    """The fused one-kernel forward pass (16-byte aligned operands) and the layer-by-layer GEMM path
+    (taken for a misaligned feature pointer) round at the same places, so they agree to FP32
+    accumulation order and the rare BF16 activation that rounds the other way."""
+    ctx = small[5]
+    p = _params(12)
+    pd, wd = _device_params(p)
+    rng = np.random.default_rng(13)
+    N = 1000
+    X = torch.from_numpy(rng.normal(size=(N, 64)).astype(np.float32)).cuda()
+    store = torch.empty(N * 64 + 1, dtype=torch.float32, device="cuda")
+    Xm = store[1:].view(N, 64)
+    Xm.copy_(X)
+    assert Xm.data_ptr() % 16 != 0
+    a = torch.empty((N, 360), dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    ctx.mlp_forward(pd, wd, X, a)
+    ctx.mlp_forward(pd, wd, Xm, b)
+    torch.cuda.synchronize()
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    rel = np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+    assert np.median(rel) < 1e-4 and rel.max() < 2e-2, (np.median(rel), rel.max())
+
+
 def test_network_gradient_and_loss(small):
     ctx = small[5]
     p = _params(5)
