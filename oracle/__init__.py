@@ -483,3 +483,43 @@ class _LearnedMixin:
 
 for _name in ("learned_ntorsions", "features", "apply", "pose_delta", "learned_mh"):
     setattr(OracleSystem, _name, getattr(_LearnedMixin, _name))
+
+
+# ------------------------------------------------------------------ external-coordinate moves
+SIGMA_TRANSLATION = 0.6   # A per dimension ("Sampling")
+ALPHA_MAX_EXTERNAL = 0.01  # moves only below this alpha ("Sampling")
+
+
+def _external_sigs(L):
+    if getattr(L, "_external", False):
+        return
+    L.oracle_random_rotation.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _d]
+    L.oracle_external_moves.argtypes = [C.c_void_p, C.c_int64, _i, C.c_int64, _d, _d, C.c_int, C.c_double,
+                                        C.c_double, C.c_uint64, C.c_uint64, _i]
+    L._external = True
+
+
+def random_rotation(a, b, c):
+    """Rotation matrix (3x3) of the quaternion built from three 32-bit words (Shoemake)."""
+    L = _load()
+    _external_sigs(L)
+    R = np.zeros(9)
+    L.oracle_random_rotation(int(a) & 0xFFFFFFFF, int(b) & 0xFFFFFFFF, int(c) & 0xFFFFFFFF, R)
+    return R.reshape(3, 3)
+
+
+def _external_moves(self, x, comps, state_of, n_moves, seed, cycle, rep_offset=0, alpha_max=ALPHA_MAX_EXTERNAL,
+                    sigma=SIGMA_TRANSLATION):
+    """n_moves external-coordinate moves per replica whose state has alpha < alpha_max.
+    Returns (x, comps, accepts [R])."""
+    _external_sigs(self._L)
+    x = np.array(x, dtype=np.float64, order="C").reshape(-1, self.na, 3)
+    comps = np.array(comps, dtype=np.float64, order="C").reshape(-1, 4)
+    R = x.shape[0]
+    acc = np.zeros(R, dtype=np.int32)
+    self._L.oracle_external_moves(self.h, R, _i32(state_of), int(rep_offset), x, comps, int(n_moves),
+                                  float(alpha_max), float(sigma), int(seed), int(cycle), acc)
+    return x, comps, acc
+
+
+OracleSystem.external_moves = _external_moves

@@ -26,6 +26,9 @@
  *   reduced_energies       "Estimation": u_kn for MBAR
  *   mbar                   "Estimation": MBAR (Shirts & Chodera 2008) self-consistent iteration
  *   statistical_inefficiency  "Equilibration and production" (Chodera 2016)
+ *   learned proposal       an extension of "Sampling" (not in the paper): network, mixture, move
+ *   external_moves         "Sampling": external-coordinate MCMC (random rotation about the centre
+ *                          of mass, Gaussian translation, Metropolis) for states with alpha < 0.01
  *
  * Parity unpinned: nothing in this file is left without a pin; see the tests.
  */
@@ -1343,6 +1346,85 @@ void oracle_learned_mh(const oracle_system* s, const double* W1, const double* b
       double u = oracle_u53(r4[0], r4[1]);
       if (logratio) logratio[r] = lr;
       if (u < exp(lr)) {
+        memcpy(xr, y, sizeof(double) * 3 * (size_t)na);
+        memcpy(cr, c1, sizeof(c1));
+        acc[r] += 1;
+      }
+    }
+  }
+  free(y);
+}
+
+/* ---------------------------------------------------------------- external-coordinate moves
+ * "Sampling": for states with alpha below a threshold (the paper: 0.01, on the coupling leg), a
+ * move rotates the ligand about its centre of mass by a uniformly random rotation (from a random
+ * unit quaternion) and translates it by a Gaussian step (0.6 A per dimension in the paper); the
+ * Metropolis criterion on the state's energy accepts it.  The proposal is symmetric, so the test
+ * is u < exp(-beta (U_k(x') - U_k(x))).
+ *
+ * Random numbers: Philox counter {d, replica, cycle * n_moves + move, 5}
+ *   d = 0: three 23-bit uniforms (words 0..2) for the quaternion;
+ *   d = 1: the translation, Box-Muller on words (0, 1) for x and y, (2, 3) for z;
+ *   d = 2: the accept uniform (53 bits from words 0, 1). */
+enum { O_PURPOSE_EXTERNAL = 5 };
+
+/* Rotation matrix (row-major) of the unit quaternion made from three uniforms by Shoemake's
+ * construction ("Uniform random rotations", Graphics Gems III, 1992), which is uniform over the
+ * rotation group. */
+void oracle_random_rotation(uint32_t a, uint32_t b, uint32_t c, double R[9]) {
+  double u1 = (double)(a >> 9) * (1.0 / 8388608.0);
+  double u2 = (double)(b >> 9) * (1.0 / 8388608.0);
+  double u3 = (double)(c >> 9) * (1.0 / 8388608.0);
+  double s1 = sqrt(1.0 - u1), s2 = sqrt(u1);
+  double qx = s1 * sin(2.0 * M_PI * u2), qy = s1 * cos(2.0 * M_PI * u2);
+  double qz = s2 * sin(2.0 * M_PI * u3), qw = s2 * cos(2.0 * M_PI * u3);
+  R[0] = 1.0 - 2.0 * (qy * qy + qz * qz);
+  R[1] = 2.0 * (qx * qy - qz * qw);
+  R[2] = 2.0 * (qx * qz + qy * qw);
+  R[3] = 2.0 * (qx * qy + qz * qw);
+  R[4] = 1.0 - 2.0 * (qx * qx + qz * qz);
+  R[5] = 2.0 * (qy * qz - qx * qw);
+  R[6] = 2.0 * (qx * qz - qy * qw);
+  R[7] = 2.0 * (qy * qz + qx * qw);
+  R[8] = 1.0 - 2.0 * (qx * qx + qy * qy);
+}
+
+/* n_moves external-coordinate moves per replica whose state has alpha < alpha_max (the warming
+ * leg's alpha = NaN never qualifies).  x [R][na][3] and comps [R][4] are updated in place; acc [R]
+ * counts accepted moves (0 for replicas without moves). */
+void oracle_external_moves(const oracle_system* s, int64_t n_rep, const int* state_of, int64_t rep_offset,
+                           double* x, double* comps, int n_moves, double alpha_max, double sigma, uint64_t seed,
+                           uint64_t cycle, int* acc) {
+  int na = s->na;
+  double* y = (double*)malloc(sizeof(double) * 3 * (size_t)na);
+  for (int64_t r = 0; r < n_rep; ++r) {
+    acc[r] = 0;
+    int k = state_of[r];
+    if (k < 0 || k >= s->K || !(s->alpha[k] < alpha_max)) continue;
+    double* xr = x + (size_t)3 * na * r;
+    double* cr = comps + 4 * r;
+    uint32_t rid = (uint32_t)(rep_offset + r);
+    for (int mv = 0; mv < n_moves; ++mv) {
+      uint32_t ctr = (uint32_t)(cycle * (uint64_t)n_moves + (uint64_t)mv);
+      uint32_t r4[4];
+      double R[9], t[3], zz, c[3], c1[4];
+      philox(seed, 0u, rid, ctr, O_PURPOSE_EXTERNAL, r4);
+      oracle_random_rotation(r4[0], r4[1], r4[2], R);
+      philox(seed, 1u, rid, ctr, O_PURPOSE_EXTERNAL, r4);
+      box_muller(r4[0], r4[1], &t[0], &t[1]);
+      box_muller(r4[2], r4[3], &t[2], &zz);
+      for (int d = 0; d < 3; ++d) t[d] *= sigma;
+      o_com(s, xr, c);
+      for (int i = 0; i < na; ++i) {
+        double v[3];
+        for (int d = 0; d < 3; ++d) v[d] = xr[3 * i + d] - c[d];
+        for (int d = 0; d < 3; ++d) y[3 * i + d] = c[d] + (R[3 * d] * v[0] + R[3 * d + 1] * v[1] + R[3 * d + 2] * v[2]) + t[d];
+      }
+      oracle_energy_force(s, y, 0.0, 0.0, NULL, c1);
+      double du = s->beta[k] * (weighted_energy(s->w_sg[k], s->w_g[k], c1) - weighted_energy(s->w_sg[k], s->w_g[k], cr));
+      philox(seed, 2u, rid, ctr, O_PURPOSE_EXTERNAL, r4);
+      double u = oracle_u53(r4[0], r4[1]);
+      if (u < exp(-du)) {
         memcpy(xr, y, sizeof(double) * 3 * (size_t)na);
         memcpy(cr, c1, sizeof(c1));
         acc[r] += 1;
