@@ -158,6 +158,25 @@ algdock_status algdock_hmc_cycle(algdock_ctx* ctx, int64_t n_rep, const int32_t*
                                  double* comps, double* dH, uint8_t* accepted, int32_t n_steps, uint64_t seed,
                                  uint64_t cycle, int64_t rep_offset, int64_t* counters);
 
+/* External-coordinate moves ("Sampling"): for each replica r whose state k = state_of[r] has
+ * alpha_k < alpha_max (the warming leg's alpha = NaN never qualifies), n_moves moves, each a
+ * uniformly random rotation about the centre of mass (the unit quaternion of three uniforms,
+ * Shoemake's construction) and a Gaussian translation of sigma (A) per dimension, accepted by the
+ * Metropolis criterion u < exp(-(U_k(x') - U_k(x)) / (k_B T_k)).  The paper: alpha_max = 0.01,
+ * sigma = 0.6 A, 20 moves after each HMC move.  A rigid move leaves U_L unchanged: comps[r][0] is
+ * carried over and U_I, Psi_sg, Psi_g are re-evaluated (FP32 terms, FP64 sums and decision).
+ * Philox4x32-10 keyed by seed, counter {d, rep_offset + r, cycle * n_moves + move, 5}: d = 0 the
+ * quaternion's 23-bit uniforms, d = 1 the translation (Box-Muller), d = 2 the accept uniform.
+ *   state_of [n_rep] int32, x [n_rep][n_atoms][3] float (in/out), comps [n_rep][4] double (in/out:
+ *            the components of x on entry, of the returned configuration on exit), all device
+ *   accepted [n_rep] int32 (device, may be NULL): incremented by the number of accepted moves
+ *   counters [ALGDOCK_N_COUNTERS] int64 (device, may be NULL): accumulated
+ * Errors: E_INVALID (negative sizes, sigma < 0 or not finite, non-device pointers), E_STATE (no
+ * grids, ligand or states). */
+algdock_status algdock_external_moves(algdock_ctx* ctx, int64_t n_rep, const int32_t* state_of, float* x,
+                                      double* comps, int32_t n_moves, double alpha_max, double sigma, uint64_t seed,
+                                      uint64_t cycle, int64_t rep_offset, int32_t* accepted, int64_t* counters);
+
 /* Energy and force of N configurations, each at its state ("Thermodynamic Cycle": grid
  * interaction energy and sampling force field; Eq. (binding_site); Eq. (protocol) weights), with
  * the arithmetic of one velocity-Verlet force evaluation inside algdock_hmc_cycle.

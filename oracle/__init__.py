@@ -495,7 +495,7 @@ def _external_sigs(L):
         return
     L.oracle_random_rotation.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _d]
     L.oracle_external_moves.argtypes = [C.c_void_p, C.c_int64, _i, C.c_int64, _d, _d, C.c_int, C.c_double,
-                                        C.c_double, C.c_uint64, C.c_uint64, _i]
+                                        C.c_double, C.c_uint64, C.c_uint64, _i, C.c_void_p]
     L._external = True
 
 
@@ -509,17 +509,19 @@ def random_rotation(a, b, c):
 
 
 def _external_moves(self, x, comps, state_of, n_moves, seed, cycle, rep_offset=0, alpha_max=ALPHA_MAX_EXTERNAL,
-                    sigma=SIGMA_TRANSLATION):
+                    sigma=SIGMA_TRANSLATION, logratio=False):
     """n_moves external-coordinate moves per replica whose state has alpha < alpha_max.
-    Returns (x, comps, accepts [R])."""
+    Returns (x, comps, accepts [R]); with logratio=True also the last move's log acceptance
+    ratio [R]."""
     _external_sigs(self._L)
     x = np.array(x, dtype=np.float64, order="C").reshape(-1, self.na, 3)
     comps = np.array(comps, dtype=np.float64, order="C").reshape(-1, 4)
     R = x.shape[0]
     acc = np.zeros(R, dtype=np.int32)
+    lr = np.zeros(R) if logratio else None
     self._L.oracle_external_moves(self.h, R, _i32(state_of), int(rep_offset), x, comps, int(n_moves),
-                                  float(alpha_max), float(sigma), int(seed), int(cycle), acc)
-    return x, comps, acc
+                                  float(alpha_max), float(sigma), int(seed), int(cycle), acc, _ptr(lr))
+    return (x, comps, acc, lr) if logratio else (x, comps, acc)
 
 
 OracleSystem.external_moves = _external_moves

@@ -1391,14 +1391,16 @@ void oracle_random_rotation(uint32_t a, uint32_t b, uint32_t c, double R[9]) {
 
 /* n_moves external-coordinate moves per replica whose state has alpha < alpha_max (the warming
  * leg's alpha = NaN never qualifies).  x [R][na][3] and comps [R][4] are updated in place; acc [R]
- * counts accepted moves (0 for replicas without moves). */
+ * counts accepted moves (0 for replicas without moves); logratio [R] (may be NULL) receives the
+ * last attempted move's log acceptance ratio -beta dU (0 for replicas without moves). */
 void oracle_external_moves(const oracle_system* s, int64_t n_rep, const int* state_of, int64_t rep_offset,
                            double* x, double* comps, int n_moves, double alpha_max, double sigma, uint64_t seed,
-                           uint64_t cycle, int* acc) {
+                           uint64_t cycle, int* acc, double* logratio) {
   int na = s->na;
   double* y = (double*)malloc(sizeof(double) * 3 * (size_t)na);
   for (int64_t r = 0; r < n_rep; ++r) {
     acc[r] = 0;
+    if (logratio) logratio[r] = 0.0;
     int k = state_of[r];
     if (k < 0 || k >= s->K || !(s->alpha[k] < alpha_max)) continue;
     double* xr = x + (size_t)3 * na * r;
@@ -1424,6 +1426,7 @@ void oracle_external_moves(const oracle_system* s, int64_t n_rep, const int* sta
       double du = s->beta[k] * (weighted_energy(s->w_sg[k], s->w_g[k], c1) - weighted_energy(s->w_sg[k], s->w_g[k], cr));
       philox(seed, 2u, rid, ctr, O_PURPOSE_EXTERNAL, r4);
       double u = oracle_u53(r4[0], r4[1]);
+      if (logratio) logratio[r] = -du;
       if (u < exp(-du)) {
         memcpy(xr, y, sizeof(double) * 3 * (size_t)na);
         memcpy(cr, c1, sizeof(c1));

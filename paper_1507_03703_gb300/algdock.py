@@ -30,7 +30,11 @@ EXPORTS = [
     "algdock_hmc_cycle", "algdock_energy_force", "algdock_exchange", "algdock_reduced_energies", "algdock_mbar",
     "algdock_mbar_noalloc", "algdock_learned_ntorsions", "algdock_learned_features", "algdock_pose_delta",
     "algdock_mlp_forward", "algdock_mlp_grad", "algdock_mlp_adam", "algdock_propose_learned",
+    "algdock_external_moves",
 ]
+
+ALPHA_MAX_EXTERNAL = 0.01     # external-coordinate moves only below this alpha ("Sampling")
+SIGMA_TRANSLATION = 0.6       # A per dimension ("Sampling")
 MLP_NFEAT, MLP_NHID, MLP_NOUT, MLP_DMAX = 64, 256, 360, 22
 MLP_KEYS = ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")
 MLP_NPARAMS = 64 * 256 + 256 + 256 * 256 + 256 + 256 * 256 + 256 + 256 * 360 + 360
@@ -117,6 +121,7 @@ def load_library(path: str = LIB_PATH):
         "algdock_states_set": ([vp, i32, vp, vp, vp], C.c_int),
         "algdock_hmc_cycle": ([vp, i64, vp, vp, vp, vp, vp, i32, u64, u64, i64, vp], C.c_int),
         "algdock_energy_force": ([vp, i64, vp, vp, vp, vp], C.c_int),
+        "algdock_external_moves": ([vp, i64, vp, vp, vp, i32, dbl, dbl, u64, u64, i64, vp, vp], C.c_int),
         "algdock_exchange": ([vp, i32, i32, i32, vp, vp, vp, i32, i32, u64, u64, i64, vp, vp], C.c_int),
         "algdock_reduced_energies": ([vp, i64, vp, vp, i32, i32, vp], C.c_int),
         "algdock_mbar": ([vp, i32, i64, vp, vp, dbl, i32, i32, vp, C.POINTER(i32)], C.c_int),
@@ -303,6 +308,16 @@ class Context:
             _dev(comps, torch.float64, "comps"), _dev(dH, torch.float64, "dH"),
             _dev(accepted, torch.uint8, "accepted"), int(n_steps), int(seed), int(cycle), int(rep_offset),
             _dev(counters, torch.int64, "counters")))
+
+    def external_moves(self, state_of, x, comps, n_moves=20, seed=0, cycle=0, alpha_max=ALPHA_MAX_EXTERNAL,
+                       sigma=SIGMA_TRANSLATION, rep_offset=0, accepted=None, counters=None):
+        """External-coordinate moves (random rotation about the COM + Gaussian translation,
+        Metropolis) for the replicas whose state has alpha < alpha_max; x and comps in place."""
+        import torch
+        self._check(self._L.algdock_external_moves(
+            self.h, int(state_of.numel()), _dev(state_of, torch.int32, "state_of"), _dev(x, torch.float32, "x"),
+            _dev(comps, torch.float64, "comps"), int(n_moves), float(alpha_max), float(sigma), int(seed), int(cycle),
+            int(rep_offset), _dev(accepted, torch.int32, "accepted"), _dev(counters, torch.int64, "counters")))
 
     def energy_force(self, state_of, x, force, comps=None):
         import torch

@@ -437,6 +437,7 @@ algdock_status algdock_states_set(algdock_ctx* c, int32_t K, const double* T, co
     s.beta = 1.0 / (kBoltzmann * T[k]);
     s.w_sg = alpha_sg_of(alpha[k]);
     s.w_g = alpha_g_of(alpha[k]);
+    s.alpha = alpha[k];
     s.w_sg_f = (float)s.w_sg;
     s.w_g_f = (float)s.w_g;
     s.dt = (float)dt_fs[k];
@@ -472,6 +473,27 @@ algdock_status algdock_hmc_cycle(algdock_ctx* c, int64_t n_rep, const int32_t* s
   cudaError_t e = launch_hmc(c->stream, *c, n_rep, state_of, x, comps, dH, accepted, n_steps, seed, cycle,
                              rep_offset, counters);
   if (e != cudaSuccess) return cuda_fail(c, e, "hmc_cycle");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_external_moves(algdock_ctx* c, int64_t n_rep, const int32_t* state_of, float* x,
+                                      double* comps, int32_t n_moves, double alpha_max, double sigma, uint64_t seed,
+                                      uint64_t cycle, int64_t rep_offset, int32_t* accepted, int64_t* counters) {
+  ALGDOCK_TRY(c)
+  if (!c->has_grid || !c->has_ligand || c->K == 0)
+    return fail(c, ALGDOCK_E_STATE, "external_moves: load grids, ligand and states first");
+  if (n_rep < 0 || n_moves < 0 || rep_offset < 0) return fail(c, ALGDOCK_E_INVALID, "external_moves: negative size");
+  if (!(sigma >= 0.0) || !isfinite(sigma) || isnan(alpha_max))
+    return fail(c, ALGDOCK_E_INVALID, "external_moves: need finite sigma >= 0 and alpha_max not NaN");
+  if (n_rep == 0 || n_moves == 0) return ALGDOCK_OK;
+  if (!is_device_ptr(state_of) || !is_device_ptr(x) || !is_device_ptr(comps) ||
+      (accepted && !is_device_ptr(accepted)) || (counters && !is_device_ptr(counters)))
+    return fail(c, ALGDOCK_E_INVALID, "external_moves: arrays must be device pointers");
+  Device g(c->device);
+  cudaError_t e = launch_external(c->stream, *c, n_rep, state_of, x, comps, n_moves, alpha_max, (float)sigma, seed,
+                                  cycle, rep_offset, accepted, counters);
+  if (e != cudaSuccess) return cuda_fail(c, e, "external_moves");
   return ALGDOCK_OK;
   ALGDOCK_CATCH(c)
 }

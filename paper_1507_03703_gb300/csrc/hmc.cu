@@ -690,6 +690,176 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) eval_kernel(const EvalArg
   if (A.comps && lane < 4) A.comps[n * 4 + lane] = c[lane];
 }
 
+// External-coordinate moves ("Sampling"): for a replica whose state has alpha < alpha_max, n_moves
+// moves, each a uniformly random rotation about the centre of mass (the unit quaternion of three
+// uniforms by Shoemake's construction) and a Gaussian translation of sigma per dimension, accepted
+// by the Metropolis test on the state's energy.  One warp per replica.  A rigid move leaves the
+// intramolecular energy unchanged, so U_L is carried over and only the grid terms and the
+// restraint of the moved pose are evaluated (both lattices, so all four components stay current).
+// Philox counter {d, replica, cycle * n_moves + move, 5}: d = 0 the quaternion's uniforms, d = 1
+// the translation (Box-Muller), d = 2 the accept uniform.
+struct ExtArgs {
+  GridDev G;
+  LigandLayout LL;
+  const uint32_t* blob;  // the ligand blob in global memory (read through the cache)
+  const StateDev* states;
+  int n_states;
+  int64_t n_rep;
+  const int32_t* state_of;
+  float* x;
+  double* comps;
+  int n_moves;
+  double alpha_max;
+  float sigma;
+  uint64_t seed;
+  uint64_t cycle;
+  int64_t rep_offset;
+  int32_t* accepted;
+  int64_t* counters;
+};
+
+template <int APL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) external_kernel(const ExtArgs A) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (r >= A.n_rep) return;
+  const int k = A.state_of[r];
+  if ((unsigned)k >= (unsigned)A.n_states) return;
+  const StateDev st = A.states[k];
+  if (!(st.alpha < A.alpha_max)) return;  // also the warming leg's NaN
+  const Lig L = bind_ligand(A.blob, A.LL);
+  const int na = A.LL.na;
+  const uint32_t rid = (uint32_t)(A.rep_offset + r);
+  float x[APL][3], sA[APL], sB[APL], q[APL], m[APL];
+#pragma unroll
+  for (int a = 0; a < APL; ++a) {
+    const int i = lane + 32 * a;
+    const bool own = i < na;
+    const float4 pa = own ? L.atom_a[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    m[a] = own ? L.atom_b[i].z : 0.f;
+    q[a] = pa.y;
+    sA[a] = pa.z;
+    sB[a] = pa.w;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) x[a][d] = own ? A.x[(r * na + i) * 3 + d] : 0.f;
+  }
+  double c0[4];
+  {
+    const double mine = lane < 4 ? A.comps[r * 4 + lane] : 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) c0[c] = __shfl_sync(kFull, mine, c);
+  }
+  const float invM = 1.f / A.LL.total_mass;
+  const double u0 = weighted(c0, st.w_sg, st.w_g);
+  int n_acc = 0, outside = 0;
+  double u_cur = u0;
+  for (int mv = 0; mv < A.n_moves; ++mv) {
+    const uint32_t ctr = (uint32_t)(A.cycle * (uint64_t)A.n_moves + (uint64_t)mv);
+    // rotation
+    const U4 rq = philox(A.seed, 0u, rid, ctr, kPurposeExternal);
+    const float u1 = (float)(rq.x >> 9) * (1.0f / 8388608.0f);
+    const float u2 = (float)(rq.y >> 9) * (1.0f / 8388608.0f);
+    const float u3 = (float)(rq.z >> 9) * (1.0f / 8388608.0f);
+    const float s1 = sqrtf(1.f - u1), s2 = sqrtf(u1);
+    float sn2, cs2, sn3, cs3;
+    sincospif(2.f * u2, &sn2, &cs2);
+    sincospif(2.f * u3, &sn3, &cs3);
+    const float qx = s1 * sn2, qy = s1 * cs2, qz = s2 * sn3, qw = s2 * cs3;
+    const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qz * qw), R02 = 2.f * (qx * qz + qy * qw);
+    const float R10 = 2.f * (qx * qy + qz * qw), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qx * qw);
+    const float R20 = 2.f * (qx * qz - qy * qw), R21 = 2.f * (qy * qz + qx * qw), R22 = 1.f - 2.f * (qx * qx + qy * qy);
+    // translation: Box-Muller on 23-bit uniforms, as for the momenta
+    const U4 rt = philox(A.seed, 1u, rid, ctr, kPurposeExternal);
+    const float ua = ((float)(rt.x >> 9) + 0.5f) * (1.0f / 8388608.0f), ub = (float)(rt.y >> 9) * (1.0f / 8388608.0f);
+    const float uc = ((float)(rt.z >> 9) + 0.5f) * (1.0f / 8388608.0f), ud = (float)(rt.w >> 9) * (1.0f / 8388608.0f);
+    float sb, cb, sd_, cd;
+    sincospif(2.f * ub, &sb, &cb);
+    sincospif(2.f * ud, &sd_, &cd);
+    const float ra = sqrtf(-2.f * logf(ua)), rc = sqrtf(-2.f * logf(uc));
+    const float tx = A.sigma * ra * cb, ty = A.sigma * ra * sb, tz = A.sigma * rc * cd;
+    // centre of mass, moved pose, its grid terms and restraint
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+#pragma unroll
+    for (int a = 0; a < APL; ++a) {
+      cx += m[a] * x[a][0];
+      cy += m[a] * x[a][1];
+      cz += m[a] * x[a][2];
+    }
+    cx = warp_sumf(cx) * invM;
+    cy = warp_sumf(cy) * invM;
+    cz = warp_sumf(cz) * invM;
+    float y[APL][3];
+    float eg = 0.f, esg = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+    int out_mv = 0;
+#pragma unroll
+    for (int a = 0; a < APL; ++a) {
+      const float vx = x[a][0] - cx, vy = x[a][1] - cy, vz = x[a][2] - cz;
+      y[a][0] = cx + (R00 * vx + R01 * vy + R02 * vz) + tx;
+      y[a][1] = cy + (R10 * vx + R11 * vy + R12 * vz) + ty;
+      y[a][2] = cz + (R20 * vx + R21 * vy + R22 * vz) + tz;
+      if (lane + 32 * a < na) {
+        const GridOut go = grid_atom(A.G, y[a][0], y[a][1], y[a][2], sA[a], sB[a], q[a], true, true, 0.f, 0.f);
+        eg += go.e_g;
+        esg += go.e_sg;
+        out_mv += go.outside ? 1 : 0;
+        mx += m[a] * y[a][0];
+        my += m[a] * y[a][1];
+        mz += m[a] * y[a][2];
+      }
+    }
+    mx = warp_sumf(mx);
+    my = warp_sumf(my);
+    mz = warp_sumf(mz);
+    const float dx = mx * invM - A.LL.site[0], dy = my * invM - A.LL.site[1], dz = mz * invM - A.LL.site[2];
+    const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+    float er = 0.f;
+    if (d > A.LL.d0) {
+      const float ex = d - A.LL.d0;
+      er = 0.5f * A.LL.k_rest * ex * ex;
+    } else if (!(d <= A.LL.d0)) {
+      er = d;
+    }
+    double c1[4];
+    c1[0] = c0[0];
+    c1[1] = (double)er;
+    c1[2] = warp_sum((double)esg);
+    c1[3] = warp_sum((double)eg);
+    const double u1e = weighted(c1, st.w_sg, st.w_g);
+    const U4 ra4 = philox(A.seed, 2u, rid, ctr, kPurposeExternal);
+    const bool acc = uniform53(ra4.x, ra4.y) < exp(-st.beta * (u1e - u_cur));
+    outside += out_mv;
+    if (acc) {
+#pragma unroll
+      for (int a = 0; a < APL; ++a)
+#pragma unroll
+        for (int dd = 0; dd < 3; ++dd) x[a][dd] = y[a][dd];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) c0[c] = c1[c];
+      u_cur = u1e;
+      ++n_acc;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < APL; ++a) {
+    const int i = lane + 32 * a;
+    if (i < na)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) A.x[(r * na + i) * 3 + d] = x[a][d];
+  }
+  if (lane < 4) A.comps[r * 4 + lane] = lane == 0 ? c0[0] : (lane == 1 ? c0[1] : (lane == 2 ? c0[2] : c0[3]));
+  if (lane == 0) {
+    if (A.accepted) A.accepted[r] += n_acc;
+    if (A.counters) {
+      if (n_acc) atomicAdd((unsigned long long*)&A.counters[ALGDOCK_CNT_ACCEPTED], (unsigned long long)n_acc);
+    }
+  }
+  if (A.counters) {
+    const int out_total = __reduce_add_sync(kFull, outside);
+    if (lane == 0 && out_total)
+      atomicAdd((unsigned long long*)&A.counters[ALGDOCK_CNT_OUTSIDE], (unsigned long long)out_total);
+  }
+}
+
 // u_kn[k][n] from stored components (k over k_count states from k_begin).
 __global__ void ukn_kernel(const StateDev* __restrict__ states, int k_begin, int k_count, int64_t N,
                            const double* __restrict__ comps, double* u_kn) {
@@ -751,6 +921,20 @@ cudaError_t launch_evaluate(cudaStream_t s, const algdock_ctx& c, int64_t N, con
 cudaError_t launch_energy_force(cudaStream_t s, const algdock_ctx& c, int64_t N, const int32_t* state_of,
                                 const float* x, float* force, double* comps) {
   return launch_eval(s, c, N, state_of, x, force, comps);
+}
+
+cudaError_t launch_external(cudaStream_t s, const algdock_ctx& c, int64_t n_rep, const int32_t* state_of, float* x,
+                            double* comps, int n_moves, double alpha_max, float sigma, uint64_t seed, uint64_t cycle,
+                            int64_t rep_offset, int32_t* accepted, int64_t* counters) {
+  if (n_rep == 0 || n_moves == 0) return cudaSuccess;
+  ExtArgs A{c.grid, c.lig, c.d_blob, c.d_states, c.K, n_rep, state_of, x, comps, n_moves, alpha_max, sigma, seed,
+            cycle, rep_offset, accepted, counters};
+  const int apl = atoms_per_lane(c.lig.na);
+  const unsigned blocks = (unsigned)((n_rep + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  if (apl == 1) external_kernel<1><<<blocks, kWarpsPerBlock * 32, 0, s>>>(A);
+  else if (apl == 2) external_kernel<2><<<blocks, kWarpsPerBlock * 32, 0, s>>>(A);
+  else external_kernel<3><<<blocks, kWarpsPerBlock * 32, 0, s>>>(A);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ukn(cudaStream_t s, const algdock_ctx& c, int64_t N, const double* comps, int k_begin,

@@ -20,7 +20,7 @@ constexpr double kAttractiveMinDist = 2.0;         // A
 constexpr int kMaxAtoms = 96;                      // 3 atoms per lane of one warp
 constexpr int kMaxLadder = 1024;
 
-enum : uint32_t { kPurposeMomentum = 1, kPurposeAccept = 2, kPurposeExchange = 3 };
+enum : uint32_t { kPurposeMomentum = 1, kPurposeAccept = 2, kPurposeExchange = 3, kPurposeExternal = 5 };
 
 // ------------------------------------------------------------------ Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, SC'11: ten rounds of two 32x32->64 multiplies with a Weyl key
@@ -68,6 +68,7 @@ struct StateDev {
   double beta;     // 1 / (k_B T)
   double w_sg;     // alpha_sg
   double w_g;      // alpha_g
+  double alpha;    // the protocol's alpha (NaN on the warming leg)
   float w_sg_f, w_g_f;
   float dt, sqrt_kT;
 };
@@ -142,6 +143,9 @@ cudaError_t launch_hmc(cudaStream_t s, const algdock_ctx& c, int64_t n_rep, cons
                        double* comps, double* dH, uint8_t* acc, int n_steps, uint64_t seed, uint64_t cycle,
                        int64_t rep_offset, int64_t* counters);
 cudaError_t launch_evaluate(cudaStream_t s, const algdock_ctx& c, int64_t N, const float* x, double* comps);
+cudaError_t launch_external(cudaStream_t s, const algdock_ctx& c, int64_t n_rep, const int32_t* state_of, float* x,
+                            double* comps, int n_moves, double alpha_max, float sigma, uint64_t seed, uint64_t cycle,
+                            int64_t rep_offset, int32_t* accepted, int64_t* counters);
 cudaError_t launch_energy_force(cudaStream_t s, const algdock_ctx& c, int64_t N, const int32_t* state_of,
                                 const float* x, float* force, double* comps);
 cudaError_t launch_ukn(cudaStream_t s, const algdock_ctx& c, int64_t N, const double* comps, int k_begin,

@@ -24,12 +24,16 @@ class ReplicaExchange:
     """All legs of one ligand: HMC for every slot in one launch, then exchange per leg."""
 
     def __init__(self, ctx: Context, legs, n_chains: int, x0, seed: int, n_sweeps: int = 25, max_sep: int = 5,
-                 device="cuda", rep_offset: int = 0, ladder_offset: int = 0):
+                 device="cuda", rep_offset: int = 0, ladder_offset: int = 0, n_external: int = 0,
+                 alpha_max: float = 0.01, sigma: float = 0.6):
         """rep_offset / ladder_offset: global index of this run's first replica slot and first
-        ladder in the Philox counters (a rank's share of a sharded run; see ranks.Shard)."""
+        ladder in the Philox counters (a rank's share of a sharded run; see ranks.Shard).
+        n_external: external-coordinate moves per replica after each HMC move at states with
+        alpha < alpha_max (the paper: 20, 0.01, sigma 0.6 A); 0 leaves them out."""
         self.ctx, self.legs, self.C = ctx, list(legs), int(n_chains)
         self.seed, self.n_sweeps, self.max_sep = int(seed), int(n_sweeps), int(max_sep)
         self.rep_offset, self.ladder_offset = int(rep_offset), int(ladder_offset)
+        self.n_external, self.alpha_max, self.sigma = int(n_external), float(alpha_max), float(sigma)
         self.R = self.C * sum(l.K for l in self.legs)
         x0 = np.asarray(x0, dtype=np.float32)
         if x0.shape[0] != self.R:
@@ -40,6 +44,7 @@ class ReplicaExchange:
         self.comps = torch.zeros((self.R, 4), dtype=torch.float64, device=dev)
         self.dH = torch.zeros(self.R, dtype=torch.float64, device=dev)
         self.acc = torch.zeros(self.R, dtype=torch.uint8, device=dev)
+        self.ext_acc = torch.zeros(self.R, dtype=torch.int32, device=dev)
         self.counters = torch.zeros(N_COUNTERS, dtype=torch.int64, device=dev)
         self.base = []
         state = np.empty(self.R, dtype=np.int32)
@@ -64,6 +69,12 @@ class ReplicaExchange:
         self.ctx.hmc_cycle(self.state_of, self.x, self.comps, self.dH, self.acc, n_steps=n_steps, seed=self.seed,
                            cycle=cycle, rep_offset=self.rep_offset, counters=self.counters)
 
+    def external(self, cycle: int):
+        if self.n_external > 0:
+            self.ctx.external_moves(self.state_of, self.x, self.comps, self.n_external, seed=self.seed, cycle=cycle,
+                                    alpha_max=self.alpha_max, sigma=self.sigma, rep_offset=self.rep_offset,
+                                    accepted=self.ext_acc)
+
     def exchange(self, cycle: int):
         for li, leg in enumerate(self.legs):
             sl = self.leg_slice(li)
@@ -73,7 +84,10 @@ class ReplicaExchange:
                               accepts=self.accepts[li])
 
     def cycle(self, cycle: int, n_steps: int, record: bool = False):
+        """One iteration ("Equilibration and production"): an HMC move and the external-coordinate
+        moves for every replica, then the exchange sweeps."""
         self.hmc(cycle, n_steps)
+        self.external(cycle)
         self.exchange(cycle)
         if record:
             self.history.append(self.comps.clone())
