@@ -38,6 +38,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-mbar", action="store_true")
     p.add_argument("--no-learned", action="store_true")
+    p.add_argument("--no-bpmf", action="store_true", help="skip the BPMF effective-samples comparison")
+    p.add_argument("--bpmf-only", action="store_true",
+                   help="set up the workload and run only the BPMF effective-samples comparison")
+    p.add_argument("--paper-cycles", type=int, default=8000)
+    p.add_argument("--learned-cycles", type=int, default=8000)
+    p.add_argument("--bpmf-window", type=int, default=1000)
     p.add_argument("--learned-only", action="store_true",
                    help="set up the workload and run only the learned-vs-plain comparison (for profiling)")
     return p.parse_args()
@@ -225,6 +231,131 @@ def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=4
     return out
 
 
+def _target_psi_g(run, li, k_local):
+    """Psi_g of the configuration at state k_local of leg li, one value per chain."""
+    import torch
+    leg = run.legs[li]
+    sl = run.leg_slice(li)
+    st = run.state_of[sl].view(run.C, leg.K)
+    slot = (st == leg.state_offset + k_local).int().argmax(dim=1)
+    return run.comps[sl].view(run.C, leg.K, 4)[torch.arange(run.C, device=st.device), slot, 3].clone()
+
+
+def profiled_bpmf_ref():
+    """The converged BPMF of the paper-scale workload from the committed convergence study, if
+    present: (value in kT, source)."""
+    try:
+        path = os.path.join(ROOT, "profiles", "bpmf_convergence_paper_scale.md")
+        for line in open(path):
+            if line.strip().startswith("bpmf_ref_kT:"):
+                return float(line.split(":", 1)[1]), "profiles/bpmf_convergence_paper_scale.md"
+    except Exception:
+        pass
+    return None, None
+
+
+def bpmf_convergence(ctx, sys_, stream, dev, paper_cycles=8000, learned_cycles=8000, window=1000, warm=200,
+                     n_external=20, n_learned=4, train_iter=300, seed=11, criterion=0.2):
+    """BPMF effective samples per second of the paper's iteration (an HMC move and 20
+    external-coordinate moves at alpha < 0.01 per replica, then 25 exchange sweeps) and of the same
+    iteration plus 4 rigid-body learned moves per replica, over both legs (64 chains x 128 states).
+    Both start from one warm state (`warm` cycles of the paper's iteration, whose poses at every
+    state also train the network).  Every `window` cycles: the window's BPMF (MBAR per leg over its
+    snapshots, one every 10 cycles), the ESS of the Psi_g series at the target state (alpha = 1,
+    300 K; sum over chains of N/g) and the GPU time of its cycles.  An arm's BPMF effective samples
+    per second count only the windows from the first one within `criterion` kT of B_ref on; B_ref is
+    the converged value of the committed convergence study, else the learned arm's second half."""
+    import torch
+
+    from paper_1507_03703_gb300 import synthetic as S
+    from paper_1507_03703_gb300.learned import LearnedProposal, effective_samples
+    from paper_1507_03703_gb300.sampler import Leg, ReplicaExchange, bpmf_kT
+    lig = sys_.ligand
+    legs = [Leg(N_STATES_BC, 0), Leg(N_STATES_CD, N_STATES_BC)]
+    R = N_CHAINS * (N_STATES_BC + N_STATES_CD)
+    base = S.place_ligand(lig, sys_.receptor, sys_.site, 128, seed=seed, n_tries=8).astype(np.float32)
+    x0 = base[np.arange(R) % base.shape[0]]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def window_bpmf(run):
+        f = []
+        for li in range(len(legs)):
+            f.append(run.free_energies(li, max_iter=20000)[0])
+        run.history = []
+        return float(bpmf_kT(f[0], f[1]))
+
+    pre = ReplicaExchange(ctx, legs, N_CHAINS, x0, seed=seed, n_external=n_external)
+    ctx.reduced_energies(R, x=pre.x, comps=pre.comps)
+    xs, cs, ss = [], [], []
+    for cyc in range(warm):
+        pre.cycle(cyc, N_VV)
+        if cyc >= warm // 2 and cyc % 10 == 0:
+            xs.append(pre.x.clone())
+            cs.append(pre.comps.clone())
+            ss.append(pre.state_of.clone())
+    lp = LearnedProposal(ctx, seed=seed, n_torsions=0)
+    losses = lp.train(torch.cat(xs), torch.cat(cs), torch.cat(ss).cpu().numpy(), n_iter=train_iter, seed=seed)
+    out = {"workload": "both legs, %d chains x %d states, %d VV steps" % (N_CHAINS, N_STATES_BC + N_STATES_CD, N_VV),
+           "target_state": "alpha = 1, 300 K", "warm_cycles": warm, "window_cycles": window,
+           "criterion_kT": criterion, "learned_training": {"poses": int(sum(x.shape[0] for x in xs)),
+                                                           "iters": train_iter, "loss_first": losses[0],
+                                                           "loss_last": losses[-1]}}
+    arms = {}
+    for name, n_cyc in (("paper", paper_cycles), ("learned", learned_cycles)):
+        run = ReplicaExchange(ctx, legs, N_CHAINS, x0, seed=seed + 1, n_external=n_external)
+        run.x.copy_(pre.x)
+        run.comps.copy_(pre.comps)
+        run.state_of.copy_(pre.state_of)
+        for li in range(len(legs)):
+            run.config_of[li].copy_(pre.config_of[li])
+        acc = torch.zeros(R, dtype=torch.int32, device=dev)
+        wins, series, ms = [], [], 0.0
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for cyc in range(n_cyc):
+            run.hmc(cyc, N_VV)
+            run.external(cyc)
+            if name == "learned":
+                lp.propose(run.state_of, run.x, run.comps, n_learned, seed=seed + 2, cycle=cyc, accepted=acc)
+            run.exchange(cyc)
+            if cyc % 10 == 0:
+                run.history.append(run.comps.clone())
+            series.append(_target_psi_g(run, 1, N_STATES_CD - 1))
+            if (cyc + 1) % window == 0:
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                w_ms = ev[0].elapsed_time(ev[1])
+                ms += w_ms
+                ess = effective_samples(torch.stack(series).cpu().numpy())
+                wins.append({"cycles": cyc + 1, "bpmf_kT": window_bpmf(run), "ess": ess, "gpu_ms": w_ms})
+                series = []
+                ev[0].record(stream)
+        arms[name] = {"cycles": n_cyc, "gpu_ms_per_cycle": ms / max(1, n_cyc), "windows": wins,
+                      "external_acceptance": float(run.ext_acc.sum().item()) / max(1, n_external * n_cyc * N_CHAINS)}
+        if name == "learned":
+            arms[name]["learned_acceptance"] = float(acc.sum().item()) / (R * n_learned * n_cyc)
+        del run
+    b_ref, src = profiled_bpmf_ref()
+    if b_ref is None:
+        late = [w["bpmf_kT"] for w in arms["learned"]["windows"]]
+        late = late[len(late) // 2:]
+        b_ref, src = float(np.mean(late)), "this run: mean of the learned arm's second-half windows"
+    out["reference"] = {"bpmf_kT": b_ref, "source": src}
+    for name, a in arms.items():
+        first = next((i for i, w in enumerate(a["windows"]) if abs(w["bpmf_kT"] - b_ref) <= criterion), None)
+        if first is None:
+            a["cycles_to_criterion"] = None
+            a["bpmf_eff_samples_per_s"] = 0.0
+        else:
+            done = a["windows"][first:]
+            a["cycles_to_criterion"] = a["windows"][first]["cycles"]
+            a["gpu_s_to_criterion"] = sum(w["gpu_ms"] for w in a["windows"][:first + 1]) * 1e-3
+            a["bpmf_eff_samples_per_s"] = sum(w["ess"] for w in done) / (sum(w["gpu_ms"] for w in done) * 1e-3)
+        a["final_abs_err_kT"] = abs(a["windows"][-1]["bpmf_kT"] - b_ref) if a["windows"] else None
+        out[name] = a
+    return out
+
+
 def oracle_cpu_baseline(sys_, n_rep=65536, n_threads=0):
     """The FP64 oracle as it stands on this host's cores: one HMC trial of 50 VV steps for a
     bounded sample of replicas spread over all states (about 10-30 s on a 16-core host)."""
@@ -350,6 +481,11 @@ def main():
         r = learned_vs_plain(ctx, sys_, stream, dev, target=N_STATES_BC + 28, cmp_cycles=20, train_iter=20)
         print(json.dumps({"learned_vs_plain": r}))
         return
+    if args.bpmf_only:
+        r = bpmf_convergence(ctx, sys_, stream, dev, paper_cycles=args.paper_cycles,
+                             learned_cycles=args.learned_cycles, window=args.bpmf_window)
+        print(json.dumps({"bpmf_eff_samples": r}))
+        return
     launches_per_step = 1 + len(legs) + 2 * len(legs)  # hmc, exchange per leg, evaluate + u_kn per leg
     for w in range(args.warmup):
         step(w)
@@ -440,6 +576,8 @@ def main():
         # the paper's own regime (alpha ~ 0.01), mid-leg, and the fully coupled end
         extra["learned_vs_plain"] = [learned_vs_plain(ctx, sys_, stream, dev, target=k) for k in
                                      (N_STATES_BC + 1, N_STATES_BC + 28, N_STATES_BC + N_STATES_CD - 1)]
+    if not args.no_bpmf and world == 1:
+        extra["bpmf_eff_samples"] = bpmf_convergence(ctx, sys_, stream, dev)
 
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,

@@ -33,30 +33,48 @@ class LearnedProposal:
         T = ctx.learned_ntorsions()
         self.T = T if n_torsions < 0 else min(T, n_torsions)
 
-    def train(self, x, comps, state: int, n_iter: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
+    def train(self, x, comps, state, n_iter: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
               pairs=None):
         """Adam on the mean negative log-density of moves between pairs of the samples
-        x [S][n_atoms][3] (float32, device) with components comps [S][4] at one state: random pairs,
-        or the given (I, J) index arrays (e.g. the same chain a few cycles apart).  Returns the loss
-        after each iteration."""
+        x [S][n_atoms][3] (float32, device) with components comps [S][4].  state: one state index
+        for all samples, or an array of S state indices (pairs are then drawn within a state).
+        Pairs: random, or the given (I, J) index arrays (e.g. the same chain a few cycles apart).
+        Returns the loss after each iteration."""
         S = x.shape[0]
         dev = x.device
         rng = np.random.default_rng(seed)
         if pairs is not None:
             PI = torch.as_tensor(np.asarray(pairs[0]), device=dev)
             PJ = torch.as_tensor(np.asarray(pairs[1]), device=dev)
-        st = torch.full((batch,), int(state), dtype=torch.int32, device=dev)
+        per_sample = np.ndim(state) > 0
+        if per_sample:
+            st_all = np.asarray(state, dtype=np.int32).ravel()
+            order = np.argsort(st_all, kind="stable")
+            counts = np.bincount(st_all)
+            starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+            st_dev = torch.from_numpy(st_all).to(dev)
+            order_dev = torch.from_numpy(order).to(dev)
+        else:
+            st = torch.full((batch,), int(state), dtype=torch.int32, device=dev)
         feat = torch.empty((batch, MLP_NFEAT), dtype=torch.float32, device=dev)
         delta = torch.empty((batch, MLP_DMAX), dtype=torch.float32, device=dev)
         losses = []
         D = 6 + self.T
         for _ in range(n_iter):
-            if pairs is None:
-                i = torch.from_numpy(rng.integers(0, S, size=batch)).to(dev)
-                j = torch.from_numpy(rng.integers(0, S, size=batch)).to(dev)
-            else:
+            if pairs is not None:
                 sel = torch.from_numpy(rng.integers(0, PI.numel(), size=batch)).to(dev)
                 i, j = PI[sel], PJ[sel]
+            elif per_sample:
+                ii = rng.integers(0, S, size=batch)
+                k = st_all[ii]
+                jj = starts[k] + (rng.random(batch) * counts[k]).astype(np.int64)
+                i = torch.from_numpy(ii).to(dev)
+                j = order_dev[torch.from_numpy(jj).to(dev)]
+            else:
+                i = torch.from_numpy(rng.integers(0, S, size=batch)).to(dev)
+                j = torch.from_numpy(rng.integers(0, S, size=batch)).to(dev)
+            if per_sample:
+                st = st_dev[i].contiguous()
             xi, xj = x[i].contiguous(), x[j].contiguous()
             self.ctx.learned_features(st, xi, comps[i].contiguous(), feat)
             self.ctx.pose_delta(xi, xj, delta)
