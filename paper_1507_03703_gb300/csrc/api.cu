@@ -360,6 +360,8 @@ algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, cons
   Y.off_inc = take(ninc);
   Y.words = w;
   if ((size_t)w * 4 > 120 * 1024) return fail(c, ALGDOCK_E_INVALID, "ligand_load: topology too large");
+  Y.off_pair = take(4 * na * na);
+  Y.words_pair = w;
   std::vector<uint32_t> blob(w, 0u);
   float* bf = (float*)blob.data();
   int32_t* bi = (int32_t*)blob.data();
@@ -396,6 +398,21 @@ algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, cons
       bf[Y.off_tor + 12 * ntor + 4 * t + n] = (float)sin(g);
     }
   }
+  // pair table: the Lorentz-Berthelot combination, the 1-4 scales and the exclusions folded into
+  // one record per ordered pair (FP64, rounded once); an excluded pair (and i == j) has zero
+  // coefficients and adds 1 to r^2 so that its arithmetic stays finite
+  for (int j = 0; j < na; ++j)
+    for (int i = 0; i < na; ++i) {
+      const int ty = ptype[(size_t)j * na + i];
+      const double s_lj = ty == 0 ? 1.0 : (ty == 1 ? 0.5 : 0.0);
+      const double s_el = ty == 0 ? 1.0 : (ty == 1 ? 1.0 / 1.2 : 0.0);
+      const double R = L->rstar[i] + L->rstar[j];
+      float* rec = bf + Y.off_pair + 4 * ((size_t)j * na + i);
+      rec[0] = ty == 2 ? 0.f : (float)(R * R);
+      rec[1] = (float)(12.0 * s_lj * sqrt(L->eps[i]) * sqrt(L->eps[j]));
+      rec[2] = (float)(kCoulomb * L->charge[i] * L->charge[j] * s_el);
+      rec[3] = ty == 2 ? 1.f : 0.f;
+    }
   int pos = 0;
   for (int i = 0; i < na; ++i) {
     bi[Y.off_inc_start + i] = pos;

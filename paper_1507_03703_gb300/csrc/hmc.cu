@@ -41,6 +41,7 @@ struct Lig {
   const float4* tor_s;
   const int* inc_start;
   const uint32_t* inc;  // slot indices
+  const float4* pair;   // [j][i] pair records (only where the table is staged)
 };
 
 __device__ inline Lig bind_ligand(const uint32_t* s, const LigandLayout& L) {
@@ -57,6 +58,7 @@ __device__ inline Lig bind_ligand(const uint32_t* s, const LigandLayout& L) {
   g.tor_s = (const float4*)(s + L.off_tor + 12 * L.ntor);
   g.inc_start = (const int*)(s + L.off_inc_start);
   g.inc = (const uint32_t*)(s + L.off_inc);
+  g.pair = (const float4*)(s + L.off_pair);
   return g;
 }
 
@@ -345,9 +347,71 @@ __device__ inline void nonbonded(const Lig& L, int na, const float4* xs, float (
   if (ENERGY) el += 0.5f * e2;
 }
 
+// Step 3 from the pair table: the same passes and lane layout as `nonbonded`, with each pair's
+// combined and scaled coefficients read as one record (R_ij^2, 12 eps_ij, 332 q_i q_j, guard)
+// instead of being formed from per-atom parameters and the pair type.
+template <int APL, bool ENERGY>
+__device__ inline void nonbonded_table(const Lig& L, int na, const float4* xs, float (&F)[APL][3], float& el) {
+  const int lane = threadIdx.x & 31;
+  float e2 = 0.f;
+#pragma unroll
+  for (int a = 0; a < APL; ++a) {
+    const int base = 32 * a;
+    const int m = na - base;
+    if (m <= 0) break;
+    const bool split = m <= 16;
+    const int il = split ? (lane & 15) : lane;
+    const int i = base + il;
+    const bool act = il < m;
+    int jb = 0, cnt = na, dir = 1;
+    if (split) {
+      const int h = (na + 1) >> 1;
+      jb = lane < 16 ? 0 : na - 1;
+      cnt = lane < 16 ? h : na - h;
+      dir = lane < 16 ? 1 : -1;
+    }
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    if (act) {
+      const float4 pi = xs[i];
+      const float4* rec = L.pair + (size_t)jb * na + i;
+      const float4* pj_ptr = xs + jb;
+      const int rstep = dir * na;
+      for (int jj = 0; jj < cnt; ++jj) {
+        const float4 pj = *pj_ptr;
+        const float4 t = *rec;
+        pj_ptr += dir;
+        rec += rstep;
+        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, t.w)));
+        const float inv_r = rsqrtf(r2);
+        const float inv_r2 = inv_r * inv_r;
+        const float s2 = t.x * inv_r2;
+        const float s6 = s2 * s2 * s2;
+        const float eel = t.z * inv_r;
+        const float fr = fmaf(t.y, fmaf(s6, s6, -s6), eel) * inv_r2;
+        fx = fmaf(fr, dx, fx);
+        fy = fmaf(fr, dy, fy);
+        fz = fmaf(fr, dz, fz);
+        if (ENERGY) e2 += fmaf(t.y * (1.f / 12.f), fmaf(s6, s6, -2.f * s6), eel);
+      }
+    }
+    if (split) {
+      fx += __shfl_xor_sync(kFull, fx, 16);
+      fy += __shfl_xor_sync(kFull, fy, 16);
+      fz += __shfl_xor_sync(kFull, fz, 16);
+    }
+    if (lane < m && (!split || lane < 16)) {
+      F[a][0] += fx;
+      F[a][1] += fy;
+      F[a][2] += fz;
+    }
+  }
+  if (ENERGY) el += 0.5f * e2;
+}
+
 // Forces on the lane's atoms (and, if ENERGY, the lane's partial energies).  xs holds all
 // positions (x, y, z, q); sf is the warp's bonded-slot scratch (3 * n_slots floats).
-template <int APL, bool ENERGY>
+template <int APL, bool ENERGY, bool TABLE = false>
 __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const GridDev& G, const float4* xs, float* sf,
                                 const float (&x)[APL][3], float (&F)[APL][3], float w_sg, float w_g, bool all_grids,
                                 Energies& en, int& outside) {
@@ -389,7 +453,8 @@ __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const Grid
       F[a][2] += sz[s];
     }
   }
-  nonbonded<APL, ENERGY>(L, na, xs, F, el);
+  if (TABLE) nonbonded_table<APL, ENERGY>(L, na, xs, F, el);
+  else nonbonded<APL, ENERGY>(L, na, xs, F, el);
   // restraint on the centre of mass
   mx = warp_sumf(mx);
   my = warp_sumf(my);
@@ -450,8 +515,8 @@ struct WarpSmem {
   float* sf;
 };
 template <int APL>
-__device__ inline WarpSmem warp_smem(uint32_t* smem, const LigandLayout& LL, int warp) {
-  uint32_t* p = smem + LL.words + warp * (4 * 32 * APL + scratch_words(LL));
+__device__ inline WarpSmem warp_smem(uint32_t* smem, int staged_words, const LigandLayout& LL, int warp) {
+  uint32_t* p = smem + staged_words + warp * (4 * 32 * APL + scratch_words(LL));
   return WarpSmem{(float4*)p, (float*)(p + 4 * 32 * APL)};
 }
 
@@ -474,16 +539,18 @@ struct HmcArgs {
   int64_t* counters;
 };
 
-template <int APL>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) hmc_kernel(const HmcArgs A) {
+// WPB warps per block; TABLE: the pair table is staged with the blob (16-warp blocks share it).
+template <int APL, int WPB, bool TABLE>
+__global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
   extern __shared__ __align__(16) uint32_t smem[];
-  stage_ligand(smem, A.blob, A.LL.words);
+  const int staged = TABLE ? A.LL.words_pair : A.LL.words;
+  stage_ligand(smem, A.blob, staged);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  const int64_t r = (int64_t)blockIdx.x * WPB + warp;
   if (r >= A.n_rep) return;
   const Lig L = bind_ligand(smem, A.LL);
-  const WarpSmem ws = warp_smem<APL>(smem, A.LL, warp);
+  const WarpSmem ws = warp_smem<APL>(smem, staged, A.LL, warp);
   float4* xs = ws.xs;
   const int na = A.LL.na;
   const int k = A.state_of[r];
@@ -536,7 +603,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) hmc_kernel(const HmcArgs 
   int outside = 0;
   Energies en;
   double c0[4], c1[4];
-  evaluate<APL, true>(A.LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
+  evaluate<APL, true, TABLE>(A.LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
   reduce_components(en, c0);
   const double K0 = 0.5 * kKineticToKcal * warp_sum((double)kin);
   for (int s = 0; s < A.n_steps; ++s) {
@@ -566,9 +633,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) hmc_kernel(const HmcArgs 
     }
     __syncwarp();
     if (s + 1 < A.n_steps) {
-      evaluate<APL, false>(A.LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, false, en, outside);
+      evaluate<APL, false, TABLE>(A.LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, false, en, outside);
     } else {
-      evaluate<APL, true>(A.LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
+      evaluate<APL, true, TABLE>(A.LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
       reduce_components(en, c1);
     }
 #pragma unroll
@@ -646,7 +713,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) eval_kernel(const EvalArg
   const int64_t n = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
   if (n >= A.N) return;
   const Lig L = bind_ligand(smem, A.LL);
-  const WarpSmem ws = warp_smem<APL>(smem, A.LL, warp);
+  const WarpSmem ws = warp_smem<APL>(smem, A.LL.words, A.LL, warp);
   const int na = A.LL.na;
   float w_sg = 0.f, w_g = 0.f;
   if (A.state_of) {
@@ -879,18 +946,21 @@ __global__ void ukn_kernel(const StateDev* __restrict__ states, int k_begin, int
 
 int atoms_per_lane(int na) { return na <= 32 ? 1 : (na <= 64 ? 2 : 3); }
 
-size_t block_smem(const LigandLayout& L, int apl) {
-  return ((size_t)L.words + (size_t)kWarpsPerBlock * (4 * 32 * apl + scratch_words(L))) * 4;
+size_t block_smem(const LigandLayout& L, int apl, int wpb = kWarpsPerBlock, bool table = false) {
+  return ((size_t)(table ? L.words_pair : L.words) + (size_t)wpb * (4 * 32 * apl + scratch_words(L))) * 4;
 }
+
+constexpr int kTableWarps = 16;  // warps per block of the pair-table HMC kernel (512 threads, 128 registers)
+constexpr size_t kMaxBlockSmem = 227 * 1024;
 
 template <typename Kernel, typename Args>
 cudaError_t launch_templated(Kernel k1, Kernel k2, Kernel k3, int apl, size_t smem, int64_t items, cudaStream_t s,
-                             const Args& A) {
+                             const Args& A, int wpb = kWarpsPerBlock) {
   Kernel k = apl == 1 ? k1 : (apl == 2 ? k2 : k3);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  k<<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(A);
+  const int64_t blocks = (items + wpb - 1) / wpb;
+  k<<<(unsigned)blocks, wpb * 32, smem, s>>>(A);
   return cudaGetLastError();
 }
 
@@ -903,7 +973,14 @@ cudaError_t launch_hmc(cudaStream_t s, const algdock_ctx& c, int64_t n_rep, cons
   HmcArgs A{c.grid, c.lig, c.d_blob, c.d_states, c.K, n_rep, state_of, x, comps, dH, acc, n_steps, seed,
             (uint32_t)cycle, rep_offset, counters};
   const int apl = atoms_per_lane(c.lig.na);
-  return launch_templated(hmc_kernel<1>, hmc_kernel<2>, hmc_kernel<3>, apl, block_smem(c.lig, apl), n_rep, s, A);
+  // the pair table where 16-warp blocks can stage it (up to 64 atoms with a small topology);
+  // otherwise the pair-type path in 4-warp blocks
+  const size_t tsmem = block_smem(c.lig, apl, kTableWarps, true);
+  if (apl <= 2 && tsmem <= kMaxBlockSmem)
+    return launch_templated(hmc_kernel<1, kTableWarps, true>, hmc_kernel<2, kTableWarps, true>,
+                            hmc_kernel<2, kTableWarps, true>, apl, tsmem, n_rep, s, A, kTableWarps);
+  return launch_templated(hmc_kernel<1, kWarpsPerBlock, false>, hmc_kernel<2, kWarpsPerBlock, false>,
+                          hmc_kernel<3, kWarpsPerBlock, false>, apl, block_smem(c.lig, apl), n_rep, s, A);
 }
 
 static cudaError_t launch_eval(cudaStream_t s, const algdock_ctx& c, int64_t N, const int32_t* state_of,
