@@ -525,3 +525,22 @@ def _external_moves(self, x, comps, state_of, n_moves, seed, cycle, rep_offset=0
 
 
 OracleSystem.external_moves = _external_moves
+
+
+# ------------------------------------------------------------------ equilibration detection
+def detect_equilibration(a, stride=1, n_cand=None):
+    """Candidates t0 = c * stride: (g of each tail [n_cand], best t0, its N_eff = (T - t0) / g)."""
+    L = _load()
+    if not getattr(L, "_equil", False):
+        L.oracle_detect_equilibration.argtypes = [C.c_int64, _d, C.c_int64, C.c_int, _d,
+                                                  C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+        L._equil = True
+    a = _f64(a).ravel()
+    T = a.size
+    if n_cand is None:
+        n_cand = (T - 2) // stride + 1
+    g = np.zeros(n_cand)
+    t0 = C.c_int64(0)
+    ne = C.c_double(0.0)
+    L.oracle_detect_equilibration(T, a, int(stride), int(n_cand), g, C.byref(t0), C.byref(ne))
+    return g, int(t0.value), float(ne.value)

@@ -29,6 +29,7 @@
  *   learned proposal       an extension of "Sampling" (not in the paper): network, mixture, move
  *   external_moves         "Sampling": external-coordinate MCMC (random rotation about the centre
  *                          of mass, Gaussian translation, Metropolis) for states with alpha < 0.01
+ *   detect_equilibration   "Equilibration and production": the start that maximises N / g
  *
  * Parity unpinned: nothing in this file is left without a pin; see the tests.
  */
@@ -1435,4 +1436,29 @@ void oracle_external_moves(const oracle_system* s, int64_t n_rep, const int* sta
     }
   }
   free(y);
+}
+
+/* ---------------------------------------------------------------- equilibration detection
+ * "Equilibration and production": the statistical inefficiency g of a series measures how many
+ * correlated samples make one independent one.  Automated detection (Chodera 2016, "A simple
+ * method for automated equilibration detection in molecular simulations") discards the start t0
+ * that maximises the effective sample count of the rest, N_eff(t0) = (T - t0) / g(a[t0:]).
+ * Candidates t0 = c * stride, c < n_cand; g_out[c] receives g of each tail; the best t0 (the
+ * earliest on ties) and its N_eff are returned. */
+void oracle_detect_equilibration(int64_t T, const double* a, int64_t stride, int n_cand, double* g_out,
+                                 int64_t* t0_best, double* neff_best) {
+  double best = -1.0;
+  int64_t bt = 0;
+  for (int c = 0; c < n_cand; ++c) {
+    int64_t t0 = (int64_t)c * stride;
+    double g = oracle_statistical_inefficiency(T - t0, a + t0);
+    g_out[c] = g;
+    double neff = (double)(T - t0) / g;
+    if (neff > best) {
+      best = neff;
+      bt = t0;
+    }
+  }
+  *t0_best = bt;
+  *neff_best = best;
 }
