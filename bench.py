@@ -309,7 +309,7 @@ def bpmf_convergence(ctx, sys_, stream, dev, paper_cycles=8000, learned_cycles=8
         for li in range(len(legs)):
             run.config_of[li].copy_(pre.config_of[li])
         acc = torch.zeros(R, dtype=torch.int32, device=dev)
-        wins, series, ms = [], [], 0.0
+        wins, series, full, ms = [], [], [], 0.0
         torch.cuda.synchronize()
         ev[0].record(stream)
         for cyc in range(n_cyc):
@@ -321,6 +321,7 @@ def bpmf_convergence(ctx, sys_, stream, dev, paper_cycles=8000, learned_cycles=8
             if cyc % 10 == 0:
                 run.history.append(run.comps.clone())
             series.append(_target_psi_g(run, 1, N_STATES_CD - 1))
+            full.append(series[-1])
             if (cyc + 1) % window == 0:
                 ev[1].record(stream)
                 torch.cuda.synchronize()
@@ -330,7 +331,11 @@ def bpmf_convergence(ctx, sys_, stream, dev, paper_cycles=8000, learned_cycles=8
                 wins.append({"cycles": cyc + 1, "bpmf_kT": window_bpmf(run), "ess": ess, "gpu_ms": w_ms})
                 series = []
                 ev[0].record(stream)
+        # automated equilibration detection on each chain's target-state series (the kernel)
+        _, t0s, neffs = ctx.detect_equilibration(torch.stack(full), stride=max(1, n_cyc // 40))
         arms[name] = {"cycles": n_cyc, "gpu_ms_per_cycle": ms / max(1, n_cyc), "windows": wins,
+                      "equilibration_cycles_median": float(t0s.double().median().item()),
+                      "n_eff_after_equilibration": float(neffs.sum().item()),
                       "external_acceptance": float(run.ext_acc.sum().item()) / max(1, n_external * n_cyc * N_CHAINS)}
         if name == "learned":
             arms[name]["learned_acceptance"] = float(acc.sum().item()) / (R * n_learned * n_cyc)

@@ -219,6 +219,22 @@ algdock_status algdock_reduced_energies(algdock_ctx* ctx, int64_t N, const float
 algdock_status algdock_mbar(algdock_ctx* ctx, int32_t K, int64_t N, const double* u_kn, const int64_t* N_k,
                             double tol, int32_t max_iter, int32_t precision_mode, double* f_k, int32_t* iters);
 
+
+/* Automated equilibration detection ("Equilibration and production": statistical inefficiency;
+ * the method of Chodera 2016).  For each of S series of length T (series s at a[t * S + s], a
+ * device double array, time-major as a history of per-chain values) and each candidate start
+ * t0 = c * stride (c < n_cand), the statistical inefficiency of the tail a[t0:],
+ *   g = 1 + 2 sum_{t >= 1} (1 - t/N) C(t), C(t) = sum_i (a_i - mu)(a_{i+t} - mu) / ((N - t) var),
+ * summed until C(t) first drops to <= 0 (N = T - t0; mu, var of the tail), goes to g [S][n_cand]
+ * (device double).  Per series, the t0 that maximises N_eff = N / g (the earliest on ties) goes
+ * to t0_best [S] (device int64, may be NULL) and that N_eff to neff_best [S] (device double, may
+ * be NULL).  Mean and variance are FP64, the lag products FP32 with FP64 sums across lanes.
+ * Errors: E_INVALID unless 2 <= T <= 50000, 1 <= S <= 65535, stride >= 1, n_cand >= 1 and
+ * (n_cand - 1) * stride <= T - 2, or for non-device pointers. */
+algdock_status algdock_detect_equilibration(algdock_ctx* ctx, int64_t T, int64_t S, const double* series,
+                                            int64_t stride, int32_t n_cand, double* g, int64_t* t0_best,
+                                            double* neff_best);
+
 /* ---------------------------------------------------------------- learned pose proposal
  * An extension of the paper's external-coordinate moves ("Sampling": a random rotation about the
  * centre of mass and a Gaussian translation, Metropolis-tested): a network proposes rigid-body and

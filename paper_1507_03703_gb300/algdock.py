@@ -30,7 +30,7 @@ EXPORTS = [
     "algdock_hmc_cycle", "algdock_energy_force", "algdock_exchange", "algdock_reduced_energies", "algdock_mbar",
     "algdock_mbar_noalloc", "algdock_learned_ntorsions", "algdock_learned_features", "algdock_pose_delta",
     "algdock_mlp_forward", "algdock_mlp_grad", "algdock_mlp_adam", "algdock_propose_learned",
-    "algdock_external_moves",
+    "algdock_external_moves", "algdock_detect_equilibration",
 ]
 
 ALPHA_MAX_EXTERNAL = 0.01     # external-coordinate moves only below this alpha ("Sampling")
@@ -122,6 +122,7 @@ def load_library(path: str = LIB_PATH):
         "algdock_hmc_cycle": ([vp, i64, vp, vp, vp, vp, vp, i32, u64, u64, i64, vp], C.c_int),
         "algdock_energy_force": ([vp, i64, vp, vp, vp, vp], C.c_int),
         "algdock_external_moves": ([vp, i64, vp, vp, vp, i32, dbl, dbl, u64, u64, i64, vp, vp], C.c_int),
+        "algdock_detect_equilibration": ([vp, i64, i64, vp, i64, i32, vp, vp, vp], C.c_int),
         "algdock_exchange": ([vp, i32, i32, i32, vp, vp, vp, i32, i32, u64, u64, i64, vp, vp], C.c_int),
         "algdock_reduced_energies": ([vp, i64, vp, vp, i32, i32, vp], C.c_int),
         "algdock_mbar": ([vp, i32, i64, vp, vp, dbl, i32, i32, vp, C.POINTER(i32)], C.c_int),
@@ -318,6 +319,24 @@ class Context:
             self.h, int(state_of.numel()), _dev(state_of, torch.int32, "state_of"), _dev(x, torch.float32, "x"),
             _dev(comps, torch.float64, "comps"), int(n_moves), float(alpha_max), float(sigma), int(seed), int(cycle),
             int(rep_offset), _dev(accepted, torch.int32, "accepted"), _dev(counters, torch.int64, "counters")))
+
+    def detect_equilibration(self, series, stride=1, n_cand=None, g=None, t0_best=None, neff_best=None):
+        """series [T][S] float64 (device): per series the statistical inefficiency of each candidate
+        tail (g [S][n_cand]), the start maximising N/g (t0_best [S] int64) and that N/g.  Returns
+        (g, t0_best, neff_best) as device tensors."""
+        import torch
+        T, S = int(series.shape[0]), int(series.numel() // max(1, series.shape[0]))
+        if n_cand is None:
+            n_cand = (T - 2) // int(stride) + 1
+        dev = series.device
+        g = torch.empty((S, n_cand), dtype=torch.float64, device=dev) if g is None else g
+        t0_best = torch.empty(S, dtype=torch.int64, device=dev) if t0_best is None else t0_best
+        neff_best = torch.empty(S, dtype=torch.float64, device=dev) if neff_best is None else neff_best
+        self._check(self._L.algdock_detect_equilibration(
+            self.h, T, S, _dev(series, torch.float64, "series"), int(stride), int(n_cand),
+            _dev(g, torch.float64, "g"), _dev(t0_best, torch.int64, "t0_best"),
+            _dev(neff_best, torch.float64, "neff_best")))
+        return g, t0_best, neff_best
 
     def energy_force(self, state_of, x, force, comps=None):
         import torch

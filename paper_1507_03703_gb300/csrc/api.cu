@@ -515,6 +515,23 @@ algdock_status algdock_external_moves(algdock_ctx* c, int64_t n_rep, const int32
   ALGDOCK_CATCH(c)
 }
 
+algdock_status algdock_detect_equilibration(algdock_ctx* c, int64_t T, int64_t S, const double* series,
+                                            int64_t stride, int32_t n_cand, double* g, int64_t* t0_best,
+                                            double* neff_best) {
+  ALGDOCK_TRY(c)
+  if (T < 2 || T > 50000 || S < 1 || S > 65535 || stride < 1 || n_cand < 1 || (int64_t)(n_cand - 1) * stride > T - 2)
+    return fail(c, ALGDOCK_E_INVALID, "detect_equilibration: need 2 <= T <= 50000, 1 <= S <= 65535, stride >= 1, "
+                                      "n_cand >= 1, (n_cand - 1) * stride <= T - 2");
+  if (!is_device_ptr(series) || !is_device_ptr(g) || (t0_best && !is_device_ptr(t0_best)) ||
+      (neff_best && !is_device_ptr(neff_best)))
+    return fail(c, ALGDOCK_E_INVALID, "detect_equilibration: arrays must be device pointers");
+  Device dg(c->device);
+  cudaError_t e = launch_equilibration(c->stream, T, S, series, stride, n_cand, g, t0_best, neff_best);
+  if (e != cudaSuccess) return cuda_fail(c, e, "detect_equilibration");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
 algdock_status algdock_energy_force(algdock_ctx* c, int64_t N, const int32_t* state_of, const float* x, float* force,
                                     double* comps) {
   ALGDOCK_TRY(c)

@@ -149,6 +149,9 @@ cudaError_t launch_evaluate(cudaStream_t s, const algdock_ctx& c, int64_t N, con
 cudaError_t launch_external(cudaStream_t s, const algdock_ctx& c, int64_t n_rep, const int32_t* state_of, float* x,
                             double* comps, int n_moves, double alpha_max, float sigma, uint64_t seed, uint64_t cycle,
                             int64_t rep_offset, int32_t* accepted, int64_t* counters);
+size_t equilibration_smem(int64_t T);
+cudaError_t launch_equilibration(cudaStream_t st, int64_t T, int64_t S, const double* a, int64_t stride, int n_cand,
+                                 double* g, int64_t* t0_best, double* neff_best);
 cudaError_t launch_energy_force(cudaStream_t s, const algdock_ctx& c, int64_t N, const int32_t* state_of,
                                 const float* x, float* force, double* comps);
 cudaError_t launch_ukn(cudaStream_t s, const algdock_ctx& c, int64_t N, const double* comps, int k_begin,
