@@ -566,7 +566,7 @@ def main():
         u = torch.empty((len(T), N), dtype=torch.float64, device=dev)
         ctx.reduced_energies(N, comps=comps_hist.reshape(N, 4), k_begin=0, k_count=len(T), u_kn=u)
         N_k = np.full(len(T), N // len(T), dtype=np.int64)
-        for mode, key in ((0, "fp64"), (1, "fp32exp")):
+        for mode, key in ((0, "fp64"), (1, "fp32exp"), (2, "fp32")):
             ctx.mbar(u, N_k, tol=1e-300, max_iter=2, precision_mode=mode, raise_on_nonconvergence=False)
             torch.cuda.synchronize()
             t = time.perf_counter()

@@ -214,7 +214,10 @@ algdock_status algdock_reduced_energies(algdock_ctx* ctx, int64_t N, const float
  *   f_i <- -ln sum_n exp(-u_in) / sum_k N_k exp(f_k - u_kn)
  * until max_i |change| < tol or max_iter iterations.  u_kn [K][N] double (device), N_k [K] int64
  * (host).  precision_mode 0: FP64 throughout; 1: exponentials in FP32 of FP64 arguments, sums in
- * FP64.  f_k [K] (host) and iters (host) receive the result.  Synchronises.  Returns
+ * FP64; 2: each sample's column shifted by its minimum (FP64, exact in the result) and stored as
+ * FP32, then FP32 arguments, exponentials and Kahan-compensated sums, FP64 only where partial sums
+ * meet (K <= 16384; extra scratch K*N*4 bytes).  f_k [K] (host) and iters (host) receive the
+ * result.  Synchronises.  Returns
  * ALGDOCK_E_NOT_CONVERGED (with the last iterate in f_k) if max_iter is reached. */
 algdock_status algdock_mbar(algdock_ctx* ctx, int32_t K, int64_t N, const double* u_kn, const int64_t* N_k,
                             double tol, int32_t max_iter, int32_t precision_mode, double* f_k, int32_t* iters);

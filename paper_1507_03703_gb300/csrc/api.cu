@@ -11,6 +11,7 @@
 
 namespace algdock {
 size_t mbar_scratch_bytes(int K, int64_t N);
+size_t mbar_scratch_bytes_mode(int K, int64_t N, int mode);
 int mbar_run(cudaStream_t s, void* scratch, int K, int64_t N, const double* u_kn, const int64_t* Nk_host,
              double tol, int max_iter, int mode, double* f_host, int* iters, int* h_flag, cudaError_t* err);
 }  // namespace algdock
@@ -726,8 +727,9 @@ algdock_status algdock_mbar(algdock_ctx* c, int32_t K, int64_t N, const double* 
                             int32_t max_iter, int32_t precision_mode, double* f_k, int32_t* iters) {
   ALGDOCK_TRY(c)
   if (K < 1 || N < 1 || !u_kn || !N_k || !f_k || !iters || max_iter < 1 || !(tol > 0) ||
-      (precision_mode != 0 && precision_mode != 1))
+      precision_mode < 0 || precision_mode > 2)
     return fail(c, ALGDOCK_E_INVALID, "mbar: bad arguments");
+  if (precision_mode == 2 && K > 16384) return fail(c, ALGDOCK_E_INVALID, "mbar: precision mode 2 takes K <= 16384");
   if (!is_device_ptr(u_kn)) return fail(c, ALGDOCK_E_INVALID, "mbar: u_kn must be a device pointer");
   int64_t total = 0;
   for (int k = 0; k < K; ++k) {
@@ -736,7 +738,7 @@ algdock_status algdock_mbar(algdock_ctx* c, int32_t K, int64_t N, const double* 
   }
   if (total != N) return fail(c, ALGDOCK_E_INVALID, "mbar: sum of N_k must equal N");
   Device g(c->device);
-  const size_t need = mbar_scratch_bytes(K, N);
+  const size_t need = mbar_scratch_bytes_mode(K, N, precision_mode);
   if (need > c->mbar_bytes) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "mbar");

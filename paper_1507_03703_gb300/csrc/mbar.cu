@@ -120,6 +120,78 @@ __global__ void finalize(int K, int n_chunks, const double2* __restrict__ part, 
   }
 }
 
+// ---------------------------------------------------------------- precision mode 2: FP32
+// Every sample's column of u_kn is shifted once by its minimum s_n (in FP64) and stored as FP32,
+// w_kn = u_kn - s_n.  The shift cancels exactly: log D_n and the state sums change by -s_n and +s_n
+// in turn.  The iterations then run in FP32 (arguments, exponentials, Kahan-compensated sums),
+// with FP64 only where the per-thread partial sums meet.  That halves the bytes read per
+// iteration and removes FP64 work from the inner loops.
+__global__ void shift_columns(int K, int64_t N, const double* __restrict__ u, float* w) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double m = INFINITY;
+  for (int k = 0; k < K; ++k) m = fmin(m, u[(int64_t)k * N + n]);
+  if (!isfinite(m)) m = 0.0;
+  for (int k = 0; k < K; ++k) w[(int64_t)k * N + n] = (float)(u[(int64_t)k * N + n] - m);
+}
+
+// Online log-sum-exp in FP32, value m + log(s - c) with the Kahan compensation c.
+struct LseF {
+  float m, s, c;
+};
+__device__ inline void lsef_add(LseF& a, float x) {
+  if (x == -INFINITY) return;
+  if (x <= a.m) {
+    const float y = __expf(x - a.m) - a.c;
+    const float t = a.s + y;
+    a.c = (t - a.s) - y;
+    a.s = t;
+  } else {
+    const float r = a.m == -INFINITY ? 0.f : __expf(a.m - x);
+    a.s = a.s * r + 1.f;
+    a.c *= r;
+    a.m = x;
+  }
+}
+
+__global__ void log_denominators_f32(int K, int64_t N, const float* __restrict__ w, const double* __restrict__ logNk,
+                                     const double* __restrict__ f, float* logD, const MbarState* st) {
+  if (st->converged) return;
+  extern __shared__ float g_k[];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) g_k[k] = (float)(logNk[k] + f[k]);
+  __syncthreads();
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  LseF a{-INFINITY, 0.f, 0.f};
+  for (int k = 0; k < K; ++k) lsef_add(a, g_k[k] - w[(int64_t)k * N + n]);
+  logD[n] = a.m + logf(a.s - a.c);
+}
+
+__global__ void __launch_bounds__(kPartialThreads) state_partials_f32(int64_t N, const float* __restrict__ w,
+                                                                      const float* __restrict__ logD, double2* part,
+                                                                      int n_chunks, const MbarState* st) {
+  if (st->converged) return;
+  const int i = blockIdx.y, chunk = blockIdx.x;
+  const int64_t begin = (int64_t)chunk * kChunk;
+  const int64_t end = min(N, begin + kChunk);
+  LseF a{-INFINITY, 0.f, 0.f};
+  const float* wi = w + (int64_t)i * N;
+  for (int64_t n = begin + threadIdx.x; n < end; n += blockDim.x) lsef_add(a, -wi[n] - logD[n]);
+  __shared__ double sm[kPartialThreads], ss[kPartialThreads];
+  sm[threadIdx.x] = a.m == -INFINITY ? -INFINITY : (double)a.m;
+  ss[threadIdx.x] = (double)a.s - (double)a.c;
+  __syncthreads();
+  for (int v = blockDim.x / 2; v > 0; v >>= 1) {
+    if (threadIdx.x < v) {
+      const Lse r = lse_merge(Lse{sm[threadIdx.x], ss[threadIdx.x]}, Lse{sm[threadIdx.x + v], ss[threadIdx.x + v]});
+      sm[threadIdx.x] = r.m;
+      ss[threadIdx.x] = r.s;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(int64_t)i * n_chunks + chunk] = make_double2(sm[0], ss[0]);
+}
+
 __global__ void init_state(int K, const int64_t* Nk, double* logNk, double* f, MbarState* st) {
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     logNk[k] = Nk[k] > 0 ? log((double)Nk[k]) : -INFINITY;
@@ -134,9 +206,13 @@ __global__ void init_state(int K, const int64_t* Nk, double* logNk, double* f, M
 }  // namespace
 
 // Scratch layout (bytes): MbarState | logNk[K] | f[K] | fnew[K] | Nk[K] (int64) | part[K][n_chunks] | logD[N]
+// (double; float in mode 2), then in mode 2 the shifted FP32 copy w[K][N] (256-byte aligned).
 size_t mbar_scratch_bytes(int K, int64_t N) {
   const int64_t n_chunks = (N + kChunk - 1) / kChunk;
   return 64 + 4 * (size_t)K * 8 + (size_t)K * n_chunks * 16 + (size_t)N * 8 + 256;
+}
+size_t mbar_scratch_bytes_mode(int K, int64_t N, int mode) {
+  return mbar_scratch_bytes(K, N) + (mode == 2 ? (size_t)K * N * sizeof(float) + 256 : 0);
 }
 
 // Runs the solver on caller-provided scratch (mbar_scratch_bytes(K, N) bytes, 256-byte aligned).
@@ -159,13 +235,27 @@ int mbar_run(cudaStream_t s, void* scratch, int K, int64_t N, const double* u_kn
   const int threads = 256;
   const unsigned blocks_n = (unsigned)((N + threads - 1) / threads);
   const dim3 grid_p((unsigned)n_chunks, (unsigned)K);
+  float* w32 = nullptr;
+  if (mode == 2) {
+    const size_t off = ((size_t)((char*)(logD + N) - (char*)scratch) + 255) & ~(size_t)255;
+    w32 = (float*)((char*)scratch + off);
+    shift_columns<<<blocks_n, threads, 0, s>>>(K, N, u_kn, w32);
+    e = cudaFuncSetAttribute(log_denominators_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(K * sizeof(float)));
+    if (e != cudaSuccess) { *err = e; return -1; }
+  }
   int done = 0;
   int issued = 0;
   int batch = 4;
   while (!done) {
     for (int b = 0; b < batch && issued < max_iter; ++b, ++issued) {
-      log_denominators<<<blocks_n, threads, 0, s>>>(K, N, u_kn, logNk, f, logD, st, mode);
-      state_partials<<<grid_p, kPartialThreads, 0, s>>>(N, u_kn, logD, part, (int)n_chunks, st, mode);
+      if (mode == 2) {
+        log_denominators_f32<<<blocks_n, threads, K * sizeof(float), s>>>(K, N, w32, logNk, f, (float*)logD, st);
+        state_partials_f32<<<grid_p, kPartialThreads, 0, s>>>(N, w32, (const float*)logD, part, (int)n_chunks, st);
+      } else {
+        log_denominators<<<blocks_n, threads, 0, s>>>(K, N, u_kn, logNk, f, logD, st, mode);
+        state_partials<<<grid_p, kPartialThreads, 0, s>>>(N, u_kn, logD, part, (int)n_chunks, st, mode);
+      }
       finalize<<<1, 256, 0, s>>>(K, (int)n_chunks, part, f, fnew, st, tol, max_iter);
     }
     e = cudaGetLastError();

@@ -154,3 +154,46 @@ def test_forces_paper_scale_sampled(paper_scale):
     states[:4] = [0, 31, 32 + 48, K - 1]
     w_sg, w_g, _ = osys.state_weights()
     _check_forces(ctx, osys, x, states, w_sg, w_g)
+
+
+def test_precision_study_paper_scale(paper_scale, capsys):
+    """The precision study of the FP32 path at paper scale (FP32 lattices, FP32 force terms, FP64
+    sums and decisions) against the FP64 oracle on the same FP32 node values, per quantity: force
+    relative error, each energy component in kcal/mol, and the energy change of 50-step HMC
+    trials.  The measured figures are printed (pytest -s) and bounded here."""
+    sys_, g32, T, alpha, dt, ctx, osys = paper_scale
+    K = len(T)
+    R = 64
+    x = configurations(sys_, R, seed=16, jitter=0.1)
+    states = (np.arange(R) * 2) % K
+    w_sg, w_g, _ = osys.state_weights()
+    xd = torch.from_numpy(x).cuda()
+    sd = torch.from_numpy(states.astype(np.int32)).cuda()
+    F = torch.empty_like(xd)
+    comps = torch.empty((R, 4), dtype=torch.float64, device="cuda")
+    ctx.energy_force(sd, xd, F, comps)
+    dH = torch.empty(R, dtype=torch.float64, device="cuda")
+    xh = xd.clone()
+    ch = torch.empty_like(comps)
+    ctx.hmc_cycle(sd, xh, ch, dH=dH, n_steps=50, seed=17, cycle=0)
+    torch.cuda.synchronize()
+    F, comps, dH = F.cpu().numpy().astype(np.float64), comps.cpu().numpy(), dH.cpu().numpy()
+    _, _, dH_o, _, _ = osys.hmc(x.astype(np.float64), states, 50, 17, 0)
+    frel, cerr, cref = [], [], []
+    for n in range(R):
+        k = states[n]
+        c_o, F_o = osys.energy_force(x[n].astype(np.float64), w_sg[k], w_g[k])
+        frel.append(np.linalg.norm(F[n] - F_o) / np.linalg.norm(F_o))
+        cerr.append(np.abs(comps[n] - c_o))
+        cref.append(np.abs(c_o))
+    frel, cerr, cref = np.array(frel), np.array(cerr), np.array(cref)
+    herr = np.abs(dH - dH_o)
+    with capsys.disabled():
+        print("\nprecision (FP32 path vs FP64 oracle, %d replicas, paper scale):" % R)
+        print("  force rel. error: median %.2e, max %.2e" % (np.median(frel), frel.max()))
+        for i, name in enumerate(("U_L", "U_I", "Psi_sg", "Psi_g")):
+            print("  %s abs. error (kcal/mol): median %.2e, max %.2e" % (name, np.median(cerr[:, i]), cerr[:, i].max()))
+        print("  dH of 50-step trials (kcal/mol): median %.2e, max %.2e" % (np.median(herr), herr.max()))
+    assert frel.max() < 1e-5
+    assert np.all(cerr <= 1e-5 * np.maximum(cref, 1.0) + 1e-4)
+    assert np.median(herr) < 1e-2

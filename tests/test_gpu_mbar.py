@@ -40,6 +40,16 @@ def test_mbar_fp32_exponentials(ctx):
     assert np.max(np.abs(f - f_o)) < 2e-6
 
 
+def test_mbar_fp32_compensated(ctx):
+    """Precision mode 2: columns shifted by their minimum in FP64 (exact in the result), then FP32
+    arguments, exponentials and Kahan-compensated sums.  The arguments carry FP32 rounding of
+    values of a few kT (~1e-7 kT each), so f agrees with the FP64 oracle to well within 1e-4 kT."""
+    u, N_k = _ukn(6, 4000, seed=6)
+    f_o, _ = oracle.mbar(u, N_k, tol=1e-10)
+    f, it = ctx.mbar(torch.from_numpy(u).cuda(), N_k, tol=1e-9, max_iter=10000, precision_mode=2)
+    assert np.max(np.abs(f - f_o)) < 1e-4
+
+
 def test_mbar_unsampled_states_and_nonconvergence(ctx):
     from paper_1507_03703_gb300.algdock import AlgdockError, E_NOT_CONVERGED
     u, N_k = _ukn(5, 1000, seed=9)
@@ -63,3 +73,47 @@ def test_mbar_identical_states(ctx):
     u = np.tile(row, (3, 1))
     f, it = ctx.mbar(torch.from_numpy(u).cuda(), np.array([200, 0, 500]), tol=1e-12)
     assert np.allclose(f, 0.0, atol=1e-12)
+
+
+def test_mbar_precision_study_K256_N1e6(ctx, capsys):
+    """MBAR at K = 256 states and N = 1e6 samples (harmonic wells in 2-D, exact samples built on
+    the device): the FP64 mode against the closed form f_k = -ln(2 pi / (beta k_k)) (relative to
+    state 0) within the statistical error, and the FP32-exponential mode against the FP64 mode.
+    Prints the errors and the iteration rates (pytest -s)."""
+    import time
+    K, Nper, D = 256, 3907, 2
+    g = torch.Generator(device="cuda").manual_seed(31)
+    bk = torch.rand(K, device="cuda", dtype=torch.float64, generator=g) * 3.5 + 0.5
+    mu = torch.rand((K, D), device="cuda", dtype=torch.float64, generator=g) * 0.6 - 0.3
+    x = (mu[:, None, :] + torch.randn((K, Nper, D), device="cuda", dtype=torch.float64, generator=g)
+         / torch.sqrt(bk)[:, None, None]).reshape(-1, D)
+    N = x.shape[0]
+    u = torch.empty((K, N), device="cuda", dtype=torch.float64)
+    for k in range(K):
+        u[k] = 0.5 * bk[k] * ((x - mu[k]) ** 2).sum(-1)
+    N_k = np.full(K, Nper, dtype=np.int64)
+    exact = -(D / 2) * np.log(2 * np.pi / bk.cpu().numpy())
+    exact -= exact[0]
+    t = time.perf_counter()
+    f64, it64 = ctx.mbar(u, N_k, tol=1e-9, max_iter=20000, precision_mode=0)
+    t64 = (time.perf_counter() - t) / it64
+    t = time.perf_counter()
+    f32, it32 = ctx.mbar(u, N_k, tol=1e-9, max_iter=20000, precision_mode=1)
+    t32 = (time.perf_counter() - t) / it32
+    ctx.mbar(u, N_k, tol=1e-9, max_iter=2, precision_mode=2, raise_on_nonconvergence=False)  # scratch
+    t = time.perf_counter()
+    fc, itc = ctx.mbar(u, N_k, tol=1e-9, max_iter=20000, precision_mode=2)
+    tc = (time.perf_counter() - t) / itc
+    err = np.abs(f64 - exact)
+    d = np.abs(f32 - f64)
+    dc = np.abs(fc - f64)
+    with capsys.disabled():
+        print("\nMBAR precision, K = %d, N = %d:" % (K, N))
+        print("  FP64 mode vs closed form: max %.3f kT, rms %.3f kT (%d iterations, %.2f ms each)"
+              % (err.max(), np.sqrt((err ** 2).mean()), it64, 1e3 * t64))
+        print("  FP32 exponentials vs FP64: max %.2e kT (%d iterations, %.2f ms each)" % (d.max(), it32, 1e3 * t32))
+        print("  FP32 compensated vs FP64: max %.2e kT (%d iterations, %.2f ms each, incl. the shift)"
+              % (dc.max(), itc, 1e3 * tc))
+    assert err.max() < 0.1
+    assert d.max() < 1e-4
+    assert dc.max() < 1e-3
