@@ -544,3 +544,160 @@ def detect_equilibration(a, stride=1, n_cand=None):
     ne = C.c_double(0.0)
     L.oracle_detect_equilibration(T, a, int(stride), int(n_cand), g, C.byref(t0), C.byref(ne))
     return g, int(t0.value), float(ne.value)
+
+
+# ------------------------------------------------------------------ protocol initialization
+def _protocol_sigs(L):
+    if getattr(L, "_protocol", False):
+        return
+    L.oracle_system_set_states.argtypes = [C.c_void_p, C.c_int, _d, _d, _d]
+    L.oracle_state_statistics.argtypes = [C.c_void_p, C.c_int64, _d, C.c_int, _d]
+    L.oracle_next_temperature.argtypes = [C.c_double] * 4
+    L.oracle_next_temperature.restype = C.c_double
+    L.oracle_next_alpha.argtypes = [C.c_double] * 7
+    L.oracle_next_alpha.restype = C.c_double
+    L.oracle_resample.argtypes = [C.c_int64, _d, C.c_int, C.c_uint64, C.c_uint32, np.ctypeslib.ndpointer(
+        dtype=np.int64, flags="C_CONTIGUOUS")]
+    L.oracle_mean_pacc.argtypes = [C.c_void_p, C.c_int64, _d, _d, C.c_int, C.c_int]
+    L.oracle_mean_pacc.restype = C.c_double
+    L.oracle_adapt_dt.argtypes = [C.c_double, C.c_double]
+    L.oracle_adapt_dt.restype = C.c_double
+    L._protocol = True
+
+
+def next_temperature(T, sigma_U, speed, T_end=600.0):
+    L = _load()
+    _protocol_sigs(L)
+    return L.oracle_next_temperature(float(T), float(sigma_U), float(speed), float(T_end))
+
+
+def next_alpha(alpha, sigma_sg, sigma_g, sigma_u, speed, T_T=300.0, T_H=600.0):
+    L = _load()
+    _protocol_sigs(L)
+    return L.oracle_next_alpha(float(alpha), float(sigma_sg), float(sigma_g), float(sigma_u), float(speed),
+                               float(T_T), float(T_H))
+
+
+def resample(logw, n_out, seed, ctr):
+    """Indices of n_out importance-resampled draws (weights exp(logw))."""
+    L = _load()
+    _protocol_sigs(L)
+    logw = _f64(logw).ravel()
+    idx = np.zeros(int(n_out), dtype=np.int64)
+    L.oracle_resample(logw.size, logw, int(n_out), int(seed), int(ctr) & 0xFFFFFFFF, idx)
+    return idx
+
+
+def adapt_dt(dt, acc):
+    L = _load()
+    _protocol_sigs(L)
+    return L.oracle_adapt_dt(float(dt), float(acc))
+
+
+def _set_states(self, T, alpha, dt):
+    _protocol_sigs(self._L)
+    self.T, self.alpha, self.dt = _f64(T), _f64(alpha), _f64(dt)
+    self.K = int(self.T.size)
+    self._L.oracle_system_set_states(self.h, self.K, self.T, self.alpha, self.dt)
+
+
+def _state_statistics(self, comps, k):
+    """{sigma[U_L + U_I], sigma[Psi_sg], sigma[Psi_g], sigma[u_k]} over the samples comps [n][4]."""
+    _protocol_sigs(self._L)
+    c = _f64(comps).reshape(-1, 4)
+    out = np.zeros(4)
+    self._L.oracle_state_statistics(self.h, c.shape[0], c, int(k), out)
+    return out
+
+
+def _mean_pacc(self, comps_a, comps_b, ka, kb):
+    _protocol_sigs(self._L)
+    a, b = _f64(comps_a).reshape(-1, 4), _f64(comps_b).reshape(-1, 4)
+    return self._L.oracle_mean_pacc(self.h, a.shape[0], a, b, int(ka), int(kb))
+
+
+OracleSystem.set_states = _set_states
+OracleSystem.state_statistics = _state_statistics
+OracleSystem.mean_pacc = _mean_pacc
+
+
+def _sample_state(osys, k, seeds, n_trials, n_steps, seed, cycle0, max_attempts=20):
+    """Sampling and adaptation at state k: n_trials HMC trials from the seeds; the time step is
+    adapted (and the run repeated from the seeds) until the acceptance lies in [0.4, 0.8].
+    Returns (comps [n_trials * n_seeds, 4], x [same, na, 3], acceptance, dt, next cycle)."""
+    dt = float(osys.dt[k])
+    cycle = cycle0
+    for _ in range(max_attempts):
+        x = np.array(seeds, dtype=np.float64)
+        st = np.full(x.shape[0], k, dtype=np.int32)
+        cs, xs, acc = [], [], 0
+        for t in range(n_trials):
+            x, c, _, a, _ = osys.hmc(x, st, n_steps, seed, cycle)
+            cycle += 1
+            cs.append(c)
+            xs.append(x.copy())
+            acc += int(a.sum())
+        rate = acc / (n_trials * x.shape[0])
+        if 0.4 <= rate <= 0.8:
+            break
+        new = adapt_dt(dt, rate)
+        if new == dt:
+            break
+        dt = new
+        dts = osys.dt.copy()
+        dts[k] = dt
+        osys.set_states(osys.T, osys.alpha, dts)
+    return np.concatenate(cs), np.concatenate(xs), rate, dt, cycle
+
+
+def build_leg(osys, leg, seeds, seed, speed=None, n_trials=40, n_steps=50, T_T=300.0, T_H=600.0, dt0=2.0,
+              max_states=400, max_reselect=40):
+    """"Initialization" of one leg, state after state: sampling and time-step adaptation at the
+    current state, the next state's parameter one thermodynamic-length step away (warming leg:
+    T; coupling leg: alpha), seeds resampled from the current state with weights exp(u_k - u_next),
+    sampling at the candidate, and the check on the mean exchange probability (below 0.4: the speed
+    shrinks by 4/5 and the candidate is placed again; above 0.99: the current state is dropped).
+    Returns dict(T, alpha, dt, pacc [neighbours], acceptance, speed)."""
+    bc = leg == "bc"
+    speed = (20.0 if bc else 0.2) if speed is None else float(speed)
+    T, A, D = ([T_T], [np.nan], [dt0]) if bc else ([T_H], [0.0], [dt0])
+    osys.set_states(T, A, D)
+    cycle = 0
+    comps_k, x_k, rate, dt, cycle = _sample_state(osys, 0, seeds, n_trials, n_steps, seed, cycle)
+    D[0] = dt
+    pacc, rates = [], [rate]
+    for _ in range(max_states):
+        k = len(T) - 1
+        if (bc and T[k] >= 600.0) or (not bc and A[k] >= 1.0):
+            break
+        sig = osys.state_statistics(comps_k, k)
+        for tries in range(max_reselect):
+            if bc:
+                Tn, An = next_temperature(T[k], sig[0], speed, 600.0), np.nan
+            else:
+                An = next_alpha(A[k], sig[1], sig[2], sig[3], speed, T_T, T_H)
+                Tn = (T_T - T_H) * An + T_H
+            osys.set_states(T + [Tn], A + [An], D + [D[k]])
+            u = ukn_from_comps(osys.T, osys.alpha, comps_k)
+            logw = u[k] - u[k + 1]
+            pick = resample(logw, seeds.shape[0], seed, 1_000_000 + cycle)
+            comps_n, x_n, rate_n, dt_n, cycle = _sample_state(osys, k + 1, x_k[pick], n_trials, n_steps, seed, cycle)
+            p = osys.mean_pacc(comps_k, comps_n, k, k + 1)
+            if p >= 0.4:
+                break
+            speed *= 0.8
+        if p > 0.99 and k > 0:  # state k is too close to its successor: the successor replaces it
+            T[k], A[k], D[k] = Tn, An, dt_n
+            osys.set_states(T, A, D)
+            pacc[-1] = osys.mean_pacc(prev_comps, comps_n, k - 1, k)
+        else:
+            T.append(Tn)
+            A.append(An)
+            D.append(dt_n)
+            pacc.append(p)
+        rates.append(rate_n)
+        prev_comps = comps_k
+        comps_k, x_k = comps_n, x_n
+        osys.set_states(T, A, D)
+    return {"T": np.array(T), "alpha": np.array(A), "dt": np.array(D), "pacc": np.array(pacc),
+            "acceptance": np.array(rates), "speed": speed}

@@ -30,6 +30,8 @@
  *   external_moves         "Sampling": external-coordinate MCMC (random rotation about the centre
  *                          of mass, Gaussian translation, Metropolis) for states with alpha < 0.01
  *   detect_equilibration   "Equilibration and production": the start that maximises N / g
+ *   protocol pieces        "Initialization": state statistics, thermodynamic-length steps in T and
+ *                          alpha, importance-resampled seeds, mean p_acc, the time-step rule
  *
  * Parity unpinned: nothing in this file is left without a pin; see the tests.
  */
@@ -390,6 +392,23 @@ oracle_system* oracle_system_create(const int n[3], const double origin[3], doub
     s->beta[k] = oracle_beta(T[k]);
   }
   return s;
+}
+
+/* Replaces the state table (used while a protocol is built state by state). */
+void oracle_system_set_states(oracle_system* s, int K, const double* T, const double* alpha, const double* dt) {
+  free(s->T); free(s->alpha); free(s->dt); free(s->w_sg); free(s->w_g); free(s->beta);
+  s->K = K;
+  s->T = dup_d(T, K);
+  s->alpha = dup_d(alpha, K);
+  s->dt = dup_d(dt, K);
+  s->w_sg = (double*)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
+  s->w_g = (double*)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
+  s->beta = (double*)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
+  for (int k = 0; k < K; ++k) {
+    s->w_sg[k] = oracle_alpha_sg(alpha[k]);
+    s->w_g[k] = oracle_alpha_g(alpha[k]);
+    s->beta[k] = oracle_beta(T[k]);
+  }
 }
 
 void oracle_system_destroy(oracle_system* s) {
@@ -1461,4 +1480,105 @@ void oracle_detect_equilibration(int64_t T, const double* a, int64_t stride, int
   }
   *t0_best = bt;
   *neff_best = best;
+}
+
+/* ---------------------------------------------------------------- protocol initialization
+ * "Initialization": states are placed one after another at even steps of thermodynamic length,
+ * Delta lambda = s / sigma_0[d l / d lambda], with seeds resampled from the previous state, a time
+ * step adapted to the Metropolis acceptance, and a check on the mean exchange probability.  The
+ * pieces below are the per-state arithmetic; the driver that runs them in order is in the Python
+ * part of the oracle (it samples with oracle_hmc). */
+
+/* Population standard deviations over n samples (components c [n][4]) at state k:
+ * out = {sigma[U_L + U_I], sigma[Psi_sg], sigma[Psi_g], sigma[u_k]}, u_k the reduced energy. */
+void oracle_state_statistics(const oracle_system* s, int64_t n, const double* comps, int k, double out[4]) {
+  double mean[4] = {0, 0, 0, 0};
+  for (int64_t i = 0; i < n; ++i) {
+    const double* c = comps + 4 * i;
+    double v[4] = {c[0] + c[1], c[2], c[3], reduced(s->beta[k], s->w_sg[k], s->w_g[k], c)};
+    for (int q = 0; q < 4; ++q) mean[q] += v[q];
+  }
+  for (int q = 0; q < 4; ++q) mean[q] /= (double)n;
+  double var[4] = {0, 0, 0, 0};
+  for (int64_t i = 0; i < n; ++i) {
+    const double* c = comps + 4 * i;
+    double v[4] = {c[0] + c[1], c[2], c[3], reduced(s->beta[k], s->w_sg[k], s->w_g[k], c)};
+    for (int q = 0; q < 4; ++q) var[q] += (v[q] - mean[q]) * (v[q] - mean[q]);
+  }
+  for (int q = 0; q < 4; ++q) out[q] = sqrt(var[q] / (double)n);
+}
+
+/* Warming leg: l = -U_S/(k_B T) - ln Z, so sigma[dl/dT] = sigma[U_S] / (k_B T^2) and the next
+ * temperature is T + speed k_B T^2 / sigma[U_S], not past T_end. */
+double oracle_next_temperature(double T, double sigma_U, double speed, double T_end) {
+  double Tn = T + speed * O_KB * T * T / sigma_U;
+  return Tn > T_end ? T_end : Tn;
+}
+
+/* Derivatives of the protocol weights of Eq. (protocol) with respect to alpha. */
+static double d_alpha_sg(double a) { return -4.0 * (2.0 * a - 1.0); }
+static double d_alpha_g(double a) {
+  double s = 2.0 * a - 1.0;
+  double z = 1000.0 * (a - 0.5);
+  double L = z >= 0.0 ? 1.0 / (1.0 + exp(-z)) : exp(z) / (1.0 + exp(z));
+  return 4.0 * s * L + s * s * 1000.0 * L * (1.0 - L);
+}
+
+/* Coupling leg, T(alpha) = (T_T - T_H) alpha + T_H: the next alpha is
+ * alpha + speed / (|d alpha_sg/d alpha| sigma[Psi_sg] / (k_B T) + |d alpha_g/d alpha| sigma[Psi_g] / (k_B T)
+ *                  + |T_T - T_H| sigma[u_alpha] / T), not past 1. */
+double oracle_next_alpha(double a, double sigma_sg, double sigma_g, double sigma_u, double speed, double T_T,
+                         double T_H) {
+  double T = (T_T - T_H) * a + T_H;
+  double rate = fabs(d_alpha_sg(a)) * sigma_sg / (O_KB * T) + fabs(d_alpha_g(a)) * sigma_g / (O_KB * T) +
+                fabs(T_T - T_H) * sigma_u / T;
+  double an = a + speed / rate;
+  return an > 1.0 ? 1.0 : an;
+}
+
+/* Sampling importance resampling: n_out indices drawn with replacement from n samples with weights
+ * proportional to exp(logw_i); draw j takes the 53-bit uniform of Philox counter {j, 0, ctr, 6}
+ * and the first index whose cumulative weight exceeds u times the total (weights relative to the
+ * largest, summed in index order). */
+void oracle_resample(int64_t n, const double* logw, int n_out, uint64_t seed, uint32_t ctr, int64_t* idx) {
+  double m = -INFINITY;
+  for (int64_t i = 0; i < n; ++i) if (logw[i] > m) m = logw[i];
+  double* cum = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double tot = 0.0;
+  for (int64_t i = 0; i < n; ++i) { tot += exp(logw[i] - m); cum[i] = tot; }
+  for (int j = 0; j < n_out; ++j) {
+    uint32_t r4[4];
+    philox(seed, (uint32_t)j, 0u, ctr, 6u, r4);
+    double u = oracle_u53(r4[0], r4[1]) * tot;
+    int64_t pick = n - 1;
+    for (int64_t i = 0; i < n; ++i) if (u < cum[i]) { pick = i; break; }
+    idx[j] = pick;
+  }
+  free(cum);
+}
+
+/* Mean exchange probability of Eq. (repXacc) over n pairs (the i-th sample of state a with the
+ * i-th of state b): min(1, exp(u_a(x_a) + u_b(x_b) - u_a(x_b) - u_b(x_a))). */
+double oracle_mean_pacc(const oracle_system* s, int64_t n, const double* comps_a, const double* comps_b, int ka,
+                        int kb) {
+  double tot = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double* ca = comps_a + 4 * i;
+    const double* cb = comps_b + 4 * i;
+    double d = reduced(s->beta[ka], s->w_sg[ka], s->w_g[ka], ca) + reduced(s->beta[kb], s->w_sg[kb], s->w_g[kb], cb) -
+               reduced(s->beta[ka], s->w_sg[ka], s->w_g[ka], cb) - reduced(s->beta[kb], s->w_sg[kb], s->w_g[kb], ca);
+    tot += d >= 0.0 ? 1.0 : exp(d);
+  }
+  return tot / (double)n;
+}
+
+/* Time-step rule of the sampling-and-adaptation step: acceptance > 0.8: +0.125 fs; < 0.1: -0.5 fs;
+ * < 0.4: -0.25 fs; kept in [0.1, 5] fs. */
+double oracle_adapt_dt(double dt, double acc) {
+  if (acc > 0.8) dt += 0.125;
+  else if (acc < 0.1) dt -= 0.5;
+  else if (acc < 0.4) dt -= 0.25;
+  if (dt < 0.1) dt = 0.1;
+  if (dt > 5.0) dt = 5.0;
+  return dt;
 }
