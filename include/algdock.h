@@ -238,6 +238,37 @@ algdock_status algdock_detect_equilibration(algdock_ctx* ctx, int64_t T, int64_t
                                             int64_t stride, int32_t n_cand, double* g, int64_t* t0_best,
                                             double* neff_best);
 
+/* ---------------------------------------------------------------- protocol initialization
+ * "Initialization": a protocol is built state by state.  Parameters of the next state are one
+ * thermodynamic-length step away, Delta lambda = s / sigma_0[d l / d lambda], with the standard
+ * deviations of the current state's samples.  Seeds for the next state are resampled with weights
+ * exp(u_k(x_i) - u_{k+1}(x_i)) (sampling importance resampling).  The mean exchange probability
+ * between the two states' samples checks the spacing.  These are the device reductions of those
+ * steps; the host chooses parameters and time steps.  All comps arrays are [N][4] double
+ * {U_L, U_I, Psi_sg, Psi_g} on the device; state indices refer to the state table.
+ * Errors: E_STATE (no states, or no ligand when configurations are gathered), E_INVALID (N < 1,
+ * state index out of range, bad pointers). */
+
+/* Population standard deviations over N samples at state k: sigma[0..3] (host) =
+ * {sigma[U_L + U_I], sigma[Psi_sg], sigma[Psi_g], sigma[u_k]}, u_k the reduced energy.  FP64.
+ * Synchronises. */
+algdock_status algdock_state_statistics(algdock_ctx* ctx, int64_t N, const double* comps, int32_t k, double* sigma);
+
+/* n_out (<= 1024) draws with replacement from the N samples, with weights exp(u_from - u_to): draw
+ * j takes the 53-bit uniform of Philox4x32-10 counter {j, 0, counter, 6} keyed by seed, and the
+ * first sample whose running weight (index order, relative to the largest) exceeds u times the
+ * total.  idx [n_out] int64 (device, may be NULL) receives the indices; if x_in ([N][n_atoms][3]
+ * float, device) is given, the chosen configurations are copied to x_out ([n_out][n_atoms][3]). */
+algdock_status algdock_resample(algdock_ctx* ctx, int64_t N, const double* comps, int32_t k_from, int32_t k_to,
+                                int32_t n_out, uint64_t seed, uint32_t counter, const float* x_in, float* x_out,
+                                int64_t* idx);
+
+/* Mean over the N pairs (i-th sample of comps_a at state ka, i-th of comps_b at state kb) of the
+ * exchange probability min(1, exp(u_a(x_a) + u_b(x_b) - u_a(x_b) - u_b(x_a))), Eq. (repXacc),
+ * into *p (host).  FP64.  Synchronises. */
+algdock_status algdock_mean_pacc(algdock_ctx* ctx, int64_t N, const double* comps_a, const double* comps_b, int32_t ka,
+                                 int32_t kb, double* p);
+
 /* ---------------------------------------------------------------- learned pose proposal
  * An extension of the paper's external-coordinate moves ("Sampling": a random rotation about the
  * centre of mass and a Gaussian translation, Metropolis-tested): a network proposes rigid-body and

@@ -30,7 +30,8 @@ EXPORTS = [
     "algdock_hmc_cycle", "algdock_energy_force", "algdock_exchange", "algdock_reduced_energies", "algdock_mbar",
     "algdock_mbar_noalloc", "algdock_learned_ntorsions", "algdock_learned_features", "algdock_pose_delta",
     "algdock_mlp_forward", "algdock_mlp_grad", "algdock_mlp_adam", "algdock_propose_learned",
-    "algdock_external_moves", "algdock_detect_equilibration",
+    "algdock_external_moves", "algdock_detect_equilibration", "algdock_state_statistics", "algdock_resample",
+    "algdock_mean_pacc",
 ]
 
 ALPHA_MAX_EXTERNAL = 0.01     # external-coordinate moves only below this alpha ("Sampling")
@@ -123,6 +124,9 @@ def load_library(path: str = LIB_PATH):
         "algdock_energy_force": ([vp, i64, vp, vp, vp, vp], C.c_int),
         "algdock_external_moves": ([vp, i64, vp, vp, vp, i32, dbl, dbl, u64, u64, i64, vp, vp], C.c_int),
         "algdock_detect_equilibration": ([vp, i64, i64, vp, i64, i32, vp, vp, vp], C.c_int),
+        "algdock_state_statistics": ([vp, i64, vp, i32, vp], C.c_int),
+        "algdock_resample": ([vp, i64, vp, i32, i32, i32, u64, C.c_uint32, vp, vp, vp], C.c_int),
+        "algdock_mean_pacc": ([vp, i64, vp, vp, i32, i32, vp], C.c_int),
         "algdock_exchange": ([vp, i32, i32, i32, vp, vp, vp, i32, i32, u64, u64, i64, vp, vp], C.c_int),
         "algdock_reduced_energies": ([vp, i64, vp, vp, i32, i32, vp], C.c_int),
         "algdock_mbar": ([vp, i32, i64, vp, vp, dbl, i32, i32, vp, C.POINTER(i32)], C.c_int),
@@ -337,6 +341,28 @@ class Context:
             _dev(g, torch.float64, "g"), _dev(t0_best, torch.int64, "t0_best"),
             _dev(neff_best, torch.float64, "neff_best")))
         return g, t0_best, neff_best
+
+    def state_statistics(self, comps, k):
+        """{sigma[U_L + U_I], sigma[Psi_sg], sigma[Psi_g], sigma[u_k]} (numpy) over comps [N][4]."""
+        import torch
+        out = np.zeros(4)
+        self._check(self._L.algdock_state_statistics(self.h, int(comps.shape[0]), _dev(comps, torch.float64, "comps"),
+                                                     int(k), out.ctypes.data))
+        return out
+
+    def resample(self, comps, k_from, k_to, n_out, seed, counter, x_in=None, x_out=None, idx=None):
+        import torch
+        self._check(self._L.algdock_resample(
+            self.h, int(comps.shape[0]), _dev(comps, torch.float64, "comps"), int(k_from), int(k_to), int(n_out),
+            int(seed), int(counter) & 0xFFFFFFFF, _dev(x_in, torch.float32, "x_in"), _dev(x_out, torch.float32, "x_out"),
+            _dev(idx, torch.int64, "idx")))
+
+    def mean_pacc(self, comps_a, comps_b, ka, kb):
+        import torch
+        p = C.c_double()
+        self._check(self._L.algdock_mean_pacc(self.h, int(comps_a.shape[0]), _dev(comps_a, torch.float64, "comps_a"),
+                                              _dev(comps_b, torch.float64, "comps_b"), int(ka), int(kb), C.byref(p)))
+        return p.value
 
     def energy_force(self, state_of, x, force, comps=None):
         import torch

@@ -5,6 +5,7 @@
 
 #include <new>
 #include <string>
+#include <initializer_list>
 #include <vector>
 
 #include "internal.cuh"
@@ -152,6 +153,7 @@ void algdock_destroy(algdock_ctx* c) {
   cudaFree(c->d_states);
   cudaFree(c->d_mbar);
   cudaFree(c->d_learn);
+  cudaFree(c->d_proto);
   cudaFreeHost(c->h_flag);
   delete c;
 }
@@ -529,6 +531,82 @@ algdock_status algdock_detect_equilibration(algdock_ctx* c, int64_t T, int64_t S
   Device dg(c->device);
   cudaError_t e = launch_equilibration(c->stream, T, S, series, stride, n_cand, g, t0_best, neff_best);
   if (e != cudaSuccess) return cuda_fail(c, e, "detect_equilibration");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+// Protocol scratch: 4 result doubles, then n weights.
+static algdock_status proto_scratch(algdock_ctx* c, int64_t n, const char* where) {
+  const size_t need = 256 + (size_t)n * sizeof(double);
+  if (need <= c->proto_bytes) return ALGDOCK_OK;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  cudaFree(c->d_proto);
+  c->d_proto = nullptr;
+  c->proto_bytes = 0;
+  e = cudaMalloc(&c->d_proto, need);
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  c->proto_bytes = need;
+  return ALGDOCK_OK;
+}
+
+static algdock_status proto_check(algdock_ctx* c, int64_t N, std::initializer_list<int> ks, const char* where) {
+  if (c->K == 0) return fail(c, ALGDOCK_E_STATE, std::string(where) + ": set the states first");
+  if (N < 1) return fail(c, ALGDOCK_E_INVALID, std::string(where) + ": N < 1");
+  for (int k : ks)
+    if (k < 0 || k >= c->K) return fail(c, ALGDOCK_E_INVALID, std::string(where) + ": state index out of range");
+  return ALGDOCK_OK;
+}
+
+algdock_status algdock_state_statistics(algdock_ctx* c, int64_t N, const double* comps, int32_t k, double* sigma) {
+  ALGDOCK_TRY(c)
+  algdock_status st = proto_check(c, N, {k}, "state_statistics");
+  if (st != ALGDOCK_OK) return st;
+  if (!sigma || !is_device_ptr(comps)) return fail(c, ALGDOCK_E_INVALID, "state_statistics: bad pointers");
+  Device g(c->device);
+  if ((st = proto_scratch(c, 1, "state_statistics")) != ALGDOCK_OK) return st;
+  double* out = (double*)c->d_proto;
+  cudaError_t e = launch_state_stats(c->stream, *c, N, comps, k, out);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sigma, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "state_statistics");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_resample(algdock_ctx* c, int64_t N, const double* comps, int32_t k_from, int32_t k_to,
+                                int32_t n_out, uint64_t seed, uint32_t counter, const float* x_in, float* x_out,
+                                int64_t* idx) {
+  ALGDOCK_TRY(c)
+  algdock_status st = proto_check(c, N, {k_from, k_to}, "resample");
+  if (st != ALGDOCK_OK) return st;
+  if (n_out < 1 || n_out > 1024) return fail(c, ALGDOCK_E_INVALID, "resample: need 1 <= n_out <= 1024");
+  if ((x_in || x_out) && !c->has_ligand) return fail(c, ALGDOCK_E_STATE, "resample: load the ligand first");
+  if (!is_device_ptr(comps) || (idx && !is_device_ptr(idx)) || (x_in && !is_device_ptr(x_in)) ||
+      (x_out && !is_device_ptr(x_out)) || (!x_in != !x_out))
+    return fail(c, ALGDOCK_E_INVALID, "resample: arrays must be device pointers (x_in and x_out together)");
+  Device g(c->device);
+  if ((st = proto_scratch(c, N, "resample")) != ALGDOCK_OK) return st;
+  double* work = (double*)((char*)c->d_proto + 256);
+  cudaError_t e = launch_resample(c->stream, *c, N, comps, k_from, k_to, n_out, seed, counter, work, idx, x_in, x_out);
+  if (e != cudaSuccess) return cuda_fail(c, e, "resample");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_mean_pacc(algdock_ctx* c, int64_t N, const double* comps_a, const double* comps_b, int32_t ka,
+                                 int32_t kb, double* p) {
+  ALGDOCK_TRY(c)
+  algdock_status st = proto_check(c, N, {ka, kb}, "mean_pacc");
+  if (st != ALGDOCK_OK) return st;
+  if (!p || !is_device_ptr(comps_a) || !is_device_ptr(comps_b)) return fail(c, ALGDOCK_E_INVALID, "mean_pacc: bad pointers");
+  Device g(c->device);
+  if ((st = proto_scratch(c, 1, "mean_pacc")) != ALGDOCK_OK) return st;
+  double* out = (double*)c->d_proto;
+  cudaError_t e = launch_pacc(c->stream, *c, N, comps_a, comps_b, ka, kb, out);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p, out, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "mean_pacc");
   return ALGDOCK_OK;
   ALGDOCK_CATCH(c)
 }

@@ -133,6 +133,9 @@ struct algdock_ctx {
   algdock::LearnedTopo ltopo{};
   void* d_learn = nullptr;
   size_t learn_bytes = 0;
+  // protocol initialization: device results (4 doubles) and resampling weights, grown on demand
+  void* d_proto = nullptr;
+  size_t proto_bytes = 0;
 };
 
 namespace algdock {
@@ -152,6 +155,13 @@ cudaError_t launch_external(cudaStream_t s, const algdock_ctx& c, int64_t n_rep,
 size_t equilibration_smem(int64_t T);
 cudaError_t launch_equilibration(cudaStream_t st, int64_t T, int64_t S, const double* a, int64_t stride, int n_cand,
                                  double* g, int64_t* t0_best, double* neff_best);
+cudaError_t launch_state_stats(cudaStream_t s, const algdock_ctx& c, int64_t n, const double* comps, int k,
+                               double* out);
+cudaError_t launch_resample(cudaStream_t s, const algdock_ctx& c, int64_t n, const double* comps, int k_from,
+                            int k_to, int n_out, uint64_t seed, uint32_t ctr, double* work, int64_t* idx,
+                            const float* x_in, float* x_out);
+cudaError_t launch_pacc(cudaStream_t s, const algdock_ctx& c, int64_t n, const double* ca, const double* cb, int ka,
+                        int kb, double* out);
 cudaError_t launch_energy_force(cudaStream_t s, const algdock_ctx& c, int64_t N, const int32_t* state_of,
                                 const float* x, float* force, double* comps);
 cudaError_t launch_ukn(cudaStream_t s, const algdock_ctx& c, int64_t N, const double* comps, int k_begin,
