@@ -39,6 +39,9 @@ def parse():
     p.add_argument("--no-mbar", action="store_true")
     p.add_argument("--no-learned", action="store_true")
     p.add_argument("--no-bpmf", action="store_true", help="skip the BPMF effective-samples comparison")
+    p.add_argument("--no-protocol", action="store_true", help="skip the protocol-initialization measurement")
+    p.add_argument("--protocol-only", action="store_true",
+                   help="set up the workload and run only the protocol-initialization measurement")
     p.add_argument("--bpmf-only", action="store_true",
                    help="set up the workload and run only the BPMF effective-samples comparison")
     p.add_argument("--paper-cycles", type=int, default=8000)
@@ -361,6 +364,41 @@ def bpmf_convergence(ctx, sys_, stream, dev, paper_cycles=8000, learned_cycles=8
     return out
 
 
+def protocol_build(ctx, sys_, stream, n_seeds=50, seed=21):
+    """Protocol initialization ("Initialization") of both legs for the paper-scale ligand with the
+    paper's settings: 50 seeds, 2000 steps (40 HMC trials of 50 steps) per state and attempt,
+    speeds s_bc = 20 and s_cd = 0.2, time steps adapted into [0.1, 5] fs.  The seeds of both legs
+    are placements of the ligand in the binding site (the coupling leg starts unbound, at alpha = 0
+    and 600 K)."""
+    import torch
+
+    from paper_1507_03703_gb300 import synthetic as S
+    from paper_1507_03703_gb300.protocol import ProtocolBuilder
+    lig = sys_.ligand
+    seeds = S.place_ligand(lig, sys_.receptor, sys_.site, n_seeds, seed=seed, n_tries=8).astype(np.float32)
+    out = {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for leg in ("bc", "cd"):
+        pb = ProtocolBuilder(ctx)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ev[0].record(stream)
+        r = pb.build_leg(leg, seeds, seed=seed)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        out[leg] = {"states": int(len(r["T"])), "wall_s": time.perf_counter() - t,
+                    "gpu_s": ev[0].elapsed_time(ev[1]) * 1e-3, "hmc_trials": r["hmc_trials"],
+                    "final_speed": r["speed"], "pacc_min": float(r["pacc"].min()) if len(r["pacc"]) else None,
+                    "pacc_mean": float(r["pacc"].mean()) if len(r["pacc"]) else None,
+                    "dt_fs_min": float(r["dt"].min()), "dt_fs_max": float(r["dt"].max()),
+                    "acceptance_mean": float(r["acceptance"].mean())}
+        if leg == "bc":
+            out[leg]["T_K"] = [round(float(v), 1) for v in r["T"]]
+        else:
+            out[leg]["alpha_first"] = [round(float(v), 4) for v in r["alpha"][:8]]
+    return out
+
+
 def oracle_cpu_baseline(sys_, n_rep=65536, n_threads=0):
     """The FP64 oracle as it stands on this host's cores: one HMC trial of 50 VV steps for a
     bounded sample of replicas spread over all states (about 10-30 s on a 16-core host)."""
@@ -486,6 +524,9 @@ def main():
         r = learned_vs_plain(ctx, sys_, stream, dev, target=N_STATES_BC + 28, cmp_cycles=20, train_iter=20)
         print(json.dumps({"learned_vs_plain": r}))
         return
+    if args.protocol_only:
+        print(json.dumps({"protocol_initialization": protocol_build(ctx, sys_, stream)}))
+        return
     if args.bpmf_only:
         r = bpmf_convergence(ctx, sys_, stream, dev, paper_cycles=args.paper_cycles,
                              learned_cycles=args.learned_cycles, window=args.bpmf_window)
@@ -581,6 +622,9 @@ def main():
         # the paper's own regime (alpha ~ 0.01), mid-leg, and the fully coupled end
         extra["learned_vs_plain"] = [learned_vs_plain(ctx, sys_, stream, dev, target=k) for k in
                                      (N_STATES_BC + 1, N_STATES_BC + 28, N_STATES_BC + N_STATES_CD - 1)]
+    if not args.no_protocol and world == 1:
+        extra["protocol_initialization"] = protocol_build(ctx, sys_, stream)
+        ctx.states_set(T, alpha, dt)
     if not args.no_bpmf and world == 1:
         extra["bpmf_eff_samples"] = bpmf_convergence(ctx, sys_, stream, dev)
 
