@@ -203,7 +203,7 @@ __device__ inline void put(float* sx, float* sy, float* sz, int s, float3 f) {
 
 // Step 1: every bonded term once, one per lane; per-role forces to the slot arrays.
 // Slots: bond t role r -> r*nb + t; angle -> 2nb + r*nang + t; torsion -> 2nb + 3nang + r*ntor + t.
-template <bool ENERGY>
+template <bool ENERGY, bool FORCES = true>
 __device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const float4* xs, float* sx, float* sy,
                                      float* sz) {
   const int lane = threadIdx.x & 31;
@@ -217,8 +217,8 @@ __device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const
     const float dr = r2 * inv_r - bp.w;
     if (ENERGY) e += bp.z * dr * dr;
     const float c = -2.f * bp.z * dr * inv_r;
-    put(sx, sy, sz, t, make_float3(c * d.x, c * d.y, c * d.z));
-    put(sx, sy, sz, nb + t, make_float3(-c * d.x, -c * d.y, -c * d.z));
+    if (FORCES) put(sx, sy, sz, t, make_float3(c * d.x, c * d.y, c * d.z));
+    if (FORCES) put(sx, sy, sz, nb + t, make_float3(-c * d.x, -c * d.y, -c * d.z));
   }
   const int ab = 2 * nb;
   for (int t = lane; t < nang; t += 32) {  // k (theta - theta0)^2
@@ -235,9 +235,9 @@ __device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const
     const float cu = __fdividef(coef * c, lu2), cw = __fdividef(coef * c, lw2), cx = coef * inv_luw;
     const float3 fa = make_float3(cx * w.x - cu * u.x, cx * w.y - cu * u.y, cx * w.z - cu * u.z);
     const float3 fc = make_float3(cx * u.x - cw * w.x, cx * u.y - cw * w.y, cx * u.z - cw * w.z);
-    put(sx, sy, sz, ab + t, fa);
-    put(sx, sy, sz, ab + nang + t, make_float3(-(fa.x + fc.x), -(fa.y + fc.y), -(fa.z + fc.z)));
-    put(sx, sy, sz, ab + 2 * nang + t, fc);
+    if (FORCES) put(sx, sy, sz, ab + t, fa);
+    if (FORCES) put(sx, sy, sz, ab + nang + t, make_float3(-(fa.x + fc.x), -(fa.y + fc.y), -(fa.z + fc.z)));
+    if (FORCES) put(sx, sy, sz, ab + 2 * nang + t, fc);
   }
   const int tb = ab + 3 * nang;
   for (int t = lane; t < ntor; t += 32) {  // sum_n V_n/2 (1 + cos(n phi - gamma_n))
@@ -271,17 +271,17 @@ __device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const
                                   -(1.f + p) * fi.z + q * fl.z);
     const float3 fk = make_float3(p * fi.x - (1.f + q) * fl.x, p * fi.y - (1.f + q) * fl.y,
                                   p * fi.z - (1.f + q) * fl.z);
-    put(sx, sy, sz, tb + t, fi);
-    put(sx, sy, sz, tb + ntor + t, fj);
-    put(sx, sy, sz, tb + 2 * ntor + t, fk);
-    put(sx, sy, sz, tb + 3 * ntor + t, fl);
+    if (FORCES) put(sx, sy, sz, tb + t, fi);
+    if (FORCES) put(sx, sy, sz, tb + ntor + t, fj);
+    if (FORCES) put(sx, sy, sz, tb + 2 * ntor + t, fk);
+    if (FORCES) put(sx, sy, sz, tb + 3 * ntor + t, fl);
   }
   return e;
 }
 
 // Step 3: nonbonded pairs.  Pass a covers atoms 32a .. 32a+31; a pass with at most 16 atoms gives
 // each atom two lanes, which split the partner range and combine with one shuffle.
-template <int APL, bool ENERGY>
+template <int APL, bool ENERGY, bool FORCES = true>
 __device__ inline void nonbonded(const Lig& L, int na, const float4* xs, float (&F)[APL][3], float& el) {
   const int lane = threadIdx.x & 31;
   float e2 = 0.f;
@@ -327,9 +327,11 @@ __device__ inline void nonbonded(const Lig& L, int na, const float4* xs, float (
         const float qq = excluded ? 0.f : (ty == 1u ? (float)(1.0 / 1.2) : 1.f) * (qi * pj.w);
         const float eel = qq * inv_r;
         const float fr = fmaf(12.f * eps, s6 * s6 - s6, eel) * inv_r2;
-        fx = fmaf(fr, dx, fx);
-        fy = fmaf(fr, dy, fy);
-        fz = fmaf(fr, dz, fz);
+        if (FORCES) {
+          fx = fmaf(fr, dx, fx);
+          fy = fmaf(fr, dy, fy);
+          fz = fmaf(fr, dz, fz);
+        }
         if (ENERGY) e2 += fmaf(eps, s6 * s6 - 2.f * s6, eel);
       }
     }
@@ -350,7 +352,7 @@ __device__ inline void nonbonded(const Lig& L, int na, const float4* xs, float (
 // Step 3 from the pair table: the same passes and lane layout as `nonbonded`, with each pair's
 // combined and scaled coefficients read as one record (R_ij^2, 12 eps_ij, 332 q_i q_j, guard)
 // instead of being formed from per-atom parameters and the pair type.
-template <int APL, bool ENERGY>
+template <int APL, bool ENERGY, bool FORCES = true>
 __device__ inline void nonbonded_table(const Lig& L, int na, const float4* xs, float (&F)[APL][3], float& el) {
   const int lane = threadIdx.x & 31;
   float e2 = 0.f;
@@ -389,9 +391,11 @@ __device__ inline void nonbonded_table(const Lig& L, int na, const float4* xs, f
         const float s6 = s2 * s2 * s2;
         const float eel = t.z * inv_r;
         const float fr = fmaf(t.y, fmaf(s6, s6, -s6), eel) * inv_r2;
-        fx = fmaf(fr, dx, fx);
-        fy = fmaf(fr, dy, fy);
-        fz = fmaf(fr, dz, fz);
+        if (FORCES) {
+          fx = fmaf(fr, dx, fx);
+          fy = fmaf(fr, dy, fy);
+          fz = fmaf(fr, dz, fz);
+        }
         if (ENERGY) e2 += fmaf(t.y * (1.f / 12.f), fmaf(s6, s6, -2.f * s6), eel);
       }
     }
@@ -411,7 +415,7 @@ __device__ inline void nonbonded_table(const Lig& L, int na, const float4* xs, f
 
 // Forces on the lane's atoms (and, if ENERGY, the lane's partial energies).  xs holds all
 // positions (x, y, z, q); sf is the warp's bonded-slot scratch (3 * n_slots floats).
-template <int APL, bool ENERGY, bool TABLE = false>
+template <int APL, bool ENERGY, bool TABLE = false, bool FORCES = true>
 __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const GridDev& G, const float4* xs, float* sf,
                                 const float (&x)[APL][3], float (&F)[APL][3], float w_sg, float w_g, bool all_grids,
                                 Energies& en, int& outside) {
@@ -420,7 +424,7 @@ __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const Grid
   float* sx = sf;
   float* sy = sf + ns;
   float* sz = sf + 2 * ns;
-  float el = bonded_terms<ENERGY>(L, LL, xs, sx, sy, sz);
+  float el = bonded_terms<ENERGY, FORCES>(L, LL, xs, sx, sy, sz);
   __syncwarp();
   const bool hard = all_grids || w_g != 0.f;
   const bool soft = all_grids || w_sg != 0.f;
@@ -437,7 +441,8 @@ __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const Grid
     my += m * x[a][1];
     mz += m * x[a][2];
     if (hard || soft) {
-      const GridOut go = grid_atom(G, x[a][0], x[a][1], x[a][2], pa.z, pa.w, pa.y, hard, soft, w_sg, w_g);
+      const GridOut go = grid_atom(G, x[a][0], x[a][1], x[a][2], pa.z, pa.w, pa.y, hard, soft, FORCES ? w_sg : 0.f,
+                                   FORCES ? w_g : 0.f);
       F[a][0] += go.fx;
       F[a][1] += go.fy;
       F[a][2] += go.fz;
@@ -445,16 +450,16 @@ __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const Grid
       esg += go.e_sg;
       outside += go.outside ? 1 : 0;
     }
-    const int b1 = L.inc_start[i + 1];
-    for (int b = L.inc_start[i]; b < b1; ++b) {
+    const int b1 = FORCES ? L.inc_start[i + 1] : 0;
+    for (int b = FORCES ? L.inc_start[i] : 0; b < b1; ++b) {
       const uint32_t s = L.inc[b];
       F[a][0] += sx[s];
       F[a][1] += sy[s];
       F[a][2] += sz[s];
     }
   }
-  if (TABLE) nonbonded_table<APL, ENERGY>(L, na, xs, F, el);
-  else nonbonded<APL, ENERGY>(L, na, xs, F, el);
+  if (TABLE) nonbonded_table<APL, ENERGY, FORCES>(L, na, xs, F, el);
+  else nonbonded<APL, ENERGY, FORCES>(L, na, xs, F, el);
   // restraint on the centre of mass
   mx = warp_sumf(mx);
   my = warp_sumf(my);
@@ -704,7 +709,8 @@ struct EvalArgs {
   double* comps;
 };
 
-template <int APL>
+// FORCES = false: energies only (the bonded force slots, grid gradients and pair forces are skipped).
+template <int APL, bool FORCES>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) eval_kernel(const EvalArgs A) {
   extern __shared__ __align__(16) uint32_t smem[];
   stage_ligand(smem, A.blob, A.LL.words);
@@ -739,10 +745,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) eval_kernel(const EvalArg
   __syncwarp();
   Energies en;
   int outside = 0;
-  evaluate<APL, true>(A.LL, L, A.G, ws.xs, ws.sf, x, F, w_sg, w_g, true, en, outside);
+  evaluate<APL, true, false, FORCES>(A.LL, L, A.G, ws.xs, ws.sf, x, F, w_sg, w_g, true, en, outside);
   double c[4];
   reduce_components(en, c);
-  if (A.force) {
+  if (FORCES && A.force) {
 #pragma unroll
     for (int a = 0; a < APL; ++a) {
       const int i = lane + 32 * a;
@@ -988,7 +994,11 @@ static cudaError_t launch_eval(cudaStream_t s, const algdock_ctx& c, int64_t N, 
   if (N == 0) return cudaSuccess;
   EvalArgs A{c.grid, c.lig, c.d_blob, c.d_states, c.K, N, state_of, x, force, comps};
   const int apl = atoms_per_lane(c.lig.na);
-  return launch_templated(eval_kernel<1>, eval_kernel<2>, eval_kernel<3>, apl, block_smem(c.lig, apl), N, s, A);
+  if (force)
+    return launch_templated(eval_kernel<1, true>, eval_kernel<2, true>, eval_kernel<3, true>, apl,
+                            block_smem(c.lig, apl), N, s, A);
+  return launch_templated(eval_kernel<1, false>, eval_kernel<2, false>, eval_kernel<3, false>, apl,
+                          block_smem(c.lig, apl), N, s, A);
 }
 
 cudaError_t launch_evaluate(cudaStream_t s, const algdock_ctx& c, int64_t N, const float* x, double* comps) {
