@@ -513,10 +513,12 @@ def main():
         run.exchange(cyc)
         if ev is not None:
             ev[2].record(stream)
+        # the snapshot: energies of every replica in one launch, then u_kn per leg
+        ctx.reduced_energies(R, x=run.x, comps=snap)
         for li, leg in enumerate(legs):
             sl = run.leg_slice(li)
-            ctx.reduced_energies(N_CHAINS * leg.K, x=run.x[sl], comps=snap[sl], k_begin=leg.state_offset,
-                                 k_count=leg.K, u_kn=u_leg[li])
+            ctx.reduced_energies(N_CHAINS * leg.K, comps=snap[sl], k_begin=leg.state_offset, k_count=leg.K,
+                                 u_kn=u_leg[li])
         if ev is not None:
             ev[3].record(stream)
 
@@ -532,7 +534,7 @@ def main():
                              learned_cycles=args.learned_cycles, window=args.bpmf_window)
         print(json.dumps({"bpmf_eff_samples": r}))
         return
-    launches_per_step = 1 + len(legs) + 2 * len(legs)  # hmc, exchange per leg, evaluate + u_kn per leg
+    launches_per_step = 1 + len(legs) + 1 + len(legs)  # hmc, exchange per leg, one evaluate, u_kn per leg
     for w in range(args.warmup):
         step(w)
     torch.cuda.synchronize()

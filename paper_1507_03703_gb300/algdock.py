@@ -257,6 +257,7 @@ class Context:
         """stream: a torch.cuda.Stream (or None for the legacy default stream)."""
         ptr = None if stream is None else C.c_void_p(stream.cuda_stream)
         self._check(self._L.algdock_set_stream(self.h, ptr))
+        self.stream = stream
 
     # ---------------------------------------------------------------- grids
     def grids_build(self, grid, receptor, ljr, lja, elec):

@@ -75,13 +75,37 @@ class ReplicaExchange:
                                     alpha_max=self.alpha_max, sigma=self.sigma, rep_offset=self.rep_offset,
                                     accepted=self.ext_acc)
 
+    def _exchange_leg(self, li, cycle):
+        leg = self.legs[li]
+        sl = self.leg_slice(li)
+        self.ctx.exchange(leg.K, leg.state_offset, self.comps[sl], self.config_of[li], self.state_of[sl],
+                          n_sweeps=self.n_sweeps, max_sep=self.max_sep, seed=self.seed, cycle=cycle,
+                          ladder_offset=self.ladder_offset + li * self.C, attempts=self.attempts[li],
+                          accepts=self.accepts[li])
+
     def exchange(self, cycle: int):
-        for li, leg in enumerate(self.legs):
-            sl = self.leg_slice(li)
-            self.ctx.exchange(leg.K, leg.state_offset, self.comps[sl], self.config_of[li], self.state_of[sl],
-                              n_sweeps=self.n_sweeps, max_sep=self.max_sep, seed=self.seed, cycle=cycle,
-                              ladder_offset=self.ladder_offset + li * self.C, attempts=self.attempts[li],
-                              accepts=self.accepts[li])
+        """Exchange sweeps on every ladder.  The legs' ladders are independent; with the context on a
+        torch stream, legs after the first run on side streams (ordered by events), so that the
+        one-block-per-ladder launches of the two legs share the GPU instead of taking turns."""
+        main = getattr(self.ctx, "stream", None)
+        if len(self.legs) < 2 or main is None:
+            for li in range(len(self.legs)):
+                self._exchange_leg(li, cycle)
+            return
+        if not hasattr(self, "_side"):
+            self._side = [torch.cuda.Stream(device=main.device) for _ in self.legs[1:]]
+        ready = torch.cuda.Event()
+        ready.record(main)
+        for li, side in enumerate(self._side, 1):
+            side.wait_event(ready)
+            self.ctx.set_stream(side)
+            self._exchange_leg(li, cycle)
+        self.ctx.set_stream(main)
+        self._exchange_leg(0, cycle)
+        for side in self._side:
+            done = torch.cuda.Event()
+            done.record(side)
+            main.wait_event(done)
 
     def cycle(self, cycle: int, n_steps: int, record: bool = False):
         """One iteration ("Equilibration and production"): an HMC move and the external-coordinate
