@@ -701,3 +701,47 @@ def build_leg(osys, leg, seeds, seed, speed=None, n_trials=40, n_steps=50, T_T=3
         osys.set_states(T, A, D)
     return {"T": np.array(T), "alpha": np.array(A), "dt": np.array(D), "pacc": np.array(pacc),
             "acceptance": np.array(rates), "speed": speed}
+
+
+# ------------------------------------------------------------------ end points: target force field and FEP
+def target_interaction(receptor, ligand, x, n_threads: int = 0):
+    """Receptor-ligand energy of the target force field, computed directly at the ligand atoms'
+    positions ("Thermodynamic Cycle": the target force field evaluates receptor-ligand
+    interactions directly, the sampling force field by grid interpolation).  x: [N, n_atoms, 3];
+    returns [N] float64 (kcal/mol)."""
+    L = _load()
+    if not getattr(L, "_target", False):
+        L.oracle_target_interaction.argtypes = [C.c_int, _d, _d, _d, _d, C.c_int, _d, _d, _d, C.c_int64, _d, _d,
+                                                C.c_int]
+        L.oracle_target_interaction.restype = C.c_int
+        L._target = True
+    x = _f64(x).reshape(-1, ligand.n_atoms, 3)
+    out = np.empty(x.shape[0])
+    L.oracle_target_interaction(receptor.n_atoms, _f64(receptor.xyz), _f64(receptor.rstar), _f64(receptor.eps),
+                                _f64(receptor.charge), ligand.n_atoms, _f64(ligand.rstar), _f64(ligand.eps),
+                                _f64(ligand.charge), x.shape[0], x, out, n_threads)
+    return out
+
+
+def fep(du):
+    """Zwanzig free energy perturbation ("Estimation": f_AB and f_DE by free energy perturbation)
+    from reduced energy differences du_n = beta (U_target - U_sampling) of N samples drawn in the
+    sampling state:  f = -ln (1/N) sum_n exp(-du_n).
+
+    Also returns the Kish effective sample size n_eff = (sum w)^2 / sum w^2 of the weights
+    w_n = exp(-du_n), the first-order (delta-method) standard error of f for independent samples,
+    sigma^2 = var(w) / (N mean(w)^2) = (N / n_eff - 1) / (N - 1), and the smallest du.
+    The weights are taken relative to the smallest du, which leaves f unchanged."""
+    import math
+    du = np.asarray(du, dtype=np.float64).reshape(-1)
+    N = du.shape[0]
+    if N == 0:
+        raise ValueError("fep needs at least one sample")
+    m = float(du.min())
+    w = np.exp(-(du - m))
+    s1 = math.fsum(w)
+    s2 = math.fsum(w * w)
+    f = m - math.log(s1 / N)
+    n_eff = s1 * s1 / s2
+    sigma = math.sqrt(max(N / n_eff - 1.0, 0.0) / (N - 1)) if N > 1 else math.nan
+    return {"f": f, "sigma": sigma, "n_eff": n_eff, "du_min": m}

@@ -32,6 +32,8 @@
  *   detect_equilibration   "Equilibration and production": the start that maximises N / g
  *   protocol pieces        "Initialization": state statistics, thermodynamic-length steps in T and
  *                          alpha, importance-resampled seeds, mean p_acc, the time-step rule
+ *   target_interaction     "Thermodynamic Cycle": the target force field's receptor-ligand energy,
+ *                          computed directly (the postprocessing of milestone D samples)
  *
  * Parity unpinned: nothing in this file is left without a pin; see the tests.
  */
@@ -1581,4 +1583,34 @@ double oracle_adapt_dt(double dt, double acc) {
   if (dt < 0.1) dt = 0.1;
   if (dt > 5.0) dt = 5.0;
   return dt;
+}
+
+/* ---------------------------------------------------------------- target force field (end points) */
+/* Receptor-ligand interaction of the target force field ("Thermodynamic Cycle": the target force
+ * field computes receptor-ligand interactions directly rather than by grid interpolation).  The
+ * same sums that define the grids are taken at each ligand atom's own position and weighted by
+ * that atom's factors:  Psi_T = sum_i sqrt(A_i) LJr(x_i) + sqrt(B_i) LJa(x_i) + q_i elec(x_i).
+ * x holds n_samples configurations [n_samples][n_lig][3]; out [n_samples].
+ * Returns the number of threads used. */
+int oracle_target_interaction(int n_rec, const double* rec_xyz, const double* rec_rstar, const double* rec_eps,
+                              const double* rec_q, int n_lig, const double* lig_rstar, const double* lig_eps,
+                              const double* lig_q, int64_t n_samples, const double* x, double* out, int n_threads) {
+  int64_t np_ = n_samples * n_lig;
+  double* ljr = (double*)malloc(sizeof(double) * (size_t)(np_ > 0 ? np_ : 1));
+  double* lja = (double*)malloc(sizeof(double) * (size_t)(np_ > 0 ? np_ : 1));
+  double* elec = (double*)malloc(sizeof(double) * (size_t)(np_ > 0 ? np_ : 1));
+  int T = 1;
+  if (np_ > 0)
+    T = oracle_grid_points(n_rec, rec_xyz, rec_rstar, rec_eps, rec_q, np_, x, ljr, lja, elec, n_threads);
+  for (int64_t s = 0; s < n_samples; ++s) {
+    double psi = 0.0;
+    for (int i = 0; i < n_lig; ++i) {
+      int64_t p = s * n_lig + i;
+      psi += sqrtA_of(lig_rstar[i], lig_eps[i]) * ljr[p] + sqrtB_of(lig_rstar[i], lig_eps[i]) * lja[p] +
+             lig_q[i] * elec[p];
+    }
+    out[s] = psi;
+  }
+  free(ljr); free(lja); free(elec);
+  return T;
 }
