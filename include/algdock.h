@@ -269,6 +269,43 @@ algdock_status algdock_resample(algdock_ctx* ctx, int64_t N, const double* comps
 algdock_status algdock_mean_pacc(algdock_ctx* ctx, int64_t N, const double* comps_a, const double* comps_b, int32_t ka,
                                  int32_t kb, double* p);
 
+/* ---------------------------------------------------------------- end points (target force field)
+ * The thermodynamic cycle starts and ends in a target force field that differs from the sampling
+ * force field ("Thermodynamic Cycle"); samples of milestones B and D are postprocessed in it and
+ * f_AB and f_DE are estimated by free energy perturbation ("Estimation", Zwanzig 1954).  Here the
+ * target force field differs from the sampling one in what the paper names as the key difference
+ * apart from solvation: receptor-ligand interactions are computed directly instead of by grid
+ * interpolation (there is no implicit solvent in either). */
+
+/* Receptor atoms for the target interaction (host or device double arrays: xyz [n_rec][3],
+ * rstar, eps (>= 0), q [n_rec]); copied to the context, which owns them.  n_rec = 0 is allowed
+ * (the interaction is then 0).  ALGDOCK_E_NUMERIC for a non-finite or negative parameter. */
+algdock_status algdock_receptor_load(algdock_ctx* ctx, int32_t n_rec, const double* rec_xyz, const double* rec_rstar,
+                                     const double* rec_eps, const double* rec_q);
+
+/* Receptor-ligand interaction of the target force field for N configurations: the grid sums of
+ * algdock_grids_build taken at each ligand atom's own position and weighted by its factors,
+ *   psi_T = sum_i [ sqrt(A_i) LJr(x_i) + sqrt(B_i) LJa(x_i) + q_i elec(x_i) ],
+ * the same energy function as the hard grids without the interpolation (so that
+ * U_T(r_RL) - U_T(r_L) - Psi_g(r_L) = psi_T - Psi_g, the exponent of the paper's reweighting of
+ * milestone D samples, Eq. (reweighing_interact)).  x: device float [N][n_atoms][3] of the loaded
+ * ligand; psi: device double [N] (kcal/mol).  Each pair term in FP32, sums over receptor tiles and
+ * over atoms in FP64; deterministic.  Needs algdock_ligand_load and algdock_receptor_load. */
+algdock_status algdock_target_interaction(algdock_ctx* ctx, int64_t N, const float* x, double* psi);
+
+/* Zwanzig free energy perturbation over N samples of the sampling state:
+ *   du_n = beta (u_target[n * stride_target] - u_sampling[n * stride_sampling]),
+ *   f = -ln (1/N) sum_n exp(-du_n)   (reduced units: the target's free energy minus the sampler's).
+ * u_sampling may be NULL (0); beta = 1 for energies already reduced.  For f_DE pass psi_T from
+ * algdock_target_interaction and Psi_g (column 3 of the components, stride 4) at beta_T.
+ * result (host double[4]): f; its first-order standard error for independent samples,
+ * sqrt((N / n_eff - 1) / (N - 1)) (NaN for N = 1); the Kish effective sample size
+ * n_eff = (sum w)^2 / sum w^2 of the weights w = exp(-du); the smallest du.  du = +inf has weight 0;
+ * NaN or -inf gives ALGDOCK_E_NUMERIC (result still written).  FP64 log-sum-exp in a fixed
+ * reduction order (deterministic).  Device arrays; synchronises. */
+algdock_status algdock_fep(algdock_ctx* ctx, int64_t N, const double* u_target, int64_t stride_target,
+                           const double* u_sampling, int64_t stride_sampling, double beta, double* result);
+
 /* ---------------------------------------------------------------- learned pose proposal
  * An extension of the paper's external-coordinate moves ("Sampling": a random rotation about the
  * centre of mass and a Gaussian translation, Metropolis-tested): a network proposes rigid-body and

@@ -31,7 +31,7 @@ EXPORTS = [
     "algdock_mbar_noalloc", "algdock_learned_ntorsions", "algdock_learned_features", "algdock_pose_delta",
     "algdock_mlp_forward", "algdock_mlp_grad", "algdock_mlp_adam", "algdock_propose_learned",
     "algdock_external_moves", "algdock_detect_equilibration", "algdock_state_statistics", "algdock_resample",
-    "algdock_mean_pacc",
+    "algdock_mean_pacc", "algdock_receptor_load", "algdock_target_interaction", "algdock_fep",
 ]
 
 ALPHA_MAX_EXTERNAL = 0.01     # external-coordinate moves only below this alpha ("Sampling")
@@ -127,6 +127,9 @@ def load_library(path: str = LIB_PATH):
         "algdock_state_statistics": ([vp, i64, vp, i32, vp], C.c_int),
         "algdock_resample": ([vp, i64, vp, i32, i32, i32, u64, C.c_uint32, vp, vp, vp], C.c_int),
         "algdock_mean_pacc": ([vp, i64, vp, vp, i32, i32, vp], C.c_int),
+        "algdock_receptor_load": ([vp, i32, vp, vp, vp, vp], C.c_int),
+        "algdock_target_interaction": ([vp, i64, vp, vp], C.c_int),
+        "algdock_fep": ([vp, i64, vp, i64, vp, i64, dbl, vp], C.c_int),
         "algdock_exchange": ([vp, i32, i32, i32, vp, vp, vp, i32, i32, u64, u64, i64, vp, vp], C.c_int),
         "algdock_reduced_energies": ([vp, i64, vp, vp, i32, i32, vp], C.c_int),
         "algdock_mbar": ([vp, i32, i64, vp, vp, dbl, i32, i32, vp, C.POINTER(i32)], C.c_int),
@@ -364,6 +367,47 @@ class Context:
         self._check(self._L.algdock_mean_pacc(self.h, int(comps_a.shape[0]), _dev(comps_a, torch.float64, "comps_a"),
                                               _dev(comps_b, torch.float64, "comps_b"), int(ka), int(kb), C.byref(p)))
         return p.value
+
+    def receptor_load(self, receptor):
+        """Receptor atoms of the target force field (host numpy or CUDA float64 arrays)."""
+        px, kx = _any(receptor.xyz, np.float64, None, "xyz")
+        pr, kr = _any(receptor.rstar, np.float64, None, "rstar")
+        pe, ke = _any(receptor.eps, np.float64, None, "eps")
+        pq, kq = _any(receptor.charge, np.float64, None, "q")
+        n = int(len(receptor.rstar))
+        self._check(self._L.algdock_receptor_load(self.h, n, px, pr, pe, pq))
+
+    def target_interaction(self, x, psi=None):
+        """Target-force-field receptor-ligand energy psi_T [N] (float64, kcal/mol) of the
+        configurations x [N, n_atoms, 3] (CUDA float32)."""
+        import torch
+        N = int(x.shape[0])
+        if psi is None:
+            psi = torch.empty(N, dtype=torch.float64, device=x.device)
+        self._check(self._L.algdock_target_interaction(self.h, N, _dev(x, torch.float32, "x"),
+                                                       _dev(psi, torch.float64, "psi")))
+        return psi
+
+    def fep(self, u_target, u_sampling=None, beta=1.0):
+        """Zwanzig estimate f = -ln <exp(-beta (u_target - u_sampling))> over the samples (1-D CUDA
+        float64 tensors, any stride, e.g. a column of the components).  Returns a dict with f, its
+        standard error for independent samples, the Kish n_eff and the smallest reduced difference."""
+        import torch
+
+        def strided(t, name):
+            if t is None:
+                return None, 0
+            if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or t.dim() != 1:
+                raise TypeError("%s must be a 1-D CUDA float64 tensor" % name)
+            return t.data_ptr(), int(t.stride(0))
+
+        pt, st = strided(u_target, "u_target")
+        ps, ss = strided(u_sampling, "u_sampling")
+        if u_sampling is not None and u_sampling.shape[0] != u_target.shape[0]:
+            raise ValueError("u_target and u_sampling differ in length")
+        out = (C.c_double * 4)()
+        self._check(self._L.algdock_fep(self.h, int(u_target.shape[0]), pt, st, ps, ss, float(beta), out))
+        return {"f": out[0], "sigma": out[1], "n_eff": out[2], "du_min": out[3]}
 
     def energy_force(self, state_of, x, force, comps=None):
         import torch

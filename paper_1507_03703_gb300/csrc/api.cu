@@ -154,6 +154,9 @@ void algdock_destroy(algdock_ctx* c) {
   cudaFree(c->d_mbar);
   cudaFree(c->d_learn);
   cudaFree(c->d_proto);
+  cudaFree(c->d_rec);
+  cudaFree(c->d_lig_fac);
+  cudaFree(c->d_fep);
   cudaFreeHost(c->h_flag);
   delete c;
 }
@@ -431,10 +434,21 @@ algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, cons
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "ligand_load");
   cudaFree(c->d_blob);
+  cudaFree(c->d_lig_fac);
   c->d_blob = nullptr;
+  c->d_lig_fac = nullptr;
   c->has_ligand = false;
+  // target-force-field factors of each atom, FP64
+  std::vector<TargetFactors> fac(na);
+  for (int i = 0; i < na; ++i) {
+    const double two_r = 2.0 * L->rstar[i];
+    fac[i] = TargetFactors{sqrtA(L->rstar[i], L->eps[i]), sqrt(2.0 * L->eps[i]) * two_r * two_r * two_r,
+                           kCoulomb * L->charge[i], 0.0};
+  }
   e = cudaMalloc(&c->d_blob, (size_t)w * 4);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_blob, blob.data(), (size_t)w * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_lig_fac, sizeof(TargetFactors) * na);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_lig_fac, fac.data(), sizeof(TargetFactors) * na, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(c, e, "ligand_load");
   c->lig = Y;
   build_learned_topo(na, nb, L->bonds, &c->ltopo);
@@ -607,6 +621,96 @@ algdock_status algdock_mean_pacc(algdock_ctx* c, int64_t N, const double* comps_
   if (e == cudaSuccess) e = cudaMemcpyAsync(p, out, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "mean_pacc");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_receptor_load(algdock_ctx* c, int32_t n_rec, const double* xyz, const double* rstar,
+                                    const double* eps, const double* q) {
+  ALGDOCK_TRY(c)
+  if (n_rec < 0 || (n_rec > 0 && (!xyz || !rstar || !eps || !q)))
+    return fail(c, ALGDOCK_E_INVALID, "receptor_load: null argument");
+  Device g(c->device);
+  std::vector<double> hx, hr, he, hq;
+  cudaError_t e = host_view(c->stream, xyz, 3 * (size_t)n_rec, hx);
+  if (e == cudaSuccess) e = host_view(c->stream, rstar, n_rec, hr);
+  if (e == cudaSuccess) e = host_view(c->stream, eps, n_rec, he);
+  if (e == cudaSuccess) e = host_view(c->stream, q, n_rec, hq);
+  if (e != cudaSuccess) return cuda_fail(c, e, "receptor_load");
+  for (int j = 0; j < n_rec; ++j)
+    if (!isfinite(hx[3 * j]) || !isfinite(hx[3 * j + 1]) || !isfinite(hx[3 * j + 2]) || !isfinite(hr[j]) ||
+        !isfinite(he[j]) || !isfinite(hq[j]) || he[j] < 0)
+      return fail(c, ALGDOCK_E_NUMERIC, "receptor_load: non-finite or negative receptor parameter");
+  // a[j] = (x_hi, y_hi, z_hi, sqrt(A_j)), b[j] = (x_lo, y_lo, z_lo, sqrt(B_j)), q[j] / 4
+  const size_t n = n_rec > 0 ? (size_t)n_rec : 1;
+  std::vector<float4> ha(n), hb(n);
+  std::vector<float> hqq(n, 0.f);
+  for (int j = 0; j < n_rec; ++j) {
+    float hi[3], lo[3];
+    for (int k = 0; k < 3; ++k) {
+      hi[k] = (float)hx[3 * j + k];
+      lo[k] = (float)(hx[3 * j + k] - (double)hi[k]);
+    }
+    const double two_r = 2.0 * hr[j];
+    ha[j] = make_float4(hi[0], hi[1], hi[2], (float)sqrtA(hr[j], he[j]));
+    hb[j] = make_float4(lo[0], lo[1], lo[2], (float)(sqrt(2.0 * he[j]) * two_r * two_r * two_r));
+    hqq[j] = (float)(hq[j] / 4.0);
+  }
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "receptor_load");
+  cudaFree(c->d_rec);
+  c->d_rec = nullptr;
+  c->n_rec = -1;
+  const size_t bytes = 32 * n + 4 * n;
+  e = cudaMalloc(&c->d_rec, bytes);
+  uint8_t* base = (uint8_t*)c->d_rec;
+  if (e == cudaSuccess) e = cudaMemcpy(base, ha.data(), 16 * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(base + 16 * n, hb.data(), 16 * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(base + 32 * n, hqq.data(), 4 * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(c, e, "receptor_load");
+  c->n_rec = n_rec;
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_target_interaction(algdock_ctx* c, int64_t N, const float* x, double* psi) {
+  ALGDOCK_TRY(c)
+  if (!c->has_ligand || c->n_rec < 0)
+    return fail(c, ALGDOCK_E_STATE, "target_interaction: load the ligand and the receptor first");
+  if (N < 0) return fail(c, ALGDOCK_E_INVALID, "target_interaction: N < 0");
+  if (N == 0) return ALGDOCK_OK;
+  if (!is_device_ptr(x) || !is_device_ptr(psi))
+    return fail(c, ALGDOCK_E_INVALID, "target_interaction: x and psi must be device pointers");
+  Device g(c->device);
+  const size_t n = c->n_rec > 0 ? (size_t)c->n_rec : 1;
+  const uint8_t* base = (const uint8_t*)c->d_rec;
+  cudaError_t e = launch_target_interaction(c->stream, N, c->lig.na, x, c->d_lig_fac, (const float4*)base,
+                                            (const float4*)(base + 16 * n), (const float*)(base + 32 * n),
+                                            c->n_rec, psi);
+  if (e != cudaSuccess) return cuda_fail(c, e, "target_interaction");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_fep(algdock_ctx* c, int64_t N, const double* u_target, int64_t stride_target,
+                           const double* u_sampling, int64_t stride_sampling, double beta, double* result) {
+  ALGDOCK_TRY(c)
+  if (N < 1 || !u_target || !result || stride_target < 0 || stride_sampling < 0 || !isfinite(beta))
+    return fail(c, ALGDOCK_E_INVALID, "fep: need N >= 1, strides >= 0, finite beta and non-null arrays");
+  if (!is_device_ptr(u_target) || (u_sampling && !is_device_ptr(u_sampling)))
+    return fail(c, ALGDOCK_E_INVALID, "fep: energies must be device pointers");
+  Device g(c->device);
+  cudaError_t e = cudaSuccess;
+  if (!c->d_fep) e = cudaMalloc(&c->d_fep, fep_scratch_bytes());
+  if (e != cudaSuccess) return cuda_fail(c, e, "fep");
+  double* out = (double*)((uint8_t*)c->d_fep + fep_scratch_bytes() - 8 * sizeof(double));
+  double h[5];
+  e = launch_fep(c->stream, N, u_target, stride_target, u_sampling, stride_sampling, beta, c->d_fep, out);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fep");
+  for (int k = 0; k < 4; ++k) result[k] = h[k];
+  if (h[4] > 0) return fail(c, ALGDOCK_E_NUMERIC, "fep: NaN or -inf energy difference");
   return ALGDOCK_OK;
   ALGDOCK_CATCH(c)
 }

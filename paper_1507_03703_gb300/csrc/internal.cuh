@@ -95,6 +95,11 @@ struct LigandLayout {
   float k_rest, d0;
 };
 
+// Target-force-field factors of one ligand atom (FP64): sqrt(A_i), sqrt(B_i), 332.0637 q_i.
+struct __align__(32) TargetFactors {
+  double sA, sB, qC, pad;
+};
+
 // Torsion tree of the learned proposal: root atom 0, the first 16 rotatable bonds in bond order.
 constexpr int kLearnTmax = 16;
 struct LearnedTopo {
@@ -136,6 +141,12 @@ struct algdock_ctx {
   // protocol initialization: device results (4 doubles) and resampling weights, grown on demand
   void* d_proto = nullptr;
   size_t proto_bytes = 0;
+  // end points: receptor atoms of the target force field (float4 a[n], float4 b[n], float q[n]),
+  // the ligand's FP64 target factors (sqrt(A_i), sqrt(B_i), 332.0637 q_i, 0), FEP scratch
+  void* d_rec = nullptr;
+  int n_rec = -1;  // -1: no receptor loaded
+  algdock::TargetFactors* d_lig_fac = nullptr;
+  void* d_fep = nullptr;
 };
 
 namespace algdock {
@@ -184,6 +195,13 @@ cudaError_t learned_propose(cudaStream_t s, const algdock_ctx& c, const float* p
                             int64_t n_rep, const int32_t* state_of, float* x, double* comps, int n_moves,
                             int n_torsions, uint64_t seed, uint64_t cycle, int64_t rep_offset, int32_t* accepted,
                             int64_t* counters, void* scratch);
+int target_samples_per_block(int na);
+cudaError_t launch_target_interaction(cudaStream_t s, int64_t N, int na, const float* x, const TargetFactors* lig_fac,
+                                      const float4* rec_a, const float4* rec_b, const float* rec_q, int n_rec,
+                                      double* psi);
+size_t fep_scratch_bytes();
+cudaError_t launch_fep(cudaStream_t s, int64_t N, const double* ut, int64_t st, const double* us, int64_t ss,
+                       double beta, void* scratch, double* out_dev);
 cudaError_t launch_exchange(cudaStream_t s, const algdock_ctx& c, int n_ladders, int K, int state_offset,
                             const double* comps, int32_t* config_of, int32_t* state_of, int n_sweeps, int max_sep,
                             uint64_t seed, uint64_t cycle, int64_t ladder_offset, int64_t* attempts,
