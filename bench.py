@@ -38,6 +38,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-mbar", action="store_true")
     p.add_argument("--no-learned", action="store_true")
+    p.add_argument("--no-fep", action="store_true", help="skip the end-point (f_DE) measurement")
+    p.add_argument("--fep-only", action="store_true", help="only the end-point (f_DE) measurement, after warm-up")
     p.add_argument("--no-bpmf", action="store_true", help="skip the BPMF effective-samples comparison")
     p.add_argument("--no-protocol", action="store_true", help="skip the protocol-initialization measurement")
     p.add_argument("--protocol-only", action="store_true",
@@ -399,6 +401,62 @@ def protocol_build(ctx, sys_, stream, n_seeds=50, seed=21):
     return out
 
 
+FLOPS_PER_TARGET_PAIR = 18  # 3 differences, r^2 (3 mul + 2 add), 1 reciprocal, 3 powers, 3 multiply-adds
+
+
+def fep_endpoint(ctx, run, sys_, stream, sm_max, n_samples=16384, first_cycle=30_000):
+    """f_DE ("Estimation": Zwanzig perturbation of milestone D samples into the target force field,
+    whose receptor-ligand energies are computed directly).  The configuration at milestone D
+    (alpha = 1, 300 K) of every chain is taken each cycle until n_samples are gathered; then the
+    target interaction (one launch over all samples) and the FEP reduction are timed with CUDA
+    events on the launching stream."""
+    import torch
+    lig, rec = sys_.ligand, sys_.receptor
+    ctx.receptor_load(rec)
+    kD = N_STATES_BC + N_STATES_CD - 1
+    dev = run.x.device
+    xs = torch.empty((n_samples, lig.n_atoms, 3), dtype=torch.float32, device=dev)
+    psi_g = torch.empty(n_samples, dtype=torch.float64, device=dev)
+    filled, cyc = 0, first_cycle
+    while filled < n_samples:
+        run.cycle(cyc, N_VV)
+        slots = torch.nonzero(run.state_of == kD).flatten()
+        take = min(int(slots.numel()), n_samples - filled)
+        xs[filled:filled + take] = run.x[slots[:take]]
+        psi_g[filled:filled + take] = run.comps[slots[:take], 3]
+        filled += take
+        cyc += 1
+    psi_t = torch.empty(n_samples, dtype=torch.float64, device=dev)
+    beta = 1.0 / (0.0019872043 * 300.0)
+    for _ in range(3):
+        ctx.target_interaction(xs, psi_t)
+        ctx.fep(psi_t, psi_g, beta=beta)
+    torch.cuda.synchronize()
+    ti, fe = [], []
+    for _ in range(10):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        ctx.target_interaction(xs, psi_t)
+        e[1].record(stream)
+        r = ctx.fep(psi_t, psi_g, beta=beta)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        ti.append(e[0].elapsed_time(e[1]))
+        fe.append(e[1].elapsed_time(e[2]))
+    ti_ms, fe_ms = float(np.median(ti)), float(np.median(fe))
+    pairs = n_samples * lig.n_atoms * rec.n_atoms
+    peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = pairs * FLOPS_PER_TARGET_PAIR / (ti_ms * 1e-3) / 1e12
+    return {"samples": n_samples, "milestone": "D (alpha = 1, 300 K)", "f_DE_kT": r["f"], "sigma_kT": r["sigma"],
+            "n_eff": r["n_eff"], "min_target_interaction_kcal": float(psi_t.min().item()),
+            "target_interaction_ms": ti_ms, "fep_reduction_ms_incl_result_copy": fe_ms, "pairs_per_s": pairs / (ti_ms * 1e-3),
+            "configurations_per_s": n_samples / ((ti_ms + fe_ms) * 1e-3),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "kernel": "target_interaction_kernel",
+                         "flops_per_launch": pairs * FLOPS_PER_TARGET_PAIR,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_max}}
+
+
 def oracle_cpu_baseline(sys_, n_rep=65536, n_threads=0):
     """The FP64 oracle as it stands on this host's cores: one HMC trial of 50 VV steps for a
     bounded sample of replicas spread over all states (about 10-30 s on a 16-core host)."""
@@ -534,6 +592,12 @@ def main():
                              learned_cycles=args.learned_cycles, window=args.bpmf_window)
         print(json.dumps({"bpmf_eff_samples": r}))
         return
+    if args.fep_only:
+        for w in range(args.warmup):
+            step(w)
+        print(json.dumps({"fep_endpoint": fep_endpoint(ctx, run, sys_, stream, measured_peaks().get("sm_max_mhz")
+                                                       or 2070.0)}))
+        return
     launches_per_step = 1 + len(legs) + 1 + len(legs)  # hmc, exchange per leg, one evaluate, u_kn per leg
     for w in range(args.warmup):
         step(w)
@@ -619,6 +683,8 @@ def main():
         f, it = ctx.mbar(u, N_k, tol=1e-10, max_iter=20000)
         extra["mbar_K"], extra["mbar_N"], extra["mbar_iters_to_1e-10"] = len(T), N, it
         del u, comps_hist
+    if not args.no_fep and rank == 0:
+        extra["fep_endpoint"] = fep_endpoint(ctx, run, sys_, stream, sm_max)
     if not args.no_learned and rank == 0:
         # rigid-body learned moves (the paper's external-coordinate moves with a learned proposal) at
         # the paper's own regime (alpha ~ 0.01), mid-leg, and the fully coupled end

@@ -641,32 +641,42 @@ algdock_status algdock_receptor_load(algdock_ctx* c, int32_t n_rec, const double
     if (!isfinite(hx[3 * j]) || !isfinite(hx[3 * j + 1]) || !isfinite(hx[3 * j + 2]) || !isfinite(hr[j]) ||
         !isfinite(he[j]) || !isfinite(hq[j]) || he[j] < 0)
       return fail(c, ALGDOCK_E_NUMERIC, "receptor_load: non-finite or negative receptor parameter");
-  // a[j] = (x_hi, y_hi, z_hi, sqrt(A_j)), b[j] = (x_lo, y_lo, z_lo, sqrt(B_j)), q[j] / 4
-  const size_t n = n_rec > 0 ? (size_t)n_rec : 1;
-  std::vector<float4> ha(n), hb(n);
-  std::vector<float> hqq(n, 0.f);
-  for (int j = 0; j < n_rec; ++j) {
-    float hi[3], lo[3];
-    for (int k = 0; k < 3; ++k) {
-      hi[k] = (float)hx[3 * j + k];
-      lo[k] = (float)(hx[3 * j + k] - (double)hi[k]);
+  // pairs of atoms (2k, 2k + 1) for the paired FP32 instructions; an odd count ends with a zero
+  // atom (no coefficients), whose terms vanish
+  const size_t n_pairs = n_rec > 0 ? ((size_t)n_rec + 1) / 2 : 1;
+  std::vector<ReceptorPair> hp(n_pairs);
+  std::vector<float2> hq2(n_pairs, make_float2(0.f, 0.f));
+  float hi[2][3], lo[2][3], sa[2], sb[2], qq[2];
+  for (size_t k = 0; k < n_pairs; ++k) {
+    for (int u = 0; u < 2; ++u) {
+      const size_t j = 2 * k + u;
+      const bool real = j < (size_t)n_rec;
+      for (int d = 0; d < 3; ++d) {
+        hi[u][d] = real ? (float)hx[3 * j + d] : 0.f;
+        lo[u][d] = real ? (float)(hx[3 * j + d] - (double)hi[u][d]) : 0.f;
+      }
+      const double two_r = real ? 2.0 * hr[j] : 0.0;
+      sa[u] = real ? (float)sqrtA(hr[j], he[j]) : 0.f;
+      sb[u] = real ? (float)(sqrt(2.0 * he[j]) * two_r * two_r * two_r) : 0.f;
+      qq[u] = real ? (float)(hq[j] / 4.0) : 0.f;
     }
-    const double two_r = 2.0 * hr[j];
-    ha[j] = make_float4(hi[0], hi[1], hi[2], (float)sqrtA(hr[j], he[j]));
-    hb[j] = make_float4(lo[0], lo[1], lo[2], (float)(sqrt(2.0 * he[j]) * two_r * two_r * two_r));
-    hqq[j] = (float)(hq[j] / 4.0);
+    hp[k].c0 = make_float4(hi[0][0], hi[1][0], hi[0][1], hi[1][1]);
+    hp[k].c1 = make_float4(hi[0][2], hi[1][2], lo[0][0], lo[1][0]);
+    hp[k].c2 = make_float4(lo[0][1], lo[1][1], lo[0][2], lo[1][2]);
+    hp[k].c3 = make_float4(sa[0], sa[1], sb[0], sb[1]);
+    hq2[k] = make_float2(qq[0], qq[1]);
   }
   e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "receptor_load");
   cudaFree(c->d_rec);
   c->d_rec = nullptr;
   c->n_rec = -1;
-  const size_t bytes = 32 * n + 4 * n;
+  const size_t bytes = sizeof(ReceptorPair) * n_pairs + sizeof(float2) * n_pairs;
   e = cudaMalloc(&c->d_rec, bytes);
   uint8_t* base = (uint8_t*)c->d_rec;
-  if (e == cudaSuccess) e = cudaMemcpy(base, ha.data(), 16 * n, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(base + 16 * n, hb.data(), 16 * n, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(base + 32 * n, hqq.data(), 4 * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(base, hp.data(), sizeof(ReceptorPair) * n_pairs, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(base + sizeof(ReceptorPair) * n_pairs, hq2.data(), sizeof(float2) * n_pairs, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(c, e, "receptor_load");
   c->n_rec = n_rec;
   return ALGDOCK_OK;
@@ -682,11 +692,11 @@ algdock_status algdock_target_interaction(algdock_ctx* c, int64_t N, const float
   if (!is_device_ptr(x) || !is_device_ptr(psi))
     return fail(c, ALGDOCK_E_INVALID, "target_interaction: x and psi must be device pointers");
   Device g(c->device);
-  const size_t n = c->n_rec > 0 ? (size_t)c->n_rec : 1;
+  const size_t n_pairs = c->n_rec > 0 ? ((size_t)c->n_rec + 1) / 2 : 1;
   const uint8_t* base = (const uint8_t*)c->d_rec;
-  cudaError_t e = launch_target_interaction(c->stream, N, c->lig.na, x, c->d_lig_fac, (const float4*)base,
-                                            (const float4*)(base + 16 * n), (const float*)(base + 32 * n),
-                                            c->n_rec, psi);
+  cudaError_t e = launch_target_interaction(c->stream, N, c->lig.na, x, c->d_lig_fac, (const ReceptorPair*)base,
+                                            (const float2*)(base + sizeof(ReceptorPair) * n_pairs),
+                                            c->n_rec > 0 ? (int)n_pairs : 0, psi);
   if (e != cudaSuccess) return cuda_fail(c, e, "target_interaction");
   return ALGDOCK_OK;
   ALGDOCK_CATCH(c)

@@ -10,9 +10,10 @@
 namespace algdock {
 namespace {
 
-constexpr int kTIThreads = 256;                     // threads of a target-interaction block
-constexpr int kTIPoints = 2 * kTIThreads;           // (sample, atom) points per block, two per thread
-constexpr int kRecTile = 256;                       // receptor atoms staged per shared-memory tile
+constexpr int kTIThreads = 128;                     // threads of a target-interaction block
+constexpr int kTIPer = 4;                           // (configuration, atom) points per thread
+constexpr int kTIPoints = kTIPer * kTIThreads;      // points per block
+constexpr int kRecPairTile = 128;                   // receptor atom pairs staged per shared-memory tile
 constexpr int kFepThreads = 256;
 constexpr int kFepMaxBlocks = 2 * 152;
 
@@ -22,86 +23,120 @@ __device__ __forceinline__ float rcp_approx(float v) {
   return r;
 }
 
-// One thread evaluates two (sample, atom) points against every receptor atom.  A block holds whole
-// samples (spb of them, spb * na <= 512 points), so the per-sample sums stay inside the block and
-// are taken in a fixed order.  Receptor atom j: a[j] = (x_hi, y_hi, z_hi, sqrt(A_j)), b[j] = (x_lo,
-// y_lo, z_lo, sqrt(B_j)), q[j] = q_j / 4, with x = x_hi + x_lo the FP64 coordinate, so that the
-// difference (x_L - x_hi) - x_lo carries the rounding of the difference rather than of the
-// coordinate.  Each term is FP32 (one approximate reciprocal; the attractive and electrostatic
-// floors at 2 A reuse it); a tile's terms are summed in FP32 and tiles in FP64.
+// Two FP32 values in one 64-bit register pair, for the paired FP32 instructions of sm_100-class
+// GPUs (add/sub/mul/fma .f32x2): one instruction serves a pair of receptor atoms.
+typedef uint64_t f32x2;
+__device__ __forceinline__ f32x2 pack2(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
+// Each thread evaluates kTIPer (configuration, atom) points against every receptor atom, two
+// receptor atoms per paired instruction.  A block holds whole configurations (spb of them,
+// spb * na <= 512 points), so the per-configuration sums stay inside the block and are taken in a
+// fixed order.  Receptor atoms j, j' = 2k, 2k + 1 (see ReceptorPair): x = x_hi + x_lo is the FP64
+// coordinate, so that the difference (x_L - x_hi) - x_lo carries the rounding of the difference
+// rather than of the coordinate.  Each term is FP32 (one approximate reciprocal; the floors of the
+// attractive and electrostatic sums at 2 A are minima of the reciprocal powers, which equal the
+// powers of max(r, 2)); a tile's terms are summed in FP32 and tiles in FP64.
 __global__ void __launch_bounds__(kTIThreads) target_interaction_kernel(
     int64_t N, int na, int spb, const float* __restrict__ x, const TargetFactors* __restrict__ lig_fac,
-    const float4* __restrict__ rec_a, const float4* __restrict__ rec_b, const float* __restrict__ rec_q, int n_rec,
-    double* __restrict__ psi) {
-  __shared__ float4 s_a[kRecTile];
-  __shared__ float4 s_b[kRecTile];
-  __shared__ float s_q[kRecTile];
+    const ReceptorPair* __restrict__ rec, const float2* __restrict__ rec_q, int n_pairs, double* __restrict__ psi) {
+  __shared__ ReceptorPair s_p[kRecPairTile];
+  __shared__ float2 s_q[kRecPairTile];
   __shared__ double s_e[kTIPoints];
   const int tid = threadIdx.x;
   const int64_t s0 = (int64_t)blockIdx.x * spb;
   const int nsamp = (int)min((int64_t)spb, N - s0);
   const int npts = nsamp * na;
-  const int p0 = tid, p1 = tid + kTIThreads;
-  const bool v0 = p0 < npts, v1 = p1 < npts;
   const float* xb = x + 3 * (s0 * na);
-  const float x0 = v0 ? xb[3 * p0] : 0.f, y0 = v0 ? xb[3 * p0 + 1] : 0.f, z0 = v0 ? xb[3 * p0 + 2] : 0.f;
-  const float x1 = v1 ? xb[3 * p1] : 0.f, y1 = v1 ? xb[3 * p1 + 1] : 0.f, z1 = v1 ? xb[3 * p1 + 2] : 0.f;
   const float rmin2 = (float)(kRepulsiveMinDist * kRepulsiveMinDist);
-  const float amin2 = (float)(kAttractiveMinDist * kAttractiveMinDist);
-  const float amin2_inv = 1.0f / amin2;
+  const float amin2_inv = (float)(1.0 / (kAttractiveMinDist * kAttractiveMinDist));
   const float amin6_inv = amin2_inv * amin2_inv * amin2_inv;
-  double r0 = 0.0, a0 = 0.0, e0 = 0.0, r1 = 0.0, a1 = 0.0, e1 = 0.0;
-  for (int base = 0; base < n_rec; base += kRecTile) {
-    const int m = min(kRecTile, n_rec - base);
+  f32x2 X[kTIPer], Y[kTIPer], Z[kTIPer];
+  double dr[kTIPer], da[kTIPer], de[kTIPer];
+#pragma unroll
+  for (int k = 0; k < kTIPer; ++k) {
+    const int p = tid + k * kTIThreads;
+    const bool v = p < npts;
+    const float a = v ? xb[3 * p] : 0.f, b = v ? xb[3 * p + 1] : 0.f, c = v ? xb[3 * p + 2] : 0.f;
+    X[k] = pack2(a, a);
+    Y[k] = pack2(b, b);
+    Z[k] = pack2(c, c);
+    dr[k] = da[k] = de[k] = 0.0;
+  }
+  for (int base = 0; base < n_pairs; base += kRecPairTile) {
+    const int m = min(kRecPairTile, n_pairs - base);
     __syncthreads();
     for (int t = tid; t < m; t += kTIThreads) {
-      s_a[t] = rec_a[base + t];
-      s_b[t] = rec_b[base + t];
+      s_p[t] = rec[base + t];
       s_q[t] = rec_q[base + t];
     }
     __syncthreads();
-    float fr0 = 0.f, fa0 = 0.f, fe0 = 0.f, fr1 = 0.f, fa1 = 0.f, fe1 = 0.f;
-#pragma unroll 4
+    f32x2 fr[kTIPer], fa[kTIPer], fe[kTIPer];
+#pragma unroll
+    for (int k = 0; k < kTIPer; ++k) fr[k] = fa[k] = fe[k] = 0ull;
+#pragma unroll 2
     for (int t = 0; t < m; ++t) {
-      const float4 A = s_a[t];
-      const float4 B = s_b[t];
-      const float Q = s_q[t];
-      {
-        const float dx = (x0 - A.x) - B.x, dy = (y0 - A.y) - B.y, dz = (z0 - A.z) - B.z;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float i2 = rcp_approx(fmaxf(r2, rmin2));
-        const float i6 = i2 * i2 * i2;
-        const bool far = r2 >= amin2;
-        fr0 = fmaf(A.w, i6 * i6, fr0);
-        fa0 = fmaf(B.w, far ? i6 : amin6_inv, fa0);
-        fe0 = fmaf(Q, far ? i2 : amin2_inv, fe0);
-      }
-      {
-        const float dx = (x1 - A.x) - B.x, dy = (y1 - A.y) - B.y, dz = (z1 - A.z) - B.z;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float i2 = rcp_approx(fmaxf(r2, rmin2));
-        const float i6 = i2 * i2 * i2;
-        const bool far = r2 >= amin2;
-        fr1 = fmaf(A.w, i6 * i6, fr1);
-        fa1 = fmaf(B.w, far ? i6 : amin6_inv, fa1);
-        fe1 = fmaf(Q, far ? i2 : amin2_inv, fe1);
+      const ReceptorPair R = s_p[t];
+      const float2 q = s_q[t];
+      const f32x2 hx = pack2(R.c0.x, R.c0.y), hy = pack2(R.c0.z, R.c0.w), hz = pack2(R.c1.x, R.c1.y);
+      const f32x2 lx = pack2(R.c1.z, R.c1.w), ly = pack2(R.c2.x, R.c2.y), lz = pack2(R.c2.z, R.c2.w);
+      const f32x2 A = pack2(R.c3.x, R.c3.y), B = pack2(R.c3.z, R.c3.w), Q = pack2(q.x, q.y);
+#pragma unroll
+      for (int k = 0; k < kTIPer; ++k) {
+        const f32x2 dx = sub2(sub2(X[k], hx), lx), dy = sub2(sub2(Y[k], hy), ly), dz = sub2(sub2(Z[k], hz), lz);
+        const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        float ra, rb;
+        unpack2(r2, ra, rb);
+        const float ia = rcp_approx(fmaxf(ra, rmin2)), ib = rcp_approx(fmaxf(rb, rmin2));
+        const f32x2 i2 = pack2(ia, ib);
+        const f32x2 i6 = mul2(mul2(i2, i2), i2);
+        fr[k] = fma2(A, mul2(i6, i6), fr[k]);
+        float sa, sb;
+        unpack2(i6, sa, sb);
+        fa[k] = fma2(B, pack2(fminf(sa, amin6_inv), fminf(sb, amin6_inv)), fa[k]);
+        fe[k] = fma2(Q, pack2(fminf(ia, amin2_inv), fminf(ib, amin2_inv)), fe[k]);
       }
     }
-    r0 += (double)fr0;
-    a0 += (double)fa0;
-    e0 += (double)fe0;
-    r1 += (double)fr1;
-    a1 += (double)fa1;
-    e1 += (double)fe1;
+#pragma unroll
+    for (int k = 0; k < kTIPer; ++k) {
+      float a, b;
+      unpack2(fr[k], a, b);
+      dr[k] += (double)a + (double)b;
+      unpack2(fa[k], a, b);
+      da[k] += (double)a + (double)b;
+      unpack2(fe[k], a, b);
+      de[k] += (double)a + (double)b;
+    }
   }
   // atom energy sqrt(A_i) LJr - sqrt(B_i) |LJa| + 332.0637 q_i elec
-  if (v0) {
-    const TargetFactors f = lig_fac[p0 % na];
-    s_e[p0] = f.sA * r0 - f.sB * a0 + f.qC * e0;
-  }
-  if (v1) {
-    const TargetFactors f = lig_fac[p1 % na];
-    s_e[p1] = f.sA * r1 - f.sB * a1 + f.qC * e1;
+#pragma unroll
+  for (int k = 0; k < kTIPer; ++k) {
+    const int p = tid + k * kTIThreads;
+    if (p < npts) {
+      const TargetFactors f = lig_fac[p % na];
+      s_e[p] = f.sA * dr[k] - f.sB * da[k] + f.qC * de[k];
+    }
   }
   __syncthreads();
   for (int k = tid; k < nsamp; k += kTIThreads) {  // up to 512 configurations (one-atom ligands)
@@ -224,13 +259,12 @@ __global__ void __launch_bounds__(kFepThreads) fep_final_kernel(int64_t N, int n
 int target_samples_per_block(int na) { return na > 0 ? kTIPoints / na : 0; }
 
 cudaError_t launch_target_interaction(cudaStream_t s, int64_t N, int na, const float* x, const TargetFactors* lig_fac,
-                                      const float4* rec_a, const float4* rec_b, const float* rec_q, int n_rec,
-                                      double* psi) {
+                                      const ReceptorPair* rec, const float2* rec_q, int n_pairs, double* psi) {
   if (N <= 0) return cudaSuccess;
   const int spb = target_samples_per_block(na);
   const int64_t blocks = (N + spb - 1) / spb;
-  target_interaction_kernel<<<(unsigned)blocks, kTIThreads, 0, s>>>(N, na, spb, x, lig_fac, rec_a, rec_b, rec_q,
-                                                                   n_rec, psi);
+  target_interaction_kernel<<<(unsigned)blocks, kTIThreads, 0, s>>>(N, na, spb, x, lig_fac, rec, rec_q, n_pairs,
+                                                                   psi);
   return cudaGetLastError();
 }
 

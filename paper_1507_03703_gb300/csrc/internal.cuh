@@ -100,6 +100,14 @@ struct __align__(32) TargetFactors {
   double sA, sB, qC, pad;
 };
 
+// Two receptor atoms j, j' of the target interaction, laid out for paired FP32 instructions:
+// c0 = (x_hi, x_hi', y_hi, y_hi'), c1 = (z_hi, z_hi', x_lo, x_lo'), c2 = (y_lo, y_lo', z_lo, z_lo'),
+// c3 = (sqrt(A), sqrt(A'), sqrt(B), sqrt(B')), with x = x_hi + x_lo the FP64 coordinate.  The
+// charges q/4 of the pair sit in a float2 array beside.  An odd count ends with a zero atom.
+struct __align__(16) ReceptorPair {
+  float4 c0, c1, c2, c3;
+};
+
 // Torsion tree of the learned proposal: root atom 0, the first 16 rotatable bonds in bond order.
 constexpr int kLearnTmax = 16;
 struct LearnedTopo {
@@ -141,7 +149,7 @@ struct algdock_ctx {
   // protocol initialization: device results (4 doubles) and resampling weights, grown on demand
   void* d_proto = nullptr;
   size_t proto_bytes = 0;
-  // end points: receptor atoms of the target force field (float4 a[n], float4 b[n], float q[n]),
+  // end points: receptor atoms of the target force field (ReceptorPair[n_pairs], float2 q[n_pairs]),
   // the ligand's FP64 target factors (sqrt(A_i), sqrt(B_i), 332.0637 q_i, 0), FEP scratch
   void* d_rec = nullptr;
   int n_rec = -1;  // -1: no receptor loaded
@@ -197,8 +205,7 @@ cudaError_t learned_propose(cudaStream_t s, const algdock_ctx& c, const float* p
                             int64_t* counters, void* scratch);
 int target_samples_per_block(int na);
 cudaError_t launch_target_interaction(cudaStream_t s, int64_t N, int na, const float* x, const TargetFactors* lig_fac,
-                                      const float4* rec_a, const float4* rec_b, const float* rec_q, int n_rec,
-                                      double* psi);
+                                      const ReceptorPair* rec, const float2* rec_q, int n_pairs, double* psi);
 size_t fep_scratch_bytes();
 cudaError_t launch_fep(cudaStream_t s, int64_t N, const double* ut, int64_t st, const double* us, int64_t ss,
                        double beta, void* scratch, double* out_dev);
