@@ -146,16 +146,17 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profiled_traffic():
-    """DRAM bytes per HMC launch from the committed ncu summary, if it was taken on the current
-    source of the kernel (else None)."""
+def profiled_traffic(profile="hmc_kernel_paper_scale.md", source="hmc.cu"):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source
+    of the kernel's file (else None)."""
     import hashlib
+    key = source.replace(".", "_") + "_sha256:"
     try:
-        text = open(os.path.join(ROOT, "profiles", "hmc_kernel_paper_scale.md")).read()
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
         vals = dict(l.strip().split(": ", 1) for l in text.splitlines() if l.strip().startswith(
-            ("traffic_bytes_per_launch:", "hmc_cu_sha256:")))
-        src = open(os.path.join(ROOT, "paper_1507_03703_gb300", "csrc", "hmc.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest() != vals["hmc_cu_sha256"]:
+            ("traffic_bytes_per_launch:", key)))
+        src = open(os.path.join(ROOT, "paper_1507_03703_gb300", "csrc", source), "rb").read()
+        if hashlib.sha256(src).hexdigest() != vals[key[:-1]]:
             return None
         return int(vals["traffic_bytes_per_launch"])
     except Exception:
@@ -453,6 +454,7 @@ def fep_endpoint(ctx, run, sys_, stream, sm_max, n_samples=16384, first_cycle=30
             "configurations_per_s": n_samples / ((ti_ms + fe_ms) * 1e-3),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "kernel": "target_interaction_kernel",
+                         "traffic": profiled_traffic("target_interaction_paper_scale.md", "endpoints.cu"),
                          "flops_per_launch": pairs * FLOPS_PER_TARGET_PAIR,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_max}}
 

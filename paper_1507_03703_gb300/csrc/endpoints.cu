@@ -273,7 +273,7 @@ size_t fep_scratch_bytes() { return sizeof(Lse) * kFepMaxBlocks + 8 * sizeof(dou
 cudaError_t launch_fep(cudaStream_t s, int64_t N, const double* ut, int64_t st, const double* us, int64_t ss,
                        double beta, void* scratch, double* out_dev) {
   Lse* part = (Lse*)scratch;
-  const int64_t want = (N + 4 * kFepThreads - 1) / (4 * kFepThreads);
+  const int64_t want = (N + kFepThreads - 1) / kFepThreads;  // one sample per thread up to 304 blocks
   const int blocks = (int)max((int64_t)1, min(want, (int64_t)kFepMaxBlocks));
   fep_partial_kernel<<<blocks, kFepThreads, 0, s>>>(N, ut, st, us, ss, beta, part);
   cudaError_t e = cudaGetLastError();
