@@ -40,6 +40,8 @@ def parse():
     p.add_argument("--no-learned", action="store_true")
     p.add_argument("--no-fep", action="store_true", help="skip the end-point (f_DE) measurement")
     p.add_argument("--fep-only", action="store_true", help="only the end-point (f_DE) measurement, after warm-up")
+    p.add_argument("--no-batch", action="store_true", help="skip the multi-ligand batch measurement")
+    p.add_argument("--batch-only", action="store_true", help="only the multi-ligand batch measurement")
     p.add_argument("--no-bpmf", action="store_true", help="skip the BPMF effective-samples comparison")
     p.add_argument("--no-protocol", action="store_true", help="skip the protocol-initialization measurement")
     p.add_argument("--protocol-only", action="store_true",
@@ -402,6 +404,152 @@ def protocol_build(ctx, sys_, stream, n_seeds=50, seed=21):
     return out
 
 
+def padded_ligand(lig, n, site):
+    """The ligand padded to n atoms with inert atoms: no charge, no Lennard-Jones well, no bonded
+    term, a mass of 1e9 amu (they stay where they are put) at distinct points of a 1 A lattice
+    around the site.  Every pair and grid term of an n-atom ligand is evaluated; the real atoms'
+    forces are unchanged except for the restraint (the heavy atoms hold the centre of mass at the
+    site), which is immaterial to throughput."""
+    from paper_1507_03703_gb300 import synthetic as S
+    k = n - lig.n_atoms
+    side = int(np.ceil(k ** (1.0 / 3.0))) if k > 0 else 1
+    g = np.stack(np.meshgrid(*[np.arange(side)] * 3, indexing="ij"), -1).reshape(-1, 3)[:k]
+    pad = g - 0.5 * (side - 1) + 0.25
+    return S.Ligand(mass=np.concatenate([lig.mass, np.full(k, 1e9)]), charge=np.concatenate([lig.charge, np.zeros(k)]),
+                    rstar=np.concatenate([lig.rstar, np.full(k, 1.5)]), eps=np.concatenate([lig.eps, np.zeros(k)]),
+                    bonds=lig.bonds, bond_k=lig.bond_k, bond_r0=lig.bond_r0, angles=lig.angles, angle_k=lig.angle_k,
+                    angle_theta0=lig.angle_theta0, torsions=lig.torsions, torsion_V=lig.torsion_V,
+                    torsion_gamma=lig.torsion_gamma, x0=np.concatenate([lig.x0, pad + np.asarray(site)]))
+
+
+def batching(dev, stream, steps=10, warmup=3, seed=3):
+    """Many ligands in one launch per atoms-per-lane class: 256 ligands of U[10, 70] atoms, 64
+    states each (16 BC + 48 CD), one chain each (16384 replicas), 50 VV steps, against one
+    129^3 x 3 grid set.  Ligand atom-force evals/s (real atoms) of the HMC launches with the
+    default shapes, the autotuned shapes, the uniform layout (every replica in the 65-96-atom
+    shape) and the padded-uniform baseline (every ligand padded to 70 atoms, uniform shape); then a
+    whole cycle (HMC + exchange on both legs) captured as one CUDA graph, replayed, against the
+    same cycle launched eagerly.  L2 is flushed between timed launches."""
+    import torch
+    from paper_1507_03703_gb300 import algdock
+    from paper_1507_03703_gb300 import synthetic as S
+    from paper_1507_03703_gb300.algdock import Context
+    from paper_1507_03703_gb300.sampler import Leg, ReplicaExchange
+    sys_, ligs = S.config_batch(seed)
+    T = np.concatenate([l.T for l in sys_.legs])
+    alpha = np.concatenate([l.alpha for l in sys_.legs])
+    dt = np.concatenate([l.dt_fs for l in sys_.legs])
+    ctx = Context(dev.index or 0)
+    ctx.set_stream(stream)
+    nx, ny, nz = sys_.grid.n
+    raw = [torch.empty((nz, ny, nx), dtype=torch.float32, device=dev) for _ in range(3)]
+    ctx.grids_build(sys_.grid, sys_.receptor, *raw)
+    ctx.grids_load(sys_.grid, *raw, vmax_e=min(algdock.soft_elec_cap(l) for l in ligs))
+    del raw
+    ctx.states_set(T, alpha, dt)
+    ctx.batch_load(ligs, sys_.site)
+    L, stride = len(ligs), max(l.n_atoms for l in ligs)
+    legs = [Leg(sys_.legs[0].K, 0), Leg(sys_.legs[1].K, sys_.legs[0].K)]
+    Ktot = sum(l.K for l in legs)
+    # one placement per ligand and state slot (4 placements per ligand, reused)
+    place = [S.place_ligand(l, sys_.receptor, sys_.site, 4, seed=50 + i, n_tries=8) for i, l in enumerate(ligs)]
+    x0 = np.zeros((L * Ktot, stride, 3), dtype=np.float32)
+    b = 0
+    for leg in legs:
+        for c in range(L):
+            for k in range(leg.K):
+                x0[b + c * leg.K + k, :ligs[c].n_atoms] = place[c][k % 4]
+        b += L * leg.K
+    run = ReplicaExchange(ctx, legs, L, x0, seed=4321, batched=True)
+    lig_of = run.lig_of()
+    ctx.batch_layout(lig_of, stride)
+    evals = float(sum(ligs[c].n_atoms for c in lig_of)) * N_VV
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def time_hmc(tag, first):
+        for w in range(warmup):
+            run.hmc(first + w, N_VV)
+        ms = []
+        for s_ in range(steps):
+            flush.fill_(float(s_))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run.hmc(first + warmup + s_, N_VV)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        m = float(np.median(ms))
+        return {"ms_per_launch": m, "evals_per_s": evals / (m * 1e-3)}
+
+    out = {"workload": "%d ligands of %d-%d atoms (mean %.1f), %d states each, 1 chain, %d VV steps, 129^3 x 3 grids"
+                       % (L, min(l.n_atoms for l in ligs), stride, np.mean([l.n_atoms for l in ligs]), Ktot, N_VV),
+           "replicas": int(len(lig_of)), "ligands_per_atoms_per_lane": [int(sum(1 for l in ligs if (l.n_atoms + 31) // 32 == k))
+                                                        for k in (1, 2, 3)]}
+    out["default"] = time_hmc("default", 0)
+    chosen, tms = ctx.batch_tune(run.state_of, run.x, n_steps=N_VV, n_timed=5)
+    out["tuned_shapes"] = [{"class": k, "replicas_per_block": w, "pair_table": t} for k, (w, t) in enumerate(chosen)]
+    out["tuner_ms_per_launch"] = tms
+    out["tuned"] = time_hmc("tuned", 100)
+    ctx.batch_layout(lig_of, stride, uniform=True)
+    out["uniform"] = time_hmc("uniform", 200)
+    out["tuned_vs_uniform"] = out["tuned"]["evals_per_s"] / out["uniform"]["evals_per_s"]
+    # padded-uniform: every ligand padded to the largest size with inert atoms, one shape for all
+    x_real = run.x.clone()
+    padded = [padded_ligand(l, stride, sys_.site) for l in ligs]
+    ctx.batch_load(padded, sys_.site)
+    ctx.batch_layout(lig_of, stride, uniform=True)
+    xp = x_real.cpu().numpy()
+    for r, c in enumerate(lig_of):
+        xp[r, ligs[c].n_atoms:] = padded[c].x0[ligs[c].n_atoms:]
+    run.x.copy_(torch.from_numpy(xp))
+    out["padded_uniform"] = time_hmc("padded", 250)
+    out["padded_uniform"]["acceptance"] = float(run.acc.float().mean().item())
+    out["tuned_vs_padded_uniform"] = out["tuned"]["evals_per_s"] / out["padded_uniform"]["evals_per_s"]
+    ctx.batch_load(ligs, sys_.site)
+    run.x.copy_(x_real)
+    ctx.batch_layout(lig_of, stride)
+    ctx.batch_tune(run.state_of, run.x, n_steps=N_VV, n_timed=5)
+    # the whole cycle, eager and as one graph
+    for w in range(warmup):
+        run.hmc(300 + w, N_VV)
+        run.exchange(300 + w)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s_ in range(steps):
+        run.hmc(400 + s_, N_VV)
+        run.exchange(400 + s_)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1) / steps
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(device=dev)
+    cap.wait_stream(stream)
+    with torch.cuda.stream(cap):
+        ctx.set_stream(cap)
+        try:
+            with torch.cuda.graph(g, stream=cap, capture_error_mode="relaxed"):
+                run.hmc(500, N_VV)
+                run.exchange(500)
+        finally:
+            ctx.set_stream(stream)
+    stream.wait_stream(cap)
+    for w in range(warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s_ in range(steps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / steps
+    out["cycle_eager_ms"] = eager_ms
+    out["cycle_graph_ms"] = graph_ms
+    out["cycle_graph_evals_per_s"] = evals / (graph_ms * 1e-3)
+    out["hmc_acceptance"] = float(run.acc.float().mean().item())
+    return out
+
+
 FLOPS_PER_TARGET_PAIR = 18  # 3 differences, r^2 (3 mul + 2 add), 1 reciprocal, 3 powers, 3 multiply-adds
 
 
@@ -594,6 +742,9 @@ def main():
                              learned_cycles=args.learned_cycles, window=args.bpmf_window)
         print(json.dumps({"bpmf_eff_samples": r}))
         return
+    if args.batch_only:
+        print(json.dumps({"batching": batching(dev, stream)}))
+        return
     if args.fep_only:
         for w in range(args.warmup):
             step(w)
@@ -687,6 +838,8 @@ def main():
         del u, comps_hist
     if not args.no_fep and rank == 0:
         extra["fep_endpoint"] = fep_endpoint(ctx, run, sys_, stream, sm_max)
+    if not args.no_batch and rank == 0 and world == 1:
+        extra["batching"] = batching(dev, stream)
     if not args.no_learned and rank == 0:
         # rigid-body learned moves (the paper's external-coordinate moves with a learned proposal) at
         # the paper's own regime (alpha ~ 0.01), mid-leg, and the fully coupled end

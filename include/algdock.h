@@ -269,6 +269,58 @@ algdock_status algdock_resample(algdock_ctx* ctx, int64_t N, const double* comps
 algdock_status algdock_mean_pacc(algdock_ctx* ctx, int64_t N, const double* comps_a, const double* comps_b, int32_t ka,
                                  int32_t kb, double* p);
 
+/* ---------------------------------------------------------------- multi-ligand batches
+ * Many ligands of uneven size against one set of grids and one state table, every replica of every
+ * ligand in one HMC launch per atoms-per-lane class (no counterpart in the paper, which runs one
+ * ligand per job; each replica's trial is the one of algdock_hmc_cycle, "Sampling").  Replicas
+ * of one ligand that are consecutive in the replica order share blocks; a block stages its
+ * ligand's tables once.  Launch classes: 0: <= 32 atoms; 1: 33-64 atoms whose per-pair table fits
+ * 16-replica blocks (the one-ligand kernel then stages it too); 2: the other 33-64-atom ligands;
+ * 3: 65-96 atoms. */
+
+/* Load n_ligands ligands (each validated as by algdock_ligand_load) with one restraint.  Replaces
+ * any earlier batch and its layout; the single-ligand state (algdock_ligand_load) is untouched. */
+algdock_status algdock_batch_load(algdock_ctx* ctx, int32_t n_ligands, const algdock_ligand* ligands,
+                                  const algdock_restraint* rest);
+
+/* Replica layout: replica r runs ligand lig_of[r] (host int32 [n_rep]); positions are stored
+ * x_stride atoms apart ([n_rep][x_stride][3] float, only the first n_atoms of each used).  Builds
+ * the work lists (runs of consecutive replicas of one ligand, longest blocks first) with a default
+ * launch shape per class (the first candidate of algdock_batch_tune that fits shared memory).
+ * uniform != 0 runs every replica in the 65-96-atom class shape (the uniform baseline of a
+ * batch).  ALGDOCK_E_INVALID if a ligand's tables exceed shared memory. */
+algdock_status algdock_batch_layout(algdock_ctx* ctx, int64_t n_rep, const int32_t* lig_of, int32_t x_stride,
+                                    int32_t uniform);
+
+/* One HMC trial for every replica of the batch, as algdock_hmc_cycle (same Philox counters, with
+ * replica index rep_offset + r).  The classes run on the context's side streams, forked from and
+ * joined to its stream, so that a graph captured on that stream holds them as parallel branches.
+ * Device arrays: state_of [n_rep], x [n_rep][x_stride][3], comps [n_rep][4], dH, acc (may be NULL),
+ * counters (may be NULL). */
+algdock_status algdock_batch_hmc_cycle(algdock_ctx* ctx, const int32_t* state_of, float* x, double* comps,
+                                       double* dH, uint8_t* acc, int32_t n_steps, uint64_t seed, uint64_t cycle,
+                                       int64_t rep_offset, int64_t* counters);
+
+/* Launch shapes (for tests and tuning reports).  algdock_hmc_shape: the one-ligand HMC kernel's
+ * replicas per block and 1 if it stages the per-pair table (host int32[2]).  algdock_batch_shapes:
+ * the same per batch class (host int32 [4][2]; 0 for an empty class).  The pair-table and the
+ * pair-type kernels round differently; the replicas per block do not change a replica's
+ * arithmetic. */
+algdock_status algdock_hmc_shape(algdock_ctx* ctx, int32_t* shape);
+algdock_status algdock_batch_shapes(algdock_ctx* ctx, int32_t* shapes);
+
+/* Autotuner over the launch shape of each class (classes 0, 1: replicas per block 16 or 8 with
+ * the pair table staged, or 4 without; class 2: 8 with the table or 4 without; class 3: 4 or 8
+ * without).  The objective is the whole batch launch, classes overlapped as in production: one
+ * pass of coordinate descent, each class in turn trying its candidates with the others held, each
+ * the median of n_timed launches (after one warm-up, CUDA events) from a scratch copy of x; a
+ * candidate replaces the incumbent only if 2 % faster.  chosen (host
+ * int32 [4][2], may be NULL): replicas per block and 1 if the table is staged, per class (0 =
+ * class empty); ms (host float, may be NULL): the chosen shapes' time per launch.  x is not
+ * modified.  Allocates scratch; synchronises. */
+algdock_status algdock_batch_tune(algdock_ctx* ctx, const int32_t* state_of, const float* x, int32_t n_steps,
+                                  int32_t n_timed, int32_t* chosen, float* ms);
+
 /* ---------------------------------------------------------------- end points (target force field)
  * The thermodynamic cycle starts and ends in a target force field that differs from the sampling
  * force field ("Thermodynamic Cycle"); samples of milestones B and D are postprocessed in it and

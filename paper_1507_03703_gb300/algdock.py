@@ -32,8 +32,11 @@ EXPORTS = [
     "algdock_mlp_forward", "algdock_mlp_grad", "algdock_mlp_adam", "algdock_propose_learned",
     "algdock_external_moves", "algdock_detect_equilibration", "algdock_state_statistics", "algdock_resample",
     "algdock_mean_pacc", "algdock_receptor_load", "algdock_target_interaction", "algdock_fep",
+    "algdock_batch_load", "algdock_batch_layout", "algdock_batch_hmc_cycle", "algdock_batch_tune",
+    "algdock_hmc_shape", "algdock_batch_shapes",
 ]
 
+BATCH_CLASSES = 4             # launch classes of a multi-ligand batch
 ALPHA_MAX_EXTERNAL = 0.01     # external-coordinate moves only below this alpha ("Sampling")
 SIGMA_TRANSLATION = 0.6       # A per dimension ("Sampling")
 MLP_NFEAT, MLP_NHID, MLP_NOUT, MLP_DMAX = 64, 256, 360, 22
@@ -130,6 +133,12 @@ def load_library(path: str = LIB_PATH):
         "algdock_receptor_load": ([vp, i32, vp, vp, vp, vp], C.c_int),
         "algdock_target_interaction": ([vp, i64, vp, vp], C.c_int),
         "algdock_fep": ([vp, i64, vp, i64, vp, i64, dbl, vp], C.c_int),
+        "algdock_batch_load": ([vp, i32, vp, vp], C.c_int),
+        "algdock_batch_layout": ([vp, i64, vp, i32, i32], C.c_int),
+        "algdock_batch_hmc_cycle": ([vp, vp, vp, vp, vp, vp, i32, u64, u64, i64, vp], C.c_int),
+        "algdock_batch_tune": ([vp, vp, vp, i32, i32, vp, vp], C.c_int),
+        "algdock_hmc_shape": ([vp, vp], C.c_int),
+        "algdock_batch_shapes": ([vp, vp], C.c_int),
         "algdock_exchange": ([vp, i32, i32, i32, vp, vp, vp, i32, i32, u64, u64, i64, vp, vp], C.c_int),
         "algdock_reduced_energies": ([vp, i64, vp, vp, i32, i32, vp], C.c_int),
         "algdock_mbar": ([vp, i32, i64, vp, vp, dbl, i32, i32, vp, C.POINTER(i32)], C.c_int),
@@ -317,6 +326,63 @@ class Context:
             _dev(comps, torch.float64, "comps"), _dev(dH, torch.float64, "dH"),
             _dev(accepted, torch.uint8, "accepted"), int(n_steps), int(seed), int(cycle), int(rep_offset),
             _dev(counters, torch.int64, "counters")))
+
+    # ---------------------------------------------------------------- multi-ligand batches
+    def batch_load(self, ligands, site, k=K_RESTRAINT, d0=D0):
+        """Load many ligands (one restraint) for batched HMC."""
+        structs, keep = [], []
+        for lig in ligands:
+            st, kp = ligand_struct(lig)
+            structs.append(st)
+            keep.append(kp)
+        arr = (LigandC * len(structs))(*structs)
+        r = RestraintC()
+        for i in range(3):
+            r.site[i] = float(site[i])
+        r.k, r.d0 = float(k), float(d0)
+        self._check(self._L.algdock_batch_load(self.h, len(structs), arr, C.byref(r)))
+        self.batch_atoms = [int(st.n_atoms) for st in structs]
+
+    def batch_layout(self, lig_of, x_stride, uniform=False):
+        """Replica r runs ligand lig_of[r]; positions are stored x_stride atoms apart."""
+        lo = np.ascontiguousarray(lig_of, dtype=np.int32)
+        self._check(self._L.algdock_batch_layout(self.h, int(lo.size), lo.ctypes.data, int(x_stride),
+                                                 1 if uniform else 0))
+        self.batch_n_rep = int(lo.size)
+
+    def batch_hmc_cycle(self, state_of, x, comps, dH=None, accepted=None, n_steps=50, seed=0, cycle=0, rep_offset=0,
+                        counters=None):
+        import torch
+        self._check(self._L.algdock_batch_hmc_cycle(
+            self.h, _dev(state_of, torch.int32, "state_of"), _dev(x, torch.float32, "x"),
+            _dev(comps, torch.float64, "comps"), _dev(dH, torch.float64, "dH"),
+            _dev(accepted, torch.uint8, "accepted"), int(n_steps), int(seed), int(cycle), int(rep_offset),
+            _dev(counters, torch.int64, "counters")))
+
+    def hmc_shape(self):
+        """(replicas per block, pair table staged) of the one-ligand HMC kernel."""
+        out = (C.c_int32 * 2)()
+        self._check(self._L.algdock_hmc_shape(self.h, out))
+        return out[0], bool(out[1])
+
+    def batch_shapes(self):
+        """[(replicas per block, pair table staged)] per batch class ((0, False) if empty)."""
+        out = (C.c_int32 * (2 * BATCH_CLASSES))()
+        self._check(self._L.algdock_batch_shapes(self.h, out))
+        return [(out[2 * k], bool(out[2 * k + 1])) for k in range(BATCH_CLASSES)]
+
+    def batch_tune(self, state_of, x, n_steps=50, n_timed=3):
+        """Choose each class's launch shape by timing the whole batch launch.  Returns
+        ([(replicas per block, table staged)] per class, ms per launch of the chosen shapes);
+        classes: <= 32 atoms, 33-64 with the pair table fitting 16-replica blocks, other 33-64,
+        65-96."""
+        import torch
+        chosen = (C.c_int32 * (2 * BATCH_CLASSES))()
+        ms = C.c_float()
+        self._check(self._L.algdock_batch_tune(self.h, _dev(state_of, torch.int32, "state_of"),
+                                               _dev(x, torch.float32, "x"), int(n_steps), int(n_timed), chosen,
+                                               C.byref(ms)))
+        return [(chosen[2 * k], bool(chosen[2 * k + 1])) for k in range(BATCH_CLASSES)], ms.value
 
     def external_moves(self, state_of, x, comps, n_moves=20, seed=0, cycle=0, alpha_max=ALPHA_MAX_EXTERNAL,
                        sigma=SIGMA_TRANSLATION, rep_offset=0, accepted=None, counters=None):

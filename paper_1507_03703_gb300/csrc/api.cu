@@ -5,6 +5,7 @@
 
 #include <new>
 #include <string>
+#include <algorithm>
 #include <initializer_list>
 #include <vector>
 
@@ -119,6 +120,248 @@ double sqrtA(double rstar, double eps) {
   return sqrt(eps) * (t * t * t * t * t * t);
 }
 
+// Validates one ligand and its restraint and builds its device tables: the layout, the blob (atom
+// records, pair types, bonded terms, incidence lists, then the per-pair table) and the FP64
+// target-force-field factors of each atom.
+algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdock_restraint* R, const std::string& who,
+                            LigandLayout& Y, std::vector<uint32_t>& blob, std::vector<TargetFactors>& fac) {
+  if (!L || !R) return fail(c, ALGDOCK_E_INVALID, who + ": null argument");
+  const int na = L->n_atoms, nb = L->n_bonds, nang = L->n_angles, ntor = L->n_torsions;
+  if (na < 1 || na > kMaxAtoms) return fail(c, ALGDOCK_E_INVALID, who + ": need 1 <= n_atoms <= 96");
+  if (nb < 0 || nang < 0 || ntor < 0) return fail(c, ALGDOCK_E_INVALID, who + ": negative term count");
+  if (!L->mass || !L->charge || !L->rstar || !L->eps || (nb && (!L->bonds || !L->bond_k || !L->bond_r0)) ||
+      (nang && (!L->angles || !L->angle_k || !L->angle_theta0)) ||
+      (ntor && (!L->torsions || !L->torsion_V || !L->torsion_gamma)))
+    return fail(c, ALGDOCK_E_INVALID, who + ": null array");
+  auto bad_idx = [&](const int32_t* idx, int n, int w) {
+    for (int t = 0; t < n * w; ++t)
+      if (idx[t] < 0 || idx[t] >= na) return true;
+    return false;
+  };
+  if (bad_idx(L->bonds, nb, 2) || bad_idx(L->angles, nang, 3) || bad_idx(L->torsions, ntor, 4))
+    return fail(c, ALGDOCK_E_INVALID, who + ": atom index out of range");
+  double M = 0.0;
+  for (int i = 0; i < na; ++i) {
+    if (!(L->mass[i] > 0) || !isfinite(L->mass[i]) || !isfinite(L->charge[i]) || !isfinite(L->rstar[i]) ||
+        !(L->eps[i] >= 0) || !isfinite(L->eps[i]))
+      return fail(c, ALGDOCK_E_NUMERIC, who + ": non-finite or invalid atom parameter");
+    M += L->mass[i];
+  }
+  for (int t = 0; t < nb; ++t)
+    if (!isfinite(L->bond_k[t]) || !isfinite(L->bond_r0[t])) return fail(c, ALGDOCK_E_NUMERIC, who + ": bond");
+  for (int t = 0; t < nang; ++t)
+    if (!isfinite(L->angle_k[t]) || !isfinite(L->angle_theta0[t]))
+      return fail(c, ALGDOCK_E_NUMERIC, who + ": angle");
+  for (int t = 0; t < 3 * ntor; ++t)
+    if (!isfinite(L->torsion_V[t]) || !isfinite(L->torsion_gamma[t]))
+      return fail(c, ALGDOCK_E_NUMERIC, who + ": torsion");
+  if (!isfinite(R->k) || !isfinite(R->d0) || !isfinite(R->site[0]) || !isfinite(R->site[1]) || !isfinite(R->site[2]))
+    return fail(c, ALGDOCK_E_NUMERIC, who + ": restraint");
+
+  // graph distances (breadth-first over the bonds): exclusions within two bonds, 1-4 at three
+  std::vector<std::vector<int>> nbr(na);
+  for (int t = 0; t < nb; ++t) {
+    nbr[L->bonds[2 * t]].push_back(L->bonds[2 * t + 1]);
+    nbr[L->bonds[2 * t + 1]].push_back(L->bonds[2 * t]);
+  }
+  // pair type [j][i]: 0 nonbonded, 1 1-4 (three bonds apart), 2 excluded (within two bonds, or i == j)
+  std::vector<uint8_t> ptype((size_t)na * na, 0);
+  std::vector<int> dist(na), queue(na);
+  for (int i = 0; i < na; ++i) {
+    std::fill(dist.begin(), dist.end(), -1);
+    dist[i] = 0;
+    int h = 0, t = 0;
+    queue[t++] = i;
+    while (h < t) {
+      const int u = queue[h++];
+      if (dist[u] >= 3) continue;
+      for (int v : nbr[u])
+        if (dist[v] < 0) {
+          dist[v] = dist[u] + 1;
+          queue[t++] = v;
+        }
+    }
+    for (int j = 0; j < na; ++j) {
+      if (dist[j] >= 0 && dist[j] <= 2) ptype[(size_t)j * na + i] = 2;
+      else if (dist[j] == 3) ptype[(size_t)j * na + i] = 1;
+    }
+  }
+  // per-atom lists of the bonded force slots that act on it (role-major slot numbering:
+  // bond t role r -> r nb + t; angle -> 2 nb + r nang + t; torsion -> 2 nb + 3 nang + r ntor + t)
+  std::vector<std::vector<uint32_t>> inc(na);
+  for (int t = 0; t < nb; ++t)
+    for (int r = 0; r < 2; ++r) inc[L->bonds[2 * t + r]].push_back((uint32_t)(r * nb + t));
+  for (int t = 0; t < nang; ++t)
+    for (int r = 0; r < 3; ++r) inc[L->angles[3 * t + r]].push_back((uint32_t)(2 * nb + r * nang + t));
+  for (int t = 0; t < ntor; ++t)
+    for (int r = 0; r < 4; ++r)
+      inc[L->torsions[4 * t + r]].push_back((uint32_t)(2 * nb + 3 * nang + r * ntor + t));
+  int ninc = 0;
+  for (auto& v : inc) ninc += (int)v.size();
+
+  memset(&Y, 0, sizeof(Y));
+  Y.na = na;
+  Y.nb = nb;
+  Y.nang = nang;
+  Y.ntor = ntor;
+  Y.ninc = ninc;
+  Y.n_slots = 2 * nb + 3 * nang + 4 * ntor;
+  int w = 0;
+  auto take = [&](int words) {
+    const int o = w;
+    w += (words + 3) & ~3;
+    return o;
+  };
+  Y.off_atom_a = take(4 * na);
+  Y.off_atom_b = take(4 * na);
+  Y.off_ptype = take((na * na + 3) / 4);
+  Y.off_bond = take(4 * nb);
+  Y.off_ang = take(8 * nang);
+  Y.off_tor = take(16 * ntor);
+  Y.off_inc_start = take(na + 1);
+  Y.off_inc = take(ninc);
+  Y.words = w;
+  if ((size_t)w * 4 > 120 * 1024) return fail(c, ALGDOCK_E_INVALID, who + ": topology too large");
+  Y.off_pair = take(4 * na * na);
+  Y.words_pair = w;
+  blob.assign(w, 0u);
+  float* bf = (float*)blob.data();
+  int32_t* bi = (int32_t*)blob.data();
+  for (int i = 0; i < na; ++i) {
+    const double m = L->mass[i];
+    const double two_r = 2.0 * L->rstar[i];
+    bf[Y.off_atom_a + 4 * i + 0] = (float)(kForceToAccel / m);
+    bf[Y.off_atom_a + 4 * i + 1] = (float)L->charge[i];
+    bf[Y.off_atom_a + 4 * i + 2] = (float)sqrtA(L->rstar[i], L->eps[i]);
+    bf[Y.off_atom_a + 4 * i + 3] = (float)(sqrt(2.0 * L->eps[i]) * two_r * two_r * two_r);
+    bf[Y.off_atom_b + 4 * i + 0] = (float)L->rstar[i];
+    bf[Y.off_atom_b + 4 * i + 1] = (float)sqrt(L->eps[i]);
+    bf[Y.off_atom_b + 4 * i + 2] = (float)m;
+    bf[Y.off_atom_b + 4 * i + 3] = (float)sqrt(kForceToAccel / m);
+  }
+  memcpy((uint8_t*)(blob.data() + Y.off_ptype), ptype.data(), ptype.size());
+  for (int t = 0; t < nb; ++t) {
+    bi[Y.off_bond + 4 * t + 0] = L->bonds[2 * t];
+    bi[Y.off_bond + 4 * t + 1] = L->bonds[2 * t + 1];
+    bf[Y.off_bond + 4 * t + 2] = (float)L->bond_k[t];
+    bf[Y.off_bond + 4 * t + 3] = (float)L->bond_r0[t];
+  }
+  for (int t = 0; t < nang; ++t) {
+    for (int k = 0; k < 3; ++k) bi[Y.off_ang + 4 * t + k] = L->angles[3 * t + k];
+    bf[Y.off_ang + 4 * nang + 4 * t + 0] = (float)L->angle_k[t];
+    bf[Y.off_ang + 4 * nang + 4 * t + 1] = (float)L->angle_theta0[t];
+  }
+  for (int t = 0; t < ntor; ++t) {
+    for (int k = 0; k < 4; ++k) bi[Y.off_tor + 4 * t + k] = L->torsions[4 * t + k];
+    for (int n = 0; n < 3; ++n) {
+      const double g = L->torsion_gamma[3 * t + n];
+      bf[Y.off_tor + 4 * ntor + 4 * t + n] = (float)(0.5 * L->torsion_V[3 * t + n]);
+      bf[Y.off_tor + 8 * ntor + 4 * t + n] = (float)cos(g);
+      bf[Y.off_tor + 12 * ntor + 4 * t + n] = (float)sin(g);
+    }
+  }
+  // pair table: the Lorentz-Berthelot combination, the 1-4 scales and the exclusions folded into
+  // one record per ordered pair (FP64, rounded once); an excluded pair (and i == j) has zero
+  // coefficients and adds 1 to r^2 so that its arithmetic stays finite
+  for (int j = 0; j < na; ++j)
+    for (int i = 0; i < na; ++i) {
+      const int ty = ptype[(size_t)j * na + i];
+      const double s_lj = ty == 0 ? 1.0 : (ty == 1 ? 0.5 : 0.0);
+      const double s_el = ty == 0 ? 1.0 : (ty == 1 ? 1.0 / 1.2 : 0.0);
+      const double R = L->rstar[i] + L->rstar[j];
+      float* rec = bf + Y.off_pair + 4 * ((size_t)j * na + i);
+      rec[0] = ty == 2 ? 0.f : (float)(R * R);
+      rec[1] = (float)(12.0 * s_lj * sqrt(L->eps[i]) * sqrt(L->eps[j]));
+      rec[2] = (float)(kCoulomb * L->charge[i] * L->charge[j] * s_el);
+      rec[3] = ty == 2 ? 1.f : 0.f;
+    }
+  int pos = 0;
+  for (int i = 0; i < na; ++i) {
+    bi[Y.off_inc_start + i] = pos;
+    for (uint32_t code : inc[i]) blob[Y.off_inc + pos++] = code;
+  }
+  bi[Y.off_inc_start + na] = pos;
+  Y.total_mass = (float)M;
+  for (int k = 0; k < 3; ++k) Y.site[k] = (float)R->site[k];
+  Y.k_rest = (float)R->k;
+  Y.d0 = (float)R->d0;
+  fac.resize(na);
+  for (int i = 0; i < na; ++i) {
+    const double two_r = 2.0 * L->rstar[i];
+    fac[i] = TargetFactors{sqrtA(L->rstar[i], L->eps[i]), sqrt(2.0 * L->eps[i]) * two_r * two_r * two_r,
+                           kCoulomb * L->charge[i], 0.0};
+  }
+  return ALGDOCK_OK;
+}
+
+// Work items of one batch class: runs of consecutive replicas of one ligand, at most wpb long,
+// ordered by decreasing cost (pair work ~ n_atoms^2 plus per-atom work), so that the block scheduler
+// starts the longest blocks first.
+void batch_items(const algdock_ctx* c, int cls, int wpb, std::vector<BatchItem>& out) {
+  out.clear();
+  const int64_t n = c->batch_n_rep;
+  for (int64_t r = 0; r < n;) {
+    const int lig = c->batch_lig_of[r];
+    const int k = c->batch_uniform ? kBatchClasses - 1 : c->h_batch[lig].cls;
+    int64_t e = r + 1;
+    while (e < n && c->batch_lig_of[e] == lig && e - r < wpb) ++e;
+    if (k == cls) out.push_back(BatchItem{lig, (int32_t)r, (int32_t)(e - r), 0});
+    r = e;
+  }
+  auto cost = [&](const BatchItem& it) {
+    const double na = c->h_batch[it.lig].LL.na;
+    return it.count * (na * na + 30.0 * na);
+  };
+  std::stable_sort(out.begin(), out.end(), [&](const BatchItem& a, const BatchItem& b) { return cost(a) > cost(b); });
+}
+
+// The largest block shared memory of a class shape over the ligands it runs (0 if none).
+size_t batch_class_smem(const algdock_ctx* c, int cls, int wpb, bool table) {
+  size_t m = 0;
+  std::vector<char> used(c->n_batch, 0);
+  for (int64_t r = 0; r < c->batch_n_rep; ++r) used[c->batch_lig_of[r]] = 1;
+  for (int l = 0; l < c->n_batch; ++l) {
+    if (!used[l]) continue;
+    const int k = c->batch_uniform ? kBatchClasses - 1 : c->h_batch[l].cls;
+    if (k != cls) continue;
+    m = std::max(m, batch_block_smem(c->h_batch[l].LL, kClassApl[cls], wpb, table));
+  }
+  return m;
+}
+
+// Sets a class's shape and uploads its items.
+cudaError_t batch_set_class(algdock_ctx* c, int cls, int wpb, bool table) {
+  BatchClass& B = c->batch_cls[cls];
+  std::vector<BatchItem> items;
+  batch_items(c, cls, wpb, items);
+  cudaFree(B.d_items);
+  B.d_items = nullptr;
+  B.n_items = (int)items.size();
+  B.wpb = wpb;
+  B.table = table;
+  B.smem = batch_class_smem(c, cls, wpb, table);
+  if (items.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&B.d_items, sizeof(BatchItem) * items.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(B.d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+void batch_free(algdock_ctx* c) {
+  cudaFree(c->d_batch);
+  cudaFree(c->d_batch_blob);
+  c->d_batch = nullptr;
+  c->d_batch_blob = nullptr;
+  for (int k = 0; k < kBatchClasses; ++k) {
+    cudaFree(c->batch_cls[k].d_items);
+    c->batch_cls[k] = BatchClass{};
+  }
+  c->n_batch = 0;
+  c->batch_n_rep = 0;
+  c->h_batch.clear();
+  c->batch_lig_of.clear();
+}
+
 }  // namespace
 
 extern "C" {
@@ -157,6 +400,12 @@ void algdock_destroy(algdock_ctx* c) {
   cudaFree(c->d_rec);
   cudaFree(c->d_lig_fac);
   cudaFree(c->d_fep);
+  batch_free(c);
+  for (int k = 0; k < kBatchClasses; ++k) {
+    if (c->batch_side[k]) cudaStreamDestroy(c->batch_side[k]);
+    if (c->batch_join[k]) cudaEventDestroy(c->batch_join[k]);
+  }
+  if (c->batch_fork) cudaEventDestroy(c->batch_fork);
   cudaFreeHost(c->h_flag);
   delete c;
 }
@@ -268,167 +517,12 @@ algdock_status algdock_grids_load(algdock_ctx* c, const algdock_grid_desc* d, co
 
 algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, const algdock_restraint* R) {
   ALGDOCK_TRY(c)
-  if (!L || !R) return fail(c, ALGDOCK_E_INVALID, "ligand_load: null argument");
-  const int na = L->n_atoms, nb = L->n_bonds, nang = L->n_angles, ntor = L->n_torsions;
-  if (na < 1 || na > kMaxAtoms) return fail(c, ALGDOCK_E_INVALID, "ligand_load: need 1 <= n_atoms <= 96");
-  if (nb < 0 || nang < 0 || ntor < 0) return fail(c, ALGDOCK_E_INVALID, "ligand_load: negative term count");
-  if (!L->mass || !L->charge || !L->rstar || !L->eps || (nb && (!L->bonds || !L->bond_k || !L->bond_r0)) ||
-      (nang && (!L->angles || !L->angle_k || !L->angle_theta0)) ||
-      (ntor && (!L->torsions || !L->torsion_V || !L->torsion_gamma)))
-    return fail(c, ALGDOCK_E_INVALID, "ligand_load: null array");
-  auto bad_idx = [&](const int32_t* idx, int n, int w) {
-    for (int t = 0; t < n * w; ++t)
-      if (idx[t] < 0 || idx[t] >= na) return true;
-    return false;
-  };
-  if (bad_idx(L->bonds, nb, 2) || bad_idx(L->angles, nang, 3) || bad_idx(L->torsions, ntor, 4))
-    return fail(c, ALGDOCK_E_INVALID, "ligand_load: atom index out of range");
-  double M = 0.0;
-  for (int i = 0; i < na; ++i) {
-    if (!(L->mass[i] > 0) || !isfinite(L->mass[i]) || !isfinite(L->charge[i]) || !isfinite(L->rstar[i]) ||
-        !(L->eps[i] >= 0) || !isfinite(L->eps[i]))
-      return fail(c, ALGDOCK_E_NUMERIC, "ligand_load: non-finite or invalid atom parameter");
-    M += L->mass[i];
-  }
-  for (int t = 0; t < nb; ++t)
-    if (!isfinite(L->bond_k[t]) || !isfinite(L->bond_r0[t])) return fail(c, ALGDOCK_E_NUMERIC, "ligand_load: bond");
-  for (int t = 0; t < nang; ++t)
-    if (!isfinite(L->angle_k[t]) || !isfinite(L->angle_theta0[t]))
-      return fail(c, ALGDOCK_E_NUMERIC, "ligand_load: angle");
-  for (int t = 0; t < 3 * ntor; ++t)
-    if (!isfinite(L->torsion_V[t]) || !isfinite(L->torsion_gamma[t]))
-      return fail(c, ALGDOCK_E_NUMERIC, "ligand_load: torsion");
-  if (!isfinite(R->k) || !isfinite(R->d0) || !isfinite(R->site[0]) || !isfinite(R->site[1]) || !isfinite(R->site[2]))
-    return fail(c, ALGDOCK_E_NUMERIC, "ligand_load: restraint");
-
-  // graph distances (breadth-first over the bonds): exclusions within two bonds, 1-4 at three
-  std::vector<std::vector<int>> nbr(na);
-  for (int t = 0; t < nb; ++t) {
-    nbr[L->bonds[2 * t]].push_back(L->bonds[2 * t + 1]);
-    nbr[L->bonds[2 * t + 1]].push_back(L->bonds[2 * t]);
-  }
-  // pair type [j][i]: 0 nonbonded, 1 1-4 (three bonds apart), 2 excluded (within two bonds, or i == j)
-  std::vector<uint8_t> ptype((size_t)na * na, 0);
-  std::vector<int> dist(na), queue(na);
-  for (int i = 0; i < na; ++i) {
-    std::fill(dist.begin(), dist.end(), -1);
-    dist[i] = 0;
-    int h = 0, t = 0;
-    queue[t++] = i;
-    while (h < t) {
-      const int u = queue[h++];
-      if (dist[u] >= 3) continue;
-      for (int v : nbr[u])
-        if (dist[v] < 0) {
-          dist[v] = dist[u] + 1;
-          queue[t++] = v;
-        }
-    }
-    for (int j = 0; j < na; ++j) {
-      if (dist[j] >= 0 && dist[j] <= 2) ptype[(size_t)j * na + i] = 2;
-      else if (dist[j] == 3) ptype[(size_t)j * na + i] = 1;
-    }
-  }
-  // per-atom lists of the bonded force slots that act on it (role-major slot numbering:
-  // bond t role r -> r nb + t; angle -> 2 nb + r nang + t; torsion -> 2 nb + 3 nang + r ntor + t)
-  std::vector<std::vector<uint32_t>> inc(na);
-  for (int t = 0; t < nb; ++t)
-    for (int r = 0; r < 2; ++r) inc[L->bonds[2 * t + r]].push_back((uint32_t)(r * nb + t));
-  for (int t = 0; t < nang; ++t)
-    for (int r = 0; r < 3; ++r) inc[L->angles[3 * t + r]].push_back((uint32_t)(2 * nb + r * nang + t));
-  for (int t = 0; t < ntor; ++t)
-    for (int r = 0; r < 4; ++r)
-      inc[L->torsions[4 * t + r]].push_back((uint32_t)(2 * nb + 3 * nang + r * ntor + t));
-  int ninc = 0;
-  for (auto& v : inc) ninc += (int)v.size();
-
   LigandLayout Y;
-  memset(&Y, 0, sizeof(Y));
-  Y.na = na;
-  Y.nb = nb;
-  Y.nang = nang;
-  Y.ntor = ntor;
-  Y.ninc = ninc;
-  Y.n_slots = 2 * nb + 3 * nang + 4 * ntor;
-  int w = 0;
-  auto take = [&](int words) {
-    const int o = w;
-    w += (words + 3) & ~3;
-    return o;
-  };
-  Y.off_atom_a = take(4 * na);
-  Y.off_atom_b = take(4 * na);
-  Y.off_ptype = take((na * na + 3) / 4);
-  Y.off_bond = take(4 * nb);
-  Y.off_ang = take(8 * nang);
-  Y.off_tor = take(16 * ntor);
-  Y.off_inc_start = take(na + 1);
-  Y.off_inc = take(ninc);
-  Y.words = w;
-  if ((size_t)w * 4 > 120 * 1024) return fail(c, ALGDOCK_E_INVALID, "ligand_load: topology too large");
-  Y.off_pair = take(4 * na * na);
-  Y.words_pair = w;
-  std::vector<uint32_t> blob(w, 0u);
-  float* bf = (float*)blob.data();
-  int32_t* bi = (int32_t*)blob.data();
-  for (int i = 0; i < na; ++i) {
-    const double m = L->mass[i];
-    const double two_r = 2.0 * L->rstar[i];
-    bf[Y.off_atom_a + 4 * i + 0] = (float)(kForceToAccel / m);
-    bf[Y.off_atom_a + 4 * i + 1] = (float)L->charge[i];
-    bf[Y.off_atom_a + 4 * i + 2] = (float)sqrtA(L->rstar[i], L->eps[i]);
-    bf[Y.off_atom_a + 4 * i + 3] = (float)(sqrt(2.0 * L->eps[i]) * two_r * two_r * two_r);
-    bf[Y.off_atom_b + 4 * i + 0] = (float)L->rstar[i];
-    bf[Y.off_atom_b + 4 * i + 1] = (float)sqrt(L->eps[i]);
-    bf[Y.off_atom_b + 4 * i + 2] = (float)m;
-    bf[Y.off_atom_b + 4 * i + 3] = (float)sqrt(kForceToAccel / m);
-  }
-  memcpy((uint8_t*)(blob.data() + Y.off_ptype), ptype.data(), ptype.size());
-  for (int t = 0; t < nb; ++t) {
-    bi[Y.off_bond + 4 * t + 0] = L->bonds[2 * t];
-    bi[Y.off_bond + 4 * t + 1] = L->bonds[2 * t + 1];
-    bf[Y.off_bond + 4 * t + 2] = (float)L->bond_k[t];
-    bf[Y.off_bond + 4 * t + 3] = (float)L->bond_r0[t];
-  }
-  for (int t = 0; t < nang; ++t) {
-    for (int k = 0; k < 3; ++k) bi[Y.off_ang + 4 * t + k] = L->angles[3 * t + k];
-    bf[Y.off_ang + 4 * nang + 4 * t + 0] = (float)L->angle_k[t];
-    bf[Y.off_ang + 4 * nang + 4 * t + 1] = (float)L->angle_theta0[t];
-  }
-  for (int t = 0; t < ntor; ++t) {
-    for (int k = 0; k < 4; ++k) bi[Y.off_tor + 4 * t + k] = L->torsions[4 * t + k];
-    for (int n = 0; n < 3; ++n) {
-      const double g = L->torsion_gamma[3 * t + n];
-      bf[Y.off_tor + 4 * ntor + 4 * t + n] = (float)(0.5 * L->torsion_V[3 * t + n]);
-      bf[Y.off_tor + 8 * ntor + 4 * t + n] = (float)cos(g);
-      bf[Y.off_tor + 12 * ntor + 4 * t + n] = (float)sin(g);
-    }
-  }
-  // pair table: the Lorentz-Berthelot combination, the 1-4 scales and the exclusions folded into
-  // one record per ordered pair (FP64, rounded once); an excluded pair (and i == j) has zero
-  // coefficients and adds 1 to r^2 so that its arithmetic stays finite
-  for (int j = 0; j < na; ++j)
-    for (int i = 0; i < na; ++i) {
-      const int ty = ptype[(size_t)j * na + i];
-      const double s_lj = ty == 0 ? 1.0 : (ty == 1 ? 0.5 : 0.0);
-      const double s_el = ty == 0 ? 1.0 : (ty == 1 ? 1.0 / 1.2 : 0.0);
-      const double R = L->rstar[i] + L->rstar[j];
-      float* rec = bf + Y.off_pair + 4 * ((size_t)j * na + i);
-      rec[0] = ty == 2 ? 0.f : (float)(R * R);
-      rec[1] = (float)(12.0 * s_lj * sqrt(L->eps[i]) * sqrt(L->eps[j]));
-      rec[2] = (float)(kCoulomb * L->charge[i] * L->charge[j] * s_el);
-      rec[3] = ty == 2 ? 1.f : 0.f;
-    }
-  int pos = 0;
-  for (int i = 0; i < na; ++i) {
-    bi[Y.off_inc_start + i] = pos;
-    for (uint32_t code : inc[i]) blob[Y.off_inc + pos++] = code;
-  }
-  bi[Y.off_inc_start + na] = pos;
-  Y.total_mass = (float)M;
-  for (int k = 0; k < 3; ++k) Y.site[k] = (float)R->site[k];
-  Y.k_rest = (float)R->k;
-  Y.d0 = (float)R->d0;
+  std::vector<uint32_t> blob;
+  std::vector<TargetFactors> fac;
+  algdock_status st = build_ligand(c, L, R, "ligand_load", Y, blob, fac);
+  if (st != ALGDOCK_OK) return st;
+  const int na = Y.na, nb = Y.nb, w = Y.words_pair;
 
   Device g(c->device);
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -438,13 +532,6 @@ algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, cons
   c->d_blob = nullptr;
   c->d_lig_fac = nullptr;
   c->has_ligand = false;
-  // target-force-field factors of each atom, FP64
-  std::vector<TargetFactors> fac(na);
-  for (int i = 0; i < na; ++i) {
-    const double two_r = 2.0 * L->rstar[i];
-    fac[i] = TargetFactors{sqrtA(L->rstar[i], L->eps[i]), sqrt(2.0 * L->eps[i]) * two_r * two_r * two_r,
-                           kCoulomb * L->charge[i], 0.0};
-  }
   e = cudaMalloc(&c->d_blob, (size_t)w * 4);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_blob, blob.data(), (size_t)w * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_lig_fac, sizeof(TargetFactors) * na);
@@ -721,6 +808,216 @@ algdock_status algdock_fep(algdock_ctx* c, int64_t N, const double* u_target, in
   if (e != cudaSuccess) return cuda_fail(c, e, "fep");
   for (int k = 0; k < 4; ++k) result[k] = h[k];
   if (h[4] > 0) return fail(c, ALGDOCK_E_NUMERIC, "fep: NaN or -inf energy difference");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_batch_load(algdock_ctx* c, int32_t n_ligands, const algdock_ligand* ligands,
+                                  const algdock_restraint* rest) {
+  ALGDOCK_TRY(c)
+  if (n_ligands < 1 || !ligands || !rest) return fail(c, ALGDOCK_E_INVALID, "batch_load: need n_ligands >= 1");
+  std::vector<BatchLigand> recs(n_ligands);
+  std::vector<uint32_t> all;
+  int max_na = 0;
+  for (int l = 0; l < n_ligands; ++l) {
+    LigandLayout Y;
+    std::vector<uint32_t> blob;
+    std::vector<TargetFactors> fac;
+    algdock_status st = build_ligand(c, &ligands[l], rest, "batch_load: ligand " + std::to_string(l), Y, blob, fac);
+    if (st != ALGDOCK_OK) return st;
+    recs[l].LL = Y;
+    recs[l].blob_off = (int64_t)all.size();  // blob sizes are multiples of 4 words: 16-byte aligned
+    recs[l].apl = Y.na <= 32 ? 1 : (Y.na <= 64 ? 2 : 3);
+    recs[l].cls = recs[l].apl == 1 ? 0 : (recs[l].apl == 3 ? 3 : (hmc_uses_table(Y) ? 1 : 2));
+    all.insert(all.end(), blob.begin(), blob.end());
+    max_na = std::max(max_na, Y.na);
+  }
+  Device g(c->device);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch_load");
+  batch_free(c);
+  for (int k = 0; k < kBatchClasses && e == cudaSuccess; ++k) {
+    if (!c->batch_side[k]) e = cudaStreamCreateWithFlags(&c->batch_side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c->batch_join[k]) e = cudaEventCreateWithFlags(&c->batch_join[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess && !c->batch_fork) e = cudaEventCreateWithFlags(&c->batch_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_batch, sizeof(BatchLigand) * n_ligands);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_batch_blob, all.size() * 4);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_batch, recs.data(), sizeof(BatchLigand) * n_ligands, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_batch_blob, all.data(), all.size() * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    batch_free(c);
+    return cuda_fail(c, e, "batch_load");
+  }
+  c->h_batch = recs;
+  c->n_batch = n_ligands;
+  c->batch_max_na = max_na;
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_batch_layout(algdock_ctx* c, int64_t n_rep, const int32_t* lig_of, int32_t x_stride,
+                                    int32_t uniform) {
+  ALGDOCK_TRY(c)
+  if (c->n_batch == 0) return fail(c, ALGDOCK_E_STATE, "batch_layout: load a batch first");
+  if (n_rep < 1 || n_rep > INT32_MAX || !lig_of || x_stride < 1 || x_stride > kMaxAtoms)
+    return fail(c, ALGDOCK_E_INVALID, "batch_layout: need n_rep >= 1, lig_of and 1 <= x_stride <= 96");
+  if (is_device_ptr(lig_of)) return fail(c, ALGDOCK_E_INVALID, "batch_layout: lig_of must be a host array");
+  for (int64_t r = 0; r < n_rep; ++r) {
+    if (lig_of[r] < 0 || lig_of[r] >= c->n_batch)
+      return fail(c, ALGDOCK_E_INVALID, "batch_layout: ligand index out of range");
+    if (c->h_batch[lig_of[r]].LL.na > x_stride)
+      return fail(c, ALGDOCK_E_INVALID, "batch_layout: x_stride is smaller than a ligand's atom count");
+  }
+  Device g(c->device);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch_layout");
+  c->batch_lig_of.assign(lig_of, lig_of + n_rep);
+  c->batch_n_rep = n_rep;
+  c->batch_x_stride = x_stride;
+  c->batch_uniform = uniform != 0;
+  // default shape per class: the first candidate whose shared memory fits every ligand it runs
+  for (int k = 0; k < kBatchClasses && e == cudaSuccess; ++k) {
+    int wpb[4];
+    bool table[4];
+    const int nc = c->batch_uniform && k < kBatchClasses - 1 ? 0 : batch_candidates(k, wpb, table);
+    int pick = -1;
+    for (int t = 0; t < nc && pick < 0; ++t)
+      if (batch_class_smem(c, k, wpb[t], table[t]) <= 227 * 1024) pick = t;
+    if (pick < 0) {
+      e = batch_set_class(c, k, 4, false);
+      if (e == cudaSuccess && c->batch_cls[k].n_items > 0 && c->batch_cls[k].smem > 227 * 1024) {
+        batch_free(c);
+        return fail(c, ALGDOCK_E_INVALID, "batch_layout: a ligand's tables exceed shared memory");
+      }
+    } else {
+      e = batch_set_class(c, k, wpb[pick], table[pick]);
+    }
+  }
+  if (e == cudaSuccess) e = batch_set_attributes(*c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch_layout");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_batch_hmc_cycle(algdock_ctx* c, const int32_t* state_of, float* x, double* comps, double* dH,
+                                       uint8_t* acc, int32_t n_steps, uint64_t seed, uint64_t cycle,
+                                       int64_t rep_offset, int64_t* counters) {
+  ALGDOCK_TRY(c)
+  if (!c->has_grid || c->K == 0 || c->batch_n_rep == 0)
+    return fail(c, ALGDOCK_E_STATE, "batch_hmc_cycle: load grids, states, a batch and its layout first");
+  if (n_steps < 0 || rep_offset < 0) return fail(c, ALGDOCK_E_INVALID, "batch_hmc_cycle: negative argument");
+  if (!is_device_ptr(state_of) || !is_device_ptr(x) || !is_device_ptr(comps) || (dH && !is_device_ptr(dH)) ||
+      (acc && !is_device_ptr(acc)) || (counters && !is_device_ptr(counters)))
+    return fail(c, ALGDOCK_E_INVALID, "batch_hmc_cycle: arrays must be device pointers");
+  Device g(c->device);
+  cudaError_t e = launch_hmc_batch(c->stream, *c, state_of, x, comps, dH, acc, n_steps, seed, cycle, rep_offset,
+                                   counters, -1);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch_hmc_cycle");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_hmc_shape(algdock_ctx* c, int32_t* shape) {
+  ALGDOCK_TRY(c)
+  if (!shape) return fail(c, ALGDOCK_E_INVALID, "hmc_shape: null argument");
+  if (!c->has_ligand) return fail(c, ALGDOCK_E_STATE, "hmc_shape: load a ligand first");
+  const bool table = hmc_uses_table(c->lig);
+  shape[0] = table ? 16 : 4;
+  shape[1] = table ? 1 : 0;
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_batch_shapes(algdock_ctx* c, int32_t* shapes) {
+  ALGDOCK_TRY(c)
+  if (!shapes) return fail(c, ALGDOCK_E_INVALID, "batch_shapes: null argument");
+  if (c->batch_n_rep == 0) return fail(c, ALGDOCK_E_STATE, "batch_shapes: set a batch layout first");
+  for (int k = 0; k < kBatchClasses; ++k) {
+    const BatchClass& B = c->batch_cls[k];
+    shapes[2 * k] = B.n_items ? B.wpb : 0;
+    shapes[2 * k + 1] = B.n_items && B.table ? 1 : 0;
+  }
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_batch_tune(algdock_ctx* c, const int32_t* state_of, const float* x, int32_t n_steps,
+                                  int32_t n_timed, int32_t* chosen, float* ms) {
+  ALGDOCK_TRY(c)
+  if (!c->has_grid || c->K == 0 || c->batch_n_rep == 0)
+    return fail(c, ALGDOCK_E_STATE, "batch_tune: load grids, states, a batch and its layout first");
+  if (n_steps < 0 || n_timed < 1 || !is_device_ptr(state_of) || !is_device_ptr(x))
+    return fail(c, ALGDOCK_E_INVALID, "batch_tune: bad arguments");
+  Device g(c->device);
+  const int64_t R = c->batch_n_rep;
+  const size_t xbytes = (size_t)R * c->batch_x_stride * 3 * sizeof(float);
+  float* xs = nullptr;
+  double* cs = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&xs, xbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&cs, (size_t)R * 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  // time of the whole batch launch (every class, overlapped as in production) with the current
+  // shapes: the median of n_timed launches after one warm-up, each from the same copy of x
+  auto whole = [&](float* out) {
+    std::vector<float> t;
+    for (int rep = 0; rep <= n_timed && e == cudaSuccess; ++rep) {
+      e = cudaMemcpyAsync(xs, x, xbytes, cudaMemcpyDeviceToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(t0, c->stream);
+      if (e == cudaSuccess)
+        e = launch_hmc_batch(c->stream, *c, state_of, xs, cs, nullptr, nullptr, n_steps, 0x7E57u, rep, 0, nullptr, -1);
+      if (e == cudaSuccess) e = cudaEventRecord(t1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      float el = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&el, t0, t1);
+      if (rep > 0) t.push_back(el);
+    }
+    std::sort(t.begin(), t.end());
+    *out = t.empty() ? 0.f : t[t.size() / 2];
+  };
+  // coordinate descent: each class in turn takes the candidate that minimises the whole launch,
+  // the others held at their current shapes; a candidate must beat the incumbent by 2 % (launch
+  // times of equal shapes scatter by about that much)
+  float best_ms = 0.f;
+  whole(&best_ms);
+  for (int k = 0; k < kBatchClasses && e == cudaSuccess; ++k) {
+    BatchClass& B = c->batch_cls[k];
+    if (B.n_items == 0) continue;
+    int wpb[4];
+    bool table[4];
+    const int nc = batch_candidates(k, wpb, table);
+    int best_w = B.wpb;
+    bool best_t = B.table;
+    for (int t = 0; t < nc && e == cudaSuccess; ++t) {
+      if (wpb[t] == best_w && table[t] == best_t) continue;
+      if (batch_class_smem(c, k, wpb[t], table[t]) > 227 * 1024) continue;
+      e = batch_set_class(c, k, wpb[t], table[t]);
+      if (e == cudaSuccess) e = batch_set_attributes(*c);
+      float m = 0.f;
+      if (e == cudaSuccess) whole(&m);
+      if (e == cudaSuccess && m < 0.98f * best_ms) {
+        best_ms = m;
+        best_w = wpb[t];
+        best_t = table[t];
+      }
+    }
+    if (e == cudaSuccess) e = batch_set_class(c, k, best_w, best_t);
+    if (e == cudaSuccess) e = batch_set_attributes(*c);
+  }
+  for (int k = 0; k < kBatchClasses && chosen; ++k) {
+    const BatchClass& B = c->batch_cls[k];
+    chosen[2 * k] = B.n_items ? B.wpb : 0;
+    chosen[2 * k + 1] = B.n_items && B.table ? 1 : 0;
+  }
+  if (ms) *ms = best_ms;
+  cudaFree(xs);
+  cudaFree(cs);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch_tune");
   return ALGDOCK_OK;
   ALGDOCK_CATCH(c)
 }

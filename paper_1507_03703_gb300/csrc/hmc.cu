@@ -542,22 +542,44 @@ struct HmcArgs {
   uint32_t cycle;
   int64_t rep_offset;
   int64_t* counters;
+  // batches only: the ligand records, this launch's work items (one per block) and the position
+  // stride of a replica (atoms)
+  const BatchLigand* bligs;
+  const BatchItem* items;
+  int x_stride;
 };
 
 // WPB warps per block; TABLE: the pair table is staged with the blob (16-warp blocks share it).
-template <int APL, int WPB, bool TABLE>
+// BATCH: the block's ligand and replicas come from its work item (a run of up to WPB replicas of
+// one ligand of a multi-ligand batch) and positions are stored x_stride atoms apart.
+template <int APL, int WPB, bool TABLE, bool BATCH = false>
 __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
   extern __shared__ __align__(16) uint32_t smem[];
-  const int staged = TABLE ? A.LL.words_pair : A.LL.words;
-  stage_ligand(smem, A.blob, staged);
+  __shared__ LigandLayout s_ll;
+  const uint32_t* blob = A.blob;
+  int64_t r_first = (int64_t)blockIdx.x * WPB;
+  int count = WPB;
+  if (BATCH) {
+    const BatchItem it = A.items[blockIdx.x];
+    if (threadIdx.x == 0) s_ll = A.bligs[it.lig].LL;
+    blob = A.blob + A.bligs[it.lig].blob_off;
+    r_first = it.r0;
+    count = it.count;
+    __syncthreads();
+  }
+  const LigandLayout& LL = BATCH ? s_ll : A.LL;
+  const int staged = TABLE ? LL.words_pair : LL.words;
+  stage_ligand(smem, blob, staged);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t r = (int64_t)blockIdx.x * WPB + warp;
+  if (warp >= count) return;
+  const int64_t r = r_first + warp;
   if (r >= A.n_rep) return;
-  const Lig L = bind_ligand(smem, A.LL);
-  const WarpSmem ws = warp_smem<APL>(smem, staged, A.LL, warp);
+  const Lig L = bind_ligand(smem, LL);
+  const WarpSmem ws = warp_smem<APL>(smem, staged, LL, warp);
   float4* xs = ws.xs;
-  const int na = A.LL.na;
+  const int na = LL.na;
+  const int64_t xstride = BATCH ? A.x_stride : na;
   const int k = A.state_of[r];
   if ((unsigned)k >= (unsigned)A.n_states) {  // invalid state index: leave the replica untouched
     if (lane == 0) {
@@ -576,7 +598,7 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
   for (int a = 0; a < APL; ++a) {
     const int i = lane + 32 * a;
     if (i < na) {
-      const float* src = A.x + (r * na + i) * 3;
+      const float* src = A.x + (r * xstride + i) * 3;
       x[a][0] = src[0];
       x[a][1] = src[1];
       x[a][2] = src[2];
@@ -608,7 +630,7 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
   int outside = 0;
   Energies en;
   double c0[4], c1[4];
-  evaluate<APL, true, TABLE>(A.LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
+  evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
   reduce_components(en, c0);
   const double K0 = 0.5 * kKineticToKcal * warp_sum((double)kin);
   for (int s = 0; s < A.n_steps; ++s) {
@@ -638,9 +660,9 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
     }
     __syncwarp();
     if (s + 1 < A.n_steps) {
-      evaluate<APL, false, TABLE>(A.LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, false, en, outside);
+      evaluate<APL, false, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, false, en, outside);
     } else {
-      evaluate<APL, true, TABLE>(A.LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
+      evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
       reduce_components(en, c1);
     }
 #pragma unroll
@@ -673,7 +695,7 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
   for (int a = 0; a < APL; ++a) {
     const int i = lane + 32 * a;
     if (i < na) {
-      float* dst = A.x + (r * na + i) * 3;
+      float* dst = A.x + (r * xstride + i) * 3;
       dst[0] = accept ? x[a][0] : x0[a][0];
       dst[1] = accept ? x[a][1] : x0[a][1];
       dst[2] = accept ? x[a][2] : x0[a][2];
@@ -972,21 +994,109 @@ cudaError_t launch_templated(Kernel k1, Kernel k2, Kernel k3, int apl, size_t sm
 
 }  // namespace
 
+bool hmc_uses_table(const LigandLayout& L) {
+  const int apl = atoms_per_lane(L.na);
+  return apl <= 2 && block_smem(L, apl, kTableWarps, true) <= kMaxBlockSmem;
+}
+
 cudaError_t launch_hmc(cudaStream_t s, const algdock_ctx& c, int64_t n_rep, const int32_t* state_of, float* x,
                        double* comps, double* dH, uint8_t* acc, int n_steps, uint64_t seed, uint64_t cycle,
                        int64_t rep_offset, int64_t* counters) {
   if (n_rep == 0) return cudaSuccess;
   HmcArgs A{c.grid, c.lig, c.d_blob, c.d_states, c.K, n_rep, state_of, x, comps, dH, acc, n_steps, seed,
-            (uint32_t)cycle, rep_offset, counters};
+            (uint32_t)cycle, rep_offset, counters, nullptr, nullptr, 0};
   const int apl = atoms_per_lane(c.lig.na);
   // the pair table where 16-warp blocks can stage it (up to 64 atoms with a small topology);
   // otherwise the pair-type path in 4-warp blocks
   const size_t tsmem = block_smem(c.lig, apl, kTableWarps, true);
-  if (apl <= 2 && tsmem <= kMaxBlockSmem)
+  if (hmc_uses_table(c.lig))
     return launch_templated(hmc_kernel<1, kTableWarps, true>, hmc_kernel<2, kTableWarps, true>,
                             hmc_kernel<2, kTableWarps, true>, apl, tsmem, n_rep, s, A, kTableWarps);
   return launch_templated(hmc_kernel<1, kWarpsPerBlock, false>, hmc_kernel<2, kWarpsPerBlock, false>,
                           hmc_kernel<3, kWarpsPerBlock, false>, apl, block_smem(c.lig, apl), n_rep, s, A);
+}
+
+// ------------------------------------------------------------------ multi-ligand batches
+size_t batch_block_smem(const LigandLayout& L, int apl, int wpb, bool table) { return block_smem(L, apl, wpb, table); }
+
+// Launch shapes tried for a class: pair-table blocks of 16 or 8 replicas, or 4-replica blocks
+// without the table (classes 0 and 1); 8-replica table blocks or 4 without (2); 4 or 8 replicas
+// without the table (3).
+int batch_candidates(int cls, int* wpb, bool* table) {
+  if (cls == 3) {
+    wpb[0] = 4, table[0] = false;
+    wpb[1] = 8, table[1] = false;
+    return 2;
+  }
+  if (cls == 2) {
+    wpb[0] = 8, table[0] = true;
+    wpb[1] = kWarpsPerBlock, table[1] = false;
+    return 2;
+  }
+  wpb[0] = kTableWarps, table[0] = true;
+  wpb[1] = 8, table[1] = true;
+  wpb[2] = kWarpsPerBlock, table[2] = false;
+  return 3;
+}
+
+namespace {
+using HmcKernel = void (*)(const HmcArgs);
+HmcKernel batch_kernel(int apl, int wpb, bool table) {
+  if (apl == 1) {
+    if (table) return wpb == kTableWarps ? hmc_kernel<1, kTableWarps, true, true> : hmc_kernel<1, 8, true, true>;
+    return hmc_kernel<1, kWarpsPerBlock, false, true>;
+  }
+  if (apl == 2) {
+    if (table) return wpb == kTableWarps ? hmc_kernel<2, kTableWarps, true, true> : hmc_kernel<2, 8, true, true>;
+    return hmc_kernel<2, kWarpsPerBlock, false, true>;
+  }
+  return wpb == 8 ? hmc_kernel<3, 8, false, true> : hmc_kernel<3, kWarpsPerBlock, false, true>;
+}
+}  // namespace
+
+cudaError_t batch_set_attributes(const algdock_ctx& c) {
+  for (int k = 0; k < kBatchClasses; ++k) {
+    const BatchClass& B = c.batch_cls[k];
+    if (B.n_items == 0) continue;
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel(kClassApl[k], B.wpb, B.table),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// One kernel per class (only_class >= 0: that class alone).  With more than one
+// class the launches go to the context's side streams, forked from and joined back to s, so that
+// they overlap (and capture into one graph with parallel branches).
+cudaError_t launch_hmc_batch(cudaStream_t s, const algdock_ctx& c, const int32_t* state_of, float* x, double* comps,
+                             double* dH, uint8_t* acc, int n_steps, uint64_t seed, uint64_t cycle, int64_t rep_offset,
+                             int64_t* counters, int only_class) {
+  HmcArgs A{c.grid, LigandLayout{}, c.d_batch_blob, c.d_states, c.K, c.batch_n_rep, state_of, x, comps, dH, acc,
+            n_steps, seed, (uint32_t)cycle, rep_offset, counters, c.d_batch, nullptr, c.batch_x_stride};
+  int active[kBatchClasses], n_active = 0;
+  for (int k = 0; k < kBatchClasses; ++k)
+    if (c.batch_cls[k].n_items > 0 && (only_class < 0 || only_class == k)) active[n_active++] = k;
+  if (n_active == 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  if (n_active > 1) e = cudaEventRecord(c.batch_fork, s);
+  for (int t = 0; t < n_active && e == cudaSuccess; ++t) {
+    const int k = active[t];
+    const BatchClass& B = c.batch_cls[k];
+    cudaStream_t st = s;
+    if (n_active > 1) {
+      st = c.batch_side[k];
+      e = cudaStreamWaitEvent(st, c.batch_fork, 0);
+      if (e != cudaSuccess) break;
+    }
+    A.items = B.d_items;
+    batch_kernel(kClassApl[k], B.wpb, B.table)<<<(unsigned)B.n_items, B.wpb * 32, B.smem, st>>>(A);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && n_active > 1) {
+      e = cudaEventRecord(c.batch_join[k], st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c.batch_join[k], 0);
+    }
+  }
+  return e;
 }
 
 static cudaError_t launch_eval(cudaStream_t s, const algdock_ctx& c, int64_t N, const int32_t* state_of,

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "algdock.h"
 
@@ -108,6 +109,30 @@ struct __align__(16) ReceptorPair {
   float4 c0, c1, c2, c3;
 };
 
+// Multi-ligand batches: one record per ligand (its layout and where its blob starts in the batch
+// blob), and one work item per block (a run of up to WPB consecutive replicas of one ligand).
+struct BatchLigand {
+  LigandLayout LL;
+  int64_t blob_off;  // in 4-byte words, a multiple of 4
+  int apl;           // atoms per lane: 1 (<= 32 atoms), 2 (<= 64), 3 (<= 96)
+  int cls;           // launch class: 0 (1 atom per lane), 1 (2, pair table fits 16-replica blocks),
+                     // 2 (2, it does not), 3 (3)
+};
+struct BatchItem {
+  int32_t lig, r0, count, pad;
+};
+// Launch shape of one class: replicas (warps) per block and whether the per-pair table is staged
+// with the blob.
+struct BatchClass {
+  int wpb = 0;
+  bool table = false;
+  BatchItem* d_items = nullptr;
+  int n_items = 0;
+  size_t smem = 0;
+};
+constexpr int kBatchClasses = 4;
+constexpr int kClassApl[kBatchClasses] = {1, 2, 2, 3};
+
 // Torsion tree of the learned proposal: root atom 0, the first 16 rotatable bonds in bond order.
 constexpr int kLearnTmax = 16;
 struct LearnedTopo {
@@ -155,6 +180,20 @@ struct algdock_ctx {
   int n_rec = -1;  // -1: no receptor loaded
   algdock::TargetFactors* d_lig_fac = nullptr;
   void* d_fep = nullptr;
+  // multi-ligand batch: ligands, their blobs, the replica layout and one launch shape per class
+  int n_batch = 0;
+  int batch_max_na = 0;
+  std::vector<algdock::BatchLigand> h_batch;
+  algdock::BatchLigand* d_batch = nullptr;
+  uint32_t* d_batch_blob = nullptr;
+  int64_t batch_n_rep = 0;
+  int batch_x_stride = 0;
+  std::vector<int32_t> batch_lig_of;
+  bool batch_uniform = false;
+  algdock::BatchClass batch_cls[algdock::kBatchClasses];
+  cudaStream_t batch_side[algdock::kBatchClasses] = {};
+  cudaEvent_t batch_fork = nullptr;
+  cudaEvent_t batch_join[algdock::kBatchClasses] = {};
 };
 
 namespace algdock {
@@ -168,6 +207,16 @@ cudaError_t launch_hmc(cudaStream_t s, const algdock_ctx& c, int64_t n_rep, cons
                        double* comps, double* dH, uint8_t* acc, int n_steps, uint64_t seed, uint64_t cycle,
                        int64_t rep_offset, int64_t* counters);
 cudaError_t launch_evaluate(cudaStream_t s, const algdock_ctx& c, int64_t N, const float* x, double* comps);
+// the one-ligand HMC launch shape: 16-replica blocks with the pair table staged, else 4 without
+bool hmc_uses_table(const LigandLayout& L);
+// batches: the block shared memory of a class shape, the candidate shapes of a class, and the
+// HMC trial of every replica of the batch (classes on forked streams, joined on s)
+size_t batch_block_smem(const LigandLayout& L, int apl, int wpb, bool table);
+int batch_candidates(int cls, int* wpb, bool* table);
+cudaError_t batch_set_attributes(const algdock_ctx& c);
+cudaError_t launch_hmc_batch(cudaStream_t s, const algdock_ctx& c, const int32_t* state_of, float* x, double* comps,
+                             double* dH, uint8_t* acc, int n_steps, uint64_t seed, uint64_t cycle, int64_t rep_offset,
+                             int64_t* counters, int only_class);
 cudaError_t launch_external(cudaStream_t s, const algdock_ctx& c, int64_t n_rep, const int32_t* state_of, float* x,
                             double* comps, int n_moves, double alpha_max, float sigma, uint64_t seed, uint64_t cycle,
                             int64_t rep_offset, int32_t* accepted, int64_t* counters);

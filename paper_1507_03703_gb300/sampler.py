@@ -25,15 +25,21 @@ class ReplicaExchange:
 
     def __init__(self, ctx: Context, legs, n_chains: int, x0, seed: int, n_sweeps: int = 25, max_sep: int = 5,
                  device="cuda", rep_offset: int = 0, ladder_offset: int = 0, n_external: int = 0,
-                 alpha_max: float = 0.01, sigma: float = 0.6):
+                 alpha_max: float = 0.01, sigma: float = 0.6, batched: bool = False):
         """rep_offset / ladder_offset: global index of this run's first replica slot and first
         ladder in the Philox counters (a rank's share of a sharded run; see ranks.Shard).
         n_external: external-coordinate moves per replica after each HMC move at states with
-        alpha < alpha_max (the paper: 20, 0.01, sigma 0.6 A); 0 leaves them out."""
+        alpha < alpha_max (the paper: 20, 0.01, sigma 0.6 A); 0 leaves them out.
+        batched: chain c runs ligand c of the context's multi-ligand batch (x0 holds each slot's
+        positions padded to a common atom stride; call ctx.batch_layout(self.lig_of(), stride)
+        before the first cycle)."""
         self.ctx, self.legs, self.C = ctx, list(legs), int(n_chains)
         self.seed, self.n_sweeps, self.max_sep = int(seed), int(n_sweeps), int(max_sep)
         self.rep_offset, self.ladder_offset = int(rep_offset), int(ladder_offset)
         self.n_external, self.alpha_max, self.sigma = int(n_external), float(alpha_max), float(sigma)
+        self.batched = bool(batched)
+        if self.batched and self.n_external:
+            raise ValueError("external-coordinate moves run on single-ligand contexts only")
         self.R = self.C * sum(l.K for l in self.legs)
         x0 = np.asarray(x0, dtype=np.float32)
         if x0.shape[0] != self.R:
@@ -65,9 +71,18 @@ class ReplicaExchange:
         b = self.base[li]
         return slice(b, b + self.C * self.legs[li].K)
 
+    def lig_of(self):
+        """Chain (batch ligand) of every slot, host int32 [R]."""
+        out = np.empty(self.R, dtype=np.int32)
+        for li, leg in enumerate(self.legs):
+            b = self.base[li]
+            out[b:b + self.C * leg.K] = np.repeat(np.arange(self.C, dtype=np.int32), leg.K)
+        return out
+
     def hmc(self, cycle: int, n_steps: int):
-        self.ctx.hmc_cycle(self.state_of, self.x, self.comps, self.dH, self.acc, n_steps=n_steps, seed=self.seed,
-                           cycle=cycle, rep_offset=self.rep_offset, counters=self.counters)
+        run = self.ctx.batch_hmc_cycle if self.batched else self.ctx.hmc_cycle
+        run(self.state_of, self.x, self.comps, self.dH, self.acc, n_steps=n_steps, seed=self.seed, cycle=cycle,
+            rep_offset=self.rep_offset, counters=self.counters)
 
     def external(self, cycle: int):
         if self.n_external > 0:

@@ -112,13 +112,17 @@ def _random_unit(rng):
             return v / n
 
 
-def make_ligand(n_atoms: int, seed: int, max_degree: int = 3) -> Ligand:
+def make_ligand(n_atoms: int, seed: int, max_degree: int = 3, min_sep: float = None) -> Ligand:
     """Random tree topology grown atom by atom, with a clash-free start geometry.
 
     Parameter ranges: bonds 1.3-1.6 A with k 300-500 kcal/mol/A^2; angles 105-120 deg with
     k 50-80 kcal/mol/rad^2; three cosine torsion terms V_n in [0, 2] kcal/mol with phase 0 or pi;
     R* in [1.5, 2.0] A; eps in [0.01, 0.2] kcal/mol; charges N(0, 0.3) e shifted to net zero;
     masses of C, N or O.
+
+    min_sep (A): grow every new atom at least this far from all atoms other than its parent and
+    the parent's neighbours, trying the open parents in random order (large trees otherwise crowd
+    atoms into clashes).  None keeps the original growth (and its random draws).
     """
     if n_atoms < 1:
         raise ValueError("n_atoms must be >= 1")
@@ -128,10 +132,8 @@ def make_ligand(n_atoms: int, seed: int, max_degree: int = 3) -> Ligand:
     pos = [np.zeros(3)]
     bond_r0 = []
     nbrs = [[]]
-    for a in range(1, n_atoms):
-        cands = [p for p in range(a) if degree[p] < max_degree]
-        p = int(rng.choice(cands))
-        r0 = float(rng.uniform(1.3, 1.6))
+
+    def grow(a, p, r0):
         best, best_score = None, -np.inf
         for _ in range(400):
             d = _random_unit(rng)
@@ -147,6 +149,50 @@ def make_ligand(n_atoms: int, seed: int, max_degree: int = 3) -> Ligand:
                 best, best_score = cand, score
             if dmin >= 2.9 and ang_pen < 8.0:
                 break
+        return best
+
+    def grow_apart(a, p, r0, sep, n_try=400):
+        # all candidate directions at once; the first that keeps sep from every atom other than
+        # the parent and its neighbours with a near-tetrahedral angle, else the best scored
+        D = rng.normal(size=(n_try, 3))
+        D /= np.linalg.norm(D, axis=1)[:, None]
+        P = np.array(pos)
+        cand = P[p] + r0 * D
+        if nbrs[p]:
+            U = P[nbrs[p]] - P[p]
+            U /= np.linalg.norm(U, axis=1)[:, None]
+            ang_pen = np.abs(np.degrees(np.arccos(np.clip(D @ U.T, -1.0, 1.0))) - 109.5).max(axis=1)
+        else:
+            ang_pen = np.zeros(n_try)
+        keep = [q for q in range(a) if q != p and q not in nbrs[p]]
+        if keep:
+            dmin = np.linalg.norm(cand[:, None, :] - P[keep][None], axis=2).min(axis=1)
+        else:
+            dmin = np.full(n_try, 10.0)
+        ok = (dmin >= sep) & (ang_pen < 12.0)
+        if ok.any():
+            return cand[int(np.argmax(ok))], True
+        score = np.minimum(dmin, sep + 0.5) * 10.0 - ang_pen
+        return cand[int(np.argmax(score))], False
+
+    for a in range(1, n_atoms):
+        cands = [p for p in range(a) if degree[p] < max_degree]
+        if min_sep is None:
+            p = int(rng.choice(cands))
+            r0 = float(rng.uniform(1.3, 1.6))
+            best = grow(a, p, r0)
+        else:
+            fallback = None
+            for p in rng.permutation(cands):
+                p = int(p)
+                r0 = float(rng.uniform(1.3, 1.6))
+                best, ok = grow_apart(a, p, r0, float(min_sep))
+                if ok:
+                    break
+                if fallback is None:
+                    fallback = (p, r0, best)
+            if not ok:
+                p, r0, best = fallback
         parent.append(p)
         degree.append(1)
         degree[p] += 1
@@ -323,6 +369,20 @@ def config_paper_scale(seed: int = 2) -> System:
     32 BC + 96 CD states, 2 fs."""
     return make_system(ligand_atoms_for_seed(seed), 4000, 129, 0.25, seed, K_bc=32, K_cd=96,
                        dt_fs=2.0)
+
+
+def config_batch(seed: int = 3, n_ligands: int = 256, lo: int = 10, hi: int = 70):
+    """Many ligands against one paper-scale grid set: n_ligands clash-free ligands of U[lo, hi]
+    atoms, a 4000-atom receptor with an 11 A pocket (room for the largest), 129^3 grids at 0.25 A,
+    16 BC + 48 CD states, 2 fs.  Returns (system without its own ligand, ligands)."""
+    rng = np.random.default_rng(np.random.SeedSequence([0xBA7, seed]))
+    sizes = rng.integers(lo, hi + 1, size=n_ligands)
+    ligs = [make_ligand(int(n), seed=int(1000 * seed + i), min_sep=2.6) for i, n in enumerate(sizes)]
+    site = np.zeros(3)
+    rec = make_receptor(4000, site, seed, pocket_radius=11.0)
+    sys_ = System(ligand=None, receptor=rec, grid=cube_grid(site, 0.25, 129), site=site,
+                  legs=[bc_ladder(16, dt_fs=2.0), cd_ladder(48, dt_fs=2.0)])
+    return sys_, ligs
 
 
 def harmonic_oscillator_samples(K: int, N_per: int, seed: int, D: int = 1):
