@@ -134,10 +134,15 @@ def test_reduced_energies_and_ukn(small):
     assert np.array_equal(u2.cpu().numpy(), u_same[7:12])
 
 
+_RAW64 = {}
+
+
 @pytest.fixture(scope="module")
 def paper_scale():
     sys_ = S.config_paper_scale(2)
-    g32 = raw_grids32(sys_)
+    raw64 = oracle.grid_direct_sum(sys_.receptor, sys_.grid)
+    _RAW64["paper"] = raw64
+    g32 = tuple(a.astype(np.float32) for a in raw64)
     T, alpha, dt = state_table(sys_)
     ctx = gpu_context(sys_, g32, T, alpha, dt)
     osys = oracle_system(sys_, g32, T, alpha, dt)
@@ -197,3 +202,53 @@ def test_precision_study_paper_scale(paper_scale, capsys):
     assert frel.max() < 1e-5
     assert np.all(cerr <= 1e-5 * np.maximum(cref, 1.0) + 1e-4)
     assert np.median(herr) < 1e-2
+
+
+def test_precision_study_bpmf_paper_scale(paper_scale, capsys):
+    """The BPMF-level error of the FP32 path at paper scale.  Samples of the two end states of the
+    cycle, B (300 K, no grids) and D (alpha = 1, 300 K), are drawn by the GPU HMC; each sample's
+    energy is taken from the FP32 path (the sampler's own components, FP32 lattices) and from the
+    FP64 oracle on FP64 lattices (the unrounded direct sums).  The FP64 BPMF differs from the FP32
+    one by Delta B = Delta f_D - Delta f_B (both legs share milestone C), each Delta f a Zwanzig
+    average over that end state's samples ("Estimation"), so the estimate covers the FP32
+    arithmetic and the FP32 rounding of the lattices.  Bound: the BPMF tolerance of 0.05 kT."""
+    sys_, g32, T, alpha, dt, ctx, osys = paper_scale
+    osys64 = oracle.OracleSystem(sys_.grid, *_RAW64["paper"], sys_.ligand, T, alpha, dt, site=sys_.site)
+    K = len(T)
+    w_sg, w_g, beta = osys64.state_weights()
+    ends = {"B": 0, "D": K - 1}
+    R = 512
+    x = configurations(sys_, 2 * R, seed=21, jitter=0.1)
+    states = np.array([ends["B"]] * R + [ends["D"]] * R, dtype=np.int32)
+    xd = torch.from_numpy(x).cuda()
+    sd = torch.from_numpy(states).cuda()
+    comps = torch.empty((2 * R, 4), dtype=torch.float64, device="cuda")
+    xs, cs = [], []
+    for cyc in range(30):
+        ctx.hmc_cycle(sd, xd, comps, n_steps=50, seed=22, cycle=cyc)
+        if cyc >= 24:
+            xs.append(xd.cpu().numpy().copy())
+            cs.append(comps.cpu().numpy().copy())
+    res = {}
+    for name, k in ends.items():
+        sel = states == k
+        du, dU = [], []
+        for xx, cc in zip(xs, cs):
+            for n in np.nonzero(sel)[0]:
+                c64, _ = osys64.energy_force(xx[n].astype(np.float64), w_sg[k], w_g[k])
+                u64 = c64[0] + c64[1] + w_sg[k] * c64[2] + w_g[k] * c64[3]
+                u32 = cc[n, 0] + cc[n, 1] + w_sg[k] * cc[n, 2] + w_g[k] * cc[n, 3]
+                dU.append(u64 - u32)
+                du.append(beta[k] * (u64 - u32))
+        r = oracle.fep(np.array(du))
+        res[name] = (r, np.array(dU))
+    dB = res["D"][0]["f"] - res["B"][0]["f"]
+    sB = float(np.hypot(res["D"][0]["sigma"], res["B"][0]["sigma"]))
+    with capsys.disabled():
+        print("\nBPMF precision (FP32 path vs FP64 oracle on FP64 lattices, %d samples per end state):" % len(res["B"][1]))
+        for name in ("B", "D"):
+            r, dU = res[name]
+            print("  %s: U64 - U32 mean %.2e, max |.| %.2e kcal/mol; Delta f %.2e kT" % (name, dU.mean(),
+                                                                                  np.abs(dU).max(), r["f"]))
+        print("  Delta BPMF (FP64 - FP32): %.2e +- %.1e kT" % (dB, sB))
+    assert abs(dB) < 0.05
