@@ -148,6 +148,41 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def gather_bytes_per_launch(alpha, R_per_state, n_atoms, n_steps):
+    """Useful lattice bytes of one HMC launch: every atom of every replica gathers the 8 corners of
+    the hard lattice (16 B each) where the state's FP32 weight alpha_g is nonzero and of the soft
+    lattice (8 B each) where alpha_sg is, in each of the n_steps - 1 force-only evaluations, and
+    both lattices in the two energy evaluations (first and last).  Weights of Eq. (protocol)."""
+    out = 0.0
+    for a in alpha:
+        if np.isnan(a):
+            w_sg = w_g = 0.0
+        else:
+            s_ = 2.0 * a - 1.0
+            z = 1000.0 * (a - 0.5)
+            lg = 1.0 / (1.0 + np.exp(-z)) if z >= 0 else np.exp(z) / (1.0 + np.exp(z))
+            w_sg, w_g = 1.0 - s_ * s_, s_ * s_ * lg
+        gated = 128.0 * (np.float32(w_g) != 0) + 64.0 * (np.float32(w_sg) != 0)
+        out += R_per_state * n_atoms * (2 * 192.0 + (n_steps - 1) * gated)
+    return out
+
+
+def gather_peak(ctx, stream, n_cells=8 * 1024 * 1024, reps=5):
+    """Measured rate (useful GB/s) of random 8-corner gathers from both loaded lattices."""
+    import torch
+    sink = ctx.gather_probe(n_cells, soft=True, seed=1)
+    ms = []
+    for r in range(reps + 2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.gather_probe(n_cells, soft=True, seed=2 + r, sink=sink)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r >= 2:
+            ms.append(e0.elapsed_time(e1))
+    return n_cells * 192.0 / (float(np.median(ms)) * 1e-3) / 1e9
+
+
 def profiled_traffic(profile="hmc_kernel_paper_scale.md", source="hmc.cu"):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source
     of the kernel's file (else None)."""
@@ -792,6 +827,16 @@ def main():
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_max,
                 "flops_per_launch": fl}
 
+    # the same kernel against the L2 gather roofline: useful lattice bytes per launch over the
+    # measured rate of random 8-corner gathers from the same lattices
+    gbytes = gather_bytes_per_launch(alpha, N_CHAINS, lig.n_atoms, N_VV)
+    g_peak = gather_peak(ctx, stream)
+    g_ach = gbytes / (hmc_avg * 1e-3) / 1e9
+    roofline_gather = {"bound": "l2_gather", "achieved": g_ach, "peak": g_peak, "unit": "GB/s",
+                       "frac": g_ach / g_peak, "kernel": "hmc_kernel", "useful_bytes_per_launch": gbytes,
+                       "peak_source": "random 8-corner cell gathers of both lattices (algdock_gather_probe), "
+                                      "measured in this run"}
+
     # end to end through the C ABI with host buffers: pinned host -> device, step, device -> host
     h_x = torch.empty((R, lig.n_atoms, 3), dtype=torch.float32, pin_memory=True)
     h_x.copy_(run.x.cpu())
@@ -855,7 +900,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(sys_, world),
-        "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+        "roofline": roofline, "roofline_gather": roofline_gather, "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clk, "breakdown_ms": {"hmc": hmc_avg, "exchange": sum(ex_ms) / len(ex_ms),
                                         "snapshot_ukn": sum(ukn_ms) / len(ukn_ms), "wall_per_step_incl_flush":
                                         1e3 * wall / args.steps},

@@ -131,6 +131,14 @@ algdock_status algdock_soft_elec_cap(const algdock_ligand* lig, double vmax_r, d
 algdock_status algdock_grids_load(algdock_ctx* ctx, const algdock_grid_desc* desc, const float* ljr,
                                   const float* lja, const float* elec, double vmax_r, double vmax_e);
 
+/* Measurement aid for the gather roofline (no counterpart in the paper, not a step of the
+ * method): n_cells 8-corner gathers from the loaded lattices at cells drawn uniformly (hard float4
+ * corners; with soft != 0 also the soft float2 corners), the access pattern of one atom's
+ * trilinear interpolation.  Useful bytes: 128 per cell, plus 64 with soft.  Time it with events on
+ * the context's stream.  sink: a device float that is written only if the folded sum takes an
+ * impossible value (it keeps every load live). */
+algdock_status algdock_gather_probe(algdock_ctx* ctx, int64_t n_cells, int32_t soft, uint64_t seed, float* sink);
+
 /* ---------------------------------------------------------------- ligand and states */
 algdock_status algdock_ligand_load(algdock_ctx* ctx, const algdock_ligand* lig, const algdock_restraint* rest);
 

@@ -33,7 +33,7 @@ EXPORTS = [
     "algdock_external_moves", "algdock_detect_equilibration", "algdock_state_statistics", "algdock_resample",
     "algdock_mean_pacc", "algdock_receptor_load", "algdock_target_interaction", "algdock_fep",
     "algdock_batch_load", "algdock_batch_layout", "algdock_batch_hmc_cycle", "algdock_batch_tune",
-    "algdock_hmc_shape", "algdock_batch_shapes",
+    "algdock_hmc_shape", "algdock_batch_shapes", "algdock_gather_probe",
 ]
 
 BATCH_CLASSES = 4             # launch classes of a multi-ligand batch
@@ -138,6 +138,7 @@ def load_library(path: str = LIB_PATH):
         "algdock_batch_hmc_cycle": ([vp, vp, vp, vp, vp, vp, i32, u64, u64, i64, vp], C.c_int),
         "algdock_batch_tune": ([vp, vp, vp, i32, i32, vp, vp], C.c_int),
         "algdock_hmc_shape": ([vp, vp], C.c_int),
+        "algdock_gather_probe": ([vp, i64, i32, u64, vp], C.c_int),
         "algdock_batch_shapes": ([vp, vp], C.c_int),
         "algdock_exchange": ([vp, i32, i32, i32, vp, vp, vp, i32, i32, u64, u64, i64, vp, vp], C.c_int),
         "algdock_reduced_energies": ([vp, i64, vp, vp, i32, i32, vp], C.c_int),
@@ -296,6 +297,15 @@ class Context:
         p2, k2 = _any(lja, np.float32, torch.float32, "lja")
         p3, k3 = _any(elec, np.float32, torch.float32, "elec")
         self._check(self._L.algdock_grids_load(self.h, C.byref(d), p1, p2, p3, float(vmax_r), float(vmax_e)))
+
+    def gather_probe(self, n_cells, soft=True, seed=1, sink=None):
+        """Enqueue n_cells random 8-corner lattice gathers (the gather roofline's peak probe)."""
+        import torch
+        if sink is None:
+            sink = torch.zeros(1, dtype=torch.float32, device="cuda:%d" % self.device)
+        self._check(self._L.algdock_gather_probe(self.h, int(n_cells), 1 if soft else 0, int(seed),
+                                                 _dev(sink, torch.float32, "sink")))
+        return sink
 
     # ---------------------------------------------------------------- ligand and states
     def ligand_load(self, lig, site, k=K_RESTRAINT, d0=D0):

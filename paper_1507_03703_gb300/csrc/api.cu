@@ -515,6 +515,18 @@ algdock_status algdock_grids_load(algdock_ctx* c, const algdock_grid_desc* d, co
   ALGDOCK_CATCH(c)
 }
 
+algdock_status algdock_gather_probe(algdock_ctx* c, int64_t n_cells, int32_t soft, uint64_t seed, float* sink) {
+  ALGDOCK_TRY(c)
+  if (!c->has_grid) return fail(c, ALGDOCK_E_STATE, "gather_probe: load grids first");
+  if (n_cells < 0 || !sink || !is_device_ptr(sink))
+    return fail(c, ALGDOCK_E_INVALID, "gather_probe: need n_cells >= 0 and a device sink");
+  Device g(c->device);
+  cudaError_t e = launch_gather_probe(c->stream, *c, n_cells, soft != 0, (uint32_t)seed, sink);
+  if (e != cudaSuccess) return cuda_fail(c, e, "gather_probe");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
 algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, const algdock_restraint* R) {
   ALGDOCK_TRY(c)
   LigandLayout Y;

@@ -92,6 +92,47 @@ __global__ void grid_prepare_kernel(int64_t n, const float* __restrict__ ljr, co
   soft[p] = make_float2((float)soft_r, (float)soft_e);
 }
 
+// Peak rate of the interpolation's gathers, for the gather roofline (not a step of the method):
+// each thread reads the 8 corners of cells drawn uniformly over the lattice (hard float4 corners,
+// and with soft the float2 corners too, as one atom's interpolation does) and folds them into a
+// sum that is stored only if it takes an impossible value, so that no load is dead.  Cells come
+// from a per-thread xorshift stream mapped to [0, n - 1) by a multiply-shift (no division).
+__device__ __forceinline__ uint32_t xorshift32(uint32_t& s) {
+  s ^= s << 13;
+  s ^= s >> 17;
+  s ^= s << 5;
+  return s;
+}
+__device__ __forceinline__ int below(uint32_t r, int n) { return (int)(((uint64_t)r * (uint32_t)n) >> 32); }
+
+template <bool SOFT>
+__global__ void __launch_bounds__(256) gather_probe_kernel(const float4* __restrict__ hard,
+                                                           const float2* __restrict__ soft, int nx, int ny, int nz,
+                                                           int64_t n_cells, uint32_t seed, float* sink) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  uint32_t st = (uint32_t)(tid * 2654435761u) ^ seed;
+  st = st ? st : 0x9E3779B9u;
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  float acc = 0.f;
+  for (int64_t c = tid; c < n_cells; c += stride) {
+    const int cx = below(xorshift32(st), nx - 1), cy = below(xorshift32(st), ny - 1),
+              cz = below(xorshift32(st), nz - 1);
+    const int64_t b = cz * sz + cy * sy + cx;
+    const float4 h0 = __ldg(hard + b), h1 = __ldg(hard + b + 1), h2 = __ldg(hard + b + sy),
+                 h3 = __ldg(hard + b + sy + 1), h4 = __ldg(hard + b + sz), h5 = __ldg(hard + b + sz + 1),
+                 h6 = __ldg(hard + b + sz + sy), h7 = __ldg(hard + b + sz + sy + 1);
+    acc += ((h0.x + h1.y) + (h2.z + h3.x)) + ((h4.y + h5.z) + (h6.x + h7.y));
+    if (SOFT) {
+      const float2 s0 = __ldg(soft + b), s1 = __ldg(soft + b + 1), s2 = __ldg(soft + b + sy),
+                   s3 = __ldg(soft + b + sy + 1), s4 = __ldg(soft + b + sz), s5 = __ldg(soft + b + sz + 1),
+                   s6 = __ldg(soft + b + sz + sy), s7 = __ldg(soft + b + sz + sy + 1);
+      acc += ((s0.x + s1.y) + (s2.x + s3.y)) + ((s4.x + s5.y) + (s6.x + s7.y));
+    }
+  }
+  if (acc == -1.2345e-31f) sink[0] = acc;
+}
+
 }  // namespace
 
 cudaError_t launch_grid_build(cudaStream_t s, const algdock_grid_desc& d, int n_rec, const double* xyz,
@@ -138,4 +179,19 @@ cudaError_t launch_grid_prepare(cudaStream_t s, size_t n_nodes, const float* ljr
   return cudaGetLastError();
 }
 
+}  // namespace algdock
+
+namespace algdock {
+cudaError_t launch_gather_probe(cudaStream_t s, const algdock_ctx& c, int64_t n_cells, bool soft, uint32_t seed,
+                                float* sink) {
+  const int threads = 256;
+  const int blocks = 152 * 8;
+  if (soft)
+    gather_probe_kernel<true><<<blocks, threads, 0, s>>>(c.d_hard, c.d_soft, c.grid.nx, c.grid.ny, c.grid.nz, n_cells,
+                                                          seed, sink);
+  else
+    gather_probe_kernel<false><<<blocks, threads, 0, s>>>(c.d_hard, c.d_soft, c.grid.nx, c.grid.ny, c.grid.nz,
+                                                           n_cells, seed, sink);
+  return cudaGetLastError();
+}
 }  // namespace algdock

@@ -203,6 +203,8 @@ cudaError_t launch_grid_build(cudaStream_t s, const algdock_grid_desc& d, int n_
                               float* elec);
 cudaError_t launch_grid_prepare(cudaStream_t s, size_t n_nodes, const float* ljr, const float* lja,
                                 const float* elec, double vmax_r, double vmax_e, float4* hard, float2* soft);
+cudaError_t launch_gather_probe(cudaStream_t s, const algdock_ctx& c, int64_t n_cells, bool soft, uint32_t seed,
+                                float* sink);
 cudaError_t launch_hmc(cudaStream_t s, const algdock_ctx& c, int64_t n_rep, const int32_t* state_of, float* x,
                        double* comps, double* dH, uint8_t* acc, int n_steps, uint64_t seed, uint64_t cycle,
                        int64_t rep_offset, int64_t* counters);

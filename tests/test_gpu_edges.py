@@ -100,3 +100,21 @@ def test_forces_at_layout_boundaries(base, n_atoms):
             assert np.all(F[n] == 0.0)
         else:
             assert np.linalg.norm(F[n] - F_o) / ref <= 1e-5
+
+
+def test_gather_probe_runs_and_keeps_its_sink(base):
+    """The gather-roofline probe (not a step of the method): it needs loaded lattices, reads only,
+    and leaves its sink untouched (the folded sum never takes the impossible value)."""
+    from paper_1507_03703_gb300 import algdock as A
+    sys_, g32, (T, alpha, dt) = base
+    ctx = A.Context(0)
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    with pytest.raises(A.AlgdockError) as e:
+        ctx.gather_probe(1000, sink=sink)
+    assert e.value.status == A.E_STATE
+    ctx.grids_load(sys_.grid, *g32, ligand=sys_.ligand)
+    for soft in (False, True):
+        ctx.gather_probe(100_000, soft=soft, seed=3, sink=sink)
+        ctx.gather_probe(0, soft=soft, sink=sink)
+    torch.cuda.synchronize()
+    assert sink.item() == 0.0
