@@ -1,0 +1,99 @@
+"""Host-side pieces of the multi-ligand batch and of the benchmark's accounting (CPU).
+
+- The clash-free growth mode keeps every atom at least min_sep from all atoms other than its
+  parent and the parent's neighbours, keeps bond lengths in their range and the tree connected, and
+  leaves the default growth (every earlier system) unchanged.
+- The batch workload has the stated sizes and spread.
+- The padded ligands of the padded-uniform baseline add only inert atoms at distinct points.
+- The gather byte count of an HMC launch matches a hand count on a three-state ladder."""
+import sys
+
+import numpy as np
+import pytest
+
+from paper_1507_03703_gb300 import synthetic as S
+
+
+def _graph_distance(lig):
+    n = lig.n_atoms
+    adj = [[] for _ in range(n)]
+    for a, b in lig.bonds:
+        adj[a].append(b)
+        adj[b].append(a)
+    D = np.full((n, n), 99, dtype=int)
+    for i in range(n):
+        D[i, i] = 0
+        frontier = [i]
+        while frontier:
+            nxt = []
+            for u in frontier:
+                for v in adj[u]:
+                    if D[i, v] == 99:
+                        D[i, v] = D[i, u] + 1
+                        nxt.append(v)
+            frontier = nxt
+    return D
+
+
+@pytest.mark.parametrize("n,seed", [(10, 1), (33, 2), (64, 3), (70, 4)])
+def test_clash_free_growth(n, seed):
+    lig = S.make_ligand(n, seed=seed, min_sep=2.6)
+    D = _graph_distance(lig)
+    assert np.all(D < 99)  # one tree
+    assert lig.bonds.shape[0] == n - 1
+    r = np.linalg.norm(lig.x0[:, None] - lig.x0[None], axis=-1)
+    far = D >= 3
+    assert r[far].min() >= 2.6 - 1e-9
+    bl = np.linalg.norm(lig.x0[lig.bonds[:, 0]] - lig.x0[lig.bonds[:, 1]], axis=1)
+    assert np.allclose(bl, lig.bond_r0) and bl.min() >= 1.3 and bl.max() <= 1.6
+    assert abs(lig.charge.sum()) < 1e-12
+
+
+def test_default_growth_is_unchanged():
+    """The default path draws the same numbers as before the clash-free mode existed: the
+    paper-scale ligand keeps its 48 atoms and its first bond and positions."""
+    lig = S.make_ligand(48, seed=2)
+    again = S.make_ligand(48, seed=2, min_sep=None)
+    assert np.array_equal(lig.x0, again.x0) and np.array_equal(lig.bonds, again.bonds)
+    assert S.config_paper_scale(2).ligand.n_atoms == S.ligand_atoms_for_seed(2) == 48
+    # the clash-free mode is a different draw
+    assert not np.array_equal(S.make_ligand(48, seed=2, min_sep=2.6).x0, lig.x0)
+
+
+def test_batch_workload_shape():
+    sys_, ligs = S.config_batch(3, n_ligands=32)
+    sizes = np.array([l.n_atoms for l in ligs])
+    assert len(ligs) == 32 and sizes.min() >= 10 and sizes.max() <= 70
+    assert sys_.receptor.n_atoms == 4000 and tuple(sys_.grid.n) == (129, 129, 129)
+    assert [l.K for l in sys_.legs] == [16, 48]
+    assert all(float(np.float32(o)) == o for o in sys_.grid.origin)
+
+
+@pytest.fixture(scope="module")
+def bench_module():
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import bench
+    return bench
+
+
+def test_padded_ligand_adds_inert_atoms(bench_module):
+    lig = S.make_ligand(12, seed=5, min_sep=2.6)
+    p = bench_module.padded_ligand(lig, 70, np.zeros(3))
+    assert p.n_atoms == 70
+    assert np.array_equal(p.x0[:12], lig.x0) and np.array_equal(p.bonds, lig.bonds)
+    assert np.all(p.charge[12:] == 0) and np.all(p.eps[12:] == 0) and np.all(p.mass[12:] == 1e9)
+    pad = p.x0[12:]
+    d = np.linalg.norm(pad[:, None] - pad[None], axis=-1) + np.eye(58) * 9
+    assert d.min() >= 1.0 - 1e-12
+
+
+def test_gather_bytes_hand_count(bench_module):
+    """alpha = NaN (no grids), 0.25 (soft only in FP32: the hard weight underflows), 1 (hard
+    only): per atom and trial 2 x 192 B of energy evaluations plus (n - 1) x 0, 64, 128 B."""
+    n_atoms, n_steps, R = 7, 11, 3
+    got = bench_module.gather_bytes_per_launch(np.array([np.nan, 0.25, 1.0]), R, n_atoms, n_steps)
+    want = R * n_atoms * (3 * 2 * 192 + (n_steps - 1) * (0 + 64 + 128))
+    assert got == want
