@@ -222,7 +222,7 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
   Y.off_inc = take(ninc);
   Y.words = w;
   if ((size_t)w * 4 > 120 * 1024) return fail(c, ALGDOCK_E_INVALID, who + ": topology too large");
-  Y.off_pair = take(4 * na * na);
+  Y.off_pair = take(2 * na * na);
   Y.words_pair = w;
   blob.assign(w, 0u);
   float* bf = (float*)blob.data();
@@ -260,20 +260,17 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
       bf[Y.off_tor + 12 * ntor + 4 * t + n] = (float)sin(g);
     }
   }
-  // pair table: the Lorentz-Berthelot combination, the 1-4 scales and the exclusions folded into
-  // one record per ordered pair (FP64, rounded once); an excluded pair (and i == j) has zero
-  // coefficients and adds 1 to r^2 so that its arithmetic stays finite
+  // pair table: the 1-4 scales and the exclusions folded into one 8-byte record per ordered pair,
+  // (12 eps_ij s_lj, 332 q_i q_j s_el) from FP64, rounded once; excluded pairs (and i == j) hold
+  // zeros.  R_ij = R*_i + R*_j is formed in the kernel from the per-atom radii.
   for (int j = 0; j < na; ++j)
     for (int i = 0; i < na; ++i) {
       const int ty = ptype[(size_t)j * na + i];
       const double s_lj = ty == 0 ? 1.0 : (ty == 1 ? 0.5 : 0.0);
       const double s_el = ty == 0 ? 1.0 : (ty == 1 ? 1.0 / 1.2 : 0.0);
-      const double R = L->rstar[i] + L->rstar[j];
-      float* rec = bf + Y.off_pair + 4 * ((size_t)j * na + i);
-      rec[0] = ty == 2 ? 0.f : (float)(R * R);
-      rec[1] = (float)(12.0 * s_lj * sqrt(L->eps[i]) * sqrt(L->eps[j]));
-      rec[2] = (float)(kCoulomb * L->charge[i] * L->charge[j] * s_el);
-      rec[3] = ty == 2 ? 1.f : 0.f;
+      float* rec = bf + Y.off_pair + 2 * ((size_t)j * na + i);
+      rec[0] = (float)(12.0 * s_lj * sqrt(L->eps[i]) * sqrt(L->eps[j]));
+      rec[1] = (float)(kCoulomb * L->charge[i] * L->charge[j] * s_el);
     }
   int pos = 0;
   for (int i = 0; i < na; ++i) {

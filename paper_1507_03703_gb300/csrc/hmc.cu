@@ -41,7 +41,7 @@ struct Lig {
   const float4* tor_s;
   const int* inc_start;
   const uint32_t* inc;  // slot indices
-  const float4* pair;   // [j][i] pair records (only where the table is staged)
+  const float2* pair;   // [j][i] pair records (only where the table is staged)
 };
 
 __device__ inline Lig bind_ligand(const uint32_t* s, const LigandLayout& L) {
@@ -58,7 +58,7 @@ __device__ inline Lig bind_ligand(const uint32_t* s, const LigandLayout& L) {
   g.tor_s = (const float4*)(s + L.off_tor + 12 * L.ntor);
   g.inc_start = (const int*)(s + L.off_inc_start);
   g.inc = (const uint32_t*)(s + L.off_inc);
-  g.pair = (const float4*)(s + L.off_pair);
+  g.pair = (const float2*)(s + L.off_pair);
   return g;
 }
 
@@ -352,6 +352,11 @@ __device__ inline void nonbonded(const Lig& L, int na, const float4* xs, float (
 // Step 3 from the pair table: the same passes and lane layout as `nonbonded`, with each pair's
 // combined and scaled coefficients read as one record (R_ij^2, 12 eps_ij, 332 q_i q_j, guard)
 // instead of being formed from per-atom parameters and the pair type.
+// The pair-table loop.  Positions carry R*_i in their fourth component (xs[j].w); each ordered pair
+// reads one 8-byte record (12 eps_ij s_LJ, 332 q_i q_j s_el), zero for excluded pairs and i == j,
+// and forms R_ij = R*_i + R*_j (Lorentz-Berthelot) in registers.  r^2 is floored at 0.01 A^2 so
+// that a zero record meets finite powers (i == j): (R_ij / r)^12 stays below 1e20 for R_ij <= 4 A.
+constexpr float kPairMinR2 = 1.0e-2f;
 template <int APL, bool ENERGY, bool FORCES = true>
 __device__ inline void nonbonded_table(const Lig& L, int na, const float4* xs, float (&F)[APL][3], float& el) {
   const int lane = threadIdx.x & 31;
@@ -375,28 +380,29 @@ __device__ inline void nonbonded_table(const Lig& L, int na, const float4* xs, f
     float fx = 0.f, fy = 0.f, fz = 0.f;
     if (act) {
       const float4 pi = xs[i];
-      const float4* rec = L.pair + (size_t)jb * na + i;
+      const float2* rec = L.pair + (size_t)jb * na + i;
       const float4* pj_ptr = xs + jb;
       const int rstep = dir * na;
       for (int jj = 0; jj < cnt; ++jj) {
         const float4 pj = *pj_ptr;
-        const float4 t = *rec;
+        const float2 t = *rec;
         pj_ptr += dir;
         rec += rstep;
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, t.w)));
+        const float r2 = fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), kPairMinR2);
+        const float R = pi.w + pj.w;
         const float inv_r = rsqrtf(r2);
         const float inv_r2 = inv_r * inv_r;
-        const float s2 = t.x * inv_r2;
+        const float s2 = (R * R) * inv_r2;
         const float s6 = s2 * s2 * s2;
-        const float eel = t.z * inv_r;
-        const float fr = fmaf(t.y, fmaf(s6, s6, -s6), eel) * inv_r2;
+        const float eel = t.y * inv_r;
+        const float fr = fmaf(t.x, fmaf(s6, s6, -s6), eel) * inv_r2;
         if (FORCES) {
           fx = fmaf(fr, dx, fx);
           fy = fmaf(fr, dy, fy);
           fz = fmaf(fr, dz, fz);
         }
-        if (ENERGY) e2 += fmaf(t.y * (1.f / 12.f), fmaf(s6, s6, -2.f * s6), eel);
+        if (ENERGY) e2 += fmaf(t.x * (1.f / 12.f), fmaf(s6, s6, -2.f * s6), eel);
       }
     }
     if (split) {
@@ -618,7 +624,8 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
       v[a][1] = rr1 * s1 * sd;
       v[a][2] = rr2 * c2 * sd;
       kin += pb.z * (v[a][0] * v[a][0] + v[a][1] * v[a][1] + v[a][2] * v[a][2]);
-      xs[i] = make_float4(x[a][0], x[a][1], x[a][2], L.atom_a[i].y);
+      // the table loop reads R*_i from the fourth component, the pair-type loop the charge
+      xs[i] = make_float4(x[a][0], x[a][1], x[a][2], TABLE ? pb.x : L.atom_a[i].y);
     } else {
       x[a][0] = x[a][1] = x[a][2] = 0.f;
       v[a][0] = v[a][1] = v[a][2] = 0.f;

@@ -88,8 +88,8 @@ struct LigandLayout {
   int off_inc_start;  // int[na + 1]
   int off_inc;        // uint32[ninc]: the bonded slots of each atom, in a fixed order
   int words;          // total of the sections above (multiple of 4)
-  int off_pair;       // float4[na][na], [j][i]: (R_ij^2, 12 eps_ij s_lj, 332 q_i q_j s_el, 1 if excluded
-                      // else 0), after the sections above
+  int off_pair;       // float2[na][na], [j][i]: (12 eps_ij s_lj, 332 q_i q_j s_el), zero if excluded or
+                      // i == j, after the sections above
   int words_pair;     // total including the pair table
   float total_mass;
   float site[3];
