@@ -350,11 +350,10 @@ __device__ inline void nonbonded(const Lig& L, int na, const float4* xs, float (
 }
 
 // Step 3 from the pair table: the same passes and lane layout as `nonbonded`, with each pair's
-// combined and scaled coefficients read as one record (R_ij^2, 12 eps_ij, 332 q_i q_j, guard)
-// instead of being formed from per-atom parameters and the pair type.
-// The pair-table loop.  Positions carry R*_i in their fourth component (xs[j].w); each ordered pair
-// reads one 8-byte record (12 eps_ij s_LJ, 332 q_i q_j s_el), zero for excluded pairs and i == j,
-// and forms R_ij = R*_i + R*_j (Lorentz-Berthelot) in registers.  r^2 is floored at 0.01 A^2 so
+// scaled coefficients read as one 8-byte record (12 eps_ij s_LJ, 332 q_i q_j s_el), zero for
+// excluded pairs and i == j, instead of being formed from per-atom parameters and the pair type.
+// Positions carry R*_i in their fourth component (xs[j].w), and R_ij = R*_i + R*_j
+// (Lorentz-Berthelot) is formed in registers.  r^2 is floored at 0.01 A^2 so
 // that a zero record meets finite powers (i == j): (R_ij / r)^12 stays below 1e20 for R_ij <= 4 A.
 constexpr float kPairMinR2 = 1.0e-2f;
 template <int APL, bool ENERGY, bool FORCES = true>
