@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
   const float dt = st.dt, hdt = 0.5f * st.dt;
   const uint32_t rid = (uint32_t)(A.rep_offset + r);
 
-  float x[APL][3], v[APL][3], F[APL][3], x0[APL][3];
+  float x[APL][3], v[APL][3], F[APL][3];
   float kin = 0.f;
 #pragma unroll
   for (int a = 0; a < APL; ++a) {
@@ -629,15 +629,17 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
       x[a][0] = x[a][1] = x[a][2] = 0.f;
       v[a][0] = v[a][1] = v[a][2] = 0.f;
     }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) x0[a][d] = x[a][d];
   }
   __syncwarp();
   int outside = 0;
   Energies en;
-  double c0[4], c1[4];
+  double c[4];
   evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
-  reduce_components(en, c0);
+  reduce_components(en, c);
+  // the starting components go out now (a rejected trial leaves them); only U0 stays live
+  const double U0 = weighted(c, st.w_sg, st.w_g);
+  if (lane < 4) A.comps[r * 4 + lane] = lane == 0 ? c[0] : (lane == 1 ? c[1] : (lane == 2 ? c[2] : c[3]));
+  double U1 = U0;
   const double K0 = 0.5 * kKineticToKcal * warp_sum((double)kin);
   for (int s = 0; s < A.n_steps; ++s) {
 #pragma unroll
@@ -669,7 +671,8 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
       evaluate<APL, false, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, false, en, outside);
     } else {
       evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
-      reduce_components(en, c1);
+      reduce_components(en, c);
+      U1 = weighted(c, st.w_sg, st.w_g);
     }
 #pragma unroll
     for (int a = 0; a < APL; ++a) {
@@ -681,10 +684,6 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
       }
     }
   }
-  if (A.n_steps == 0) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) c1[c] = c0[c];
-  }
   kin = 0.f;
 #pragma unroll
   for (int a = 0; a < APL; ++a) {
@@ -692,22 +691,24 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
     if (i < na) kin += L.atom_b[i].z * (v[a][0] * v[a][0] + v[a][1] * v[a][1] + v[a][2] * v[a][2]);
   }
   const double K1 = 0.5 * kKineticToKcal * warp_sum((double)kin);
-  const double U0 = weighted(c0, st.w_sg, st.w_g), U1 = weighted(c1, st.w_sg, st.w_g);
   const double dH = (K1 + U1) - (K0 + U0);
   const U4 o = philox(A.seed, 0u, rid, A.cycle, kPurposeAccept);
   const double u = uniform53(o.x, o.y);
   const bool accept = u < exp(-dH / st.kT);
+  if (accept) {  // a rejected trial leaves the stored positions and components as they were
 #pragma unroll
-  for (int a = 0; a < APL; ++a) {
-    const int i = lane + 32 * a;
-    if (i < na) {
-      float* dst = A.x + (r * xstride + i) * 3;
-      dst[0] = accept ? x[a][0] : x0[a][0];
-      dst[1] = accept ? x[a][1] : x0[a][1];
-      dst[2] = accept ? x[a][2] : x0[a][2];
+    for (int a = 0; a < APL; ++a) {
+      const int i = lane + 32 * a;
+      if (i < na) {
+        float* dst = A.x + (r * xstride + i) * 3;
+        dst[0] = x[a][0];
+        dst[1] = x[a][1];
+        dst[2] = x[a][2];
+      }
     }
+    if (A.n_steps > 0 && lane < 4)
+      A.comps[r * 4 + lane] = lane == 0 ? c[0] : (lane == 1 ? c[1] : (lane == 2 ? c[2] : c[3]));
   }
-  if (lane < 4) A.comps[r * 4 + lane] = accept ? c1[lane] : c0[lane];
   if (lane == 0) {
     if (A.dH) A.dH[r] = dH;
     if (A.acc) A.acc[r] = accept ? 1 : 0;
