@@ -745,3 +745,34 @@ def fep(du):
     n_eff = s1 * s1 / s2
     sigma = math.sqrt(max(N / n_eff - 1.0, 0.0) / (N - 1)) if N > 1 else math.nan
     return {"f": f, "sigma": sigma, "n_eff": n_eff, "du_min": m}
+
+
+# ------------------------------------------------------------------ state insertion between cycles
+def split_ladder(T, alpha, dt, attempts, accepts, threshold=0.4, T_T=300.0, T_H=600.0):
+    """The between-cycle insertion rule ("Equilibration and production"): wherever the mean
+    replica-exchange acceptance between neighbouring states a and a+1 over the cycle fell below
+    the threshold (0.4), one state is placed between them.  Its parameters are the midpoint of
+    the leg's control parameter: the geometric mean of the temperatures on the warming leg (alpha
+    NaN, geometric temperatures), the mean alpha on the coupling leg with T = T_H + (T_T - T_H)
+    alpha; its time step is the smaller of the two.  attempts / accepts hold the neighbour-pair
+    counts [K - 1].  Returns (T, alpha, dt, inserted) with inserted the new states' indices in
+    the returned ladder."""
+    T, alpha, dt = list(map(float, T)), list(map(float, alpha)), list(map(float, dt))
+    K = len(T)
+    split = [a for a in range(K - 1) if attempts[a] > 0 and accepts[a] / attempts[a] < threshold]
+    oT, oA, oD, inserted = [], [], [], []
+    for k in range(K):
+        oT.append(T[k])
+        oA.append(alpha[k])
+        oD.append(dt[k])
+        if k in split:
+            if alpha[k] != alpha[k]:  # NaN: the warming leg
+                newT, newA = (T[k] * T[k + 1]) ** 0.5, float("nan")
+            else:
+                newA = 0.5 * (alpha[k] + alpha[k + 1])
+                newT = T_H + (T_T - T_H) * newA
+            inserted.append(len(oT))
+            oT.append(newT)
+            oA.append(newA)
+            oD.append(min(dt[k], dt[k + 1]))
+    return np.array(oT), np.array(oA), np.array(oD), inserted
