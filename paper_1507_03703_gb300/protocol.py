@@ -69,6 +69,33 @@ def adapt_dt(dt, acc):
     return min(5.0, max(0.1, dt))
 
 
+def insertions(T, alpha, dt, attempts, accepts, threshold=0.4, T_T=300.0, T_H=600.0):
+    """Between cycles ("Equilibration and production"): a state goes between every neighbour
+    pair (a, a+1) whose exchange acceptance over the cycle is below the threshold (pairs never
+    attempted are left alone), at the midpoint of the leg's control parameter (the geometric mean
+    temperature on the warming leg, the mean alpha with T(alpha) on the coupling leg) and with the
+    smaller time step.  attempts / accepts: neighbour-pair counts [K - 1].  Returns the new
+    (T, alpha, dt) and, for each new state, (its index, the index of its lower neighbour)."""
+    T, alpha, dt = np.asarray(T, float), np.asarray(alpha, float), np.asarray(dt, float)
+    att, acc = np.asarray(attempts, float), np.asarray(accepts, float)
+    nT, nA, nD, new = [], [], [], []
+    for k in range(T.size):
+        nT.append(T[k])
+        nA.append(alpha[k])
+        nD.append(dt[k])
+        if k + 1 < T.size and att[k] > 0 and acc[k] / att[k] < threshold:
+            if math.isnan(alpha[k]):
+                t, a = math.sqrt(T[k] * T[k + 1]), math.nan
+            else:
+                a = 0.5 * (alpha[k] + alpha[k + 1])
+                t = T_H + (T_T - T_H) * a
+            new.append((len(nT), len(nT) - 1))
+            nT.append(t)
+            nA.append(a)
+            nD.append(min(dt[k], dt[k + 1]))
+    return np.array(nT), np.array(nA), np.array(nD), new
+
+
 class ProtocolBuilder:
     """Builds the states of one leg on a context whose grids and ligand are loaded; the context's
     state table is replaced as states are added."""

@@ -131,6 +131,95 @@ class ReplicaExchange:
         if record:
             self.history.append(self.comps.clone())
 
+    def acceptance(self, li: int):
+        """Neighbour-pair exchange acceptance of leg li since its counters were last reset, [K - 1]."""
+        att = self.attempts[li][0, :-1].double().cpu().numpy()
+        acc = self.accepts[li][0, :-1].double().cpu().numpy()
+        return np.divide(acc, att, out=np.full_like(att, np.nan), where=att > 0)
+
+    def insert_states(self, T, alpha, dt, threshold=0.4, seed=0, counter=0):
+        """Between cycles ("Equilibration and production"): where a leg's neighbour exchange
+        acceptance over the cycles since the last insertion fell below the threshold, insert a
+        state (protocol.insertions) and populate it by sampling importance resampling: each chain's
+        configuration for the new state is drawn from the configurations at its lower neighbour,
+        all chains pooled, with weights exp(u_lower - u_new) (the library's resample kernel).
+        T, alpha, dt: the context's whole state table, which this run's legs make up in order.
+        Rebuilds the state table, the replica buffers (identity permutations), zeroes the exchange
+        counters and clears the recorded history (a sharded run renumbers its replicas: its rank
+        offsets follow the new ladder sizes).  Returns the new (T, alpha, dt) and, per leg, the
+        indices of the inserted states within the leg."""
+        from .protocol import insertions
+        T, alpha, dt = np.asarray(T, float), np.asarray(alpha, float), np.asarray(dt, float)
+        if T.size != sum(l.K for l in self.legs) or any(
+                l.state_offset != sum(m.K for m in self.legs[:i]) for i, l in enumerate(self.legs)):
+            raise ValueError("insert_states needs the run's legs to make up the whole state table, in order")
+        dev = self.x.device
+        plans, nT, nA, nD = [], [], [], []
+        for li, leg in enumerate(self.legs):
+            o = leg.state_offset
+            att = self.attempts[li][0, :leg.K - 1].cpu().numpy()
+            acc = self.accepts[li][0, :leg.K - 1].cpu().numpy()
+            lt, la, ld, new = insertions(T[o:o + leg.K], alpha[o:o + leg.K], dt[o:o + leg.K], att, acc, threshold)
+            plans.append((lt.size, new))
+            nT.append(lt)
+            nA.append(la)
+            nD.append(ld)
+        if all(not new for _, new in plans):
+            return T, alpha, dt, [[] for _ in self.legs]
+        newT, newA, newD = np.concatenate(nT), np.concatenate(nA), np.concatenate(nD)
+        self.ctx.states_set(newT, newA, newD)
+        C, na = self.C, self.n_atoms
+        xs_legs, cs_legs, legs, off = [], [], [], 0
+        for li, (leg, (K2, new)) in enumerate(zip(self.legs, plans)):
+            sl = self.leg_slice(li)
+            # configurations and components by state: slot config_of[c, k] of chain c holds state k
+            cfg = self.config_of[li].view(C, leg.K).long()
+            rows = (torch.arange(C, device=dev)[:, None] * leg.K + cfg).reshape(-1)
+            xk = self.x[sl][rows].view(C, leg.K, na, 3)
+            ck = self.comps[sl][rows].view(C, leg.K, 4)
+            old_pos = [k2 for k2 in range(K2) if k2 not in {n for n, _ in new}]
+            x2 = torch.empty((C, K2, na, 3), dtype=self.x.dtype, device=dev)
+            c2 = torch.empty((C, K2, 4), dtype=torch.float64, device=dev)
+            x2[:, old_pos] = xk
+            c2[:, old_pos] = ck
+            for j, (n, lower) in enumerate(new):
+                k_lower = old_pos.index(lower)
+                pool_c = ck[:, k_lower].contiguous()
+                pool_x = xk[:, k_lower].contiguous()
+                idx = torch.empty(C, dtype=torch.int64, device=dev)
+                xo = torch.empty((C, na, 3), dtype=self.x.dtype, device=dev)
+                self.ctx.resample(pool_c, off + lower, off + n, C, seed, counter + 1000 * li + j, x_in=pool_x,
+                                  x_out=xo, idx=idx)
+                x2[:, n] = xo
+                c2[:, n] = pool_c[idx]
+            xs_legs.append(x2.reshape(-1, na, 3))
+            cs_legs.append(c2.reshape(-1, 4))
+            legs.append(Leg(K2, off))
+            off += K2
+        self.legs = legs
+        self.R = C * sum(l.K for l in legs)
+        self.x = torch.cat(xs_legs).contiguous()
+        self.comps = torch.cat(cs_legs).contiguous()
+        self.dH = torch.zeros(self.R, dtype=torch.float64, device=dev)
+        self.acc = torch.zeros(self.R, dtype=torch.uint8, device=dev)
+        self.ext_acc = torch.zeros(self.R, dtype=torch.int32, device=dev)
+        self.base, state = [], np.empty(self.R, dtype=np.int32)
+        self.config_of, self.attempts, self.accepts = [], [], []
+        b = 0
+        for leg in legs:
+            self.base.append(b)
+            for c in range(C):
+                state[b + c * leg.K: b + (c + 1) * leg.K] = leg.state_offset + np.arange(leg.K)
+            self.config_of.append(torch.arange(leg.K, dtype=torch.int32, device=dev).repeat(C).contiguous())
+            self.attempts.append(torch.zeros((self.max_sep, leg.K), dtype=torch.int64, device=dev))
+            self.accepts.append(torch.zeros((self.max_sep, leg.K), dtype=torch.int64, device=dev))
+            b += C * leg.K
+        self.state_of = torch.from_numpy(state).to(dev)
+        self.history = []
+        if self.batched:
+            self.ctx.batch_layout(self.lig_of(), na)
+        return newT, newA, newD, [[n for n, _ in new] for _, new in plans]
+
     def free_energies(self, li: int, tol=1e-10, max_iter=10000, precision_mode=0, chains=None):
         """MBAR over the recorded components of leg li (optionally a subset of chains)."""
         leg = self.legs[li]

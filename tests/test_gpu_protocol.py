@@ -111,3 +111,63 @@ def test_gpu_coupling_leg_is_slowed_until_neighbours_overlap():
     assert np.all(r["pacc"] >= 0.4)
     assert r["alpha"][0] == 0.0 and r["alpha"][-1] == 1.0 and np.all(np.diff(r["alpha"]) > 0)
     assert np.allclose(r["T"], 600.0 - 300.0 * r["alpha"])
+
+
+def test_gpu_state_insertion_between_cycles():
+    """Between cycles ("Equilibration and production"): a ladder with wide gaps (warming 300 and
+    600 K; coupling alpha 0, 0.5, 1) runs 3 cycles; every neighbour pair whose exchange acceptance
+    fell below 0.4 gets a state at the midpoint (the oracle's rule on the same counts), the old
+    states keep their configurations bit for bit, and each new state's configurations are the
+    importance-resampled draws (the oracle's indices) from its lower neighbour's configurations
+    pooled over the chains.  The rebuilt run then cycles on."""
+    from paper_1507_03703_gb300.sampler import Leg, ReplicaExchange
+    sys_ = S.config_small(1)
+    g32 = raw_grids32(sys_)
+    T = np.array([300.0, 600.0, 600.0, 450.0, 300.0])
+    A = np.array([np.nan, np.nan, 0.0, 0.5, 1.0])
+    D = np.full(5, 2.0)
+    ctx = gpu_context(sys_, g32, T, A, D)
+    C = 32
+    legs = [Leg(2, 0), Leg(3, 2)]
+    run = ReplicaExchange(ctx, legs, C, configurations(sys_, C * 5, seed=9, jitter=0.1), seed=5)
+    for cyc in range(3):
+        run.cycle(cyc, 20)
+    na = sys_.ligand.n_atoms
+    att = [run.attempts[li][0].cpu().numpy()[:l.K - 1] for li, l in enumerate(legs)]
+    acc = [run.accepts[li][0].cpu().numpy()[:l.K - 1] for li, l in enumerate(legs)]
+    by_state = []
+    for li, leg in enumerate(legs):
+        sl = run.leg_slice(li)
+        cfg = run.config_of[li].view(C, leg.K).long().cpu().numpy()
+        rows = (np.arange(C)[:, None] * leg.K + cfg).reshape(-1)
+        by_state.append((run.x[sl].cpu().numpy()[rows].reshape(C, leg.K, na, 3),
+                         run.comps[sl].cpu().numpy()[rows].reshape(C, leg.K, 4)))
+    nT, nA, nD, ins = run.insert_states(T, A, D, seed=13, counter=0)
+    off_old, off_new = 0, 0
+    for li, leg in enumerate(legs):
+        sl = slice(off_old, off_old + leg.K)
+        oT, oA, oD, o_ins = oracle.split_ladder(T[sl], A[sl], D[sl], att[li], acc[li])
+        assert ins[li] == o_ins
+        K2 = oT.size
+        assert np.allclose(nT[off_new:off_new + K2], oT, rtol=1e-15) and np.array_equal(nD[off_new:off_new + K2], oD)
+        xk, ck = by_state[li]
+        new_leg = run.legs[li]
+        assert new_leg.K == K2 and new_leg.state_offset == off_new
+        x2 = run.x[run.leg_slice(li)].cpu().numpy().reshape(C, K2, na, 3)
+        c2 = run.comps[run.leg_slice(li)].cpu().numpy().reshape(C, K2, 4)
+        old_pos = [k for k in range(K2) if k not in o_ins]
+        assert np.array_equal(x2[:, old_pos], xk) and np.array_equal(c2[:, old_pos], ck)
+        for j, n in enumerate(o_ins):
+            lower = old_pos.index(n - 1)
+            pool_c = ck[:, lower]
+            u = oracle.ukn_from_comps(nT, nA, pool_c)
+            idx = oracle.resample(u[off_new + n - 1] - u[off_new + n], C, 13, 1000 * li + j)
+            assert np.array_equal(x2[:, n], xk[idx, lower]) and np.array_equal(c2[:, n], pool_c[idx])
+        off_old += leg.K
+        off_new += K2
+    assert sum(len(i) for i in ins) >= 2  # the wide gaps exchange rarely
+    assert run.R == C * sum(l.K for l in run.legs) and run.history == []
+    for cyc in range(3, 5):
+        run.cycle(cyc, 20)
+    torch.cuda.synchronize()
+    assert all(np.all(np.isfinite(run.acceptance(li)[~np.isnan(run.acceptance(li))])) for li in range(2))

@@ -25,3 +25,29 @@ def test_temperature_step_and_time_step_rule():
             assert P.adapt_dt(dt, acc) == oracle.adapt_dt(dt, acc)
     assert math.isclose(P.d_alpha_g(0.5), 0.0, abs_tol=1e-15)
     assert np.sign(P.d_alpha_sg(0.2)) > 0 > np.sign(P.d_alpha_sg(0.8))
+
+
+def test_state_insertion_rule_matches_the_oracle():
+    """protocol.insertions (the host's between-cycle rule) against oracle.split_ladder on random
+    ladders and exchange counts of both legs: the same insertions, parameters equal to rounding."""
+    from paper_1507_03703_gb300.protocol import insertions
+    rng = np.random.default_rng(41)
+    for trial in range(200):
+        K = int(rng.integers(2, 12))
+        if trial % 2:
+            T = np.sort(rng.uniform(300, 600, K))
+            A = np.full(K, np.nan)
+        else:
+            A = np.sort(rng.uniform(0, 1, K))
+            T = 600.0 - 300.0 * A
+        D = rng.uniform(0.5, 3.0, K)
+        att = rng.integers(0, 50, K - 1)
+        acc = np.minimum(att, rng.integers(0, 50, K - 1))
+        hT, hA, hD, new = insertions(T, A, D, att, acc)
+        oT, oA, oD, ins = oracle.split_ladder(T, A, D, att, acc)
+        assert [n for n, _ in new] == ins
+        assert all(lower == n - 1 for n, lower in new)
+        # independent arithmetic (sqrt against a power of 1/2): equal to rounding
+        assert np.allclose(hT, oT, rtol=1e-15, atol=0) and np.array_equal(hD, oD)
+        assert np.array_equal(np.isnan(hA), np.isnan(oA))
+        assert np.allclose(hA[~np.isnan(hA)], oA[~np.isnan(oA)], rtol=1e-15, atol=0)
