@@ -131,6 +131,24 @@ algdock_status algdock_soft_elec_cap(const algdock_ligand* lig, double vmax_r, d
 algdock_status algdock_grids_load(algdock_ctx* ctx, const algdock_grid_desc* desc, const float* ljr,
                                   const float* lja, const float* elec, double vmax_r, double vmax_e);
 
+/* ---------------------------------------------------------------- the all-FP64 path
+ * The FP64 arm of the precision study (no counterpart in the paper): the same energy function
+ * as algdock_energy_force with every operation in FP64, on FP64 lattices and the ligand's FP64
+ * parameters (kept by algdock_ligand_load).  One thread per configuration; a study tool, not a
+ * fast path. */
+
+/* FP64 lattices from raw grids (host or device double [nz][ny][nx]), derived as algdock_grids_load
+ * does (4th root of the capped repulsive grid, tanh-capped soft grids) but kept in FP64.  They
+ * are separate from the FP32 lattices. */
+algdock_status algdock_grids_load_f64(algdock_ctx* ctx, const algdock_grid_desc* desc, const double* ljr,
+                                      const double* lja, const double* elec, double vmax_r, double vmax_e);
+
+/* Components {U_L, U_I, Psi_sg, Psi_g} (comps [N][4] double) and, with force != NULL, the force
+ * [N][n_atoms][3] double of the state state_of[n] (NULL: grid weights zero) for configurations
+ * x [N][n_atoms][3] float, all in FP64.  Device arrays. */
+algdock_status algdock_energy_force_f64(algdock_ctx* ctx, int64_t N, const int32_t* state_of, const float* x,
+                                        double* force, double* comps);
+
 /* Measurement aid for the gather roofline (no counterpart in the paper, not a step of the
  * method): n_cells 8-corner gathers from the loaded lattices at cells drawn uniformly (hard float4
  * corners; with soft != 0 also the soft float2 corners), the access pattern of one atom's

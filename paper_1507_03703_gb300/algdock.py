@@ -33,7 +33,8 @@ EXPORTS = [
     "algdock_external_moves", "algdock_detect_equilibration", "algdock_state_statistics", "algdock_resample",
     "algdock_mean_pacc", "algdock_receptor_load", "algdock_target_interaction", "algdock_fep",
     "algdock_batch_load", "algdock_batch_layout", "algdock_batch_hmc_cycle", "algdock_batch_tune",
-    "algdock_hmc_shape", "algdock_batch_shapes", "algdock_gather_probe",
+    "algdock_hmc_shape", "algdock_batch_shapes", "algdock_gather_probe", "algdock_grids_load_f64",
+    "algdock_energy_force_f64",
 ]
 
 BATCH_CLASSES = 4             # launch classes of a multi-ligand batch
@@ -139,6 +140,8 @@ def load_library(path: str = LIB_PATH):
         "algdock_batch_tune": ([vp, vp, vp, i32, i32, vp, vp], C.c_int),
         "algdock_hmc_shape": ([vp, vp], C.c_int),
         "algdock_gather_probe": ([vp, i64, i32, u64, vp], C.c_int),
+        "algdock_grids_load_f64": ([vp, C.POINTER(GridDesc), vp, vp, vp, dbl, dbl], C.c_int),
+        "algdock_energy_force_f64": ([vp, i64, vp, vp, vp, vp], C.c_int),
         "algdock_batch_shapes": ([vp, vp], C.c_int),
         "algdock_exchange": ([vp, i32, i32, i32, vp, vp, vp, i32, i32, u64, u64, i64, vp, vp], C.c_int),
         "algdock_reduced_energies": ([vp, i64, vp, vp, i32, i32, vp], C.c_int),
@@ -297,6 +300,28 @@ class Context:
         p2, k2 = _any(lja, np.float32, torch.float32, "lja")
         p3, k3 = _any(elec, np.float32, torch.float32, "elec")
         self._check(self._L.algdock_grids_load(self.h, C.byref(d), p1, p2, p3, float(vmax_r), float(vmax_e)))
+
+    def grids_load_f64(self, grid, ljr, lja, elec, vmax_r=VMAX_R, vmax_e=None, ligand=None):
+        """FP64 lattices for the all-FP64 path from raw FP64 grids (numpy or CUDA float64)."""
+        import torch
+        if vmax_e is None:
+            vmax_e = soft_elec_cap(ligand, vmax_r) if ligand is not None else math.inf
+        d = grid_desc(grid)
+        p1, k1 = _any(ljr, np.float64, torch.float64, "ljr")
+        p2, k2 = _any(lja, np.float64, torch.float64, "lja")
+        p3, k3 = _any(elec, np.float64, torch.float64, "elec")
+        self._check(self._L.algdock_grids_load_f64(self.h, C.byref(d), p1, p2, p3, float(vmax_r), float(vmax_e)))
+
+    def energy_force_f64(self, x, state_of=None, force=None, comps=None):
+        """All-FP64 components [N, 4] (and forces [N, n_atoms, 3] if a force tensor is given)."""
+        import torch
+        N = int(x.shape[0])
+        if comps is None:
+            comps = torch.empty((N, 4), dtype=torch.float64, device=x.device)
+        self._check(self._L.algdock_energy_force_f64(self.h, N, _dev(state_of, torch.int32, "state_of"),
+                                                     _dev(x, torch.float32, "x"), _dev(force, torch.float64, "force"),
+                                                     _dev(comps, torch.float64, "comps")))
+        return comps
 
     def gather_probe(self, n_cells, soft=True, seed=1, sink=None):
         """Enqueue n_cells random 8-corner lattice gathers (the gather roofline's peak probe)."""

@@ -124,7 +124,8 @@ double sqrtA(double rstar, double eps) {
 // records, pair types, bonded terms, incidence lists, then the per-pair table) and the FP64
 // target-force-field factors of each atom.
 algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdock_restraint* R, const std::string& who,
-                            LigandLayout& Y, std::vector<uint32_t>& blob, std::vector<TargetFactors>& fac) {
+                            LigandLayout& Y, std::vector<uint32_t>& blob, std::vector<TargetFactors>& fac,
+                            Lig64* Y64 = nullptr, std::vector<double>* blob64 = nullptr) {
   if (!L || !R) return fail(c, ALGDOCK_E_INVALID, who + ": null argument");
   const int na = L->n_atoms, nb = L->n_bonds, nang = L->n_angles, ntor = L->n_torsions;
   if (na < 1 || na > kMaxAtoms) return fail(c, ALGDOCK_E_INVALID, who + ": need 1 <= n_atoms <= 96");
@@ -288,6 +289,60 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
     fac[i] = TargetFactors{sqrtA(L->rstar[i], L->eps[i]), sqrt(2.0 * L->eps[i]) * two_r * two_r * two_r,
                            kCoulomb * L->charge[i], 0.0};
   }
+  if (Y64 && blob64) {  // the all-FP64 path's copy of the parameters, unrounded
+    Lig64& G = *Y64;
+    std::vector<double>& d = *blob64;
+    G.na = na;
+    G.nb = nb;
+    G.nang = nang;
+    G.ntor = ntor;
+    G.off_atom = 0;
+    G.off_bond = 6 * na;
+    G.off_ang = G.off_bond + 4 * nb;
+    G.off_tor = G.off_ang + 5 * nang;
+    G.off_ptype = G.off_tor + 10 * ntor;
+    G.n_doubles = G.off_ptype + na * na;
+    d.assign(G.n_doubles > 0 ? G.n_doubles : 1, 0.0);
+    for (int i = 0; i < na; ++i) {
+      const double two_r = 2.0 * L->rstar[i];
+      double* a = &d[G.off_atom + 6 * i];
+      a[0] = L->mass[i];
+      a[1] = L->charge[i];
+      a[2] = sqrtA(L->rstar[i], L->eps[i]);
+      a[3] = sqrt(2.0 * L->eps[i]) * two_r * two_r * two_r;
+      a[4] = L->rstar[i];
+      a[5] = sqrt(L->eps[i]);
+    }
+    for (int t = 0; t < nb; ++t) {
+      double* b = &d[G.off_bond + 4 * t];
+      b[0] = L->bonds[2 * t];
+      b[1] = L->bonds[2 * t + 1];
+      b[2] = L->bond_k[t];
+      b[3] = L->bond_r0[t];
+    }
+    for (int t = 0; t < nang; ++t) {
+      double* a = &d[G.off_ang + 5 * t];
+      for (int k = 0; k < 3; ++k) a[k] = L->angles[3 * t + k];
+      a[3] = L->angle_k[t];
+      a[4] = L->angle_theta0[t];
+    }
+    for (int t = 0; t < ntor; ++t) {
+      double* q = &d[G.off_tor + 10 * t];
+      for (int k = 0; k < 4; ++k) q[k] = L->torsions[4 * t + k];
+      for (int m = 0; m < 3; ++m) {
+        q[4 + m] = 0.5 * L->torsion_V[3 * t + m];
+        q[7 + m] = L->torsion_gamma[3 * t + m];
+      }
+    }
+    for (int j = 0; j < na; ++j)
+      for (int i = 0; i < na; ++i) d[G.off_ptype + (size_t)j * na + i] = ptype[(size_t)j * na + i];
+    double M = 0.0;
+    for (int i = 0; i < na; ++i) M += L->mass[i];
+    G.total_mass = M;
+    for (int k = 0; k < 3; ++k) G.site[k] = R->site[k];
+    G.k_rest = R->k;
+    G.d0 = R->d0;
+  }
   return ALGDOCK_OK;
 }
 
@@ -397,6 +452,8 @@ void algdock_destroy(algdock_ctx* c) {
   cudaFree(c->d_rec);
   cudaFree(c->d_lig_fac);
   cudaFree(c->d_fep);
+  cudaFree(c->d_lig64);
+  cudaFree(c->d_grid64);
   batch_free(c);
   for (int k = 0; k < kBatchClasses; ++k) {
     if (c->batch_side[k]) cudaStreamDestroy(c->batch_side[k]);
@@ -512,6 +569,77 @@ algdock_status algdock_grids_load(algdock_ctx* c, const algdock_grid_desc* d, co
   ALGDOCK_CATCH(c)
 }
 
+algdock_status algdock_grids_load_f64(algdock_ctx* c, const algdock_grid_desc* d, const double* ljr, const double* lja,
+                                      const double* elec, double vmax_r, double vmax_e) {
+  ALGDOCK_TRY(c)
+  if (!d || !ljr || !lja || !elec) return fail(c, ALGDOCK_E_INVALID, "grids_load_f64: null argument");
+  if (d->n[0] < 2 || d->n[1] < 2 || d->n[2] < 2 || !(d->spacing > 0))
+    return fail(c, ALGDOCK_E_INVALID, "grids_load_f64: lattice needs n >= 2 and spacing > 0");
+  if (!(vmax_r > 0) || !(vmax_e > 0)) return fail(c, ALGDOCK_E_INVALID, "grids_load_f64: caps must be > 0");
+  const size_t n = (size_t)d->n[0] * d->n[1] * d->n[2];
+  if (n > ((size_t)1 << 31)) return fail(c, ALGDOCK_E_INVALID, "grids_load_f64: lattice too large");
+  Device g(c->device);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "grids_load_f64");
+  if (n != c->grid64_nodes) {
+    cudaFree(c->d_grid64);
+    c->d_grid64 = nullptr;
+    c->has_grid64 = false;
+    e = cudaMalloc(&c->d_grid64, n * (sizeof(Hard64) + sizeof(Soft64)));
+    if (e != cudaSuccess) return cuda_fail(c, e, "grids_load_f64");
+    c->grid64_nodes = n;
+  }
+  Hard64* hard = (Hard64*)c->d_grid64;
+  Soft64* soft = (Soft64*)((uint8_t*)c->d_grid64 + n * sizeof(Hard64));
+  const void *pr, *pa, *pe;
+  void *or_ = nullptr, *oa = nullptr, *oe = nullptr;
+  e = device_view(c->stream, ljr, n * 8, &pr, &or_);
+  if (e == cudaSuccess) e = device_view(c->stream, lja, n * 8, &pa, &oa);
+  if (e == cudaSuccess) e = device_view(c->stream, elec, n * 8, &pe, &oe);
+  if (e == cudaSuccess)
+    e = launch_grid_prepare64(c->stream, n, (const double*)pr, (const double*)pa, (const double*)pe, vmax_r, vmax_e,
+                              hard, soft);
+  if (or_ || oa || oe) {
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = e2;
+    cudaFree(or_);
+    cudaFree(oa);
+    cudaFree(oe);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "grids_load_f64");
+  GridDev64 G;
+  G.hard = hard;
+  G.soft = soft;
+  G.nx = d->n[0];
+  G.ny = d->n[1];
+  G.nz = d->n[2];
+  G.ox = d->origin[0];
+  G.oy = d->origin[1];
+  G.oz = d->origin[2];
+  G.h = d->spacing;
+  c->grid64 = G;
+  c->has_grid64 = true;
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_energy_force_f64(algdock_ctx* c, int64_t N, const int32_t* state_of, const float* x,
+                                        double* force, double* comps) {
+  ALGDOCK_TRY(c)
+  if (!c->has_grid64 || !c->has_ligand || (state_of && c->K == 0))
+    return fail(c, ALGDOCK_E_STATE, "energy_force_f64: load FP64 grids, the ligand (and states) first");
+  if (N < 0 || !comps) return fail(c, ALGDOCK_E_INVALID, "energy_force_f64: need N >= 0 and comps");
+  if (N == 0) return ALGDOCK_OK;
+  if (!is_device_ptr(x) || !is_device_ptr(comps) || (state_of && !is_device_ptr(state_of)) ||
+      (force && !is_device_ptr(force)))
+    return fail(c, ALGDOCK_E_INVALID, "energy_force_f64: arrays must be device pointers");
+  Device g(c->device);
+  cudaError_t e = launch_eval64(c->stream, *c, N, state_of, x, force, comps);
+  if (e != cudaSuccess) return cuda_fail(c, e, "energy_force_f64");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
 algdock_status algdock_gather_probe(algdock_ctx* c, int64_t n_cells, int32_t soft, uint64_t seed, float* sink) {
   ALGDOCK_TRY(c)
   if (!c->has_grid) return fail(c, ALGDOCK_E_STATE, "gather_probe: load grids first");
@@ -529,7 +657,9 @@ algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, cons
   LigandLayout Y;
   std::vector<uint32_t> blob;
   std::vector<TargetFactors> fac;
-  algdock_status st = build_ligand(c, L, R, "ligand_load", Y, blob, fac);
+  Lig64 Y64{};
+  std::vector<double> blob64;
+  algdock_status st = build_ligand(c, L, R, "ligand_load", Y, blob, fac, &Y64, &blob64);
   if (st != ALGDOCK_OK) return st;
   const int na = Y.na, nb = Y.nb, w = Y.words_pair;
 
@@ -545,8 +675,14 @@ algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, cons
   if (e == cudaSuccess) e = cudaMemcpy(c->d_blob, blob.data(), (size_t)w * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_lig_fac, sizeof(TargetFactors) * na);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_lig_fac, fac.data(), sizeof(TargetFactors) * na, cudaMemcpyHostToDevice);
+  cudaFree(c->d_lig64);
+  c->d_lig64 = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_lig64, sizeof(double) * blob64.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->d_lig64, blob64.data(), sizeof(double) * blob64.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(c, e, "ligand_load");
   c->lig = Y;
+  c->lig64 = Y64;
   build_learned_topo(na, nb, L->bonds, &c->ltopo);
   c->has_ligand = true;
   return ALGDOCK_OK;

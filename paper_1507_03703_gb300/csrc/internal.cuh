@@ -109,6 +109,31 @@ struct __align__(16) ReceptorPair {
   float4 c0, c1, c2, c3;
 };
 
+// The all-FP64 evaluation path (the precision study's FP64 arm): the ligand's parameters in FP64,
+// as offsets (in doubles) into one device buffer, and FP64 lattices.
+struct Lig64 {
+  int na, nb, nang, ntor;
+  int off_atom;   // [na][6]: mass, q, sqrt(A), sqrt(B), R*, sqrt(eps)
+  int off_bond;   // [nb][4]: i, j (as doubles), k, r0
+  int off_ang;    // [nang][5]: i, j, k, k_theta, theta0
+  int off_tor;    // [ntor][10]: i, j, k, l, V1/2, V2/2, V3/2, gamma1, gamma2, gamma3
+  int off_ptype;  // [na][na] pair types as doubles: 0 nonbonded, 1 1-4, 2 excluded
+  int n_doubles;
+  double total_mass, site[3], k_rest, d0;
+};
+struct __align__(32) Hard64 {
+  double r, a, e, pad;  // LJr^(1/4), LJa, elec
+};
+struct __align__(16) Soft64 {
+  double r, e;  // sLJr^(1/4), selec
+};
+struct GridDev64 {
+  const Hard64* hard;
+  const Soft64* soft;
+  int nx, ny, nz;
+  double ox, oy, oz, h;
+};
+
 // Multi-ligand batches: one record per ligand (its layout and where its blob starts in the batch
 // blob), and one work item per block (a run of up to WPB consecutive replicas of one ligand).
 struct BatchLigand {
@@ -180,6 +205,13 @@ struct algdock_ctx {
   int n_rec = -1;  // -1: no receptor loaded
   algdock::TargetFactors* d_lig_fac = nullptr;
   void* d_fep = nullptr;
+  // all-FP64 evaluation path: FP64 ligand tables (built with the ligand) and FP64 lattices
+  algdock::Lig64 lig64{};
+  double* d_lig64 = nullptr;
+  bool has_grid64 = false;
+  algdock::GridDev64 grid64{};
+  void* d_grid64 = nullptr;
+  size_t grid64_nodes = 0;
   // multi-ligand batch: ligands, their blobs, the replica layout and one launch shape per class
   int n_batch = 0;
   int batch_max_na = 0;
@@ -215,6 +247,11 @@ bool hmc_uses_table(const LigandLayout& L);
 // HMC trial of every replica of the batch (classes on forked streams, joined on s)
 size_t batch_block_smem(const LigandLayout& L, int apl, int wpb, bool table);
 int batch_candidates(int cls, int* wpb, bool* table);
+// all-FP64 path: lattice derivation and the evaluation of N configurations (one thread each)
+cudaError_t launch_grid_prepare64(cudaStream_t s, size_t n_nodes, const double* ljr, const double* lja,
+                                  const double* elec, double vmax_r, double vmax_e, Hard64* hard, Soft64* soft);
+cudaError_t launch_eval64(cudaStream_t s, const algdock_ctx& c, int64_t N, const int32_t* state_of, const float* x,
+                          double* force, double* comps);
 cudaError_t batch_set_attributes(const algdock_ctx& c);
 cudaError_t launch_hmc_batch(cudaStream_t s, const algdock_ctx& c, const int32_t* state_of, float* x, double* comps,
                              double* dH, uint8_t* acc, int n_steps, uint64_t seed, uint64_t cycle, int64_t rep_offset,
