@@ -46,13 +46,54 @@ __device__ inline Lse lse_merge(Lse a, Lse b) {
   return Lse{b.m, b.s + a.s * exp(a.m - b.m)};
 }
 
+// Block merge of (m, s) pairs with FP64 maxima and sums and FP32 rescale factors
+// exp(m - M) (about 1e-7 relative each, as the FP32 exponentials of precision mode 1); the result
+// is valid in thread 0, and every thread of the block must call it.
+__device__ inline Lse block_merge_mixed(double m, double s) {
+  __shared__ double s_m[kPartialThreads / 32], s_s[kPartialThreads / 32];
+  const unsigned full = 0xffffffffu;
+  double wm = m;
+  for (int o = 16; o > 0; o >>= 1) wm = fmax(wm, __shfl_xor_sync(full, wm, o));
+  double t = (m == -INFINITY) ? 0.0 : s * (double)expf((float)(m - wm));
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(full, t, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_m[warp] = wm;
+    s_s[warp] = t;
+  }
+  __syncthreads();
+  Lse r{-INFINITY, 0.0};
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    const double pm = lane < nw ? s_m[lane] : -INFINITY;
+    const double ps = lane < nw ? s_s[lane] : 0.0;
+    double bm = pm;
+    for (int o = 16; o > 0; o >>= 1) bm = fmax(bm, __shfl_xor_sync(full, bm, o));
+    double v = (pm == -INFINITY) ? 0.0 : ps * (double)expf((float)(pm - bm));
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
+    r = Lse{bm, v};
+  }
+  return r;
+}
+
 __global__ void log_denominators(int K, int64_t N, const double* __restrict__ u, const double* __restrict__ logNk,
                                  const double* __restrict__ f, double* logD, const MbarState* st, int mode) {
   if (st->converged) return;
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   Lse a{-INFINITY, 0.0};
-  for (int k = 0; k < K; ++k) lse_add(a, logNk[k] + f[k] - u[(int64_t)k * N + n], mode);
+  // eight independent loads in flight, then the updates in the same order as one at a time
+  constexpr int kAhead = 8;
+  const double* col = u + n;
+  int k = 0;
+  for (; k + kAhead <= K; k += kAhead) {
+    double v[kAhead];
+#pragma unroll
+    for (int j = 0; j < kAhead; ++j) v[j] = __ldg(col + (int64_t)(k + j) * N);
+#pragma unroll
+    for (int j = 0; j < kAhead; ++j) lse_add(a, logNk[k + j] + f[k + j] - v[j], mode);
+  }
+  for (; k < K; ++k) lse_add(a, logNk[k] + f[k] - __ldg(col + (int64_t)k * N), mode);
   logD[n] = a.m + log(a.s);
 }
 
@@ -65,7 +106,25 @@ __global__ void __launch_bounds__(kPartialThreads) state_partials(int64_t N, con
   const int64_t end = min(N, begin + kChunk);
   Lse a{-INFINITY, 0.0};
   const double* ui = u + (int64_t)i * N;
-  for (int64_t n = begin + threadIdx.x; n < end; n += blockDim.x) lse_add(a, -ui[n] - logD[n], mode);
+  constexpr int kAhead = 8;
+  const int64_t stride = blockDim.x;
+  int64_t n = begin + threadIdx.x;
+  for (; n + (kAhead - 1) * stride < end; n += kAhead * stride) {
+    double v[kAhead], d[kAhead];
+#pragma unroll
+    for (int j = 0; j < kAhead; ++j) {
+      v[j] = __ldg(ui + n + j * stride);
+      d[j] = __ldg(logD + n + j * stride);
+    }
+#pragma unroll
+    for (int j = 0; j < kAhead; ++j) lse_add(a, -v[j] - d[j], mode);
+  }
+  for (; n < end; n += stride) lse_add(a, -ui[n] - logD[n], mode);
+  if (mode == 1) {  // FP32 exponentials: the block merge takes FP32 factors as well
+    const Lse r = block_merge_mixed(a.m, a.s);
+    if (threadIdx.x == 0) part[(int64_t)i * n_chunks + chunk] = make_double2(r.m, r.s);
+    return;
+  }
   __shared__ double sm[kPartialThreads], ss[kPartialThreads];
   sm[threadIdx.x] = a.m;
   ss[threadIdx.x] = a.s;
@@ -81,16 +140,28 @@ __global__ void __launch_bounds__(kPartialThreads) state_partials(int64_t N, con
   if (threadIdx.x == 0) part[(int64_t)i * n_chunks + chunk] = make_double2(sm[0], ss[0]);
 }
 
+// F32_FACTORS (precision mode 2, whose partial maxima are floats): the chunks' pairs are merged
+// as in block_merge_f32, the exact maximum and FP32 rescale factors with an FP64 sum, instead of
+// FP64 exponentials.
+template <bool F32_FACTORS>
 __global__ void finalize(int K, int n_chunks, const double2* __restrict__ part, double* f, double* fnew,
                          MbarState* st, double tol, int max_iter) {
   if (st->converged) return;
   __shared__ double s_delta[256];
   // new free energies, one state per thread (strided)
   for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    const double2* pi = part + (int64_t)i * n_chunks;
     Lse a{-INFINITY, 0.0};
-    for (int c = 0; c < n_chunks; ++c) {
-      const double2 p = part[(int64_t)i * n_chunks + c];
-      a = lse_merge(a, Lse{p.x, p.y});
+    if (F32_FACTORS) {
+      float M = -INFINITY;
+      for (int c = 0; c < n_chunks; ++c) M = fmaxf(M, (float)pi[c].x);
+      double S = 0.0;
+      if (M != -INFINITY)
+        for (int c = 0; c < n_chunks; ++c)
+          if (pi[c].x != -INFINITY) S += pi[c].y * (double)expf((float)pi[c].x - M);
+      a = Lse{M == -INFINITY ? -INFINITY : (double)M, S};
+    } else {
+      for (int c = 0; c < n_chunks; ++c) a = lse_merge(a, Lse{pi[c].x, pi[c].y});
     }
     fnew[i] = -(a.m + log(a.s));
   }
@@ -154,6 +225,38 @@ __device__ inline void lsef_add(LseF& a, float x) {
   }
 }
 
+// One (max, sum) pair from every thread's (m, s): the exact maximum M (a float), then
+// sum_t s_t exp(m_t - M) with the factor in FP32 (about 1e-7 relative, independent between
+// threads) and the sum in FP64, over the warp by shuffles and over the warps in shared memory.
+// The result is valid in thread 0; every thread of the block must call it.
+__device__ inline Lse block_merge_f32(float m, double s) {
+  __shared__ float s_m[kPartialThreads / 32];
+  __shared__ double s_s[kPartialThreads / 32];
+  const unsigned full = 0xffffffffu;
+  float wm = m;
+  for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(full, wm, o));
+  double t = (m == -INFINITY) ? 0.0 : s * (double)expf(m - wm);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(full, t, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_m[warp] = wm;
+    s_s[warp] = t;
+  }
+  __syncthreads();
+  Lse r{-INFINITY, 0.0};
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    const float pm = lane < nw ? s_m[lane] : -INFINITY;
+    const double ps = lane < nw ? s_s[lane] : 0.0;
+    float bm = pm;
+    for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(full, bm, o));
+    double u = (pm == -INFINITY) ? 0.0 : ps * (double)expf(pm - bm);
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(full, u, o);
+    r = Lse{bm == -INFINITY ? -INFINITY : (double)bm, u};
+  }
+  return r;
+}
+
 __global__ void log_denominators_f32(int K, int64_t N, const float* __restrict__ w, const double* __restrict__ logNk,
                                      const double* __restrict__ f, float* logD, const MbarState* st) {
   if (st->converged) return;
@@ -163,7 +266,19 @@ __global__ void log_denominators_f32(int K, int64_t N, const float* __restrict__
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   LseF a{-INFINITY, 0.f, 0.f};
-  for (int k = 0; k < K; ++k) lsef_add(a, g_k[k] - w[(int64_t)k * N + n]);
+  // eight independent loads in flight before the dependent log-sum-exp updates (each thread walks
+  // its column; a warp's loads of one state are one coalesced row segment)
+  constexpr int kAhead = 8;
+  const float* col = w + n;
+  int k = 0;
+  for (; k + kAhead <= K; k += kAhead) {
+    float v[kAhead];
+#pragma unroll
+    for (int j = 0; j < kAhead; ++j) v[j] = __ldg(col + (int64_t)(k + j) * N);
+#pragma unroll
+    for (int j = 0; j < kAhead; ++j) lsef_add(a, g_k[k + j] - v[j]);
+  }
+  for (; k < K; ++k) lsef_add(a, g_k[k] - __ldg(col + (int64_t)k * N));
   logD[n] = a.m + logf(a.s - a.c);
 }
 
@@ -176,20 +291,26 @@ __global__ void __launch_bounds__(kPartialThreads) state_partials_f32(int64_t N,
   const int64_t end = min(N, begin + kChunk);
   LseF a{-INFINITY, 0.f, 0.f};
   const float* wi = w + (int64_t)i * N;
-  for (int64_t n = begin + threadIdx.x; n < end; n += blockDim.x) lsef_add(a, -wi[n] - logD[n]);
-  __shared__ double sm[kPartialThreads], ss[kPartialThreads];
-  sm[threadIdx.x] = a.m == -INFINITY ? -INFINITY : (double)a.m;
-  ss[threadIdx.x] = (double)a.s - (double)a.c;
-  __syncthreads();
-  for (int v = blockDim.x / 2; v > 0; v >>= 1) {
-    if (threadIdx.x < v) {
-      const Lse r = lse_merge(Lse{sm[threadIdx.x], ss[threadIdx.x]}, Lse{sm[threadIdx.x + v], ss[threadIdx.x + v]});
-      sm[threadIdx.x] = r.m;
-      ss[threadIdx.x] = r.s;
+  // eight independent pairs of loads in flight per thread, then the dependent updates
+  constexpr int kAhead = 8;
+  const int64_t stride = blockDim.x;
+  int64_t n = begin + threadIdx.x;
+  for (; n + (kAhead - 1) * stride < end; n += kAhead * stride) {
+    float v[kAhead], d[kAhead];
+#pragma unroll
+    for (int j = 0; j < kAhead; ++j) {
+      v[j] = __ldg(wi + n + j * stride);
+      d[j] = __ldg(logD + n + j * stride);
     }
-    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kAhead; ++j) lsef_add(a, -v[j] - d[j]);
   }
-  if (threadIdx.x == 0) part[(int64_t)i * n_chunks + chunk] = make_double2(sm[0], ss[0]);
+  for (; n < end; n += stride) lsef_add(a, -wi[n] - logD[n]);
+  // block merge without FP64 exponentials (slow on this GPU): the exact maximum of the partials'
+  // maxima, each partial rescaled by an FP32 exp of its (non-positive) offset, the rescaled sums
+  // added in FP64; first within each warp, then over the warps
+  const Lse r = block_merge_f32(a.m, (double)a.s - (double)a.c);
+  if (threadIdx.x == 0) part[(int64_t)i * n_chunks + chunk] = make_double2(r.m, r.s);
 }
 
 __global__ void init_state(int K, const int64_t* Nk, double* logNk, double* f, MbarState* st) {
@@ -256,7 +377,10 @@ int mbar_run(cudaStream_t s, void* scratch, int K, int64_t N, const double* u_kn
         log_denominators<<<blocks_n, threads, 0, s>>>(K, N, u_kn, logNk, f, logD, st, mode);
         state_partials<<<grid_p, kPartialThreads, 0, s>>>(N, u_kn, logD, part, (int)n_chunks, st, mode);
       }
-      finalize<<<1, 256, 0, s>>>(K, (int)n_chunks, part, f, fnew, st, tol, max_iter);
+      if (mode == 2)
+        finalize<true><<<1, 256, 0, s>>>(K, (int)n_chunks, part, f, fnew, st, tol, max_iter);
+      else
+        finalize<false><<<1, 256, 0, s>>>(K, (int)n_chunks, part, f, fnew, st, tol, max_iter);
     }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_flag, &st->converged, sizeof(int), cudaMemcpyDeviceToHost, s);
