@@ -148,6 +148,47 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def mbar_hbm_roofline(ctx, dev, K=256, n_per=3907, short=10, long=40):
+    """MBAR precision mode 2 against HBM at the precision study's size (K = 256 harmonic wells in
+    2-D, about 1e6 exact samples built on the device, u_kn of 2 GB in FP64, 1 GB as the shifted
+    FP32 copy): each iteration reads the FP32 u_kn twice (2 K N 4 bytes) and writes and reads the
+    log denominators (2 N 4 bytes).  Seconds per iteration from two solves of fixed lengths, timed
+    with CUDA events on the context's stream (the difference cancels the shift and the setup)."""
+    import torch
+    g = torch.Generator(device=dev).manual_seed(31)
+    bk = torch.rand(K, device=dev, dtype=torch.float64, generator=g) * 3.5 + 0.5
+    mu = torch.rand((K, 2), device=dev, dtype=torch.float64, generator=g) * 0.6 - 0.3
+    x = (mu[:, None, :] + torch.randn((K, n_per, 2), device=dev, dtype=torch.float64, generator=g)
+         / torch.sqrt(bk)[:, None, None]).reshape(-1, 2)
+    N = x.shape[0]
+    u = torch.empty((K, N), device=dev, dtype=torch.float64)
+    for k in range(K):
+        u[k] = 0.5 * bk[k] * ((x - mu[k]) ** 2).sum(-1)
+    N_k = np.full(K, n_per, dtype=np.int64)
+    ctx.mbar(u, N_k, tol=1e-300, max_iter=2, precision_mode=2, raise_on_nonconvergence=False)
+    times = {}
+    stream = torch.cuda.current_stream(dev)
+    for m in (short, long):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.mbar(u, N_k, tol=1e-300, max_iter=m, precision_mode=2, raise_on_nonconvergence=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[m] = e0.elapsed_time(e1) * 1e-3
+    per_it = (times[long] - times[short]) / (long - short)
+    bytes_it = 2.0 * K * N * 4 + 2.0 * N * 4
+    peak = measured_peaks().get("hbm_gbs")
+    achieved = bytes_it / per_it / 1e9
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak if peak else None, "kernel": "MBAR iteration, precision mode 2",
+           "workload": "K = %d, N = %d" % (K, N), "ms_per_iteration": per_it * 1e3,
+           "bytes_per_iteration": bytes_it, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)"}
+    del u, x
+    torch.cuda.empty_cache()
+    return out
+
+
 def gather_bytes_per_launch(alpha, R_per_state, n_atoms, n_steps):
     """Useful lattice bytes of one HMC launch: every atom of every replica gathers the 8 corners of
     the hard lattice (16 B each) where the state's FP32 weight alpha_g is nonzero and of the soft
@@ -881,6 +922,7 @@ def main():
         f, it = ctx.mbar(u, N_k, tol=1e-10, max_iter=20000)
         extra["mbar_K"], extra["mbar_N"], extra["mbar_iters_to_1e-10"] = len(T), N, it
         del u, comps_hist
+        extra["mbar_roofline"] = mbar_hbm_roofline(ctx, dev)
     if not args.no_fep and rank == 0:
         extra["fep_endpoint"] = fep_endpoint(ctx, run, sys_, stream, sm_max)
     if not args.no_batch and rank == 0 and world == 1:
