@@ -148,7 +148,29 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def mbar_hbm_roofline(ctx, dev, K=256, n_per=3907, short=10, long=40):
+def mbar_seconds_per_iteration(ctx, u, N_k, mode, stream, short=4, long=14):
+    """Seconds per MBAR iteration: two solves stopped after short and long iterations (tolerance
+    zero, so neither stops on its own unless the iterates stop changing), timed with CUDA events,
+    the time difference over the difference of the iterations each solve reports.  The
+    difference cancels the per-solve setup (the shift of mode 2, the first launches)."""
+    import torch
+    ctx.mbar(u, N_k, tol=1e-300, max_iter=2, precision_mode=mode, raise_on_nonconvergence=False)
+    t, it = {}, {}
+    for m in (short, long):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, n_it = ctx.mbar(u, N_k, tol=1e-300, max_iter=m, precision_mode=mode, raise_on_nonconvergence=False)
+        it[m] = m if n_it < 0 else n_it  # -1: stopped at max_iter, not converged
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t[m] = e0.elapsed_time(e1) * 1e-3
+    if it[long] <= it[short]:
+        raise RuntimeError("MBAR stopped before %d iterations; cannot time an iteration" % long)
+    return (t[long] - t[short]) / (it[long] - it[short])
+
+
+def mbar_hbm_roofline(ctx, dev, K=256, n_per=3907, short=4, long=14):
     """MBAR precision mode 2 against HBM at the precision study's size (K = 256 harmonic wells in
     2-D, about 1e6 exact samples built on the device, u_kn of 2 GB in FP64, 1 GB as the shifted
     FP32 copy): each iteration reads the FP32 u_kn twice (2 K N 4 bytes) and writes and reads the
@@ -165,18 +187,7 @@ def mbar_hbm_roofline(ctx, dev, K=256, n_per=3907, short=10, long=40):
     for k in range(K):
         u[k] = 0.5 * bk[k] * ((x - mu[k]) ** 2).sum(-1)
     N_k = np.full(K, n_per, dtype=np.int64)
-    ctx.mbar(u, N_k, tol=1e-300, max_iter=2, precision_mode=2, raise_on_nonconvergence=False)
-    times = {}
-    stream = torch.cuda.current_stream(dev)
-    for m in (short, long):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        ctx.mbar(u, N_k, tol=1e-300, max_iter=m, precision_mode=2, raise_on_nonconvergence=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times[m] = e0.elapsed_time(e1) * 1e-3
-    per_it = (times[long] - times[short]) / (long - short)
+    per_it = mbar_seconds_per_iteration(ctx, u, N_k, 2, torch.cuda.current_stream(dev), short, long)
     bytes_it = 2.0 * K * N * 4 + 2.0 * N * 4
     peak = measured_peaks().get("hbm_gbs")
     achieved = bytes_it / per_it / 1e9
@@ -913,12 +924,7 @@ def main():
         ctx.reduced_energies(N, comps=comps_hist.reshape(N, 4), k_begin=0, k_count=len(T), u_kn=u)
         N_k = np.full(len(T), N // len(T), dtype=np.int64)
         for mode, key in ((0, "fp64"), (1, "fp32exp"), (2, "fp32")):
-            ctx.mbar(u, N_k, tol=1e-300, max_iter=2, precision_mode=mode, raise_on_nonconvergence=False)
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            ctx.mbar(u, N_k, tol=1e-300, max_iter=50, precision_mode=mode, raise_on_nonconvergence=False)
-            el = time.perf_counter() - t
-            extra["mbar_%s_iters_per_s" % key] = 50 / el
+            extra["mbar_%s_iters_per_s" % key] = 1.0 / mbar_seconds_per_iteration(ctx, u, N_k, mode, stream)
         f, it = ctx.mbar(u, N_k, tol=1e-10, max_iter=20000)
         extra["mbar_K"], extra["mbar_N"], extra["mbar_iters_to_1e-10"] = len(T), N, it
         del u, comps_hist
