@@ -460,7 +460,7 @@ algdock_status algdock_propose_learned(algdock_ctx* ctx, const float* params, co
  * loads the library holds it until the process exits); the call itself allocates nothing and
  * does not use the context's own MBAR scratch.
  *  - Sizes whose scratch exceeds 8 MiB (about 8 bytes per sample plus 16 bytes per state and
- *    8192-sample chunk, e.g. N up to ~1e6 samples for K = 128) are rejected with
+ *    chunk of 8192-32768 samples, e.g. N up to ~1e6 samples for K = 128) are rejected with
  *    ALGDOCK_E_INVALID and a message naming the bytes needed.
  *  - The first call on a device looks up the array's device address (once per device, with that
  *    device current); make that first call before any stream capture.

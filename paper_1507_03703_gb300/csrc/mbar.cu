@@ -1,10 +1,11 @@
 // MBAR (Shirts & Chodera 2008; "Estimation") by self-consistent iteration in log-sum-exp form.
 //
-// One iteration is three kernels on the stream:
+// One iteration is four kernels on the stream:
 //   1. log_denominators: for every sample n, log D_n = ln sum_k N_k exp(f_k - u_kn)   (one thread per n)
 //   2. state_partials:   for every state i and a chunk of samples, the (max, sum) pair of
 //                        exp(-u_in - log D_n)                                       (block per (chunk, i))
-//   3. finalize:         f_i <- -ln sum_n ..., gauge f_0 = 0, convergence flag       (one block)
+//   3. merge_chunks:     f_i <- -ln sum_n ..., the chunks' pairs of each state merged (one warp per state)
+//   4. finalize:         gauge f_0 = 0, convergence flag                             (one block)
 // Every kernel returns at once when the device flag says the iteration has converged, so the host
 // can enqueue iterations in batches and poll the flag between batches.
 #include <math.h>
@@ -18,7 +19,14 @@ namespace algdock {
 namespace {
 
 constexpr int kPartialThreads = 256;
-constexpr int kChunk = 8192;  // samples per state_partials block
+// Samples per state_partials block: the largest power of two in [8192, 32768] that still gives a
+// full wave of blocks (K x chunks >= 152 SMs x 8 resident blocks), so that large solves spread
+// each block's merge over more loads and small ones keep every SM busy.
+inline int64_t mbar_chunk(int K, int64_t N) {
+  int64_t c = 32768;
+  while (c > 8192 && (int64_t)K * ((N + c - 1) / c) < 152 * 8) c >>= 1;
+  return c;
+}
 
 struct MbarState {
   int converged;
@@ -46,36 +54,6 @@ __device__ inline Lse lse_merge(Lse a, Lse b) {
   return Lse{b.m, b.s + a.s * exp(a.m - b.m)};
 }
 
-// Block merge of (m, s) pairs with FP64 maxima and sums and FP32 rescale factors
-// exp(m - M) (about 1e-7 relative each, as the FP32 exponentials of precision mode 1); the result
-// is valid in thread 0, and every thread of the block must call it.
-__device__ inline Lse block_merge_mixed(double m, double s) {
-  __shared__ double s_m[kPartialThreads / 32], s_s[kPartialThreads / 32];
-  const unsigned full = 0xffffffffu;
-  double wm = m;
-  for (int o = 16; o > 0; o >>= 1) wm = fmax(wm, __shfl_xor_sync(full, wm, o));
-  double t = (m == -INFINITY) ? 0.0 : s * (double)expf((float)(m - wm));
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(full, t, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    s_m[warp] = wm;
-    s_s[warp] = t;
-  }
-  __syncthreads();
-  Lse r{-INFINITY, 0.0};
-  if (warp == 0) {
-    const int nw = blockDim.x >> 5;
-    const double pm = lane < nw ? s_m[lane] : -INFINITY;
-    const double ps = lane < nw ? s_s[lane] : 0.0;
-    double bm = pm;
-    for (int o = 16; o > 0; o >>= 1) bm = fmax(bm, __shfl_xor_sync(full, bm, o));
-    double v = (pm == -INFINITY) ? 0.0 : ps * (double)expf((float)(pm - bm));
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
-    r = Lse{bm, v};
-  }
-  return r;
-}
-
 __global__ void log_denominators(int K, int64_t N, const double* __restrict__ u, const double* __restrict__ logNk,
                                  const double* __restrict__ f, double* logD, const MbarState* st, int mode) {
   if (st->converged) return;
@@ -97,13 +75,14 @@ __global__ void log_denominators(int K, int64_t N, const double* __restrict__ u,
   logD[n] = a.m + log(a.s);
 }
 
-__global__ void __launch_bounds__(kPartialThreads) state_partials(int64_t N, const double* __restrict__ u,
+__global__ void __launch_bounds__(kPartialThreads) state_partials(int64_t N, int64_t chunk_len,
+                                                                  const double* __restrict__ u,
                                                                   const double* __restrict__ logD, double2* part,
                                                                   int n_chunks, const MbarState* st, int mode) {
   if (st->converged) return;
   const int i = blockIdx.y, chunk = blockIdx.x;
-  const int64_t begin = (int64_t)chunk * kChunk;
-  const int64_t end = min(N, begin + kChunk);
+  const int64_t begin = (int64_t)chunk * chunk_len;
+  const int64_t end = min(N, begin + chunk_len);
   Lse a{-INFINITY, 0.0};
   const double* ui = u + (int64_t)i * N;
   constexpr int kAhead = 8;
@@ -120,11 +99,6 @@ __global__ void __launch_bounds__(kPartialThreads) state_partials(int64_t N, con
     for (int j = 0; j < kAhead; ++j) lse_add(a, -v[j] - d[j], mode);
   }
   for (; n < end; n += stride) lse_add(a, -ui[n] - logD[n], mode);
-  if (mode == 1) {  // FP32 exponentials: the block merge takes FP32 factors as well
-    const Lse r = block_merge_mixed(a.m, a.s);
-    if (threadIdx.x == 0) part[(int64_t)i * n_chunks + chunk] = make_double2(r.m, r.s);
-    return;
-  }
   __shared__ double sm[kPartialThreads], ss[kPartialThreads];
   sm[threadIdx.x] = a.m;
   ss[threadIdx.x] = a.s;
@@ -140,31 +114,10 @@ __global__ void __launch_bounds__(kPartialThreads) state_partials(int64_t N, con
   if (threadIdx.x == 0) part[(int64_t)i * n_chunks + chunk] = make_double2(sm[0], ss[0]);
 }
 
-// F32_FACTORS (precision mode 2, whose partial maxima are floats): the chunks' pairs are merged
-// as in block_merge_f32, the exact maximum and FP32 rescale factors with an FP64 sum, instead of
-// FP64 exponentials.
-template <bool F32_FACTORS>
-__global__ void finalize(int K, int n_chunks, const double2* __restrict__ part, double* f, double* fnew,
-                         MbarState* st, double tol, int max_iter) {
+// The gauge f_0 = 0 and the convergence test on f^new (formed by merge_chunks).
+__global__ void finalize(int K, double* f, double* fnew, MbarState* st, double tol, int max_iter) {
   if (st->converged) return;
   __shared__ double s_delta[256];
-  // new free energies, one state per thread (strided)
-  for (int i = threadIdx.x; i < K; i += blockDim.x) {
-    const double2* pi = part + (int64_t)i * n_chunks;
-    Lse a{-INFINITY, 0.0};
-    if (F32_FACTORS) {
-      float M = -INFINITY;
-      for (int c = 0; c < n_chunks; ++c) M = fmaxf(M, (float)pi[c].x);
-      double S = 0.0;
-      if (M != -INFINITY)
-        for (int c = 0; c < n_chunks; ++c)
-          if (pi[c].x != -INFINITY) S += pi[c].y * (double)expf((float)pi[c].x - M);
-      a = Lse{M == -INFINITY ? -INFINITY : (double)M, S};
-    } else {
-      for (int c = 0; c < n_chunks; ++c) a = lse_merge(a, Lse{pi[c].x, pi[c].y});
-    }
-    fnew[i] = -(a.m + log(a.s));
-  }
   __syncthreads();
   const double f0 = fnew[0];
   double dmax = 0.0;
@@ -282,13 +235,14 @@ __global__ void log_denominators_f32(int K, int64_t N, const float* __restrict__
   logD[n] = a.m + logf(a.s - a.c);
 }
 
-__global__ void __launch_bounds__(kPartialThreads) state_partials_f32(int64_t N, const float* __restrict__ w,
+__global__ void __launch_bounds__(kPartialThreads) state_partials_f32(int64_t N, int64_t chunk_len,
+                                                                      const float* __restrict__ w,
                                                                       const float* __restrict__ logD, double2* part,
                                                                       int n_chunks, const MbarState* st) {
   if (st->converged) return;
   const int i = blockIdx.y, chunk = blockIdx.x;
-  const int64_t begin = (int64_t)chunk * kChunk;
-  const int64_t end = min(N, begin + kChunk);
+  const int64_t begin = (int64_t)chunk * chunk_len;
+  const int64_t end = min(N, begin + chunk_len);
   LseF a{-INFINITY, 0.f, 0.f};
   const float* wi = w + (int64_t)i * N;
   // eight independent pairs of loads in flight per thread, then the dependent updates
@@ -313,6 +267,40 @@ __global__ void __launch_bounds__(kPartialThreads) state_partials_f32(int64_t N,
   if (threadIdx.x == 0) part[(int64_t)i * n_chunks + chunk] = make_double2(r.m, r.s);
 }
 
+// Each state's chunk pairs merged by one warp into f_i^new = -(M + ln S): lanes take every 32nd
+// chunk, then a butterfly over the lanes.  F32 (precision mode 2, whose maxima are floats): the
+// exact maximum, FP32 rescale factors and an FP64 sum.  Otherwise FP64 log-sum-exp merges (the
+// merge is symmetric in its operands, so every lane ends with the same bits).  finalize then
+// applies the gauge and the convergence test.
+template <bool F32>
+__global__ void merge_chunks(int K, int n_chunks, const double2* __restrict__ part, double* fnew,
+                             const MbarState* st) {
+  if (st->converged) return;
+  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (i >= K) return;
+  const unsigned full = 0xffffffffu;
+  const double2* pi = part + (int64_t)i * n_chunks;
+  if (F32) {
+    float M = -INFINITY;
+    for (int c = lane; c < n_chunks; c += 32) M = fmaxf(M, (float)pi[c].x);
+    for (int o = 16; o > 0; o >>= 1) M = fmaxf(M, __shfl_xor_sync(full, M, o));
+    double S = 0.0;
+    if (M != -INFINITY)
+      for (int c = lane; c < n_chunks; c += 32)
+        if (pi[c].x != -INFINITY) S += pi[c].y * (double)expf((float)pi[c].x - M);
+    for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(full, S, o);
+    if (lane == 0) fnew[i] = M == -INFINITY ? INFINITY : -((double)M + log(S));
+  } else {
+    Lse a{-INFINITY, 0.0};
+    for (int c = lane; c < n_chunks; c += 32) a = lse_merge(a, Lse{pi[c].x, pi[c].y});
+    for (int o = 16; o > 0; o >>= 1) {
+      const Lse b{__shfl_xor_sync(full, a.m, o), __shfl_xor_sync(full, a.s, o)};
+      a = lse_merge(a, b);
+    }
+    if (lane == 0) fnew[i] = -(a.m + log(a.s));
+  }
+}
+
 __global__ void init_state(int K, const int64_t* Nk, double* logNk, double* f, MbarState* st) {
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     logNk[k] = Nk[k] > 0 ? log((double)Nk[k]) : -INFINITY;
@@ -329,7 +317,8 @@ __global__ void init_state(int K, const int64_t* Nk, double* logNk, double* f, M
 // Scratch layout (bytes): MbarState | logNk[K] | f[K] | fnew[K] | Nk[K] (int64) | part[K][n_chunks] | logD[N]
 // (double; float in mode 2), then in mode 2 the shifted FP32 copy w[K][N] (256-byte aligned).
 size_t mbar_scratch_bytes(int K, int64_t N) {
-  const int64_t n_chunks = (N + kChunk - 1) / kChunk;
+  const int64_t chunk_len = mbar_chunk(K, N);
+  const int64_t n_chunks = (N + chunk_len - 1) / chunk_len;
   return 64 + 4 * (size_t)K * 8 + (size_t)K * n_chunks * 16 + (size_t)N * 8 + 256;
 }
 size_t mbar_scratch_bytes_mode(int K, int64_t N, int mode) {
@@ -341,7 +330,8 @@ size_t mbar_scratch_bytes_mode(int K, int64_t N, int mode) {
 // -1 on a CUDA error (then *err is set).
 int mbar_run(cudaStream_t s, void* scratch, int K, int64_t N, const double* u_kn, const int64_t* Nk_host,
              double tol, int max_iter, int mode, double* f_host, int* iters, int* h_flag, cudaError_t* err) {
-  const int64_t n_chunks = (N + kChunk - 1) / kChunk;
+  const int64_t chunk_len = mbar_chunk(K, N);
+  const int64_t n_chunks = (N + chunk_len - 1) / chunk_len;
   char* p = (char*)scratch;
   MbarState* st = (MbarState*)p;
   double* logNk = (double*)(p + 64);
@@ -372,15 +362,18 @@ int mbar_run(cudaStream_t s, void* scratch, int K, int64_t N, const double* u_kn
     for (int b = 0; b < batch && issued < max_iter; ++b, ++issued) {
       if (mode == 2) {
         log_denominators_f32<<<blocks_n, threads, K * sizeof(float), s>>>(K, N, w32, logNk, f, (float*)logD, st);
-        state_partials_f32<<<grid_p, kPartialThreads, 0, s>>>(N, w32, (const float*)logD, part, (int)n_chunks, st);
+        state_partials_f32<<<grid_p, kPartialThreads, 0, s>>>(N, chunk_len, w32, (const float*)logD, part,
+                                                              (int)n_chunks, st);
       } else {
         log_denominators<<<blocks_n, threads, 0, s>>>(K, N, u_kn, logNk, f, logD, st, mode);
-        state_partials<<<grid_p, kPartialThreads, 0, s>>>(N, u_kn, logD, part, (int)n_chunks, st, mode);
+        state_partials<<<grid_p, kPartialThreads, 0, s>>>(N, chunk_len, u_kn, logD, part, (int)n_chunks, st, mode);
       }
+      const unsigned merge_blocks = (unsigned)((K * 32 + 255) / 256);
       if (mode == 2)
-        finalize<true><<<1, 256, 0, s>>>(K, (int)n_chunks, part, f, fnew, st, tol, max_iter);
+        merge_chunks<true><<<merge_blocks, 256, 0, s>>>(K, (int)n_chunks, part, fnew, st);
       else
-        finalize<false><<<1, 256, 0, s>>>(K, (int)n_chunks, part, f, fnew, st, tol, max_iter);
+        merge_chunks<false><<<merge_blocks, 256, 0, s>>>(K, (int)n_chunks, part, fnew, st);
+      finalize<<<1, 256, 0, s>>>(K, f, fnew, st, tol, max_iter);
     }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_flag, &st->converged, sizeof(int), cudaMemcpyDeviceToHost, s);
