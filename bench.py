@@ -596,19 +596,11 @@ def batching(dev, stream, steps=10, warmup=3, seed=3):
     run.x.copy_(x_real)
     ctx.batch_layout(lig_of, stride)
     ctx.batch_tune(run.state_of, run.x, n_steps=N_VV, n_timed=5)
-    # the whole cycle, eager and as one graph
+    # the whole cycle, eager and as one graph, timed in alternation (three rounds of 10 cycles
+    # each) so that both arms run on the same evolving configurations
     for w in range(warmup):
         run.hmc(300 + w, N_VV)
         run.exchange(300 + w)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for s_ in range(steps):
-        run.hmc(400 + s_, N_VV)
-        run.exchange(400 + s_)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    eager_ms = e0.elapsed_time(e1) / steps
     g = torch.cuda.CUDAGraph()
     cap = torch.cuda.Stream(device=dev)
     cap.wait_stream(stream)
@@ -624,12 +616,23 @@ def batching(dev, stream, steps=10, warmup=3, seed=3):
     for w in range(warmup):
         g.replay()
     torch.cuda.synchronize()
-    e0.record(stream)
-    for s_ in range(steps):
-        g.replay()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    graph_ms = e0.elapsed_time(e1) / steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eager, graph = [], []
+    for rnd in range(3):
+        e0.record(stream)
+        for s_ in range(steps):
+            run.hmc(400 + 100 * rnd + s_, N_VV)
+            run.exchange(400 + 100 * rnd + s_)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        eager.append(e0.elapsed_time(e1) / steps)
+        e0.record(stream)
+        for s_ in range(steps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        graph.append(e0.elapsed_time(e1) / steps)
+    eager_ms, graph_ms = float(np.median(eager)), float(np.median(graph))
     out["cycle_eager_ms"] = eager_ms
     out["cycle_graph_ms"] = graph_ms
     out["cycle_graph_evals_per_s"] = evals / (graph_ms * 1e-3)
