@@ -6,6 +6,12 @@
  * Paper: D. D. L. Minh, "Alchemical Grid Dock (AlGDock): Binding Free Energy Calculations between
  * Flexible Ligands and Rigid Receptors", arXiv:1507.03703.
  *
+ * Call groups, in the order below: lifecycle; grids; the all-FP64 evaluation path and the gather
+ * probe; ligand and states; sampling (HMC trial, external-coordinate moves, forces and energies,
+ * replica exchange); estimation (u_kn, MBAR, equilibration detection); protocol initialization;
+ * multi-ligand batches; the end points (target force field and free energy perturbation); the
+ * learned pose proposal; the allocation-free MBAR.
+ *
  * Conventions for every call:
  *  - Units: A, kcal/mol, amu, fs, K, elementary charge.
  *  - Every call returns algdock_status (ALGDOCK_OK = 0).  No C++ exception crosses the ABI.
