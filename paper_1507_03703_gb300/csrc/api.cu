@@ -223,7 +223,7 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
   Y.off_inc = take(ninc);
   Y.words = w;
   if ((size_t)w * 4 > 120 * 1024) return fail(c, ALGDOCK_E_INVALID, who + ": topology too large");
-  Y.off_pair = take(2 * na * na);
+  Y.off_pair = take(4 * ((na + 1) / 2) * na);
   Y.words_pair = w;
   blob.assign(w, 0u);
   float* bf = (float*)blob.data();
@@ -261,17 +261,20 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
       bf[Y.off_tor + 12 * ntor + 4 * t + n] = (float)sin(g);
     }
   }
-  // pair table: the 1-4 scales and the exclusions folded into one 8-byte record per ordered pair,
+  // pair table: the 1-4 scales and the exclusions folded into 8 bytes per ordered pair,
   // (12 eps_ij s_lj, 332 q_i q_j s_el) from FP64, rounded once; excluded pairs (and i == j) hold
-  // zeros.  R_ij = R*_i + R*_j is formed in the kernel from the per-atom radii.
-  for (int j = 0; j < na; ++j)
+  // zeros.  R_ij = R*_i + R*_j is formed in the kernel from the per-atom radii.  Partners are
+  // taken two at a time (j = 2p, 2p + 1; an odd na ends with a zero partner j = na), and the two
+  // records of atom i share one 16-byte entry (e_ij, e_ij', c_ij, c_ij'), so that one load feeds
+  // paired FP32 instructions.
+  for (int j = 0; j < 2 * ((na + 1) / 2); ++j)
     for (int i = 0; i < na; ++i) {
-      const int ty = ptype[(size_t)j * na + i];
+      const int ty = j < na ? ptype[(size_t)j * na + i] : 2;
       const double s_lj = ty == 0 ? 1.0 : (ty == 1 ? 0.5 : 0.0);
       const double s_el = ty == 0 ? 1.0 : (ty == 1 ? 1.0 / 1.2 : 0.0);
-      float* rec = bf + Y.off_pair + 2 * ((size_t)j * na + i);
-      rec[0] = (float)(12.0 * s_lj * sqrt(L->eps[i]) * sqrt(L->eps[j]));
-      rec[1] = (float)(kCoulomb * L->charge[i] * L->charge[j] * s_el);
+      float* rec = bf + Y.off_pair + 4 * ((size_t)(j >> 1) * na + i) + (j & 1);
+      rec[0] = ty == 2 ? 0.f : (float)(12.0 * s_lj * sqrt(L->eps[i]) * sqrt(L->eps[j]));
+      rec[2] = ty == 2 ? 0.f : (float)(kCoulomb * L->charge[i] * L->charge[j] * s_el);
     }
   int pos = 0;
   for (int i = 0; i < na; ++i) {
@@ -1028,10 +1031,11 @@ algdock_status algdock_batch_layout(algdock_ctx* c, int64_t n_rep, const int32_t
     const int nc = c->batch_uniform && k < kBatchClasses - 1 ? 0 : batch_candidates(k, wpb, table);
     int pick = -1;
     for (int t = 0; t < nc && pick < 0; ++t)
-      if (batch_class_smem(c, k, wpb[t], table[t]) <= 227 * 1024) pick = t;
+      if (batch_class_smem(c, k, wpb[t], table[t]) <= batch_smem_limit(kClassApl[k], wpb[t], table[t])) pick = t;
     if (pick < 0) {
       e = batch_set_class(c, k, 4, false);
-      if (e == cudaSuccess && c->batch_cls[k].n_items > 0 && c->batch_cls[k].smem > 227 * 1024) {
+      if (e == cudaSuccess && c->batch_cls[k].n_items > 0 &&
+          c->batch_cls[k].smem > batch_smem_limit(kClassApl[k], 4, false)) {
         batch_free(c);
         return fail(c, ALGDOCK_E_INVALID, "batch_layout: a ligand's tables exceed shared memory");
       }
@@ -1138,7 +1142,7 @@ algdock_status algdock_batch_tune(algdock_ctx* c, const int32_t* state_of, const
     bool best_t = B.table;
     for (int t = 0; t < nc && e == cudaSuccess; ++t) {
       if (wpb[t] == best_w && table[t] == best_t) continue;
-      if (batch_class_smem(c, k, wpb[t], table[t]) > 227 * 1024) continue;
+      if (batch_class_smem(c, k, wpb[t], table[t]) > batch_smem_limit(kClassApl[k], wpb[t], table[t])) continue;
       e = batch_set_class(c, k, wpb[t], table[t]);
       if (e == cudaSuccess) e = batch_set_attributes(*c);
       float m = 0.f;

@@ -23,33 +23,6 @@ __device__ __forceinline__ float rcp_approx(float v) {
   return r;
 }
 
-// Two FP32 values in one 64-bit register pair, for the paired FP32 instructions of sm_100-class
-// GPUs (add/sub/mul/fma .f32x2): one instruction serves a pair of receptor atoms.
-typedef uint64_t f32x2;
-__device__ __forceinline__ f32x2 pack2(float a, float b) {
-  f32x2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void unpack2(f32x2 v, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-  f32x2 r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
-  f32x2 r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-  f32x2 r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-
 // Each thread evaluates kTIPer (configuration, atom) points against every receptor atom, two
 // receptor atoms per paired instruction.  A block holds whole configurations (spb of them,
 // spb * na <= 512 points), so the per-configuration sums stay inside the block and are taken in a

@@ -41,7 +41,7 @@ struct Lig {
   const float4* tor_s;
   const int* inc_start;
   const uint32_t* inc;  // slot indices
-  const float2* pair;   // [j][i] pair records (only where the table is staged)
+  const float4* pair;   // [p][i]: records of atom i with partners 2p, 2p + 1 (only where the table is staged)
 };
 
 __device__ inline Lig bind_ligand(const uint32_t* s, const LigandLayout& L) {
@@ -58,7 +58,7 @@ __device__ inline Lig bind_ligand(const uint32_t* s, const LigandLayout& L) {
   g.tor_s = (const float4*)(s + L.off_tor + 12 * L.ntor);
   g.inc_start = (const int*)(s + L.off_inc_start);
   g.inc = (const uint32_t*)(s + L.off_inc);
-  g.pair = (const float2*)(s + L.off_pair);
+  g.pair = (const float4*)(s + L.off_pair);
   return g;
 }
 
@@ -350,16 +350,33 @@ __device__ inline void nonbonded(const Lig& L, int na, const float4* xs, float (
 }
 
 // Step 3 from the pair table: the same passes and lane layout as `nonbonded`, with each pair's
-// scaled coefficients read as one 8-byte record (12 eps_ij s_LJ, 332 q_i q_j s_el), zero for
-// excluded pairs and i == j, instead of being formed from per-atom parameters and the pair type.
-// Positions carry R*_i in their fourth component (xs[j].w), and R_ij = R*_i + R*_j
-// (Lorentz-Berthelot) is formed in registers.  r^2 is floored at 0.01 A^2 so
+// scaled coefficients read from the table (12 eps_ij s_LJ, 332 q_i q_j s_el; zero for excluded
+// pairs and i == j) instead of being formed from per-atom parameters and the pair type.
+// R_ij = R*_i + R*_j (Lorentz-Berthelot) is formed in registers.  r^2 is floored at 0.01 A^2 so
 // that a zero record meets finite powers (i == j): (R_ij / r)^12 stays below 1e20 for R_ij <= 4 A.
+//
+// Partners come two at a time (j = 2p, 2p + 1), and the two terms share paired FP32 instructions:
+// the positions are read from the pair-interleaved mirror xp (8 floats per partner pair:
+// x, x', y, y', z, z', R*, R*'), the coefficients from one 16-byte record per atom and partner
+// pair, so that every operand pair arrives in one aligned register pair.  An odd na ends with a
+// zero partner (zero position and radius, zero records).  Each half accumulates its own forces and
+// energy; the halves are added at the end of a pass.
 constexpr float kPairMinR2 = 1.0e-2f;
+
+// Writes atom i's coordinates into the pair-interleaved mirror.
+__device__ inline void put_pair_pos(float* xp, int i, float x, float y, float z) {
+  float* b = xp + 8 * (i >> 1) + (i & 1);
+  b[0] = x;
+  b[2] = y;
+  b[4] = z;
+}
+
 template <int APL, bool ENERGY, bool FORCES = true>
-__device__ inline void nonbonded_table(const Lig& L, int na, const float4* xs, float (&F)[APL][3], float& el) {
+__device__ inline void nonbonded_table(const Lig& L, int na, const float* xp, float (&F)[APL][3], float& el) {
   const int lane = threadIdx.x & 31;
-  float e2 = 0.f;
+  const int P = (na + 1) >> 1;
+  const f32x2 one = pack2(1.f, 1.f), two = pack2(2.f, 2.f), twelfth = pack2(1.f / 12.f, 1.f / 12.f);
+  f32x2 e2 = 0ull;  // (0.f, 0.f)
 #pragma unroll
   for (int a = 0; a < APL; ++a) {
     const int base = 32 * a;
@@ -369,41 +386,55 @@ __device__ inline void nonbonded_table(const Lig& L, int na, const float4* xs, f
     const int il = split ? (lane & 15) : lane;
     const int i = base + il;
     const bool act = il < m;
-    int jb = 0, cnt = na, dir = 1;
+    int pb = 0, cnt = P, dir = 1;
     if (split) {
-      const int h = (na + 1) >> 1;
-      jb = lane < 16 ? 0 : na - 1;
-      cnt = lane < 16 ? h : na - h;
+      const int h = (P + 1) >> 1;
+      pb = lane < 16 ? 0 : P - 1;
+      cnt = lane < 16 ? h : P - h;
       dir = lane < 16 ? 1 : -1;
     }
-    float fx = 0.f, fy = 0.f, fz = 0.f;
+    f32x2 fx2 = 0ull, fy2 = 0ull, fz2 = 0ull;
     if (act) {
-      const float4 pi = xs[i];
-      const float2* rec = L.pair + (size_t)jb * na + i;
-      const float4* pj_ptr = xs + jb;
-      const int rstep = dir * na;
+      const float* own = xp + 8 * (i >> 1) + (i & 1);
+      const f32x2 X = pack2(own[0], own[0]), Y = pack2(own[2], own[2]), Z = pack2(own[4], own[4]);
+      const f32x2 Ri = pack2(own[6], own[6]);
+      const float4* rec = L.pair + (size_t)pb * na + i;
+      const float4* pp = (const float4*)xp + 2 * pb;
+      const int rstep = dir * na, pstep = 2 * dir;
+#pragma unroll 2
       for (int jj = 0; jj < cnt; ++jj) {
-        const float4 pj = *pj_ptr;
-        const float2 t = *rec;
-        pj_ptr += dir;
+        const float4 q0 = pp[0];  // (x, x', y, y')
+        const float4 q1 = pp[1];  // (z, z', R*, R*')
+        const float4 t = *rec;    // (e, e', c, c')
+        pp += pstep;
         rec += rstep;
-        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-        const float r2 = fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), kPairMinR2);
-        const float R = pi.w + pj.w;
-        const float inv_r = rsqrtf(r2);
-        const float inv_r2 = inv_r * inv_r;
-        const float s2 = (R * R) * inv_r2;
-        const float s6 = s2 * s2 * s2;
-        const float eel = t.y * inv_r;
-        const float fr = fmaf(t.x, fmaf(s6, s6, -s6), eel) * inv_r2;
+        const f32x2 dx = sub2(X, pack2(q0.x, q0.y)), dy = sub2(Y, pack2(q0.z, q0.w));
+        const f32x2 dz = sub2(Z, pack2(q1.x, q1.y));
+        float ra, rb;
+        unpack2(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), ra, rb);
+        const f32x2 inv_r = pack2(rsqrtf(fmaxf(ra, kPairMinR2)), rsqrtf(fmaxf(rb, kPairMinR2)));
+        const f32x2 R = add2(Ri, pack2(q1.z, q1.w));
+        const f32x2 inv_r2 = mul2(inv_r, inv_r);
+        const f32x2 s2 = mul2(mul2(R, R), inv_r2);
+        const f32x2 s6 = mul2(mul2(s2, s2), s2);
+        const f32x2 e = pack2(t.x, t.y);
+        const f32x2 eel = mul2(pack2(t.z, t.w), inv_r);
         if (FORCES) {
-          fx = fmaf(fr, dx, fx);
-          fy = fmaf(fr, dy, fy);
-          fz = fmaf(fr, dz, fz);
+          const f32x2 fr = mul2(fma2(e, mul2(s6, sub2(s6, one)), eel), inv_r2);
+          fx2 = fma2(fr, dx, fx2);
+          fy2 = fma2(fr, dy, fy2);
+          fz2 = fma2(fr, dz, fz2);
         }
-        if (ENERGY) e2 += fmaf(t.x * (1.f / 12.f), fmaf(s6, s6, -2.f * s6), eel);
+        if (ENERGY) e2 = add2(e2, fma2(mul2(e, twelfth), mul2(s6, sub2(s6, two)), eel));
       }
     }
+    float fx, fy, fz, ha, hb;
+    unpack2(fx2, fx, ha);
+    fx += ha;
+    unpack2(fy2, fy, ha);
+    fy += ha;
+    unpack2(fz2, fz, hb);
+    fz += hb;
     if (split) {
       fx += __shfl_xor_sync(kFull, fx, 16);
       fy += __shfl_xor_sync(kFull, fy, 16);
@@ -415,7 +446,11 @@ __device__ inline void nonbonded_table(const Lig& L, int na, const float4* xs, f
       F[a][2] += fz;
     }
   }
-  if (ENERGY) el += 0.5f * e2;
+  if (ENERGY) {
+    float ea, eb;
+    unpack2(e2, ea, eb);
+    el += 0.5f * (ea + eb);
+  }
 }
 
 // Forces on the lane's atoms (and, if ENERGY, the lane's partial energies).  xs holds all
@@ -423,7 +458,7 @@ __device__ inline void nonbonded_table(const Lig& L, int na, const float4* xs, f
 template <int APL, bool ENERGY, bool TABLE = false, bool FORCES = true>
 __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const GridDev& G, const float4* xs, float* sf,
                                 const float (&x)[APL][3], float (&F)[APL][3], float w_sg, float w_g, bool all_grids,
-                                Energies& en, int& outside) {
+                                Energies& en, int& outside, const float* xp = nullptr) {
   const int lane = threadIdx.x & 31;
   const int na = LL.na, ns = LL.n_slots;
   float* sx = sf;
@@ -463,7 +498,7 @@ __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const Grid
       F[a][2] += sz[s];
     }
   }
-  if (TABLE) nonbonded_table<APL, ENERGY, FORCES>(L, na, xs, F, el);
+  if (TABLE) nonbonded_table<APL, ENERGY, FORCES>(L, na, xp, F, el);
   else nonbonded<APL, ENERGY, FORCES>(L, na, xs, F, el);
   // restraint on the centre of mass
   mx = warp_sumf(mx);
@@ -516,18 +551,24 @@ __device__ inline void stage_ligand(uint32_t* s, const uint32_t* __restrict__ bl
   for (int i = threadIdx.x; i < words / 4; i += blockDim.x) dst[i] = src[i];
 }
 
-// Shared memory of one block: ligand blob, then per warp 32*APL float4 positions and the
-// bonded-slot scratch (3 * n_slots floats, rounded up to 16 bytes).
+// Shared memory of one block: ligand blob, then per warp 32*APL float4 positions, with the pair
+// table also the pair-interleaved mirror of the pair loop (32*APL * 4 floats), and the bonded-slot
+// scratch (3 * n_slots floats, rounded up to 16 bytes).
 __host__ __device__ inline int scratch_words(const LigandLayout& L) { return (3 * L.n_slots + 3) & ~3; }
+__host__ __device__ inline int warp_words(const LigandLayout& L, int apl, bool table) {
+  return (table ? 8 : 4) * 32 * apl + scratch_words(L);
+}
 
 struct WarpSmem {
   float4* xs;
+  float* xp;  // pair-interleaved positions (table kernels only)
   float* sf;
 };
-template <int APL>
+template <int APL, bool TABLE = false>
 __device__ inline WarpSmem warp_smem(uint32_t* smem, int staged_words, const LigandLayout& LL, int warp) {
-  uint32_t* p = smem + staged_words + warp * (4 * 32 * APL + scratch_words(LL));
-  return WarpSmem{(float4*)p, (float*)(p + 4 * 32 * APL)};
+  uint32_t* p = smem + staged_words + warp * warp_words(LL, APL, TABLE);
+  float* xp = TABLE ? (float*)(p + 4 * 32 * APL) : nullptr;
+  return WarpSmem{(float4*)p, xp, (float*)(p + (TABLE ? 8 : 4) * 32 * APL)};
 }
 
 struct HmcArgs {
@@ -581,9 +622,14 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
   const int64_t r = r_first + warp;
   if (r >= A.n_rep) return;
   const Lig L = bind_ligand(smem, LL);
-  const WarpSmem ws = warp_smem<APL>(smem, staged, LL, warp);
+  const WarpSmem ws = warp_smem<APL, TABLE>(smem, staged, LL, warp);
   float4* xs = ws.xs;
+  float* xp = ws.xp;
   const int na = LL.na;
+  if (TABLE && (na & 1) && lane == 0) {  // the zero partner that completes the last pair
+    put_pair_pos(xp, na, 0.f, 0.f, 0.f);
+    xp[8 * (na >> 1) + 7] = 0.f;
+  }
   const int64_t xstride = BATCH ? A.x_stride : na;
   const int k = A.state_of[r];
   if ((unsigned)k >= (unsigned)A.n_states) {  // invalid state index: leave the replica untouched
@@ -623,8 +669,13 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
       v[a][1] = rr1 * s1 * sd;
       v[a][2] = rr2 * c2 * sd;
       kin += pb.z * (v[a][0] * v[a][0] + v[a][1] * v[a][1] + v[a][2] * v[a][2]);
-      // the table loop reads R*_i from the fourth component, the pair-type loop the charge
-      xs[i] = make_float4(x[a][0], x[a][1], x[a][2], TABLE ? pb.x : L.atom_a[i].y);
+      // the pair-type loop reads the charge from the fourth component; the table loop reads
+      // positions and R*_i from the pair-interleaved mirror
+      xs[i] = make_float4(x[a][0], x[a][1], x[a][2], L.atom_a[i].y);
+      if (TABLE) {
+        put_pair_pos(xp, i, x[a][0], x[a][1], x[a][2]);
+        xp[8 * (i >> 1) + 6 + (i & 1)] = pb.x;  // R*_i
+      }
     } else {
       x[a][0] = x[a][1] = x[a][2] = 0.f;
       v[a][0] = v[a][1] = v[a][2] = 0.f;
@@ -634,7 +685,7 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
   int outside = 0;
   Energies en;
   double c[4];
-  evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
+  evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside, xp);
   reduce_components(en, c);
   // the starting components go out now (a rejected trial leaves them); only U0 stays live
   const double U0 = weighted(c, st.w_sg, st.w_g);
@@ -664,13 +715,14 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
         p.y = x[a][1];
         p.z = x[a][2];
         xs[i] = p;
+        if (TABLE) put_pair_pos(xp, i, x[a][0], x[a][1], x[a][2]);
       }
     }
     __syncwarp();
     if (s + 1 < A.n_steps) {
-      evaluate<APL, false, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, false, en, outside);
+      evaluate<APL, false, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, false, en, outside, xp);
     } else {
-      evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside);
+      evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside, xp);
       reduce_components(en, c);
       U1 = weighted(c, st.w_sg, st.w_g);
     }
@@ -982,7 +1034,7 @@ __global__ void ukn_kernel(const StateDev* __restrict__ states, int k_begin, int
 int atoms_per_lane(int na) { return na <= 32 ? 1 : (na <= 64 ? 2 : 3); }
 
 size_t block_smem(const LigandLayout& L, int apl, int wpb = kWarpsPerBlock, bool table = false) {
-  return ((size_t)(table ? L.words_pair : L.words) + (size_t)wpb * (4 * 32 * apl + scratch_words(L))) * 4;
+  return ((size_t)(table ? L.words_pair : L.words) + (size_t)wpb * warp_words(L, apl, table)) * 4;
 }
 
 constexpr int kTableWarps = 16;  // warps per block of the pair-table HMC kernel (512 threads, 128 registers)
@@ -1060,6 +1112,16 @@ HmcKernel batch_kernel(int apl, int wpb, bool table) {
   return wpb == 8 ? hmc_kernel<3, 8, false, true> : hmc_kernel<3, kWarpsPerBlock, false, true>;
 }
 }  // namespace
+
+size_t batch_smem_limit(int apl, int wpb, bool table) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, batch_kernel(apl, wpb, table)) != cudaSuccess)
+    return 0;
+  return (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+}
 
 cudaError_t batch_set_attributes(const algdock_ctx& c) {
   for (int k = 0; k < kBatchClasses; ++k) {

@@ -21,6 +21,38 @@ constexpr double kAttractiveMinDist = 2.0;         // A
 constexpr int kMaxAtoms = 96;                      // 3 atoms per lane of one warp
 constexpr int kMaxLadder = 1024;
 
+// Two FP32 values in one 64-bit register pair, for the paired FP32 instructions of sm_100-class
+// GPUs (add/sub/mul/fma .f32x2, round to nearest): one instruction serves two independent terms.
+typedef uint64_t f32x2;
+__device__ __forceinline__ f32x2 pack2(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
 enum : uint32_t { kPurposeMomentum = 1, kPurposeAccept = 2, kPurposeExchange = 3, kPurposeExternal = 5 };
 
 // ------------------------------------------------------------------ Philox4x32-10
@@ -88,8 +120,9 @@ struct LigandLayout {
   int off_inc_start;  // int[na + 1]
   int off_inc;        // uint32[ninc]: the bonded slots of each atom, in a fixed order
   int words;          // total of the sections above (multiple of 4)
-  int off_pair;       // float2[na][na], [j][i]: (12 eps_ij s_lj, 332 q_i q_j s_el), zero if excluded or
-                      // i == j, after the sections above
+  int off_pair;       // float4[(na + 1) / 2][na], [p][i]: for the partner pair j = 2p, 2p + 1,
+                      // (e_ij, e_ij', c_ij, c_ij') with e = 12 eps_ij s_lj and c = 332 q_i q_j s_el,
+                      // zero if excluded, i == j or j = na (odd na); after the sections above
   int words_pair;     // total including the pair table
   float total_mass;
   float site[3];
@@ -246,6 +279,9 @@ bool hmc_uses_table(const LigandLayout& L);
 // batches: the block shared memory of a class shape, the candidate shapes of a class, and the
 // HMC trial of every replica of the batch (classes on forked streams, joined on s)
 size_t batch_block_smem(const LigandLayout& L, int apl, int wpb, bool table);
+// Dynamic shared memory a batch kernel of this shape may request on the current device: the
+// per-block opt-in limit less the kernel's static shared memory (0 if the query fails).
+size_t batch_smem_limit(int apl, int wpb, bool table);
 int batch_candidates(int cls, int* wpb, bool* table);
 // all-FP64 path: lattice derivation and the evaluation of N configurations (one thread each)
 cudaError_t launch_grid_prepare64(cudaStream_t s, size_t n_nodes, const double* ljr, const double* lja,

@@ -200,3 +200,20 @@ def test_layout_errors(batch):
     with pytest.raises(AlgdockError):
         ctx.batch_layout(np.array([0, len(ligs)], dtype=np.int32), STRIDE)
     ctx.batch_layout(lig_of, STRIDE)
+
+
+def test_layout_counts_the_kernels_static_shared_memory():
+    """The 33-64-atom ligands of the 256-ligand workload include one whose 16-replica table block
+    asks for 16 bytes less dynamic shared memory than 227 KB; with the batch kernel's own static
+    shared memory (its copy of the ligand layout) that is over the per-block limit.  The layout
+    must pick another shape for its class rather than fail the launch attribute."""
+    from paper_1507_03703_gb300.algdock import Context
+    sys_, ligs = S.config_batch(3)
+    mid = [l for l in ligs if 33 <= l.n_atoms <= 64]
+    ctx = Context(0)
+    ctx.batch_load(mid, sys_.site)
+    lig_of = np.repeat(np.arange(len(mid)), 2).astype(np.int32)
+    ctx.batch_layout(lig_of, 64)
+    shapes = ctx.batch_shapes()
+    assert shapes[1] == (8, True)  # the 62-atom ligand keeps the table in 8-replica blocks
+    assert shapes[2] == (8, True)  # 63-64-atom ligands whose 16-replica table blocks exceed 227 KB
