@@ -967,6 +967,7 @@ algdock_status algdock_batch_load(algdock_ctx* c, int32_t n_ligands, const algdo
   std::vector<BatchLigand> recs(n_ligands);
   std::vector<uint32_t> all;
   int max_na = 0;
+  Device g(c->device);  // the class test queries the batch kernels' limits on this device
   for (int l = 0; l < n_ligands; ++l) {
     LigandLayout Y;
     std::vector<uint32_t> blob;
@@ -976,11 +977,10 @@ algdock_status algdock_batch_load(algdock_ctx* c, int32_t n_ligands, const algdo
     recs[l].LL = Y;
     recs[l].blob_off = (int64_t)all.size();  // blob sizes are multiples of 4 words: 16-byte aligned
     recs[l].apl = Y.na <= 32 ? 1 : (Y.na <= 64 ? 2 : 3);
-    recs[l].cls = recs[l].apl == 1 ? 0 : (recs[l].apl == 3 ? 3 : (hmc_uses_table(Y) ? 1 : 2));
+    recs[l].cls = recs[l].apl == 1 ? 0 : (recs[l].apl == 3 ? 3 : (batch_uses_table16(Y) ? 1 : 2));
     all.insert(all.end(), blob.begin(), blob.end());
     max_na = std::max(max_na, Y.na);
   }
-  Device g(c->device);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "batch_load");
   batch_free(c);

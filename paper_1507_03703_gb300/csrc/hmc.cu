@@ -1123,6 +1123,11 @@ size_t batch_smem_limit(int apl, int wpb, bool table) {
   return (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
 }
 
+bool batch_uses_table16(const LigandLayout& L) {
+  const int apl = atoms_per_lane(L.na);
+  return apl <= 2 && block_smem(L, apl, kTableWarps, true) <= batch_smem_limit(apl, kTableWarps, true);
+}
+
 cudaError_t batch_set_attributes(const algdock_ctx& c) {
   for (int k = 0; k < kBatchClasses; ++k) {
     const BatchClass& B = c.batch_cls[k];

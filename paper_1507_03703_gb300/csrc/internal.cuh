@@ -282,6 +282,9 @@ size_t batch_block_smem(const LigandLayout& L, int apl, int wpb, bool table);
 // Dynamic shared memory a batch kernel of this shape may request on the current device: the
 // per-block opt-in limit less the kernel's static shared memory (0 if the query fails).
 size_t batch_smem_limit(int apl, int wpb, bool table);
+// Whether a ligand's pair-table batch kernel fits 16-replica blocks (batch class 1 rather than 2
+// for 33-64 atoms).
+bool batch_uses_table16(const LigandLayout& L);
 int batch_candidates(int cls, int* wpb, bool* table);
 // all-FP64 path: lattice derivation and the evaluation of N configurations (one thread each)
 cudaError_t launch_grid_prepare64(cudaStream_t s, size_t n_nodes, const double* ljr, const double* lja,

@@ -205,8 +205,9 @@ def test_layout_errors(batch):
 def test_layout_counts_the_kernels_static_shared_memory():
     """The 33-64-atom ligands of the 256-ligand workload include one whose 16-replica table block
     asks for 16 bytes less dynamic shared memory than 227 KB; with the batch kernel's own static
-    shared memory (its copy of the ligand layout) that is over the per-block limit.  The layout
-    must pick another shape for its class rather than fail the launch attribute."""
+    shared memory (its copy of the ligand layout) that is over the per-block limit.  That ligand
+    joins the class of 8-replica table blocks, with the 63-64-atom ligands that exceed the limit
+    outright, and the rest keep 16-replica blocks: the layout sets every launch attribute."""
     from paper_1507_03703_gb300.algdock import Context
     sys_, ligs = S.config_batch(3)
     mid = [l for l in ligs if 33 <= l.n_atoms <= 64]
@@ -215,5 +216,5 @@ def test_layout_counts_the_kernels_static_shared_memory():
     lig_of = np.repeat(np.arange(len(mid)), 2).astype(np.int32)
     ctx.batch_layout(lig_of, 64)
     shapes = ctx.batch_shapes()
-    assert shapes[1] == (8, True)  # the 62-atom ligand keeps the table in 8-replica blocks
-    assert shapes[2] == (8, True)  # 63-64-atom ligands whose 16-replica table blocks exceed 227 KB
+    assert shapes[1] == (16, True)
+    assert shapes[2] == (8, True)
