@@ -36,6 +36,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--clocks-csv", default=None,
+                   help="keep the nvidia-smi samples of the timed region in this file (default: a temporary file)")
     p.add_argument("--no-mbar", action="store_true")
     p.add_argument("--no-learned", action="store_true")
     p.add_argument("--no-fep", action="store_true", help="skip the end-point (f_DE) measurement")
@@ -105,14 +107,20 @@ class Clocks:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, path=None):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.keep = path is not None
+        if path is None:
+            import tempfile
+            fd, path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+        self.path = path
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            if os.path.dirname(self.path):
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
@@ -121,6 +129,13 @@ class Clocks:
             self.proc = None
 
     def stop(self):
+        try:
+            return self._summary()
+        finally:
+            if not self.keep and os.path.exists(self.path):
+                os.remove(self.path)
+
+    def _summary(self):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -846,7 +861,7 @@ def main():
         step(w)
     torch.cuda.synchronize()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    clocks = Clocks(local)
+    clocks = Clocks(local, args.clocks_csv)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
