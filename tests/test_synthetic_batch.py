@@ -5,7 +5,9 @@
   leaves the default growth (every earlier system) unchanged.
 - The batch workload has the stated sizes and spread.
 - The padded ligands of the padded-uniform baseline add only inert atoms at distinct points.
-- The gather byte count of an HMC launch matches a hand count on a three-state ladder."""
+- The gather byte count of an HMC launch matches a hand count on a three-state ladder.
+- The clock sampler's sample file is temporary unless named."""
+import os
 import sys
 
 import numpy as np
@@ -97,3 +99,16 @@ def test_gather_bytes_hand_count(bench_module):
     got = bench_module.gather_bytes_per_launch(np.array([np.nan, 0.25, 1.0]), R, n_atoms, n_steps)
     want = R * n_atoms * (3 * 2 * 192 + (n_steps - 1) * (0 + 64 + 128))
     assert got == want
+
+
+def test_clock_sampler_file_handling(bench_module, tmp_path, monkeypatch):
+    """Without nvidia-smi the sampler reports nothing; its default sample file is temporary and
+    removed after the summary, a named one is kept."""
+    monkeypatch.setenv("PATH", str(tmp_path))  # no nvidia-smi on the path
+    c = bench_module.Clocks(0)
+    c.start()
+    assert c.stop() is None and not os.path.exists(c.path)
+    kept = tmp_path / "clocks.csv"
+    c = bench_module.Clocks(0, str(kept))
+    c.start()
+    assert c.stop() is None and kept.exists()
