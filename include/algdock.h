@@ -307,8 +307,9 @@ algdock_status algdock_mean_pacc(algdock_ctx* ctx, int64_t N, const double* comp
  * ligand per job; each replica's trial is the one of algdock_hmc_cycle, "Sampling").  Replicas
  * of one ligand that are consecutive in the replica order share blocks; a block stages its
  * ligand's tables once.  Launch classes: 0: <= 32 atoms; 1: 33-64 atoms whose per-pair table fits
- * 16-replica blocks (the one-ligand kernel then stages it too); 2: the other 33-64-atom ligands;
- * 3: 65-96 atoms. */
+ * 16-replica blocks of the batch kernel (its dynamic shared memory plus the kernel's own static
+ * shared memory within the device's per-block limit; the one-ligand kernel then stages the table
+ * too); 2: the other 33-64-atom ligands; 3: 65-96 atoms. */
 
 /* Load n_ligands ligands (each validated as by algdock_ligand_load) with one restraint.  Replaces
  * any earlier batch and its layout; the single-ligand state (algdock_ligand_load) is untouched. */
@@ -318,7 +319,8 @@ algdock_status algdock_batch_load(algdock_ctx* ctx, int32_t n_ligands, const alg
 /* Replica layout: replica r runs ligand lig_of[r] (host int32 [n_rep]); positions are stored
  * x_stride atoms apart ([n_rep][x_stride][3] float, only the first n_atoms of each used).  Builds
  * the work lists (runs of consecutive replicas of one ligand, longest blocks first) with a default
- * launch shape per class (the first candidate of algdock_batch_tune that fits shared memory).
+ * launch shape per class (the first candidate of algdock_batch_tune whose shared memory, with the
+ * kernel's static shared memory, fits the device's per-block limit).
  * uniform != 0 runs every replica in the 65-96-atom class shape (the uniform baseline of a
  * batch).  ALGDOCK_E_INVALID if a ligand's tables exceed shared memory. */
 algdock_status algdock_batch_layout(algdock_ctx* ctx, int64_t n_rep, const int32_t* lig_of, int32_t x_stride,
