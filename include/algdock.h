@@ -248,7 +248,7 @@ algdock_status algdock_reduced_energies(algdock_ctx* ctx, int64_t N, const float
  * (host).  precision_mode 0: FP64 throughout; 1: exponentials in FP32 of FP64 arguments, sums in
  * FP64; 2: each sample's column shifted by its minimum (FP64, exact in the result) and stored as
  * FP32, then FP32 arguments, exponentials and Kahan-compensated sums, FP64 only where partial sums
- * meet (K <= 16384; extra scratch K*N*4 bytes).  f_k [K] (host) and iters (host) receive the
+ * meet (K <= 16384; extra scratch K*N*4 bytes).  K <= 65535 in every mode.  f_k [K] (host) and iters (host) receive the
  * result.  Synchronises.  Returns
  * ALGDOCK_E_NOT_CONVERGED (with the last iterate in f_k) if max_iter is reached. */
 algdock_status algdock_mbar(algdock_ctx* ctx, int32_t K, int64_t N, const double* u_kn, const int64_t* N_k,
@@ -463,15 +463,19 @@ algdock_status algdock_propose_learned(algdock_ctx* ctx, const float* params, co
 /* MBAR without any device allocation.  The paper has no counterpart: this is a service of this
  * library for callers that cannot call cudaMalloc - for example a host framework whose caching
  * allocator owns all device memory and forbids direct allocations, or a service that reserves its
- * whole memory budget at start-up.  Same arguments, arithmetic and results as algdock_mbar, but
- * the solver's scratch is a fixed 8 MiB array in the library's own device memory (every GPU that
- * loads the library holds it until the process exits); the call itself allocates nothing and
- * does not use the context's own MBAR scratch.
+ * whole memory budget at start-up.  Same arguments, arithmetic and results as algdock_mbar for
+ * precision modes 0 and 1, but the solver's scratch is a fixed 8 MiB array in the library's own
+ * device memory (every GPU that loads the library holds it until the process exits); the call
+ * itself allocates nothing and does not use the context's own MBAR scratch.
+ *  - precision_mode 2 is rejected (ALGDOCK_E_INVALID with its own message): its FP32 copy of
+ *    u_kn (K*N*4 bytes) does not fit the fixed array.  K above 65535 is rejected as well.
  *  - Sizes whose scratch exceeds 8 MiB (about 8 bytes per sample plus 16 bytes per state and
  *    chunk of 8192-32768 samples, e.g. N up to ~1e6 samples for K = 128) are rejected with
  *    ALGDOCK_E_INVALID and a message naming the bytes needed.
  *  - The first call on a device looks up the array's device address (once per device, with that
- *    device current); make that first call before any stream capture.
+ *    device current) and keeps it for the life of the process; make that first call before any
+ *    stream capture.  The kept address does not survive cudaDeviceReset: a process that resets
+ *    the device must not call this entry point afterwards.
  *  - Every call on a device shares the one array, which keeps the last call's contents (each call
  *    re-initialises what it reads).  Calls whose work overlaps on the GPU (from several host
  *    threads or streams) race on it: serialise them. */

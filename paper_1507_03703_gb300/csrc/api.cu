@@ -1368,6 +1368,9 @@ algdock_status algdock_mbar(algdock_ctx* c, int32_t K, int64_t N, const double* 
       precision_mode < 0 || precision_mode > 2)
     return fail(c, ALGDOCK_E_INVALID, "mbar: bad arguments");
   if (precision_mode == 2 && K > 16384) return fail(c, ALGDOCK_E_INVALID, "mbar: precision mode 2 takes K <= 16384");
+  if (K > kMbarMaxStates)
+    return fail(c, ALGDOCK_E_INVALID, "mbar: K = " + std::to_string(K) + " exceeds the " +
+                                          std::to_string(kMbarMaxStates) + " states one launch grid dimension can hold");
   if (!is_device_ptr(u_kn)) return fail(c, ALGDOCK_E_INVALID, "mbar: u_kn must be a device pointer");
   int64_t total = 0;
   for (int k = 0; k < K; ++k) {

@@ -20,6 +20,7 @@ constexpr double kRepulsiveMinDist = 0.01;         // A
 constexpr double kAttractiveMinDist = 2.0;         // A
 constexpr int kMaxAtoms = 96;                      // 3 atoms per lane of one warp
 constexpr int kMaxLadder = 1024;
+constexpr int kMbarMaxStates = 65535;             // MBAR's state_partials grid has one y-index per state
 
 // Two FP32 values in one 64-bit register pair, for the paired FP32 instructions of sm_100-class
 // GPUs (add/sub/mul/fma .f32x2, round to nearest): one instruction serves two independent terms.

@@ -432,9 +432,18 @@ extern "C" algdock_status algdock_mbar_noalloc(algdock_ctx* c, int32_t K, int64_
                                                int32_t precision_mode, double* f_k, int32_t* iters) {
   if (!c) return ALGDOCK_E_INVALID;
   try {
-    if (K < 1 || N < 1 || !u_kn || !N_k || !f_k || !iters || max_iter < 1 || !(tol > 0) ||
-        (precision_mode != 0 && precision_mode != 1)) {
+    if (K < 1 || N < 1 || !u_kn || !N_k || !f_k || !iters || max_iter < 1 || !(tol > 0)) {
       c->err = "mbar_noalloc: bad arguments";
+      return ALGDOCK_E_INVALID;
+    }
+    if (precision_mode != 0 && precision_mode != 1) {
+      c->err = "mbar_noalloc: precision_mode must be 0 or 1 (mode 2 keeps an FP32 copy of u_kn, K*N*4 bytes, "
+               "which the fixed scratch array does not hold; use algdock_mbar for mode 2)";
+      return ALGDOCK_E_INVALID;
+    }
+    if (K > algdock::kMbarMaxStates) {
+      c->err = "mbar_noalloc: K = " + std::to_string(K) + " exceeds the " + std::to_string(algdock::kMbarMaxStates) +
+               " states one launch grid dimension can hold";
       return ALGDOCK_E_INVALID;
     }
     int64_t total = 0;
@@ -486,6 +495,10 @@ extern "C" algdock_status algdock_mbar_noalloc(algdock_ctx* c, int32_t K, int64_
     }
     return ALGDOCK_OK;
   } catch (...) {
+    try {
+      c->err = "mbar_noalloc: host exception";
+    } catch (...) {
+    }
     return ALGDOCK_E_INVALID;
   }
 }

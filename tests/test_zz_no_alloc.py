@@ -58,3 +58,18 @@ def test_noalloc_mbar_rejects_sizes_beyond_its_buffer():
     st, _, _ = _noalloc(ctx, u, np.array([N // 2, N - N // 2]))
     assert st == E_INVALID
     assert "bytes of scratch" in ctx.last_error()
+
+
+def test_noalloc_mbar_rejects_precision_mode_2_by_name():
+    """Mode 2 keeps an FP32 copy of u_kn that the fixed array does not hold: the call says so."""
+    from paper_1507_03703_gb300.algdock import E_INVALID, Context
+    ctx = Context(0)
+    u = torch.zeros((2, 10), dtype=torch.float64, device="cuda")
+    L = ctx._L
+    f = np.zeros(2)
+    it = ctypes.c_int32()
+    Nk = np.array([5, 5], dtype=np.int64)
+    st = L.algdock_mbar_noalloc(ctx.h, 2, 10, u.data_ptr(), Nk.ctypes.data, 1e-10, 100, 2, f.ctypes.data,
+                                ctypes.byref(it))
+    assert st == E_INVALID
+    assert "precision_mode" in ctx.last_error()
