@@ -318,14 +318,16 @@ def bpmf_kT(f_bc, f_cd):
 
 
 def run_ladder(osys, x0, n_chains, n_cycles, n_steps, seed, n_sweeps=25, max_sep=5, rep_offset=0,
-               ladder_offset=0, burn_in=0, n_threads=0):
+               ladder_offset=0, burn_in=0, n_threads=0, n_external=0):
     """Replica-exchange HMC on one ladder (the oracle's own driver of the sampling loop).
 
     Slot r = c*K + i holds one configuration of chain c; config_of[c, k] is the slot index (within
-    the chain) of the configuration at state k.  Each cycle: one HMC trial per slot at its state,
-    then ``n_sweeps`` exchange sweeps per chain.  After ``burn_in`` cycles every slot's components
-    are recorded with its state.  Returns (comps [S, 4], state [S], acceptance per state [K],
-    exchange accepts / attempts [max_sep, K], final x).
+    the chain) of the configuration at state k.  Each cycle ("Equilibration and production"): one
+    HMC trial per slot at its state, then ``n_external`` external-coordinate moves of every slot
+    whose state has alpha < 0.01 ("Sampling"; 0: none), then ``n_sweeps`` exchange sweeps per
+    chain.  After ``burn_in`` cycles every slot's components are recorded with its state.  Returns
+    (comps [S, 4], state [S], acceptance per state [K], exchange accepts / attempts [max_sep, K],
+    final x).
     """
     K = osys.K
     x = np.array(x0, dtype=np.float64).reshape(n_chains * K, osys.na, 3)
@@ -341,6 +343,8 @@ def run_ladder(osys, x0, n_chains, n_cycles, n_steps, seed, n_sweeps=25, max_sep
             state_of[c * K + config_of[c]] = np.arange(K, dtype=np.int32)
         x, comps, dH, acc, _ = osys.hmc(x, state_of, n_steps, seed, cyc, rep_offset=rep_offset,
                                         n_threads=n_threads)
+        if n_external > 0:
+            x, comps, _ = osys.external_moves(x, comps, state_of, n_external, seed, cyc, rep_offset=rep_offset)
         np.add.at(hmc_acc, state_of, acc)
         np.add.at(hmc_n, state_of, 1)
         config_of, att, ac = exchange(osys.T, osys.alpha, comps.reshape(n_chains, K, 4), config_of, n_sweeps,

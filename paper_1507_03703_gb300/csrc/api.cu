@@ -121,7 +121,7 @@ double sqrtA(double rstar, double eps) {
 }
 
 // Validates one ligand and its restraint and builds its device tables: the layout, the blob (atom
-// records, pair types, bonded terms, incidence lists, then the per-pair table) and the FP64
+// records, pair types, bonded terms, the bonded-force gather schedule, then the per-pair table) and the FP64
 // target-force-field factors of each atom.
 algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdock_restraint* R, const std::string& who,
                             LigandLayout& Y, std::vector<uint32_t>& blob, std::vector<TargetFactors>& fac,
@@ -197,16 +197,50 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
   for (int t = 0; t < ntor; ++t)
     for (int r = 0; r < 4; ++r)
       inc[L->torsions[4 * t + r]].push_back((uint32_t)(2 * nb + 3 * nang + r * ntor + t));
-  int ninc = 0;
-  for (auto& v : inc) ninc += (int)v.size();
+  // Gather schedule of the bonded forces: every slot belongs to exactly one atom, so the slots
+  // sorted by atom form one list of n_slots entries.  It is cut into runs of Lr entries, one run
+  // per lane, which balances the per-lane work however the slots are spread over atoms.  A lane
+  // adds its entries in order and, at the last entry of each atom within its run, stores the
+  // partial sum in that entry's slot (which no other lane reads).  Lr is at least a third of the
+  // largest atom's count, so that an atom's entries meet at most 4 runs: its owner then adds at
+  // most 4 partial sums, in run order.
+  const int n_slots = 2 * nb + 3 * nang + 4 * ntor;
+  if (n_slots >= 0x7fff) return fail(c, ALGDOCK_E_INVALID, who + ": too many bonded terms");
+  std::vector<uint32_t> ent;
+  std::vector<int> ent_atom;
+  int max_inc = 0;
+  for (int i = 0; i < na; ++i) {
+    max_inc = std::max(max_inc, (int)inc[i].size());
+    for (uint32_t code : inc[i]) {
+      ent.push_back(code);
+      ent_atom.push_back(i);
+    }
+  }
+  const int Lr = n_slots == 0 ? 0 : std::max((n_slots + 31) / 32, (max_inc + 2) / 3);
+  const int gs_iters = (Lr + 3) / 4;
+  std::vector<uint16_t> gs((size_t)gs_iters * 32 * 4, (uint16_t)n_slots);
+  std::vector<uint16_t> gp((size_t)na * 4, (uint16_t)n_slots);
+  std::vector<int> n_part(na, 0);
+  for (int l = 0; l < 32 && Lr > 0; ++l)
+    for (int j = 0; j < Lr; ++j) {
+      const int e = l * Lr + j;
+      if (e >= n_slots) break;
+      const bool last = j == Lr - 1 || e + 1 == n_slots || ent_atom[e + 1] != ent_atom[e];
+      gs[((size_t)(j / 4) * 32 + l) * 4 + (j % 4)] = (uint16_t)(ent[e] | (last ? 0x8000u : 0u));
+      if (last) {
+        const int a = ent_atom[e];
+        if (n_part[a] >= 4) return fail(c, ALGDOCK_E_INVALID, who + ": gather schedule overflow");
+        gp[(size_t)a * 4 + n_part[a]++] = (uint16_t)ent[e];
+      }
+    }
 
   memset(&Y, 0, sizeof(Y));
   Y.na = na;
   Y.nb = nb;
   Y.nang = nang;
   Y.ntor = ntor;
-  Y.ninc = ninc;
-  Y.n_slots = 2 * nb + 3 * nang + 4 * ntor;
+  Y.gs_iters = gs_iters;
+  Y.n_slots = n_slots;
   int w = 0;
   auto take = [&](int words) {
     const int o = w;
@@ -219,8 +253,8 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
   Y.off_bond = take(4 * nb);
   Y.off_ang = take(8 * nang);
   Y.off_tor = take(16 * ntor);
-  Y.off_inc_start = take(na + 1);
-  Y.off_inc = take(ninc);
+  Y.off_gs = take(gs_iters * 64);
+  Y.off_gp = take(2 * na);
   Y.words = w;
   if ((size_t)w * 4 > 120 * 1024) return fail(c, ALGDOCK_E_INVALID, who + ": topology too large");
   Y.off_pair = take(4 * ((na + 1) / 2) * na);
@@ -276,12 +310,8 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
       rec[0] = ty == 2 ? 0.f : (float)(12.0 * s_lj * sqrt(L->eps[i]) * sqrt(L->eps[j]));
       rec[2] = ty == 2 ? 0.f : (float)(kCoulomb * L->charge[i] * L->charge[j] * s_el);
     }
-  int pos = 0;
-  for (int i = 0; i < na; ++i) {
-    bi[Y.off_inc_start + i] = pos;
-    for (uint32_t code : inc[i]) blob[Y.off_inc + pos++] = code;
-  }
-  bi[Y.off_inc_start + na] = pos;
+  if (!gs.empty()) memcpy((uint8_t*)(blob.data() + Y.off_gs), gs.data(), gs.size() * sizeof(uint16_t));
+  memcpy((uint8_t*)(blob.data() + Y.off_gp), gp.data(), gp.size() * sizeof(uint16_t));
   Y.total_mass = (float)M;
   for (int k = 0; k < 3; ++k) Y.site[k] = (float)R->site[k];
   Y.k_rest = (float)R->k;
@@ -437,6 +467,12 @@ algdock_status algdock_create(int device, algdock_ctx** out) {
     delete c;
     return ALGDOCK_E_CUDA;
   }
+  if (cudaMalloc(&c->d_work, 256) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(c->h_flag);
+    delete c;
+    return ALGDOCK_E_OOM;
+  }
   *out = c;
   return ALGDOCK_OK;
 }
@@ -464,6 +500,7 @@ void algdock_destroy(algdock_ctx* c) {
   }
   if (c->batch_fork) cudaEventDestroy(c->batch_fork);
   cudaFreeHost(c->h_flag);
+  cudaFree(c->d_work);
   delete c;
 }
 

@@ -20,6 +20,8 @@
 // deterministic.
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace algdock {
@@ -39,8 +41,8 @@ struct Lig {
   const float4* tor_v;
   const float4* tor_c;
   const float4* tor_s;
-  const int* inc_start;
-  const uint32_t* inc;  // slot indices
+  const uint2* gs;  // gather schedule: [gs_iters][32] words of four 16-bit entries
+  const uint2* gp;  // [na]: four 16-bit partial-sum slots per atom
   const float4* pair;   // [p][i]: records of atom i with partners 2p, 2p + 1 (only where the table is staged)
 };
 
@@ -56,8 +58,8 @@ __device__ inline Lig bind_ligand(const uint32_t* s, const LigandLayout& L) {
   g.tor_v = (const float4*)(s + L.off_tor + 4 * L.ntor);
   g.tor_c = (const float4*)(s + L.off_tor + 8 * L.ntor);
   g.tor_s = (const float4*)(s + L.off_tor + 12 * L.ntor);
-  g.inc_start = (const int*)(s + L.off_inc_start);
-  g.inc = (const uint32_t*)(s + L.off_inc);
+  g.gs = (const uint2*)(s + L.off_gs);
+  g.gp = (const uint2*)(s + L.off_gp);
   g.pair = (const float4*)(s + L.off_pair);
   return g;
 }
@@ -89,7 +91,7 @@ __device__ inline void axis_coord(float x, float o, float inv_h, int n, int& c, 
     fl = 0.f;
     frac = 0.f;
     inside = false;
-  } else if (fl + frac >= (float)(n - 1)) {
+  } else if (!(fl + frac < (float)(n - 1))) {  // at or beyond the last node, including u = +inf
     fl = (float)(n - 2);
     frac = 1.f;
     if (u + ue > (float)(n - 1)) inside = false;
@@ -195,17 +197,12 @@ __device__ inline float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y +
 __device__ inline float3 cross(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
-__device__ inline void put(float* sx, float* sy, float* sz, int s, float3 f) {
-  sx[s] = f.x;
-  sy[s] = f.y;
-  sz[s] = f.z;
-}
+__device__ inline void put(float4* sl, int s, float3 f) { sl[s] = make_float4(f.x, f.y, f.z, 0.f); }
 
-// Step 1: every bonded term once, one per lane; per-role forces to the slot arrays.
+// Step 1: every bonded term once, one per lane; per-role forces to the warp's float4 slots.
 // Slots: bond t role r -> r*nb + t; angle -> 2nb + r*nang + t; torsion -> 2nb + 3nang + r*ntor + t.
 template <bool ENERGY, bool FORCES = true>
-__device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const float4* xs, float* sx, float* sy,
-                                     float* sz) {
+__device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const float4* xs, float4* sl) {
   const int lane = threadIdx.x & 31;
   float e = 0.f;
   const int nb = LL.nb, nang = LL.nang, ntor = LL.ntor;
@@ -217,8 +214,8 @@ __device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const
     const float dr = r2 * inv_r - bp.w;
     if (ENERGY) e += bp.z * dr * dr;
     const float c = -2.f * bp.z * dr * inv_r;
-    if (FORCES) put(sx, sy, sz, t, make_float3(c * d.x, c * d.y, c * d.z));
-    if (FORCES) put(sx, sy, sz, nb + t, make_float3(-c * d.x, -c * d.y, -c * d.z));
+    if (FORCES) put(sl, t, make_float3(c * d.x, c * d.y, c * d.z));
+    if (FORCES) put(sl, nb + t, make_float3(-c * d.x, -c * d.y, -c * d.z));
   }
   const int ab = 2 * nb;
   for (int t = lane; t < nang; t += 32) {  // k (theta - theta0)^2
@@ -235,9 +232,9 @@ __device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const
     const float cu = __fdividef(coef * c, lu2), cw = __fdividef(coef * c, lw2), cx = coef * inv_luw;
     const float3 fa = make_float3(cx * w.x - cu * u.x, cx * w.y - cu * u.y, cx * w.z - cu * u.z);
     const float3 fc = make_float3(cx * u.x - cw * w.x, cx * u.y - cw * w.y, cx * u.z - cw * w.z);
-    if (FORCES) put(sx, sy, sz, ab + t, fa);
-    if (FORCES) put(sx, sy, sz, ab + nang + t, make_float3(-(fa.x + fc.x), -(fa.y + fc.y), -(fa.z + fc.z)));
-    if (FORCES) put(sx, sy, sz, ab + 2 * nang + t, fc);
+    if (FORCES) put(sl, ab + t, fa);
+    if (FORCES) put(sl, ab + nang + t, make_float3(-(fa.x + fc.x), -(fa.y + fc.y), -(fa.z + fc.z)));
+    if (FORCES) put(sl, ab + 2 * nang + t, fc);
   }
   const int tb = ab + 3 * nang;
   for (int t = lane; t < ntor; t += 32) {  // sum_n V_n/2 (1 + cos(n phi - gamma_n))
@@ -271,10 +268,10 @@ __device__ inline float bonded_terms(const Lig& L, const LigandLayout& LL, const
                                   -(1.f + p) * fi.z + q * fl.z);
     const float3 fk = make_float3(p * fi.x - (1.f + q) * fl.x, p * fi.y - (1.f + q) * fl.y,
                                   p * fi.z - (1.f + q) * fl.z);
-    if (FORCES) put(sx, sy, sz, tb + t, fi);
-    if (FORCES) put(sx, sy, sz, tb + ntor + t, fj);
-    if (FORCES) put(sx, sy, sz, tb + 2 * ntor + t, fk);
-    if (FORCES) put(sx, sy, sz, tb + 3 * ntor + t, fl);
+    if (FORCES) put(sl, tb + t, fi);
+    if (FORCES) put(sl, tb + ntor + t, fj);
+    if (FORCES) put(sl, tb + 2 * ntor + t, fk);
+    if (FORCES) put(sl, tb + 3 * ntor + t, fl);
   }
   return e;
 }
@@ -453,19 +450,46 @@ __device__ inline void nonbonded_table(const Lig& L, int na, const float* xp, fl
   }
 }
 
+// Step 2a: the bonded forces gathered over the lanes' balanced runs of the atom-sorted slot list
+// (the gather schedule): each lane adds its run in order and stores the partial sum of every atom
+// it ends in that atom's last slot of the run.
+__device__ inline void gather_runs(const Lig& L, const LigandLayout& LL, float4* sl) {
+  const int lane = threadIdx.x & 31;
+  float ax = 0.f, ay = 0.f, az = 0.f;
+  const uint2* gs = L.gs + lane;
+  for (int j = 0; j < LL.gs_iters; ++j) {
+    const uint2 w = gs[32 * j];
+    const uint32_t e[4] = {w.x & 0xffffu, w.x >> 16, w.y & 0xffffu, w.y >> 16};
+    float4 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = sl[e[k] & 0x7fffu];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ax += v[k].x;
+      ay += v[k].y;
+      az += v[k].z;
+      if (e[k] & 0x8000u) {
+        sl[e[k] & 0x7fffu] = make_float4(ax, ay, az, 0.f);
+        ax = ay = az = 0.f;
+      }
+    }
+  }
+}
+
 // Forces on the lane's atoms (and, if ENERGY, the lane's partial energies).  xs holds all
-// positions (x, y, z, q); sf is the warp's bonded-slot scratch (3 * n_slots floats).
+// positions (x, y, z, q); sl is the warp's bonded-slot scratch (n_slots + 1 float4, the last zero).
 template <int APL, bool ENERGY, bool TABLE = false, bool FORCES = true>
-__device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const GridDev& G, const float4* xs, float* sf,
+__device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const GridDev& G, const float4* xs, float4* sl,
                                 const float (&x)[APL][3], float (&F)[APL][3], float w_sg, float w_g, bool all_grids,
                                 Energies& en, int& outside, const float* xp = nullptr) {
   const int lane = threadIdx.x & 31;
-  const int na = LL.na, ns = LL.n_slots;
-  float* sx = sf;
-  float* sy = sf + ns;
-  float* sz = sf + 2 * ns;
-  float el = bonded_terms<ENERGY, FORCES>(L, LL, xs, sx, sy, sz);
+  const int na = LL.na;
+  float el = bonded_terms<ENERGY, FORCES>(L, LL, xs, sl);
   __syncwarp();
+  if (FORCES) {
+    gather_runs(L, LL, sl);
+    __syncwarp();
+  }
   const bool hard = all_grids || w_g != 0.f;
   const bool soft = all_grids || w_sg != 0.f;
   float eg = 0.f, esg = 0.f;
@@ -490,12 +514,12 @@ __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const Grid
       esg += go.e_sg;
       outside += go.outside ? 1 : 0;
     }
-    const int b1 = FORCES ? L.inc_start[i + 1] : 0;
-    for (int b = FORCES ? L.inc_start[i] : 0; b < b1; ++b) {
-      const uint32_t s = L.inc[b];
-      F[a][0] += sx[s];
-      F[a][1] += sy[s];
-      F[a][2] += sz[s];
+    if (FORCES) {  // the atom's partial sums, in run order
+      const uint2 p = L.gp[i];
+      const float4 q0 = sl[p.x & 0xffffu], q1 = sl[p.x >> 16], q2 = sl[p.y & 0xffffu], q3 = sl[p.y >> 16];
+      F[a][0] += ((q0.x + q1.x) + q2.x) + q3.x;
+      F[a][1] += ((q0.y + q1.y) + q2.y) + q3.y;
+      F[a][2] += ((q0.z + q1.z) + q2.z) + q3.z;
     }
   }
   if (TABLE) nonbonded_table<APL, ENERGY, FORCES>(L, na, xp, F, el);
@@ -553,8 +577,8 @@ __device__ inline void stage_ligand(uint32_t* s, const uint32_t* __restrict__ bl
 
 // Shared memory of one block: ligand blob, then per warp 32*APL float4 positions, with the pair
 // table also the pair-interleaved mirror of the pair loop (32*APL * 4 floats), and the bonded-slot
-// scratch (3 * n_slots floats, rounded up to 16 bytes).
-__host__ __device__ inline int scratch_words(const LigandLayout& L) { return (3 * L.n_slots + 3) & ~3; }
+// scratch (n_slots + 1 float4, the last a zero slot).
+__host__ __device__ inline int scratch_words(const LigandLayout& L) { return 4 * (L.n_slots + 1); }
 __host__ __device__ inline int warp_words(const LigandLayout& L, int apl, bool table) {
   return (table ? 8 : 4) * 32 * apl + scratch_words(L);
 }
@@ -562,13 +586,15 @@ __host__ __device__ inline int warp_words(const LigandLayout& L, int apl, bool t
 struct WarpSmem {
   float4* xs;
   float* xp;  // pair-interleaved positions (table kernels only)
-  float* sf;
+  float4* sl;  // bonded-force slots
 };
 template <int APL, bool TABLE = false>
 __device__ inline WarpSmem warp_smem(uint32_t* smem, int staged_words, const LigandLayout& LL, int warp) {
   uint32_t* p = smem + staged_words + warp * warp_words(LL, APL, TABLE);
   float* xp = TABLE ? (float*)(p + 4 * 32 * APL) : nullptr;
-  return WarpSmem{(float4*)p, xp, (float*)(p + (TABLE ? 8 : 4) * 32 * APL)};
+  float4* sl = (float4*)(p + (TABLE ? 8 : 4) * 32 * APL);
+  if ((threadIdx.x & 31) == 0) sl[LL.n_slots] = make_float4(0.f, 0.f, 0.f, 0.f);  // the zero slot
+  return WarpSmem{(float4*)p, xp, sl};
 }
 
 struct HmcArgs {
@@ -593,43 +619,19 @@ struct HmcArgs {
   const BatchLigand* bligs;
   const BatchItem* items;
   int x_stride;
+  unsigned long long* work;  // single-ligand launches: replicas handed out so far (zero at launch), or NULL
 };
 
-// WPB warps per block; TABLE: the pair table is staged with the blob (16-warp blocks share it).
-// BATCH: the block's ligand and replicas come from its work item (a run of up to WPB replicas of
-// one ligand of a multi-ligand batch) and positions are stored x_stride atoms apart.
-template <int APL, int WPB, bool TABLE, bool BATCH = false>
-__global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ LigandLayout s_ll;
-  const uint32_t* blob = A.blob;
-  int64_t r_first = (int64_t)blockIdx.x * WPB;
-  int count = WPB;
-  if (BATCH) {
-    const BatchItem it = A.items[blockIdx.x];
-    if (threadIdx.x == 0) s_ll = A.bligs[it.lig].LL;
-    blob = A.blob + A.bligs[it.lig].blob_off;
-    r_first = it.r0;
-    count = it.count;
-    __syncthreads();
-  }
-  const LigandLayout& LL = BATCH ? s_ll : A.LL;
-  const int staged = TABLE ? LL.words_pair : LL.words;
-  stage_ligand(smem, blob, staged);
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp >= count) return;
-  const int64_t r = r_first + warp;
-  if (r >= A.n_rep) return;
-  const Lig L = bind_ligand(smem, LL);
-  const WarpSmem ws = warp_smem<APL, TABLE>(smem, staged, LL, warp);
+// One HMC trial of replica r by the calling warp: momenta, n_steps of velocity Verlet, the
+// Metropolis test, and the write-back of an accepted trial.  xs / xp / sl are the warp's
+// shared-memory arrays (the zero partner of an odd atom count is already in xp).
+template <int APL, bool TABLE, bool BATCH>
+__device__ __forceinline__ void hmc_trial(const HmcArgs& A, const LigandLayout& LL, const Lig& L, const WarpSmem& ws,
+                                          int64_t r) {
+  const int lane = threadIdx.x & 31;
   float4* xs = ws.xs;
   float* xp = ws.xp;
   const int na = LL.na;
-  if (TABLE && (na & 1) && lane == 0) {  // the zero partner that completes the last pair
-    put_pair_pos(xp, na, 0.f, 0.f, 0.f);
-    xp[8 * (na >> 1) + 7] = 0.f;
-  }
   const int64_t xstride = BATCH ? A.x_stride : na;
   const int k = A.state_of[r];
   if ((unsigned)k >= (unsigned)A.n_states) {  // invalid state index: leave the replica untouched
@@ -685,7 +687,7 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
   int outside = 0;
   Energies en;
   double c[4];
-  evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside, xp);
+  evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sl, x, F, st.w_sg_f, st.w_g_f, true, en, outside, xp);
   reduce_components(en, c);
   // the starting components go out now (a rejected trial leaves them); only U0 stays live
   const double U0 = weighted(c, st.w_sg, st.w_g);
@@ -720,9 +722,9 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
     }
     __syncwarp();
     if (s + 1 < A.n_steps) {
-      evaluate<APL, false, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, false, en, outside, xp);
+      evaluate<APL, false, TABLE>(LL, L, A.G, xs, ws.sl, x, F, st.w_sg_f, st.w_g_f, false, en, outside, xp);
     } else {
-      evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sf, x, F, st.w_sg_f, st.w_g_f, true, en, outside, xp);
+      evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sl, x, F, st.w_sg_f, st.w_g_f, true, en, outside, xp);
       reduce_components(en, c);
       U1 = weighted(c, st.w_sg, st.w_g);
     }
@@ -773,6 +775,58 @@ __global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
       if (out_total) atomicAdd((unsigned long long*)&A.counters[ALGDOCK_CNT_OUTSIDE], (unsigned long long)out_total);
     }
   }
+}
+
+
+// WPB warps per block; TABLE: the pair table is staged with the blob (16-warp blocks share it).
+// BATCH: the block's ligand and replicas come from its work item (a run of up to WPB replicas of
+// one ligand of a multi-ligand batch) and positions are stored x_stride atoms apart.
+// Otherwise, with A.work set, the blocks are persistent: each warp takes replicas from the work
+// counter until all n_rep are handed out, highest index first (the coupling leg, whose trials
+// gather the lattices, before the cheaper warming leg), so that no SM idles while another still
+// runs a last wave of blocks.  Which warp runs a replica does not change its result.
+template <int APL, int WPB, bool TABLE, bool BATCH = false>
+__global__ void __launch_bounds__(WPB * 32) hmc_kernel(const HmcArgs A) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ LigandLayout s_ll;
+  const uint32_t* blob = A.blob;
+  int64_t r_first = (int64_t)blockIdx.x * WPB;
+  int count = WPB;
+  if (BATCH) {
+    const BatchItem it = A.items[blockIdx.x];
+    if (threadIdx.x == 0) s_ll = A.bligs[it.lig].LL;
+    blob = A.blob + A.bligs[it.lig].blob_off;
+    r_first = it.r0;
+    count = it.count;
+    __syncthreads();
+  }
+  const LigandLayout& LL = BATCH ? s_ll : A.LL;
+  const int staged = TABLE ? LL.words_pair : LL.words;
+  stage_ligand(smem, blob, staged);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp >= count) return;
+  const Lig L = bind_ligand(smem, LL);
+  const WarpSmem ws = warp_smem<APL, TABLE>(smem, staged, LL, warp);
+  const int na = LL.na;
+  if (TABLE && (na & 1) && lane == 0) {  // the zero partner that completes the last pair
+    put_pair_pos(ws.xp, na, 0.f, 0.f, 0.f);
+    ws.xp[8 * (na >> 1) + 7] = 0.f;
+  }
+  if (!BATCH && A.work) {
+    for (;;) {
+      unsigned long long t = 0;
+      if (lane == 0) t = atomicAdd(A.work, 1ull);
+      t = __shfl_sync(kFull, t, 0);
+      if (t >= (unsigned long long)A.n_rep) break;
+      __syncwarp();  // the previous trial's reads of the warp's shared arrays are done
+      hmc_trial<APL, TABLE, BATCH>(A, LL, L, ws, A.n_rep - 1 - (int64_t)t);
+    }
+    return;
+  }
+  const int64_t r = r_first + warp;
+  if (r >= A.n_rep) return;
+  hmc_trial<APL, TABLE, BATCH>(A, LL, L, ws, r);
 }
 
 // Energy (and, with force != NULL, force) of stored configurations, one warp each.  With
@@ -826,7 +880,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) eval_kernel(const EvalArg
   __syncwarp();
   Energies en;
   int outside = 0;
-  evaluate<APL, true, false, FORCES>(A.LL, L, A.G, ws.xs, ws.sf, x, F, w_sg, w_g, true, en, outside);
+  evaluate<APL, true, false, FORCES>(A.LL, L, A.G, ws.xs, ws.sl, x, F, w_sg, w_g, true, en, outside);
   double c[4];
   reduce_components(en, c);
   if (FORCES && A.force) {
@@ -1063,16 +1117,30 @@ cudaError_t launch_hmc(cudaStream_t s, const algdock_ctx& c, int64_t n_rep, cons
                        int64_t rep_offset, int64_t* counters) {
   if (n_rep == 0) return cudaSuccess;
   HmcArgs A{c.grid, c.lig, c.d_blob, c.d_states, c.K, n_rep, state_of, x, comps, dH, acc, n_steps, seed,
-            (uint32_t)cycle, rep_offset, counters, nullptr, nullptr, 0};
+            (uint32_t)cycle, rep_offset, counters, nullptr, nullptr, 0, c.d_work};
   const int apl = atoms_per_lane(c.lig.na);
   // the pair table where 16-warp blocks can stage it (up to 64 atoms with a small topology);
   // otherwise the pair-type path in 4-warp blocks
-  const size_t tsmem = block_smem(c.lig, apl, kTableWarps, true);
-  if (hmc_uses_table(c.lig))
-    return launch_templated(hmc_kernel<1, kTableWarps, true>, hmc_kernel<2, kTableWarps, true>,
-                            hmc_kernel<2, kTableWarps, true>, apl, tsmem, n_rep, s, A, kTableWarps);
-  return launch_templated(hmc_kernel<1, kWarpsPerBlock, false>, hmc_kernel<2, kWarpsPerBlock, false>,
-                          hmc_kernel<3, kWarpsPerBlock, false>, apl, block_smem(c.lig, apl), n_rep, s, A);
+  const bool table = hmc_uses_table(c.lig);
+  void (*k)(const HmcArgs);
+  if (table) k = apl == 1 ? hmc_kernel<1, kTableWarps, true> : hmc_kernel<2, kTableWarps, true>;
+  else k = apl == 1 ? hmc_kernel<1, kWarpsPerBlock, false>
+                    : (apl == 2 ? hmc_kernel<2, kWarpsPerBlock, false> : hmc_kernel<3, kWarpsPerBlock, false>);
+  const int wpb = table ? kTableWarps : kWarpsPerBlock;
+  const size_t smem = table ? block_smem(c.lig, apl, kTableWarps, true) : block_smem(c.lig, apl);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // persistent blocks: as many as fit on the device at once, never more than the replicas need
+  int per_sm = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, wpb * 32, smem);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
+  if (e != cudaSuccess) return e;
+  const int64_t need = (n_rep + wpb - 1) / wpb;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * sms));
+  e = cudaMemsetAsync(c.d_work, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)blocks, wpb * 32, smem, s>>>(A);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ multi-ligand batches
@@ -1146,7 +1214,7 @@ cudaError_t launch_hmc_batch(cudaStream_t s, const algdock_ctx& c, const int32_t
                              double* dH, uint8_t* acc, int n_steps, uint64_t seed, uint64_t cycle, int64_t rep_offset,
                              int64_t* counters, int only_class) {
   HmcArgs A{c.grid, LigandLayout{}, c.d_batch_blob, c.d_states, c.K, c.batch_n_rep, state_of, x, comps, dH, acc,
-            n_steps, seed, (uint32_t)cycle, rep_offset, counters, c.d_batch, nullptr, c.batch_x_stride};
+            n_steps, seed, (uint32_t)cycle, rep_offset, counters, c.d_batch, nullptr, c.batch_x_stride, nullptr};
   int active[kBatchClasses], n_active = 0;
   for (int k = 0; k < kBatchClasses; ++k)
     if (c.batch_cls[k].n_items > 0 && (only_class < 0 || only_class == k)) active[n_active++] = k;

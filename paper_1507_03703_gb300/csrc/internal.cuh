@@ -110,16 +110,19 @@ struct StateDev {
 // Ligand blob header: word offsets (4-byte words, each section 16-byte aligned) into one
 // contiguous buffer that a CTA copies into shared memory.
 struct LigandLayout {
-  int na, nb, nang, ntor, ninc;
-  int n_slots;     // bonded force slots: 2 nb + 3 nang + 4 ntor
+  int na, nb, nang, ntor;
+  int gs_iters;    // iterations (of four entries each) of the bonded-force gather schedule per lane
+  int n_slots;     // bonded force slots: 2 nb + 3 nang + 4 ntor (float4 each), then one zero slot
   int off_atom_a;  // float4[na]: (accel factor 4.184e-4/m, q, sqrt(A), sqrt(B))
   int off_atom_b;  // float4[na]: (R*, sqrt(eps), m, sqrt(4.184e-4/m))
   int off_ptype;   // uint8[na][na], [j][i]: 0 nonbonded pair, 1 1-4 pair, 2 excluded (incl. i == j)
   int off_bond;    // float4[nb]: (i, j as int bits, k, r0)
   int off_ang;     // int4[nang] (i, j, k, 0) then float4[nang] (k, theta0, 0, 0)
   int off_tor;     // int4[ntor] (i, j, k, l), float4 (V1/2, V2/2, V3/2, 0), float4 cos(gamma), float4 sin(gamma)
-  int off_inc_start;  // int[na + 1]
-  int off_inc;        // uint32[ninc]: the bonded slots of each atom, in a fixed order
+  int off_gs;         // uint16[gs_iters][32][4]: lane l's run of the atom-sorted slot list, 4 per
+                      // iteration; bit 15 marks the last entry of an atom within the run (the
+                      // run's partial sum is stored in that slot); padding entries name the zero slot
+  int off_gp;         // uint16[na][4]: the slots holding atom i's partial sums (padded with the zero slot)
   int words;          // total of the sections above (multiple of 4)
   int off_pair;       // float4[(na + 1) / 2][na], [p][i]: for the partner pair j = 2p, 2p + 1,
                       // (e_ij, e_ij', c_ij, c_ij') with e = 12 eps_ij s_lj and c = 332 q_i q_j s_el,
@@ -226,6 +229,8 @@ struct algdock_ctx {
   size_t mbar_bytes = 0;
   // pinned host word for convergence polling
   int* h_flag = nullptr;
+  // work counter of the single-ligand HMC launch (replicas handed out to warps; zeroed per launch)
+  unsigned long long* d_work = nullptr;
   // learned proposal: torsion tree and scratch grown on demand
   algdock::LearnedTopo ltopo{};
   void* d_learn = nullptr;
