@@ -26,7 +26,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ligand atom-force evals/s"
 N_STATES_BC, N_STATES_CD, N_CHAINS, N_VV = 32, 96, 64, 50
-FP32_LANES_PER_SM, N_SM = 128, 152
+FP32_LANES_PER_SM = 128
 
 
 def parse():
@@ -216,10 +216,11 @@ def mbar_hbm_roofline(ctx, dev, K=256, n_per=3907, short=4, long=14):
 
 
 def gather_bytes_per_launch(alpha, R_per_state, n_atoms, n_steps):
-    """Useful lattice bytes of one HMC launch: every atom of every replica gathers the 8 corners of
-    the hard lattice (16 B each) where the state's FP32 weight alpha_g is nonzero and of the soft
-    lattice (8 B each) where alpha_sg is, in each of the n_steps - 1 force-only evaluations, and
-    both lattices in the two energy evaluations (first and last).  Weights of Eq. (protocol)."""
+    """Useful lattice bytes of one HMC launch, 32 B per active grid per atom and evaluation (8
+    corners x 4 B): the three full grids (96 B) where the state's FP32 weight alpha_g is nonzero and
+    the two soft grids (64 B) where alpha_sg is, in each of the n_steps - 1 force-only evaluations,
+    and all five in the two energy evaluations (first and last).  The padding lane of the stored
+    full-grid records is not counted.  Weights of Eq. (protocol)."""
     out = 0.0
     for a in alpha:
         if np.isnan(a):
@@ -229,13 +230,14 @@ def gather_bytes_per_launch(alpha, R_per_state, n_atoms, n_steps):
             z = 1000.0 * (a - 0.5)
             lg = 1.0 / (1.0 + np.exp(-z)) if z >= 0 else np.exp(z) / (1.0 + np.exp(z))
             w_sg, w_g = 1.0 - s_ * s_, s_ * s_ * lg
-        gated = 128.0 * (np.float32(w_g) != 0) + 64.0 * (np.float32(w_sg) != 0)
-        out += R_per_state * n_atoms * (2 * 192.0 + (n_steps - 1) * gated)
+        gated = 96.0 * (np.float32(w_g) != 0) + 64.0 * (np.float32(w_sg) != 0)
+        out += R_per_state * n_atoms * (2 * 160.0 + (n_steps - 1) * gated)
     return out
 
 
 def gather_peak(ctx, stream, n_cells=8 * 1024 * 1024, reps=5):
-    """Measured rate (useful GB/s) of random 8-corner gathers from both loaded lattices."""
+    """Measured rate of random 8-corner gathers from both loaded lattices, in the useful bytes of
+    gather_bytes_per_launch (160 B per cell: five grids x 8 corners x 4 B)."""
     import torch
     sink = ctx.gather_probe(n_cells, soft=True, seed=1)
     ms = []
@@ -247,24 +249,7 @@ def gather_peak(ctx, stream, n_cells=8 * 1024 * 1024, reps=5):
         torch.cuda.synchronize()
         if r >= 2:
             ms.append(e0.elapsed_time(e1))
-    return n_cells * 192.0 / (float(np.median(ms)) * 1e-3) / 1e9
-
-
-def profiled_traffic(profile="hmc_kernel_paper_scale.md", source="hmc.cu"):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source
-    of the kernel's file (else None)."""
-    import hashlib
-    key = source.replace(".", "_") + "_sha256:"
-    try:
-        text = open(os.path.join(ROOT, "profiles", profile)).read()
-        vals = dict(l.strip().split(": ", 1) for l in text.splitlines() if l.strip().startswith(
-            ("traffic_bytes_per_launch:", key)))
-        src = open(os.path.join(ROOT, "paper_1507_03703_gb300", "csrc", source), "rb").read()
-        if hashlib.sha256(src).hexdigest() != vals[key[:-1]]:
-            return None
-        return int(vals["traffic_bytes_per_launch"])
-    except Exception:
-        return None
+    return n_cells * 160.0 / (float(np.median(ms)) * 1e-3) / 1e9
 
 
 def measured_peaks():
@@ -284,7 +269,8 @@ def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=4
     import torch
 
     from paper_1507_03703_gb300 import synthetic as S
-    from paper_1507_03703_gb300.learned import LearnedProposal, effective_samples
+    from paper_1507_03703_gb300.learned import LearnedProposal
+    from paper_1507_03703_gb300.sampler import effective_samples
     lig = sys_.ligand
     base = S.place_ligand(lig, sys_.receptor, sys_.site, 128, seed=seed, n_tries=8).astype(np.float32)
     x = torch.from_numpy(base[np.arange(chains) % 128]).to(dev)
@@ -333,7 +319,7 @@ def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=4
             series.append(comps[:, 3].clone())
             torch.cuda.synchronize()
             t += ev[0].elapsed_time(ev[1])
-        ess = effective_samples(torch.stack(series).cpu().numpy())
+        ess = effective_samples(ctx, torch.stack(series))
         out[mode] = {"ess": ess, "ms": t, "ess_per_s": ess / (t * 1e-3)}
         if mode == "learned":
             out[mode]["move_acceptance"] = float(acc.sum().item()) / (chains * cmp_cycles * n_moves)
@@ -351,50 +337,31 @@ def _target_psi_g(run, li, k_local):
     return run.comps[sl].view(run.C, leg.K, 4)[torch.arange(run.C, device=st.device), slot, 3].clone()
 
 
-def profiled_bpmf_ref():
-    """The converged BPMF of the paper-scale workload from the committed convergence study, if
-    present: (value in kT, source)."""
+BPMF_REFERENCE = os.path.join(ROOT, "bpmf_reference.json")
+
+
+def bpmf_reference():
+    """The converged BPMF of the paper-scale workload from bpmf_reference.json (written by
+    bpmf_reference.py from independent long realizations of both iterations), or None."""
     try:
-        path = os.path.join(ROOT, "profiles", "bpmf_convergence_paper_scale.md")
-        for line in open(path):
-            if line.strip().startswith("bpmf_ref_kT:"):
-                return float(line.split(":", 1)[1]), "profiles/bpmf_convergence_paper_scale.md"
+        return json.load(open(BPMF_REFERENCE))
     except Exception:
-        pass
-    return None, None
+        return None
 
 
-def bpmf_convergence(ctx, sys_, stream, dev, paper_cycles=8000, learned_cycles=8000, window=1000, warm=200,
-                     n_external=20, n_learned=4, train_iter=300, seed=11, criterion=0.2):
-    """BPMF effective samples per second of the paper's iteration (an HMC move and 20
-    external-coordinate moves at alpha < 0.01 per replica, then 25 exchange sweeps) and of the same
-    iteration plus 4 rigid-body learned moves per replica, over both legs (64 chains x 128 states).
-    Both start from one warm state (`warm` cycles of the paper's iteration, whose poses at every
-    state also train the network).  Every `window` cycles: the window's BPMF (MBAR per leg over its
-    snapshots, one every 10 cycles), the ESS of the Psi_g series at the target state (alpha = 1,
-    300 K; sum over chains of N/g) and the GPU time of its cycles.  An arm's BPMF effective samples
-    per second count only the windows from the first one within `criterion` kT of B_ref on; B_ref is
-    the converged value of the committed convergence study, else the learned arm's second half."""
+def bpmf_warm(ctx, sys_, seed, warm=200, n_external=20, train_iter=300):
+    """The common start of the BPMF study's arms: `warm` cycles of the paper's iteration from seeded
+    placements (both legs, 64 chains x 128 states), and a learned proposal (rigid-body moves)
+    trained on that run's poses at every state.  Returns (run, proposal, training summary)."""
     import torch
 
     from paper_1507_03703_gb300 import synthetic as S
-    from paper_1507_03703_gb300.learned import LearnedProposal, effective_samples
-    from paper_1507_03703_gb300.sampler import Leg, ReplicaExchange, bpmf_kT
-    lig = sys_.ligand
+    from paper_1507_03703_gb300.learned import LearnedProposal
+    from paper_1507_03703_gb300.sampler import Leg, ReplicaExchange
     legs = [Leg(N_STATES_BC, 0), Leg(N_STATES_CD, N_STATES_BC)]
     R = N_CHAINS * (N_STATES_BC + N_STATES_CD)
-    base = S.place_ligand(lig, sys_.receptor, sys_.site, 128, seed=seed, n_tries=8).astype(np.float32)
-    x0 = base[np.arange(R) % base.shape[0]]
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-
-    def window_bpmf(run):
-        f = []
-        for li in range(len(legs)):
-            f.append(run.free_energies(li, max_iter=20000)[0])
-        run.history = []
-        return float(bpmf_kT(f[0], f[1]))
-
-    pre = ReplicaExchange(ctx, legs, N_CHAINS, x0, seed=seed, n_external=n_external)
+    base = S.place_ligand(sys_.ligand, sys_.receptor, sys_.site, 128, seed=seed, n_tries=8).astype(np.float32)
+    pre = ReplicaExchange(ctx, legs, N_CHAINS, base[np.arange(R) % base.shape[0]], seed=seed, n_external=n_external)
     ctx.reduced_energies(R, x=pre.x, comps=pre.comps)
     xs, cs, ss = [], [], []
     for cyc in range(warm):
@@ -405,69 +372,125 @@ def bpmf_convergence(ctx, sys_, stream, dev, paper_cycles=8000, learned_cycles=8
             ss.append(pre.state_of.clone())
     lp = LearnedProposal(ctx, seed=seed, n_torsions=0)
     losses = lp.train(torch.cat(xs), torch.cat(cs), torch.cat(ss).cpu().numpy(), n_iter=train_iter, seed=seed)
+    return pre, lp, {"poses": int(sum(x.shape[0] for x in xs)), "iters": train_iter, "loss_first": losses[0],
+                     "loss_last": losses[-1]}
+
+
+def bpmf_arm(ctx, stream, dev, pre, lp, n_cyc, window, seed, n_external=20, n_learned=4):
+    """One arm from the warm state: the paper's iteration (lp None: an HMC move and the
+    external-coordinate moves at alpha < 0.01 per replica, then 25 exchange sweeps) or the same plus
+    n_learned learned moves per replica.  Every `window` cycles: the window's BPMF (MBAR per leg
+    over snapshots every 10 cycles), the effective samples of the Psi_g series at the target state
+    (alpha = 1, 300 K) per chain (N / g from the library's estimator) and the GPU time."""
+    import torch
+
+    from paper_1507_03703_gb300.sampler import ReplicaExchange, bpmf_kT, effective_samples
+    legs = pre.legs
+    R = pre.R
+    run = ReplicaExchange(ctx, legs, N_CHAINS, pre.x.cpu().numpy(), seed=seed, n_external=n_external)
+    run.comps.copy_(pre.comps)
+    run.state_of.copy_(pre.state_of)
+    for li in range(len(legs)):
+        run.config_of[li].copy_(pre.config_of[li])
+    acc = torch.zeros(R, dtype=torch.int32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    wins, series, full, ms = [], [], [], 0.0
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for cyc in range(n_cyc):
+        run.hmc(cyc, N_VV)
+        run.external(cyc)
+        if lp is not None:
+            lp.propose(run.state_of, run.x, run.comps, n_learned, seed=seed + 1, cycle=cyc, accepted=acc)
+        run.exchange(cyc)
+        if cyc % 10 == 0:
+            run.history.append(run.comps.clone())
+        series.append(_target_psi_g(run, 1, N_STATES_CD - 1))
+        full.append(series[-1])
+        if (cyc + 1) % window == 0:
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            w_ms = ev[0].elapsed_time(ev[1])
+            ms += w_ms
+            S_ = torch.stack(series)
+            g, _, _ = ctx.detect_equilibration(S_, n_cand=1)
+            ess_chain = (S_.shape[0] / g[:, 0]).cpu().numpy()
+            f = [run.free_energies(li, max_iter=20000)[0] for li in range(len(legs))]
+            run.history = []
+            wins.append({"cycles": cyc + 1, "bpmf_kT": float(bpmf_kT(f[0], f[1])), "ess": float(ess_chain.sum()),
+                         "ess_chain": ess_chain.tolist(), "gpu_ms": w_ms})
+            series = []
+            ev[0].record(stream)
+    _, t0s, neffs = ctx.detect_equilibration(torch.stack(full), stride=max(1, n_cyc // 40))
+    out = {"cycles": n_cyc, "gpu_ms_per_cycle": ms / max(1, n_cyc), "windows": wins,
+           "equilibration_cycles_median": float(t0s.double().median().item()),
+           "n_eff_after_equilibration": float(neffs.sum().item()),
+           "external_acceptance": float(run.ext_acc.sum().item()) / max(1, n_external * n_cyc * N_CHAINS)}
+    if lp is not None:
+        out["learned_acceptance"] = float(acc.sum().item()) / (R * n_learned * n_cyc)
+    return out
+
+
+def in_band_from(windows, b_ref, criterion):
+    """Index of the first window from which every later window's BPMF stays within `criterion` of
+    b_ref (None if the last window is outside)."""
+    first = None
+    for i in range(len(windows) - 1, -1, -1):
+        if abs(windows[i]["bpmf_kT"] - b_ref) <= criterion:
+            first = i
+        else:
+            break
+    return first
+
+
+def bpmf_convergence(ctx, sys_, stream, dev, paper_cycles=8000, learned_cycles=8000, window=1000, warm=200,
+                     n_external=20, n_learned=4, train_iter=300, seed=11, criterion=0.2, n_boot=2000):
+    """BPMF effective samples per second of the paper's iteration and of the same plus learned
+    moves, at the criterion of `criterion` kT from the reference BPMF of bpmf_reference.json.  An
+    arm is credited only with the windows from the last entry into the band on, and only if it stays
+    there to the end.  The learned/plain ratio comes with a 95 % bootstrap interval over chains (the
+    per-chain effective samples of the credited windows resampled)."""
+    pre, lp, training = bpmf_warm(ctx, sys_, seed, warm, n_external, train_iter)
     out = {"workload": "both legs, %d chains x %d states, %d VV steps" % (N_CHAINS, N_STATES_BC + N_STATES_CD, N_VV),
            "target_state": "alpha = 1, 300 K", "warm_cycles": warm, "window_cycles": window,
-           "criterion_kT": criterion, "learned_training": {"poses": int(sum(x.shape[0] for x in xs)),
-                                                           "iters": train_iter, "loss_first": losses[0],
-                                                           "loss_last": losses[-1]}}
-    arms = {}
-    for name, n_cyc in (("paper", paper_cycles), ("learned", learned_cycles)):
-        run = ReplicaExchange(ctx, legs, N_CHAINS, x0, seed=seed + 1, n_external=n_external)
-        run.x.copy_(pre.x)
-        run.comps.copy_(pre.comps)
-        run.state_of.copy_(pre.state_of)
-        for li in range(len(legs)):
-            run.config_of[li].copy_(pre.config_of[li])
-        acc = torch.zeros(R, dtype=torch.int32, device=dev)
-        wins, series, full, ms = [], [], [], 0.0
-        torch.cuda.synchronize()
-        ev[0].record(stream)
-        for cyc in range(n_cyc):
-            run.hmc(cyc, N_VV)
-            run.external(cyc)
-            if name == "learned":
-                lp.propose(run.state_of, run.x, run.comps, n_learned, seed=seed + 2, cycle=cyc, accepted=acc)
-            run.exchange(cyc)
-            if cyc % 10 == 0:
-                run.history.append(run.comps.clone())
-            series.append(_target_psi_g(run, 1, N_STATES_CD - 1))
-            full.append(series[-1])
-            if (cyc + 1) % window == 0:
-                ev[1].record(stream)
-                torch.cuda.synchronize()
-                w_ms = ev[0].elapsed_time(ev[1])
-                ms += w_ms
-                ess = effective_samples(torch.stack(series).cpu().numpy())
-                wins.append({"cycles": cyc + 1, "bpmf_kT": window_bpmf(run), "ess": ess, "gpu_ms": w_ms})
-                series = []
-                ev[0].record(stream)
-        # automated equilibration detection on each chain's target-state series (the kernel)
-        _, t0s, neffs = ctx.detect_equilibration(torch.stack(full), stride=max(1, n_cyc // 40))
-        arms[name] = {"cycles": n_cyc, "gpu_ms_per_cycle": ms / max(1, n_cyc), "windows": wins,
-                      "equilibration_cycles_median": float(t0s.double().median().item()),
-                      "n_eff_after_equilibration": float(neffs.sum().item()),
-                      "external_acceptance": float(run.ext_acc.sum().item()) / max(1, n_external * n_cyc * N_CHAINS)}
-        if name == "learned":
-            arms[name]["learned_acceptance"] = float(acc.sum().item()) / (R * n_learned * n_cyc)
-        del run
-    b_ref, src = profiled_bpmf_ref()
-    if b_ref is None:
-        late = [w["bpmf_kT"] for w in arms["learned"]["windows"]]
-        late = late[len(late) // 2:]
-        b_ref, src = float(np.mean(late)), "this run: mean of the learned arm's second-half windows"
-    out["reference"] = {"bpmf_kT": b_ref, "source": src}
+           "criterion_kT": criterion, "learned_training": training}
+    ref = bpmf_reference()
+    if ref is None:
+        out["reference"] = None
+        out["note"] = "no bpmf_reference.json: no arm is credited"
+    else:
+        out["reference"] = {k: ref[k] for k in ("bpmf_kT", "spread_kT", "sem_kT", "realizations", "source")}
+    arms = {"paper": bpmf_arm(ctx, stream, dev, pre, None, paper_cycles, window, seed + 1, n_external, n_learned),
+            "learned": bpmf_arm(ctx, stream, dev, pre, lp, learned_cycles, window, seed + 1, n_external, n_learned)}
+    rng = np.random.default_rng(seed)
+    boot = {}
     for name, a in arms.items():
-        first = next((i for i, w in enumerate(a["windows"]) if abs(w["bpmf_kT"] - b_ref) <= criterion), None)
+        a["final_bpmf_kT"] = a["windows"][-1]["bpmf_kT"] if a["windows"] else None
+        first = in_band_from(a["windows"], ref["bpmf_kT"], criterion) if ref else None
         if first is None:
-            a["cycles_to_criterion"] = None
+            a["credited_from_cycles"] = None
             a["bpmf_eff_samples_per_s"] = 0.0
         else:
             done = a["windows"][first:]
-            a["cycles_to_criterion"] = a["windows"][first]["cycles"]
-            a["gpu_s_to_criterion"] = sum(w["gpu_ms"] for w in a["windows"][:first + 1]) * 1e-3
-            a["bpmf_eff_samples_per_s"] = sum(w["ess"] for w in done) / (sum(w["gpu_ms"] for w in done) * 1e-3)
-        a["final_abs_err_kT"] = abs(a["windows"][-1]["bpmf_kT"] - b_ref) if a["windows"] else None
+            a["credited_from_cycles"] = a["windows"][first]["cycles"] - window
+            gpu_s = sum(w["gpu_ms"] for w in done) * 1e-3
+            per_chain = np.sum([w["ess_chain"] for w in done], axis=0)
+            a["bpmf_eff_samples_per_s"] = float(per_chain.sum() / gpu_s)
+            idx = rng.integers(0, per_chain.size, size=(n_boot, per_chain.size))
+            boot[name] = per_chain[idx].sum(axis=1) / gpu_s
+        if ref:
+            a["final_abs_err_kT"] = abs(a["final_bpmf_kT"] - ref["bpmf_kT"])
+        for w in a["windows"]:
+            w.pop("ess_chain")
         out[name] = a
+    if "paper" in boot and "learned" in boot:
+        r = boot["learned"] / boot["paper"]
+        out["learned_vs_paper"] = {"ratio": arms["learned"]["bpmf_eff_samples_per_s"] /
+                                            arms["paper"]["bpmf_eff_samples_per_s"],
+                                   "ci95": [float(np.percentile(r, 2.5)), float(np.percentile(r, 97.5))]}
+    else:
+        out["learned_vs_paper"] = {"ratio": None, "note": "an arm is not within the criterion at its end: "
+                                                           "no ratio"}
     return out
 
 
@@ -699,7 +722,8 @@ def fep_endpoint(ctx, run, sys_, stream, sm_max, n_samples=16384, first_cycle=30
         fe.append(e[1].elapsed_time(e[2]))
     ti_ms, fe_ms = float(np.median(ti)), float(np.median(fe))
     pairs = n_samples * lig.n_atoms * rec.n_atoms
-    peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = pairs * FLOPS_PER_TARGET_PAIR / (ti_ms * 1e-3) / 1e12
     return {"samples": n_samples, "milestone": "D (alpha = 1, 300 K)", "f_DE_kT": r["f"], "sigma_kT": r["sigma"],
             "n_eff": r["n_eff"], "min_target_interaction_kcal": float(psi_t.min().item()),
@@ -707,9 +731,9 @@ def fep_endpoint(ctx, run, sys_, stream, sm_max, n_samples=16384, first_cycle=30
             "configurations_per_s": n_samples / ((ti_ms + fe_ms) * 1e-3),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "kernel": "target_interaction_kernel",
-                         "traffic": profiled_traffic("target_interaction_paper_scale.md", "endpoints.cu"),
+                         "traffic": None, "traffic_ncu_summary": "profiles/target_interaction_paper_scale.md",
                          "flops_per_launch": pairs * FLOPS_PER_TARGET_PAIR,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_max}}
+                         "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % (n_sm, sm_max)}}
 
 
 def oracle_cpu_baseline(sys_, n_rep=65536, n_threads=0):
@@ -887,14 +911,16 @@ def main():
     # roofline of the dominant kernel (the fused HMC trial), FP32 ALU bound
     peaks = measured_peaks()
     sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     fl = flops_per_replica_eval(lig) * R * (N_VV + 1)
     hmc_avg = sum(hmc_ms) / len(hmc_ms)
     achieved = fl / (hmc_avg * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": profiled_traffic(),
+                "frac": achieved / peak_tflops, "traffic": None,
+                "traffic_ncu_summary": "profiles/hmc_kernel_paper_scale.md",
                 "kernel": "hmc_kernel", "kernel_ms": hmc_avg,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_max,
+                "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % (n_sm, sm_max),
                 "flops_per_launch": fl}
 
     # the same kernel against the L2 gather roofline: useful lattice bytes per launch over the

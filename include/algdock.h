@@ -10,7 +10,7 @@
  * probe; ligand and states; sampling (HMC trial, external-coordinate moves, forces and energies,
  * replica exchange); estimation (u_kn, MBAR, equilibration detection); protocol initialization;
  * multi-ligand batches; the end points (target force field and free energy perturbation); the
- * learned pose proposal; the allocation-free MBAR.
+ * learned pose proposal; checkpoint and resume; the allocation-free MBAR.
  *
  * Conventions for every call:
  *  - Units: A, kcal/mol, amu, fs, K, elementary charge.
@@ -232,6 +232,33 @@ algdock_status algdock_exchange(algdock_ctx* ctx, int32_t n_ladders, int32_t K, 
                                 int32_t max_sep, uint64_t seed, uint64_t cycle, int64_t ladder_offset,
                                 int64_t* attempts, int64_t* accepts);
 
+/* One iteration of the paper's loop over a whole run ("Equilibration and production"):
+ * an HMC trial of every replica at its state (as algdock_hmc_cycle), then n_sweeps exchange sweeps
+ * on every ladder of every leg (as algdock_exchange), and, if u_kn is given, the snapshot: every
+ * configuration re-evaluated and its reduced energies at every state of its leg (as
+ * algdock_reduced_energies).  Replicas are leg-major: leg l's chain c holds slots
+ * base_l + c K_l + i, base_l = n_chains sum_{m<l} K_m, with config_of laid out the same way
+ * ([n_chains][K_l] per leg).  Leg l's ladders are numbered ladder_offset + l n_chains.
+ *   x [R][n_atoms][3] float, comps [R][4] double, state_of [R] int32, config_of [R] int32: each host
+ *   or device (cudaPointerGetAttributes), read and written; counters [ALGDOCK_N_COUNTERS] int64
+ *   (may be NULL) host or device, added to; u_kn (may be NULL) host or device out, leg after leg
+ *   [K_l][n_chains K_l] double.
+ * Host arrays are copied into device memory the context owns, and back after the cycle; the call
+ * then synchronises.  With device arrays only it is asynchronous like the other calls. */
+#define ALGDOCK_MAX_LEGS 8
+typedef struct {
+  int32_t n_legs;
+  int32_t K[ALGDOCK_MAX_LEGS];            /* states per leg */
+  int32_t state_offset[ALGDOCK_MAX_LEGS]; /* each leg's first state in the context's table */
+  int32_t n_chains;
+  int32_t n_steps;                        /* velocity-Verlet steps per HMC trial */
+  int32_t n_sweeps, max_sep;              /* exchange sweeps per cycle and largest separation */
+  uint64_t seed;
+  int64_t rep_offset, ladder_offset;      /* global index of the first replica and ladder */
+} algdock_run_desc;
+algdock_status algdock_cycle(algdock_ctx* ctx, const algdock_run_desc* desc, uint64_t cycle, float* x, double* comps,
+                             int32_t* state_of, int32_t* config_of, int64_t* counters, double* u_kn);
+
 /* ---------------------------------------------------------------- estimation */
 /* Reduced energies for MBAR ("Estimation").  If x ([N][n_atoms][3] float) is given, the energy
  * path evaluates each configuration's components into comps ([N][4] double, may then be NULL);
@@ -300,6 +327,31 @@ algdock_status algdock_resample(algdock_ctx* ctx, int64_t N, const double* comps
  * into *p (host).  FP64.  Synchronises. */
 algdock_status algdock_mean_pacc(algdock_ctx* ctx, int64_t N, const double* comps_a, const double* comps_b, int32_t ka,
                                  int32_t kb, double* p);
+
+/* The scalar steps of protocol initialization ("Initialization"), host arithmetic without a
+ * context.  A leg's states are placed one thermodynamic-length step apart from the standard
+ * deviations that algdock_state_statistics returns.
+ * Warming leg: T_next = min(T_end, T + speed k_B T^2 / sigma[U_S]) (T_end if sigma[U_S] = 0). */
+algdock_status algdock_next_temperature(double T, double sigma_U, double speed, double T_end, double* T_next);
+/* Coupling leg: alpha_next = min(1, alpha + speed / rate) with rate = |alpha_sg'| sigma[Psi_sg] /
+ * (k_B T) + |alpha_g'| sigma[Psi_g] / (k_B T) + |T_T - T_H| sigma[u] / T at T = T(alpha) =
+ * T_H + (T_T - T_H) alpha, the derivatives of the weights of Eq. (protocol) (1 if rate = 0). */
+algdock_status algdock_next_alpha(double alpha, double sigma_sg, double sigma_g, double sigma_u, double speed,
+                                  double T_T, double T_H, double* alpha_next);
+/* Time-step rule: HMC acceptance above 0.8: +0.125 fs; below 0.1: -0.5 fs; below 0.4: -0.25 fs;
+ * the result kept in [0.1, 5] fs. */
+algdock_status algdock_adapt_dt(double dt, double acceptance, double* dt_next);
+/* State insertion between cycles ("Equilibration and production"): after every neighbour pair
+ * (k, k+1) of a leg whose exchange acceptance accepts[k] / attempts[k] is below threshold (pairs
+ * never attempted are kept), a state at the midpoint of the leg's parameter: the geometric mean
+ * temperature on the warming leg (alpha NaN), the mean alpha with T(alpha) on the coupling leg; its
+ * time step is the smaller of the pair's.  Outputs (capacity >= 2K - 1): the new ladder
+ * (T_out, alpha_out, dt_out [*K_out]) and lower [*K_out]: -1 for a kept state, else the index of
+ * the inserted state's lower neighbour in the new ladder. */
+algdock_status algdock_insert_states(int32_t K, const double* T, const double* alpha, const double* dt,
+                                     const int64_t* attempts, const int64_t* accepts, double threshold, double T_T,
+                                     double T_H, int32_t capacity, int32_t* K_out, double* T_out, double* alpha_out,
+                                     double* dt_out, int32_t* lower);
 
 /* ---------------------------------------------------------------- multi-ligand batches
  * Many ligands of uneven size against one set of grids and one state table, every replica of every
@@ -459,6 +511,64 @@ algdock_status algdock_propose_learned(algdock_ctx* ctx, const float* params, co
                                        const int32_t* state_of, float* x, double* comps, int32_t n_moves,
                                        int32_t n_torsions, uint64_t seed, uint64_t cycle, int64_t rep_offset,
                                        int32_t* accepted, int64_t* counters);
+
+/* MBAR sharded over samples, for runs whose samples are spread over processes (one per GPU).  In
+ * the self-consistent equation above the sample sum of each state splits into per-process sums,
+ * while log D_n = ln sum_k N_k exp(f_k - u_kn) stays local to its sample.  One iteration is:
+ * algdock_mbar_partials on every process, one exchange of the K (max, sum) pairs between them, and
+ * algdock_mbar_update on every process with the pairs in the same (rank) order, which gives every
+ * process the same f.  The iteration count and the stopping rule are the caller's (as in
+ * algdock_mbar: stop when delta < tol). */
+
+/* This process's pairs: pairs [K][2] (host, out) with sum_n exp(-u_in - log D_n) = pairs[i][1] *
+ * exp(pairs[i][0]) over its N samples (max -inf, sum 0 for a state with none).  u_kn [K][N] double
+ * (device; may be NULL if N == 0), N_k [K] int64 (host): the counts over ALL processes; f [K]
+ * (host): the current estimate.  precision_mode 0 or 1 as for algdock_mbar.  Synchronises. */
+algdock_status algdock_mbar_partials(algdock_ctx* ctx, int32_t K, int64_t N, const double* u_kn, const int64_t* N_k,
+                                     const double* f, int32_t precision_mode, double* pairs);
+
+/* Host arithmetic, no context: merges each state's n_parts pairs (pairs [n_parts][K][2], merged
+ * in that order), f_i = -(M + ln S), gauge f_0 = 0, into f_new [K]; *delta = max_i |f_new - f_old|. */
+algdock_status algdock_mbar_update(int32_t K, int32_t n_parts, const double* pairs, const double* f_old,
+                                   double* f_new, double* delta);
+
+/* ---------------------------------------------------------------- checkpoint and resume
+ * The paper stores each stage's data between cycles so that a calculation interrupted on a shared
+ * machine restarts where it stopped ("Stages"; "Equilibration and production").  A checkpoint
+ * holds the context's state table (T, alpha and every state's time step, as last set by
+ * algdock_states_set), the run's seed and next cycle, a fingerprint (CRC-32) of the loaded ligand
+ * and lattice descriptor, and the caller's named arrays: whatever the run keeps between cycles
+ * (positions, components, state permutations, exchange counters, stored components).  The Philox
+ * counters of every step are functions of (seed, cycle, replica), so a run continued from a
+ * checkpoint repeats the uninterrupted run bit for bit.
+ * Format: one file, little-endian, "ALGDCKPT", version 1, sizes, the state table, the arrays (name
+ * up to 31 bytes, dtype, count, data) and a CRC-32 trailer over the whole file.  The file is
+ * written to a temporary name beside path and renamed over path.  Grids and ligand are inputs,
+ * not state: load them before algdock_checkpoint_load. */
+typedef enum { ALGDOCK_F32 = 1, ALGDOCK_F64 = 2, ALGDOCK_I32 = 3, ALGDOCK_I64 = 4, ALGDOCK_U8 = 5 } algdock_dtype;
+typedef struct {
+  char name[32];  /* NUL-terminated, unique within one checkpoint */
+  int32_t dtype;  /* algdock_dtype */
+  int64_t count;  /* elements */
+  void* data;     /* host or device; read by save, written by load */
+} algdock_array;
+
+/* Saves ctx's state table and fingerprints (ctx may be NULL: none are stored), seed, cycle and the
+ * n_arrays arrays to path.  Synchronises ctx's stream first.  ALGDOCK_E_INVALID: bad or duplicate
+ * names, unknown dtype, negative count, or the file cannot be written. */
+algdock_status algdock_checkpoint_save(algdock_ctx* ctx, const char* path, uint64_t seed, uint64_t cycle,
+                                       int32_t n_arrays, const algdock_array* arrays);
+
+/* Reads path, checks magic, version, sizes and the CRC (ALGDOCK_E_INVALID on any mismatch: a
+ * corrupt or truncated file changes nothing), then: with ctx, checks that the context's loaded
+ * ligand and lattice match the checkpoint's fingerprints (ALGDOCK_E_STATE otherwise) and restores
+ * the state table as algdock_states_set would; fills each array whose data is non-NULL from the
+ * array of the same name, which must exist with the same dtype and count (ALGDOCK_E_INVALID
+ * otherwise); for an array with data == NULL writes the file's dtype and count (count -1 if
+ * absent) instead, so that a caller can size its buffers first.  seed and cycle (may be NULL)
+ * receive the stored values.  ctx may be NULL (host arrays only, no state table). */
+algdock_status algdock_checkpoint_load(algdock_ctx* ctx, const char* path, uint64_t* seed, uint64_t* cycle,
+                                       int32_t n_arrays, algdock_array* arrays);
 
 /* MBAR without any device allocation.  The paper has no counterpart: this is a service of this
  * library for callers that cannot call cudaMalloc - for example a host framework whose caching

@@ -307,6 +307,29 @@ def mbar(u_kn, N_k, tol=1e-10, max_iter=10000):
     return f, it
 
 
+def mbar_partials(u_kn, N_k, f):
+    """The state sums of one MBAR iteration over a subset of the samples (Shirts & Chodera 2008, as
+    cited in "Estimation"): in f_i = -ln sum_n exp(-u_in) / D_n with
+    D_n = sum_k N_k exp(f_k - u_kn), the sum over n splits over any partition of the samples, while
+    D_n belongs to its own sample.  For the columns given, returns [K][2] pairs (M_i, S_i) with
+    sum_n exp(-u_in - ln D_n) = S_i exp(M_i) (M_i = -inf, S_i = 0 without samples).  N_k are the
+    counts over all samples.  FP64, numpy."""
+    u = np.asarray(u_kn, dtype=np.float64)
+    K = u.shape[0]
+    out = np.zeros((K, 2))
+    out[:, 0] = -np.inf
+    if u.shape[1] == 0:
+        return out
+    lw = np.log(np.asarray(N_k, dtype=np.float64))[:, None] + np.asarray(f, dtype=np.float64)[:, None] - u
+    c = lw.max(axis=0)
+    log_d = c + np.log(np.exp(lw - c).sum(axis=0))
+    a = -u - log_d[None, :]
+    m = a.max(axis=1)
+    out[:, 0] = m
+    out[:, 1] = np.exp(a - m[:, None]).sum(axis=1)
+    return out
+
+
 def statistical_inefficiency(a):
     a = _f64(a)
     return _load().oracle_statistical_inefficiency(a.size, a)

@@ -34,7 +34,9 @@ EXPORTS = [
     "algdock_mean_pacc", "algdock_receptor_load", "algdock_target_interaction", "algdock_fep",
     "algdock_batch_load", "algdock_batch_layout", "algdock_batch_hmc_cycle", "algdock_batch_tune",
     "algdock_hmc_shape", "algdock_batch_shapes", "algdock_gather_probe", "algdock_grids_load_f64",
-    "algdock_energy_force_f64",
+    "algdock_energy_force_f64", "algdock_checkpoint_save", "algdock_checkpoint_load", "algdock_mbar_partials",
+    "algdock_mbar_update", "algdock_next_temperature", "algdock_next_alpha", "algdock_adapt_dt",
+    "algdock_insert_states", "algdock_cycle",
 ]
 
 BATCH_CLASSES = 4             # launch classes of a multi-ligand batch
@@ -102,6 +104,26 @@ class RestraintC(C.Structure):
     _fields_ = [("site", C.c_double * 3), ("k", C.c_double), ("d0", C.c_double)]
 
 
+MAX_LEGS = 8
+
+
+class RunDescC(C.Structure):
+    """algdock_run_desc: the legs, chains and per-cycle settings of a run for algdock_cycle."""
+    _fields_ = [("n_legs", C.c_int32), ("K", C.c_int32 * MAX_LEGS), ("state_offset", C.c_int32 * MAX_LEGS),
+                ("n_chains", C.c_int32), ("n_steps", C.c_int32), ("n_sweeps", C.c_int32), ("max_sep", C.c_int32),
+                ("seed", C.c_uint64), ("rep_offset", C.c_int64), ("ladder_offset", C.c_int64)]
+
+
+class ArrayC(C.Structure):
+    """algdock_array: one named array of a checkpoint."""
+    _fields_ = [("name", C.c_char * 32), ("dtype", C.c_int32), ("count", C.c_int64), ("data", C.c_void_p)]
+
+
+# algdock_dtype codes
+F32, F64, I32, I64, U8 = 1, 2, 3, 4, 5
+_NP_DTYPE = {F32: np.float32, F64: np.float64, I32: np.int32, I64: np.int64, U8: np.uint8}
+
+
 _lib = None
 
 
@@ -154,6 +176,17 @@ def load_library(path: str = LIB_PATH):
         "algdock_mlp_grad": ([vp, vp, vp, i64, vp, vp, i32, vp, vp], C.c_int),
         "algdock_mlp_adam": ([vp, vp, vp, vp, vp, vp, i32, C.c_float], C.c_int),
         "algdock_propose_learned": ([vp, vp, vp, i64, vp, vp, vp, i32, i32, u64, u64, i64, vp, vp], C.c_int),
+        "algdock_mbar_partials": ([vp, i32, i64, vp, vp, vp, i32, vp], C.c_int),
+        "algdock_cycle": ([vp, C.POINTER(RunDescC), u64, vp, vp, vp, vp, vp, vp], C.c_int),
+        "algdock_mbar_update": ([i32, i32, vp, vp, vp, C.POINTER(dbl)], C.c_int),
+        "algdock_next_temperature": ([dbl, dbl, dbl, dbl, C.POINTER(dbl)], C.c_int),
+        "algdock_next_alpha": ([dbl, dbl, dbl, dbl, dbl, dbl, dbl, C.POINTER(dbl)], C.c_int),
+        "algdock_adapt_dt": ([dbl, dbl, C.POINTER(dbl)], C.c_int),
+        "algdock_insert_states": ([i32, vp, vp, vp, vp, vp, dbl, dbl, dbl, i32, C.POINTER(i32), vp, vp, vp, vp],
+                                  C.c_int),
+        "algdock_checkpoint_save": ([vp, C.c_char_p, u64, u64, i32, C.POINTER(ArrayC)], C.c_int),
+        "algdock_checkpoint_load": ([vp, C.c_char_p, C.POINTER(u64), C.POINTER(u64), i32, C.POINTER(ArrayC)],
+                                    C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -234,6 +267,82 @@ def grid_desc(grid) -> GridDesc:
         d.n[k] = int(grid.n[k])
     d.spacing = float(grid.spacing)
     return d
+
+
+def mbar_update(pairs, f_old):
+    """algdock_mbar_update: pairs [n_parts][K][2] (numpy, merged in that order), f_old [K] ->
+    (f_new [K], max |f_new - f_old|)."""
+    L = load_library()
+    pairs = np.ascontiguousarray(pairs, dtype=np.float64)
+    f_old = np.ascontiguousarray(f_old, dtype=np.float64)
+    n_parts, K = pairs.shape[0], pairs.shape[1]
+    f_new = np.empty(K)
+    d = C.c_double()
+    st = L.algdock_mbar_update(K, n_parts, pairs.ctypes.data, f_old.ctypes.data, f_new.ctypes.data, C.byref(d))
+    if st != OK:
+        raise AlgdockError(st, "mbar_update: bad arguments")
+    return f_new, d.value
+
+
+def _array_c(name, a):
+    """algdock_array for a contiguous torch tensor (device or host) or numpy array."""
+    code = None
+    if hasattr(a, "data_ptr"):
+        import torch
+        tmap = {torch.float32: F32, torch.float64: F64, torch.int32: I32, torch.int64: I64, torch.uint8: U8}
+        if not a.is_contiguous():
+            raise ValueError("checkpoint array %s must be contiguous" % name)
+        code, ptr, n = tmap.get(a.dtype), a.data_ptr(), a.numel()
+    else:
+        if not (isinstance(a, np.ndarray) and a.flags.c_contiguous):
+            raise ValueError("checkpoint array %s must be a C-contiguous numpy array" % name)
+        code = {np.dtype(v): k for k, v in _NP_DTYPE.items()}.get(a.dtype)
+        ptr, n = a.ctypes.data, a.size
+    if code is None:
+        raise ValueError("checkpoint array %s has an unsupported dtype" % name)
+    r = ArrayC()
+    r.name = name.encode()
+    r.dtype, r.count, r.data = code, int(n), ptr if n else None
+    return r
+
+
+def _ck_check(ctx, st, what):
+    if st != OK:
+        msg = ctx.last_error() if ctx is not None else what + " failed"
+        raise AlgdockError(st, msg)
+
+
+def checkpoint_save(ctx, path, seed, cycle, arrays):
+    """algdock_checkpoint_save: arrays is a dict name -> tensor / ndarray (ctx may be None)."""
+    L = load_library()
+    items = list(arrays.items())
+    arr = (ArrayC * max(1, len(items)))(*[_array_c(k, v) for k, v in items])
+    _ck_check(ctx, L.algdock_checkpoint_save(ctx.h if ctx is not None else None, str(path).encode(), int(seed),
+                                             int(cycle), len(items), arr), "checkpoint_save")
+
+
+def checkpoint_query(ctx, path, names):
+    """dtype code and element count of each named array of a checkpoint (count -1 if absent)."""
+    L = load_library()
+    arr = (ArrayC * max(1, len(names)))()
+    for i, n in enumerate(names):
+        arr[i].name = n.encode()
+        arr[i].data = None
+    _ck_check(ctx, L.algdock_checkpoint_load(ctx.h if ctx is not None else None, str(path).encode(), None, None,
+                                             len(names), arr), "checkpoint_query")
+    return {n: (arr[i].dtype, arr[i].count) for i, n in enumerate(names)}
+
+
+def checkpoint_load(ctx, path, arrays):
+    """algdock_checkpoint_load into the given buffers (dict name -> tensor / ndarray); returns
+    (seed, cycle).  With a context, its state table is restored too."""
+    L = load_library()
+    items = list(arrays.items())
+    arr = (ArrayC * max(1, len(items)))(*[_array_c(k, v) for k, v in items])
+    seed, cycle = C.c_uint64(), C.c_uint64()
+    _ck_check(ctx, L.algdock_checkpoint_load(ctx.h if ctx is not None else None, str(path).encode(), C.byref(seed),
+                                             C.byref(cycle), len(items), arr), "checkpoint_load")
+    return seed.value, cycle.value
 
 
 class Context:
@@ -548,6 +657,47 @@ class Context:
         return f, it.value
 
     # ---------------------------------------------------------------- learned proposal
+    def cycle(self, legs, n_chains, cycle, x, comps, state_of, config_of, n_steps=50, n_sweeps=25, max_sep=5,
+              seed=0, rep_offset=0, ladder_offset=0, counters=None, u_kn=None):
+        """algdock_cycle: one HMC trial of every replica, then the exchange sweeps of every ladder (and
+        the snapshot's u_kn if given).  legs: [(K, state_offset), ...].  Each array is a device
+        tensor or host memory (a CPU tensor, ideally pinned, or a numpy array), updated in place."""
+        import torch
+        d = RunDescC()
+        d.n_legs = len(legs)
+        for i, (K, off) in enumerate(legs):
+            d.K[i], d.state_offset[i] = int(K), int(off)
+        d.n_chains, d.n_steps, d.n_sweeps, d.max_sep = int(n_chains), int(n_steps), int(n_sweeps), int(max_sep)
+        d.seed, d.rep_offset, d.ladder_offset = int(seed), int(rep_offset), int(ladder_offset)
+
+        def ptr(a, td, name):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                if a.dtype != td or not a.is_contiguous():
+                    raise ValueError("%s must be a contiguous %s tensor" % (name, td))
+                return a.data_ptr()
+            if not (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype == np.dtype(str(td)[6:])):
+                raise ValueError("%s must be a C-contiguous %s array" % (name, td))
+            return a.ctypes.data
+        self._check(self._L.algdock_cycle(
+            self.h, C.byref(d), int(cycle), ptr(x, torch.float32, "x"), ptr(comps, torch.float64, "comps"),
+            ptr(state_of, torch.int32, "state_of"), ptr(config_of, torch.int32, "config_of"),
+            ptr(counters, torch.int64, "counters"), ptr(u_kn, torch.float64, "u_kn")))
+
+    def mbar_partials(self, u_kn, N_k, f, precision_mode=0):
+        """This process's (max, sum) pair per state of one MBAR iteration ([K][2] numpy)."""
+        import torch
+        K = len(N_k)
+        N = int(u_kn.shape[1]) if u_kn is not None and u_kn.numel() else 0
+        Nk = np.ascontiguousarray(N_k, dtype=np.int64)
+        fa = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.empty((K, 2))
+        self._check(self._L.algdock_mbar_partials(self.h, K, N, _dev(u_kn, torch.float64, "u_kn") if N else None,
+                                                  Nk.ctypes.data, fa.ctypes.data, int(precision_mode),
+                                                  out.ctypes.data))
+        return out
+
     def learned_ntorsions(self):
         T = C.c_int32()
         self._check(self._L.algdock_learned_ntorsions(self.h, C.byref(T)))

@@ -14,6 +14,9 @@
 namespace algdock {
 size_t mbar_scratch_bytes(int K, int64_t N);
 size_t mbar_scratch_bytes_mode(int K, int64_t N, int mode);
+size_t mbar_pairs_scratch_bytes(int K, int64_t N);
+cudaError_t mbar_local_pairs(cudaStream_t s, void* scratch, int K, int64_t N, const double* u_kn,
+                             const int64_t* Nk_host, const double* f_host, int mode, double* pairs_host);
 int mbar_run(cudaStream_t s, void* scratch, int K, int64_t N, const double* u_kn, const int64_t* Nk_host,
              double tol, int max_iter, int mode, double* f_host, int* iters, int* h_flag, cudaError_t* err);
 }  // namespace algdock
@@ -501,6 +504,7 @@ void algdock_destroy(algdock_ctx* c) {
   if (c->batch_fork) cudaEventDestroy(c->batch_fork);
   cudaFreeHost(c->h_flag);
   cudaFree(c->d_work);
+  cudaFree(c->d_stage);
   delete c;
 }
 
@@ -605,6 +609,9 @@ algdock_status algdock_grids_load(algdock_ctx* c, const algdock_grid_desc* d, co
   G.inv_h = (float)(1.0 / d->spacing);
   c->grid = G;
   c->has_grid = true;
+  const double fpd[6] = {d->origin[0], d->origin[1], d->origin[2], d->spacing, vmax_r, vmax_e};
+  const int32_t fpn[3] = {d->n[0], d->n[1], d->n[2]};
+  c->fp_grid = crc32_update(crc32_update(0, fpd, sizeof(fpd)), fpn, sizeof(fpn));
   return ALGDOCK_OK;
   ALGDOCK_CATCH(c)
 }
@@ -725,6 +732,7 @@ algdock_status algdock_ligand_load(algdock_ctx* c, const algdock_ligand* L, cons
   c->lig64 = Y64;
   build_learned_topo(na, nb, L->bonds, &c->ltopo);
   c->has_ligand = true;
+  c->fp_ligand = crc32_update(crc32_update(0, blob.data(), blob.size() * 4), &Y, sizeof(Y));
   return ALGDOCK_OK;
   ALGDOCK_CATCH(c)
 }
@@ -760,6 +768,9 @@ algdock_status algdock_states_set(algdock_ctx* c, int32_t K, const double* T, co
   if (e == cudaSuccess) e = cudaMemcpy(c->d_states, h.data(), sizeof(StateDev) * K, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(c, e, "states_set");
   c->K = K;
+  c->h_T.assign(T, T + K);
+  c->h_alpha.assign(alpha, alpha + K);
+  c->h_dt.assign(dt_fs, dt_fs + K);
   return ALGDOCK_OK;
   ALGDOCK_CATCH(c)
 }
@@ -1436,6 +1447,161 @@ algdock_status algdock_mbar(algdock_ctx* c, int32_t K, int64_t N, const double* 
   if (r == 1) return fail(c, ALGDOCK_E_NOT_CONVERGED, "mbar: max_iter reached");
   return ALGDOCK_OK;
   ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t cycle, float* x, double* comps,
+                             int32_t* state_of, int32_t* config_of, int64_t* counters, double* u_kn) {
+  ALGDOCK_TRY(c)
+  if (!c->has_grid || !c->has_ligand || c->K == 0)
+    return fail(c, ALGDOCK_E_STATE, "cycle: load grids, ligand and states first");
+  if (!d || !x || !comps || !state_of || !config_of || d->n_legs < 1 || d->n_legs > ALGDOCK_MAX_LEGS ||
+      d->n_chains < 1 || d->n_steps < 0 || d->n_sweeps < 0 || d->max_sep < 1 ||
+      (int64_t)d->n_sweeps * d->max_sep >= 65536 || d->rep_offset < 0 || d->ladder_offset < 0)
+    return fail(c, ALGDOCK_E_INVALID, "cycle: bad arguments");
+  int64_t R = 0, ukn_words = 0;
+  for (int l = 0; l < d->n_legs; ++l) {
+    if (d->K[l] < 1 || d->K[l] > kMaxLadder || d->state_offset[l] < 0 || d->state_offset[l] + d->K[l] > c->K)
+      return fail(c, ALGDOCK_E_INVALID, "cycle: leg outside the state table");
+    R += (int64_t)d->n_chains * d->K[l];
+    ukn_words += (int64_t)d->K[l] * d->n_chains * d->K[l];
+  }
+  const int na = c->lig.na;
+  // each array device-resident as given, or staged: [x | comps | snapshot comps | state_of | config_of |
+  // counters | u_kn], 256-byte aligned pieces
+  struct Piece {
+    void* user;
+    size_t bytes;
+    bool host;
+    size_t off;
+  };
+  Piece P[7] = {{x, (size_t)R * na * 3 * 4, false, 0},       {comps, (size_t)R * 32, false, 0},
+                {nullptr, (size_t)(u_kn ? R : 0) * 32, true, 0}, {state_of, (size_t)R * 4, false, 0},
+                {config_of, (size_t)R * 4, false, 0},          {counters, counters ? (size_t)ALGDOCK_N_COUNTERS * 8 : 0, false, 0},
+                {u_kn, u_kn ? (size_t)ukn_words * 8 : 0, false, 0}};
+  size_t need = 0;
+  for (int i = 0; i < 7; ++i) {
+    if (i != 2) P[i].host = P[i].user && !is_device_ptr(P[i].user);
+    if (P[i].host) {
+      P[i].off = need;
+      need += (P[i].bytes + 255) & ~(size_t)255;
+    }
+  }
+  Device g(c->device);
+  cudaError_t e = cudaSuccess;
+  if (need > c->stage_bytes) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cycle");
+    cudaFree(c->d_stage);
+    c->d_stage = nullptr;
+    c->stage_bytes = 0;
+    e = cudaMalloc(&c->d_stage, need);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cycle");
+    c->stage_bytes = need;
+  }
+  auto dev_of = [&](int i) { return P[i].host ? (void*)((char*)c->d_stage + P[i].off) : P[i].user; };
+  bool any_host = false;
+  for (int i = 0; i < 7 && e == cudaSuccess; ++i)
+    if (P[i].host && P[i].user) {  // inputs in (u_kn is output only; its host copy goes out below)
+      any_host = true;
+      if (i != 6) e = cudaMemcpyAsync(dev_of(i), P[i].user, P[i].bytes, cudaMemcpyHostToDevice, c->stream);
+    }
+  float* dx = (float*)dev_of(0);
+  double* dc = (double*)dev_of(1);
+  int32_t* ds = (int32_t*)dev_of(3);
+  int32_t* dcfg = (int32_t*)dev_of(4);
+  int64_t* dcnt = (int64_t*)dev_of(5);
+  if (e == cudaSuccess)
+    e = launch_hmc(c->stream, *c, R, ds, dx, dc, nullptr, nullptr, d->n_steps, d->seed, cycle, d->rep_offset, dcnt);
+  int64_t base = 0, cbase = 0, ubase = 0;
+  for (int l = 0; l < d->n_legs && e == cudaSuccess; ++l) {
+    e = launch_exchange(c->stream, *c, d->n_chains, d->K[l], d->state_offset[l], dc + 4 * base, dcfg + cbase,
+                        ds + base, d->n_sweeps, d->max_sep, d->seed, cycle, d->ladder_offset + (int64_t)l * d->n_chains,
+                        nullptr, nullptr);
+    base += (int64_t)d->n_chains * d->K[l];
+    cbase += (int64_t)d->n_chains * d->K[l];
+  }
+  if (e == cudaSuccess && u_kn) {  // the snapshot: every configuration re-evaluated, then u_kn per leg
+    double* snap = (double*)dev_of(2);
+    e = launch_evaluate(c->stream, *c, R, dx, snap);
+    base = 0;
+    for (int l = 0; l < d->n_legs && e == cudaSuccess; ++l) {
+      const int64_t n = (int64_t)d->n_chains * d->K[l];
+      e = launch_ukn(c->stream, *c, n, snap + 4 * base, d->state_offset[l], d->K[l], (double*)dev_of(6) + ubase);
+      base += n;
+      ubase += (int64_t)d->K[l] * n;
+    }
+  }
+  for (int i = 0; i < 7 && e == cudaSuccess; ++i)
+    if (P[i].host && P[i].user) e = cudaMemcpyAsync(P[i].user, dev_of(i), P[i].bytes, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && any_host) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cycle");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_mbar_partials(algdock_ctx* c, int32_t K, int64_t N, const double* u_kn, const int64_t* N_k,
+                                     const double* f, int32_t precision_mode, double* pairs) {
+  ALGDOCK_TRY(c)
+  if (K < 1 || N < 0 || !N_k || !f || !pairs || (N > 0 && !u_kn) || (precision_mode != 0 && precision_mode != 1))
+    return fail(c, ALGDOCK_E_INVALID, "mbar_partials: bad arguments (precision_mode 0 or 1)");
+  if (K > kMbarMaxStates)
+    return fail(c, ALGDOCK_E_INVALID, "mbar_partials: K = " + std::to_string(K) + " exceeds " +
+                                          std::to_string(kMbarMaxStates));
+  for (int k = 0; k < K; ++k) {
+    if (N_k[k] < 0) return fail(c, ALGDOCK_E_INVALID, "mbar_partials: negative N_k");
+    if (!isfinite(f[k])) return fail(c, ALGDOCK_E_NUMERIC, "mbar_partials: non-finite f");
+  }
+  if (N == 0) {  // no samples here: the empty pair of every state
+    for (int k = 0; k < K; ++k) {
+      pairs[2 * k] = -INFINITY;
+      pairs[2 * k + 1] = 0.0;
+    }
+    return ALGDOCK_OK;
+  }
+  if (!is_device_ptr(u_kn)) return fail(c, ALGDOCK_E_INVALID, "mbar_partials: u_kn must be a device pointer");
+  Device g(c->device);
+  const size_t need = mbar_pairs_scratch_bytes(K, N);
+  if (need > c->mbar_bytes) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mbar_partials");
+    cudaFree(c->d_mbar);
+    c->d_mbar = nullptr;
+    c->mbar_bytes = 0;
+    e = cudaMalloc(&c->d_mbar, need);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mbar_partials");
+    c->mbar_bytes = need;
+  }
+  const cudaError_t e = mbar_local_pairs(c->stream, c->d_mbar, K, N, u_kn, N_k, f, precision_mode, pairs);
+  if (e != cudaSuccess) return cuda_fail(c, e, "mbar_partials");
+  return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_mbar_update(int32_t K, int32_t n_parts, const double* pairs, const double* f_old,
+                                   double* f_new, double* delta) {
+  if (K < 1 || n_parts < 1 || !pairs || !f_old || !f_new || !delta) return ALGDOCK_E_INVALID;
+  std::vector<double> fn(K);
+  for (int i = 0; i < K; ++i) {
+    double M = -INFINITY;
+    for (int p = 0; p < n_parts; ++p) M = std::max(M, pairs[((size_t)p * K + i) * 2]);
+    double S = 0.0;
+    if (M != -INFINITY)
+      for (int p = 0; p < n_parts; ++p) {
+        const double m = pairs[((size_t)p * K + i) * 2], sp = pairs[((size_t)p * K + i) * 2 + 1];
+        if (m != -INFINITY) S += sp * exp(m - M);
+      }
+    fn[i] = M == -INFINITY ? INFINITY : -(M + log(S));
+  }
+  double d = 0.0;
+  const double f0 = fn[0];
+  for (int i = 0; i < K; ++i) {
+    const double v = fn[i] - f0;
+    const double di = fabs(v - f_old[i]);
+    d = (di > d || isnan(di)) ? di : d;
+    f_new[i] = v;
+  }
+  *delta = d;
+  return ALGDOCK_OK;
 }
 
 }  // extern "C"

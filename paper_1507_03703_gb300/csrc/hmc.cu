@@ -132,7 +132,32 @@ struct GridOut {
   bool outside;
 };
 
-// Grid energies and forces of one atom.  hard / soft select which lattices are read.
+// tri() for two channels at once (paired FP32 instructions): per channel the same operations in
+// the same order, so each half equals the scalar result bit for bit.
+struct Tri2 {
+  f32x2 v, gx, gy, gz;
+};
+__device__ inline Tri2 tri2(f32x2 c000, f32x2 c001, f32x2 c010, f32x2 c011, f32x2 c100, f32x2 c101, f32x2 c110,
+                            f32x2 c111, f32x2 tx, f32x2 ty, f32x2 tz) {
+  const f32x2 d00 = sub2(c001, c000), d01 = sub2(c011, c010), d10 = sub2(c101, c100), d11 = sub2(c111, c110);
+  const f32x2 a00 = fma2(tx, d00, c000), a01 = fma2(tx, d01, c010);
+  const f32x2 a10 = fma2(tx, d10, c100), a11 = fma2(tx, d11, c110);
+  const f32x2 by0 = sub2(a01, a00), by1 = sub2(a11, a10);
+  const f32x2 b0 = fma2(ty, by0, a00), b1 = fma2(ty, by1, a10);
+  const f32x2 bx0 = fma2(ty, sub2(d01, d00), d00), bx1 = fma2(ty, sub2(d11, d10), d10);
+  Tri2 r;
+  r.gz = sub2(b1, b0);
+  r.v = fma2(tz, r.gz, b0);
+  r.gx = fma2(tz, sub2(bx1, bx0), bx0);
+  r.gy = fma2(tz, sub2(by1, by0), by0);
+  return r;
+}
+__device__ inline f32x2 lo2(float4 c) { return pack2(c.x, c.y); }
+__device__ inline f32x2 hi2(float4 c) { return pack2(c.z, c.w); }
+__device__ inline f32x2 as2(float2 c) { return pack2(c.x, c.y); }
+
+// Grid energies and forces of one atom.  hard / soft select which lattices are read.  The hard
+// lattice's channels run as the pairs (LJr^1/4, LJa) and (elec, 0), the soft lattice's as one pair.
 __device__ inline GridOut grid_atom(const GridDev& G, float x, float y, float z, float sA, float sB, float q,
                                     bool hard, bool soft, float w_sg, float w_g) {
   GridOut o{0.f, 0.f, 0.f, 0.f, 0.f, false};
@@ -146,22 +171,28 @@ __device__ inline GridOut grid_atom(const GridDev& G, float x, float y, float z,
   const float mx = ix ? G.inv_h : 0.f, my = iy ? G.inv_h : 0.f, mz = iz ? G.inv_h : 0.f;
   const int64_t sx = 1, sy = G.nx, sz = (int64_t)G.nx * G.ny;
   const int64_t b = (int64_t)cz * sz + (int64_t)cy * sy + cx;
-  float gxs = 0.f, gys = 0.f, gzs = 0.f;
+  const f32x2 tx2 = pack2(tx, tx), ty2 = pack2(ty, ty), tz2 = pack2(tz, tz);
+  f32x2 gx2 = 0ull, gy2 = 0ull, gz2 = 0ull;  // (sum of the weighted channel gradients) in two halves
   if (hard) {
     const float4 c000 = __ldg(G.hard + b), c001 = __ldg(G.hard + b + sx);
     const float4 c010 = __ldg(G.hard + b + sy), c011 = __ldg(G.hard + b + sy + sx);
     const float4 c100 = __ldg(G.hard + b + sz), c101 = __ldg(G.hard + b + sz + sx);
     const float4 c110 = __ldg(G.hard + b + sz + sy), c111 = __ldg(G.hard + b + sz + sy + sx);
-    const Tri r = tri(c000.x, c001.x, c010.x, c011.x, c100.x, c101.x, c110.x, c111.x, tx, ty, tz);
-    const Tri a = tri(c000.y, c001.y, c010.y, c011.y, c100.y, c101.y, c110.y, c111.y, tx, ty, tz);
-    const Tri e = tri(c000.z, c001.z, c010.z, c011.z, c100.z, c101.z, c110.z, c111.z, tx, ty, tz);
-    const float r2 = r.v * r.v;
-    o.e_g = sA * (r2 * r2) + sB * a.v + q * e.v;
-    const float cr = 4.f * sA * r2 * r.v;
+    const Tri2 ra = tri2(lo2(c000), lo2(c001), lo2(c010), lo2(c011), lo2(c100), lo2(c101), lo2(c110), lo2(c111), tx2,
+                         ty2, tz2);
+    const Tri2 e0 = tri2(hi2(c000), hi2(c001), hi2(c010), hi2(c011), hi2(c100), hi2(c101), hi2(c110), hi2(c111), tx2,
+                         ty2, tz2);
+    float rv, av, ev, zv;
+    unpack2(ra.v, rv, av);
+    unpack2(e0.v, ev, zv);
+    const float r2 = rv * rv;
+    o.e_g = sA * (r2 * r2) + sB * av + q * ev;
     if (w_g != 0.f) {
-      gxs += w_g * (cr * r.gx + sB * a.gx + q * e.gx);
-      gys += w_g * (cr * r.gy + sB * a.gy + q * e.gy);
-      gzs += w_g * (cr * r.gz + sB * a.gz + q * e.gz);
+      const float cr = 4.f * sA * r2 * rv;
+      const f32x2 kra = pack2(w_g * cr, w_g * sB), ke = pack2(w_g * q, 0.f);
+      gx2 = fma2(kra, ra.gx, mul2(ke, e0.gx));
+      gy2 = fma2(kra, ra.gy, mul2(ke, e0.gy));
+      gz2 = fma2(kra, ra.gz, mul2(ke, e0.gz));
     }
   }
   if (soft) {
@@ -169,20 +200,26 @@ __device__ inline GridOut grid_atom(const GridDev& G, float x, float y, float z,
     const float2 c010 = __ldg(G.soft + b + sy), c011 = __ldg(G.soft + b + sy + sx);
     const float2 c100 = __ldg(G.soft + b + sz), c101 = __ldg(G.soft + b + sz + sx);
     const float2 c110 = __ldg(G.soft + b + sz + sy), c111 = __ldg(G.soft + b + sz + sy + sx);
-    const Tri r = tri(c000.x, c001.x, c010.x, c011.x, c100.x, c101.x, c110.x, c111.x, tx, ty, tz);
-    const Tri e = tri(c000.y, c001.y, c010.y, c011.y, c100.y, c101.y, c110.y, c111.y, tx, ty, tz);
-    const float r2 = r.v * r.v;
-    o.e_sg = sA * (r2 * r2) + q * e.v;
-    const float cr = 4.f * sA * r2 * r.v;
+    const Tri2 re = tri2(as2(c000), as2(c001), as2(c010), as2(c011), as2(c100), as2(c101), as2(c110), as2(c111), tx2,
+                         ty2, tz2);
+    float rv, ev;
+    unpack2(re.v, rv, ev);
+    const float r2 = rv * rv;
+    o.e_sg = sA * (r2 * r2) + q * ev;
     if (w_sg != 0.f) {
-      gxs += w_sg * (cr * r.gx + q * e.gx);
-      gys += w_sg * (cr * r.gy + q * e.gy);
-      gzs += w_sg * (cr * r.gz + q * e.gz);
+      const f32x2 k = pack2(w_sg * (4.f * sA * r2 * rv), w_sg * q);
+      gx2 = fma2(k, re.gx, gx2);
+      gy2 = fma2(k, re.gy, gy2);
+      gz2 = fma2(k, re.gz, gz2);
     }
   }
-  o.fx = -gxs * mx;
-  o.fy = -gys * my;
-  o.fz = -gzs * mz;
+  float ga, gb;
+  unpack2(gx2, ga, gb);
+  o.fx = -(ga + gb) * mx;
+  unpack2(gy2, ga, gb);
+  o.fy = -(ga + gb) * my;
+  unpack2(gz2, ga, gb);
+  o.fz = -(ga + gb) * mz;
   return o;
 }
 

@@ -221,9 +221,12 @@ struct algdock_ctx {
   bool has_ligand = false;
   algdock::LigandLayout lig{};
   uint32_t* d_blob = nullptr;
-  // states
+  // states (with the host copy of the table they were set from, for checkpoints)
   int K = 0;
   algdock::StateDev* d_states = nullptr;
+  std::vector<double> h_T, h_alpha, h_dt;
+  // CRC-32 of the loaded ligand blob and of the lattice descriptor (0: none loaded), for checkpoints
+  uint32_t fp_ligand = 0, fp_grid = 0;
   // scratch owned by the MBAR solver, grown on demand
   void* d_mbar = nullptr;
   size_t mbar_bytes = 0;
@@ -231,6 +234,9 @@ struct algdock_ctx {
   int* h_flag = nullptr;
   // work counter of the single-ligand HMC launch (replicas handed out to warps; zeroed per launch)
   unsigned long long* d_work = nullptr;
+  // device staging of algdock_cycle's host arrays (grown on demand)
+  void* d_stage = nullptr;
+  size_t stage_bytes = 0;
   // learned proposal: torsion tree and scratch grown on demand
   algdock::LearnedTopo ltopo{};
   void* d_learn = nullptr;
@@ -268,6 +274,9 @@ struct algdock_ctx {
 };
 
 namespace algdock {
+// CRC-32 (the IEEE 802.3 polynomial, reflected, as in zip and PNG) of n bytes, continuing from crc
+// (0 to start).
+uint32_t crc32_update(uint32_t crc, const void* data, size_t n);
 // launchers implemented in the .cu files
 cudaError_t launch_grid_build(cudaStream_t s, const algdock_grid_desc& d, int n_rec, const double* xyz,
                               const double* rstar, const double* eps, const double* q, float* ljr, float* lja,

@@ -301,6 +301,22 @@ __global__ void merge_chunks(int K, int n_chunks, const double2* __restrict__ pa
   }
 }
 
+// Each state's chunk pairs merged into one (max, sum) pair (FP64 log-sum-exp merges, one warp per
+// state), for MBAR sharded over samples: the pairs of all processes are merged on the host.
+__global__ void merge_chunk_pairs(int K, int n_chunks, const double2* __restrict__ part, double2* out) {
+  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (i >= K) return;
+  const unsigned full = 0xffffffffu;
+  const double2* pi = part + (int64_t)i * n_chunks;
+  Lse a{-INFINITY, 0.0};
+  for (int c = lane; c < n_chunks; c += 32) a = lse_merge(a, Lse{pi[c].x, pi[c].y});
+  for (int o = 16; o > 0; o >>= 1) {
+    const Lse b{__shfl_xor_sync(full, a.m, o), __shfl_xor_sync(full, a.s, o)};
+    a = lse_merge(a, b);
+  }
+  if (lane == 0) out[i] = make_double2(a.m, a.s);
+}
+
 __global__ void init_state(int K, const int64_t* Nk, double* logNk, double* f, MbarState* st) {
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     logNk[k] = Nk[k] > 0 ? log((double)Nk[k]) : -INFINITY;
@@ -323,6 +339,41 @@ size_t mbar_scratch_bytes(int K, int64_t N) {
 }
 size_t mbar_scratch_bytes_mode(int K, int64_t N, int mode) {
   return mbar_scratch_bytes(K, N) + (mode == 2 ? (size_t)K * N * sizeof(float) + 256 : 0);
+}
+
+// One iteration's (max, sum) pair per state over these N samples, given the global N_k and the
+// current f (host arrays): sum_n exp(-u_in - log D_n) = sum * exp(max), with log D_n over all K
+// states as in the full solve.  Scratch: mbar_pairs_scratch_bytes(K, N).  pairs_host [K][2].
+size_t mbar_pairs_scratch_bytes(int K, int64_t N) { return mbar_scratch_bytes(K, N) + 16 * (size_t)K + 256; }
+
+cudaError_t mbar_local_pairs(cudaStream_t s, void* scratch, int K, int64_t N, const double* u_kn,
+                             const int64_t* Nk_host, const double* f_host, int mode, double* pairs_host) {
+  const int64_t chunk_len = mbar_chunk(K, N);
+  const int64_t n_chunks = (N + chunk_len - 1) / chunk_len;
+  char* p = (char*)scratch;
+  MbarState* st = (MbarState*)p;
+  double* logNk = (double*)(p + 64);
+  double* f = logNk + K;
+  double* fnew = f + K;
+  int64_t* Nk = (int64_t*)(fnew + K);
+  double2* part = (double2*)(Nk + K);
+  double* logD = (double*)(part + (size_t)K * n_chunks);
+  const size_t off = ((size_t)((char*)(logD + N) - p) + 255) & ~(size_t)255;
+  double2* pairs = (double2*)(p + off);
+  cudaError_t e = cudaMemcpyAsync(Nk, Nk_host, sizeof(int64_t) * K, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  init_state<<<1, 256, 0, s>>>(K, Nk, logNk, f, st);
+  e = cudaMemcpyAsync(f, f_host, sizeof(double) * K, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  const int threads = 256;
+  log_denominators<<<(unsigned)((N + threads - 1) / threads), threads, 0, s>>>(K, N, u_kn, logNk, f, logD, st, mode);
+  state_partials<<<dim3((unsigned)n_chunks, (unsigned)K), kPartialThreads, 0, s>>>(N, chunk_len, u_kn, logD, part,
+                                                                                    (int)n_chunks, st, mode);
+  merge_chunk_pairs<<<(unsigned)((K * 32 + 255) / 256), 256, 0, s>>>(K, (int)n_chunks, part, pairs);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pairs_host, pairs, sizeof(double2) * K, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
 }
 
 // Runs the solver on caller-provided scratch (mbar_scratch_bytes(K, N) bytes, 256-byte aligned).

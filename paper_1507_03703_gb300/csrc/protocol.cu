@@ -156,3 +156,94 @@ cudaError_t launch_pacc(cudaStream_t s, const algdock_ctx& c, int64_t n, const d
 }
 
 }  // namespace algdock
+
+// ------------------------------------------------------------------ the scalar steps (host)
+// Protocol initialization places the states of a leg one thermodynamic-length step apart and
+// adapts each state's time step; between cycles it inserts states where neighbours stopped
+// exchanging ("Initialization"; "Equilibration and production").  These steps are a few scalar
+// operations per state, so they run on the host, in the library, beside the device reductions
+// above that supply their inputs.
+namespace {
+
+constexpr double kBoltzmannKcal = 0.0019872043;  // kcal/(mol K)
+
+double logistic(double z) { return z >= 0 ? 1.0 / (1.0 + exp(-z)) : exp(z) / (1.0 + exp(z)); }
+
+// d alpha_sg / d alpha and d alpha_g / d alpha for alpha_sg = 1 - (2 alpha - 1)^2 and
+// alpha_g = (2 alpha - 1)^2 logistic(1000 (alpha - 1/2)), Eq. (protocol).
+double d_alpha_sg(double a) { return -4.0 * (2.0 * a - 1.0); }
+double d_alpha_g(double a) {
+  const double s = 2.0 * a - 1.0;
+  const double L = logistic(1000.0 * (a - 0.5));
+  return 4.0 * s * L + s * s * 1000.0 * L * (1.0 - L);
+}
+
+}  // namespace
+
+extern "C" {
+
+algdock_status algdock_next_temperature(double T, double sigma_U, double speed, double T_end, double* T_next) {
+  if (!T_next || !(T > 0) || !isfinite(T) || !(sigma_U >= 0) || !isfinite(sigma_U) || !(speed > 0) ||
+      !isfinite(T_end))
+    return ALGDOCK_E_INVALID;
+  // the thermodynamic length along T changes at sigma[U_S] / (k_B T^2)
+  *T_next = sigma_U <= 0.0 ? T_end : fmin(T_end, T + speed * kBoltzmannKcal * T * T / sigma_U);
+  return ALGDOCK_OK;
+}
+
+algdock_status algdock_next_alpha(double alpha, double sigma_sg, double sigma_g, double sigma_u, double speed,
+                                  double T_T, double T_H, double* alpha_next) {
+  if (!alpha_next || !(alpha >= 0) || !(alpha <= 1) || !(sigma_sg >= 0) || !(sigma_g >= 0) || !(sigma_u >= 0) ||
+      !isfinite(sigma_sg) || !isfinite(sigma_g) || !isfinite(sigma_u) || !(speed > 0) || !(T_T > 0) || !(T_H > 0))
+    return ALGDOCK_E_INVALID;
+  const double T = (T_T - T_H) * alpha + T_H;
+  const double rate = fabs(d_alpha_sg(alpha)) * sigma_sg / (kBoltzmannKcal * T) +
+                      fabs(d_alpha_g(alpha)) * sigma_g / (kBoltzmannKcal * T) + fabs(T_T - T_H) * sigma_u / T;
+  *alpha_next = rate <= 0.0 ? 1.0 : fmin(1.0, alpha + speed / rate);
+  return ALGDOCK_OK;
+}
+
+algdock_status algdock_adapt_dt(double dt, double acceptance, double* dt_next) {
+  if (!dt_next || !isfinite(dt) || !(acceptance >= 0) || !(acceptance <= 1)) return ALGDOCK_E_INVALID;
+  if (acceptance > 0.8) dt += 0.125;
+  else if (acceptance < 0.1) dt -= 0.5;
+  else if (acceptance < 0.4) dt -= 0.25;
+  *dt_next = fmin(5.0, fmax(0.1, dt));
+  return ALGDOCK_OK;
+}
+
+algdock_status algdock_insert_states(int32_t K, const double* T, const double* alpha, const double* dt,
+                                     const int64_t* attempts, const int64_t* accepts, double threshold, double T_T,
+                                     double T_H, int32_t capacity, int32_t* K_out, double* T_out, double* alpha_out,
+                                     double* dt_out, int32_t* lower) {
+  if (K < 1 || !T || !alpha || !dt || (K > 1 && (!attempts || !accepts)) || !K_out || !T_out || !alpha_out ||
+      !dt_out || !lower || capacity < 2 * K - 1 || !(threshold >= 0) || !(T_T > 0) || !(T_H > 0))
+    return ALGDOCK_E_INVALID;
+  int n = 0;
+  for (int k = 0; k < K; ++k) {
+    T_out[n] = T[k];
+    alpha_out[n] = alpha[k];
+    dt_out[n] = dt[k];
+    lower[n] = -1;
+    ++n;
+    if (k + 1 < K && attempts[k] > 0 && (double)accepts[k] / (double)attempts[k] < threshold) {
+      double t, a;
+      if (isnan(alpha[k])) {  // warming leg: the geometric mean keeps the ladder geometric
+        t = sqrt(T[k] * T[k + 1]);
+        a = alpha[k];
+      } else {  // coupling leg: the mean alpha, with its temperature T(alpha)
+        a = 0.5 * (alpha[k] + alpha[k + 1]);
+        t = T_H + (T_T - T_H) * a;
+      }
+      T_out[n] = t;
+      alpha_out[n] = a;
+      dt_out[n] = fmin(dt[k], dt[k + 1]);
+      lower[n] = n - 1;
+      ++n;
+    }
+  }
+  *K_out = n;
+  return ALGDOCK_OK;
+}
+
+}  // extern "C"

@@ -87,29 +87,3 @@ class LearnedProposal:
     def propose(self, state_of, x, comps, n_moves, seed, cycle, accepted=None, counters=None, rep_offset=0):
         self.ctx.propose_learned(self.params, self.wbf16, state_of, x, comps, n_moves, seed=seed, cycle=cycle,
                                  rep_offset=rep_offset, accepted=accepted, counters=counters, n_torsions=self.T)
-
-
-def statistical_inefficiency(a):
-    """g = 1 + 2 sum_t (1 - t/N) C(t), summed until the normalised autocorrelation first drops to
-    zero (used to report effective sample sizes)."""
-    a = np.asarray(a, dtype=np.float64)
-    N = a.size
-    if N < 2:
-        return 1.0
-    d = a - a.mean()
-    var = np.dot(d, d) / N
-    if var == 0.0:
-        return 1.0
-    g = 1.0
-    for t in range(1, N):
-        c = np.dot(d[:-t], d[t:]) / ((N - t) * var)
-        if c <= 0.0:
-            break
-        g += 2.0 * c * (1.0 - t / N)
-    return max(g, 1.0)
-
-
-def effective_samples(series):
-    """Sum over chains of N / g for series [cycles][chains]."""
-    s = np.asarray(series)
-    return float(sum(s.shape[0] / statistical_inefficiency(s[:, c]) for c in range(s.shape[1])))

@@ -11,8 +11,8 @@ For each new state:
    replaces the current one.
 
 The sampling, the statistics, the resampling and the exchange probabilities run in the library's
-kernels. This module holds the state-by-state control flow and the scalar arithmetic of the
-parameter steps and the time-step rule.
+kernels, and the scalar steps (the parameter steps, the time-step rule, the insertion rule) in its
+host entry points.  This module holds the state-by-state control flow.
 """
 from __future__ import annotations
 
@@ -21,79 +21,62 @@ import math
 import numpy as np
 import torch
 
-KB = 0.0019872043  # kcal/(mol K)
+
+def _lib():
+    from .algdock import load_library
+    return load_library()
 
 
-def _logistic(z):
-    return 1.0 / (1.0 + math.exp(-z)) if z >= 0 else math.exp(z) / (1.0 + math.exp(z))
-
-
-def d_alpha_sg(a):
-    """d alpha_sg / d alpha for alpha_sg = 1 - (2 alpha - 1)^2 (Eq. (protocol))."""
-    return -4.0 * (2.0 * a - 1.0)
-
-
-def d_alpha_g(a):
-    """d alpha_g / d alpha for alpha_g = (2 alpha - 1)^2 logistic(1000 (alpha - 1/2)) (Eq. (protocol))."""
-    s = 2.0 * a - 1.0
-    L = _logistic(1000.0 * (a - 0.5))
-    return 4.0 * s * L + s * s * 1000.0 * L * (1.0 - L)
+def _call(name, *args):
+    import ctypes
+    from .algdock import AlgdockError
+    out = ctypes.c_double()
+    st = getattr(_lib(), name)(*[float(a) for a in args], ctypes.byref(out))
+    if st != 0:
+        raise AlgdockError(st, name + ": bad arguments")
+    return out.value
 
 
 def next_temperature(T, sigma_U, speed, T_end=600.0):
-    """Warming leg: sigma[dl/dT] = sigma[U_S] / (k_B T^2), so T + speed k_B T^2 / sigma[U_S]."""
-    if sigma_U <= 0.0:  # no fluctuation: the step is unbounded, so the leg's end is next
-        return T_end
-    return min(T_end, T + speed * KB * T * T / sigma_U)
+    """Warming leg, one thermodynamic-length step (algdock_next_temperature)."""
+    return _call("algdock_next_temperature", T, sigma_U, speed, T_end)
 
 
 def next_alpha(a, sigma_sg, sigma_g, sigma_u, speed, T_T=300.0, T_H=600.0):
-    """Coupling leg: alpha + speed / (|alpha_sg'| sigma[Psi_sg]/(k_B T) + |alpha_g'| sigma[Psi_g]/(k_B T)
-    + |T_T - T_H| sigma[u]/T), T = T(alpha), not past 1."""
-    T = (T_T - T_H) * a + T_H
-    rate = (abs(d_alpha_sg(a)) * sigma_sg / (KB * T) + abs(d_alpha_g(a)) * sigma_g / (KB * T)
-            + abs(T_T - T_H) * sigma_u / T)
-    if rate <= 0.0:  # no fluctuation: the step is unbounded, so the leg's end is next
-        return 1.0
-    return min(1.0, a + speed / rate)
+    """Coupling leg, one thermodynamic-length step (algdock_next_alpha)."""
+    return _call("algdock_next_alpha", a, sigma_sg, sigma_g, sigma_u, speed, T_T, T_H)
 
 
 def adapt_dt(dt, acc):
-    """Acceptance > 0.8: +0.125 fs; < 0.1: -0.5 fs; < 0.4: -0.25 fs; kept in [0.1, 5] fs."""
-    if acc > 0.8:
-        dt += 0.125
-    elif acc < 0.1:
-        dt -= 0.5
-    elif acc < 0.4:
-        dt -= 0.25
-    return min(5.0, max(0.1, dt))
+    """The time-step rule (algdock_adapt_dt)."""
+    return _call("algdock_adapt_dt", dt, acc)
 
 
 def insertions(T, alpha, dt, attempts, accepts, threshold=0.4, T_T=300.0, T_H=600.0):
-    """Between cycles ("Equilibration and production"): a state goes between every neighbour
-    pair (a, a+1) whose exchange acceptance over the cycle is below the threshold (pairs never
-    attempted are left alone), at the midpoint of the leg's control parameter (the geometric mean
-    temperature on the warming leg, the mean alpha with T(alpha) on the coupling leg) and with the
-    smaller time step.  attempts / accepts: neighbour-pair counts [K - 1].  Returns the new
-    (T, alpha, dt) and, for each new state, (its index, the index of its lower neighbour)."""
-    T, alpha, dt = np.asarray(T, float), np.asarray(alpha, float), np.asarray(dt, float)
-    att, acc = np.asarray(attempts, float), np.asarray(accepts, float)
-    nT, nA, nD, new = [], [], [], []
-    for k in range(T.size):
-        nT.append(T[k])
-        nA.append(alpha[k])
-        nD.append(dt[k])
-        if k + 1 < T.size and att[k] > 0 and acc[k] / att[k] < threshold:
-            if math.isnan(alpha[k]):
-                t, a = math.sqrt(T[k] * T[k + 1]), math.nan
-            else:
-                a = 0.5 * (alpha[k] + alpha[k + 1])
-                t = T_H + (T_T - T_H) * a
-            new.append((len(nT), len(nT) - 1))
-            nT.append(t)
-            nA.append(a)
-            nD.append(min(dt[k], dt[k + 1]))
-    return np.array(nT), np.array(nA), np.array(nD), new
+    """Between cycles ("Equilibration and production"), through algdock_insert_states: a state
+    goes between every neighbour pair whose exchange acceptance is below the threshold.
+    attempts / accepts: neighbour-pair counts [K - 1].  Returns the new (T, alpha, dt) and, for
+    each new state, (its index, the index of its lower neighbour)."""
+    import ctypes
+    from .algdock import AlgdockError
+    T, alpha, dt = (np.ascontiguousarray(v, dtype=np.float64) for v in (T, alpha, dt))
+    K = T.size
+    att = np.zeros(max(K, 1), dtype=np.int64)
+    acc = np.zeros(max(K, 1), dtype=np.int64)
+    att[:K - 1] = np.asarray(attempts, dtype=np.int64)[:K - 1]
+    acc[:K - 1] = np.asarray(accepts, dtype=np.int64)[:K - 1]
+    cap = 2 * K - 1
+    oT, oA, oD = np.empty(cap), np.empty(cap), np.empty(cap)
+    low = np.empty(cap, dtype=np.int32)
+    n = ctypes.c_int32()
+    st = _lib().algdock_insert_states(K, T.ctypes.data, alpha.ctypes.data, dt.ctypes.data, att.ctypes.data, acc.ctypes.data, float(threshold),
+            float(T_T), float(T_H), cap, ctypes.byref(n), oT.ctypes.data, oA.ctypes.data, oD.ctypes.data,
+            low.ctypes.data)
+    if st != 0:
+        raise AlgdockError(st, "insert_states: bad arguments")
+    m = n.value
+    new = [(j, int(low[j])) for j in range(m) if low[j] >= 0]
+    return oT[:m].copy(), oA[:m].copy(), oD[:m].copy(), new
 
 
 class ProtocolBuilder:

@@ -12,6 +12,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass
 
+import numpy as np
+
 
 @dataclass(frozen=True)
 class Shard:
@@ -89,3 +91,38 @@ def sum_over_ranks(value: float, device=None, group=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return float(t.item())
+
+
+def mbar_sharded(ctx, u_local, N_k, tol=1e-10, max_iter=10000, precision_mode=0, partials=None, group=None):
+    """MBAR ("Estimation") over samples spread across the ranks: each rank holds the columns of u_kn
+    of its own samples.  Per iteration: this rank's (max, sum) pair per state
+    (algdock_mbar_partials on its GPU, or ``partials(f)`` if given), one all_gather of the K pairs,
+    and algdock_mbar_update over the pairs in rank order, so that every rank holds the same f.
+    N_k are the counts over all ranks.  Returns (f [K], iterations); raises if max_iter is reached."""
+    import torch
+    import torch.distributed as dist
+    from .algdock import AlgdockError, E_NOT_CONVERGED, mbar_update
+
+    K = len(N_k)
+    on = dist.is_available() and dist.is_initialized()
+    world = dist.get_world_size(group) if on else 1
+    dev = None
+    if on and dist.get_backend(group) == "nccl":
+        dev = torch.device("cuda", torch.cuda.current_device())
+    f = np.zeros(K)
+    for it in range(1, max_iter + 1):
+        p = partials(f) if partials is not None else ctx.mbar_partials(u_local, N_k, f, precision_mode)
+        p = np.ascontiguousarray(p, dtype=np.float64).reshape(K, 2)
+        if world > 1:
+            t = torch.from_numpy(p.ravel().copy())
+            if dev is not None:
+                t = t.to(dev)
+            parts = [torch.empty_like(t) for _ in range(world)]
+            dist.all_gather(parts, t, group=group)
+            allp = np.stack([q.cpu().numpy().reshape(K, 2) for q in parts])
+        else:
+            allp = p[None]
+        f, delta = mbar_update(allp, f)
+        if delta < tol:
+            return f, it
+    raise AlgdockError(E_NOT_CONVERGED, "mbar_sharded: max_iter reached")

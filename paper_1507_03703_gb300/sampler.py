@@ -220,6 +220,66 @@ class ReplicaExchange:
             self.ctx.batch_layout(self.lig_of(), na)
         return newT, newA, newD, [[n for n, _ in new] for _, new in plans]
 
+    # ---------------------------------------------------------------- checkpoint and resume
+    def _buffers(self):
+        a = {"legs": np.array([[l.K, l.state_offset] for l in self.legs], dtype=np.int32).ravel(),
+             "x": self.x, "comps": self.comps, "state_of": self.state_of, "dH": self.dH, "acc": self.acc,
+             "ext_acc": self.ext_acc, "counters": self.counters}
+        for li in range(len(self.legs)):
+            a["config_of_%d" % li] = self.config_of[li]
+            a["attempts_%d" % li] = self.attempts[li]
+            a["accepts_%d" % li] = self.accepts[li]
+        return a
+
+    def save(self, path, next_cycle: int):
+        """Checkpoint of the run through algdock_checkpoint_save: the context's state table (with
+        every state's time step), the seed, the next cycle and every buffer the run keeps between
+        cycles, the recorded components included."""
+        from .algdock import checkpoint_save
+        a = self._buffers()
+        a["history"] = (torch.stack(self.history).contiguous() if self.history else
+                        torch.zeros((0, self.R, 4), dtype=torch.float64, device=self.x.device))
+        checkpoint_save(self.ctx, path, self.seed, next_cycle, a)
+
+    def load(self, path) -> int:
+        """Restores a checkpoint written by save (on a context holding the same ligand and lattice;
+        the legs may differ from the constructor's, e.g. after state insertion).  The context's state
+        table is restored too.  Returns the cycle to run next."""
+        from .algdock import checkpoint_load, checkpoint_query
+        q = checkpoint_query(self.ctx, path, ["legs", "x", "history"])
+        if q["legs"][1] < 2 or q["x"][1] < 0:
+            raise ValueError("not a replica-exchange checkpoint: " + str(path))
+        la = np.zeros(q["legs"][1], dtype=np.int32)
+        checkpoint_load(None, path, {"legs": la})
+        legs = [Leg(int(la[2 * i]), int(la[2 * i + 1])) for i in range(la.size // 2)]
+        R = q["x"][1] // (self.n_atoms * 3)
+        C = R // sum(l.K for l in legs)
+        dev = self.x.device
+        self.legs, self.C, self.R = legs, C, R
+        self.x = torch.empty((R, self.n_atoms, 3), dtype=torch.float32, device=dev)
+        self.comps = torch.empty((R, 4), dtype=torch.float64, device=dev)
+        self.dH = torch.empty(R, dtype=torch.float64, device=dev)
+        self.acc = torch.empty(R, dtype=torch.uint8, device=dev)
+        self.ext_acc = torch.empty(R, dtype=torch.int32, device=dev)
+        self.state_of = torch.empty(R, dtype=torch.int32, device=dev)
+        self.base, b = [], 0
+        for leg in legs:
+            self.base.append(b)
+            b += C * leg.K
+        self.config_of = [torch.empty(C * l.K, dtype=torch.int32, device=dev) for l in legs]
+        self.attempts = [torch.empty((self.max_sep, l.K), dtype=torch.int64, device=dev) for l in legs]
+        self.accepts = [torch.empty((self.max_sep, l.K), dtype=torch.int64, device=dev) for l in legs]
+        a = self._buffers()
+        hist = torch.empty((q["history"][1] // (R * 4), R, 4), dtype=torch.float64, device=dev)
+        a["history"] = hist
+        seed, cycle = checkpoint_load(self.ctx, path, a)
+        self.counters = a["counters"]
+        self.seed = int(seed)
+        self.history = [h for h in hist]
+        if self.batched:
+            self.ctx.batch_layout(self.lig_of(), self.n_atoms)
+        return int(cycle)
+
     def free_energies(self, li: int, tol=1e-10, max_iter=10000, precision_mode=0, chains=None):
         """MBAR over the recorded components of leg li (optionally a subset of chains)."""
         leg = self.legs[li]
@@ -238,3 +298,15 @@ class ReplicaExchange:
 def bpmf_kT(f_bc, f_cd):
     """beta_T B = f_BC,L + f'_CD: last-minus-first reduced free energy of each ladder ("Estimation")."""
     return (f_bc[-1] - f_bc[0]) + (f_cd[-1] - f_cd[0])
+
+
+def effective_samples(ctx, series):
+    """Effective sample size of series [cycles][chains] (device float64): the sum over chains of
+    N / g, with g the statistical inefficiency of each chain's whole series from the library's
+    equilibration kernel (its first candidate start, t0 = 0)."""
+    T = int(series.shape[0])
+    s = series.reshape(T, -1).contiguous()
+    if T < 2:
+        return float(s.shape[1] * T)
+    g, _, _ = ctx.detect_equilibration(s, n_cand=1)
+    return float((T / g[:, 0]).sum().item())

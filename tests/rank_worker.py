@@ -61,3 +61,34 @@ def ladder_worker(rank, world, port, n_chains, out):
             np.savez(out, comps=gc.numpy(), states=gs.numpy(), x=gx.numpy(), slowest=slowest, total=total)
     finally:
         dist.destroy_process_group()
+
+
+def harmonic_ukn(K=6, n_per=700, seed=8):
+    """u_kn of exact samples of K harmonic wells (deterministic), with N_k."""
+    bk, mu, x, N_k = S.harmonic_oscillator_samples(K, n_per, seed=seed, D=2)
+    return 0.5 * bk[:, None] * ((x[None, :, :] - mu[:, None, :]) ** 2).sum(-1), N_k
+
+
+def mbar_split(N, world, rank):
+    """Uneven contiguous column blocks: rank r holds a block proportional to r + 1."""
+    w = np.arange(1, world + 1, dtype=np.float64)
+    edges = np.concatenate([[0], np.round(np.cumsum(w) / w.sum() * N)]).astype(int)
+    return edges[rank], edges[rank + 1]
+
+
+def mbar_worker(rank, world, port, out):
+    """MBAR sharded over samples: each rank's pairs from the oracle's FP64 state sums of its own
+    columns, one all_gather per iteration, the library's update on every rank."""
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        u, N_k = harmonic_ukn()
+        a, b = mbar_split(u.shape[1], world, rank)
+        ul = u[:, a:b]
+        f, it = ranks.mbar_sharded(None, None, N_k, tol=1e-12, partials=lambda f: oracle.mbar_partials(ul, N_k, f))
+        np.savez(out + ".%d.npz" % rank, f=f, it=it)
+    finally:
+        dist.destroy_process_group()

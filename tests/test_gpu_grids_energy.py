@@ -201,7 +201,10 @@ def test_precision_study_paper_scale(paper_scale, capsys):
         print("  dH of 50-step trials (kcal/mol): median %.2e, max %.2e" % (np.median(herr), herr.max()))
     assert frel.max() < 1e-5
     assert np.all(cerr <= 1e-5 * np.maximum(cref, 1.0) + 1e-4)
-    assert np.median(herr) < 1e-2
+    # measured: median 4.6e-4, max 1.8e-3 kcal/mol.  FP32 and FP64 trajectories part slowly over 50
+    # steps, so every trial's dH is bounded, not only the typical one.
+    assert np.median(herr) < 2e-3
+    assert herr.max() < 2e-2
 
 
 def test_precision_study_bpmf_paper_scale(paper_scale, capsys):
@@ -252,3 +255,35 @@ def test_precision_study_bpmf_paper_scale(paper_scale, capsys):
                                                                                   np.abs(dU).max(), r["f"]))
         print("  Delta BPMF (FP64 - FP32): %.2e +- %.1e kT" % (dB, sB))
     assert abs(dB) < 0.05
+
+
+def test_exchange_bit_exact_on_paper_scale_components(paper_scale, capsys):
+    """Replica exchange (Eq. (repXacc)) on components the energy path gives for paper-scale
+    configurations: U_L of hundreds of kcal/mol and grid terms of tens, over the 32 warming and 96
+    coupling states.  Each decision takes the FP32 shortcut only when the FP32 log-ratio is more
+    than 1e-3 + 1e-6 sum|terms| from the log-uniform; at these magnitudes that band is wide, and
+    the permutations and counts must still equal the oracle's FP64 decisions bit for bit."""
+    sys_, g32, T, alpha, dt, ctx, osys = paper_scale
+    K = len(T)
+    Kbc = int(np.sum(np.isnan(alpha)))
+    for (k0, Kl), L, seed in (((0, Kbc), 8, 41), ((Kbc, K - Kbc), 8, 42)):
+        x = configurations(sys_, L * Kl, seed=seed, jitter=0.1)
+        c = torch.empty((L * Kl, 4), dtype=torch.float64, device="cuda")
+        ctx.reduced_energies(L * Kl, x=torch.from_numpy(x).cuda(), comps=c)
+        comps = c.cpu().numpy().reshape(L, Kl, 4)
+        with capsys.disabled():
+            print("\nexchange on paper-scale components, states %d-%d: median |U_L| %.0f, |Psi_sg| %.1f, |Psi_g| %.1f"
+                  % (k0, k0 + Kl - 1, *np.median(np.abs(comps[..., [0, 2, 3]]), axis=(0, 1))))
+        assert np.median(np.abs(comps[..., 0])) > 100.0
+        cfg0 = np.stack([np.random.default_rng(seed + l).permutation(Kl) for l in range(L)]).astype(np.int32)
+        cfg_o, att_o, acc_o = oracle.exchange(T[k0:k0 + Kl], alpha[k0:k0 + Kl], comps, cfg0, 25, 5, 0xABCDEF, 3,
+                                              ladder_offset=5)
+        cfg = torch.from_numpy(cfg0.copy()).cuda()
+        att = torch.zeros((5, Kl), dtype=torch.int64, device="cuda")
+        acc = torch.zeros((5, Kl), dtype=torch.int64, device="cuda")
+        ctx.exchange(Kl, k0, c.view(L, Kl, 4), cfg, None, n_sweeps=25, max_sep=5, seed=0xABCDEF, cycle=3,
+                     ladder_offset=5, attempts=att, accepts=acc)
+        assert np.array_equal(cfg.cpu().numpy(), cfg_o)
+        assert np.array_equal(att.cpu().numpy(), att_o)
+        assert np.array_equal(acc.cpu().numpy(), acc_o)
+        assert acc_o.sum() > 0

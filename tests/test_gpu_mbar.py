@@ -43,11 +43,12 @@ def test_mbar_fp32_exponentials(ctx):
 def test_mbar_fp32_compensated(ctx):
     """Precision mode 2: columns shifted by their minimum in FP64 (exact in the result), then FP32
     arguments, exponentials and Kahan-compensated sums.  The arguments carry FP32 rounding of
-    values of a few kT (~1e-7 kT each), so f agrees with the FP64 oracle to well within 1e-4 kT."""
+    values of a few kT (~1e-7 kT each), so f agrees with the FP64 oracle within 1e-6 kT."""
     u, N_k = _ukn(6, 4000, seed=6)
     f_o, _ = oracle.mbar(u, N_k, tol=1e-10)
     f, it = ctx.mbar(torch.from_numpy(u).cuda(), N_k, tol=1e-9, max_iter=10000, precision_mode=2)
-    assert np.max(np.abs(f - f_o)) < 1e-4
+    # measured: about 3e-8 kT; the bound is the 1e-6 kT stated for the FP32 modes
+    assert np.max(np.abs(f - f_o)) < 1e-6
 
 
 def test_mbar_unsampled_states_and_nonconvergence(ctx):
@@ -115,5 +116,31 @@ def test_mbar_precision_study_K256_N1e6(ctx, capsys):
         print("  FP32 compensated vs FP64: max %.2e kT (%d iterations, %.2f ms each, incl. the shift)"
               % (dc.max(), itc, 1e3 * tc))
     assert err.max() < 0.1
-    assert d.max() < 1e-4
-    assert dc.max() < 1e-3
+    assert d.max() < 1e-6   # measured 1.0e-8 kT
+    assert dc.max() < 1e-6  # measured 3.0e-8 kT
+
+
+def test_mbar_partials_match_the_oracle_and_a_sharded_solve_matches_one_process(ctx):
+    """MBAR sharded over samples: the device's (max, sum) state pairs of one iteration equal the
+    oracle's FP64 state sums of the same columns (1e-12 relative), and a solve whose samples sit in
+    three uneven shards (launched one after another on this GPU, merged on the host by the library's
+    update, as the ranks of a multi-GPU run do) equals the one-process device solve within 1e-10 kT."""
+    from paper_1507_03703_gb300.algdock import mbar_update
+    u, N_k = _ukn(8, 5000, seed=12)
+    ud = torch.from_numpy(u).cuda()
+    f = np.linspace(0.0, 1.5, 8)
+    p_dev = ctx.mbar_partials(ud, N_k, f)
+    p_ora = oracle.mbar_partials(u, N_k, f)
+    assert np.max(np.abs(p_dev[:, 0] - p_ora[:, 0])) < 1e-12
+    assert np.max(np.abs(p_dev[:, 1] / p_ora[:, 1] - 1)) < 1e-12
+    cuts = [0, 7000, 7001, u.shape[1]]
+    shards = [ud[:, a:b].contiguous() for a, b in zip(cuts, cuts[1:])]
+    g, it = np.zeros(8), 0
+    for it in range(1, 10001):
+        g, d = mbar_update(np.stack([ctx.mbar_partials(s, N_k, g) for s in shards]), g)
+        if d < 1e-12:
+            break
+    f_one, _ = ctx.mbar(ud, N_k, tol=1e-12)
+    assert np.max(np.abs(g - f_one)) < 1e-10
+    empty = ctx.mbar_partials(ud[:, :0], N_k, f)
+    assert np.all(empty[:, 0] == -np.inf) and np.all(empty[:, 1] == 0)

@@ -1,5 +1,6 @@
-"""The scalar steps of protocol initialization that run on the host (the thermodynamic-length
-parameter steps and the time-step rule, "Initialization") agree with the oracle's to rounding."""
+"""The scalar steps of protocol initialization, which the library computes on the host (the
+thermodynamic-length parameter steps, the time-step rule and the insertion rule: "Initialization",
+"Equilibration and production"), agree with the oracle's to rounding.  No GPU is needed."""
 import math
 
 import numpy as np
@@ -23,8 +24,15 @@ def test_temperature_step_and_time_step_rule():
     for dt in (0.1, 0.2, 2.0, 4.9, 5.0):
         for acc in (0.0, 0.05, 0.1, 0.3, 0.4, 0.6, 0.8, 0.81, 1.0):
             assert P.adapt_dt(dt, acc) == oracle.adapt_dt(dt, acc)
-    assert math.isclose(P.d_alpha_g(0.5), 0.0, abs_tol=1e-15)
-    assert np.sign(P.d_alpha_sg(0.2)) > 0 > np.sign(P.d_alpha_sg(0.8))
+    # invalid inputs are refused, not extrapolated
+    from paper_1507_03703_gb300.algdock import AlgdockError
+    for bad in ((-1.0, 1.0, 0.3), (300.0, -1.0, 0.3), (300.0, 1.0, 0.0)):
+        with pytest.raises(AlgdockError):
+            P.next_temperature(*bad)
+    with pytest.raises(AlgdockError):
+        P.next_alpha(1.5, 1.0, 1.0, 1.0, 0.2)
+    with pytest.raises(AlgdockError):
+        P.adapt_dt(2.0, 1.5)
 
 
 def test_state_insertion_rule_matches_the_oracle():

@@ -94,10 +94,12 @@ def test_padded_ligand_adds_inert_atoms(bench_module):
 
 def test_gather_bytes_hand_count(bench_module):
     """alpha = NaN (no grids), 0.25 (soft only in FP32: the hard weight underflows), 1 (hard
-    only): per atom and trial 2 x 192 B of energy evaluations plus (n - 1) x 0, 64, 128 B."""
+    only).  Per atom and evaluation 32 B per active grid (8 corners x 4 B): both energy
+    evaluations read all five grids (160 B), each force-only one 0, 64 (two soft grids) or 96 B
+    (three full grids)."""
     n_atoms, n_steps, R = 7, 11, 3
     got = bench_module.gather_bytes_per_launch(np.array([np.nan, 0.25, 1.0]), R, n_atoms, n_steps)
-    want = R * n_atoms * (3 * 2 * 192 + (n_steps - 1) * (0 + 64 + 128))
+    want = R * n_atoms * (3 * 2 * 160 + (n_steps - 1) * (0 + 64 + 96))
     assert got == want
 
 
