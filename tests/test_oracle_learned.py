@@ -190,3 +190,81 @@ def test_learned_chain_samples_the_dihedral_marginal():
     expect = w / w.sum() * len(phis)
     # samples within a chain are correlated: allow a generous multiple of the Poisson error
     assert np.all(np.abs(hist - expect) < 6 * np.sqrt(expect * 5) + 20), (hist, expect.round())
+
+
+def test_features_of_a_closed_form_geometry():
+    """The feature vector (reading L1 of the learned proposal's definitions) of a four-atom chain
+    whose every feature is known in closed form: equal masses (the centre of mass is the mean of
+    the positions), a dihedral of exactly 60 degrees about the one rotatable bond 1-2 (cos 1/2,
+    sin sqrt(3)/2 with the usual sign convention), a state with alpha = 1/2 (alpha_sg = 1 and
+    alpha_g = 0 exactly) at 450 K, and components whose asinh(c / 10) are 1, 0, -1/2, 2."""
+    lig = S.make_ligand(4, seed=7)
+    lig.bonds = np.array([[0, 1], [1, 2], [2, 3]], dtype=np.int32)
+    lig.angles = np.array([[0, 1, 2], [1, 2, 3]], dtype=np.int32)
+    lig.angle_k, lig.angle_theta0 = np.full(2, 60.0), np.full(2, 1.9)
+    lig.torsions = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    lig.torsion_V, lig.torsion_gamma = np.zeros((1, 3)), np.zeros((1, 3))
+    lig.bond_k, lig.bond_r0 = np.full(3, 300.0), np.full(3, 1.5)
+    lig.mass = np.full(4, 12.0)
+    phi = np.pi / 3
+    x = np.array([[0.0, 1.5, 0.0], [0.0, 0.0, 0.0], [1.5, 0.0, 0.0],
+                  [1.5, 1.5 * np.cos(phi), 1.5 * np.sin(phi)]])
+    site = np.array([0.25, -0.5, 1.0])
+    g = S.cube_grid(np.zeros(3), 1.0, 3)
+    z = np.zeros((3, 3, 3))
+    osys = oracle.OracleSystem(g, z, z, z, lig, [450.0], [0.5], [2.0], site=site, d0=4.0)
+    assert osys.learned_ntorsions() == 1
+    comps = np.array([10 * np.sinh(1.0), 0.0, -10 * np.sinh(0.5), 10 * np.sinh(2.0)])
+    f = osys.features(x, comps, 0)
+    com = np.array([0.75, (1.5 + 0.75) / 4, 1.5 * np.sqrt(3) / 8])
+    want = np.zeros(64)
+    want[0:3] = (com - site) / 4.0
+    want[3:6] = (x[0] - com) / np.linalg.norm(x[0] - com)
+    want[6:9] = (x[3] - com) / np.linalg.norm(x[3] - com)
+    want[9:11] = [0.5, np.sqrt(3) / 2]
+    want[41:44] = [1.0, 0.0, 2.0 / 3.0]
+    want[44:48] = [1.0, 0.0, -0.5, 2.0]
+    assert np.max(np.abs(f - want)) < 1e-12, np.nonzero(np.abs(f - want) > 1e-12)
+    # the opposite handedness flips only the sine
+    x2 = x.copy()
+    x2[3, 2] = -x2[3, 2]
+    f2 = osys.features(x2, comps, 0)
+    assert abs(f2[9] - 0.5) < 1e-12 and abs(f2[10] + np.sqrt(3) / 2) < 1e-12
+
+
+def test_mlp_forward_of_a_hand_valued_network():
+    """A network with a handful of dyadic weights, evaluated by hand: every value is exact in
+    FP64, every bias enters, and ReLU cuts exactly the negative pre-activations (h1[1], h1[2],
+    h2[1] below), so a dropped bias, a misplaced ReLU or a transposed weight changes the result."""
+    oracle.set_bf16_activations(False)
+    p = {"W1": np.zeros((256, 64)), "b1": np.zeros(256), "W2": np.zeros((256, 256)), "b2": np.zeros(256),
+         "W3": np.zeros((256, 256)), "b3": np.zeros(256), "W4": np.zeros((360, 256)), "b4": np.zeros(360)}
+    p["W1"][0, 0], p["b1"][0] = 2.0, -1.0      # h1[0] = relu(2 - 1) = 1
+    p["W1"][1, 0], p["b1"][1] = -3.0, 0.5      # h1[1] = relu(-3 + 0.5) = 0
+    p["W1"][2, 1] = 1.0                        # h1[2] = relu(x1 = -2) = 0
+    p["W1"][3, 1], p["b1"][3] = -0.25, 0.0     # h1[3] = relu(0.5) = 0.5
+    p["W2"][0, 0], p["W2"][0, 1], p["W2"][0, 3], p["b2"][0] = 3.0, 7.0, 0.5, 0.25   # h2[0] = 3 + 0.25 + 0.25 = 3.5
+    p["W2"][1, 0], p["b2"][1] = -1.0, 0.5      # h2[1] = relu(-0.5) = 0
+    p["W3"][0, 0], p["b3"][0] = 0.5, -1.0      # h3[0] = relu(1.75 - 1) = 0.75
+    p["W3"][1, 0], p["W3"][1, 1], p["b3"][1] = 1.0, 9.0, 0.125   # h3[1] = 3.625
+    p["W4"][0, 0], p["W4"][0, 1], p["b4"][0] = 2.0, -1.0, 0.5    # out[0] = 1.5 - 3.625 + 0.5 = -1.625
+    p["W4"][5, 1] = 1.0                        # out[5] = 3.625
+    p["b4"][7] = -4.0                          # out[7] = -4
+    X = np.zeros((2, 64))
+    X[0, 0], X[0, 1] = 1.0, -2.0
+    out, h1, h2, h3 = oracle.mlp_forward(p, X)
+    w1 = np.zeros(256)
+    w1[[0, 3]] = [1.0, 0.5]
+    w2 = np.zeros(256)
+    w2[0] = 3.5
+    w3 = np.zeros(256)
+    w3[[0, 1]] = [0.75, 3.625]
+    wo = np.zeros(360)
+    wo[[0, 5, 7]] = [-1.625, 3.625, -4.0]
+    assert np.array_equal(h1[0], w1) and np.array_equal(h2[0], w2) and np.array_equal(h3[0], w3)
+    assert np.array_equal(out[0], wo)
+    # the zero input: only the biases that survive ReLU reach the output
+    z1 = np.zeros(256)
+    z1[1] = 0.5
+    assert np.array_equal(h1[1], z1)
+    assert h2[1, 0] == 0.25 + 7.0 * 0.5 and h2[1, 1] == 0.5
