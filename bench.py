@@ -259,8 +259,8 @@ def measured_peaks():
         return {}
 
 
-def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=40, train_iter=300, cmp_cycles=200,
-                     n_moves=4, lag=None, seed=7, target=N_STATES_BC, n_torsions=0):
+def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=489, train_iter=500, cmp_cycles=200,
+                     n_moves=4, lag=None, seed=7, target=N_STATES_BC, n_torsions=-1):
     """Effective samples per second at one state of plain HMC and of HMC plus learned proposals,
     after training the proposal on the plain run's own samples: moves between random pairs of
     samples (lag None) or between poses of the same chain `lag` cycles apart.  The default state
@@ -933,28 +933,31 @@ def main():
                        "peak_source": "random 8-corner cell gathers of both lattices (algdock_gather_probe), "
                                       "measured in this run"}
 
-    # end to end through the C ABI with host buffers: pinned host -> device, step, device -> host
-    h_x = torch.empty((R, lig.n_atoms, 3), dtype=torch.float32, pin_memory=True)
-    h_x.copy_(run.x.cpu())
-    h_out = torch.empty_like(h_x).pin_memory()
-    h_c = torch.empty((R, 4), dtype=torch.float64, pin_memory=True)
+    # end to end through the C ABI with host buffers: algdock_cycle takes the run's arrays in pinned
+    # host memory, copies them in, runs the step (HMC trial, exchange of both legs, snapshot u_kn
+    # into a device buffer) and copies them back before it returns
+    legs_desc = [(l.K, l.state_offset) for l in legs]
+    h_x = run.x.cpu().pin_memory()
+    h_c = run.comps.cpu().pin_memory()
+    h_s = run.state_of.cpu().pin_memory()
+    h_cfg = torch.cat(run.config_of).cpu().pin_memory()
+    u_all = torch.empty(sum(l.K * N_CHAINS * l.K for l in legs), dtype=torch.float64, device=dev)
     e2e_steps = max(2, min(args.steps, 5))
     torch.cuda.synchronize()
     es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     es.record(stream)
     for s in range(e2e_steps):
-        run.x.copy_(h_x, non_blocking=True)
-        step(10_000 + s)
-        h_out.copy_(run.x, non_blocking=True)
-        h_c.copy_(run.comps, non_blocking=True)
+        ctx.cycle(legs_desc, N_CHAINS, 10_000 + s, h_x, h_c, h_s, h_cfg, n_steps=N_VV, seed=run.seed,
+                  rep_offset=run.rep_offset, ladder_offset=run.ladder_offset, counters=run.counters, u_kn=u_all)
     ee.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(es.elapsed_time(ee) / e2e_steps, device=dev)
+    io_bytes = int(h_x.numel() * 4 + h_c.numel() * 8 + h_s.numel() * 4 + h_cfg.numel() * 4)
     e2e = {"value": world * R * lig.n_atoms * N_VV / (e2e_ms * 1e-3), "unit": "evals/s",
-           "h2d_bytes_per_step": int(h_x.numel() * 4), "d2h_bytes_per_step": int(h_out.numel() * 4 + h_c.numel() * 8)}
+           "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes, "call": "algdock_cycle, pinned host arrays"}
 
     acc = run.counters.cpu().numpy()
-    n_trials = R * (args.warmup + args.steps + e2e_steps)
+    n_trials = R * (args.warmup + args.steps + e2e_steps)  # the counters include the e2e steps
     extra = {}
     if not args.no_mbar and rank == 0:
         # MBAR over K = 128 states and ~1e5 samples recorded from the run
@@ -978,8 +981,10 @@ def main():
     if not args.no_batch and rank == 0 and world == 1:
         extra["batching"] = batching(dev, stream)
     if not args.no_learned and rank == 0:
-        # rigid-body learned moves (the paper's external-coordinate moves with a learned proposal) at
-        # the paper's own regime (alpha ~ 0.01), mid-leg, and the fully coupled end
+        # the learned proposal at the sizes of its configuration: a network trained on 2048 chains x
+        # 489 cycles = 1,001,472 plain-HMC poses of the state, batches of 4096 (the tensor-core
+        # path), moves of the rigid body and of every torsion; at the paper's own regime of
+        # external-coordinate moves (alpha ~ 0.01), mid-leg, and the fully coupled end
         extra["learned_vs_plain"] = [learned_vs_plain(ctx, sys_, stream, dev, target=k) for k in
                                      (N_STATES_BC + 1, N_STATES_BC + 28, N_STATES_BC + N_STATES_CD - 1)]
     if not args.no_protocol and world == 1:

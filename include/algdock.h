@@ -501,6 +501,18 @@ algdock_status algdock_mlp_grad(algdock_ctx* ctx, const float* params, const uin
 algdock_status algdock_mlp_adam(algdock_ctx* ctx, float* params, uint16_t* wbf16, const float* grad, float* m, float* v,
                                 int32_t step, float lr);
 
+/* The tensor-core GEMM of the network (tcgen05 with tensor-memory accumulators, operands by TMA;
+ * no counterpart in the paper): C = epi(A . B^T) with A [M][K] (row stride lda) and B [N][K] (ldb)
+ * BF16 bit patterns, device, 16-byte aligned, lda and ldb multiples of 8; C [M][ldc] device.
+ * epilogue 0: FP32; 1: FP32 + bias[N]; 2: BF16 max(0, . + bias[N]); 3: BF16, zero where
+ * mask[M][ldm] (BF16) <= 0.  n_split > 1 (epilogue 0 only) splits K into FP32 partial products at
+ * C + z M ldc, z < number of slices.  Synchronises; ALGDOCK_E_CUDA if a bounded wait of the kernel
+ * ran out.  algdock_mlp_forward and algdock_mlp_grad take this path from 4096 rows (and then
+ * synchronise too). */
+algdock_status algdock_gemm_bf16(algdock_ctx* ctx, int32_t M, int32_t N, int32_t K, const uint16_t* A, int32_t lda,
+                                 const uint16_t* B, int32_t ldb, void* C, int32_t ldc, int32_t epilogue,
+                                 const float* bias, const uint16_t* mask, int32_t ldm, int32_t n_split);
+
 /* n_moves learned proposals for each of n_rep replicas at its state (state_of), each accepted or
  * rejected as above in FP64.  n_torsions limits the moved torsions to the first
  * min(T, n_torsions) (negative: all T); the mixture then covers 6 + that many dimensions, and

@@ -36,7 +36,7 @@ EXPORTS = [
     "algdock_hmc_shape", "algdock_batch_shapes", "algdock_gather_probe", "algdock_grids_load_f64",
     "algdock_energy_force_f64", "algdock_checkpoint_save", "algdock_checkpoint_load", "algdock_mbar_partials",
     "algdock_mbar_update", "algdock_next_temperature", "algdock_next_alpha", "algdock_adapt_dt",
-    "algdock_insert_states", "algdock_cycle",
+    "algdock_insert_states", "algdock_cycle", "algdock_gemm_bf16",
 ]
 
 BATCH_CLASSES = 4             # launch classes of a multi-ligand batch
@@ -178,6 +178,7 @@ def load_library(path: str = LIB_PATH):
         "algdock_propose_learned": ([vp, vp, vp, i64, vp, vp, vp, i32, i32, u64, u64, i64, vp, vp], C.c_int),
         "algdock_mbar_partials": ([vp, i32, i64, vp, vp, vp, i32, vp], C.c_int),
         "algdock_cycle": ([vp, C.POINTER(RunDescC), u64, vp, vp, vp, vp, vp, vp], C.c_int),
+        "algdock_gemm_bf16": ([vp, i32, i32, i32, vp, i32, vp, i32, vp, i32, i32, vp, vp, i32, i32], C.c_int),
         "algdock_mbar_update": ([i32, i32, vp, vp, vp, C.POINTER(dbl)], C.c_int),
         "algdock_next_temperature": ([dbl, dbl, dbl, dbl, C.POINTER(dbl)], C.c_int),
         "algdock_next_alpha": ([dbl, dbl, dbl, dbl, dbl, dbl, dbl, C.POINTER(dbl)], C.c_int),
@@ -684,6 +685,17 @@ class Context:
             self.h, C.byref(d), int(cycle), ptr(x, torch.float32, "x"), ptr(comps, torch.float64, "comps"),
             ptr(state_of, torch.int32, "state_of"), ptr(config_of, torch.int32, "config_of"),
             ptr(counters, torch.int64, "counters"), ptr(u_kn, torch.float64, "u_kn")))
+
+    def gemm_bf16(self, A, B, C, epilogue=0, bias=None, mask=None, n_split=1):
+        """algdock_gemm_bf16: C = epi(A . B^T) on tcgen05; A [M][K], B [N][K] bfloat16 (or int16 bit
+        patterns) device tensors, C [M][N] (or [slices][M][N] with n_split) float32 / bfloat16."""
+        import torch
+        M, K = A.shape
+        N = B.shape[0]
+        self._check(self._L.algdock_gemm_bf16(
+            self.h, int(M), int(N), int(K), A.data_ptr(), int(A.stride(0)), B.data_ptr(), int(B.stride(0)),
+            C.data_ptr(), int(N), int(epilogue), bias.data_ptr() if bias is not None else None,
+            mask.data_ptr() if mask is not None else None, int(N), int(n_split)))
 
     def mbar_partials(self, u_kn, N_k, f, precision_mode=0):
         """This process's (max, sum) pair per state of one MBAR iteration ([K][2] numpy)."""

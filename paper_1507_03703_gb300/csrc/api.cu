@@ -91,6 +91,19 @@ cudaError_t device_view(cudaStream_t s, const void* p, size_t bytes, const void*
   return cudaSuccess;
 }
 
+// The device word where the tensor-core (tcgen05) GEMMs report a bounded wait that ran out, and its
+// check: synchronises the context's stream and turns a set word into ALGDOCK_E_CUDA.
+int* tc_err_word(algdock_ctx* c) { return (int*)((char*)c->d_work + 64); }
+algdock_status tc_check(algdock_ctx* c, const char* where) {
+  cudaError_t e = cudaMemcpyAsync(c->h_flag, tc_err_word(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  if (*c->h_flag != 0)
+    return fail(c, ALGDOCK_E_CUDA, std::string(where) + ": a tensor-core GEMM wait timed out (code " +
+                                       std::to_string(*c->h_flag) + ")");
+  return ALGDOCK_OK;
+}
+
 // Host copy of a (host or device) double array.
 cudaError_t host_view(cudaStream_t s, const double* p, size_t n, std::vector<double>& out) {
   out.resize(n);
@@ -1348,9 +1361,11 @@ algdock_status algdock_mlp_forward(algdock_ctx* c, const float* params, const ui
   Device g(c->device);
   algdock_status st = learn_scratch(c, learned_forward_scratch(N), "mlp_forward");
   if (st != ALGDOCK_OK) return st;
-  cudaError_t e = learned_forward(c->stream, params, wbf16, N, feat, out, c->d_learn);
+  const bool tc = N >= kTcMinRows;
+  cudaError_t e = tc ? cudaMemsetAsync(tc_err_word(c), 0, sizeof(int), c->stream) : cudaSuccess;
+  if (e == cudaSuccess) e = learned_forward(c->stream, params, wbf16, N, feat, out, c->d_learn, tc_err_word(c));
   if (e != cudaSuccess) return cuda_fail(c, e, "mlp_forward");
-  return ALGDOCK_OK;
+  return tc ? tc_check(c, "mlp_forward") : ALGDOCK_OK;
   ALGDOCK_CATCH(c)
 }
 
@@ -1365,9 +1380,12 @@ algdock_status algdock_mlp_grad(algdock_ctx* c, const float* params, const uint1
   Device g(c->device);
   algdock_status st = learn_scratch(c, learned_grad_scratch(N), "mlp_grad");
   if (st != ALGDOCK_OK) return st;
-  cudaError_t e = learned_grad(c->stream, params, wbf16, N, feat, delta, D, grad, loss, c->d_learn);
+  const bool tc = N >= kTcMinRows;
+  cudaError_t e = tc ? cudaMemsetAsync(tc_err_word(c), 0, sizeof(int), c->stream) : cudaSuccess;
+  if (e == cudaSuccess)
+    e = learned_grad(c->stream, params, wbf16, N, feat, delta, D, grad, loss, c->d_learn, tc_err_word(c));
   if (e != cudaSuccess) return cuda_fail(c, e, "mlp_grad");
-  return ALGDOCK_OK;
+  return tc ? tc_check(c, "mlp_grad") : ALGDOCK_OK;
   ALGDOCK_CATCH(c)
 }
 
@@ -1536,6 +1554,29 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
   if (e == cudaSuccess && any_host) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cycle");
   return ALGDOCK_OK;
+  ALGDOCK_CATCH(c)
+}
+
+algdock_status algdock_gemm_bf16(algdock_ctx* c, int32_t M, int32_t N, int32_t K, const uint16_t* A, int32_t lda,
+                                 const uint16_t* B, int32_t ldb, void* C, int32_t ldc, int32_t epilogue,
+                                 const float* bias, const uint16_t* mask, int32_t ldm, int32_t n_split) {
+  ALGDOCK_TRY(c)
+  if (M < 0 || N < 0 || K < 1 || lda < K || ldb < K || lda % 8 || ldb % 8 || epilogue < 0 || epilogue > 3 ||
+      ldc < N || n_split < 1 || ((epilogue == 1 || epilogue == 2) && !bias) || (epilogue == 3 && (!mask || ldm < N)) ||
+      (n_split > 1 && epilogue != 0))
+    return fail(c, ALGDOCK_E_INVALID, "gemm_bf16: bad arguments");
+  if (M == 0 || N == 0) return ALGDOCK_OK;
+  if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C) || (bias && !is_device_ptr(bias)) ||
+      (mask && !is_device_ptr(mask)))
+    return fail(c, ALGDOCK_E_INVALID, "gemm_bf16: arrays must be device pointers");
+  if ((((uintptr_t)A) | ((uintptr_t)B)) & 15) return fail(c, ALGDOCK_E_INVALID, "gemm_bf16: A and B 16-byte aligned");
+  Device g(c->device);
+  if (!umma_supported(c->device)) return fail(c, ALGDOCK_E_INVALID, "gemm_bf16: needs an sm_100-class device");
+  cudaError_t e = cudaMemsetAsync(tc_err_word(c), 0, sizeof(int), c->stream);
+  if (e == cudaSuccess)
+    e = umma_gemm(c->stream, M, N, K, A, lda, B, ldb, C, ldc, epilogue, bias, mask, ldm, n_split, tc_err_word(c));
+  if (e != cudaSuccess) return cuda_fail(c, e, "gemm_bf16");
+  return tc_check(c, "gemm_bf16");
   ALGDOCK_CATCH(c)
 }
 

@@ -332,12 +332,23 @@ cudaError_t learned_features(cudaStream_t s, const algdock_ctx& c, int64_t N, co
                              const float* x, const double* comps, float* feat);
 cudaError_t learned_pose_delta(cudaStream_t s, const algdock_ctx& c, int64_t N, const float* x, const float* y,
                                float* delta);
+// tcgen05 BF16 GEMM (umma.cu): C = epi(A . B^T), A [M][K], B [N][K] row-major BF16; epi 0: FP32,
+// 1: FP32 + bias, 2: BF16 ReLU(+ bias), 3: BF16 masked by mask > 0; n_split > 1 splits K into FP32
+// partial tiles C + z M ldc.  *err (device int) is set if a bounded wait runs out.
+bool umma_supported(int device);
+cudaError_t umma_gemm(cudaStream_t s, int M, int N, int K, const void* A, int lda, const void* B, int ldb, void* C,
+                      int ldc, int epi, const float* bias, const void* mask, int ldm, int n_split, int* err);
+int umma_split_count(int K, int n_split);
+cudaError_t transpose_to_bf16(cudaStream_t s, int rows, int cols, const void* in, int ld_in, bool in_f32, void* out,
+                              int ld_out);
+// Rows from which the learned network's forward pass and gradient run on tcgen05 (with tc_err set).
+constexpr int64_t kTcMinRows = 4096;
 size_t learned_forward_scratch(int64_t N);
 cudaError_t learned_forward(cudaStream_t s, const float* params, const uint16_t* wbf16, int64_t N, const float* feat,
-                            float* out, void* scratch);
+                            float* out, void* scratch, int* tc_err = nullptr);
 size_t learned_grad_scratch(int64_t N);
 cudaError_t learned_grad(cudaStream_t s, const float* params, const uint16_t* wbf16, int64_t N, const float* feat,
-                         const float* delta, int D, float* grad, float* loss, void* scratch);
+                         const float* delta, int D, float* grad, float* loss, void* scratch, int* tc_err = nullptr);
 cudaError_t learned_adam(cudaStream_t s, float* params, uint16_t* wbf16, const float* grad, float* m, float* v, int step,
                          float lr);
 size_t learned_propose_scratch(int64_t n_rep, int na);

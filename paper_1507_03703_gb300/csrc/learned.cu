@@ -1078,7 +1078,49 @@ cudaError_t learned_pose_delta(cudaStream_t s, const algdock_ctx& c, int64_t N, 
 // Scratch of the forward pass: the packed weights, then h1, h2, h3 (BF16 [N][256]) for the
 // layer-by-layer path.
 static size_t packed_bytes() { return align256((size_t)F_PACKED * sizeof(bf16)); }
-size_t learned_forward_scratch(int64_t N) { return packed_bytes() + 3 * align256((size_t)N * NHID * sizeof(bf16)); }
+size_t learned_forward_scratch(int64_t N) {
+  return packed_bytes() + 3 * align256((size_t)N * NHID * sizeof(bf16)) + align256((size_t)N * NFEAT * sizeof(bf16));
+}
+
+// The tensor-core (tcgen05) path: from kTcMinRows rows, on an sm_100-class device, with an error word.
+static bool use_tc(int64_t N, const int* err) {
+  if (!err || N < kTcMinRows || N > (int64_t)1 << 30) return false;
+  static std::atomic<int> ok[64];  // 0 unknown, 1 yes, 2 no
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  int v = ok[dev].load(std::memory_order_acquire);
+  if (v == 0) {
+    v = umma_supported(dev) ? 1 : 2;
+    ok[dev].store(v, std::memory_order_release);
+  }
+  return v == 1;
+}
+
+__global__ void to_bf16_kernel(int64_t n, const float* __restrict__ in, bf16* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __float2bfloat16(in[i]);
+}
+
+// The four layers as tcgen05 GEMMs with fused epilogues (BF16 hidden activations, FP32 outputs).
+static cudaError_t forward_tc(cudaStream_t s, const float* params, const bf16* W, int64_t N, const float* feat,
+                              float* out, bf16* f16, bf16* h1, bf16* h2, bf16* h3, int* err) {
+  const int n = (int)N;
+  to_bf16_kernel<<<(unsigned)((N * NFEAT + 255) / 256), 256, 0, s>>>(N * NFEAT, feat, f16);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = umma_gemm(s, n, NHID, NFEAT, f16, NFEAT, W + WOFF_1, NFEAT, h1, NHID, EPI_RELU_BF16, params + OFF_B1, nullptr,
+                  0, 1, err);
+  if (e == cudaSuccess)
+    e = umma_gemm(s, n, NHID, NHID, h1, NHID, W + WOFF_2, NHID, h2, NHID, EPI_RELU_BF16, params + OFF_B2, nullptr, 0, 1,
+                  err);
+  if (e == cudaSuccess)
+    e = umma_gemm(s, n, NHID, NHID, h2, NHID, W + WOFF_3, NHID, h3, NHID, EPI_RELU_BF16, params + OFF_B3, nullptr, 0, 1,
+                  err);
+  if (e == cudaSuccess)
+    e = umma_gemm(s, n, NOUT, NHID, h3, NHID, W + WOFF_4, NHID, out, NOUT, EPI_F32_BIAS, params + OFF_B4, nullptr, 0, 1,
+                  err);
+  return e;
+}
 
 static cudaError_t pack_weights(cudaStream_t s, const bf16* W, bf16* Wp) {
   pack_weights_kernel<<<(F_PACKED + 255) / 256, 256, 0, s>>>(W, Wp);
@@ -1128,12 +1170,15 @@ static cudaError_t forward_run(cudaStream_t s, const float* params, const bf16* 
 // Forward pass with its scratch laid out as learned_forward_scratch; pack: (re)pack the weights
 // first (false when an earlier call on the same scratch and weights already did).
 static cudaError_t forward_scratch(cudaStream_t s, const float* params, const uint16_t* wbf16, int64_t N,
-                                   const float* feat, float* out, void* scratch, bool pack) {
+                                   const float* feat, float* out, void* scratch, bool pack, int* tc_err = nullptr) {
   if (N == 0) return cudaSuccess;
   char* p = (char*)scratch;
   bf16* Wp = (bf16*)p;
   p += packed_bytes();
   const size_t hb = align256((size_t)N * NHID * sizeof(bf16));
+  if (use_tc(N, tc_err))
+    return forward_tc(s, params, (const bf16*)wbf16, N, feat, out, (bf16*)(p + 3 * hb), (bf16*)p, (bf16*)(p + hb),
+                      (bf16*)(p + 2 * hb), tc_err);
   if (pack) {
     const cudaError_t e = pack_weights(s, (const bf16*)wbf16, Wp);
     if (e != cudaSuccess) return e;
@@ -1143,20 +1188,48 @@ static cudaError_t forward_scratch(cudaStream_t s, const float* params, const ui
 }
 
 cudaError_t learned_forward(cudaStream_t s, const float* params, const uint16_t* wbf16, int64_t N, const float* feat,
-                            float* out, void* scratch) {
-  return forward_scratch(s, params, wbf16, N, feat, out, scratch, true);
+                            float* out, void* scratch, int* tc_err) {
+  return forward_scratch(s, params, wbf16, N, feat, out, scratch, true, tc_err);
 }
 
 // Scratch of the gradient: h1..h3, dh (two BF16 buffers), out and dout (FP32), dout (BF16), loss
 // rows, and the split partial products of the weight gradients.
+static int64_t pad8(int64_t n) { return (n + 7) / 8 * 8; }
+
 size_t learned_grad_scratch(int64_t N) {
   return 5 * align256((size_t)N * NHID * sizeof(bf16)) + 2 * align256((size_t)N * NOUT * sizeof(float)) +
          align256((size_t)N * NOUT * sizeof(bf16)) + align256((size_t)N * sizeof(float)) +
-         align256((size_t)kWgradSplit * NOUT * NHID * sizeof(float)) + packed_bytes();
+         align256((size_t)kWgradSplit * NOUT * NHID * sizeof(float)) + packed_bytes() +
+         // the tensor-core path: operands transposed for the weight gradients, a transposed weight
+         // matrix and the BF16 features
+         align256((size_t)NOUT * pad8(N) * sizeof(bf16)) + align256((size_t)NHID * pad8(N) * sizeof(bf16)) +
+         align256((size_t)NHID * NOUT * sizeof(bf16)) + align256((size_t)N * NFEAT * sizeof(bf16));
+}
+
+// Weight gradient C[M][N] = sum_n A[n][M] B[n][N] on tcgen05: both factors transposed to K-major
+// ([M][n] and [N][n]), the batch split into FP32 partial products summed in slice order.
+static cudaError_t wgrad_tc(cudaStream_t s, int M, int N, int n, const void* A, int lda, bool a_f32, const void* B,
+                            int ldb, bool b_f32, float* C, float* part, bf16* TA, bf16* TB, int* err) {
+  const int np = (int)pad8(n);
+  cudaError_t e = transpose_to_bf16(s, n, M, A, lda, a_f32, TA, np);
+  if (e == cudaSuccess) e = transpose_to_bf16(s, n, N, B, ldb, b_f32, TB, np);
+  if (e == cudaSuccess) e = umma_gemm(s, M, N, n, TA, np, TB, np, part, N, EPI_F32, nullptr, nullptr, 0, kWgradSplit, err);
+  if (e != cudaSuccess) return e;
+  const int nz = umma_split_count(n, kWgradSplit);
+  splitk_reduce_kernel<<<(M * N + 255) / 256, 256, 0, s>>>(M * N, nz, part, C);
+  return cudaGetLastError();
+}
+
+// Input gradient dX[n][N] = (dY[n][K] . W[K][N]) masked by H > 0, on tcgen05 with W transposed.
+static cudaError_t dgrad_tc(cudaStream_t s, int n, int N, int K, const bf16* dY, const bf16* W, const bf16* H, bf16* dX,
+                            bf16* WT, int* err) {
+  cudaError_t e = transpose_to_bf16(s, K, N, W, N, false, WT, K);
+  if (e == cudaSuccess) e = umma_gemm(s, n, N, K, dY, K, WT, K, dX, N, EPI_MASK_BF16, nullptr, H, N, 1, err);
+  return e;
 }
 
 cudaError_t learned_grad(cudaStream_t s, const float* params, const uint16_t* wbf16, int64_t N, const float* feat,
-                         const float* delta, int D, float* grad, float* loss, void* scratch) {
+                         const float* delta, int D, float* grad, float* loss, void* scratch, int* tc_err) {
   if (N == 0) return cudaSuccess;
   const bf16* W = (const bf16*)wbf16;
   char* p = (char*)scratch;
@@ -1174,6 +1247,35 @@ cudaError_t learned_grad(cudaStream_t s, const float* params, const uint16_t* wb
   float* part = (float*)((char*)lrow + align256((size_t)N * sizeof(float)));
   bf16* Wp = (bf16*)((char*)part + align256((size_t)kWgradSplit * NOUT * NHID * sizeof(float)));
   const int n = (int)N;
+  if (use_tc(N, tc_err)) {
+    char* q = (char*)Wp + packed_bytes();
+    bf16* TA = (bf16*)q;
+    q += align256((size_t)NOUT * pad8(N) * sizeof(bf16));
+    bf16* TB = (bf16*)q;
+    q += align256((size_t)NHID * pad8(N) * sizeof(bf16));
+    bf16* WT = (bf16*)q;
+    q += align256((size_t)NHID * NOUT * sizeof(bf16));
+    bf16* f16 = (bf16*)q;
+    cudaError_t e = forward_tc(s, params, W, N, feat, out, f16, h1, h2, h3, tc_err);
+    if (e != cudaSuccess) return e;
+    nll_kernel<<<(unsigned)((N + 3) / 4), 128, 0, s>>>(N, D, out, delta, dout, dout16, lrow);
+    if (loss) sum_kernel<<<1, 256, 0, s>>>(N, lrow, 1.f / (float)N, loss);
+    e = wgrad_tc(s, NOUT, NHID, n, dout16, NOUT, false, h3, NHID, false, grad + OFF_W4, part, TA, TB, tc_err);
+    if (e == cudaSuccess) e = colsum<float>(s, n, NOUT, dout, grad + OFF_B4, part);
+    if (e == cudaSuccess) e = dgrad_tc(s, n, NHID, NOUT, dout16, W + WOFF_4, h3, dA, WT, tc_err);
+    if (e == cudaSuccess) e = wgrad_tc(s, NHID, NHID, n, dA, NHID, false, h2, NHID, false, grad + OFF_W3, part, TA, TB,
+                                       tc_err);
+    if (e == cudaSuccess) e = colsum<bf16>(s, n, NHID, dA, grad + OFF_B3, part);
+    if (e == cudaSuccess) e = dgrad_tc(s, n, NHID, NHID, dA, W + WOFF_3, h2, dB, WT, tc_err);
+    if (e == cudaSuccess) e = wgrad_tc(s, NHID, NHID, n, dB, NHID, false, h1, NHID, false, grad + OFF_W2, part, TA, TB,
+                                       tc_err);
+    if (e == cudaSuccess) e = colsum<bf16>(s, n, NHID, dB, grad + OFF_B2, part);
+    if (e == cudaSuccess) e = dgrad_tc(s, n, NHID, NHID, dB, W + WOFF_2, h1, dA, WT, tc_err);
+    if (e == cudaSuccess) e = wgrad_tc(s, NHID, NFEAT, n, dA, NHID, false, feat, NFEAT, true, grad + OFF_W1, part, TA,
+                                       TB, tc_err);
+    if (e == cudaSuccess) e = colsum<bf16>(s, n, NHID, dA, grad + OFF_B1, part);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
   cudaError_t e = pack_weights(s, W, Wp);
   if (e == cudaSuccess) e = forward_run(s, params, W, Wp, N, feat, out, h1, h2, h3, true);
   if (e != cudaSuccess) return e;
