@@ -203,6 +203,12 @@ __global__ void __launch_bounds__(128, 1)
   const int row = m0 + 32 * warp + lane;
   float* Cf = (float*)P.C + (size_t)blockIdx.z * P.c_zstride;
   bf16* Cb = (bf16*)P.C;
+  // vector epilogue: 16-byte aligned rows of C (and of the mask and the bias where they are read)
+  const int esz = (EPI == 0 || EPI == 1) ? 4 : 2;
+  const bool vec_ok = ((uintptr_t)P.C % 16 == 0) && ((size_t)P.ldc * esz) % 16 == 0 && (n0 * esz) % 16 == 0 &&
+                      (EPI != 3 || ((uintptr_t)P.mask % 16 == 0 && ((size_t)P.ldm * 2) % 16 == 0)) &&
+                      (!(EPI == 1 || EPI == 2) || (uintptr_t)P.bias % 16 == 0) &&
+                      (EPI != 0 || (P.c_zstride * 4) % 16 == 0);
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 16) {
     float v[16];
@@ -213,9 +219,47 @@ __global__ void __launch_bounds__(128, 1)
       for (int j = 0; j < 16; ++j) v[j] = 0.f;
     }
     if (row >= P.M) continue;
+    const int col0 = n0 + c0;
+    if (col0 + 16 <= P.N && vec_ok) {  // 16-byte loads and stores of the thread's 16 columns
+      if (EPI == 1 || EPI == 2) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 b = __ldg((const float4*)(P.bias + col0) + q);
+          v[4 * q] += b.x;
+          v[4 * q + 1] += b.y;
+          v[4 * q + 2] += b.z;
+          v[4 * q + 3] += b.w;
+        }
+      }
+      if (EPI == 0 || EPI == 1) {
+        float4* dst = (float4*)(Cf + (size_t)row * P.ldc + col0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      } else {
+        if (EPI == 3) {
+          const uint4* mk = (const uint4*)(P.mask + (size_t)row * P.ldm + col0);
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const uint4 m = __ldg(mk + q);
+            const bf16* mh = (const bf16*)&m;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (!(__bfloat162float(mh[j]) > 0.f)) v[8 * q + j] = 0.f;
+          }
+        }
+        uint4 out[2];
+        bf16* oh = (bf16*)out;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) oh[j] = __float2bfloat16(EPI == 2 ? (v[j] > 0.f ? v[j] : 0.f) : v[j]);
+        uint4* dst = (uint4*)(Cb + (size_t)row * P.ldc + col0);
+        dst[0] = out[0];
+        dst[1] = out[1];
+      }
+      continue;
+    }
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      const int col = n0 + c0 + j;
+      const int col = col0 + j;
       if (col >= P.N) break;
       float x = v[j];
       if (EPI == 1 || EPI == 2) x += P.bias[col];
@@ -318,6 +362,8 @@ cudaError_t launch_epi(cudaStream_t s, int bn, const CUtensorMap& a, const CUten
 
 }  // namespace
 
+int umma_split_count(int K, int n_split);
+
 bool umma_supported(int device) {
   int major = 0;
   if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device) != cudaSuccess) {
@@ -332,7 +378,15 @@ cudaError_t umma_gemm(cudaStream_t s, int M, int N, int K, const void* A, int ld
   if (M <= 0 || N <= 0) return cudaSuccess;
   // the operands' TMA rules: 16-byte aligned bases and row strides
   if (K <= 0 || lda % 8 || ldb % 8 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || !err) return cudaErrorInvalidValue;
-  const int bn = N <= 64 ? 64 : (N <= 128 || N > 256 ? 128 : 256);
+  // tile width: wider tiles read A fewer times, narrower ones give more CTAs; the widest that still
+  // gives about two waves of the 152 SMs, down to 64
+  const int mt = (M + kUM - 1) / kUM, zs = n_split < 1 ? 1 : umma_split_count(K, n_split);
+  int bn = 64;
+  for (int c : {256, 128})
+    if (N >= c && (int64_t)mt * ((N + c - 1) / c) * zs >= 2 * 152) {
+      bn = c;
+      break;
+    }
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, M, K, lda, kUM) || !make_map(&mb, B, N, K, ldb, bn)) return cudaErrorInvalidValue;
   n_split = n_split < 1 ? 1 : n_split;
