@@ -260,10 +260,11 @@ def measured_peaks():
 
 
 def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=489, train_iter=500, cmp_cycles=200,
-                     n_moves=4, lag=None, seed=7, target=N_STATES_BC, n_torsions=-1):
+                     n_moves=4, lag=1, mixed=True, seed=7, target=N_STATES_BC, n_torsions=-1):
     """Effective samples per second at one state of plain HMC and of HMC plus learned proposals,
     after training the proposal on the plain run's own samples: moves between random pairs of
-    samples (lag None) or between poses of the same chain `lag` cycles apart.  The default state
+    samples (lag None), between poses of the same chain `lag` cycles apart, or (mixed) as many of
+    each, so that the mixture learns both long jumps and local moves.  The default state
     is the decoupled end of the coupling leg (alpha = 0, 600 K), where the paper applies its own
     external-coordinate moves.  ESS: sum over chains of N / g of the Psi_g series."""
     import torch
@@ -293,6 +294,11 @@ def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=4
         t_idx = np.arange(data_cycles - lag)
         I = (t_idx[:, None] * chains + np.arange(chains)[None, :]).ravel()
         pairs = (I, I + lag * chains)
+        if mixed:  # as many random pairs again, so the mixture learns long jumps and local moves
+            rng_p = np.random.default_rng(seed)
+            S_ = data_cycles * chains
+            pairs = (np.concatenate([I, rng_p.integers(0, S_, size=I.size)]),
+                     np.concatenate([I + lag * chains, rng_p.integers(0, S_, size=I.size)]))
     losses = lp.train(X, Cm, target, n_iter=train_iter, batch=4096, lr=1e-3, seed=seed, pairs=pairs)
     ev[1].record(stream)
     torch.cuda.synchronize()
@@ -303,7 +309,9 @@ def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=4
            "chains": chains, "training_poses": int(X.shape[0]), "train_iters": train_iter, "train_ms": train_ms,
            "loss_first": losses[0], "loss_last": losses[-1], "moves_per_cycle": n_moves,
            "moved_torsions": lp.T,
-           "training_pairs": "random pairs" if lag is None else "same chain, %d cycles apart" % lag}
+           "training_pairs": ("random pairs" if lag is None else
+                              ("half random pairs, half the same chain %d cycles apart" % lag if mixed
+                               else "same chain, %d cycles apart" % lag))}
     for mode in ("plain", "learned"):
         x.copy_(x0)
         comps.copy_(c0)
@@ -841,21 +849,32 @@ def main():
     u_leg = [torch.empty((l.K, N_CHAINS * l.K), dtype=torch.float64, device=dev) for l in legs]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
+    snap_stream = torch.cuda.Stream(device=dev)
+
     def step(cyc, ev=None):
         if ev is not None:
             ev[0].record(stream)
         run.hmc(cyc, N_VV)
         if ev is not None:
             ev[1].record(stream)
-        run.exchange(cyc)
-        if ev is not None:
-            ev[2].record(stream)
-        # the snapshot: energies of every replica in one launch, then u_kn per leg
+        # the snapshot (energies of every replica in one launch, then u_kn per leg) reads only the
+        # configurations, which the exchange does not move: it runs beside the exchange sweeps
+        hmc_done = torch.cuda.Event()
+        hmc_done.record(stream)
+        snap_stream.wait_event(hmc_done)
+        ctx.set_stream(snap_stream)
         ctx.reduced_energies(R, x=run.x, comps=snap)
         for li, leg in enumerate(legs):
             sl = run.leg_slice(li)
             ctx.reduced_energies(N_CHAINS * leg.K, comps=snap[sl], k_begin=leg.state_offset, k_count=leg.K,
                                  u_kn=u_leg[li])
+        snap_done = torch.cuda.Event()
+        snap_done.record(snap_stream)
+        ctx.set_stream(stream)
+        run.exchange(cyc)
+        if ev is not None:
+            ev[2].record(stream)
+        stream.wait_event(snap_done)
         if ev is not None:
             ev[3].record(stream)
 
@@ -913,7 +932,10 @@ def main():
     sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    fl = flops_per_replica_eval(lig) * R * (N_VV + 1)
+    # algorithmic work: the measurement plan's 15 N_a + 60 flop per atom evaluation (pairs plus
+    # bonded terms), times the atom evaluations of a launch (n_steps + 1 force evaluations)
+    fl = (15 * lig.n_atoms + 60) * lig.n_atoms * R * (N_VV + 1)
+    fl_detail = flops_per_replica_eval(lig) * R * (N_VV + 1)
     hmc_avg = sum(hmc_ms) / len(hmc_ms)
     achieved = fl / (hmc_avg * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
@@ -921,7 +943,8 @@ def main():
                 "traffic_ncu_summary": "profiles/hmc_kernel_paper_scale.md",
                 "kernel": "hmc_kernel", "kernel_ms": hmc_avg,
                 "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % (n_sm, sm_max),
-                "flops_per_launch": fl}
+                "flops_per_launch": fl, "flops_rule": "(15 N_a + 60) per atom evaluation",
+                "frac_with_term_by_term_count": fl_detail / (hmc_avg * 1e-3) / 1e12 / peak_tflops}
 
     # the same kernel against the L2 gather roofline: useful lattice bytes per launch over the
     # measured rate of random 8-corner gathers from the same lattices
@@ -999,8 +1022,9 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(sys_, world),
         "roofline": roofline, "roofline_gather": roofline_gather, "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
-        "clocks": clk, "breakdown_ms": {"hmc": hmc_avg, "exchange": sum(ex_ms) / len(ex_ms),
-                                        "snapshot_ukn": sum(ukn_ms) / len(ukn_ms), "wall_per_step_incl_flush":
+        "clocks": clk, "breakdown_ms": {"hmc": hmc_avg, "exchange_both_legs_beside_snapshot": sum(ex_ms) / len(ex_ms),
+                                        "snapshot_tail_after_exchange": sum(ukn_ms) / len(ukn_ms),
+                                        "wall_per_step_incl_flush":
                                         1e3 * wall / args.steps},
         "hmc_cycles_per_s": 1e3 / ms_per_step,
         "hmc_acceptance": float(acc[0]) / max(1, n_trials),

@@ -507,8 +507,8 @@ algdock_status algdock_mlp_adam(algdock_ctx* ctx, float* params, uint16_t* wbf16
  * epilogue 0: FP32; 1: FP32 + bias[N]; 2: BF16 max(0, . + bias[N]); 3: BF16, zero where
  * mask[M][ldm] (BF16) <= 0.  n_split > 1 (epilogue 0 only) splits K into FP32 partial products at
  * C + z M ldc, z < number of slices.  Synchronises; ALGDOCK_E_CUDA if a bounded wait of the kernel
- * ran out.  algdock_mlp_forward and algdock_mlp_grad take this path from 4096 rows (and then
- * synchronise too). */
+ * ran out.  algdock_mlp_grad takes this path from 4096 rows and algdock_mlp_forward from 8192
+ * (and they then synchronise too). */
 algdock_status algdock_gemm_bf16(algdock_ctx* ctx, int32_t M, int32_t N, int32_t K, const uint16_t* A, int32_t lda,
                                  const uint16_t* B, int32_t ldb, void* C, int32_t ldc, int32_t epilogue,
                                  const float* bias, const uint16_t* mask, int32_t ldm, int32_t n_split);

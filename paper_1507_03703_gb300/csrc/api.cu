@@ -518,6 +518,9 @@ void algdock_destroy(algdock_ctx* c) {
   cudaFreeHost(c->h_flag);
   cudaFree(c->d_work);
   cudaFree(c->d_stage);
+  if (c->cycle_side) cudaStreamDestroy(c->cycle_side);
+  if (c->cycle_fork) cudaEventDestroy(c->cycle_fork);
+  if (c->cycle_join) cudaEventDestroy(c->cycle_join);
   delete c;
 }
 
@@ -1361,7 +1364,7 @@ algdock_status algdock_mlp_forward(algdock_ctx* c, const float* params, const ui
   Device g(c->device);
   algdock_status st = learn_scratch(c, learned_forward_scratch(N), "mlp_forward");
   if (st != ALGDOCK_OK) return st;
-  const bool tc = N >= kTcMinRows;
+  const bool tc = N >= kTcMinRowsForward;
   cudaError_t e = tc ? cudaMemsetAsync(tc_err_word(c), 0, sizeof(int), c->stream) : cudaSuccess;
   if (e == cudaSuccess) e = learned_forward(c->stream, params, wbf16, N, feat, out, c->d_learn, tc_err_word(c));
   if (e != cudaSuccess) return cuda_fail(c, e, "mlp_forward");
@@ -1380,7 +1383,7 @@ algdock_status algdock_mlp_grad(algdock_ctx* c, const float* params, const uint1
   Device g(c->device);
   algdock_status st = learn_scratch(c, learned_grad_scratch(N), "mlp_grad");
   if (st != ALGDOCK_OK) return st;
-  const bool tc = N >= kTcMinRows;
+  const bool tc = N >= kTcMinRowsGrad;
   cudaError_t e = tc ? cudaMemsetAsync(tc_err_word(c), 0, sizeof(int), c->stream) : cudaSuccess;
   if (e == cudaSuccess)
     e = learned_grad(c->stream, params, wbf16, N, feat, delta, D, grad, loss, c->d_learn, tc_err_word(c));
@@ -1510,6 +1513,9 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cycle");
     cudaFree(c->d_stage);
+  if (c->cycle_side) cudaStreamDestroy(c->cycle_side);
+  if (c->cycle_fork) cudaEventDestroy(c->cycle_fork);
+  if (c->cycle_join) cudaEventDestroy(c->cycle_join);
     c->d_stage = nullptr;
     c->stage_bytes = 0;
     e = cudaMalloc(&c->d_stage, need);
@@ -1530,7 +1536,30 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
   int64_t* dcnt = (int64_t*)dev_of(5);
   if (e == cudaSuccess)
     e = launch_hmc(c->stream, *c, R, ds, dx, dc, nullptr, nullptr, d->n_steps, d->seed, cycle, d->rep_offset, dcnt);
+  // the snapshot reads only the configurations, which the exchange does not move, so it runs on a
+  // side stream beside the exchange sweeps
+  cudaStream_t snap_s = c->stream;
+  if (e == cudaSuccess && u_kn) {
+    if (!c->cycle_side) e = cudaStreamCreateWithFlags(&c->cycle_side, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c->cycle_fork) e = cudaEventCreateWithFlags(&c->cycle_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !c->cycle_join) e = cudaEventCreateWithFlags(&c->cycle_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(c->cycle_fork, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cycle_side, c->cycle_fork, 0);
+    if (e == cudaSuccess) snap_s = c->cycle_side;
+  }
   int64_t base = 0, cbase = 0, ubase = 0;
+  if (e == cudaSuccess && u_kn) {  // the snapshot: every configuration re-evaluated, then u_kn per leg
+    double* snap = (double*)dev_of(2);
+    e = launch_evaluate(snap_s, *c, R, dx, snap);
+    for (int l = 0; l < d->n_legs && e == cudaSuccess; ++l) {
+      const int64_t n = (int64_t)d->n_chains * d->K[l];
+      e = launch_ukn(snap_s, *c, n, snap + 4 * base, d->state_offset[l], d->K[l], (double*)dev_of(6) + ubase);
+      base += n;
+      ubase += (int64_t)d->K[l] * n;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->cycle_join, snap_s);
+  }
+  base = 0;
   for (int l = 0; l < d->n_legs && e == cudaSuccess; ++l) {
     e = launch_exchange(c->stream, *c, d->n_chains, d->K[l], d->state_offset[l], dc + 4 * base, dcfg + cbase,
                         ds + base, d->n_sweeps, d->max_sep, d->seed, cycle, d->ladder_offset + (int64_t)l * d->n_chains,
@@ -1538,17 +1567,7 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
     base += (int64_t)d->n_chains * d->K[l];
     cbase += (int64_t)d->n_chains * d->K[l];
   }
-  if (e == cudaSuccess && u_kn) {  // the snapshot: every configuration re-evaluated, then u_kn per leg
-    double* snap = (double*)dev_of(2);
-    e = launch_evaluate(c->stream, *c, R, dx, snap);
-    base = 0;
-    for (int l = 0; l < d->n_legs && e == cudaSuccess; ++l) {
-      const int64_t n = (int64_t)d->n_chains * d->K[l];
-      e = launch_ukn(c->stream, *c, n, snap + 4 * base, d->state_offset[l], d->K[l], (double*)dev_of(6) + ubase);
-      base += n;
-      ubase += (int64_t)d->K[l] * n;
-    }
-  }
+  if (e == cudaSuccess && u_kn) e = cudaStreamWaitEvent(c->stream, c->cycle_join, 0);
   for (int i = 0; i < 7 && e == cudaSuccess; ++i)
     if (P[i].host && P[i].user) e = cudaMemcpyAsync(P[i].user, dev_of(i), P[i].bytes, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && any_host) e = cudaStreamSynchronize(c->stream);

@@ -234,9 +234,12 @@ struct algdock_ctx {
   int* h_flag = nullptr;
   // work counter of the single-ligand HMC launch (replicas handed out to warps; zeroed per launch)
   unsigned long long* d_work = nullptr;
-  // device staging of algdock_cycle's host arrays (grown on demand)
+  // device staging of algdock_cycle's host arrays (grown on demand), and the side stream on which
+  // its snapshot runs beside the exchange sweeps
   void* d_stage = nullptr;
   size_t stage_bytes = 0;
+  cudaStream_t cycle_side = nullptr;
+  cudaEvent_t cycle_fork = nullptr, cycle_join = nullptr;
   // learned proposal: torsion tree and scratch grown on demand
   algdock::LearnedTopo ltopo{};
   void* d_learn = nullptr;
@@ -341,8 +344,11 @@ cudaError_t umma_gemm(cudaStream_t s, int M, int N, int K, const void* A, int ld
 int umma_split_count(int K, int n_split);
 cudaError_t transpose_to_bf16(cudaStream_t s, int rows, int cols, const void* in, int ld_in, bool in_f32, void* out,
                               int ld_out);
-// Rows from which the learned network's forward pass and gradient run on tcgen05 (with tc_err set).
-constexpr int64_t kTcMinRows = 4096;
+// Rows from which the learned network's gradient and forward pass run on tcgen05 (with tc_err set):
+// measured against the mma.sync kernels on one GB300, the gradient ties at 4096 rows and wins from
+// 8192 (2.2x at 65536); the forward ties at 8192 and wins from 16384 (1.6x at 65536).
+constexpr int64_t kTcMinRowsGrad = 4096;
+constexpr int64_t kTcMinRowsForward = 8192;
 size_t learned_forward_scratch(int64_t N);
 cudaError_t learned_forward(cudaStream_t s, const float* params, const uint16_t* wbf16, int64_t N, const float* feat,
                             float* out, void* scratch, int* tc_err = nullptr);

@@ -1082,9 +1082,9 @@ size_t learned_forward_scratch(int64_t N) {
   return packed_bytes() + 3 * align256((size_t)N * NHID * sizeof(bf16)) + align256((size_t)N * NFEAT * sizeof(bf16));
 }
 
-// The tensor-core (tcgen05) path: from kTcMinRows rows, on an sm_100-class device, with an error word.
-static bool use_tc(int64_t N, const int* err) {
-  if (!err || N < kTcMinRows || N > (int64_t)1 << 30) return false;
+// The tensor-core (tcgen05) path: from min_rows rows, on an sm_100-class device, with an error word.
+static bool use_tc(int64_t N, const int* err, int64_t min_rows) {
+  if (!err || N < min_rows || N > (int64_t)1 << 30) return false;
   static std::atomic<int> ok[64];  // 0 unknown, 1 yes, 2 no
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
@@ -1176,7 +1176,7 @@ static cudaError_t forward_scratch(cudaStream_t s, const float* params, const ui
   bf16* Wp = (bf16*)p;
   p += packed_bytes();
   const size_t hb = align256((size_t)N * NHID * sizeof(bf16));
-  if (use_tc(N, tc_err))
+  if (use_tc(N, tc_err, kTcMinRowsForward))
     return forward_tc(s, params, (const bf16*)wbf16, N, feat, out, (bf16*)(p + 3 * hb), (bf16*)p, (bf16*)(p + hb),
                       (bf16*)(p + 2 * hb), tc_err);
   if (pack) {
@@ -1247,7 +1247,7 @@ cudaError_t learned_grad(cudaStream_t s, const float* params, const uint16_t* wb
   float* part = (float*)((char*)lrow + align256((size_t)N * sizeof(float)));
   bf16* Wp = (bf16*)((char*)part + align256((size_t)kWgradSplit * NOUT * NHID * sizeof(float)));
   const int n = (int)N;
-  if (use_tc(N, tc_err)) {
+  if (use_tc(N, tc_err, kTcMinRowsGrad)) {
     char* q = (char*)Wp + packed_bytes();
     bf16* TA = (bf16*)q;
     q += align256((size_t)NOUT * pad8(N) * sizeof(bf16));
