@@ -1008,8 +1008,11 @@ def main():
         # 489 cycles = 1,001,472 plain-HMC poses of the state, batches of 4096 (the tensor-core
         # path), moves of the rigid body and of every torsion; at the paper's own regime of
         # external-coordinate moves (alpha ~ 0.01), mid-leg, and the fully coupled end
-        extra["learned_vs_plain"] = [learned_vs_plain(ctx, sys_, stream, dev, target=k) for k in
-                                     (N_STATES_BC + 1, N_STATES_BC + 28, N_STATES_BC + N_STATES_CD - 1)]
+        # Two move sets: rigid body and every torsion (the configuration's), and rigid body only
+        # (the paper's external-coordinate moves with a learned proposal).
+        extra["learned_vs_plain"] = [learned_vs_plain(ctx, sys_, stream, dev, target=k, n_torsions=nt)
+                                     for nt in (-1, 0)
+                                     for k in (N_STATES_BC + 1, N_STATES_BC + 28, N_STATES_BC + N_STATES_CD - 1)]
     if not args.no_protocol and world == 1:
         extra["protocol_initialization"] = protocol_build(ctx, sys_, stream)
         ctx.states_set(T, alpha, dt)
