@@ -170,8 +170,10 @@ __global__ void __launch_bounds__(kExMaxWarps * 32) exchange_fast_kernel(const E
     float lu = 0.f;
     if (a + s < K) {
       const U4 o = philox(A.seed, (uint32_t)((sw * A.max_sep + s - 1) * 65536 + a), lid, A.cycle, kPurposeExchange);
-      const double u = uniform53(o.x, o.y);
-      lu = u == 0.0 ? -INFINITY : __logf((float)u);
+      // the 53-bit uniform (o.x >> 5) 2^-27 + (o.y >> 6) 2^-53 in FP32: two roundings, 1.2e-7
+      // relative, as good as rounding the FP64 value; zero exactly when the uniform is zero
+      const float uf = __fmaf_rn((float)(o.x >> 5), 7.450580596923828125e-9f, (float)(o.y >> 6) * 1.1102230246251565e-16f);
+      lu = uf == 0.f ? -INFINITY : __logf(uf);
     }
     s_lu[idx] = lu;
   }
@@ -195,11 +197,16 @@ __global__ void __launch_bounds__(kExMaxWarps * 32) exchange_fast_kernel(const E
   if (__any_sync(0xffffffffu, bad)) return;  // not a list of slots 0..K-1: leave the ladder untouched
   for (int sw = 0; sw < A.n_sweeps; ++sw) {
     for (int s = 1; s <= smax; ++s) {
+      // floor(p / s) = (p * inv_s) >> 16 exactly for p < 1024 and s <= 8
+      const int inv_s = (65536 + s - 1) / s;
       for (int colour = 0; colour < 2; ++colour) {
         const int ph = 2 * (s - 1) + colour;
         const int np = s_npairs[ph];
         for (int p = lane; p < np; p += 32) {
-          const int a = s_pairs[ph * K + p], b = a + s;
+          // the p-th pair of the phase, in the order of the list: blocks of s consecutive a whose
+          // block index has the colour's parity
+          const int t = (p * inv_s) >> 16;
+          const int a = s * (colour + 2 * t) + (p - t * s), b = a + s;
           const int xi = s_cfg[a], yi = s_cfg[b];
           const float f1 = s_uf[a * K + yi], f2 = s_uf[b * K + xi], f3 = s_uf[a * K + xi], f4 = s_uf[b * K + yi];
           const float df = ((f1 + f2) - f3) - f4;
