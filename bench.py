@@ -4,7 +4,8 @@
 Workload (one GPU): a 48-atom synthetic ligand (seed 2), a 4000-atom receptor, three 129^3 grids at
 0.25 A, 32 warming + 96 coupling states, 64 independent chains (8192 replicas).  One step = one HMC
 trial of 50 velocity-Verlet steps for every replica, 25 replica-exchange sweeps on each of the 128
-ladders, and the energy re-evaluation + u_kn of the step's snapshot.  Metric: ligand atom-force
+ladders, and the u_kn of the step's snapshot (every replica at every state of its leg, from the
+energy components of the trial's final evaluation).  Metric: ligand atom-force
 evaluations per second (replicas x atoms x VV steps / time).  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -845,7 +846,6 @@ def main():
     x0 = base[np.arange(R) % base.shape[0]]
     run = ReplicaExchange(ctx, legs, N_CHAINS, x0, seed=1000, rep_offset=sh.rep_offset(N_STATES_BC + N_STATES_CD),
                           ladder_offset=sh.ladder_offset(len(legs)))
-    snap = torch.empty((R, 4), dtype=torch.float64, device=dev)
     u_leg = [torch.empty((l.K, N_CHAINS * l.K), dtype=torch.float64, device=dev) for l in legs]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
@@ -857,16 +857,15 @@ def main():
         run.hmc(cyc, N_VV)
         if ev is not None:
             ev[1].record(stream)
-        # the snapshot (energies of every replica in one launch, then u_kn per leg) reads only the
-        # configurations, which the exchange does not move: it runs beside the exchange sweeps
+        # the snapshot (u_kn per leg from the components the trial's final energy evaluation left)
+        # reads only the components, which the exchange does not move: it runs beside the sweeps
         hmc_done = torch.cuda.Event()
         hmc_done.record(stream)
         snap_stream.wait_event(hmc_done)
         ctx.set_stream(snap_stream)
-        ctx.reduced_energies(R, x=run.x, comps=snap)
         for li, leg in enumerate(legs):
             sl = run.leg_slice(li)
-            ctx.reduced_energies(N_CHAINS * leg.K, comps=snap[sl], k_begin=leg.state_offset, k_count=leg.K,
+            ctx.reduced_energies(N_CHAINS * leg.K, comps=run.comps[sl], k_begin=leg.state_offset, k_count=leg.K,
                                  u_kn=u_leg[li])
         snap_done = torch.cuda.Event()
         snap_done.record(snap_stream)
@@ -899,7 +898,7 @@ def main():
         print(json.dumps({"fep_endpoint": fep_endpoint(ctx, run, sys_, stream, measured_peaks().get("sm_max_mhz")
                                                        or 2070.0)}))
         return
-    launches_per_step = 1 + len(legs) + 1 + len(legs)  # hmc, exchange per leg, one evaluate, u_kn per leg
+    launches_per_step = 1 + len(legs) + len(legs)  # hmc, exchange per leg, u_kn per leg
     for w in range(args.warmup):
         step(w)
     torch.cuda.synchronize()

@@ -102,9 +102,44 @@ enum {
   ALGDOCK_N_COUNTERS = 4
 };
 
+/* The method's adjustable arguments ("Sampling", "Equilibration and production", "Estimation").
+ * They are the settings of the context's own run (algdock_replicas_init, algdock_run) and the
+ * defaults that algdock_mbar takes for tol = 0, max_iter = 0 and precision_mode = -1; every other
+ * call that takes one of these quantities as an argument uses its argument.
+ * algdock_params_default writes: 50 velocity-Verlet steps per HMC trial, 25 exchange sweeps of
+ * separations 1..5 per cycle, no external-coordinate moves (the paper's setting is n_external = 20
+ * at alpha_max = 0.01 with sigma_ext = 0.6 A), MBAR to 1e-10 kT in at most 10000 iterations in
+ * FP64 (precision mode 0), checks off. */
+typedef struct {
+  int32_t n_steps;        /* velocity-Verlet steps per HMC trial, >= 0 */
+  int32_t n_sweeps;       /* exchange sweeps per cycle, >= 0 */
+  int32_t max_sep;        /* largest state separation of an exchange attempt, >= 1; n_sweeps * max_sep < 65536 */
+  int32_t n_external;     /* external-coordinate moves per replica after each HMC trial, >= 0 */
+  double alpha_max;       /* ... at the states with alpha < alpha_max */
+  double sigma_ext;       /* translation standard deviation of an external move (A), finite, >= 0 */
+  double mbar_tol;        /* > 0 */
+  int32_t mbar_max_iter;  /* >= 1 */
+  int32_t mbar_precision; /* algdock_mbar's precision_mode, 0..2 */
+  /* nonzero: every cycle of algdock_cycle and algdock_run (and algdock_replicas_init) checks its
+   * results on the device - positions and energy components finite (else ALGDOCK_E_NUMERIC),
+   * every state index inside the table and every ladder's config_of a permutation that agrees
+   * with state_of (else ALGDOCK_E_STATE) - and then synchronises the stream.  The arrays keep the
+   * cycle's results either way. */
+  int32_t checks;
+} algdock_params;
+
 /* ---------------------------------------------------------------- lifecycle */
-algdock_status algdock_create(int device, algdock_ctx** out);
+/* Writes the defaults above into *params. */
+algdock_status algdock_params_default(algdock_params* params);
+/* Creates a context on CUDA device `device`.  seed keys every Philox stream of the context's own
+ * run (the calls that take a seed argument use theirs); params may be NULL (the defaults).
+ * ALGDOCK_E_INVALID for out-of-range params, ALGDOCK_E_CUDA for a bad device. */
+algdock_status algdock_create(int device, uint64_t seed, const algdock_params* params, algdock_ctx** out);
 void algdock_destroy(algdock_ctx* ctx);
+/* Replaces the context's params (validated as in algdock_create); the next cycle uses them. */
+algdock_status algdock_set_params(algdock_ctx* ctx, const algdock_params* params);
+/* Reads the context's params and seed (either pointer may be NULL). */
+algdock_status algdock_get_params(algdock_ctx* ctx, algdock_params* params, uint64_t* seed);
 /* stream: a cudaStream_t (NULL = legacy default stream). */
 algdock_status algdock_set_stream(algdock_ctx* ctx, void* stream);
 const char* algdock_last_error(const algdock_ctx* ctx);
@@ -233,10 +268,12 @@ algdock_status algdock_exchange(algdock_ctx* ctx, int32_t n_ladders, int32_t K, 
                                 int64_t* attempts, int64_t* accepts);
 
 /* One iteration of the paper's loop over a whole run ("Equilibration and production"):
- * an HMC trial of every replica at its state (as algdock_hmc_cycle), then n_sweeps exchange sweeps
- * on every ladder of every leg (as algdock_exchange), and, if u_kn is given, the snapshot: every
- * configuration re-evaluated and its reduced energies at every state of its leg (as
- * algdock_reduced_energies).  Replicas are leg-major: leg l's chain c holds slots
+ * an HMC trial of every replica at its state (as algdock_hmc_cycle), the external-coordinate moves
+ * if desc->n_external > 0 (as algdock_external_moves), then n_sweeps exchange sweeps on every
+ * ladder of every leg (as algdock_exchange), and, if u_kn is given, the snapshot: the reduced
+ * energies of every configuration at every state of its leg, formed from the components that the
+ * trial's final energy evaluation and the moves left in comps (as algdock_reduced_energies from
+ * comps; U_k is linear in the components, so nothing is evaluated twice).  Replicas are leg-major: leg l's chain c holds slots
  * base_l + c K_l + i, base_l = n_chains sum_{m<l} K_m, with config_of laid out the same way
  * ([n_chains][K_l] per leg).  Leg l's ladders are numbered ladder_offset + l n_chains.
  *   x [R][n_atoms][3] float, comps [R][4] double, state_of [R] int32, config_of [R] int32: each host
@@ -255,9 +292,39 @@ typedef struct {
   int32_t n_sweeps, max_sep;              /* exchange sweeps per cycle and largest separation */
   uint64_t seed;
   int64_t rep_offset, ladder_offset;      /* global index of the first replica and ladder */
+  int32_t n_external;                     /* external-coordinate moves after the HMC trial (0: none), */
+  double alpha_max, sigma_ext;            /* as algdock_external_moves, between the trial and the sweeps */
 } algdock_run_desc;
 algdock_status algdock_cycle(algdock_ctx* ctx, const algdock_run_desc* desc, uint64_t cycle, float* x, double* comps,
                              int32_t* state_of, int32_t* config_of, int64_t* counters, double* u_kn);
+
+/* ---------------------------------------------------------------- the context's own run */
+/* Replicas owned by the context, in algdock_cycle's layout: n_legs legs, leg l with K[l] states
+ * starting at state_offset[l] of the state table, n_chains chains per leg; R = n_chains sum K[l]
+ * replicas, leg-major, chain c of leg l at slots base_l + c K[l] + i (i = 0..K[l]-1).
+ *   x0 [R][n_atoms][3] float, host or device: the starting configurations.
+ * Each slot starts at its own state (state_of = state_offset[l] + i, config_of = i), its energy
+ * components are evaluated, the counters are zeroed.  rep_offset and ladder_offset are the global
+ * indices of the first replica and ladder, as in algdock_run_desc (0 for a one-process run).
+ * Replaces any replicas the context held.  Synchronises the stream. */
+algdock_status algdock_replicas_init(algdock_ctx* ctx, int32_t n_legs, const int32_t* K, const int32_t* state_offset,
+                                     int32_t n_chains, int64_t rep_offset, int64_t ladder_offset, const float* x0);
+/* n_cycles cycles of the paper's loop over the context's replicas (algdock_cycle with the
+ * context's params and seed), cycles first_cycle .. first_cycle + n_cycles - 1.  u_kn (may be NULL,
+ * host or device) receives each cycle's snapshot, cycle after cycle, each laid out as
+ * algdock_cycle's u_kn. */
+algdock_status algdock_run(algdock_ctx* ctx, int32_t n_cycles, uint64_t first_cycle, double* u_kn);
+/* Copies the replicas out (each pointer may be NULL; host or device): x [R][n_atoms][3] float,
+ * comps [R][4] double, state_of [R] int32, config_of [R] int32, counters [ALGDOCK_N_COUNTERS]
+ * int64.  Synchronises the stream. */
+algdock_status algdock_replicas_get(algdock_ctx* ctx, float* x, double* comps, int32_t* state_of,
+                                    int32_t* config_of, int64_t* counters);
+/* Saves the replicas, their layout, the seed and next_cycle as a checkpoint (the format of
+ * algdock_checkpoint_save, arrays "replicas.*"); algdock_replicas_load restores all of them (the
+ * grids and ligand must be loaded; the state table comes from the file), so that algdock_run from
+ * the restored next_cycle repeats the uninterrupted run bit for bit. */
+algdock_status algdock_replicas_save(algdock_ctx* ctx, const char* path, uint64_t next_cycle);
+algdock_status algdock_replicas_load(algdock_ctx* ctx, const char* path, uint64_t* next_cycle);
 
 /* ---------------------------------------------------------------- estimation */
 /* Reduced energies for MBAR ("Estimation").  If x ([N][n_atoms][3] float) is given, the energy
@@ -275,8 +342,9 @@ algdock_status algdock_reduced_energies(algdock_ctx* ctx, int64_t N, const float
  * (host).  precision_mode 0: FP64 throughout; 1: exponentials in FP32 of FP64 arguments, sums in
  * FP64; 2: each sample's column shifted by its minimum (FP64, exact in the result) and stored as
  * FP32, then FP32 arguments, exponentials and Kahan-compensated sums, FP64 only where partial sums
- * meet (K <= 16384; extra scratch K*N*4 bytes).  K <= 65535 in every mode.  f_k [K] (host) and iters (host) receive the
- * result.  Synchronises.  Returns
+ * meet (K <= 16384; extra scratch K*N*4 bytes).  K <= 65535 in every mode.  tol = 0, max_iter = 0
+ * and precision_mode = -1 take the context's params (mbar_tol, mbar_max_iter, mbar_precision).
+ * f_k [K] (host) and iters (host) receive the result.  Synchronises.  Returns
  * ALGDOCK_E_NOT_CONVERGED (with the last iterate in f_k) if max_iter is reached. */
 algdock_status algdock_mbar(algdock_ctx* ctx, int32_t K, int64_t N, const double* u_kn, const int64_t* N_k,
                             double tol, int32_t max_iter, int32_t precision_mode, double* f_k, int32_t* iters);

@@ -36,7 +36,9 @@ EXPORTS = [
     "algdock_hmc_shape", "algdock_batch_shapes", "algdock_gather_probe", "algdock_grids_load_f64",
     "algdock_energy_force_f64", "algdock_checkpoint_save", "algdock_checkpoint_load", "algdock_mbar_partials",
     "algdock_mbar_update", "algdock_next_temperature", "algdock_next_alpha", "algdock_adapt_dt",
-    "algdock_insert_states", "algdock_cycle", "algdock_gemm_bf16",
+    "algdock_insert_states", "algdock_cycle", "algdock_gemm_bf16", "algdock_params_default", "algdock_set_params",
+    "algdock_get_params", "algdock_replicas_init", "algdock_run", "algdock_replicas_get", "algdock_replicas_save",
+    "algdock_replicas_load",
 ]
 
 BATCH_CLASSES = 4             # launch classes of a multi-ligand batch
@@ -111,7 +113,15 @@ class RunDescC(C.Structure):
     """algdock_run_desc: the legs, chains and per-cycle settings of a run for algdock_cycle."""
     _fields_ = [("n_legs", C.c_int32), ("K", C.c_int32 * MAX_LEGS), ("state_offset", C.c_int32 * MAX_LEGS),
                 ("n_chains", C.c_int32), ("n_steps", C.c_int32), ("n_sweeps", C.c_int32), ("max_sep", C.c_int32),
-                ("seed", C.c_uint64), ("rep_offset", C.c_int64), ("ladder_offset", C.c_int64)]
+                ("seed", C.c_uint64), ("rep_offset", C.c_int64), ("ladder_offset", C.c_int64),
+                ("n_external", C.c_int32), ("alpha_max", C.c_double), ("sigma_ext", C.c_double)]
+
+
+class ParamsC(C.Structure):
+    """algdock_params: the method's adjustable arguments held by a context."""
+    _fields_ = [("n_steps", C.c_int32), ("n_sweeps", C.c_int32), ("max_sep", C.c_int32), ("n_external", C.c_int32),
+                ("alpha_max", C.c_double), ("sigma_ext", C.c_double), ("mbar_tol", C.c_double),
+                ("mbar_max_iter", C.c_int32), ("mbar_precision", C.c_int32), ("checks", C.c_int32)]
 
 
 class ArrayC(C.Structure):
@@ -137,7 +147,15 @@ def load_library(path: str = LIB_PATH):
     L = C.CDLL(path)
     vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
     sig = {
-        "algdock_create": ([C.c_int, C.POINTER(vp)], C.c_int),
+        "algdock_create": ([C.c_int, u64, C.POINTER(ParamsC), C.POINTER(vp)], C.c_int),
+        "algdock_params_default": ([C.POINTER(ParamsC)], C.c_int),
+        "algdock_set_params": ([vp, C.POINTER(ParamsC)], C.c_int),
+        "algdock_get_params": ([vp, C.POINTER(ParamsC), C.POINTER(u64)], C.c_int),
+        "algdock_replicas_init": ([vp, i32, vp, vp, i32, i64, i64, vp], C.c_int),
+        "algdock_run": ([vp, i32, u64, vp], C.c_int),
+        "algdock_replicas_get": ([vp, vp, vp, vp, vp, vp], C.c_int),
+        "algdock_replicas_save": ([vp, C.c_char_p, u64], C.c_int),
+        "algdock_replicas_load": ([vp, C.c_char_p, C.POINTER(u64)], C.c_int),
         "algdock_destroy": ([vp], None),
         "algdock_set_stream": ([vp, vp], C.c_int),
         "algdock_last_error": ([vp], C.c_char_p),
@@ -346,13 +364,41 @@ def checkpoint_load(ctx, path, arrays):
     return seed.value, cycle.value
 
 
+def default_params(**fields) -> ParamsC:
+    """algdock_params_default, with the given fields replaced."""
+    p = ParamsC()
+    load_library().algdock_params_default(C.byref(p))
+    for k, v in fields.items():
+        if k not in dict(ParamsC._fields_):
+            raise TypeError("unknown algdock_params field %r" % k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(a, td, name):
+    """Data pointer of a contiguous torch tensor (device or host) or C-contiguous numpy array."""
+    import torch
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        if a.dtype != td or not a.is_contiguous():
+            raise ValueError("%s must be a contiguous %s tensor" % (name, td))
+        return a.data_ptr()
+    if not (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype == np.dtype(str(td)[6:])):
+        raise ValueError("%s must be a C-contiguous %s array" % (name, td))
+    return a.ctypes.data
+
+
 class Context:
     """One algdock_ctx on a CUDA device.  Method names follow the C calls without the prefix."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, seed: int = 0, **params):
+        """params: any field of algdock_params (n_steps, n_sweeps, max_sep, n_external, alpha_max,
+        sigma_ext, mbar_tol, mbar_max_iter, mbar_precision, checks); the rest keep their defaults."""
         self._L = load_library()
         h = C.c_void_p()
-        st = self._L.algdock_create(int(device), C.byref(h))
+        p = default_params(**params)
+        st = self._L.algdock_create(int(device), int(seed), C.byref(p), C.byref(h))
         if st != OK:
             raise AlgdockError(st, "algdock_create(%d) failed" % device)
         self.h = h
@@ -659,10 +705,12 @@ class Context:
 
     # ---------------------------------------------------------------- learned proposal
     def cycle(self, legs, n_chains, cycle, x, comps, state_of, config_of, n_steps=50, n_sweeps=25, max_sep=5,
-              seed=0, rep_offset=0, ladder_offset=0, counters=None, u_kn=None):
-        """algdock_cycle: one HMC trial of every replica, then the exchange sweeps of every ladder (and
-        the snapshot's u_kn if given).  legs: [(K, state_offset), ...].  Each array is a device
-        tensor or host memory (a CPU tensor, ideally pinned, or a numpy array), updated in place."""
+              seed=0, rep_offset=0, ladder_offset=0, counters=None, u_kn=None, n_external=0,
+              alpha_max=ALPHA_MAX_EXTERNAL, sigma=SIGMA_TRANSLATION):
+        """algdock_cycle: one HMC trial of every replica, the external-coordinate moves (n_external > 0),
+        then the exchange sweeps of every ladder (and the snapshot's u_kn if given).  legs: [(K,
+        state_offset), ...].  Each array is a device tensor or host memory (a CPU tensor, ideally
+        pinned, or a numpy array), updated in place."""
         import torch
         d = RunDescC()
         d.n_legs = len(legs)
@@ -670,21 +718,68 @@ class Context:
             d.K[i], d.state_offset[i] = int(K), int(off)
         d.n_chains, d.n_steps, d.n_sweeps, d.max_sep = int(n_chains), int(n_steps), int(n_sweeps), int(max_sep)
         d.seed, d.rep_offset, d.ladder_offset = int(seed), int(rep_offset), int(ladder_offset)
-
-        def ptr(a, td, name):
-            if a is None:
-                return None
-            if isinstance(a, torch.Tensor):
-                if a.dtype != td or not a.is_contiguous():
-                    raise ValueError("%s must be a contiguous %s tensor" % (name, td))
-                return a.data_ptr()
-            if not (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype == np.dtype(str(td)[6:])):
-                raise ValueError("%s must be a C-contiguous %s array" % (name, td))
-            return a.ctypes.data
+        d.n_external, d.alpha_max, d.sigma_ext = int(n_external), float(alpha_max), float(sigma)
         self._check(self._L.algdock_cycle(
-            self.h, C.byref(d), int(cycle), ptr(x, torch.float32, "x"), ptr(comps, torch.float64, "comps"),
-            ptr(state_of, torch.int32, "state_of"), ptr(config_of, torch.int32, "config_of"),
-            ptr(counters, torch.int64, "counters"), ptr(u_kn, torch.float64, "u_kn")))
+            self.h, C.byref(d), int(cycle), _ptr(x, torch.float32, "x"), _ptr(comps, torch.float64, "comps"),
+            _ptr(state_of, torch.int32, "state_of"), _ptr(config_of, torch.int32, "config_of"),
+            _ptr(counters, torch.int64, "counters"), _ptr(u_kn, torch.float64, "u_kn")))
+
+    # ------------------------------------------------------------ the context's own run
+    def params(self) -> dict:
+        """The context's algdock_params as a dict, and its seed under "seed"."""
+        p, seed = ParamsC(), C.c_uint64()
+        self._check(self._L.algdock_get_params(self.h, C.byref(p), C.byref(seed)))
+        out = {name: getattr(p, name) for name, _ in ParamsC._fields_}
+        out["seed"] = seed.value
+        return out
+
+    def set_params(self, **fields):
+        """algdock_set_params with the given fields replaced in the context's current params."""
+        p = ParamsC()
+        self._check(self._L.algdock_get_params(self.h, C.byref(p), None))
+        for k, v in fields.items():
+            if k not in dict(ParamsC._fields_):
+                raise TypeError("unknown algdock_params field %r" % k)
+            setattr(p, k, v)
+        self._check(self._L.algdock_set_params(self.h, C.byref(p)))
+
+    def replicas_init(self, legs, n_chains, x0, rep_offset=0, ladder_offset=0):
+        """algdock_replicas_init: legs [(K, state_offset), ...]; x0 [R][n_atoms][3] float32, a device or
+        host tensor or numpy array, R = n_chains * sum(K)."""
+        import torch
+        K = (C.c_int32 * len(legs))(*[int(k) for k, _ in legs])
+        off = (C.c_int32 * len(legs))(*[int(o) for _, o in legs])
+        self._replica_legs = [(int(k), int(o)) for k, o in legs]
+        self._replica_chains = int(n_chains)
+        self._check(self._L.algdock_replicas_init(self.h, len(legs), K, off, int(n_chains), int(rep_offset),
+                                                  int(ladder_offset), _ptr(x0, torch.float32, "x0")))
+
+    def ukn_words(self) -> int:
+        """Doubles of one cycle's snapshot for the context's replicas (sum over legs of K^2 n_chains)."""
+        return sum(K * K * self._replica_chains for K, _ in self._replica_legs)
+
+    def run(self, n_cycles, first_cycle=0, u_kn=None):
+        """algdock_run: n_cycles cycles over the context's replicas; u_kn (may be None) a float64
+        device or host array of n_cycles * ukn_words() doubles."""
+        import torch
+        self._check(self._L.algdock_run(self.h, int(n_cycles), int(first_cycle), _ptr(u_kn, torch.float64, "u_kn")))
+
+    def replicas_get(self, x=None, comps=None, state_of=None, config_of=None, counters=None):
+        """algdock_replicas_get into the given arrays (device or host; None skips)."""
+        import torch
+        self._check(self._L.algdock_replicas_get(
+            self.h, _ptr(x, torch.float32, "x"), _ptr(comps, torch.float64, "comps"),
+            _ptr(state_of, torch.int32, "state_of"), _ptr(config_of, torch.int32, "config_of"),
+            _ptr(counters, torch.int64, "counters")))
+
+    def replicas_save(self, path, next_cycle):
+        self._check(self._L.algdock_replicas_save(self.h, str(path).encode(), int(next_cycle)))
+
+    def replicas_load(self, path) -> int:
+        """algdock_replicas_load; returns the stored next cycle."""
+        nxt = C.c_uint64()
+        self._check(self._L.algdock_replicas_load(self.h, str(path).encode(), C.byref(nxt)))
+        return nxt.value
 
     def gemm_bf16(self, A, B, C, epilogue=0, bias=None, mask=None, n_split=1):
         """algdock_gemm_bf16: C = epi(A . B^T) on tcgen05; A [M][K], B [N][K] bfloat16 (or int16 bit

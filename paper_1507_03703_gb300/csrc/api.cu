@@ -467,9 +467,15 @@ void batch_free(algdock_ctx* c) {
 
 extern "C" {
 
-algdock_status algdock_create(int device, algdock_ctx** out) {
+algdock_status algdock_create(int device, uint64_t seed, const algdock_params* params, algdock_ctx** out) {
   if (!out) return ALGDOCK_E_INVALID;
   *out = nullptr;
+  algdock_params p;
+  algdock_params_default(&p);
+  if (params) {
+    if (params_check(nullptr, *params) != ALGDOCK_OK) return ALGDOCK_E_INVALID;
+    p = *params;
+  }
   int n = 0;
   if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
     cudaGetLastError();
@@ -478,6 +484,8 @@ algdock_status algdock_create(int device, algdock_ctx** out) {
   algdock_ctx* c = new (std::nothrow) algdock_ctx();
   if (!c) return ALGDOCK_E_OOM;
   c->device = device;
+  c->seed = seed;
+  c->params = p;
   Device g(device);
   if (cudaMallocHost(&c->h_flag, sizeof(int)) != cudaSuccess) {
     delete c;
@@ -518,6 +526,7 @@ void algdock_destroy(algdock_ctx* c) {
   cudaFreeHost(c->h_flag);
   cudaFree(c->d_work);
   cudaFree(c->d_stage);
+  cudaFree(c->d_rbuf);
   if (c->cycle_side) cudaStreamDestroy(c->cycle_side);
   if (c->cycle_fork) cudaEventDestroy(c->cycle_fork);
   if (c->cycle_join) cudaEventDestroy(c->cycle_join);
@@ -548,6 +557,7 @@ algdock_status algdock_grids_build(algdock_ctx* c, const algdock_grid_desc* d, i
                                    const double* rstar, const double* eps, const double* q, float* ljr, float* lja,
                                    float* elec) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_grids_build");
   if (!d || n_rec < 0 || (n_rec > 0 && (!xyz || !rstar || !eps || !q)) || !ljr || !lja || !elec)
     return fail(c, ALGDOCK_E_INVALID, "grids_build: null argument");
   if (d->n[0] < 2 || d->n[1] < 2 || d->n[2] < 2 || !(d->spacing > 0))
@@ -795,6 +805,7 @@ algdock_status algdock_hmc_cycle(algdock_ctx* c, int64_t n_rep, const int32_t* s
                                  double* dH, uint8_t* accepted, int32_t n_steps, uint64_t seed, uint64_t cycle,
                                  int64_t rep_offset, int64_t* counters) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_hmc_cycle");
   if (!c->has_grid || !c->has_ligand || c->K == 0)
     return fail(c, ALGDOCK_E_STATE, "hmc_cycle: load grids, ligand and states first");
   if (n_rep < 0 || n_steps < 0 || rep_offset < 0) return fail(c, ALGDOCK_E_INVALID, "hmc_cycle: negative size");
@@ -814,6 +825,7 @@ algdock_status algdock_external_moves(algdock_ctx* c, int64_t n_rep, const int32
                                       double* comps, int32_t n_moves, double alpha_max, double sigma, uint64_t seed,
                                       uint64_t cycle, int64_t rep_offset, int32_t* accepted, int64_t* counters) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_external_moves");
   if (!c->has_grid || !c->has_ligand || c->K == 0)
     return fail(c, ALGDOCK_E_STATE, "external_moves: load grids, ligand and states first");
   if (n_rep < 0 || n_moves < 0 || rep_offset < 0) return fail(c, ALGDOCK_E_INVALID, "external_moves: negative size");
@@ -835,6 +847,7 @@ algdock_status algdock_detect_equilibration(algdock_ctx* c, int64_t T, int64_t S
                                             int64_t stride, int32_t n_cand, double* g, int64_t* t0_best,
                                             double* neff_best) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_detect_equilibration");
   if (T < 2 || T > 50000 || S < 1 || S > 65535 || stride < 1 || n_cand < 1 || (int64_t)(n_cand - 1) * stride > T - 2)
     return fail(c, ALGDOCK_E_INVALID, "detect_equilibration: need 2 <= T <= 50000, 1 <= S <= 65535, stride >= 1, "
                                       "n_cand >= 1, (n_cand - 1) * stride <= T - 2");
@@ -984,6 +997,7 @@ algdock_status algdock_receptor_load(algdock_ctx* c, int32_t n_rec, const double
 
 algdock_status algdock_target_interaction(algdock_ctx* c, int64_t N, const float* x, double* psi) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_target_interaction");
   if (!c->has_ligand || c->n_rec < 0)
     return fail(c, ALGDOCK_E_STATE, "target_interaction: load the ligand and the receptor first");
   if (N < 0) return fail(c, ALGDOCK_E_INVALID, "target_interaction: N < 0");
@@ -1004,6 +1018,7 @@ algdock_status algdock_target_interaction(algdock_ctx* c, int64_t N, const float
 algdock_status algdock_fep(algdock_ctx* c, int64_t N, const double* u_target, int64_t stride_target,
                            const double* u_sampling, int64_t stride_sampling, double beta, double* result) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_fep");
   if (N < 1 || !u_target || !result || stride_target < 0 || stride_sampling < 0 || !isfinite(beta))
     return fail(c, ALGDOCK_E_INVALID, "fep: need N >= 1, strides >= 0, finite beta and non-null arrays");
   if (!is_device_ptr(u_target) || (u_sampling && !is_device_ptr(u_sampling)))
@@ -1117,6 +1132,7 @@ algdock_status algdock_batch_hmc_cycle(algdock_ctx* c, const int32_t* state_of, 
                                        uint8_t* acc, int32_t n_steps, uint64_t seed, uint64_t cycle,
                                        int64_t rep_offset, int64_t* counters) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_batch_hmc_cycle");
   if (!c->has_grid || c->K == 0 || c->batch_n_rep == 0)
     return fail(c, ALGDOCK_E_STATE, "batch_hmc_cycle: load grids, states, a batch and its layout first");
   if (n_steps < 0 || rep_offset < 0) return fail(c, ALGDOCK_E_INVALID, "batch_hmc_cycle: negative argument");
@@ -1238,6 +1254,7 @@ algdock_status algdock_batch_tune(algdock_ctx* c, const int32_t* state_of, const
 algdock_status algdock_energy_force(algdock_ctx* c, int64_t N, const int32_t* state_of, const float* x, float* force,
                                     double* comps) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_energy_force");
   if (!c->has_grid || !c->has_ligand || c->K == 0)
     return fail(c, ALGDOCK_E_STATE, "energy_force: load grids, ligand and states first");
   if (N < 0) return fail(c, ALGDOCK_E_INVALID, "energy_force: N < 0");
@@ -1256,6 +1273,7 @@ algdock_status algdock_exchange(algdock_ctx* c, int32_t n_ladders, int32_t K, in
                                 int32_t max_sep, uint64_t seed, uint64_t cycle, int64_t ladder_offset,
                                 int64_t* attempts, int64_t* accepts) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_exchange");
   if (c->K == 0) return fail(c, ALGDOCK_E_STATE, "exchange: set states first");
   if (n_ladders < 0 || K < 1 || K > kMaxLadder || state_offset < 0 || state_offset + K > c->K || n_sweeps < 0 ||
       max_sep < 1 || (int64_t)n_sweeps * max_sep >= 65536 || ladder_offset < 0)
@@ -1276,6 +1294,7 @@ algdock_status algdock_exchange(algdock_ctx* c, int32_t n_ladders, int32_t K, in
 algdock_status algdock_reduced_energies(algdock_ctx* c, int64_t N, const float* x, double* comps, int32_t k_begin,
                                         int32_t k_count, double* u_kn) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_reduced_energies");
   if (N < 0) return fail(c, ALGDOCK_E_INVALID, "reduced_energies: N < 0");
   if (N == 0) return ALGDOCK_OK;
   if (!x && !comps) return fail(c, ALGDOCK_E_INVALID, "reduced_energies: need x or comps");
@@ -1357,6 +1376,7 @@ algdock_status algdock_pose_delta(algdock_ctx* c, int64_t N, const float* x, con
 algdock_status algdock_mlp_forward(algdock_ctx* c, const float* params, const uint16_t* wbf16, int64_t N,
                                    const float* feat, float* out) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_mlp_forward");
   if (N < 0 || N > (int64_t)1 << 30) return fail(c, ALGDOCK_E_INVALID, "mlp_forward: bad N");
   if (N == 0) return ALGDOCK_OK;
   if (!is_device_ptr(params) || !is_device_ptr(wbf16) || !is_device_ptr(feat) || !is_device_ptr(out))
@@ -1375,6 +1395,7 @@ algdock_status algdock_mlp_forward(algdock_ctx* c, const float* params, const ui
 algdock_status algdock_mlp_grad(algdock_ctx* c, const float* params, const uint16_t* wbf16, int64_t N, const float* feat,
                                 const float* delta, int32_t D, float* grad, float* loss) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_mlp_grad");
   if (N < 1 || N > (int64_t)1 << 30 || D < 1 || D > ALGDOCK_MLP_DMAX)
     return fail(c, ALGDOCK_E_INVALID, "mlp_grad: bad N or D");
   if (!is_device_ptr(params) || !is_device_ptr(wbf16) || !is_device_ptr(feat) || !is_device_ptr(delta) ||
@@ -1395,6 +1416,7 @@ algdock_status algdock_mlp_grad(algdock_ctx* c, const float* params, const uint1
 algdock_status algdock_mlp_adam(algdock_ctx* c, float* params, uint16_t* wbf16, const float* grad, float* m, float* v,
                                 int32_t step, float lr) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_mlp_adam");
   if (step < 1 || !(lr >= 0.f)) return fail(c, ALGDOCK_E_INVALID, "mlp_adam: step >= 1 and lr >= 0");
   if (!is_device_ptr(params) || !is_device_ptr(wbf16) || !is_device_ptr(grad) || !is_device_ptr(m) ||
       !is_device_ptr(v))
@@ -1411,6 +1433,7 @@ algdock_status algdock_propose_learned(algdock_ctx* c, const float* params, cons
                                        int32_t n_torsions, uint64_t seed, uint64_t cycle, int64_t rep_offset,
                                        int32_t* accepted, int64_t* counters) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_propose_learned");
   if (!c->has_grid || !c->has_ligand || c->K == 0)
     return fail(c, ALGDOCK_E_STATE, "propose_learned: load grids, ligand and states first");
   if (n_rep < 0 || n_rep > (int64_t)1 << 30 || n_moves < 0 || rep_offset < 0)
@@ -1433,6 +1456,10 @@ algdock_status algdock_propose_learned(algdock_ctx* c, const float* params, cons
 algdock_status algdock_mbar(algdock_ctx* c, int32_t K, int64_t N, const double* u_kn, const int64_t* N_k, double tol,
                             int32_t max_iter, int32_t precision_mode, double* f_k, int32_t* iters) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_mbar");
+  if (tol == 0.0) tol = c->params.mbar_tol;
+  if (max_iter == 0) max_iter = c->params.mbar_max_iter;
+  if (precision_mode == -1) precision_mode = c->params.mbar_precision;
   if (K < 1 || N < 1 || !u_kn || !N_k || !f_k || !iters || max_iter < 1 || !(tol > 0) ||
       precision_mode < 0 || precision_mode > 2)
     return fail(c, ALGDOCK_E_INVALID, "mbar: bad arguments");
@@ -1477,8 +1504,11 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
     return fail(c, ALGDOCK_E_STATE, "cycle: load grids, ligand and states first");
   if (!d || !x || !comps || !state_of || !config_of || d->n_legs < 1 || d->n_legs > ALGDOCK_MAX_LEGS ||
       d->n_chains < 1 || d->n_steps < 0 || d->n_sweeps < 0 || d->max_sep < 1 ||
-      (int64_t)d->n_sweeps * d->max_sep >= 65536 || d->rep_offset < 0 || d->ladder_offset < 0)
+      (int64_t)d->n_sweeps * d->max_sep >= 65536 || d->rep_offset < 0 || d->ladder_offset < 0 ||
+      d->n_external < 0 || (d->n_external > 0 && (isnan(d->alpha_max) || !(d->sigma_ext >= 0.0) ||
+                                                    !isfinite(d->sigma_ext))))
     return fail(c, ALGDOCK_E_INVALID, "cycle: bad arguments");
+  NvtxRange range("algdock_cycle");
   int64_t R = 0, ukn_words = 0;
   for (int l = 0; l < d->n_legs; ++l) {
     if (d->K[l] < 1 || d->K[l] > kMaxLadder || d->state_offset[l] < 0 || d->state_offset[l] + d->K[l] > c->K)
@@ -1487,21 +1517,24 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
     ukn_words += (int64_t)d->K[l] * d->n_chains * d->K[l];
   }
   const int na = c->lig.na;
-  // each array device-resident as given, or staged: [x | comps | snapshot comps | state_of | config_of |
-  // counters | u_kn], 256-byte aligned pieces
+  // each array device-resident as given, or staged: [x | comps | state_of | config_of | counters |
+  // u_kn], 256-byte aligned pieces
   struct Piece {
     void* user;
     size_t bytes;
     bool host;
     size_t off;
   };
-  Piece P[7] = {{x, (size_t)R * na * 3 * 4, false, 0},       {comps, (size_t)R * 32, false, 0},
-                {nullptr, (size_t)(u_kn ? R : 0) * 32, true, 0}, {state_of, (size_t)R * 4, false, 0},
-                {config_of, (size_t)R * 4, false, 0},          {counters, counters ? (size_t)ALGDOCK_N_COUNTERS * 8 : 0, false, 0},
-                {u_kn, u_kn ? (size_t)ukn_words * 8 : 0, false, 0}};
+  constexpr int kPieces = 6;
+  Piece P[kPieces] = {{x, (size_t)R * na * 3 * 4, false, 0},
+                      {comps, (size_t)R * 32, false, 0},
+                      {state_of, (size_t)R * 4, false, 0},
+                      {config_of, (size_t)R * 4, false, 0},
+                      {counters, counters ? (size_t)ALGDOCK_N_COUNTERS * 8 : 0, false, 0},
+                      {u_kn, u_kn ? (size_t)ukn_words * 8 : 0, false, 0}};
   size_t need = 0;
-  for (int i = 0; i < 7; ++i) {
-    if (i != 2) P[i].host = P[i].user && !is_device_ptr(P[i].user);
+  for (int i = 0; i < kPieces; ++i) {
+    P[i].host = P[i].user && !is_device_ptr(P[i].user);
     if (P[i].host) {
       P[i].off = need;
       need += (P[i].bytes + 255) & ~(size_t)255;
@@ -1513,9 +1546,6 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cycle");
     cudaFree(c->d_stage);
-  if (c->cycle_side) cudaStreamDestroy(c->cycle_side);
-  if (c->cycle_fork) cudaEventDestroy(c->cycle_fork);
-  if (c->cycle_join) cudaEventDestroy(c->cycle_join);
     c->d_stage = nullptr;
     c->stage_bytes = 0;
     e = cudaMalloc(&c->d_stage, need);
@@ -1524,20 +1554,27 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
   }
   auto dev_of = [&](int i) { return P[i].host ? (void*)((char*)c->d_stage + P[i].off) : P[i].user; };
   bool any_host = false;
-  for (int i = 0; i < 7 && e == cudaSuccess; ++i)
+  for (int i = 0; i < kPieces && e == cudaSuccess; ++i)
     if (P[i].host && P[i].user) {  // inputs in (u_kn is output only; its host copy goes out below)
       any_host = true;
-      if (i != 6) e = cudaMemcpyAsync(dev_of(i), P[i].user, P[i].bytes, cudaMemcpyHostToDevice, c->stream);
+      if (i != 5) e = cudaMemcpyAsync(dev_of(i), P[i].user, P[i].bytes, cudaMemcpyHostToDevice, c->stream);
     }
   float* dx = (float*)dev_of(0);
   double* dc = (double*)dev_of(1);
-  int32_t* ds = (int32_t*)dev_of(3);
-  int32_t* dcfg = (int32_t*)dev_of(4);
-  int64_t* dcnt = (int64_t*)dev_of(5);
-  if (e == cudaSuccess)
+  int32_t* ds = (int32_t*)dev_of(2);
+  int32_t* dcfg = (int32_t*)dev_of(3);
+  int64_t* dcnt = (int64_t*)dev_of(4);
+  if (e == cudaSuccess) {
+    NvtxRange r("algdock_cycle: HMC trial");
     e = launch_hmc(c->stream, *c, R, ds, dx, dc, nullptr, nullptr, d->n_steps, d->seed, cycle, d->rep_offset, dcnt);
-  // the snapshot reads only the configurations, which the exchange does not move, so it runs on a
-  // side stream beside the exchange sweeps
+  }
+  if (e == cudaSuccess && d->n_external > 0) {
+    NvtxRange r("algdock_cycle: external moves");
+    e = launch_external(c->stream, *c, R, ds, dx, dc, d->n_external, d->alpha_max, (float)d->sigma_ext, d->seed,
+                        cycle, d->rep_offset, nullptr, dcnt);
+  }
+  // the snapshot reads only the components of the configurations, which the exchange does not
+  // move, so it runs on a side stream beside the exchange sweeps
   cudaStream_t snap_s = c->stream;
   if (e == cudaSuccess && u_kn) {
     if (!c->cycle_side) e = cudaStreamCreateWithFlags(&c->cycle_side, cudaStreamNonBlocking);
@@ -1548,18 +1585,21 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
     if (e == cudaSuccess) snap_s = c->cycle_side;
   }
   int64_t base = 0, cbase = 0, ubase = 0;
-  if (e == cudaSuccess && u_kn) {  // the snapshot: every configuration re-evaluated, then u_kn per leg
-    double* snap = (double*)dev_of(2);
-    e = launch_evaluate(snap_s, *c, R, dx, snap);
+  if (e == cudaSuccess && u_kn) {
+    // the snapshot: u_kn per leg from the components of every configuration, which the trial's
+    // final energy evaluation (and the external moves) left in comps; U_k is linear in them, so
+    // no configuration is evaluated a second time
+    NvtxRange r("algdock_cycle: snapshot");
     for (int l = 0; l < d->n_legs && e == cudaSuccess; ++l) {
       const int64_t n = (int64_t)d->n_chains * d->K[l];
-      e = launch_ukn(snap_s, *c, n, snap + 4 * base, d->state_offset[l], d->K[l], (double*)dev_of(6) + ubase);
+      e = launch_ukn(snap_s, *c, n, dc + 4 * base, d->state_offset[l], d->K[l], (double*)dev_of(5) + ubase);
       base += n;
       ubase += (int64_t)d->K[l] * n;
     }
     if (e == cudaSuccess) e = cudaEventRecord(c->cycle_join, snap_s);
   }
   base = 0;
+  NvtxRange rx("algdock_cycle: exchange");
   for (int l = 0; l < d->n_legs && e == cudaSuccess; ++l) {
     e = launch_exchange(c->stream, *c, d->n_chains, d->K[l], d->state_offset[l], dc + 4 * base, dcfg + cbase,
                         ds + base, d->n_sweeps, d->max_sep, d->seed, cycle, d->ladder_offset + (int64_t)l * d->n_chains,
@@ -1568,10 +1608,17 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
     cbase += (int64_t)d->n_chains * d->K[l];
   }
   if (e == cudaSuccess && u_kn) e = cudaStreamWaitEvent(c->stream, c->cycle_join, 0);
-  for (int i = 0; i < 7 && e == cudaSuccess; ++i)
+  const bool checks = c->params.checks != 0;
+  if (e == cudaSuccess && checks) {
+    e = launch_run_check(c->stream, *c, *d, dx, dc, ds, dcfg, check_word(c));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->h_flag, check_word(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  }
+  for (int i = 0; i < kPieces && e == cudaSuccess; ++i)
     if (P[i].host && P[i].user) e = cudaMemcpyAsync(P[i].user, dev_of(i), P[i].bytes, cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess && any_host) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && (any_host || checks)) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cycle");
+  if (checks) return check_status(c, *c->h_flag, "cycle");
   return ALGDOCK_OK;
   ALGDOCK_CATCH(c)
 }
@@ -1580,6 +1627,7 @@ algdock_status algdock_gemm_bf16(algdock_ctx* c, int32_t M, int32_t N, int32_t K
                                  const uint16_t* B, int32_t ldb, void* C, int32_t ldc, int32_t epilogue,
                                  const float* bias, const uint16_t* mask, int32_t ldm, int32_t n_split) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_gemm_bf16");
   if (M < 0 || N < 0 || K < 1 || lda < K || ldb < K || lda % 8 || ldb % 8 || epilogue < 0 || epilogue > 3 ||
       ldc < N || n_split < 1 || ((epilogue == 1 || epilogue == 2) && !bias) || (epilogue == 3 && (!mask || ldm < N)) ||
       (n_split > 1 && epilogue != 0))
@@ -1602,6 +1650,7 @@ algdock_status algdock_gemm_bf16(algdock_ctx* c, int32_t M, int32_t N, int32_t K
 algdock_status algdock_mbar_partials(algdock_ctx* c, int32_t K, int64_t N, const double* u_kn, const int64_t* N_k,
                                      const double* f, int32_t precision_mode, double* pairs) {
   ALGDOCK_TRY(c)
+  NvtxRange range("algdock_mbar_partials");
   if (K < 1 || N < 0 || !N_k || !f || !pairs || (N > 0 && !u_kn) || (precision_mode != 0 && precision_mode != 1))
     return fail(c, ALGDOCK_E_INVALID, "mbar_partials: bad arguments (precision_mode 0 or 1)");
   if (K > kMbarMaxStates)

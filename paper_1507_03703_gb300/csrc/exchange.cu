@@ -4,10 +4,15 @@
 // Within one (separation, colour) phase the pairs (a, a+s) with floor(a/s) % 2 == colour are
 // disjoint, so a warp's lanes attempt them concurrently; phases follow one another in a fixed
 // order, which makes the result a deterministic function of the components and the Philox
-// counters.  The slot components do not change during the sweeps, so for K <= 160 the reduced
-// energies u_k(x_i) of every state and slot are computed once per ladder into shared memory
-// (by all four warps of the ladder's block) before one warp runs the sweeps; larger ladders
-// evaluate them per attempt.  Both give bit-identical decisions: the same FP64 expression.
+// counters.  The slot components do not change during the sweeps, so the energies a sweep reads
+// are tabulated once per ladder before one warp runs the sweeps:
+//  - ladders of up to 128 states (exchange_fast_kernel): FP32 energies shifted per slot, with a
+//    bound on their rounding error, and the FP32 log-uniform of every attempt; the sweeping warp
+//    keeps the ladder's configuration in registers and decides from the FP32 values wherever the
+//    bound allows, otherwise by the FP64 test;
+//  - up to 160 states (exchange_matrix_kernel): the FP64 u_k(x_i) of every state and slot;
+//  - larger ladders (exchange_direct_kernel): FP64 energies per attempt.
+// All three give the decisions of the same FP64 expression, bit for bit.
 #include <math.h>
 
 #include "internal.cuh"
@@ -16,6 +21,7 @@ namespace algdock {
 namespace {
 
 constexpr int kExMaxWarps = 4;
+constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMatrixMaxK = 160;  // K^2 doubles of shared memory
 
 struct SlotE {
@@ -119,50 +125,64 @@ __device__ inline bool load_ladder(const ExArgs& A, int64_t l, int* s_cfg, unsig
   return !__any_sync(0xffffffffu, bad);
 }
 
+// The fast kernel: one block per ladder of at most kFastMaxK states.
+constexpr int kFastMaxK = 128;     // four slots per lane of the sweeping warp
+constexpr int kFastThreads = 256;  // eight warps fill the tables, warp 0 sweeps
+constexpr size_t kFastSmemMax = 220 * 1024;
+
 // Shared-memory bytes of the fast kernel for a ladder of K states.
 __host__ __device__ inline size_t fast_smem_bytes(int K, int n_sweeps, int max_sep) {
   const int smax = max_sep < K - 1 ? max_sep : K - 1;
-  return (size_t)K * K * (sizeof(double) + sizeof(float)) +  // u in FP64 and FP32
+  return (size_t)K * (3 * sizeof(double) + sizeof(SlotE)) +          // states and slots in FP64
+         (size_t)K * 2 * sizeof(float4) +                             // FP32 state factors, centred slots
+         (size_t)K * K * sizeof(float2) +                             // shifted u and its magnitude bound
          (size_t)n_sweeps * (smax > 0 ? smax : 1) * K * sizeof(float) +  // log-uniforms
-         (size_t)2 * (smax > 0 ? smax : 1) * K * sizeof(int) +           // pair lists
-         (size_t)K * (3 * sizeof(double) + sizeof(SlotE) + sizeof(int)) +   // states, slots, config
-         (size_t)max_sep * K * sizeof(unsigned) + 64;                    // accept counters
+         (size_t)max_sep * K * sizeof(unsigned);                      // accept counters
 }
 
-// One ladder per block.  All warps fill u_k(x_i) (FP64, and its FP32 rounding), the pair list of
-// every (separation, colour) phase and the FP32 log-uniform of every attempt; warp 0 then sweeps,
-// deciding each attempt from the FP32 values when the margin to the boundary exceeds a bound on
-// their rounding error, and otherwise exactly as the FP64 test.
-__global__ void __launch_bounds__(kExMaxWarps * 32) exchange_fast_kernel(const ExArgs A) {
+// One ladder per block.  The energy difference of a swap,
+//   d = u_a(y) + u_b(x) - u_a(x) - u_b(y),
+// is unchanged when a constant per state or per slot is subtracted from every u_k(x_i).  The
+// block therefore tabulates, in FP32, v_k(x_i) = beta_k (e_i + w_sg,k psg_i + w_g,k pg_i) with each
+// slot component taken relative to its minimum over the ladder (e = U_L + U_I), together with
+// m_k(x_i) = |beta_k e_i| + |beta_k w_sg,k psg_i| + |beta_k w_g,k pg_i| in the same shifted
+// variables.  Each entry is within 5 2^-24 m of the exact shifted value (one rounding of each
+// centred component and each factor, three products, two sums), and the estimate of d from four
+// entries within 7 2^-24 of the sum of their m.  With the FP32 log-uniform (error below 2e-5) a
+// decision is taken from the estimate when its margin to the boundary ln u = -d exceeds
+// 1e-4 + 1e-6 sum(m); otherwise from the FP64 test itself, so every decision is the FP64 one.
+//
+// Warp 0 sweeps with the ladder's configuration in registers: slot k = 32 g + lane in register g.
+// In the phase (s, colour) a slot k is the lower member a of a pair when floor(k/s) has the
+// colour's parity and k + s < K, the upper member b when it has the other parity and k >= s.
+// Both members read their partner's configuration by a shuffle, their own row's entry at it, and
+// the partner's partial sum by a second shuffle; the two partial sums are added in either order
+// (FP32 addition commutes), so both members take the same decision and update their own register.
+template <int KG>
+__global__ void __launch_bounds__(kFastThreads) exchange_fast_kernel(const ExArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int K = A.K;
   const int smax = min(A.max_sep, K - 1);
   const int sm1 = smax > 0 ? smax : 1;
-  double* s_u = (double*)smem_raw;                       // [K][K]
-  double* s_st = s_u + (size_t)K * K;                     // [K][3]
-  SlotE* s_slot = (SlotE*)(s_st + 3 * K);                 // [K]
-  float* s_uf = (float*)(s_slot + K);                     // [K][K]
-  float* s_lu = s_uf + (size_t)K * K;                     // [n_sweeps][smax][K]
-  int* s_pairs = (int*)(s_lu + (size_t)A.n_sweeps * sm1 * K);  // [smax][2][K/2+1]... stored [smax][2][K]
-  int* s_cfg = s_pairs + 2 * sm1 * K;
-  unsigned* s_acc = (unsigned*)(s_cfg + K);               // [max_sep][K]
-  __shared__ int s_npairs[2 * 8];
+  double* s_st = (double*)smem_raw;                                    // [K][3]: beta, w_sg, w_g
+  SlotE* s_slot = (SlotE*)(s_st + 3 * K);                              // [K]
+  float4* s_w = (float4*)(s_slot + K);                                 // [K]: beta, beta w_sg, beta w_g
+  float4* s_d = s_w + K;                                               // [K]: centred slot components
+  float2* s_fm = (float2*)(s_d + K);                                   // [K][K]: v_k(x_i), m_k(x_i)
+  float* s_lu = (float*)(s_fm + (size_t)K * K);                        // [n_sweeps][smax][K]
+  unsigned* s_acc = (unsigned*)(s_lu + (size_t)A.n_sweeps * sm1 * K);  // [max_sep][K]
   const int64_t l = blockIdx.x;
   const uint32_t lid = (uint32_t)(A.ladder_offset + l);
+  const int lane = threadIdx.x & 31;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     const StateDev st = A.states[A.state_offset + k];
     s_st[3 * k] = st.beta;
     s_st[3 * k + 1] = st.w_sg;
     s_st[3 * k + 2] = st.w_g;
+    s_w[k] = make_float4((float)st.beta, (float)(st.beta * st.w_sg), (float)(st.beta * st.w_g), 0.f);
     s_slot[k] = load_slot(A.comps + (l * K + k) * 4);
   }
-  if (threadIdx.x < 2 * smax) {  // pair list of phase (s, colour), ascending a
-    const int s = threadIdx.x / 2 + 1, colour = threadIdx.x % 2;
-    int n = 0;
-    for (int a = 0; a + s < K; ++a)
-      if ((a / s) % 2 == colour) s_pairs[(2 * (s - 1) + colour) * K + n++] = a;
-    s_npairs[threadIdx.x] = n;
-  }
+  for (int i = threadIdx.x; i < A.max_sep * K; i += blockDim.x) s_acc[i] = 0u;
   const int n_att = A.n_sweeps * smax * K;
   for (int idx = threadIdx.x; idx < n_att; idx += blockDim.x) {
     const int a = idx % K, ss = idx / K;
@@ -178,67 +198,132 @@ __global__ void __launch_bounds__(kExMaxWarps * 32) exchange_fast_kernel(const E
     s_lu[idx] = lu;
   }
   __syncthreads();
+  {  // every warp forms the minima (fmin skips NaN; a non-finite slot only sends its pairs to FP64)
+    double me = INFINITY, msg = INFINITY, mg = INFINITY;
+    for (int i = lane; i < K; i += 32) {
+      me = fmin(me, s_slot[i].e);
+      msg = fmin(msg, s_slot[i].psg);
+      mg = fmin(mg, s_slot[i].pg);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      me = fmin(me, __shfl_xor_sync(kFull, me, o));
+      msg = fmin(msg, __shfl_xor_sync(kFull, msg, o));
+      mg = fmin(mg, __shfl_xor_sync(kFull, mg, o));
+    }
+    for (int i = threadIdx.x; i < K; i += blockDim.x)
+      s_d[i] = make_float4((float)(s_slot[i].e - me), (float)(s_slot[i].psg - msg), (float)(s_slot[i].pg - mg), 0.f);
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int k = e / K, i = e - k * K;
-    const double v = reduced(s_st[3 * k], s_st[3 * k + 1], s_st[3 * k + 2], s_slot[i]);
-    s_u[e] = v;
-    s_uf[e] = (float)v;
+    const float4 w = s_w[k], d = s_d[i];
+    const float t0 = w.x * d.x, t1 = w.y * d.y, t2 = w.z * d.z;
+    s_fm[e] = make_float2((t0 + t1) + t2, (fabsf(t0) + fabsf(t1)) + fabsf(t2));
   }
   __syncthreads();
   if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
+  int cfg[KG];
+  float uo[KG], mo[KG];  // the entry of the slot's own state at its own configuration
   bool bad = false;
-  for (int i = lane; i < K; i += 32) {
-    s_cfg[i] = A.config_of[l * K + i];
-    bad |= (unsigned)s_cfg[i] >= (unsigned)K;
+#pragma unroll
+  for (int g = 0; g < KG; ++g) {
+    const int k = 32 * g + lane;
+    cfg[g] = k < K ? A.config_of[l * K + k] : 0;
+    bad |= (unsigned)cfg[g] >= (unsigned)K;
   }
-  for (int i = lane; i < A.max_sep * K; i += 32) s_acc[i] = 0u;
-  __syncwarp();
-  if (__any_sync(0xffffffffu, bad)) return;  // not a list of slots 0..K-1: leave the ladder untouched
+  if (__any_sync(kFull, bad)) return;  // not a list of slots 0..K-1: leave the ladder untouched
+#pragma unroll
+  for (int g = 0; g < KG; ++g) {
+    const int k = 32 * g + lane;
+    const float2 v = s_fm[(k < K ? k : 0) * K + cfg[g]];
+    uo[g] = v.x;
+    mo[g] = v.y;
+  }
+  auto U = [&](int k, int i) { return reduced(s_st[3 * k], s_st[3 * k + 1], s_st[3 * k + 2], s_slot[i]); };
+  // the lane's role in every phase: bit (2 (s - 1) + colour) KG + g of `lower` when its slot of
+  // group g is the lower member of a pair, of `active` when it is either member
+  uint64_t lower_bits = 0, active_bits = 0;
+  for (int s = 1; s <= smax; ++s)
+    for (int colour = 0; colour < 2; ++colour)
+#pragma unroll
+      for (int g = 0; g < KG; ++g) {
+        const int k = 32 * g + lane;
+        const bool own = (k / s) % 2 == colour;
+        const bool lo = own && k + s < K, hi = !own && k >= s && k < K;
+        const int bit = (2 * (s - 1) + colour) * KG + g;
+        lower_bits |= (uint64_t)lo << bit;
+        active_bits |= (uint64_t)(lo || hi) << bit;
+      }
   for (int sw = 0; sw < A.n_sweeps; ++sw) {
-    for (int s = 1; s <= smax; ++s) {
-      // floor(p / s) = (p * inv_s) >> 16 exactly for p < 1024 and s <= 8
-      const int inv_s = (65536 + s - 1) / s;
+    const float* lu_sw = s_lu + (size_t)sw * smax * K;
+    uint32_t acc_bits = 0;  // bit (s - 1) KG + g: the pair whose lower member is this slot was accepted
+#pragma unroll
+    for (int s = 1; s <= 8; ++s) {
+      if (s > smax) break;
+      const bool wrap_up = lane + s >= 32, wrap_dn = lane < s;
+#pragma unroll
       for (int colour = 0; colour < 2; ++colour) {
         const int ph = 2 * (s - 1) + colour;
-        const int np = s_npairs[ph];
-        for (int p = lane; p < np; p += 32) {
-          // the p-th pair of the phase, in the order of the list: blocks of s consecutive a whose
-          // block index has the colour's parity
-          const int t = (p * inv_s) >> 16;
-          const int a = s * (colour + 2 * t) + (p - t * s), b = a + s;
-          const int xi = s_cfg[a], yi = s_cfg[b];
-          const float f1 = s_uf[a * K + yi], f2 = s_uf[b * K + xi], f3 = s_uf[a * K + xi], f4 = s_uf[b * K + yi];
-          const float df = ((f1 + f2) - f3) - f4;
-          // |df - d| <= 2^-22 (|f1| + |f2| + |f3| + |f4|) from the roundings; ln-uniform error < 2e-5
-          const float band = 1e-3f + 1e-6f * (fabsf(f1) + fabsf(f2) + fabsf(f3) + fabsf(f4));
-          const float lu = s_lu[((sw * smax) + (s - 1)) * K + a];
-          bool acc;
-          if (lu != -INFINITY && lu < -df - band) {
-            acc = true;
-          } else if (lu != -INFINITY && lu > -df + band) {
-            acc = false;
-          } else {  // close to the boundary, or not finite: the FP64 test itself
-            double d = __dadd_rn(s_u[a * K + yi], s_u[b * K + xi]);
-            d = __dsub_rn(d, s_u[a * K + xi]);
-            d = __dsub_rn(d, s_u[b * K + yi]);
+        int cu[KG], cd[KG];
+#pragma unroll
+        for (int g = 0; g < KG; ++g) {
+          cu[g] = __shfl_sync(kFull, cfg[g], (lane + s) & 31);
+          cd[g] = __shfl_sync(kFull, cfg[g], (lane - s) & 31);
+        }
+#pragma unroll
+        for (int g = 0; g < KG; ++g) {
+          const bool act = (active_bits >> (ph * KG + g)) & 1u;
+          const bool lo = (lower_bits >> (ph * KG + g)) & 1u;
+          // the partner: state k + s (lower member) or k - s (upper member), holding configuration
+          // pc; the other group's register where the partner's lane wraps (never for an active
+          // slot at the first or last group)
+          const int k = 32 * g + lane;
+          const int vu = wrap_up ? cu[g + 1 < KG ? g + 1 : g] : cu[g];
+          const int vd = wrap_dn ? cd[g > 0 ? g - 1 : 0] : cd[g];
+          const int pc = act ? (lo ? vu : vd) : 0;
+          const int ks = act ? k : 0, ps = act ? (lo ? k + s : k - s) : 0, own = act ? cfg[g] : 0;
+          const float2 f_kp = s_fm[ks * K + pc];   // own state at the partner's configuration
+          const float2 f_po = s_fm[ps * K + own];  // partner's state at this configuration
+          const float2 f_pp = s_fm[ps * K + pc];   // partner's state at its own configuration
+          const int a = lo ? k : k - s;
+          const float lu = lu_sw[(s - 1) * K + (act ? a : 0)];
+          // this member's half of d and the partner's, each formed from the same two entries on
+          // both lanes (uo is the stored f_k at the own configuration), added in either order
+          const float df = (f_kp.x - uo[g]) + (f_po.x - f_pp.x);
+          const float band = 1e-4f + 1e-6f * ((f_kp.y + mo[g]) + (f_po.y + f_pp.y));
+          const bool sure_acc = lu != -INFINITY && lu < -df - band;
+          const bool sure_rej = lu != -INFINITY && lu > -df + band;
+          bool acc = sure_acc;
+          if (act && !sure_acc && !sure_rej) {  // close to the boundary, or not finite: the FP64 test itself
+            const int x = lo ? own : pc, y = lo ? pc : own, b = a + s;
+            double d = __dadd_rn(U(a, y), U(b, x));
+            d = __dsub_rn(d, U(a, x));
+            d = __dsub_rn(d, U(b, y));
             const U4 o = philox(A.seed, (uint32_t)((sw * A.max_sep + s - 1) * 65536 + a), lid, A.cycle,
                                 kPurposeExchange);
             acc = (d <= 0.0) || (uniform53(o.x, o.y) < exp(-d));
           }
-          if (acc) {
-            s_cfg[a] = yi;
-            s_cfg[b] = xi;
-            s_acc[(s - 1) * K + a] += 1u;
-          }
+          acc = acc && act;
+          cfg[g] = acc ? pc : cfg[g];
+          uo[g] = acc ? f_kp.x : uo[g];
+          mo[g] = acc ? f_kp.y : mo[g];
+          acc_bits |= (uint32_t)(acc && lo) << ((s - 1) * KG + g);
         }
-        __syncwarp();
       }
     }
+    while (acc_bits) {  // this sweep's accepts into the counters (one lane per lower member)
+      const int bit = __ffs(acc_bits) - 1;
+      acc_bits &= acc_bits - 1;
+      s_acc[(bit / KG) * K + 32 * (bit % KG) + lane] += 1u;
+    }
   }
-  for (int k = lane; k < K; k += 32) {
-    A.config_of[l * K + k] = s_cfg[k];
-    if (A.state_of) A.state_of[l * K + s_cfg[k]] = A.state_offset + k;
+  __syncwarp();
+#pragma unroll
+  for (int g = 0; g < KG; ++g) {
+    const int k = 32 * g + lane;
+    if (k >= K) continue;
+    A.config_of[l * K + k] = cfg[g];
+    if (A.state_of) A.state_of[l * K + cfg[g]] = A.state_offset + k;
   }
   for (int i = lane; i < A.max_sep * K; i += 32) {
     const int s = i / K + 1, a = i % K;
@@ -316,10 +401,15 @@ cudaError_t launch_exchange(cudaStream_t s, const algdock_ctx& c, int n_ladders,
            (uint32_t)cycle, ladder_offset, attempts, accepts};
   const size_t counters = (size_t)2 * max_sep * K * sizeof(unsigned);
   const size_t fast = fast_smem_bytes(K, n_sweeps, max_sep);
-  if (max_sep <= 8 && fast <= 200 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(exchange_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast);
+  if (K <= kFastMaxK && max_sep <= 8 && fast <= kFastSmemMax) {
+    const int kg = (K + 31) / 32;
+    void (*fn)(ExArgs) = kg == 1   ? exchange_fast_kernel<1>
+                         : kg == 2 ? exchange_fast_kernel<2>
+                         : kg == 3 ? exchange_fast_kernel<3>
+                                   : exchange_fast_kernel<4>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast);
     if (e != cudaSuccess) return e;
-    exchange_fast_kernel<<<n_ladders, kExMaxWarps * 32, fast, s>>>(A);
+    fn<<<n_ladders, kFastThreads, fast, s>>>(A);
     return cudaGetLastError();
   }
   if (K <= kMatrixMaxK) {

@@ -6,9 +6,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "algdock.h"
 
 namespace algdock {
+
+// A named NVTX range over one scope (a call or one stage of it): profilers that record NVTX show
+// the host-side span in which the stage's work is enqueued.  Without a profiler attached the push
+// and pop return at once.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Unit conventions: A, kcal/mol, amu, fs.
 constexpr double kBoltzmann = 0.0019872043;        // kcal / (mol K)
@@ -240,6 +252,20 @@ struct algdock_ctx {
   size_t stage_bytes = 0;
   cudaStream_t cycle_side = nullptr;
   cudaEvent_t cycle_fork = nullptr, cycle_join = nullptr;
+  // the context's seed and the method's adjustable arguments (algdock_create, algdock_set_params)
+  uint64_t seed = 0;
+  algdock_params params{};
+  // replicas owned by the context (algdock_replicas_init), in algdock_cycle's layout: one buffer
+  // [x | comps | state_of | config_of | counters]
+  bool has_replicas = false;
+  algdock_run_desc run{};
+  int64_t n_replicas = 0;
+  void* d_rbuf = nullptr;
+  float* d_rx = nullptr;
+  double* d_rcomps = nullptr;
+  int32_t* d_rstate = nullptr;
+  int32_t* d_rcfg = nullptr;
+  int64_t* d_rcnt = nullptr;
   // learned proposal: torsion tree and scratch grown on demand
   algdock::LearnedTopo ltopo{};
   void* d_learn = nullptr;
@@ -277,6 +303,14 @@ struct algdock_ctx {
 };
 
 namespace algdock {
+// Device-side checks of a cycle's results (params.checks): the flag word in the context's work
+// buffer, the check kernel over a run's arrays, and the status a set flag turns into.
+int* check_word(algdock_ctx* c);
+cudaError_t launch_run_check(cudaStream_t s, const algdock_ctx& c, const algdock_run_desc& d, const float* x,
+                             const double* comps, const int32_t* state_of, const int32_t* config_of, int* flag);
+algdock_status check_status(algdock_ctx* c, int bits, const char* where);
+algdock_status params_check(algdock_ctx* c, const algdock_params& p);
+
 // CRC-32 (the IEEE 802.3 polynomial, reflected, as in zip and PNG) of n bytes, continuing from crc
 // (0 to start).
 uint32_t crc32_update(uint32_t crc, const void* data, size_t n);

@@ -1,8 +1,8 @@
 """algdock_cycle, one iteration of the paper's loop over a whole run ("Equilibration and
 production": an HMC move of every replica, then the exchange sweeps of every ladder, then the
-snapshot's reduced energies), with the run's arrays in host memory or on the device.  Both must
-repeat, bit for bit, the same cycles made of the separate calls (algdock_hmc_cycle,
-algdock_exchange, algdock_reduced_energies) on device buffers."""
+snapshot's reduced energies from the components the trial left), with the run's arrays in host
+memory or on the device.  Both must repeat, bit for bit, the same cycles made of the separate
+calls (algdock_hmc_cycle, algdock_exchange, algdock_reduced_energies) on device buffers."""
 import numpy as np
 import pytest
 
@@ -30,16 +30,16 @@ def test_cycle_with_host_or_device_arrays_repeats_the_separate_calls():
     for cyc in range(n_cyc):
         ref.hmc(cyc, steps)
         ref.exchange(cyc)
-        snap = torch.empty((R, 4), dtype=torch.float64, device="cuda")
-        ctx.reduced_energies(R, x=ref.x, comps=snap)
         parts = []
         for li, (K, off) in enumerate(legs):
             u = torch.empty((K, C * K), dtype=torch.float64, device="cuda")
-            ctx.reduced_energies(C * K, comps=snap[ref.leg_slice(li)], k_begin=off, k_count=K, u_kn=u)
+            ctx.reduced_energies(C * K, comps=ref.comps[ref.leg_slice(li)], k_begin=off, k_count=K, u_kn=u)
             parts.append(u.reshape(-1))
         ukn_ref.append(torch.cat(parts).cpu().numpy())
     n_ukn = sum(K * C * K for K, _ in legs)
-    for where in ("host", "device"):
+    # device first, so that the host pass grows the staging buffer after the snapshot's side stream
+    # and events exist, and a device pass after it still uses them
+    for where in ("device", "host", "device"):
         st0 = np.concatenate([np.tile(off + np.arange(K), C) for K, off in legs]).astype(np.int32)
         cfg0 = np.concatenate([np.tile(np.arange(K), C) for K, _ in legs]).astype(np.int32)
         arrays = {"x": torch.from_numpy(x0.copy()), "comps": torch.zeros((R, 4), dtype=torch.float64),
