@@ -140,6 +140,20 @@ __host__ __device__ inline size_t fast_smem_bytes(int K, int n_sweeps, int max_s
          (size_t)max_sep * K * sizeof(unsigned);                      // accept counters
 }
 
+// The FP64 test of one attempt (pair a, a + s of sweep sw; configurations x at a and y at a + s),
+// for the decisions the FP32 estimate leaves open.  Out of line: it is rare, and one copy serves
+// every unrolled phase of the sweep loop.
+__device__ __noinline__ bool exact_swap(const ExArgs& A, const double* s_st, const SlotE* s_slot, uint32_t lid, int sw,
+                                        int s, int a, int x, int y) {
+  auto U = [&](int k, int i) { return reduced(s_st[3 * k], s_st[3 * k + 1], s_st[3 * k + 2], s_slot[i]); };
+  const int b = a + s;
+  double d = __dadd_rn(U(a, y), U(b, x));
+  d = __dsub_rn(d, U(a, x));
+  d = __dsub_rn(d, U(b, y));
+  const U4 o = philox(A.seed, (uint32_t)((sw * A.max_sep + s - 1) * 65536 + a), lid, A.cycle, kPurposeExchange);
+  return (d <= 0.0) || (uniform53(o.x, o.y) < exp(-d));
+}
+
 // One ladder per block.  The energy difference of a swap,
 //   d = u_a(y) + u_b(x) - u_a(x) - u_b(y),
 // is unchanged when a constant per state or per slot is subtracted from every u_k(x_i).  The
@@ -239,7 +253,6 @@ __global__ void __launch_bounds__(kFastThreads) exchange_fast_kernel(const ExArg
     uo[g] = v.x;
     mo[g] = v.y;
   }
-  auto U = [&](int k, int i) { return reduced(s_st[3 * k], s_st[3 * k + 1], s_st[3 * k + 2], s_slot[i]); };
   // the lane's role in every phase: bit (2 (s - 1) + colour) KG + g of `lower` when its slot of
   // group g is the lower member of a pair, of `active` when it is either member
   uint64_t lower_bits = 0, active_bits = 0;
@@ -257,10 +270,9 @@ __global__ void __launch_bounds__(kFastThreads) exchange_fast_kernel(const ExArg
   for (int sw = 0; sw < A.n_sweeps; ++sw) {
     const float* lu_sw = s_lu + (size_t)sw * smax * K;
     uint32_t acc_bits = 0;  // bit (s - 1) KG + g: the pair whose lower member is this slot was accepted
-#pragma unroll
-    for (int s = 1; s <= 8; ++s) {
-      if (s > smax) break;
+    for (int s = 1; s <= smax; ++s) {
       const bool wrap_up = lane + s >= 32, wrap_dn = lane < s;
+      const float* lu_s = lu_sw + (s - 1) * K;
 #pragma unroll
       for (int colour = 0; colour < 2; ++colour) {
         const int ph = 2 * (s - 1) + colour;
@@ -286,7 +298,7 @@ __global__ void __launch_bounds__(kFastThreads) exchange_fast_kernel(const ExArg
           const float2 f_po = s_fm[ps * K + own];  // partner's state at this configuration
           const float2 f_pp = s_fm[ps * K + pc];   // partner's state at its own configuration
           const int a = lo ? k : k - s;
-          const float lu = lu_sw[(s - 1) * K + (act ? a : 0)];
+          const float lu = lu_s[act ? a : 0];
           // this member's half of d and the partner's, each formed from the same two entries on
           // both lanes (uo is the stored f_k at the own configuration), added in either order
           const float df = (f_kp.x - uo[g]) + (f_po.x - f_pp.x);
@@ -294,15 +306,8 @@ __global__ void __launch_bounds__(kFastThreads) exchange_fast_kernel(const ExArg
           const bool sure_acc = lu != -INFINITY && lu < -df - band;
           const bool sure_rej = lu != -INFINITY && lu > -df + band;
           bool acc = sure_acc;
-          if (act && !sure_acc && !sure_rej) {  // close to the boundary, or not finite: the FP64 test itself
-            const int x = lo ? own : pc, y = lo ? pc : own, b = a + s;
-            double d = __dadd_rn(U(a, y), U(b, x));
-            d = __dsub_rn(d, U(a, x));
-            d = __dsub_rn(d, U(b, y));
-            const U4 o = philox(A.seed, (uint32_t)((sw * A.max_sep + s - 1) * 65536 + a), lid, A.cycle,
-                                kPurposeExchange);
-            acc = (d <= 0.0) || (uniform53(o.x, o.y) < exp(-d));
-          }
+          if (act && !sure_acc && !sure_rej)  // close to the boundary, or not finite: the FP64 test itself
+            acc = exact_swap(A, s_st, s_slot, lid, sw, s, a, lo ? own : pc, lo ? pc : own);
           acc = acc && act;
           cfg[g] = acc ? pc : cfg[g];
           uo[g] = acc ? f_kp.x : uo[g];
