@@ -127,7 +127,7 @@ __device__ inline bool load_ladder(const ExArgs& A, int64_t l, int* s_cfg, unsig
 
 // The fast kernel: one block per ladder of at most kFastMaxK states.
 constexpr int kFastMaxK = 128;     // four slots per lane of the sweeping warp
-constexpr int kFastThreads = 256;  // eight warps fill the tables, warp 0 sweeps
+constexpr int kFastThreads = 640;  // twenty warps fill the tables, warp 0 sweeps
 constexpr size_t kFastSmemMax = 220 * 1024;
 
 // Shared-memory bytes of the fast kernel for a ladder of K states.
@@ -282,37 +282,57 @@ __global__ void __launch_bounds__(kFastThreads) exchange_fast_kernel(const ExArg
           cu[g] = __shfl_sync(kFull, cfg[g], (lane + s) & 31);
           cd[g] = __shfl_sync(kFull, cfg[g], (lane - s) & 31);
         }
+        // every group's partner, table entries and log-uniform first, then the decisions: the loads
+        // of all groups are in flight together
+        bool act[KG], lo[KG];
+        int pc[KG], own[KG], a[KG];
+        float2 f_kp[KG], f_po[KG], f_pp[KG];
+        float lu[KG];
 #pragma unroll
         for (int g = 0; g < KG; ++g) {
-          const bool act = (active_bits >> (ph * KG + g)) & 1u;
-          const bool lo = (lower_bits >> (ph * KG + g)) & 1u;
+          act[g] = (active_bits >> (ph * KG + g)) & 1u;
+          lo[g] = (lower_bits >> (ph * KG + g)) & 1u;
           // the partner: state k + s (lower member) or k - s (upper member), holding configuration
           // pc; the other group's register where the partner's lane wraps (never for an active
           // slot at the first or last group)
           const int k = 32 * g + lane;
           const int vu = wrap_up ? cu[g + 1 < KG ? g + 1 : g] : cu[g];
           const int vd = wrap_dn ? cd[g > 0 ? g - 1 : 0] : cd[g];
-          const int pc = act ? (lo ? vu : vd) : 0;
-          const int ks = act ? k : 0, ps = act ? (lo ? k + s : k - s) : 0, own = act ? cfg[g] : 0;
-          const float2 f_kp = s_fm[ks * K + pc];   // own state at the partner's configuration
-          const float2 f_po = s_fm[ps * K + own];  // partner's state at this configuration
-          const float2 f_pp = s_fm[ps * K + pc];   // partner's state at its own configuration
-          const int a = lo ? k : k - s;
-          const float lu = lu_s[act ? a : 0];
+          pc[g] = act[g] ? (lo[g] ? vu : vd) : 0;
+          own[g] = act[g] ? cfg[g] : 0;
+          const int ks = act[g] ? k : 0, ps = act[g] ? (lo[g] ? k + s : k - s) : 0;
+          f_kp[g] = s_fm[ks * K + pc[g]];      // own state at the partner's configuration
+          f_po[g] = s_fm[ps * K + own[g]];     // partner's state at this configuration
+          f_pp[g] = s_fm[ps * K + pc[g]];      // partner's state at its own configuration
+          a[g] = lo[g] ? k : k - s;
+          lu[g] = lu_s[act[g] ? a[g] : 0];
+        }
+        bool acc[KG];
+        unsigned open = 0u;  // groups whose decision needs the FP64 test
+#pragma unroll
+        for (int g = 0; g < KG; ++g) {
           // this member's half of d and the partner's, each formed from the same two entries on
-          // both lanes (uo is the stored f_k at the own configuration), added in either order
-          const float df = (f_kp.x - uo[g]) + (f_po.x - f_pp.x);
-          const float band = 1e-4f + 1e-6f * ((f_kp.y + mo[g]) + (f_po.y + f_pp.y));
-          const bool sure_acc = lu != -INFINITY && lu < -df - band;
-          const bool sure_rej = lu != -INFINITY && lu > -df + band;
-          bool acc = sure_acc;
-          if (act && !sure_acc && !sure_rej)  // close to the boundary, or not finite: the FP64 test itself
-            acc = exact_swap(A, s_st, s_slot, lid, sw, s, a, lo ? own : pc, lo ? pc : own);
-          acc = acc && act;
-          cfg[g] = acc ? pc : cfg[g];
-          uo[g] = acc ? f_kp.x : uo[g];
-          mo[g] = acc ? f_kp.y : mo[g];
-          acc_bits |= (uint32_t)(acc && lo) << ((s - 1) * KG + g);
+          // both lanes (uo is the stored entry at the own configuration), added in either order
+          const float df = (f_kp[g].x - uo[g]) + (f_po[g].x - f_pp[g].x);
+          const float band = 1e-4f + 1e-6f * ((f_kp[g].y + mo[g]) + (f_po[g].y + f_pp[g].y));
+          const bool sure_acc = lu[g] != -INFINITY && lu[g] < -df - band;
+          const bool sure_rej = lu[g] != -INFINITY && lu[g] > -df + band;
+          acc[g] = sure_acc;
+          open |= (unsigned)(act[g] && !sure_acc && !sure_rej) << g;
+        }
+        if (__any_sync(kFull, open != 0u)) {  // close to the boundary, or not finite: the FP64 test itself
+#pragma unroll
+          for (int g = 0; g < KG; ++g)
+            if ((open >> g) & 1u)
+              acc[g] = exact_swap(A, s_st, s_slot, lid, sw, s, a[g], lo[g] ? own[g] : pc[g], lo[g] ? pc[g] : own[g]);
+        }
+#pragma unroll
+        for (int g = 0; g < KG; ++g) {
+          const bool take = acc[g] && act[g];
+          cfg[g] = take ? pc[g] : cfg[g];
+          uo[g] = take ? f_kp[g].x : uo[g];
+          mo[g] = take ? f_kp[g].y : mo[g];
+          acc_bits |= (uint32_t)(take && lo[g]) << ((s - 1) * KG + g);
         }
       }
     }
