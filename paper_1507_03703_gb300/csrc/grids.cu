@@ -76,9 +76,11 @@ __global__ void __launch_bounds__(kBuildThreads) grid_build_kernel(int nx, int n
 }
 
 // Derived lattices, computed in FP64 and rounded once to FP32.
-__global__ void grid_prepare_kernel(int64_t n, const float* __restrict__ ljr, const float* __restrict__ lja,
+// Node p's values go into its own x-pair record (first half) and into the record of its x - 1
+// neighbour in the same row (second half); the record of a row's last node gets a zero second half.
+__global__ void grid_prepare_kernel(int64_t n, int nx, const float* __restrict__ ljr, const float* __restrict__ lja,
                                     const float* __restrict__ elec, double vmax_r, double vmax_e, float4* hard,
-                                    float2* soft) {
+                                    float4* soft) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   double v = (double)ljr[p];
@@ -88,8 +90,20 @@ __global__ void grid_prepare_kernel(int64_t n, const float* __restrict__ ljr, co
   const double root = pow(v, 0.25);
   const double soft_r = isinf(vmax_r) ? root : pow(vmax_r * tanh(v / vmax_r), 0.25);
   const double soft_e = isinf(vmax_e) ? e : vmax_e * tanh(e / vmax_e);
-  hard[p] = make_float4((float)root, lja[p], elec[p], 0.f);
-  soft[p] = make_float2((float)soft_r, (float)soft_e);
+  const float4 h = make_float4((float)root, lja[p], elec[p], 0.f);
+  const float2 sf = make_float2((float)soft_r, (float)soft_e);
+  float2* soft2 = (float2*)soft;
+  const int x = (int)(p % nx);
+  hard[2 * p] = h;
+  soft2[2 * p] = sf;
+  if (x > 0) {
+    hard[2 * (p - 1) + 1] = h;
+    soft2[2 * (p - 1) + 1] = sf;
+  }
+  if (x == nx - 1) {
+    hard[2 * p + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    soft2[2 * p + 1] = make_float2(0.f, 0.f);
+  }
 }
 
 // Peak rate of the interpolation's gathers, for the gather roofline (not a step of the method):
@@ -107,7 +121,7 @@ __device__ __forceinline__ int below(uint32_t r, int n) { return (int)(((uint64_
 
 template <bool SOFT>
 __global__ void __launch_bounds__(256) gather_probe_kernel(const float4* __restrict__ hard,
-                                                           const float2* __restrict__ soft, int nx, int ny, int nz,
+                                                           const float4* __restrict__ soft, int nx, int ny, int nz,
                                                            int64_t n_cells, uint32_t seed, float* sink) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -119,15 +133,18 @@ __global__ void __launch_bounds__(256) gather_probe_kernel(const float4* __restr
     const int cx = below(xorshift32(st), nx - 1), cy = below(xorshift32(st), ny - 1),
               cz = below(xorshift32(st), nz - 1);
     const int64_t b = cz * sz + cy * sy + cx;
-    const float4 h0 = __ldg(hard + b), h1 = __ldg(hard + b + 1), h2 = __ldg(hard + b + sy),
-                 h3 = __ldg(hard + b + sy + 1), h4 = __ldg(hard + b + sz), h5 = __ldg(hard + b + sz + 1),
-                 h6 = __ldg(hard + b + sz + sy), h7 = __ldg(hard + b + sz + sy + 1);
+    // the cell's x-pair records, as the interpolation reads them: four 32-byte hard records and
+    // (with SOFT) four 16-byte soft records
+    float4 h0, h1, h2, h3, h4, h5, h6, h7;
+    ldg_pair(hard + 2 * b, h0, h1);
+    ldg_pair(hard + 2 * (b + sy), h2, h3);
+    ldg_pair(hard + 2 * (b + sz), h4, h5);
+    ldg_pair(hard + 2 * (b + sz + sy), h6, h7);
     acc += ((h0.x + h1.y) + (h2.z + h3.x)) + ((h4.y + h5.z) + (h6.x + h7.y));
     if (SOFT) {
-      const float2 s0 = __ldg(soft + b), s1 = __ldg(soft + b + 1), s2 = __ldg(soft + b + sy),
-                   s3 = __ldg(soft + b + sy + 1), s4 = __ldg(soft + b + sz), s5 = __ldg(soft + b + sz + 1),
-                   s6 = __ldg(soft + b + sz + sy), s7 = __ldg(soft + b + sz + sy + 1);
-      acc += ((s0.x + s1.y) + (s2.x + s3.y)) + ((s4.x + s5.y) + (s6.x + s7.y));
+      const float4 s0 = __ldg(soft + b), s1 = __ldg(soft + b + sy), s2 = __ldg(soft + b + sz),
+                   s3 = __ldg(soft + b + sz + sy);
+      acc += ((s0.x + s1.w) + (s2.x + s3.w)) + ((s0.z + s1.y) + (s2.z + s3.y));
     }
   }
   if (acc == -1.2345e-31f) sink[0] = acc;
@@ -170,12 +187,12 @@ cudaError_t launch_grid_build(cudaStream_t s, const algdock_grid_desc& d, int n_
   return e;
 }
 
-cudaError_t launch_grid_prepare(cudaStream_t s, size_t n_nodes, const float* ljr, const float* lja,
-                                const float* elec, double vmax_r, double vmax_e, float4* hard, float2* soft) {
+cudaError_t launch_grid_prepare(cudaStream_t s, size_t n_nodes, int nx, const float* ljr, const float* lja,
+                                const float* elec, double vmax_r, double vmax_e, float4* hard, float4* soft) {
   const int threads = 256;
   const size_t blocks = (n_nodes + threads - 1) / threads;
-  grid_prepare_kernel<<<(unsigned)blocks, threads, 0, s>>>((int64_t)n_nodes, ljr, lja, elec, vmax_r, vmax_e, hard,
-                                                            soft);
+  grid_prepare_kernel<<<(unsigned)blocks, threads, 0, s>>>((int64_t)n_nodes, nx, ljr, lja, elec, vmax_r, vmax_e,
+                                                            hard, soft);
   return cudaGetLastError();
 }
 

@@ -154,7 +154,6 @@ __device__ inline Tri2 tri2(f32x2 c000, f32x2 c001, f32x2 c010, f32x2 c011, f32x
 }
 __device__ inline f32x2 lo2(float4 c) { return pack2(c.x, c.y); }
 __device__ inline f32x2 hi2(float4 c) { return pack2(c.z, c.w); }
-__device__ inline f32x2 as2(float2 c) { return pack2(c.x, c.y); }
 
 // Grid energies and forces of one atom.  hard / soft select which lattices are read.  The hard
 // lattice's channels run as the pairs (LJr^1/4, LJa) and (elec, 0), the soft lattice's as one pair.
@@ -169,15 +168,16 @@ __device__ inline GridOut grid_atom(const GridDev& G, float x, float y, float z,
   axis_coord(z, G.oz, G.inv_h, G.nz, cz, tz, iz);
   o.outside = !(ix && iy && iz);
   const float mx = ix ? G.inv_h : 0.f, my = iy ? G.inv_h : 0.f, mz = iz ? G.inv_h : 0.f;
-  const int64_t sx = 1, sy = G.nx, sz = (int64_t)G.nx * G.ny;
+  const int64_t sy = G.nx, sz = (int64_t)G.nx * G.ny;
   const int64_t b = (int64_t)cz * sz + (int64_t)cy * sy + cx;
   const f32x2 tx2 = pack2(tx, tx), ty2 = pack2(ty, ty), tz2 = pack2(tz, tz);
   f32x2 gx2 = 0ull, gy2 = 0ull, gz2 = 0ull;  // (sum of the weighted channel gradients) in two halves
-  if (hard) {
-    const float4 c000 = __ldg(G.hard + b), c001 = __ldg(G.hard + b + sx);
-    const float4 c010 = __ldg(G.hard + b + sy), c011 = __ldg(G.hard + b + sy + sx);
-    const float4 c100 = __ldg(G.hard + b + sz), c101 = __ldg(G.hard + b + sz + sx);
-    const float4 c110 = __ldg(G.hard + b + sz + sy), c111 = __ldg(G.hard + b + sz + sy + sx);
+  if (hard) {  // four x-pair records: corners (x, x+1) of each (y, z) edge in one 32-byte load
+    float4 c000, c001, c010, c011, c100, c101, c110, c111;
+    ldg_pair(G.hard + 2 * b, c000, c001);
+    ldg_pair(G.hard + 2 * (b + sy), c010, c011);
+    ldg_pair(G.hard + 2 * (b + sz), c100, c101);
+    ldg_pair(G.hard + 2 * (b + sz + sy), c110, c111);
     const Tri2 ra = tri2(lo2(c000), lo2(c001), lo2(c010), lo2(c011), lo2(c100), lo2(c101), lo2(c110), lo2(c111), tx2,
                          ty2, tz2);
     const Tri2 e0 = tri2(hi2(c000), hi2(c001), hi2(c010), hi2(c011), hi2(c100), hi2(c101), hi2(c110), hi2(c111), tx2,
@@ -195,13 +195,10 @@ __device__ inline GridOut grid_atom(const GridDev& G, float x, float y, float z,
       gz2 = fma2(kra, ra.gz, mul2(ke, e0.gz));
     }
   }
-  if (soft) {
-    const float2 c000 = __ldg(G.soft + b), c001 = __ldg(G.soft + b + sx);
-    const float2 c010 = __ldg(G.soft + b + sy), c011 = __ldg(G.soft + b + sy + sx);
-    const float2 c100 = __ldg(G.soft + b + sz), c101 = __ldg(G.soft + b + sz + sx);
-    const float2 c110 = __ldg(G.soft + b + sz + sy), c111 = __ldg(G.soft + b + sz + sy + sx);
-    const Tri2 re = tri2(as2(c000), as2(c001), as2(c010), as2(c011), as2(c100), as2(c101), as2(c110), as2(c111), tx2,
-                         ty2, tz2);
+  if (soft) {  // four 16-byte x-pair records
+    const float4 e00 = __ldg(G.soft + b), e01 = __ldg(G.soft + b + sy);
+    const float4 e10 = __ldg(G.soft + b + sz), e11 = __ldg(G.soft + b + sz + sy);
+    const Tri2 re = tri2(lo2(e00), hi2(e00), lo2(e01), hi2(e01), lo2(e10), hi2(e10), lo2(e11), hi2(e11), tx2, ty2, tz2);
     float rv, ev;
     unpack2(re.v, rv, ev);
     const float r2 = rv * rv;
