@@ -603,7 +603,7 @@ algdock_status algdock_grids_load(algdock_ctx* c, const algdock_grid_desc* d, co
     c->d_soft = nullptr;
     c->has_grid = false;
     e = cudaMalloc(&c->d_hard, 2 * n * sizeof(float4));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_soft, n * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_soft, 2 * n * sizeof(float4));
     if (e != cudaSuccess) return cuda_fail(c, e, "grids_load");
     c->grid_nodes = n;
   }
@@ -613,8 +613,8 @@ algdock_status algdock_grids_load(algdock_ctx* c, const algdock_grid_desc* d, co
   if (e == cudaSuccess) e = device_view(c->stream, lja, n * 4, &pa, &oa);
   if (e == cudaSuccess) e = device_view(c->stream, elec, n * 4, &pe, &oe);
   if (e == cudaSuccess)
-    e = launch_grid_prepare(c->stream, n, d->n[0], (const float*)pr, (const float*)pa, (const float*)pe, vmax_r,
-                            vmax_e, c->d_hard, c->d_soft);
+    e = launch_grid_prepare(c->stream, n, d->n[0], d->n[1], (const float*)pr, (const float*)pa, (const float*)pe,
+                            vmax_r, vmax_e, c->d_hard, c->d_soft);
   if (or_ || oa || oe) {
     cudaError_t e2 = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) e = e2;

@@ -76,11 +76,13 @@ __global__ void __launch_bounds__(kBuildThreads) grid_build_kernel(int nx, int n
 }
 
 // Derived lattices, computed in FP64 and rounded once to FP32.
-// Node p's values go into its own x-pair record (first half) and into the record of its x - 1
-// neighbour in the same row (second half); the record of a row's last node gets a zero second half.
-__global__ void grid_prepare_kernel(int64_t n, int nx, const float* __restrict__ ljr, const float* __restrict__ lja,
-                                    const float* __restrict__ elec, double vmax_r, double vmax_e, float4* hard,
-                                    float4* soft) {
+// Node p's hard values go into its own x-pair record (first half) and into the record of its x - 1
+// neighbour in the same row (second half); its soft values go into the (x, y) quad records of
+// itself and of its x - 1, y - 1 and (x - 1, y - 1) neighbours in the same plane.  Halves that
+// would hold a node past the last one of a row or column are zero (no cell starts there).
+__global__ void grid_prepare_kernel(int64_t n, int nx, int ny, const float* __restrict__ ljr,
+                                    const float* __restrict__ lja, const float* __restrict__ elec, double vmax_r,
+                                    double vmax_e, float4* hard, float4* soft) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   double v = (double)ljr[p];
@@ -92,18 +94,18 @@ __global__ void grid_prepare_kernel(int64_t n, int nx, const float* __restrict__
   const double soft_e = isinf(vmax_e) ? e : vmax_e * tanh(e / vmax_e);
   const float4 h = make_float4((float)root, lja[p], elec[p], 0.f);
   const float2 sf = make_float2((float)soft_r, (float)soft_e);
-  float2* soft2 = (float2*)soft;
-  const int x = (int)(p % nx);
+  const int x = (int)(p % nx), y = (int)((p / nx) % ny);
   hard[2 * p] = h;
-  soft2[2 * p] = sf;
-  if (x > 0) {
-    hard[2 * (p - 1) + 1] = h;
-    soft2[2 * (p - 1) + 1] = sf;
-  }
-  if (x == nx - 1) {
-    hard[2 * p + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    soft2[2 * p + 1] = make_float2(0.f, 0.f);
-  }
+  if (x > 0) hard[2 * (p - 1) + 1] = h;
+  if (x == nx - 1) hard[2 * p + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  float2* q = (float2*)soft;  // 4 float2 per record: nodes (x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1)
+  const float2 zero = make_float2(0.f, 0.f);
+  q[4 * p] = sf;
+  if (x > 0) q[4 * (p - 1) + 1] = sf;
+  if (y > 0) q[4 * (p - nx) + 2] = sf;
+  if (x > 0 && y > 0) q[4 * (p - nx - 1) + 3] = sf;
+  if (x == nx - 1) q[4 * p + 1] = q[4 * p + 3] = zero;
+  if (y == ny - 1) q[4 * p + 2] = q[4 * p + 3] = zero;
 }
 
 // Peak rate of the interpolation's gathers, for the gather roofline (not a step of the method):
@@ -133,8 +135,8 @@ __global__ void __launch_bounds__(256) gather_probe_kernel(const float4* __restr
     const int cx = below(xorshift32(st), nx - 1), cy = below(xorshift32(st), ny - 1),
               cz = below(xorshift32(st), nz - 1);
     const int64_t b = cz * sz + cy * sy + cx;
-    // the cell's x-pair records, as the interpolation reads them: four 32-byte hard records and
-    // (with SOFT) four 16-byte soft records
+    // the cell's records, as the interpolation reads them: four 32-byte hard x-pair records and
+    // (with SOFT) two 32-byte soft quad records
     float4 h0, h1, h2, h3, h4, h5, h6, h7;
     ldg_pair(hard + 2 * b, h0, h1);
     ldg_pair(hard + 2 * (b + sy), h2, h3);
@@ -142,8 +144,9 @@ __global__ void __launch_bounds__(256) gather_probe_kernel(const float4* __restr
     ldg_pair(hard + 2 * (b + sz + sy), h6, h7);
     acc += ((h0.x + h1.y) + (h2.z + h3.x)) + ((h4.y + h5.z) + (h6.x + h7.y));
     if (SOFT) {
-      const float4 s0 = __ldg(soft + b), s1 = __ldg(soft + b + sy), s2 = __ldg(soft + b + sz),
-                   s3 = __ldg(soft + b + sz + sy);
+      float4 s0, s1, s2, s3;
+      ldg_pair(soft + 2 * b, s0, s1);
+      ldg_pair(soft + 2 * (b + sz), s2, s3);
       acc += ((s0.x + s1.w) + (s2.x + s3.w)) + ((s0.z + s1.y) + (s2.z + s3.y));
     }
   }
@@ -187,12 +190,12 @@ cudaError_t launch_grid_build(cudaStream_t s, const algdock_grid_desc& d, int n_
   return e;
 }
 
-cudaError_t launch_grid_prepare(cudaStream_t s, size_t n_nodes, int nx, const float* ljr, const float* lja,
+cudaError_t launch_grid_prepare(cudaStream_t s, size_t n_nodes, int nx, int ny, const float* ljr, const float* lja,
                                 const float* elec, double vmax_r, double vmax_e, float4* hard, float4* soft) {
   const int threads = 256;
   const size_t blocks = (n_nodes + threads - 1) / threads;
-  grid_prepare_kernel<<<(unsigned)blocks, threads, 0, s>>>((int64_t)n_nodes, nx, ljr, lja, elec, vmax_r, vmax_e,
-                                                            hard, soft);
+  grid_prepare_kernel<<<(unsigned)blocks, threads, 0, s>>>((int64_t)n_nodes, nx, ny, ljr, lja, elec, vmax_r,
+                                                            vmax_e, hard, soft);
   return cudaGetLastError();
 }
 

@@ -195,9 +195,10 @@ __device__ inline GridOut grid_atom(const GridDev& G, float x, float y, float z,
       gz2 = fma2(kra, ra.gz, mul2(ke, e0.gz));
     }
   }
-  if (soft) {  // four 16-byte x-pair records
-    const float4 e00 = __ldg(G.soft + b), e01 = __ldg(G.soft + b + sy);
-    const float4 e10 = __ldg(G.soft + b + sz), e11 = __ldg(G.soft + b + sz + sy);
+  if (soft) {  // two (x, y) quad records: the corners of the cell's lower and upper z face
+    float4 e00, e01, e10, e11;
+    ldg_pair(G.soft + 2 * b, e00, e01);
+    ldg_pair(G.soft + 2 * (b + sz), e10, e11);
     const Tri2 re = tri2(lo2(e00), hi2(e00), lo2(e01), hi2(e01), lo2(e10), hi2(e10), lo2(e11), hi2(e11), tx2, ty2, tz2);
     float rv, ev;
     unpack2(re.v, rv, ev);

@@ -99,21 +99,22 @@ __host__ __device__ inline double uniform53(uint32_t a, uint32_t b) {
 }
 
 // ------------------------------------------------------------------ device-side tables
-// Interpolation lattices, stored as x-pair records so that the two corners of a cell edge along x
-// come in one load.  Record b = (z ny + y) nx + x holds nodes x and x + 1 of row (y, z):
-//   hard: 2 float4 per record (32 bytes), (LJr^(1/4), LJa, elec, 0) of node x, then of node x + 1;
-//   soft: 1 float4 per record (16 bytes), (sLJr^(1/4), selec) of node x, then of node x + 1.
-// The record of the last node of a row has a zero second half (a cell never starts there).
+// Interpolation lattices, stored as records of neighbouring nodes so that a cell's corners come in
+// few loads.  Record b = (z ny + y) nx + x:
+//   hard: an x-pair, 2 float4 (32 bytes): (LJr^(1/4), LJa, elec, 0) of nodes x and x + 1 of row (y, z);
+//   soft: an (x, y) quad, 2 float4 (32 bytes): (sLJr^(1/4), selec) of nodes (x, y), (x + 1, y),
+//         (x, y + 1), (x + 1, y + 1) of plane z.
+// Parts that would hold a node past the last one of a row or column are zero (no cell starts there).
 struct GridDev {
   const float4* hard;  // [n_nodes][2]
-  const float4* soft;  // [n_nodes]
+  const float4* soft;  // [n_nodes][2]
   int nx, ny, nz;
   float ox, oy, oz;  // origin, exactly the FP32 value used by the split subtraction
   float inv_h;
 };
 
-// One 32-byte x-pair record of the hard lattice in a single 256-bit load (read-only path; the
-// record is 32-byte aligned: the lattice is a cudaMalloc allocation of whole records).
+// One 32-byte lattice record in a single 256-bit load (read-only path; the record is 32-byte
+// aligned: each lattice is a cudaMalloc allocation of whole records).
 __device__ __forceinline__ void ldg_pair(const float4* p, float4& a, float4& b) {
   asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
       : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
@@ -239,7 +240,7 @@ struct algdock_ctx {
   bool has_grid = false;
   algdock::GridDev grid{};
   float4* d_hard = nullptr;  // x-pair records, 2 float4 per node
-  float4* d_soft = nullptr;  // x-pair records, 1 float4 per node
+  float4* d_soft = nullptr;  // (x, y) quad records, 2 float4 per node
   size_t grid_nodes = 0;
   // ligand
   bool has_ligand = false;
@@ -330,7 +331,7 @@ uint32_t crc32_update(uint32_t crc, const void* data, size_t n);
 cudaError_t launch_grid_build(cudaStream_t s, const algdock_grid_desc& d, int n_rec, const double* xyz,
                               const double* rstar, const double* eps, const double* q, float* ljr, float* lja,
                               float* elec);
-cudaError_t launch_grid_prepare(cudaStream_t s, size_t n_nodes, int nx, const float* ljr, const float* lja,
+cudaError_t launch_grid_prepare(cudaStream_t s, size_t n_nodes, int nx, int ny, const float* ljr, const float* lja,
                                 const float* elec, double vmax_r, double vmax_e, float4* hard, float4* soft);
 cudaError_t launch_gather_probe(cudaStream_t s, const algdock_ctx& c, int64_t n_cells, bool soft, uint32_t seed,
                                 float* sink);
