@@ -260,6 +260,29 @@ def measured_peaks():
         return {}
 
 
+# DRAM bytes (read + write) per launch of a kernel from one ncu capture of the bench command, with
+# a fingerprint of the sources the kernel was built from at the time: the figure is reported only
+# while those sources are unchanged.
+NCU_TRAFFIC = {
+    "hmc_kernel": {"bytes_per_launch": 16074752,
+                   "sources": ("hmc.cu", "internal.cuh", "grids.cu"),
+                   "sha256": "9c800e00104d1317d2490035a966a109c366bb546c01a5bf46a72dc3acfece39"},
+}
+
+
+def captured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from its ncu capture, or None if its sources changed."""
+    import hashlib
+    rec = NCU_TRAFFIC.get(kernel)
+    if rec is None:
+        return None
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        with open(os.path.join(ROOT, "paper_1507_03703_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes_per_launch"] if h.hexdigest() == rec["sha256"] else None
+
+
 def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=489, train_iter=500, cmp_cycles=200,
                      n_moves=4, lag=1, mixed=True, seed=7, target=N_STATES_BC, n_torsions=-1):
     """Effective samples per second at one state of plain HMC and of HMC plus learned proposals,
@@ -938,7 +961,7 @@ def main():
     hmc_avg = sum(hmc_ms) / len(hmc_ms)
     achieved = fl / (hmc_avg * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
+                "frac": achieved / peak_tflops, "traffic": captured_traffic("hmc_kernel"),
                 "traffic_ncu_summary": "profiles/hmc_kernel_paper_scale.md",
                 "kernel": "hmc_kernel", "kernel_ms": hmc_avg,
                 "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % (n_sm, sm_max),
