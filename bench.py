@@ -266,7 +266,7 @@ def measured_peaks():
 NCU_TRAFFIC = {
     "hmc_kernel": {"bytes_per_launch": 16074752,
                    "sources": ("hmc.cu", "internal.cuh", "grids.cu"),
-                   "sha256": "9c800e00104d1317d2490035a966a109c366bb546c01a5bf46a72dc3acfece39"},
+                   "sha256": "dcc1b0b45b31b10d1263c3809cff2bf2ece1c3b356589f45a28a79f473b80a93"},
 }
 
 

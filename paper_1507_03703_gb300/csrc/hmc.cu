@@ -106,34 +106,16 @@ __device__ inline void axis_coord(float x, float o, float inv_h, int n, int& c, 
   t = frac;
 }
 
-// Trilinear value and gradient (in lattice units) of one channel from 8 corner values c_zyx.
-struct Tri {
-  float v, gx, gy, gz;
-};
-__device__ inline Tri tri(const float c000, const float c001, const float c010, const float c011, const float c100,
-                          const float c101, const float c110, const float c111, float tx, float ty, float tz) {
-  const float a00 = fmaf(tx, c001 - c000, c000), d00 = c001 - c000;
-  const float a01 = fmaf(tx, c011 - c010, c010), d01 = c011 - c010;
-  const float a10 = fmaf(tx, c101 - c100, c100), d10 = c101 - c100;
-  const float a11 = fmaf(tx, c111 - c110, c110), d11 = c111 - c110;
-  const float b0 = fmaf(ty, a01 - a00, a00), bx0 = fmaf(ty, d01 - d00, d00), by0 = a01 - a00;
-  const float b1 = fmaf(ty, a11 - a10, a10), bx1 = fmaf(ty, d11 - d10, d10), by1 = a11 - a10;
-  Tri r;
-  r.v = fmaf(tz, b1 - b0, b0);
-  r.gx = fmaf(tz, bx1 - bx0, bx0);
-  r.gy = fmaf(tz, by1 - by0, by0);
-  r.gz = b1 - b0;
-  return r;
-}
-
 struct GridOut {
   float e_g, e_sg;   // Psi_g, Psi_sg contributions of this atom
   float fx, fy, fz;  // -(w_sg dPsi_sg + w_g dPsi_g)/dx
   bool outside;
 };
 
-// tri() for two channels at once (paired FP32 instructions): per channel the same operations in
-// the same order, so each half equals the scalar result bit for bit.
+// Trilinear value and gradient (in lattice units) of two channels at once from the 8 corner values
+// c_zyx, in paired FP32 instructions: per channel, the edge differences along x and the values
+// interpolated along x, then along y (with the y and x gradients), then along z.  Each half
+// performs the operations of the one-channel interpolant in the same order.
 struct Tri2 {
   f32x2 v, gx, gy, gz;
 };
