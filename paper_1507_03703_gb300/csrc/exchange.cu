@@ -137,7 +137,32 @@ __host__ __device__ inline size_t fast_smem_bytes(int K, int n_sweeps, int max_s
          (size_t)K * 2 * sizeof(float4) +                             // FP32 state factors, centred slots
          (size_t)K * K * sizeof(float2) +                             // shifted u and its magnitude bound
          (size_t)n_sweeps * (smax > 0 ? smax : 1) * K * sizeof(float) +  // log-uniforms
-         (size_t)max_sep * K * sizeof(unsigned);                      // accept counters
+         (size_t)max_sep * K * sizeof(unsigned) +                     // accept counters
+         (size_t)2 * kFastMaxK * sizeof(int);                         // the team sweep's slot buffers
+}
+
+// The fast kernels' shared memory.
+struct FastTables {
+  double* st;     // [K][3]: beta, w_sg, w_g
+  SlotE* slot;    // [K]
+  float4* w;      // [K]: beta, beta w_sg, beta w_g
+  float4* d;      // [K]: centred slot components
+  float2* fm;     // [K][K]: v_k(x_i), m_k(x_i)
+  float* lu;      // [n_sweeps][smax][K]
+  unsigned* acc;  // [max_sep][K]
+  int* cbuf;      // [2][kFastMaxK]: configurations published by the team sweep, by phase parity
+};
+__device__ inline FastTables fast_carve(unsigned char* smem, int K, int n_sweeps, int sm1, int max_sep) {
+  FastTables T;
+  T.st = (double*)smem;
+  T.slot = (SlotE*)(T.st + 3 * K);
+  T.w = (float4*)(T.slot + K);
+  T.d = T.w + K;
+  T.fm = (float2*)(T.d + K);
+  T.lu = (float*)(T.fm + (size_t)K * K);
+  T.acc = (unsigned*)(T.lu + (size_t)n_sweeps * sm1 * K);
+  T.cbuf = (int*)(T.acc + (size_t)max_sep * K);
+  return T;
 }
 
 // The FP64 test of one attempt (pair a, a + s of sweep sw; configurations x at a and y at a + s),
@@ -172,31 +197,19 @@ __device__ __noinline__ bool exact_swap(const ExArgs& A, const double* s_st, con
 // Both members read their partner's configuration by a shuffle, their own row's entry at it, and
 // the partner's partial sum by a second shuffle; the two partial sums are added in either order
 // (FP32 addition commutes), so both members take the same decision and update their own register.
-template <int KG>
-__global__ void __launch_bounds__(kFastThreads) exchange_fast_kernel(const ExArgs A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int K = A.K;
-  const int smax = min(A.max_sep, K - 1);
-  const int sm1 = smax > 0 ? smax : 1;
-  double* s_st = (double*)smem_raw;                                    // [K][3]: beta, w_sg, w_g
-  SlotE* s_slot = (SlotE*)(s_st + 3 * K);                              // [K]
-  float4* s_w = (float4*)(s_slot + K);                                 // [K]: beta, beta w_sg, beta w_g
-  float4* s_d = s_w + K;                                               // [K]: centred slot components
-  float2* s_fm = (float2*)(s_d + K);                                   // [K][K]: v_k(x_i), m_k(x_i)
-  float* s_lu = (float*)(s_fm + (size_t)K * K);                        // [n_sweeps][smax][K]
-  unsigned* s_acc = (unsigned*)(s_lu + (size_t)A.n_sweeps * sm1 * K);  // [max_sep][K]
+// The tables of one ladder, by all threads of the block (ends with a block barrier).
+__device__ inline void fast_tables(const ExArgs& A, const FastTables& T, int K, int smax, uint32_t lid) {
   const int64_t l = blockIdx.x;
-  const uint32_t lid = (uint32_t)(A.ladder_offset + l);
   const int lane = threadIdx.x & 31;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     const StateDev st = A.states[A.state_offset + k];
-    s_st[3 * k] = st.beta;
-    s_st[3 * k + 1] = st.w_sg;
-    s_st[3 * k + 2] = st.w_g;
-    s_w[k] = make_float4((float)st.beta, (float)(st.beta * st.w_sg), (float)(st.beta * st.w_g), 0.f);
-    s_slot[k] = load_slot(A.comps + (l * K + k) * 4);
+    T.st[3 * k] = st.beta;
+    T.st[3 * k + 1] = st.w_sg;
+    T.st[3 * k + 2] = st.w_g;
+    T.w[k] = make_float4((float)st.beta, (float)(st.beta * st.w_sg), (float)(st.beta * st.w_g), 0.f);
+    T.slot[k] = load_slot(A.comps + (l * K + k) * 4);
   }
-  for (int i = threadIdx.x; i < A.max_sep * K; i += blockDim.x) s_acc[i] = 0u;
+  for (int i = threadIdx.x; i < A.max_sep * K; i += blockDim.x) T.acc[i] = 0u;
   const int n_att = A.n_sweeps * smax * K;
   for (int idx = threadIdx.x; idx < n_att; idx += blockDim.x) {
     const int a = idx % K, ss = idx / K;
@@ -209,15 +222,15 @@ __global__ void __launch_bounds__(kFastThreads) exchange_fast_kernel(const ExArg
       const float uf = __fmaf_rn((float)(o.x >> 5), 7.450580596923828125e-9f, (float)(o.y >> 6) * 1.1102230246251565e-16f);
       lu = uf == 0.f ? -INFINITY : __logf(uf);
     }
-    s_lu[idx] = lu;
+    T.lu[idx] = lu;
   }
   __syncthreads();
   {  // every warp forms the minima (fmin skips NaN; a non-finite slot only sends its pairs to FP64)
     double me = INFINITY, msg = INFINITY, mg = INFINITY;
     for (int i = lane; i < K; i += 32) {
-      me = fmin(me, s_slot[i].e);
-      msg = fmin(msg, s_slot[i].psg);
-      mg = fmin(mg, s_slot[i].pg);
+      me = fmin(me, T.slot[i].e);
+      msg = fmin(msg, T.slot[i].psg);
+      mg = fmin(mg, T.slot[i].pg);
     }
     for (int o = 16; o > 0; o >>= 1) {
       me = fmin(me, __shfl_xor_sync(kFull, me, o));
@@ -225,16 +238,34 @@ __global__ void __launch_bounds__(kFastThreads) exchange_fast_kernel(const ExArg
       mg = fmin(mg, __shfl_xor_sync(kFull, mg, o));
     }
     for (int i = threadIdx.x; i < K; i += blockDim.x)
-      s_d[i] = make_float4((float)(s_slot[i].e - me), (float)(s_slot[i].psg - msg), (float)(s_slot[i].pg - mg), 0.f);
+      T.d[i] = make_float4((float)(T.slot[i].e - me), (float)(T.slot[i].psg - msg), (float)(T.slot[i].pg - mg), 0.f);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int k = e / K, i = e - k * K;
-    const float4 w = s_w[k], d = s_d[i];
+    const float4 w = T.w[k], d = T.d[i];
     const float t0 = w.x * d.x, t1 = w.y * d.y, t2 = w.z * d.z;
-    s_fm[e] = make_float2((t0 + t1) + t2, (fabsf(t0) + fabsf(t1)) + fabsf(t2));
+    T.fm[e] = make_float2((t0 + t1) + t2, (fabsf(t0) + fabsf(t1)) + fabsf(t2));
   }
   __syncthreads();
+}
+
+template <int KG>
+__global__ void __launch_bounds__(kFastThreads) exchange_fast_kernel(const ExArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = A.K;
+  const int smax = min(A.max_sep, K - 1);
+  const int sm1 = smax > 0 ? smax : 1;
+  const FastTables T = fast_carve(smem_raw, K, A.n_sweeps, sm1, A.max_sep);
+  const double* s_st = T.st;
+  const SlotE* s_slot = T.slot;
+  const float2* s_fm = T.fm;
+  const float* s_lu = T.lu;
+  unsigned* s_acc = T.acc;
+  const int64_t l = blockIdx.x;
+  const uint32_t lid = (uint32_t)(A.ladder_offset + l);
+  const int lane = threadIdx.x & 31;
+  fast_tables(A, T, K, smax, lid);
   if (threadIdx.x >= 32) return;
   int cfg[KG];
   float uo[KG], mo[KG];  // the entry of the slot's own state at its own configuration
@@ -357,6 +388,97 @@ __global__ void __launch_bounds__(kFastThreads) exchange_fast_kernel(const ExArg
   }
 }
 
+// The sweeps of a ladder of more than 32 states by a team of KG warps, warp w holding slot
+// k = 32 w + lane in one register.  The roles, table entries and decisions are those of the
+// single-warp sweep; what differs is how a member learns its partner's configuration: at every
+// phase each warp publishes its slots' configurations to one of two shared-memory buffers
+// (alternating by phase parity), the team meets at a named barrier, and each member reads its
+// partner's entry.  A warp can reach the next phase's write only after every warp has passed the
+// barrier of the current one, so the buffer it writes is no longer read.  Every team warp runs the
+// same block-uniform loops with one barrier per phase, and none leaves before the end.
+constexpr int kTeamBarrier = 1;
+template <int KG>
+__global__ void __launch_bounds__(kFastThreads) exchange_team_kernel(const ExArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = A.K;
+  const int smax = min(A.max_sep, K - 1);
+  const int sm1 = smax > 0 ? smax : 1;
+  const FastTables T = fast_carve(smem_raw, K, A.n_sweeps, sm1, A.max_sep);
+  const int64_t l = blockIdx.x;
+  const uint32_t lid = (uint32_t)(A.ladder_offset + l);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  fast_tables(A, T, K, smax, lid);
+  const int k = 32 * warp + lane;
+  int cfg = warp < KG && k < K ? A.config_of[l * K + k] : 0;
+  const bool bad = warp < KG && k < K && (unsigned)cfg >= (unsigned)K;
+  // not a list of slots 0..K-1: every thread leaves, the ladder untouched
+  if (__syncthreads_or(bad)) return;
+  if (warp >= KG) return;
+  const float2 own0 = T.fm[(k < K ? k : 0) * K + cfg];
+  float uo = own0.x, mo = own0.y;
+  // the slot's role in every phase: bit 2 (s - 1) + colour of `lower` / `active`
+  uint32_t lower_bits = 0, active_bits = 0;
+  for (int s = 1; s <= smax; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      const bool own = (k / s) % 2 == colour;
+      const bool lo = own && k + s < K, hi = !own && k >= s && k < K;
+      lower_bits |= (uint32_t)lo << (2 * (s - 1) + colour);
+      active_bits |= (uint32_t)(lo || hi) << (2 * (s - 1) + colour);
+    }
+  int phase = 0;
+  for (int sw = 0; sw < A.n_sweeps; ++sw) {
+    const float* lu_sw = T.lu + (size_t)sw * smax * K;
+    uint32_t acc_bits = 0;  // bit s - 1: the pair whose lower member is this slot was accepted
+    for (int s = 1; s <= smax; ++s) {
+      const float* lu_s = lu_sw + (s - 1) * K;
+#pragma unroll
+      for (int colour = 0; colour < 2; ++colour, ++phase) {
+        int* buf = T.cbuf + (phase & 1) * kFastMaxK;
+        buf[k] = cfg;
+        asm volatile("bar.sync %0, %1;" ::"r"(kTeamBarrier), "r"(32 * KG) : "memory");
+        const int ph = 2 * (s - 1) + colour;
+        const bool act = (active_bits >> ph) & 1u;
+        const bool lo = (lower_bits >> ph) & 1u;
+        const int pslot = lo ? k + s : k - s;
+        const int pc = act ? buf[pslot] : 0;
+        const int ks = act ? k : 0, ps = act ? pslot : 0, own = act ? cfg : 0;
+        const float2 f_kp = T.fm[ks * K + pc];   // own state at the partner's configuration
+        const float2 f_po = T.fm[ps * K + own];  // partner's state at this configuration
+        const float2 f_pp = T.fm[ps * K + pc];   // partner's state at its own configuration
+        const int a = lo ? k : k - s;
+        const float lu = lu_s[act ? a : 0];
+        const float df = (f_kp.x - uo) + (f_po.x - f_pp.x);
+        const float band = 1e-4f + 1e-6f * ((f_kp.y + mo) + (f_po.y + f_pp.y));
+        const bool sure_acc = lu != -INFINITY && lu < -df - band;
+        const bool sure_rej = lu != -INFINITY && lu > -df + band;
+        bool acc = sure_acc;
+        if (act && !sure_acc && !sure_rej)  // close to the boundary, or not finite: the FP64 test itself
+          acc = exact_swap(A, T.st, T.slot, lid, sw, s, a, lo ? own : pc, lo ? pc : own);
+        const bool take = acc && act;
+        cfg = take ? pc : cfg;
+        uo = take ? f_kp.x : uo;
+        mo = take ? f_kp.y : mo;
+        acc_bits |= (uint32_t)(take && lo) << (s - 1);
+      }
+    }
+    while (acc_bits) {  // this sweep's accepts of the pairs this slot leads
+      const int bit = __ffs(acc_bits) - 1;
+      acc_bits &= acc_bits - 1;
+      T.acc[bit * K + k] += 1u;
+    }
+  }
+  if (k < K) {
+    A.config_of[l * K + k] = cfg;
+    if (A.state_of) A.state_of[l * K + cfg] = A.state_offset + k;
+    for (int s = 1; s <= A.max_sep; ++s) {
+      const int i = (s - 1) * K + k;
+      if (A.attempts && s <= smax && k + s < K)
+        atomicAdd((unsigned long long*)&A.attempts[i], (unsigned long long)A.n_sweeps);
+      if (A.accepts && T.acc[i]) atomicAdd((unsigned long long*)&A.accepts[i], (unsigned long long)T.acc[i]);
+    }
+  }
+}
+
 // One ladder per block: all warps fill u[k][i], warp 0 sweeps.
 __global__ void __launch_bounds__(kExMaxWarps * 32) exchange_matrix_kernel(const ExArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -429,9 +551,9 @@ cudaError_t launch_exchange(cudaStream_t s, const algdock_ctx& c, int n_ladders,
   if (K <= kFastMaxK && max_sep <= 8 && fast <= kFastSmemMax) {
     const int kg = (K + 31) / 32;
     void (*fn)(ExArgs) = kg == 1   ? exchange_fast_kernel<1>
-                         : kg == 2 ? exchange_fast_kernel<2>
-                         : kg == 3 ? exchange_fast_kernel<3>
-                                   : exchange_fast_kernel<4>;
+                         : kg == 2 ? exchange_team_kernel<2>
+                         : kg == 3 ? exchange_team_kernel<3>
+                                   : exchange_team_kernel<4>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast);
     if (e != cudaSuccess) return e;
     fn<<<n_ladders, kFastThreads, fast, s>>>(A);
