@@ -190,14 +190,7 @@ __device__ __noinline__ bool exact_swap(const ExArgs& A, const double* s_st, con
 // entries within 7 2^-24 of the sum of their m.  With the FP32 log-uniform (error below 2e-5) a
 // decision is taken from the estimate when its margin to the boundary ln u = -d exceeds
 // 1e-4 + 1e-6 sum(m); otherwise from the FP64 test itself, so every decision is the FP64 one.
-//
-// Warp 0 sweeps with the ladder's configuration in registers: slot k = 32 g + lane in register g.
-// In the phase (s, colour) a slot k is the lower member a of a pair when floor(k/s) has the
-// colour's parity and k + s < K, the upper member b when it has the other parity and k >= s.
-// Both members read their partner's configuration by a shuffle, their own row's entry at it, and
-// the partner's partial sum by a second shuffle; the two partial sums are added in either order
-// (FP32 addition commutes), so both members take the same decision and update their own register.
-// The tables of one ladder, by all threads of the block (ends with a block barrier).
+// The tables of one ladder are built by all threads of the block (ends with a block barrier).
 __device__ inline void fast_tables(const ExArgs& A, const FastTables& T, int K, int smax, uint32_t lid) {
   const int64_t l = blockIdx.x;
   const int lane = threadIdx.x & 31;
@@ -250,6 +243,13 @@ __device__ inline void fast_tables(const ExArgs& A, const FastTables& T, int K, 
   __syncthreads();
 }
 
+// Ladders of up to 32 states: warp 0 sweeps with the ladder's configuration in registers, slot
+// k = 32 g + lane in register g.  In the phase (s, colour) a slot k is the lower member a of a
+// pair when floor(k/s) has the colour's parity and k + s < K, the upper member b when it has the
+// other parity and k >= s.  Each member reads its partner's configuration by a shuffle, then its
+// own row's entry at that configuration and the partner's row at both configurations, so both
+// members form d from the same four entries (FP32 addition commutes), take the same decision and
+// update their own register.
 template <int KG>
 __global__ void __launch_bounds__(kFastThreads) exchange_fast_kernel(const ExArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
