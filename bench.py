@@ -987,7 +987,11 @@ def main():
     h_s = run.state_of.cpu().pin_memory()
     h_cfg = torch.cat(run.config_of).cpu().pin_memory()
     u_all = torch.empty(sum(l.K * N_CHAINS * l.K for l in legs), dtype=torch.float64, device=dev)
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = max(2, min(args.steps, 10))
+    # one untimed call first: the context allocates its staging buffer and side stream on the first
+    # call with host arrays
+    ctx.cycle(legs_desc, N_CHAINS, 9_999, h_x, h_c, h_s, h_cfg, n_steps=N_VV, seed=run.seed,
+              rep_offset=run.rep_offset, ladder_offset=run.ladder_offset, counters=run.counters, u_kn=u_all)
     torch.cuda.synchronize()
     es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     es.record(stream)
@@ -1002,7 +1006,7 @@ def main():
            "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes, "call": "algdock_cycle, pinned host arrays"}
 
     acc = run.counters.cpu().numpy()
-    n_trials = R * (args.warmup + args.steps + e2e_steps)  # the counters include the e2e steps
+    n_trials = R * (args.warmup + args.steps + e2e_steps + 1)  # the counters include the e2e steps
     extra = {}
     if not args.no_mbar and rank == 0:
         # MBAR over K = 128 states and ~1e5 samples recorded from the run

@@ -1575,8 +1575,13 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
   }
   // the snapshot reads only the components of the configurations, which the exchange does not
   // move, so it runs on a side stream beside the exchange sweeps
+  // the positions and components are final once the trial and the moves are done (the exchange
+  // permutes states, not configurations): host copies of them go back on the side stream too,
+  // beside the sweeps
+  const bool early_out = P[0].host || P[1].host;
+  const bool side = u_kn || early_out;
   cudaStream_t snap_s = c->stream;
-  if (e == cudaSuccess && u_kn) {
+  if (e == cudaSuccess && side) {
     if (!c->cycle_side) e = cudaStreamCreateWithFlags(&c->cycle_side, cudaStreamNonBlocking);
     if (e == cudaSuccess && !c->cycle_fork) e = cudaEventCreateWithFlags(&c->cycle_fork, cudaEventDisableTiming);
     if (e == cudaSuccess && !c->cycle_join) e = cudaEventCreateWithFlags(&c->cycle_join, cudaEventDisableTiming);
@@ -1596,8 +1601,10 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
       base += n;
       ubase += (int64_t)d->K[l] * n;
     }
-    if (e == cudaSuccess) e = cudaEventRecord(c->cycle_join, snap_s);
   }
+  for (int i = 0; i < 2 && e == cudaSuccess && side; ++i)
+    if (P[i].host && P[i].user) e = cudaMemcpyAsync(P[i].user, dev_of(i), P[i].bytes, cudaMemcpyDeviceToHost, snap_s);
+  if (e == cudaSuccess && side) e = cudaEventRecord(c->cycle_join, snap_s);
   base = 0;
   NvtxRange rx("algdock_cycle: exchange");
   for (int l = 0; l < d->n_legs && e == cudaSuccess; ++l) {
@@ -1607,14 +1614,14 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
     base += (int64_t)d->n_chains * d->K[l];
     cbase += (int64_t)d->n_chains * d->K[l];
   }
-  if (e == cudaSuccess && u_kn) e = cudaStreamWaitEvent(c->stream, c->cycle_join, 0);
+  if (e == cudaSuccess && side) e = cudaStreamWaitEvent(c->stream, c->cycle_join, 0);
   const bool checks = c->params.checks != 0;
   if (e == cudaSuccess && checks) {
     e = launch_run_check(c->stream, *c, *d, dx, dc, ds, dcfg, check_word(c));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(c->h_flag, check_word(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   }
-  for (int i = 0; i < kPieces && e == cudaSuccess; ++i)
+  for (int i = side ? 2 : 0; i < kPieces && e == cudaSuccess; ++i)
     if (P[i].host && P[i].user) e = cudaMemcpyAsync(P[i].user, dev_of(i), P[i].bytes, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && (any_host || checks)) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cycle");
