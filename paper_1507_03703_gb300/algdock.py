@@ -779,6 +779,13 @@ class Context:
         """algdock_replicas_load; returns the stored next cycle."""
         nxt = C.c_uint64()
         self._check(self._L.algdock_replicas_load(self.h, str(path).encode(), C.byref(nxt)))
+        # the layout the context restored: n_legs, n_chains, rep_offset, ladder_offset, K[], offsets[]
+        _, count = checkpoint_query(None, path, ["replicas.layout"])["replicas.layout"]
+        w = np.zeros(count, dtype=np.int64)
+        checkpoint_load(None, path, {"replicas.layout": w})
+        n_legs = int(w[0])
+        self._replica_chains = int(w[1])
+        self._replica_legs = [(int(w[4 + l]), int(w[4 + n_legs + l])) for l in range(n_legs)]
         return nxt.value
 
     def gemm_bf16(self, A, B, C, epilogue=0, bias=None, mask=None, n_split=1):

@@ -112,6 +112,7 @@ def test_replicas_resume_from_checkpoint_is_bit_identical(small, tmp_path):
     b, _ = _ctx(small, seed=1, n_steps=10, n_sweeps=6)  # another seed: the checkpoint's is restored
     assert b.replicas_load(path) == 3
     assert b.params()["seed"] == 4242
+    assert b.ukn_words() == a.ukn_words()
     b.run(4, first_cycle=3)
     got = _get(b, R, na)
     for k in want:
