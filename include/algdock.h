@@ -6,9 +6,11 @@
  * Paper: D. D. L. Minh, "Alchemical Grid Dock (AlGDock): Binding Free Energy Calculations between
  * Flexible Ligands and Rigid Receptors", arXiv:1507.03703.
  *
- * Call groups, in the order below: lifecycle; grids; the all-FP64 evaluation path and the gather
- * probe; ligand and states; sampling (HMC trial, external-coordinate moves, forces and energies,
- * replica exchange); estimation (u_kn, MBAR, equilibration detection); protocol initialization;
+ * Call groups, in the order below: lifecycle (with the method's adjustable arguments); grids; the
+ * all-FP64 evaluation path and the gather probe; ligand and states; sampling (HMC trial,
+ * external-coordinate moves, forces and energies, replica exchange, one whole cycle); the
+ * context's own run (replicas held by the context); estimation (u_kn, MBAR, equilibration
+ * detection); protocol initialization;
  * multi-ligand batches; the end points (target force field and free energy perturbation); the
  * learned pose proposal; checkpoint and resume; the allocation-free MBAR.
  *
