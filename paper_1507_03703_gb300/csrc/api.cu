@@ -136,6 +136,184 @@ double sqrtA(double rstar, double eps) {
   return sqrt(eps) * (t * t * t * t * t * t);
 }
 
+// SplitMix64 (Steele, Lea and Flood, 2014): the deterministic stream of the gather-layout search.
+uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+int below(uint64_t& s, int n) { return (int)(((splitmix64(s) >> 32) * (uint64_t)n) >> 32); }
+
+// Wavefronts of one quarter-warp's 16-byte shared-memory load of bonded slots: 16-byte slots fall
+// into 8 bank groups (slot mod 8), the lanes that read one slot share a wavefront, and distinct
+// slots of one group take one wavefront each.
+int wavefronts(const uint32_t* id, int n) {
+  int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0}, worst = 0;
+  for (int a = 0; a < n; ++a) {
+    bool seen = false;
+    for (int b = 0; b < a; ++b) seen = seen || id[b] == id[a];
+    if (!seen) worst = std::max(worst, ++cnt[id[a] & 7]);
+  }
+  return worst;
+}
+
+// Layout of the bonded-force gather chosen against shared-memory bank conflicts.  The kernel's lane l
+// adds the entries of run lane_run[l] of the atom-sorted slot list, so at run position j the four
+// quarter-warps each load 8 slots; the owner lanes then load the atoms' partial sums.  Three choices
+// keep every force term (only the order of the FP32 additions moves) and move the slots among the 8
+// bank groups: the order of the terms
+// of each kind (a term's slots are base + role n + position), the order of the entries within an
+// atom's block, and which lane adds which run.  A simulated annealing over swaps of each kind, with
+// integer acceptance (a worsening by d wavefronts is taken with probability 2^-(d b), b rising from 1
+// to 32, then greedy) and a fixed seed, minimises the total wavefronts; the result depends on the
+// topology only.
+struct GatherPlan {
+  int na = 0, Lr = 0, n_slots = 0, ng = 0;
+  int base[3] = {0, 0, 0}, n[3] = {0, 0, 0}, roles[3] = {2, 3, 4};
+  std::vector<int> term_at[3];  // per kind: the input term at each position
+  std::vector<uint32_t> ent;    // slot of each entry of the atom-sorted list
+  std::vector<int> pos_of;      // entry holding each slot
+  std::vector<int> blk0, blk1;  // each atom's block of entries
+  std::vector<int> atom_of;     // atom of each entry
+  std::vector<int> lane_run, run_lane;
+  std::vector<int> part_pos;    // [na][4]: entry whose slot receives the atom's k-th partial sum, or -1
+  std::vector<int> part_grp;    // per entry: the partial-sum load group that reads it, or -1
+  std::vector<int> cost;        // wavefronts per load group
+
+  int gather_group(int e) const { return (e % Lr) * 4 + run_lane[e / Lr] / 8; }
+  int group_cost(int g) const {
+    uint32_t id[8];
+    int m = 0;
+    if (g < 4 * Lr) {
+      const int j = g / 4, q = g % 4;
+      for (int l = 8 * q; l < 8 * q + 8; ++l) {
+        const int e = lane_run[l] * Lr + j;
+        id[m++] = e < n_slots ? ent[e] : (uint32_t)n_slots;
+      }
+    } else {
+      const int h = g - 4 * Lr, k = (h / 4) % 4;
+      for (int i = 32 * (h / 16) + 8 * (h % 4), i1 = i + 8; i < i1 && i < na; ++i) {
+        const int e = part_pos[4 * i + k];
+        id[m++] = e >= 0 ? ent[e] : (uint32_t)n_slots;
+      }
+    }
+    return m ? wavefronts(id, m) : 0;
+  }
+
+  void swap_entries(int e1, int e2) {
+    std::swap(ent[e1], ent[e2]);
+    pos_of[ent[e1]] = e1;
+    pos_of[ent[e2]] = e2;
+  }
+  void swap_terms(int kind, int p1, int p2) {
+    for (int r = 0; r < roles[kind]; ++r)
+      swap_entries(pos_of[base[kind] + r * n[kind] + p1], pos_of[base[kind] + r * n[kind] + p2]);
+    std::swap(term_at[kind][p1], term_at[kind][p2]);
+  }
+  void swap_lanes(int l1, int l2) {
+    std::swap(lane_run[l1], lane_run[l2]);
+    run_lane[lane_run[l1]] = l1;
+    run_lane[lane_run[l2]] = l2;
+  }
+
+  void optimise() {
+    cost.resize(ng);
+    int cur = 0, floor = 0;
+    for (int g = 0; g < ng; ++g) {
+      cost[g] = group_cost(g);
+      cur += cost[g];
+      floor += cost[g] > 0 ? 1 : 0;
+    }
+    int best = cur;
+    GatherPlan keep = *this;
+    const int terms = n[0] + n[1] + n[2];
+    const long iters = std::min<long>(200000, 300L * n_slots);
+    uint64_t rs = 0x5deece66dull ^ (uint64_t)n_slots;
+    std::vector<int> aff, fresh;
+    auto add = [&](int g) {
+      if (std::find(aff.begin(), aff.end(), g) == aff.end()) aff.push_back(g);
+    };
+    auto touch = [&](int e) {
+      add(gather_group(e));
+      if (part_grp[e] >= 0) add(part_grp[e]);
+    };
+    for (long it = 0; it < iters && best > floor; ++it) {
+      aff.clear();
+      // half of the entry and term swaps start from an entry of a conflicted gather load
+      int tgt = -1;
+      if (splitmix64(rs) & 1)
+        for (int k = 0; k < 8 && tgt < 0; ++k) {
+          const int g = below(rs, 4 * Lr);
+          const int e = lane_run[8 * (g % 4) + below(rs, 8)] * Lr + g / 4;
+          if (cost[g] > 1 && e < n_slots) tgt = e;
+        }
+      const int m = below(rs, 20);
+      int kind = -1, a1 = 0, a2 = 0;
+      if (m < 8) {  // two entries of one atom's block
+        const int i = tgt >= 0 ? atom_of[tgt] : below(rs, na);
+        const int len = blk1[i] - blk0[i];
+        if (len < 2) continue;
+        a1 = tgt >= 0 ? tgt : blk0[i] + below(rs, len);
+        a2 = blk0[i] + below(rs, len - 1);
+        if (a2 >= a1) ++a2;
+        touch(a1);
+        touch(a2);
+        swap_entries(a1, a2);
+      } else if (m < 17) {  // two terms of one kind
+        if (tgt >= 0) {
+          const int id = (int)ent[tgt];
+          kind = id < base[1] ? 0 : (id < base[2] ? 1 : 2);
+        } else {
+          const int u = below(rs, terms);
+          kind = u < n[0] ? 0 : (u < n[0] + n[1] ? 1 : 2);
+        }
+        if (n[kind] < 2) continue;
+        a1 = tgt >= 0 ? ((int)ent[tgt] - base[kind]) % n[kind] : below(rs, n[kind]);
+        a2 = below(rs, n[kind] - 1);
+        if (a2 >= a1) ++a2;
+        for (int r = 0; r < roles[kind]; ++r) {
+          touch(pos_of[base[kind] + r * n[kind] + a1]);
+          touch(pos_of[base[kind] + r * n[kind] + a2]);
+        }
+        swap_terms(kind, a1, a2);
+      } else {  // the runs of two lanes in different quarter-warps
+        kind = 3;
+        a1 = below(rs, 32);
+        a2 = 8 * ((a1 / 8 + 1 + below(rs, 3)) % 4) + below(rs, 8);
+        for (int j = 0; j < Lr; ++j) {
+          add(j * 4 + a1 / 8);
+          add(j * 4 + a2 / 8);
+        }
+        swap_lanes(a1, a2);
+      }
+      int d = 0;
+      fresh.resize(aff.size());
+      for (size_t k = 0; k < aff.size(); ++k) {
+        fresh[k] = group_cost(aff[k]);
+        d += fresh[k] - cost[aff[k]];
+      }
+      const int b = it < iters * 9 / 10 ? 1 + (int)(32 * it / iters) : 64;
+      const bool take = d <= 0 || (d * b < 64 && (splitmix64(rs) >> (64 - d * b)) == 0);
+      if (take) {
+        for (size_t k = 0; k < aff.size(); ++k) cost[aff[k]] = fresh[k];
+        cur += d;
+        if (cur < best) {
+          best = cur;
+          keep = *this;
+        }
+      } else if (kind < 0) {
+        swap_entries(a1, a2);
+      } else if (kind < 3) {
+        swap_terms(kind, a1, a2);
+      } else {
+        swap_lanes(a1, a2);
+      }
+    }
+    if (best < cur) *this = keep;
+  }
+};
+
 // Validates one ligand and its restraint and builds its device tables: the layout, the blob (atom
 // records, pair types, bonded terms, the bonded-force gather schedule, then the per-pair table) and the FP64
 // target-force-field factors of each atom.
@@ -203,8 +381,8 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
       else if (dist[j] == 3) ptype[(size_t)j * na + i] = 1;
     }
   }
-  // per-atom lists of the bonded force slots that act on it (role-major slot numbering:
-  // bond t role r -> r nb + t; angle -> 2 nb + r nang + t; torsion -> 2 nb + 3 nang + r ntor + t)
+  // per-atom lists of the bonded force slots that act on it (role-major slot numbering by term
+  // position: bond role r -> r nb + p; angle -> 2 nb + r nang + p; torsion -> 2 nb + 3 nang + r ntor + p)
   std::vector<std::vector<uint32_t>> inc(na);
   for (int t = 0; t < nb; ++t)
     for (int r = 0; r < 2; ++r) inc[L->bonds[2 * t + r]].push_back((uint32_t)(r * nb + t));
@@ -219,36 +397,66 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
   // adds its entries in order and, at the last entry of each atom within its run, stores the
   // partial sum in that entry's slot (which no other lane reads).  Lr is at least a third of the
   // largest atom's count, so that an atom's entries meet at most 4 runs: its owner then adds at
-  // most 4 partial sums, in run order.
+  // most 4 partial sums, in run order.  The term order, the entry order within each atom and the
+  // lane of each run are then chosen against shared-memory bank conflicts (GatherPlan).
   const int n_slots = 2 * nb + 3 * nang + 4 * ntor;
   if (n_slots >= 0x7fff) return fail(c, ALGDOCK_E_INVALID, who + ": too many bonded terms");
-  std::vector<uint32_t> ent;
-  std::vector<int> ent_atom;
+  GatherPlan P;
+  P.na = na;
+  P.n_slots = n_slots;
+  P.base[1] = 2 * nb;
+  P.base[2] = 2 * nb + 3 * nang;
+  P.n[0] = nb;
+  P.n[1] = nang;
+  P.n[2] = ntor;
+  for (int k = 0; k < 3; ++k)
+    for (int t = 0; t < P.n[k]; ++t) P.term_at[k].push_back(t);
+  std::vector<int>& ent_atom = P.atom_of;
   int max_inc = 0;
   for (int i = 0; i < na; ++i) {
     max_inc = std::max(max_inc, (int)inc[i].size());
+    P.blk0.push_back((int)P.ent.size());
     for (uint32_t code : inc[i]) {
-      ent.push_back(code);
+      P.ent.push_back(code);
       ent_atom.push_back(i);
     }
+    P.blk1.push_back((int)P.ent.size());
   }
   const int Lr = n_slots == 0 ? 0 : std::max((n_slots + 31) / 32, (max_inc + 2) / 3);
   const int gs_iters = (Lr + 3) / 4;
   std::vector<uint16_t> gs((size_t)gs_iters * 32 * 4, (uint16_t)n_slots);
   std::vector<uint16_t> gp((size_t)na * 4, (uint16_t)n_slots);
-  std::vector<int> n_part(na, 0);
-  for (int l = 0; l < 32 && Lr > 0; ++l)
-    for (int j = 0; j < Lr; ++j) {
-      const int e = l * Lr + j;
-      if (e >= n_slots) break;
-      const bool last = j == Lr - 1 || e + 1 == n_slots || ent_atom[e + 1] != ent_atom[e];
-      gs[((size_t)(j / 4) * 32 + l) * 4 + (j % 4)] = (uint16_t)(ent[e] | (last ? 0x8000u : 0u));
-      if (last) {
+  if (n_slots > 0) {
+    P.Lr = Lr;
+    P.pos_of.assign(n_slots + 1, -1);
+    for (int e = 0; e < n_slots; ++e) P.pos_of[P.ent[e]] = e;
+    P.part_pos.assign((size_t)na * 4, -1);
+    P.part_grp.assign(n_slots, -1);
+    std::vector<int> n_part(na, 0);
+    for (int e = 0; e < n_slots; ++e)
+      if (e % Lr == Lr - 1 || e + 1 == n_slots || ent_atom[e + 1] != ent_atom[e]) {
         const int a = ent_atom[e];
         if (n_part[a] >= 4) return fail(c, ALGDOCK_E_INVALID, who + ": gather schedule overflow");
-        gp[(size_t)a * 4 + n_part[a]++] = (uint16_t)ent[e];
+        P.part_pos[4 * a + n_part[a]] = e;
+        P.part_grp[e] = 4 * Lr + ((a / 32) * 4 + n_part[a]) * 4 + (a % 32) / 8;
+        ++n_part[a];
       }
+    P.ng = 4 * Lr + 16 * ((na + 31) / 32);
+    for (int l = 0; l < 32; ++l) {
+      P.lane_run.push_back(l);
+      P.run_lane.push_back(l);
     }
+    P.optimise();
+    for (int l = 0; l < 32; ++l)
+      for (int j = 0; j < Lr; ++j) {
+        const int e = P.lane_run[l] * Lr + j;
+        if (e >= n_slots) break;
+        const bool last = P.part_grp[e] >= 0;
+        gs[((size_t)(j / 4) * 32 + l) * 4 + (j % 4)] = (uint16_t)(P.ent[e] | (last ? 0x8000u : 0u));
+      }
+    for (int i = 0; i < 4 * na; ++i)
+      if (P.part_pos[i] >= 0) gp[i] = (uint16_t)P.ent[P.part_pos[i]];
+  }
 
   memset(&Y, 0, sizeof(Y));
   Y.na = na;
@@ -291,24 +499,28 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
     bf[Y.off_atom_b + 4 * i + 3] = (float)sqrt(kForceToAccel / m);
   }
   memcpy((uint8_t*)(blob.data() + Y.off_ptype), ptype.data(), ptype.size());
-  for (int t = 0; t < nb; ++t) {
-    bi[Y.off_bond + 4 * t + 0] = L->bonds[2 * t];
-    bi[Y.off_bond + 4 * t + 1] = L->bonds[2 * t + 1];
-    bf[Y.off_bond + 4 * t + 2] = (float)L->bond_k[t];
-    bf[Y.off_bond + 4 * t + 3] = (float)L->bond_r0[t];
+  // bonded terms at their gather-plan positions (position p holds input term P.term_at[kind][p])
+  for (int p = 0; p < nb; ++p) {
+    const int t = P.term_at[0][p];
+    bi[Y.off_bond + 4 * p + 0] = L->bonds[2 * t];
+    bi[Y.off_bond + 4 * p + 1] = L->bonds[2 * t + 1];
+    bf[Y.off_bond + 4 * p + 2] = (float)L->bond_k[t];
+    bf[Y.off_bond + 4 * p + 3] = (float)L->bond_r0[t];
   }
-  for (int t = 0; t < nang; ++t) {
-    for (int k = 0; k < 3; ++k) bi[Y.off_ang + 4 * t + k] = L->angles[3 * t + k];
-    bf[Y.off_ang + 4 * nang + 4 * t + 0] = (float)L->angle_k[t];
-    bf[Y.off_ang + 4 * nang + 4 * t + 1] = (float)L->angle_theta0[t];
+  for (int p = 0; p < nang; ++p) {
+    const int t = P.term_at[1][p];
+    for (int k = 0; k < 3; ++k) bi[Y.off_ang + 4 * p + k] = L->angles[3 * t + k];
+    bf[Y.off_ang + 4 * nang + 4 * p + 0] = (float)L->angle_k[t];
+    bf[Y.off_ang + 4 * nang + 4 * p + 1] = (float)L->angle_theta0[t];
   }
-  for (int t = 0; t < ntor; ++t) {
-    for (int k = 0; k < 4; ++k) bi[Y.off_tor + 4 * t + k] = L->torsions[4 * t + k];
+  for (int p = 0; p < ntor; ++p) {
+    const int t = P.term_at[2][p];
+    for (int k = 0; k < 4; ++k) bi[Y.off_tor + 4 * p + k] = L->torsions[4 * t + k];
     for (int n = 0; n < 3; ++n) {
       const double g = L->torsion_gamma[3 * t + n];
-      bf[Y.off_tor + 4 * ntor + 4 * t + n] = (float)(0.5 * L->torsion_V[3 * t + n]);
-      bf[Y.off_tor + 8 * ntor + 4 * t + n] = (float)cos(g);
-      bf[Y.off_tor + 12 * ntor + 4 * t + n] = (float)sin(g);
+      bf[Y.off_tor + 4 * ntor + 4 * p + n] = (float)(0.5 * L->torsion_V[3 * t + n]);
+      bf[Y.off_tor + 8 * ntor + 4 * p + n] = (float)cos(g);
+      bf[Y.off_tor + 12 * ntor + 4 * p + n] = (float)sin(g);
     }
   }
   // pair table: the 1-4 scales and the exclusions folded into 8 bytes per ordered pair,
