@@ -158,11 +158,12 @@ int wavefronts(const uint32_t* id, int n) {
   return worst;
 }
 
-// Layout of the bonded-force gather chosen against shared-memory bank conflicts.  The kernel's lane l
-// adds the entries of run lane_run[l] of the atom-sorted slot list, so at run position j the four
-// quarter-warps each load 8 slots; the owner lanes then load the atoms' partial sums.  Three choices
-// keep every force term (only the order of the FP32 additions moves) and move the slots among the 8
-// bank groups: the order of the terms
+// Layout of the bonded terms and their force gather, chosen against shared-memory bank conflicts.  In
+// each round of the bonded terms a quarter-warp loads the positions of its 8 terms' atoms, role by
+// role (16 bytes per atom); the kernel's lane l then adds the entries of run lane_run[l] of the
+// atom-sorted slot list, so at run position j the four quarter-warps each load 8 slots; the owner
+// lanes then load the atoms' partial sums.  Three choices keep every force term (only the order of
+// the FP32 additions moves) and move the loads among the 8 bank groups: the order of the terms
 // of each kind (a term's slots are base + role n + position), the order of the entries within an
 // atom's block, and which lane adds which run.  A simulated annealing over swaps of each kind, with
 // integer acceptance (a worsening by d wavefronts is taken with probability 2^-(d b), b rising from 1
@@ -179,13 +180,22 @@ struct GatherPlan {
   std::vector<int> lane_run, run_lane;
   std::vector<int> part_pos;    // [na][4]: entry whose slot receives the atom's k-th partial sum, or -1
   std::vector<int> part_grp;    // per entry: the partial-sum load group that reads it, or -1
+  std::vector<int> tatom[3];    // per kind: the atoms of each input term, roles[kind] per term
+  int toff[3] = {0, 0, 0};      // first position-load group of each kind
   std::vector<int> cost;        // wavefronts per load group
 
   int gather_group(int e) const { return (e % Lr) * 4 + run_lane[e / Lr] / 8; }
+  // the load group of the role-r positions read by the quarter-warp holding term position p
+  int term_group(int kind, int p, int r) const { return toff[kind] + ((p / 32) * roles[kind] + r) * 4 + (p % 32) / 8; }
   int group_cost(int g) const {
     uint32_t id[8];
     int m = 0;
-    if (g < 4 * Lr) {
+    if (g >= toff[0]) {  // a bonded-term round's load of one role's atom positions (16 bytes per atom)
+      const int kind = g >= toff[2] ? 2 : (g >= toff[1] ? 1 : 0);
+      const int h = g - toff[kind], q = h % 4, r = (h / 4) % roles[kind], round = h / (4 * roles[kind]);
+      for (int p = 32 * round + 8 * q; p < 32 * round + 8 * q + 8 && p < n[kind]; ++p)
+        id[m++] = (uint32_t)tatom[kind][(size_t)term_at[kind][p] * roles[kind] + r];
+    } else if (g < 4 * Lr) {
       const int j = g / 4, q = g % 4;
       for (int l = 8 * q; l < 8 * q + 8; ++l) {
         const int e = lane_run[l] * Lr + j;
@@ -240,15 +250,28 @@ struct GatherPlan {
     };
     for (long it = 0; it < iters && best > floor; ++it) {
       aff.clear();
-      // half of the entry and term swaps start from an entry of a conflicted gather load
-      int tgt = -1;
+      // half of the entry and term swaps start from a conflicted load: an entry of a gather load,
+      // or a term of a position load
+      int tgt = -1, tkind = -1, tpos = -1;
       if (splitmix64(rs) & 1)
-        for (int k = 0; k < 8 && tgt < 0; ++k) {
-          const int g = below(rs, 4 * Lr);
-          const int e = lane_run[8 * (g % 4) + below(rs, 8)] * Lr + g / 4;
-          if (cost[g] > 1 && e < n_slots) tgt = e;
+        for (int k = 0; k < 8 && tgt < 0 && tkind < 0; ++k) {
+          const int g = below(rs, ng);
+          if (cost[g] <= 1) continue;
+          if (g < 4 * Lr) {
+            const int e = lane_run[8 * (g % 4) + below(rs, 8)] * Lr + g / 4;
+            if (e < n_slots) tgt = e;
+          } else if (g >= toff[0]) {
+            const int kd = g >= toff[2] ? 2 : (g >= toff[1] ? 1 : 0);
+            const int h = g - toff[kd];
+            const int p = 32 * (h / (4 * roles[kd])) + 8 * (h % 4) + below(rs, 8);
+            if (p < n[kd]) {
+              tkind = kd;
+              tpos = p;
+            }
+          }
         }
-      const int m = below(rs, 20);
+      int m = below(rs, 20);
+      if (tkind >= 0) m = 8;
       int kind = -1, a1 = 0, a2 = 0;
       if (m < 8) {  // two entries of one atom's block
         const int i = tgt >= 0 ? atom_of[tgt] : below(rs, na);
@@ -261,7 +284,9 @@ struct GatherPlan {
         touch(a2);
         swap_entries(a1, a2);
       } else if (m < 17) {  // two terms of one kind
-        if (tgt >= 0) {
+        if (tkind >= 0) {
+          kind = tkind;
+        } else if (tgt >= 0) {
           const int id = (int)ent[tgt];
           kind = id < base[1] ? 0 : (id < base[2] ? 1 : 2);
         } else {
@@ -269,12 +294,14 @@ struct GatherPlan {
           kind = u < n[0] ? 0 : (u < n[0] + n[1] ? 1 : 2);
         }
         if (n[kind] < 2) continue;
-        a1 = tgt >= 0 ? ((int)ent[tgt] - base[kind]) % n[kind] : below(rs, n[kind]);
+        a1 = tkind >= 0 ? tpos : (tgt >= 0 ? ((int)ent[tgt] - base[kind]) % n[kind] : below(rs, n[kind]));
         a2 = below(rs, n[kind] - 1);
         if (a2 >= a1) ++a2;
         for (int r = 0; r < roles[kind]; ++r) {
           touch(pos_of[base[kind] + r * n[kind] + a1]);
           touch(pos_of[base[kind] + r * n[kind] + a2]);
+          add(term_group(kind, a1, r));
+          add(term_group(kind, a2, r));
         }
         swap_terms(kind, a1, a2);
       } else {  // the runs of two lanes in different quarter-warps
@@ -411,6 +438,9 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
   P.n[2] = ntor;
   for (int k = 0; k < 3; ++k)
     for (int t = 0; t < P.n[k]; ++t) P.term_at[k].push_back(t);
+  P.tatom[0].assign(L->bonds, L->bonds + 2 * nb);
+  P.tatom[1].assign(L->angles, L->angles + 3 * nang);
+  P.tatom[2].assign(L->torsions, L->torsions + 4 * ntor);
   std::vector<int>& ent_atom = P.atom_of;
   int max_inc = 0;
   for (int i = 0; i < na; ++i) {
@@ -442,6 +472,10 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
         ++n_part[a];
       }
     P.ng = 4 * Lr + 16 * ((na + 31) / 32);
+    for (int k = 0; k < 3; ++k) {
+      P.toff[k] = P.ng;
+      P.ng += ((P.n[k] + 31) / 32) * P.roles[k] * 4;
+    }
     for (int l = 0; l < 32; ++l) {
       P.lane_run.push_back(l);
       P.run_lane.push_back(l);

@@ -386,7 +386,8 @@ __device__ inline void put_pair_pos(float* xp, int i, float x, float y, float z)
 }
 
 template <int APL, bool ENERGY, bool FORCES = true>
-__device__ inline void nonbonded_table(const Lig& L, int na, const float* xp, float (&F)[APL][3], float& el) {
+__device__ inline void nonbonded_table(const Lig& L, int na, const float4* xs, const float* xp, float (&F)[APL][3],
+                                       float& el) {
   const int lane = threadIdx.x & 31;
   const int P = (na + 1) >> 1;
   const f32x2 one = pack2(1.f, 1.f), two = pack2(2.f, 2.f), twelfth = pack2(1.f / 12.f, 1.f / 12.f);
@@ -409,9 +410,9 @@ __device__ inline void nonbonded_table(const Lig& L, int na, const float* xp, fl
     }
     f32x2 fx2 = 0ull, fy2 = 0ull, fz2 = 0ull;
     if (act) {
-      const float* own = xp + 8 * (i >> 1) + (i & 1);
-      const f32x2 X = pack2(own[0], own[0]), Y = pack2(own[2], own[2]), Z = pack2(own[4], own[4]);
-      const f32x2 Ri = pack2(own[6], own[6]);
+      const float4 own = xs[i];  // (x, y, z, R*_i) in the table path
+      const f32x2 X = pack2(own.x, own.x), Y = pack2(own.y, own.y), Z = pack2(own.z, own.z);
+      const f32x2 Ri = pack2(own.w, own.w);
       const float4* rec = L.pair + (size_t)pb * na + i;
       const float4* pp = (const float4*)xp + 2 * pb;
       const int rstep = dir * na, pstep = 2 * dir;
@@ -494,7 +495,8 @@ __device__ inline void gather_runs(const Lig& L, const LigandLayout& LL, float4*
 }
 
 // Forces on the lane's atoms (and, if ENERGY, the lane's partial energies).  xs holds all
-// positions (x, y, z, q); sl is the warp's bonded-slot scratch (n_slots + 1 float4, the last zero).
+// positions (x, y, z, q), with R*_i in place of q when TABLE; sl is the warp's bonded-slot scratch
+// (n_slots + 1 float4, the last zero).
 template <int APL, bool ENERGY, bool TABLE = false, bool FORCES = true>
 __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const GridDev& G, const float4* xs, float4* sl,
                                 const float (&x)[APL][3], float (&F)[APL][3], float w_sg, float w_g, bool all_grids,
@@ -539,7 +541,7 @@ __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const Grid
       F[a][2] += ((q0.z + q1.z) + q2.z) + q3.z;
     }
   }
-  if (TABLE) nonbonded_table<APL, ENERGY, FORCES>(L, na, xp, F, el);
+  if (TABLE) nonbonded_table<APL, ENERGY, FORCES>(L, na, xs, xp, F, el);
   else nonbonded<APL, ENERGY, FORCES>(L, na, xs, F, el);
   // restraint on the centre of mass
   mx = warp_sumf(mx);
@@ -688,9 +690,9 @@ __device__ __forceinline__ void hmc_trial(const HmcArgs& A, const LigandLayout& 
       v[a][1] = rr1 * s1 * sd;
       v[a][2] = rr2 * c2 * sd;
       kin += pb.z * (v[a][0] * v[a][0] + v[a][1] * v[a][1] + v[a][2] * v[a][2]);
-      // the pair-type loop reads the charge from the fourth component; the table loop reads
-      // positions and R*_i from the pair-interleaved mirror
-      xs[i] = make_float4(x[a][0], x[a][1], x[a][2], L.atom_a[i].y);
+      // the fourth component: the charge for the pair-type loop, R*_i for the table loop (which
+      // reads the partners' positions and radii from the pair-interleaved mirror)
+      xs[i] = make_float4(x[a][0], x[a][1], x[a][2], TABLE ? pb.x : L.atom_a[i].y);
       if (TABLE) {
         put_pair_pos(xp, i, x[a][0], x[a][1], x[a][2]);
         xp[8 * (i >> 1) + 6 + (i & 1)] = pb.x;  // R*_i
