@@ -499,8 +499,8 @@ __device__ inline void gather_runs(const Lig& L, const LigandLayout& LL, float4*
 // (n_slots + 1 float4, the last zero).
 template <int APL, bool ENERGY, bool TABLE = false, bool FORCES = true>
 __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const GridDev& G, const float4* xs, float4* sl,
-                                const float (&x)[APL][3], float (&F)[APL][3], float w_sg, float w_g, bool all_grids,
-                                Energies& en, int& outside, const float* xp = nullptr) {
+                                const float (&x)[APL][3], const float (&mass)[APL], float (&F)[APL][3], float w_sg,
+                                float w_g, bool all_grids, Energies& en, int& outside, const float* xp = nullptr) {
   const int lane = threadIdx.x & 31;
   const int na = LL.na;
   float el = bonded_terms<ENERGY, FORCES>(L, LL, xs, sl);
@@ -519,10 +519,9 @@ __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const Grid
     F[a][0] = F[a][1] = F[a][2] = 0.f;
     if (i >= na) continue;
     const float4 pa = L.atom_a[i];
-    const float m = L.atom_b[i].z;
-    mx += m * x[a][0];
-    my += m * x[a][1];
-    mz += m * x[a][2];
+    mx += mass[a] * x[a][0];
+    my += mass[a] * x[a][1];
+    mz += mass[a] * x[a][2];
     if (hard || soft) {
       const GridOut go = grid_atom(G, x[a][0], x[a][1], x[a][2], pa.z, pa.w, pa.y, hard, soft, FORCES ? w_sg : 0.f,
                                    FORCES ? w_g : 0.f);
@@ -559,10 +558,9 @@ __device__ inline void evaluate(const LigandLayout& LL, const Lig& L, const Grid
     for (int a = 0; a < APL; ++a) {
       const int i = lane + 32 * a;
       if (i >= na) continue;
-      const float m = L.atom_b[i].z;
-      F[a][0] += c * m * dx;
-      F[a][1] += c * m * dy;
-      F[a][2] += c * m * dz;
+      F[a][0] += c * mass[a] * dx;
+      F[a][1] += c * mass[a] * dy;
+      F[a][2] += c * mass[a] * dz;
     }
   } else if (!(d <= LL.d0)) {  // NaN centre of mass: make the energy NaN
     er = d;
@@ -665,6 +663,7 @@ __device__ __forceinline__ void hmc_trial(const HmcArgs& A, const LigandLayout& 
   const uint32_t rid = (uint32_t)(A.rep_offset + r);
 
   float x[APL][3], v[APL][3], F[APL][3];
+  float mass[APL], accel[APL];  // the lane's atoms' masses and force-to-acceleration factors
   float kin = 0.f;
 #pragma unroll
   for (int a = 0; a < APL; ++a) {
@@ -685,6 +684,8 @@ __device__ __forceinline__ void hmc_trial(const HmcArgs& A, const LigandLayout& 
       sincospif(2.f * u2, &s1, &c1);
       sincospif(2.f * u4, &s2, &c2);
       const float4 pb = L.atom_b[i];
+      mass[a] = pb.z;
+      accel[a] = L.atom_a[i].x;
       const float sd = st.sqrt_kT * pb.w;  // sqrt(kT * 4.184e-4 / m)
       v[a][0] = rr1 * c1 * sd;
       v[a][1] = rr1 * s1 * sd;
@@ -700,13 +701,14 @@ __device__ __forceinline__ void hmc_trial(const HmcArgs& A, const LigandLayout& 
     } else {
       x[a][0] = x[a][1] = x[a][2] = 0.f;
       v[a][0] = v[a][1] = v[a][2] = 0.f;
+      mass[a] = accel[a] = 0.f;
     }
   }
   __syncwarp();
   int outside = 0;
   Energies en;
   double c[4];
-  evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sl, x, F, st.w_sg_f, st.w_g_f, true, en, outside, xp);
+  evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sl, x, mass, F, st.w_sg_f, st.w_g_f, true, en, outside, xp);
   reduce_components(en, c);
   // the starting components go out now (a rejected trial leaves them); only U0 stays live
   const double U0 = weighted(c, st.w_sg, st.w_g);
@@ -718,10 +720,9 @@ __device__ __forceinline__ void hmc_trial(const HmcArgs& A, const LigandLayout& 
     for (int a = 0; a < APL; ++a) {
       const int i = lane + 32 * a;
       if (i < na) {
-        const float acc = L.atom_a[i].x;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          v[a][d] = fmaf(hdt * acc, F[a][d], v[a][d]);
+          v[a][d] = fmaf(hdt * accel[a], F[a][d], v[a][d]);
           x[a][d] = fmaf(dt, v[a][d], x[a][d]);
         }
       }
@@ -741,9 +742,9 @@ __device__ __forceinline__ void hmc_trial(const HmcArgs& A, const LigandLayout& 
     }
     __syncwarp();
     if (s + 1 < A.n_steps) {
-      evaluate<APL, false, TABLE>(LL, L, A.G, xs, ws.sl, x, F, st.w_sg_f, st.w_g_f, false, en, outside, xp);
+      evaluate<APL, false, TABLE>(LL, L, A.G, xs, ws.sl, x, mass, F, st.w_sg_f, st.w_g_f, false, en, outside, xp);
     } else {
-      evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sl, x, F, st.w_sg_f, st.w_g_f, true, en, outside, xp);
+      evaluate<APL, true, TABLE>(LL, L, A.G, xs, ws.sl, x, mass, F, st.w_sg_f, st.w_g_f, true, en, outside, xp);
       reduce_components(en, c);
       U1 = weighted(c, st.w_sg, st.w_g);
     }
@@ -751,9 +752,8 @@ __device__ __forceinline__ void hmc_trial(const HmcArgs& A, const LigandLayout& 
     for (int a = 0; a < APL; ++a) {
       const int i = lane + 32 * a;
       if (i < na) {
-        const float acc = L.atom_a[i].x;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) v[a][d] = fmaf(hdt * acc, F[a][d], v[a][d]);
+        for (int d = 0; d < 3; ++d) v[a][d] = fmaf(hdt * accel[a], F[a][d], v[a][d]);
       }
     }
   }
@@ -761,7 +761,7 @@ __device__ __forceinline__ void hmc_trial(const HmcArgs& A, const LigandLayout& 
 #pragma unroll
   for (int a = 0; a < APL; ++a) {
     const int i = lane + 32 * a;
-    if (i < na) kin += L.atom_b[i].z * (v[a][0] * v[a][0] + v[a][1] * v[a][1] + v[a][2] * v[a][2]);
+    if (i < na) kin += mass[a] * (v[a][0] * v[a][0] + v[a][1] * v[a][1] + v[a][2] * v[a][2]);
   }
   const double K1 = 0.5 * kKineticToKcal * warp_sum((double)kin);
   const double dH = (K1 + U1) - (K0 + U0);
@@ -882,7 +882,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) eval_kernel(const EvalArg
     w_sg = A.states[k].w_sg_f;
     w_g = A.states[k].w_g_f;
   }
-  float x[APL][3], F[APL][3];
+  float x[APL][3], F[APL][3], mass[APL];
 #pragma unroll
   for (int a = 0; a < APL; ++a) {
     const int i = lane + 32 * a;
@@ -891,15 +891,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) eval_kernel(const EvalArg
       x[a][0] = src[0];
       x[a][1] = src[1];
       x[a][2] = src[2];
+      mass[a] = L.atom_b[i].z;
       ws.xs[i] = make_float4(x[a][0], x[a][1], x[a][2], L.atom_a[i].y);
     } else {
-      x[a][0] = x[a][1] = x[a][2] = 0.f;
+      x[a][0] = x[a][1] = x[a][2] = mass[a] = 0.f;
     }
   }
   __syncwarp();
   Energies en;
   int outside = 0;
-  evaluate<APL, true, false, FORCES>(A.LL, L, A.G, ws.xs, ws.sl, x, F, w_sg, w_g, true, en, outside);
+  evaluate<APL, true, false, FORCES>(A.LL, L, A.G, ws.xs, ws.sl, x, mass, F, w_sg, w_g, true, en, outside);
   double c[4];
   reduce_components(en, c);
   if (FORCES && A.force) {
