@@ -3,10 +3,15 @@
 #include <math.h>
 #include <string.h>
 
-#include <new>
-#include <string>
 #include <algorithm>
+#include <atomic>
 #include <initializer_list>
+#include <map>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.cuh"
@@ -170,6 +175,7 @@ int wavefronts(const uint32_t* id, int n) {
 // to 32, then greedy) and a fixed seed, minimises the total wavefronts; the result depends on the
 // topology only.
 struct GatherPlan {
+  bool ok = true;
   int na = 0, Lr = 0, n_slots = 0, ng = 0;
   int base[3] = {0, 0, 0}, n[3] = {0, 0, 0}, roles[3] = {2, 3, 4};
   std::vector<int> term_at[3];  // per kind: the input term at each position
@@ -341,6 +347,162 @@ struct GatherPlan {
   }
 };
 
+// The gather plan of a ligand whose atom indices are in range.  ok is false if an atom's entries
+// would meet more than 4 runs.
+GatherPlan make_plan(const algdock_ligand* L) {
+  const int na = L->n_atoms, nb = L->n_bonds, nang = L->n_angles, ntor = L->n_torsions;
+  // per-atom lists of the bonded force slots that act on it (role-major slot numbering by term
+  // position: bond role r -> r nb + p; angle -> 2 nb + r nang + p; torsion -> 2 nb + 3 nang + r ntor + p)
+  std::vector<std::vector<uint32_t>> inc(na);
+  for (int t = 0; t < nb; ++t)
+    for (int r = 0; r < 2; ++r) inc[L->bonds[2 * t + r]].push_back((uint32_t)(r * nb + t));
+  for (int t = 0; t < nang; ++t)
+    for (int r = 0; r < 3; ++r) inc[L->angles[3 * t + r]].push_back((uint32_t)(2 * nb + r * nang + t));
+  for (int t = 0; t < ntor; ++t)
+    for (int r = 0; r < 4; ++r)
+      inc[L->torsions[4 * t + r]].push_back((uint32_t)(2 * nb + 3 * nang + r * ntor + t));
+  // Gather schedule of the bonded forces: every slot belongs to exactly one atom, so the slots
+  // sorted by atom form one list of n_slots entries.  It is cut into runs of Lr entries, one run
+  // per lane, which balances the per-lane work however the slots are spread over atoms.  A lane
+  // adds its entries in order and, at the last entry of each atom within its run, stores the
+  // partial sum in that entry's slot (which no other lane reads).  Lr is at least a third of the
+  // largest atom's count, so that an atom's entries meet at most 4 runs: its owner then adds at
+  // most 4 partial sums, in run order.  The term order, the entry order within each atom and the
+  // lane of each run are then chosen against shared-memory bank conflicts (GatherPlan).
+  const int n_slots = 2 * nb + 3 * nang + 4 * ntor;
+  GatherPlan P;
+  P.na = na;
+  P.n_slots = n_slots;
+  P.base[1] = 2 * nb;
+  P.base[2] = 2 * nb + 3 * nang;
+  P.n[0] = nb;
+  P.n[1] = nang;
+  P.n[2] = ntor;
+  for (int k = 0; k < 3; ++k)
+    for (int t = 0; t < P.n[k]; ++t) P.term_at[k].push_back(t);
+  P.tatom[0].assign(L->bonds, L->bonds + 2 * nb);
+  P.tatom[1].assign(L->angles, L->angles + 3 * nang);
+  P.tatom[2].assign(L->torsions, L->torsions + 4 * ntor);
+  std::vector<int>& ent_atom = P.atom_of;
+  int max_inc = 0;
+  for (int i = 0; i < na; ++i) {
+    max_inc = std::max(max_inc, (int)inc[i].size());
+    P.blk0.push_back((int)P.ent.size());
+    for (uint32_t code : inc[i]) {
+      P.ent.push_back(code);
+      ent_atom.push_back(i);
+    }
+    P.blk1.push_back((int)P.ent.size());
+  }
+  const int Lr = n_slots == 0 ? 0 : std::max((n_slots + 31) / 32, (max_inc + 2) / 3);
+  P.Lr = Lr;
+  if (n_slots > 0) {
+    P.pos_of.assign(n_slots + 1, -1);
+    for (int e = 0; e < n_slots; ++e) P.pos_of[P.ent[e]] = e;
+    P.part_pos.assign((size_t)na * 4, -1);
+    P.part_grp.assign(n_slots, -1);
+    std::vector<int> n_part(na, 0);
+    for (int e = 0; e < n_slots; ++e)
+      if (e % Lr == Lr - 1 || e + 1 == n_slots || ent_atom[e + 1] != ent_atom[e]) {
+        const int a = ent_atom[e];
+        if (n_part[a] >= 4) {
+          P.ok = false;
+          return P;
+        }
+        P.part_pos[4 * a + n_part[a]] = e;
+        P.part_grp[e] = 4 * Lr + ((a / 32) * 4 + n_part[a]) * 4 + (a % 32) / 8;
+        ++n_part[a];
+      }
+    P.ng = 4 * Lr + 16 * ((na + 31) / 32);
+    for (int k = 0; k < 3; ++k) {
+      P.toff[k] = P.ng;
+      P.ng += ((P.n[k] + 31) / 32) * P.roles[k] * 4;
+    }
+    for (int l = 0; l < 32; ++l) {
+      P.lane_run.push_back(l);
+      P.run_lane.push_back(l);
+    }
+    P.optimise();
+  }
+  return P;
+}
+
+// Plans by topology: the layout depends on the terms' atom indices only, so the contexts of one
+// process and the ligands of a batch that share a topology share one search.  At most 4096
+// topologies are kept.
+std::mutex& plan_mutex() {
+  static std::mutex m;
+  return m;
+}
+std::map<std::vector<int32_t>, GatherPlan>& plan_cache() {
+  static auto* m = new std::map<std::vector<int32_t>, GatherPlan>();
+  return *m;
+}
+std::vector<int32_t> plan_key(const algdock_ligand* L) {
+  std::vector<int32_t> k = {L->n_atoms, L->n_bonds, L->n_angles, L->n_torsions};
+  if (L->n_bonds > 0) k.insert(k.end(), L->bonds, L->bonds + 2 * L->n_bonds);
+  if (L->n_angles > 0) k.insert(k.end(), L->angles, L->angles + 3 * L->n_angles);
+  if (L->n_torsions > 0) k.insert(k.end(), L->torsions, L->torsions + 4 * L->n_torsions);
+  return k;
+}
+GatherPlan cached_plan(const algdock_ligand* L) {
+  const std::vector<int32_t> key = plan_key(L);
+  {
+    std::lock_guard<std::mutex> g(plan_mutex());
+    const auto it = plan_cache().find(key);
+    if (it != plan_cache().end()) return it->second;
+  }
+  GatherPlan P = make_plan(L);
+  std::lock_guard<std::mutex> g(plan_mutex());
+  if (plan_cache().size() >= 4096) plan_cache().clear();
+  plan_cache().emplace(key, P);
+  return P;
+}
+
+// Whether make_plan can run on L: non-null index arrays, counts in range, indices within the atoms.
+bool plannable(const algdock_ligand* L) {
+  const int na = L->n_atoms;
+  if (na < 1 || na > kMaxAtoms || L->n_bonds < 0 || L->n_angles < 0 || L->n_torsions < 0) return false;
+  if ((L->n_bonds && !L->bonds) || (L->n_angles && !L->angles) || (L->n_torsions && !L->torsions)) return false;
+  if (2 * L->n_bonds + 3 * L->n_angles + 4 * L->n_torsions >= 0x7fff) return false;
+  auto in_range = [&](const int32_t* idx, int n) {
+    for (int t = 0; t < n; ++t)
+      if (idx[t] < 0 || idx[t] >= na) return false;
+    return true;
+  };
+  return in_range(L->bonds, 2 * L->n_bonds) && in_range(L->angles, 3 * L->n_angles) &&
+         in_range(L->torsions, 4 * L->n_torsions);
+}
+
+// Searches the plans of a batch's distinct uncached topologies on the host's cores.  A ligand that
+// cannot be planned is left to build_ligand, which reports it.
+void plan_all(const algdock_ligand* ligs, int n) {
+  std::vector<int> todo;
+  {
+    std::set<std::vector<int32_t>> seen;
+    std::lock_guard<std::mutex> g(plan_mutex());
+    for (int l = 0; l < n; ++l) {
+      if (!plannable(&ligs[l])) continue;
+      std::vector<int32_t> key = plan_key(&ligs[l]);
+      if (plan_cache().count(key) || seen.count(key)) continue;
+      seen.insert(std::move(key));
+      todo.push_back(l);
+    }
+  }
+  const int nt = std::min<int>((int)todo.size(), std::max(1u, std::thread::hardware_concurrency()));
+  if (nt <= 1) return;
+  std::atomic<int> next(0);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([&]() {
+      try {
+        for (int k = next++; k < (int)todo.size(); k = next++) cached_plan(&ligs[todo[k]]);
+      } catch (...) {  // a plan that failed to allocate is searched again by build_ligand
+      }
+    });
+  for (auto& th : pool) th.join();
+}
+
 // Validates one ligand and its restraint and builds its device tables: the layout, the blob (atom
 // records, pair types, bonded terms, the bonded-force gather schedule, then the per-pair table) and the FP64
 // target-force-field factors of each atom.
@@ -408,89 +570,24 @@ algdock_status build_ligand(algdock_ctx* c, const algdock_ligand* L, const algdo
       else if (dist[j] == 3) ptype[(size_t)j * na + i] = 1;
     }
   }
-  // per-atom lists of the bonded force slots that act on it (role-major slot numbering by term
-  // position: bond role r -> r nb + p; angle -> 2 nb + r nang + p; torsion -> 2 nb + 3 nang + r ntor + p)
-  std::vector<std::vector<uint32_t>> inc(na);
-  for (int t = 0; t < nb; ++t)
-    for (int r = 0; r < 2; ++r) inc[L->bonds[2 * t + r]].push_back((uint32_t)(r * nb + t));
-  for (int t = 0; t < nang; ++t)
-    for (int r = 0; r < 3; ++r) inc[L->angles[3 * t + r]].push_back((uint32_t)(2 * nb + r * nang + t));
-  for (int t = 0; t < ntor; ++t)
-    for (int r = 0; r < 4; ++r)
-      inc[L->torsions[4 * t + r]].push_back((uint32_t)(2 * nb + 3 * nang + r * ntor + t));
-  // Gather schedule of the bonded forces: every slot belongs to exactly one atom, so the slots
-  // sorted by atom form one list of n_slots entries.  It is cut into runs of Lr entries, one run
-  // per lane, which balances the per-lane work however the slots are spread over atoms.  A lane
-  // adds its entries in order and, at the last entry of each atom within its run, stores the
-  // partial sum in that entry's slot (which no other lane reads).  Lr is at least a third of the
-  // largest atom's count, so that an atom's entries meet at most 4 runs: its owner then adds at
-  // most 4 partial sums, in run order.  The term order, the entry order within each atom and the
-  // lane of each run are then chosen against shared-memory bank conflicts (GatherPlan).
+  // the bonded-force gather schedule of this topology (make_plan)
   const int n_slots = 2 * nb + 3 * nang + 4 * ntor;
   if (n_slots >= 0x7fff) return fail(c, ALGDOCK_E_INVALID, who + ": too many bonded terms");
-  GatherPlan P;
-  P.na = na;
-  P.n_slots = n_slots;
-  P.base[1] = 2 * nb;
-  P.base[2] = 2 * nb + 3 * nang;
-  P.n[0] = nb;
-  P.n[1] = nang;
-  P.n[2] = ntor;
-  for (int k = 0; k < 3; ++k)
-    for (int t = 0; t < P.n[k]; ++t) P.term_at[k].push_back(t);
-  P.tatom[0].assign(L->bonds, L->bonds + 2 * nb);
-  P.tatom[1].assign(L->angles, L->angles + 3 * nang);
-  P.tatom[2].assign(L->torsions, L->torsions + 4 * ntor);
-  std::vector<int>& ent_atom = P.atom_of;
-  int max_inc = 0;
-  for (int i = 0; i < na; ++i) {
-    max_inc = std::max(max_inc, (int)inc[i].size());
-    P.blk0.push_back((int)P.ent.size());
-    for (uint32_t code : inc[i]) {
-      P.ent.push_back(code);
-      ent_atom.push_back(i);
-    }
-    P.blk1.push_back((int)P.ent.size());
-  }
-  const int Lr = n_slots == 0 ? 0 : std::max((n_slots + 31) / 32, (max_inc + 2) / 3);
+  const GatherPlan P = cached_plan(L);
+  if (!P.ok) return fail(c, ALGDOCK_E_INVALID, who + ": gather schedule overflow");
+  const int Lr = P.Lr;
   const int gs_iters = (Lr + 3) / 4;
   std::vector<uint16_t> gs((size_t)gs_iters * 32 * 4, (uint16_t)n_slots);
   std::vector<uint16_t> gp((size_t)na * 4, (uint16_t)n_slots);
-  if (n_slots > 0) {
-    P.Lr = Lr;
-    P.pos_of.assign(n_slots + 1, -1);
-    for (int e = 0; e < n_slots; ++e) P.pos_of[P.ent[e]] = e;
-    P.part_pos.assign((size_t)na * 4, -1);
-    P.part_grp.assign(n_slots, -1);
-    std::vector<int> n_part(na, 0);
-    for (int e = 0; e < n_slots; ++e)
-      if (e % Lr == Lr - 1 || e + 1 == n_slots || ent_atom[e + 1] != ent_atom[e]) {
-        const int a = ent_atom[e];
-        if (n_part[a] >= 4) return fail(c, ALGDOCK_E_INVALID, who + ": gather schedule overflow");
-        P.part_pos[4 * a + n_part[a]] = e;
-        P.part_grp[e] = 4 * Lr + ((a / 32) * 4 + n_part[a]) * 4 + (a % 32) / 8;
-        ++n_part[a];
-      }
-    P.ng = 4 * Lr + 16 * ((na + 31) / 32);
-    for (int k = 0; k < 3; ++k) {
-      P.toff[k] = P.ng;
-      P.ng += ((P.n[k] + 31) / 32) * P.roles[k] * 4;
+  for (int l = 0; l < 32 && Lr > 0; ++l)
+    for (int j = 0; j < Lr; ++j) {
+      const int e = P.lane_run[l] * Lr + j;
+      if (e >= n_slots) break;
+      const bool last = P.part_grp[e] >= 0;
+      gs[((size_t)(j / 4) * 32 + l) * 4 + (j % 4)] = (uint16_t)(P.ent[e] | (last ? 0x8000u : 0u));
     }
-    for (int l = 0; l < 32; ++l) {
-      P.lane_run.push_back(l);
-      P.run_lane.push_back(l);
-    }
-    P.optimise();
-    for (int l = 0; l < 32; ++l)
-      for (int j = 0; j < Lr; ++j) {
-        const int e = P.lane_run[l] * Lr + j;
-        if (e >= n_slots) break;
-        const bool last = P.part_grp[e] >= 0;
-        gs[((size_t)(j / 4) * 32 + l) * 4 + (j % 4)] = (uint16_t)(P.ent[e] | (last ? 0x8000u : 0u));
-      }
-    for (int i = 0; i < 4 * na; ++i)
-      if (P.part_pos[i] >= 0) gp[i] = (uint16_t)P.ent[P.part_pos[i]];
-  }
+  for (int i = 0; i < 4 * na && Lr > 0; ++i)
+    if (P.part_pos[i] >= 0) gp[i] = (uint16_t)P.ent[P.part_pos[i]];
 
   memset(&Y, 0, sizeof(Y));
   Y.na = na;
@@ -1293,6 +1390,7 @@ algdock_status algdock_batch_load(algdock_ctx* c, int32_t n_ligands, const algdo
   std::vector<uint32_t> all;
   int max_na = 0;
   Device g(c->device);  // the class test queries the batch kernels' limits on this device
+  plan_all(ligands, n_ligands);
   for (int l = 0; l < n_ligands; ++l) {
     LigandLayout Y;
     std::vector<uint32_t> blob;
