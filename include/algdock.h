@@ -194,14 +194,37 @@ algdock_status algdock_energy_force_f64(algdock_ctx* ctx, int64_t N, const int32
 
 /* Measurement aid for the gather roofline (no counterpart in the paper, not a step of the
  * method): n_cells 8-corner gathers from the loaded lattices at cells drawn uniformly (hard float4
- * corners; with soft != 0 also the soft float2 corners), the access pattern of one atom's
- * trilinear interpolation.  Useful bytes: 128 per cell, plus 64 with soft.  Time it with events on
+ * corners; with soft != 0 also the soft corners), through the lattice records and loads of one
+ * atom's trilinear interpolation.  Useful bytes: 96 per cell (three grids; the records' fourth
+ * lane is padding), plus 64 with soft.  Time it with events on
  * the context's stream.  sink: a device float that is written only if the folded sum takes an
  * impossible value (it keeps every load live). */
 algdock_status algdock_gather_probe(algdock_ctx* ctx, int64_t n_cells, int32_t soft, uint64_t seed, float* sink);
 
 /* ---------------------------------------------------------------- ligand and states */
 algdock_status algdock_ligand_load(algdock_ctx* ctx, const algdock_ligand* lig, const algdock_restraint* rest);
+
+/* The shared-memory layout of the bonded forces that algdock_ligand_load and algdock_batch_load
+ * build for this ligand's topology (host only: no context, no device).  In each force evaluation
+ * the bonded terms run one per lane in rounds of 32, kind by kind (bonds, angles, torsions); the
+ * term at position p of kind k writes its role-r force to slot base_k + r n_k + p (base 0,
+ * 2 n_bonds, 2 n_bonds + 3 n_angles; n_k the kind's count).  The slots, listed atom by atom, are
+ * added by the 32 lanes in runs of Lr = max(ceil(n_slots / 32), ceil(m / 3)) entries (m the
+ * largest number of slots of one atom), each lane's partial sum of an atom stored at that atom's
+ * last entry in the run.  The term order, the order of the slots within each atom and the lane of
+ * each run are chosen against shared-memory bank conflicts.  Outputs (each may be NULL):
+ *   term_order [n_bonds + n_angles + n_torsions]: the input term at each position, bonds first;
+ *   slots [n_slots = 2 n_bonds + 3 n_angles + 4 n_torsions]: the slot list, atom by atom;
+ *   lane_run [32]: the run each lane adds;
+ *   wavefronts [2]: the shared-memory wavefronts per force evaluation of the three loads the
+ *   layout arranges (each term round's loads of one role's atom positions, the gather's slot
+ *   loads at each run position, the owners' loads of each atom's k-th partial sum), counted per
+ *   quarter-warp as the largest number of distinct 16-byte addresses (slot or atom) in one of the
+ *   8 bank groups (address mod 8): [0] for the input order, [1] for the layout.
+ * Deterministic for a topology.  ALGDOCK_E_INVALID for a topology algdock_ligand_load rejects
+ * (an index out of range, too many terms, an atom whose slots would meet more than 4 runs). */
+algdock_status algdock_gather_layout(const algdock_ligand* lig, int32_t* term_order, uint16_t* slots,
+                                     int32_t* lane_run, int32_t* wavefronts);
 
 /* K thermodynamic states (host arrays): temperature T (K), alchemical progress alpha, and the
  * velocity-Verlet time step dt (fs).  Eq. (protocol): the grid weights are

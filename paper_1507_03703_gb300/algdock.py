@@ -38,7 +38,7 @@ EXPORTS = [
     "algdock_mbar_update", "algdock_next_temperature", "algdock_next_alpha", "algdock_adapt_dt",
     "algdock_insert_states", "algdock_cycle", "algdock_gemm_bf16", "algdock_params_default", "algdock_set_params",
     "algdock_get_params", "algdock_replicas_init", "algdock_run", "algdock_replicas_get", "algdock_replicas_save",
-    "algdock_replicas_load",
+    "algdock_replicas_load", "algdock_gather_layout",
 ]
 
 BATCH_CLASSES = 4             # launch classes of a multi-ligand batch
@@ -161,6 +161,7 @@ def load_library(path: str = LIB_PATH):
         "algdock_last_error": ([vp], C.c_char_p),
         "algdock_grids_build": ([vp, C.POINTER(GridDesc), i32, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "algdock_soft_elec_cap": ([C.POINTER(LigandC), dbl, C.POINTER(dbl)], C.c_int),
+        "algdock_gather_layout": ([C.POINTER(LigandC), vp, vp, vp, vp], C.c_int),
         "algdock_grids_load": ([vp, C.POINTER(GridDesc), vp, vp, vp, dbl, dbl], C.c_int),
         "algdock_ligand_load": ([vp, C.POINTER(LigandC), C.POINTER(RestraintC)], C.c_int),
         "algdock_states_set": ([vp, i32, vp, vp, vp], C.c_int),
@@ -277,6 +278,25 @@ def soft_elec_cap(lig, vmax_r: float = VMAX_R) -> float:
     if st != OK:
         raise AlgdockError(st, "soft_elec_cap: invalid ligand")
     return out.value
+
+
+def gather_layout(lig):
+    """algdock_gather_layout: the bonded-force layout of lig's topology, as a dict of term_order
+    [n_terms], slots [n_slots], lane_run [32] and wavefronts (input order, layout)."""
+    L = load_library()
+    s, keep = ligand_struct(lig)
+    n_terms = s.n_bonds + s.n_angles + s.n_torsions
+    n_slots = 2 * s.n_bonds + 3 * s.n_angles + 4 * s.n_torsions
+    order = np.zeros(max(n_terms, 1), np.int32)
+    slots = np.zeros(max(n_slots, 1), np.uint16)
+    lane_run = np.zeros(32, np.int32)
+    wf = np.zeros(2, np.int32)
+    st = L.algdock_gather_layout(C.byref(s), order.ctypes.data, slots.ctypes.data, lane_run.ctypes.data,
+                                 wf.ctypes.data)
+    if st != OK:
+        raise AlgdockError(st, "gather_layout: invalid topology")
+    return {"term_order": order[:n_terms], "slots": slots[:n_slots], "lane_run": lane_run,
+            "wavefronts": (int(wf[0]), int(wf[1]))}
 
 
 def grid_desc(grid) -> GridDesc:

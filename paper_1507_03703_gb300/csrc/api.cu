@@ -189,6 +189,7 @@ struct GatherPlan {
   std::vector<int> tatom[3];    // per kind: the atoms of each input term, roles[kind] per term
   int toff[3] = {0, 0, 0};      // first position-load group of each kind
   std::vector<int> cost;        // wavefronts per load group
+  int wf_before = 0, wf_after = 0;  // total wavefronts of the input order and of the layout
 
   int gather_group(int e) const { return (e % Lr) * 4 + run_lane[e / Lr] / 8; }
   // the load group of the role-r positions read by the quarter-warp holding term position p
@@ -241,6 +242,7 @@ struct GatherPlan {
       cur += cost[g];
       floor += cost[g] > 0 ? 1 : 0;
     }
+    wf_before = cur;
     int best = cur;
     GatherPlan keep = *this;
     const int terms = n[0] + n[1] + n[2];
@@ -344,6 +346,7 @@ struct GatherPlan {
       }
     }
     if (best < cur) *this = keep;
+    wf_after = best;
   }
 };
 
@@ -894,6 +897,31 @@ algdock_status algdock_soft_elec_cap(const algdock_ligand* lig, double vmax_r, d
   }
   *vmax_e = vmax_r * best;
   return ALGDOCK_OK;
+}
+
+algdock_status algdock_gather_layout(const algdock_ligand* lig, int32_t* term_order, uint16_t* slots,
+                                     int32_t* lane_run, int32_t* wavefronts) {
+  try {
+    if (!lig || !plannable(lig)) return ALGDOCK_E_INVALID;
+    const GatherPlan P = cached_plan(lig);
+    if (!P.ok) return ALGDOCK_E_INVALID;
+    if (term_order) {
+      int o = 0;
+      for (int k = 0; k < 3; ++k)
+        for (int t : P.term_at[k]) term_order[o++] = t;
+    }
+    if (slots)
+      for (size_t e = 0; e < P.ent.size(); ++e) slots[e] = (uint16_t)P.ent[e];
+    if (lane_run)
+      for (int l = 0; l < 32; ++l) lane_run[l] = P.lane_run.empty() ? l : P.lane_run[l];
+    if (wavefronts) {
+      wavefronts[0] = P.wf_before;
+      wavefronts[1] = P.wf_after;
+    }
+    return ALGDOCK_OK;
+  } catch (...) {
+    return ALGDOCK_E_OOM;
+  }
 }
 
 algdock_status algdock_grids_build(algdock_ctx* c, const algdock_grid_desc* d, int32_t n_rec, const double* xyz,
