@@ -234,6 +234,12 @@ struct GatherPlan {
     run_lane[lane_run[l2]] = l2;
   }
 
+  // Releases what only the search uses; the build reads term_at, ent, lane_run, part_pos, part_grp.
+  void compact() {
+    for (auto* v : {&pos_of, &blk0, &blk1, &atom_of, &run_lane, &cost, &tatom[0], &tatom[1], &tatom[2]})
+      std::vector<int>().swap(*v);
+  }
+
   void optimise() {
     cost.resize(ng);
     int cur = 0, floor = 0;
@@ -431,8 +437,8 @@ GatherPlan make_plan(const algdock_ligand* L) {
 }
 
 // Plans by topology: the layout depends on the terms' atom indices only, so the contexts of one
-// process and the ligands of a batch that share a topology share one search.  At most 4096
-// topologies are kept.
+// process and the ligands of a batch that share a topology share one search.  At most 1024
+// topologies are kept, each with only what the ligand build reads.
 std::mutex& plan_mutex() {
   static std::mutex m;
   return m;
@@ -456,8 +462,9 @@ GatherPlan cached_plan(const algdock_ligand* L) {
     if (it != plan_cache().end()) return it->second;
   }
   GatherPlan P = make_plan(L);
+  P.compact();
   std::lock_guard<std::mutex> g(plan_mutex());
-  if (plan_cache().size() >= 4096) plan_cache().clear();
+  if (plan_cache().size() >= 1024) plan_cache().clear();
   plan_cache().emplace(key, P);
   return P;
 }
@@ -495,14 +502,17 @@ void plan_all(const algdock_ligand* ligs, int n) {
   const int nt = std::min<int>((int)todo.size(), std::max(1u, std::thread::hardware_concurrency()));
   if (nt <= 1) return;
   std::atomic<int> next(0);
+  auto work = [&]() {
+    try {
+      for (int k = next++; k < (int)todo.size(); k = next++) cached_plan(&ligs[todo[k]]);
+    } catch (...) {  // a plan that failed to allocate is searched again by build_ligand
+    }
+  };
   std::vector<std::thread> pool;
-  for (int t = 0; t < nt; ++t)
-    pool.emplace_back([&]() {
-      try {
-        for (int k = next++; k < (int)todo.size(); k = next++) cached_plan(&ligs[todo[k]]);
-      } catch (...) {  // a plan that failed to allocate is searched again by build_ligand
-      }
-    });
+  try {
+    for (int t = 0; t < nt; ++t) pool.emplace_back(work);
+  } catch (...) {  // fewer threads than asked: those started take the whole list
+  }
   for (auto& th : pool) th.join();
 }
 
