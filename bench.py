@@ -264,9 +264,9 @@ def measured_peaks():
 # a fingerprint of the sources the kernel was built from at the time: the figure is reported only
 # while those sources are unchanged.
 NCU_TRAFFIC = {
-    "hmc_kernel": {"bytes_per_launch": 16058880,
+    "hmc_kernel": {"bytes_per_launch": 16062208,
                    "sources": ("hmc.cu", "internal.cuh", "grids.cu"),
-                   "sha256": "7c3282cce865ad953982a7dbc0e164e4501b49b0300997bfe56822bc9b9fdee5"},
+                   "sha256": "ca9be75fe0d54704e86ff1767d16f578868d3c1203635c164ad9ee6386ce0b9e"},
 }
 
 
