@@ -305,8 +305,11 @@ algdock_status algdock_exchange(algdock_ctx* ctx, int32_t n_ladders, int32_t K, 
  *   or device (cudaPointerGetAttributes), read and written; counters [ALGDOCK_N_COUNTERS] int64
  *   (may be NULL) host or device, added to; u_kn (may be NULL) host or device out, leg after leg
  *   [K_l][n_chains K_l] double.
- * Host arrays are copied into device memory the context owns, and back after the cycle; the call
- * then synchronises.  With device arrays only it is asynchronous like the other calls. */
+ * On a device that reaches host memory over a coherent link (NVLink-C2C: the device attribute
+ * cudaDevAttrHostNativeAtomicSupported), x, comps, state_of and config_of in pinned host memory
+ * (cudaMemoryTypeHost) are read and written in place by the cycle's kernels.  Other host arrays
+ * are copied into device memory the context owns, and back after the cycle.  With any host array
+ * the call then synchronises; with device arrays only it is asynchronous like the other calls. */
 #define ALGDOCK_MAX_LEGS 8
 typedef struct {
   int32_t n_legs;

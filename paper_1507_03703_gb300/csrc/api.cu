@@ -843,6 +843,13 @@ algdock_status algdock_create(int device, uint64_t seed, const algdock_params* p
   c->seed = seed;
   c->params = p;
   Device g(device);
+  int coherent = 0, mappable = 0;
+  if (cudaDeviceGetAttribute(&coherent, cudaDevAttrHostNativeAtomicSupported, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&mappable, cudaDevAttrCanMapHostMemory, device) != cudaSuccess) {
+    cudaGetLastError();
+    coherent = mappable = 0;
+  }
+  c->host_coherent = coherent && mappable;
   if (cudaMallocHost(&c->h_flag, sizeof(int)) != cudaSuccess) {
     delete c;
     return ALGDOCK_E_CUDA;
@@ -1899,28 +1906,43 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
     ukn_words += (int64_t)d->K[l] * d->n_chains * d->K[l];
   }
   const int na = c->lig.na;
-  // each array device-resident as given, or staged: [x | comps | state_of | config_of | counters |
-  // u_kn], 256-byte aligned pieces
+  // each array device-resident as given; or, for the positions, components and permutations in
+  // pinned host memory on a device with a coherent host link, read and written in place by the
+  // kernels (plain loads and stores only); or else staged: [x | comps | state_of | config_of |
+  // counters | u_kn], 256-byte aligned pieces
   struct Piece {
     void* user;
     size_t bytes;
     bool host;
     size_t off;
+    void* mapped;
   };
   constexpr int kPieces = 6;
-  Piece P[kPieces] = {{x, (size_t)R * na * 3 * 4, false, 0},
-                      {comps, (size_t)R * 32, false, 0},
-                      {state_of, (size_t)R * 4, false, 0},
-                      {config_of, (size_t)R * 4, false, 0},
-                      {counters, counters ? (size_t)ALGDOCK_N_COUNTERS * 8 : 0, false, 0},
-                      {u_kn, u_kn ? (size_t)ukn_words * 8 : 0, false, 0}};
+  Piece P[kPieces] = {{x, (size_t)R * na * 3 * 4, false, 0, nullptr},
+                      {comps, (size_t)R * 32, false, 0, nullptr},
+                      {state_of, (size_t)R * 4, false, 0, nullptr},
+                      {config_of, (size_t)R * 4, false, 0, nullptr},
+                      {counters, counters ? (size_t)ALGDOCK_N_COUNTERS * 8 : 0, false, 0, nullptr},
+                      {u_kn, u_kn ? (size_t)ukn_words * 8 : 0, false, 0, nullptr}};
   size_t need = 0;
+  bool any_mapped = false;
   for (int i = 0; i < kPieces; ++i) {
-    P[i].host = P[i].user && !is_device_ptr(P[i].user);
-    if (P[i].host) {
-      P[i].off = need;
-      need += (P[i].bytes + 255) & ~(size_t)255;
+    if (!P[i].user) continue;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, P[i].user) != cudaSuccess) {
+      cudaGetLastError();
+      a.type = cudaMemoryTypeUnregistered;
+      a.devicePointer = nullptr;
     }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) continue;
+    if (i < 4 && c->host_coherent && a.type == cudaMemoryTypeHost && a.devicePointer) {
+      P[i].mapped = a.devicePointer;
+      any_mapped = true;
+      continue;
+    }
+    P[i].host = true;
+    P[i].off = need;
+    need += (P[i].bytes + 255) & ~(size_t)255;
   }
   Device g(c->device);
   cudaError_t e = cudaSuccess;
@@ -1934,7 +1956,9 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
     if (e != cudaSuccess) return cuda_fail(c, e, "cycle");
     c->stage_bytes = need;
   }
-  auto dev_of = [&](int i) { return P[i].host ? (void*)((char*)c->d_stage + P[i].off) : P[i].user; };
+  auto dev_of = [&](int i) {
+    return P[i].mapped ? P[i].mapped : (P[i].host ? (void*)((char*)c->d_stage + P[i].off) : P[i].user);
+  };
   bool any_host = false;
   for (int i = 0; i < kPieces && e == cudaSuccess; ++i)
     if (P[i].host && P[i].user) {  // inputs in (u_kn is output only; its host copy goes out below)
@@ -2005,7 +2029,7 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
   }
   for (int i = side ? 2 : 0; i < kPieces && e == cudaSuccess; ++i)
     if (P[i].host && P[i].user) e = cudaMemcpyAsync(P[i].user, dev_of(i), P[i].bytes, cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess && (any_host || checks)) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && (any_host || any_mapped || checks)) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cycle");
   if (checks) return check_status(c, *c->h_flag, "cycle");
   return ALGDOCK_OK;

@@ -263,6 +263,9 @@ struct algdock_ctx {
   // its snapshot runs beside the exchange sweeps
   void* d_stage = nullptr;
   size_t stage_bytes = 0;
+  // the device reaches host memory over a coherent link (NVLink-C2C on Grace: host-native atomics),
+  // so algdock_cycle's kernels read and write pinned host arrays in place instead of staging them
+  bool host_coherent = false;
   cudaStream_t cycle_side = nullptr;
   cudaEvent_t cycle_fork = nullptr, cycle_join = nullptr;
   // the context's seed and the method's adjustable arguments (algdock_create, algdock_set_params)

@@ -37,9 +37,10 @@ def test_cycle_with_host_or_device_arrays_repeats_the_separate_calls():
             parts.append(u.reshape(-1))
         ukn_ref.append(torch.cat(parts).cpu().numpy())
     n_ukn = sum(K * C * K for K, _ in legs)
-    # device first, so that the host pass grows the staging buffer after the snapshot's side stream
-    # and events exist, and a device pass after it still uses them
-    for where in ("device", "host", "device"):
+    # device first, so that the host passes grow the staging buffer after the snapshot's side stream
+    # and events exist, and a device pass after them still uses them.  Pinned host arrays are used
+    # in place on a device with a coherent host link (staged otherwise); pageable ones are staged.
+    for where in ("device", "host", "pageable", "device"):
         st0 = np.concatenate([np.tile(off + np.arange(K), C) for K, off in legs]).astype(np.int32)
         cfg0 = np.concatenate([np.tile(np.arange(K), C) for K, _ in legs]).astype(np.int32)
         arrays = {"x": torch.from_numpy(x0.copy()), "comps": torch.zeros((R, 4), dtype=torch.float64),
@@ -47,13 +48,18 @@ def test_cycle_with_host_or_device_arrays_repeats_the_separate_calls():
                   "counters": torch.zeros(4, dtype=torch.int64), "u_kn": torch.zeros(n_ukn, dtype=torch.float64)}
         if where == "host":
             arrays = {k: v.pin_memory() for k, v in arrays.items()}
+        elif where == "pageable":
+            arrays = {k: v.numpy() for k, v in arrays.items()}
         else:
             arrays = {k: v.cuda() for k, v in arrays.items()}
         for cyc in range(n_cyc):
             ctx.cycle(legs, C, cyc, arrays["x"], arrays["comps"], arrays["state_of"], arrays["config_of"],
                       n_steps=steps, seed=seed, counters=arrays["counters"], u_kn=arrays["u_kn"])
-            assert np.array_equal(arrays["u_kn"].cpu().numpy(), ukn_ref[cyc]), (where, cyc)
+            u_now = arrays["u_kn"] if where == "pageable" else arrays["u_kn"].cpu().numpy()
+            assert np.array_equal(u_now, ukn_ref[cyc]), (where, cyc)
         torch.cuda.synchronize()
+        if where == "pageable":
+            arrays = {k: torch.from_numpy(v) for k, v in arrays.items()}
         assert torch.equal(arrays["x"].cpu(), ref.x.cpu()), where
         assert torch.equal(arrays["comps"].cpu(), ref.comps.cpu()), where
         assert torch.equal(arrays["state_of"].cpu(), ref.state_of.cpu()), where
