@@ -306,9 +306,10 @@ algdock_status algdock_exchange(algdock_ctx* ctx, int32_t n_ladders, int32_t K, 
  *   (may be NULL) host or device, added to; u_kn (may be NULL) host or device out, leg after leg
  *   [K_l][n_chains K_l] double.
  * On a device that reaches host memory over a coherent link (NVLink-C2C: the device attribute
- * cudaDevAttrHostNativeAtomicSupported), x, comps, state_of and config_of in pinned host memory
- * (cudaMemoryTypeHost) are read and written in place by the cycle's kernels.  Other host arrays
- * are copied into device memory the context owns, and back after the cycle.  With any host array
+ * cudaDevAttrHostNativeAtomicSupported), x, comps, state_of, config_of and u_kn in pinned host
+ * memory (cudaMemoryTypeHost) are read and written in place by the cycle's kernels.  Other host
+ * arrays (pageable ones, and the counters) are copied into device memory the context owns, and
+ * back after the cycle.  With any host array
  * the call then synchronises; with device arrays only it is asynchronous like the other calls. */
 #define ALGDOCK_MAX_LEGS 8
 typedef struct {

@@ -1906,10 +1906,10 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
     ukn_words += (int64_t)d->K[l] * d->n_chains * d->K[l];
   }
   const int na = c->lig.na;
-  // each array device-resident as given; or, for the positions, components and permutations in
-  // pinned host memory on a device with a coherent host link, read and written in place by the
-  // kernels (plain loads and stores only); or else staged: [x | comps | state_of | config_of |
-  // counters | u_kn], 256-byte aligned pieces
+  // each array device-resident as given; or, for the positions, components, permutations and u_kn
+  // in pinned host memory on a device with a coherent host link, read and written in place by the
+  // kernels (plain loads and stores only; the counters take atomics); or else staged: [x | comps |
+  // state_of | config_of | counters | u_kn], 256-byte aligned pieces
   struct Piece {
     void* user;
     size_t bytes;
@@ -1935,7 +1935,7 @@ algdock_status algdock_cycle(algdock_ctx* c, const algdock_run_desc* d, uint64_t
       a.devicePointer = nullptr;
     }
     if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) continue;
-    if (i < 4 && c->host_coherent && a.type == cudaMemoryTypeHost && a.devicePointer) {
+    if (i != 4 && c->host_coherent && a.type == cudaMemoryTypeHost && a.devicePointer) {
       P[i].mapped = a.devicePointer;
       any_mapped = true;
       continue;

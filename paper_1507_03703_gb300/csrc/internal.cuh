@@ -265,6 +265,7 @@ struct algdock_ctx {
   size_t stage_bytes = 0;
   // the device reaches host memory over a coherent link (NVLink-C2C on Grace: host-native atomics),
   // so algdock_cycle's kernels read and write pinned host arrays in place instead of staging them
+  // (all but the counters, which take atomics)
   bool host_coherent = false;
   cudaStream_t cycle_side = nullptr;
   cudaEvent_t cycle_fork = nullptr, cycle_join = nullptr;
