@@ -242,11 +242,11 @@ struct GatherPlan {
 
   void optimise() {
     cost.resize(ng);
-    int cur = 0, floor = 0;
+    int cur = 0, lower = 0;  // lower: one wavefront per load that reads anything
     for (int g = 0; g < ng; ++g) {
       cost[g] = group_cost(g);
       cur += cost[g];
-      floor += cost[g] > 0 ? 1 : 0;
+      lower += cost[g] > 0 ? 1 : 0;
     }
     wf_before = cur;
     int best = cur;
@@ -262,7 +262,7 @@ struct GatherPlan {
       add(gather_group(e));
       if (part_grp[e] >= 0) add(part_grp[e]);
     };
-    for (long it = 0; it < iters && best > floor; ++it) {
+    for (long it = 0; it < iters && best > lower; ++it) {
       aff.clear();
       // half of the entry and term swaps start from a conflicted load: an entry of a gather load,
       // or a term of a position load
