@@ -260,18 +260,19 @@ def measured_peaks():
         return {}
 
 
-# DRAM bytes (read + write) per launch of a kernel from one ncu capture of the bench command, with
-# a fingerprint of the sources the kernel was built from at the time: the figure is reported only
-# while those sources are unchanged.
+# DRAM bytes (read + write) and warp instructions per launch of a kernel from one ncu capture of
+# the bench command, with a fingerprint of the sources the kernel was built from at the time: the
+# figures are reported only while those sources are unchanged.
 NCU_TRAFFIC = {
-    "hmc_kernel": {"bytes_per_launch": 11305984,
+    "hmc_kernel": {"bytes_per_launch": 11305984, "warp_instructions_per_launch": 1310285150,
                    "sources": ("hmc.cu", "internal.cuh", "grids.cu"),
                    "sha256": "4534b47f86cbe5ae0b75a683b4845996a3f3f4ea7aad13c7c2c1e305a693bec0"},
 }
 
 
-def captured_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from its ncu capture, or None if its sources changed."""
+def captured_traffic(kernel, field="bytes_per_launch"):
+    """A per-launch figure of `kernel` from its ncu capture (DRAM bytes by default), or None if its
+    sources changed."""
     import hashlib
     rec = NCU_TRAFFIC.get(kernel)
     if rec is None:
@@ -280,7 +281,7 @@ def captured_traffic(kernel):
     for f in rec["sources"]:
         with open(os.path.join(ROOT, "paper_1507_03703_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return rec["bytes_per_launch"] if h.hexdigest() == rec["sha256"] else None
+    return rec.get(field) if h.hexdigest() == rec["sha256"] else None
 
 
 def learned_vs_plain(ctx, sys_, stream, dev, chains=2048, burn=20, data_cycles=489, train_iter=500, cmp_cycles=200,
@@ -968,6 +969,17 @@ def main():
                 "flops_per_launch": fl, "flops_rule": "(15 N_a + 60) per atom evaluation",
                 "frac_with_term_by_term_count": fl_detail / (hmc_avg * 1e-3) / 1e12 / peak_tflops}
 
+    # the same kernel against the SMs' issue rate (four warp instructions per cycle per SM): the
+    # instructions of its ncu capture over the launch time, while the kernel's sources are unchanged
+    inst = captured_traffic("hmc_kernel", "warp_instructions_per_launch")
+    issue_peak = 4 * n_sm * sm_max * 1e6
+    roofline_issue = None
+    if inst:
+        roofline_issue = {"bound": "issue", "achieved": inst / (hmc_avg * 1e-3), "peak": issue_peak,
+                          "unit": "warp instructions/s", "frac": inst / (hmc_avg * 1e-3) / issue_peak,
+                          "kernel": "hmc_kernel", "warp_instructions_per_launch": inst,
+                          "peak_source": "%d SMs x 4 schedulers x %.0f MHz" % (n_sm, sm_max)}
+
     # the same kernel against the L2 gather roofline: useful lattice bytes per launch over the
     # measured rate of random 8-corner gathers from the same lattices
     gbytes = gather_bytes_per_launch(alpha, N_CHAINS, lig.n_atoms, N_VV)
@@ -1049,7 +1061,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(sys_, world),
-        "roofline": roofline, "roofline_gather": roofline_gather, "e2e": e2e,
+        "roofline": roofline, "roofline_gather": roofline_gather, "roofline_issue": roofline_issue, "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk, "breakdown_ms": {"hmc": hmc_avg, "exchange_both_legs_beside_snapshot": sum(ex_ms) / len(ex_ms),
                                         "snapshot_tail_after_exchange": sum(ukn_ms) / len(ukn_ms),
