@@ -138,7 +138,8 @@ __host__ __device__ inline size_t fast_smem_bytes(int K, int n_sweeps, int max_s
          (size_t)K * K * sizeof(float2) +                             // shifted u and its magnitude bound
          (size_t)n_sweeps * (smax > 0 ? smax : 1) * K * sizeof(float) +  // log-uniforms
          (size_t)max_sep * K * sizeof(unsigned) +                     // accept counters
-         (size_t)2 * kFastMaxK * sizeof(int);                         // the team sweep's slot buffers
+         (size_t)2 * kFastMaxK * sizeof(int) +                        // the team sweep's slot buffers
+         (size_t)n_sweeps * sizeof(int);                              // sweeps' log-uniforms ready
 }
 
 // The fast kernels' shared memory.
@@ -151,6 +152,7 @@ struct FastTables {
   float* lu;      // [n_sweeps][smax][K]
   unsigned* acc;  // [max_sep][K]
   int* cbuf;      // [2][kFastMaxK]: configurations published by the team sweep, by phase parity
+  int* ready;     // [n_sweeps]: drawing warps done with each sweep's log-uniforms
 };
 __device__ inline FastTables fast_carve(unsigned char* smem, int K, int n_sweeps, int sm1, int max_sep) {
   FastTables T;
@@ -162,6 +164,7 @@ __device__ inline FastTables fast_carve(unsigned char* smem, int K, int n_sweeps
   T.lu = (float*)(T.fm + (size_t)K * K);
   T.acc = (unsigned*)(T.lu + (size_t)n_sweeps * sm1 * K);
   T.cbuf = (int*)(T.acc + (size_t)max_sep * K);
+  T.ready = T.cbuf + 2 * kFastMaxK;
   return T;
 }
 
@@ -191,7 +194,54 @@ __device__ __noinline__ bool exact_swap(const ExArgs& A, const double* s_st, con
 // decision is taken from the estimate when its margin to the boundary ln u = -d exceeds
 // 1e-4 + 1e-6 sum(m); otherwise from the FP64 test itself, so every decision is the FP64 one.
 // The tables of one ladder are built by all threads of the block (ends with a block barrier).
-__device__ inline void fast_tables(const ExArgs& A, const FastTables& T, int K, int smax, uint32_t lid) {
+// Attempt idx's FP32 log-uniform (idx = (sweep smax + s - 1) K + a: pair a, a + s of the sweep).
+__device__ inline float log_uniform(const ExArgs& A, int idx, int K, int smax, uint32_t lid) {
+  const int a = idx % K, ss = idx / K;
+  const int s = ss % smax + 1, sw = ss / smax;
+  if (a + s >= K) return 0.f;
+  const U4 o = philox(A.seed, (uint32_t)((sw * A.max_sep + s - 1) * 65536 + a), lid, A.cycle, kPurposeExchange);
+  // the 53-bit uniform (o.x >> 5) 2^-27 + (o.y >> 6) 2^-53 in FP32: two roundings, 1.2e-7
+  // relative, as good as rounding the FP64 value; zero exactly when the uniform is zero
+  const float uf = __fmaf_rn((float)(o.x >> 5), 7.450580596923828125e-9f, (float)(o.y >> 6) * 1.1102230246251565e-16f);
+  return uf == 0.f ? -INFINITY : __logf(uf);
+}
+
+// The warps that do not sweep draw the log-uniforms of sweeps 1.. while the sweep runs, sweep by
+// sweep; each publishes its share of a sweep by one shared-memory counter (after a block fence).
+__device__ inline void draw_sweeps(const ExArgs& A, const FastTables& T, int K, int smax, uint32_t lid, int first_warp) {
+  const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) - first_warp;
+  const int n_w = (int)(blockDim.x >> 5) - first_warp;
+  const int per = smax * K;
+  for (int sw = 1; sw < A.n_sweeps; ++sw) {
+    for (int idx = sw * per + 32 * w + lane; idx < (sw + 1) * per; idx += 32 * n_w)
+      T.lu[idx] = log_uniform(A, idx, K, smax, lid);
+    __syncwarp();
+    __threadfence_block();
+    if (lane == 0) atomicAdd(&T.ready[sw], 1);
+  }
+}
+
+// Before sweep sw (>= 1): waits, bounded, until all n_w drawing warps have published its
+// log-uniforms; if the wait runs out, the sweeping warp draws them itself (the same values).
+__device__ inline void await_sweep(const ExArgs& A, const FastTables& T, int K, int smax, uint32_t lid, int sw,
+                                   int n_w) {
+  const volatile int* r = T.ready + sw;
+  int spins = 0;
+  while (*r < n_w && spins < (1 << 20)) {
+    __nanosleep(64);
+    ++spins;
+  }
+  __threadfence_block();
+  if (*r < n_w) {
+    const int per = smax * K;
+    for (int idx = sw * per + (threadIdx.x & 31); idx < (sw + 1) * per; idx += 32)
+      T.lu[idx] = log_uniform(A, idx, K, smax, lid);
+    __syncwarp();
+  }
+}
+
+__device__ inline void fast_tables(const ExArgs& A, const FastTables& T, int K, int smax, uint32_t lid,
+                                   int n_drawn) {
   const int64_t l = blockIdx.x;
   const int lane = threadIdx.x & 31;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -203,20 +253,11 @@ __device__ inline void fast_tables(const ExArgs& A, const FastTables& T, int K, 
     T.slot[k] = load_slot(A.comps + (l * K + k) * 4);
   }
   for (int i = threadIdx.x; i < A.max_sep * K; i += blockDim.x) T.acc[i] = 0u;
-  const int n_att = A.n_sweeps * smax * K;
-  for (int idx = threadIdx.x; idx < n_att; idx += blockDim.x) {
-    const int a = idx % K, ss = idx / K;
-    const int s = ss % smax + 1, sw = ss / smax;
-    float lu = 0.f;
-    if (a + s < K) {
-      const U4 o = philox(A.seed, (uint32_t)((sw * A.max_sep + s - 1) * 65536 + a), lid, A.cycle, kPurposeExchange);
-      // the 53-bit uniform (o.x >> 5) 2^-27 + (o.y >> 6) 2^-53 in FP32: two roundings, 1.2e-7
-      // relative, as good as rounding the FP64 value; zero exactly when the uniform is zero
-      const float uf = __fmaf_rn((float)(o.x >> 5), 7.450580596923828125e-9f, (float)(o.y >> 6) * 1.1102230246251565e-16f);
-      lu = uf == 0.f ? -INFINITY : __logf(uf);
-    }
-    T.lu[idx] = lu;
-  }
+  for (int i = threadIdx.x; i < A.n_sweeps; i += blockDim.x) T.ready[i] = 0;
+  // the log-uniforms of the first n_drawn sweeps; the team kernels draw the later sweeps' beside
+  // the sweeps (draw_sweeps)
+  const int n_first = min(n_drawn, A.n_sweeps) * smax * K;
+  for (int idx = threadIdx.x; idx < n_first; idx += blockDim.x) T.lu[idx] = log_uniform(A, idx, K, smax, lid);
   __syncthreads();
   {  // every warp forms the minima (fmin skips NaN; a non-finite slot only sends its pairs to FP64)
     double me = INFINITY, msg = INFINITY, mg = INFINITY;
@@ -265,7 +306,8 @@ __global__ void __launch_bounds__(kFastThreads) exchange_fast_kernel(const ExArg
   const int64_t l = blockIdx.x;
   const uint32_t lid = (uint32_t)(A.ladder_offset + l);
   const int lane = threadIdx.x & 31;
-  fast_tables(A, T, K, smax, lid);
+  // every sweep's log-uniforms first: beside a one-warp sweep the drawing warps gained nothing
+  fast_tables(A, T, K, smax, lid, A.n_sweeps);
   if (threadIdx.x >= 32) return;
   int cfg[KG];
   float uo[KG], mo[KG];  // the entry of the slot's own state at its own configuration
@@ -407,13 +449,16 @@ __global__ void __launch_bounds__(kFastThreads) exchange_team_kernel(const ExArg
   const int64_t l = blockIdx.x;
   const uint32_t lid = (uint32_t)(A.ladder_offset + l);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  fast_tables(A, T, K, smax, lid);
+  fast_tables(A, T, K, smax, lid, 1);
   const int k = 32 * warp + lane;
   int cfg = warp < KG && k < K ? A.config_of[l * K + k] : 0;
   const bool bad = warp < KG && k < K && (unsigned)cfg >= (unsigned)K;
   // not a list of slots 0..K-1: every thread leaves, the ladder untouched
   if (__syncthreads_or(bad)) return;
-  if (warp >= KG) return;
+  if (warp >= KG) {
+    if (smax > 0) draw_sweeps(A, T, K, smax, lid, KG);
+    return;
+  }
   const float2 own0 = T.fm[(k < K ? k : 0) * K + cfg];
   float uo = own0.x, mo = own0.y;
   // the slot's role in every phase: bit 2 (s - 1) + colour of `lower` / `active`
@@ -427,6 +472,7 @@ __global__ void __launch_bounds__(kFastThreads) exchange_team_kernel(const ExArg
     }
   int phase = 0;
   for (int sw = 0; sw < A.n_sweeps; ++sw) {
+    if (sw > 0 && smax > 0) await_sweep(A, T, K, smax, lid, sw, (int)(blockDim.x >> 5) - KG);
     const float* lu_sw = T.lu + (size_t)sw * smax * K;
     uint32_t acc_bits = 0;  // bit s - 1: the pair whose lower member is this slot was accepted
     for (int s = 1; s <= smax; ++s) {
