@@ -114,3 +114,42 @@ def test_clock_sampler_file_handling(bench_module, tmp_path, monkeypatch):
     c = bench_module.Clocks(0, str(kept))
     c.start()
     assert c.stop() is None and kept.exists()
+
+
+def test_bpmf_credit_starts_where_the_estimate_stays_in_band(bench_module):
+    """An arm is credited from the first window after which every later window stays within the
+    criterion of the reference, and not at all if its last window is outside."""
+    w = lambda *b: [{"bpmf_kT": v} for v in b]
+    f = bench_module.in_band_from
+    assert f(w(-18.0, -18.8, -18.95, -18.85), -18.9, 0.2) == 1
+    assert f(w(-18.8, -19.2, -18.95, -18.85), -18.9, 0.2) == 2  # left the band once: counted after
+    assert f(w(-17.5, -18.7, -18.84, -19.10, -19.15), -18.9, 0.2) is None  # drifted out at the end
+    assert f(w(-18.9, -18.9), -18.9, 0.2) == 0
+    assert f([], -18.9, 0.2) is None
+
+
+def test_term_by_term_flop_count_of_a_chain(bench_module):
+    """A five-atom chain 0-1-2-3-4: 4 bonds, 3 angles, 2 torsions, and the pairs more than two
+    bonds apart (0-3, 0-4, 1-4), against the stated 26 / 20 / 60 / 100 / 182 flop per pair,
+    bond, angle, torsion and atom."""
+    class Chain:
+        n_atoms = 5
+        bonds = [(0, 1), (1, 2), (2, 3), (3, 4)]
+        angles = [(0, 1, 2), (1, 2, 3), (2, 3, 4)]
+        torsions = [(0, 1, 2, 3), (1, 2, 3, 4)]
+    assert bench_module.flops_per_replica_eval(Chain) == 26 * 3 + 20 * 4 + 60 * 3 + 100 * 2 + 182 * 5
+
+
+def test_captured_figures_follow_the_source_fingerprint(bench_module, monkeypatch):
+    """A captured ncu figure is reported only while the fingerprint of its sources matches."""
+    rec = dict(bench_module.NCU_TRAFFIC["hmc_kernel"])
+    monkeypatch.setitem(bench_module.NCU_TRAFFIC, "hmc_kernel", rec)
+    got = bench_module.captured_traffic("hmc_kernel")
+    assert got in (None, rec["bytes_per_launch"])
+    if got is not None:  # the committed fingerprint matches the committed sources
+        assert bench_module.captured_traffic("hmc_kernel", "warp_instructions_per_launch") == \
+            rec["warp_instructions_per_launch"]
+    rec["sha256"] = "0" * 64
+    assert bench_module.captured_traffic("hmc_kernel") is None
+    assert bench_module.captured_traffic("hmc_kernel", "warp_instructions_per_launch") is None
+    assert bench_module.captured_traffic("no_such_kernel") is None
